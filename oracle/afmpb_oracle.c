@@ -1,0 +1,801 @@
+/*
+ * afmpb_oracle.c -- plain, slow, FP64 CPU oracle for the node-patch boundary-integral
+ * matvec of the linearized Poisson-Boltzmann solver (AFMPB, arXiv 1710.06316).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test-suite, the smoke check and the bench's CPU
+ * baseline may load this library.  It shares no code, header, table or helper with the
+ * CUDA library: it is written directly from the paper's equations.
+ *
+ * What it computes (paper Sec. 2):
+ *   Eq. 3   second-kind BIE for f = phi_ext, h = d phi_ext / dn on the surface S
+ *   Eq. 4-5 node-patch discretisation:
+ *             [ (alpha I + B)   -A         ] [f]   1/eps_out [ sum_k q_k G_pk       ]
+ *             [  D              alpha I - C] [h] =           [ sum_k q_k dG_pk/dn0  ]
+ *           with alpha = 1/(2 eps_bar) + 1/2, eps_bar = eps_out / eps_in
+ *   Eq. 6   A, B, C, D = integrals over the node patch of t of the kernel combinations
+ *           G - u, dG/dn / eps_bar - du/dn, dG/dn0 - du/dn0 / eps_bar,
+ *           (d2G/dn0dn - d2u/dn0dn) / eps_bar, where G = 1/(4 pi r), u = exp(-kappa r)/(4 pi r),
+ *           n = normal at the source t, n0 = normal at the target p.
+ *   Sec. 2 (after Eq. 6): for far pairs the integrand is constant on the patch
+ *           (coefficient = patch area x kernel at the nodes); near pairs are integrated
+ *           over the patch detail.
+ *   Eq. 7   GMRES stop test  |res| <= eps_rel ||b||_2 + eps_abs.
+ *   Sec. 3.4 restarted GMRES following SPARSKIT, no preconditioner; Sec. 5: modified
+ *           Gram-Schmidt with re-orthogonalisation.
+ *
+ * Readings where the paper is silent (each also listed in the design notes):
+ *   R1  node normal  = normalised area-weighted sum of incident facet normals
+ *                      (unless the caller supplies normals).
+ *   R2  patch        = for each incident triangle T = (v, a, b) the quad
+ *                      (v, m_va, c_T, m_vb), split into (v, m_va, c_T), (v, c_T, m_vb);
+ *                      each has area(T)/6 and the facet normal of T (Fig. 1).
+ *   R3  near set     t in N(p) iff t == p or |x_p - x_t| < c_near (rho_p + rho_t),
+ *                      rho_v = largest distance from v to one of its patch vertices.
+ *   R4  near rule    7-point degree-5 Radon rule on each patch sub-triangle, split 1 -> 4
+ *                      while dist(x_p, centroid) < 3 * longest edge, at most 6 times.
+ *   R5  self term    patch projected on the tangent plane of n_p: B_pp = C_pp = 0,
+ *                      A_pp = int (1 - e^{-kr}) / (4 pi r),
+ *                      D_pp = (1/eps_bar) int (1 - e^{-kr}(1 + kr)) / (4 pi r^3),
+ *                      Duffy (polar) map about x_p, 16 x 16 Gauss-Legendre.
+ *   R6  RHS second row uses dG/dn0 (Eq. 4 prints G_pk there; Eq. 3 and Eq. 5 fix it).
+ *   R7  energy       E = 1/2 sum_k q_k phi_reac(r_k) with the interior Green representation
+ *                      phi_reac(r) = sum_t a_t [eps_bar h_t G(r,x_t) - f_t dG/dn_t(r,x_t)],
+ *                      converted with 4 pi K_c, K_c = 332.0636 kcal A / (mol e^2).
+ *   R8  GMRES        x0 = 0; restart = Krylov dimension m; a second Gram-Schmidt pass
+ *                      only when ||w|| dropped below eta ||w_before|| (eta = 1e-3 by
+ *                      default): the paper's inner-product counts (Sec. 5: 77 for 11
+ *                      iterations, 4,803 for 133 with restart 80) equal plain MGS, so the
+ *                      second pass must be rare.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <stdio.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_PI 3.14159265358979323846
+#define ORC_KC 332.0636
+
+typedef struct {
+    int64_t n, nt;
+    double *xyz;          /* [n*3] */
+    int32_t *tri;         /* [nt*3] */
+    double *tri_area;     /* [nt] */
+    double *tri_nrm;      /* [nt*3] unit facet normals */
+    double *area;         /* [n] patch areas */
+    double *nrm;          /* [n*3] node normals */
+    double *rho;          /* [n] patch radius */
+    int64_t *inc_ptr;     /* [n+1] node -> incident triangles */
+    int32_t *inc_tri;     /* [3*nt] */
+    double eps_in, eps_out, kappa, c_near, ebar, alpha;
+    /* quadrature controls (R4, R5) */
+    int max_depth;
+    double refine_ratio;
+    int gl_n;
+    double gl_x[64], gl_w[64];   /* Gauss-Legendre on [0,1] */
+    /* cached near CSR: coefficients of the near rule (quad or self) */
+    int64_t nnz;
+    int64_t *nptr;
+    int32_t *ncol;
+    double *ncoef;        /* [nnz*4] A,B,C,D */
+} orc_ctx;
+
+/* ------------------------------------------------------------------------------ */
+/* small vector helpers                                                            */
+/* ------------------------------------------------------------------------------ */
+static inline double dot3(const double *a, const double *b) { return a[0]*b[0] + a[1]*b[1] + a[2]*b[2]; }
+static inline void sub3(const double *a, const double *b, double *o) { o[0]=a[0]-b[0]; o[1]=a[1]-b[1]; o[2]=a[2]-b[2]; }
+static inline void cross3(const double *a, const double *b, double *o) {
+    o[0] = a[1]*b[2] - a[2]*b[1]; o[1] = a[2]*b[0] - a[0]*b[2]; o[2] = a[0]*b[1] - a[1]*b[0];
+}
+static inline double norm3(const double *a) { return sqrt(dot3(a, a)); }
+static inline double dist3(const double *a, const double *b) { double d[3]; sub3(a, b, d); return norm3(d); }
+
+/* Gauss-Legendre nodes on [-1,1] by Newton iteration on P_n, mapped to [0,1]. */
+static void gauss_legendre01(int n, double *x, double *w) {
+    for (int i = 0; i < n; i++) {
+        double z = cos(ORC_PI * (i + 0.75) / (n + 0.5));
+        double dp = 0.0;
+        for (int it = 0; it < 100; it++) {
+            double p0 = 1.0, p1 = z;
+            for (int k = 2; k <= n; k++) {
+                double pk = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+                p0 = p1; p1 = pk;
+            }
+            /* p1 = P_n(z), p0 = P_{n-1}(z) */
+            dp = n * (z * p1 - p0) / (z * z - 1.0);
+            double dz = p1 / dp;
+            z -= dz;
+            if (fabs(dz) < 1e-16) break;
+        }
+        {
+            double p0 = 1.0, p1 = z;
+            for (int k = 2; k <= n; k++) {
+                double pk = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+                p0 = p1; p1 = pk;
+            }
+            dp = n * (z * p1 - p0) / (z * z - 1.0);
+        }
+        x[i] = 0.5 * (z + 1.0);
+        w[i] = 1.0 / ((1.0 - z * z) * dp * dp);   /* = (2/((1-z^2) P'^2)) / 2 */
+    }
+}
+
+/* ------------------------------------------------------------------------------ */
+/* kernels (Sec. 2, below Eq. 3)                                                   */
+/* d = x_target - y_source.  Outputs the eight kernel values used by Eq. 6:         */
+/*   G, dG/dn, dG/dn0, d2G/dn0dn, u, du/dn, du/dn0, d2u/dn0dn                       */
+/* ------------------------------------------------------------------------------ */
+static void kernels8(double kappa, const double *d, const double *n0, const double *n, double *k8) {
+    double r2 = dot3(d, d);
+    double r = sqrt(r2);
+    double ndn = dot3(n, d);    /* source normal . d */
+    double n0d = dot3(n0, d);   /* target normal . d */
+    double nn0 = dot3(n, n0);
+    double fp = 4.0 * ORC_PI;
+    double G = 1.0 / (fp * r);
+    double G3 = 1.0 / (fp * r * r2);
+    double G5 = 3.0 * G3 / r2;
+    double e = exp(-kappa * r);
+    double kr = kappa * r;
+    /* written so that kappa = 0 reproduces the Laplace values bit for bit */
+    double g1 = (e * (1.0 + kr)) * G3;
+    double g2 = (e * (1.0 + kr + kr * kr / 3.0)) * G5;
+    k8[0] = G;
+    k8[1] = ndn * G3;                           /* grad_y G . n  */
+    k8[2] = -n0d * G3;                          /* grad_x G . n0 */
+    k8[3] = nn0 * G3 - ndn * n0d * G5;
+    k8[4] = e * G;
+    k8[5] = ndn * g1;
+    k8[6] = -n0d * g1;
+    k8[7] = nn0 * g1 - ndn * n0d * g2;
+}
+
+/* Eq. 6 integrands from the eight kernel values. */
+static inline void abcd_from_k8(const double *k8, double ebar, double *o) {
+    o[0] = k8[0] - k8[4];
+    o[1] = k8[1] / ebar - k8[5];
+    o[2] = k8[2] - k8[6] / ebar;
+    o[3] = (k8[3] - k8[7]) / ebar;
+}
+
+/* ------------------------------------------------------------------------------ */
+/* geometry                                                                        */
+/* ------------------------------------------------------------------------------ */
+static void build_geometry(orc_ctx *c, const double *normals) {
+    int64_t n = c->n, nt = c->nt;
+    c->tri_area = (double *)calloc((size_t)nt, sizeof(double));
+    c->tri_nrm = (double *)calloc((size_t)nt * 3, sizeof(double));
+    c->area = (double *)calloc((size_t)n, sizeof(double));
+    c->nrm = (double *)calloc((size_t)n * 3, sizeof(double));
+    c->rho = (double *)calloc((size_t)n, sizeof(double));
+    c->inc_ptr = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
+    c->inc_tri = (int32_t *)calloc((size_t)nt * 3, sizeof(int32_t));
+    for (int64_t t = 0; t < nt; t++) {
+        const double *a = c->xyz + 3 * (int64_t)c->tri[3*t], *b = c->xyz + 3 * (int64_t)c->tri[3*t+1],
+                     *q = c->xyz + 3 * (int64_t)c->tri[3*t+2];
+        double e1[3], e2[3], cr[3];
+        sub3(b, a, e1); sub3(q, a, e2); cross3(e1, e2, cr);
+        double l = norm3(cr);
+        c->tri_area[t] = 0.5 * l;
+        for (int k = 0; k < 3; k++) c->tri_nrm[3*t+k] = cr[k] / l;
+        for (int k = 0; k < 3; k++) c->inc_ptr[c->tri[3*t+k] + 1]++;
+    }
+    for (int64_t v = 0; v < n; v++) c->inc_ptr[v+1] += c->inc_ptr[v];
+    int64_t *fill = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    memcpy(fill, c->inc_ptr, sizeof(int64_t) * (size_t)n);
+    for (int64_t t = 0; t < nt; t++)
+        for (int k = 0; k < 3; k++) c->inc_tri[fill[c->tri[3*t+k]]++] = (int32_t)t;
+    free(fill);
+    /* patch area (R2: each incident triangle contributes area/3), normal (R1), rho (R3) */
+    for (int64_t v = 0; v < n; v++) {
+        double s[3] = {0, 0, 0}, A = 0, rho = 0;
+        const double *xv = c->xyz + 3 * v;
+        for (int64_t j = c->inc_ptr[v]; j < c->inc_ptr[v+1]; j++) {
+            int32_t t = c->inc_tri[j];
+            A += c->tri_area[t] / 3.0;
+            for (int k = 0; k < 3; k++) s[k] += c->tri_area[t] * c->tri_nrm[3*t+k];
+            double cen[3] = {0, 0, 0};
+            for (int k = 0; k < 3; k++) {
+                const double *xk = c->xyz + 3 * (int64_t)c->tri[3*t+k];
+                for (int d = 0; d < 3; d++) cen[d] += xk[d] / 3.0;
+                if (c->tri[3*t+k] != v) {
+                    double m[3];
+                    for (int d = 0; d < 3; d++) m[d] = 0.5 * (xv[d] + xk[d]);
+                    double dm = dist3(m, xv);
+                    if (dm > rho) rho = dm;
+                }
+            }
+            double dc = dist3(cen, xv);
+            if (dc > rho) rho = dc;
+        }
+        c->area[v] = A;
+        c->rho[v] = rho;
+        if (normals) {
+            double l = norm3(normals + 3 * v);
+            for (int k = 0; k < 3; k++) c->nrm[3*v+k] = normals[3*v+k] / l;
+        } else {
+            double l = norm3(s);
+            for (int k = 0; k < 3; k++) c->nrm[3*v+k] = s[k] / l;
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------------ */
+/* public: context                                                                  */
+/* ------------------------------------------------------------------------------ */
+orc_ctx *orc_create(int64_t n, const double *xyz, int64_t nt, const int32_t *tri,
+                    const double *normals, double eps_in, double eps_out, double kappa,
+                    double c_near) {
+    orc_ctx *c = (orc_ctx *)calloc(1, sizeof(orc_ctx));
+    c->n = n; c->nt = nt;
+    c->xyz = (double *)malloc(sizeof(double) * 3 * (size_t)n);
+    memcpy(c->xyz, xyz, sizeof(double) * 3 * (size_t)n);
+    c->tri = (int32_t *)malloc(sizeof(int32_t) * 3 * (size_t)nt);
+    memcpy(c->tri, tri, sizeof(int32_t) * 3 * (size_t)nt);
+    c->eps_in = eps_in; c->eps_out = eps_out; c->kappa = kappa; c->c_near = c_near;
+    c->ebar = eps_out / eps_in;
+    c->alpha = 0.5 / c->ebar + 0.5;
+    c->max_depth = 6;
+    c->refine_ratio = 3.0;
+    c->gl_n = 16;
+    gauss_legendre01(c->gl_n, c->gl_x, c->gl_w);
+    build_geometry(c, normals);
+    return c;
+}
+
+static void free_near(orc_ctx *c) {
+    free(c->nptr); free(c->ncol); free(c->ncoef);
+    c->nptr = NULL; c->ncol = NULL; c->ncoef = NULL; c->nnz = 0;
+}
+
+void orc_destroy(orc_ctx *c) {
+    if (!c) return;
+    free(c->xyz); free(c->tri); free(c->tri_area); free(c->tri_nrm); free(c->area);
+    free(c->nrm); free(c->rho); free(c->inc_ptr); free(c->inc_tri);
+    free_near(c);
+    free(c);
+}
+
+/* Change the near-rule controls (used only by the self-convergence pin). */
+void orc_set_quadrature(orc_ctx *c, int max_depth, double refine_ratio, int gl_n) {
+    if (gl_n > 64) gl_n = 64;
+    c->max_depth = max_depth; c->refine_ratio = refine_ratio; c->gl_n = gl_n;
+    gauss_legendre01(gl_n, c->gl_x, c->gl_w);
+    free_near(c);
+}
+
+void orc_get_geometry(const orc_ctx *c, double *area, double *nrm, double *rho) {
+    if (area) memcpy(area, c->area, sizeof(double) * (size_t)c->n);
+    if (nrm) memcpy(nrm, c->nrm, sizeof(double) * 3 * (size_t)c->n);
+    if (rho) memcpy(rho, c->rho, sizeof(double) * (size_t)c->n);
+}
+
+double orc_alpha(const orc_ctx *c) { return c->alpha; }
+
+/* Mesh check: every directed edge (i,j) must appear exactly once and its reverse exactly
+ * once (closed, edge-manifold, consistently oriented); triangles non-degenerate; signed
+ * volume positive (outward orientation).  Returns 0 if valid, else a positive code:
+ * 1 index out of range, 2 degenerate triangle, 3 open/non-manifold/mis-oriented edge,
+ * 4 inward orientation. */
+static int cmp_edge(const void *a, const void *b) {
+    const int64_t *x = (const int64_t *)a, *y = (const int64_t *)b;
+    return (*x > *y) - (*x < *y);
+}
+int orc_mesh_check(int64_t n, int64_t nt, const int32_t *tri, const double *xyz,
+                   int64_t *euler, double *volume) {
+    for (int64_t i = 0; i < 3 * nt; i++) if (tri[i] < 0 || tri[i] >= n) return 1;
+    double vol = 0;
+    for (int64_t t = 0; t < nt; t++) {
+        int32_t a = tri[3*t], b = tri[3*t+1], q = tri[3*t+2];
+        if (a == b || b == q || a == q) return 2;
+        double e1[3], e2[3], cr[3];
+        sub3(xyz + 3*(int64_t)b, xyz + 3*(int64_t)a, e1); sub3(xyz + 3*(int64_t)q, xyz + 3*(int64_t)a, e2);
+        cross3(e1, e2, cr);
+        if (norm3(cr) == 0.0) return 2;
+        vol += dot3(xyz + 3*(int64_t)a, cr) / 6.0;
+    }
+    int64_t ne = 3 * nt;
+    int64_t *dir = (int64_t *)malloc(sizeof(int64_t) * (size_t)ne);
+    int64_t *rev = (int64_t *)malloc(sizeof(int64_t) * (size_t)ne);
+    for (int64_t t = 0; t < nt; t++)
+        for (int k = 0; k < 3; k++) {
+            int64_t i = tri[3*t+k], j = tri[3*t+(k+1)%3];
+            dir[3*t+k] = i * n + j;
+            rev[3*t+k] = j * n + i;
+        }
+    qsort(dir, (size_t)ne, sizeof(int64_t), cmp_edge);
+    qsort(rev, (size_t)ne, sizeof(int64_t), cmp_edge);
+    int bad = 0;
+    for (int64_t i = 0; i < ne; i++) {
+        if (i > 0 && dir[i] == dir[i-1]) { bad = 1; break; }
+        if (dir[i] != rev[i]) { bad = 1; break; }
+    }
+    free(dir); free(rev);
+    if (bad) return 3;
+    if (euler) *euler = n - ne / 2 + nt;
+    if (volume) *volume = vol;
+    if (vol <= 0) return 4;
+    return 0;
+}
+
+/* ------------------------------------------------------------------------------ */
+/* coefficient rules                                                                */
+/* ------------------------------------------------------------------------------ */
+/* Far rule (Sec. 2 after Eq. 6): integrand constant on the patch of t. */
+static void point_coeffs(const orc_ctx *c, int64_t p, int64_t t, double *o) {
+    double d[3], k8[8];
+    sub3(c->xyz + 3*p, c->xyz + 3*t, d);
+    kernels8(c->kappa, d, c->nrm + 3*p, c->nrm + 3*t, k8);
+    abcd_from_k8(k8, c->ebar, o);
+    for (int k = 0; k < 4; k++) o[k] *= c->area[t];
+}
+
+/* 7-point degree-5 rule of Radon on a triangle: barycentric points and weights
+ * (weights sum to 1; multiply by the area). */
+static void radon7(double *bary, double *w) {
+    double s15 = sqrt(15.0);
+    double a1 = (6.0 - s15) / 21.0, a2 = (6.0 + s15) / 21.0;
+    double w1 = (155.0 - s15) / 1200.0, w2 = (155.0 + s15) / 1200.0;
+    double pts[7][3] = {
+        {1.0/3, 1.0/3, 1.0/3},
+        {a1, a1, 1 - 2*a1}, {a1, 1 - 2*a1, a1}, {1 - 2*a1, a1, a1},
+        {a2, a2, 1 - 2*a2}, {a2, 1 - 2*a2, a2}, {1 - 2*a2, a2, a2}};
+    double ww[7] = {9.0/40, w1, w1, w1, w2, w2, w2};
+    for (int i = 0; i < 7; i++) { for (int k = 0; k < 3; k++) bary[3*i+k] = pts[i][k]; w[i] = ww[i]; }
+}
+
+/* Near rule R4 over one flat triangle (v0,v1,v2) with source normal ns, target x/n0.
+ * Recursive 1 -> 4 refinement. Accumulates A,B,C,D into acc. */
+static void tri_quad_rec(const orc_ctx *c, const double *x, const double *n0,
+                         const double *v0, const double *v1, const double *v2,
+                         const double *ns, int depth, double *acc) {
+    double cen[3], e01[3], e12[3], e20[3];
+    for (int k = 0; k < 3; k++) cen[k] = (v0[k] + v1[k] + v2[k]) / 3.0;
+    sub3(v1, v0, e01); sub3(v2, v1, e12); sub3(v0, v2, e20);
+    double diam = fmax(norm3(e01), fmax(norm3(e12), norm3(e20)));
+    if (depth < c->max_depth && dist3(x, cen) < c->refine_ratio * diam) {
+        double m01[3], m12[3], m20[3];
+        for (int k = 0; k < 3; k++) {
+            m01[k] = 0.5 * (v0[k] + v1[k]); m12[k] = 0.5 * (v1[k] + v2[k]); m20[k] = 0.5 * (v2[k] + v0[k]);
+        }
+        tri_quad_rec(c, x, n0, v0, m01, m20, ns, depth + 1, acc);
+        tri_quad_rec(c, x, n0, m01, v1, m12, ns, depth + 1, acc);
+        tri_quad_rec(c, x, n0, m20, m12, v2, ns, depth + 1, acc);
+        tri_quad_rec(c, x, n0, m01, m12, m20, ns, depth + 1, acc);
+        return;
+    }
+    double cr[3], e02[3];
+    sub3(v2, v0, e02);
+    cross3(e01, e02, cr);
+    double A = 0.5 * norm3(cr);
+    double bary[21], w[7];
+    radon7(bary, w);
+    for (int i = 0; i < 7; i++) {
+        double y[3], d[3], k8[8], o[4];
+        for (int k = 0; k < 3; k++) y[k] = bary[3*i] * v0[k] + bary[3*i+1] * v1[k] + bary[3*i+2] * v2[k];
+        sub3(x, y, d);
+        kernels8(c->kappa, d, n0, ns, k8);
+        abcd_from_k8(k8, c->ebar, o);
+        for (int k = 0; k < 4; k++) acc[k] += A * w[i] * o[k];
+    }
+}
+
+/* The two patch sub-triangles of node v inside triangle t (R2), oriented like t. */
+static void patch_pieces(const orc_ctx *c, int64_t v, int32_t t, double s[2][3][3]) {
+    int k0 = 0;
+    for (int k = 0; k < 3; k++) if (c->tri[3*t+k] == v) k0 = k;
+    const double *xv = c->xyz + 3*v;
+    const double *xa = c->xyz + 3*(int64_t)c->tri[3*t+(k0+1)%3];
+    const double *xb = c->xyz + 3*(int64_t)c->tri[3*t+(k0+2)%3];
+    double ma[3], mb[3], cen[3];
+    for (int k = 0; k < 3; k++) {
+        ma[k] = 0.5 * (xv[k] + xa[k]); mb[k] = 0.5 * (xv[k] + xb[k]);
+        cen[k] = (xv[k] + xa[k] + xb[k]) / 3.0;
+    }
+    for (int k = 0; k < 3; k++) {
+        s[0][0][k] = xv[k]; s[0][1][k] = ma[k]; s[0][2][k] = cen[k];
+        s[1][0][k] = xv[k]; s[1][1][k] = cen[k]; s[1][2][k] = mb[k];
+    }
+}
+
+/* Near rule for t != p: sum over the patch pieces of t. */
+static void quad_coeffs(const orc_ctx *c, int64_t p, int64_t t, double *o) {
+    o[0] = o[1] = o[2] = o[3] = 0;
+    for (int64_t j = c->inc_ptr[t]; j < c->inc_ptr[t+1]; j++) {
+        int32_t T = c->inc_tri[j];
+        double s[2][3][3];
+        patch_pieces(c, t, T, s);
+        for (int q = 0; q < 2; q++)
+            tri_quad_rec(c, c->xyz + 3*p, c->nrm + 3*p, s[q][0], s[q][1], s[q][2],
+                         c->tri_nrm + 3*T, 0, o);
+    }
+}
+
+/* Self term R5: patch of p projected on the tangent plane at x_p, Duffy map about x_p. */
+static void self_coeffs(const orc_ctx *c, int64_t p, double *o) {
+    const double *xp = c->xyz + 3*p, *np = c->nrm + 3*p;
+    double k = c->kappa, fp = 4.0 * ORC_PI;
+    double Asum = 0, Dsum = 0;
+    for (int64_t j = c->inc_ptr[p]; j < c->inc_ptr[p+1]; j++) {
+        int32_t T = c->inc_tri[j];
+        double s[2][3][3];
+        patch_pieces(c, p, T, s);
+        for (int q = 0; q < 2; q++) {
+            double e1[3], e2[3];
+            /* project the two far vertices onto the tangent plane, relative to x_p */
+            for (int v = 1; v <= 2; v++) {
+                double dv[3];
+                sub3(s[q][v], xp, dv);
+                double h = dot3(dv, np);
+                double *e = (v == 1) ? e1 : e2;
+                for (int m = 0; m < 3; m++) e[m] = dv[m] - h * np[m];
+            }
+            double cr[3];
+            cross3(e1, e2, cr);
+            double J = norm3(cr);             /* |e1 x e2| */
+            for (int it = 0; it < c->gl_n; it++) {
+                double tt = c->gl_x[it], wt = c->gl_w[it];
+                double w[3];
+                for (int m = 0; m < 3; m++) w[m] = e1[m] + tt * (e2[m] - e1[m]);
+                double l = norm3(w);
+                for (int is = 0; is < c->gl_n; is++) {
+                    double ss = c->gl_x[is], ws = c->gl_w[is];
+                    double x = k * ss * l;          /* kappa r, r = s l */
+                    /* A: (1 - e^{-kr})/(4 pi r) * (J s)  ->  J (1 - e^{-x}) / (4 pi l) */
+                    double fa = -expm1(-x) / (fp * l);
+                    /* D: (1 - e^{-kr}(1+kr))/(4 pi r^3) * (J s) -> J (1 - e^{-x}(1+x)) / (4 pi s^2 l^3) */
+                    double num;
+                    if (x < 0.05) {
+                        /* sum_{j>=2} (-1)^j (j-1)/j! x^j */
+                        double term = x * x / 2.0, acc = term;
+                        for (int jj = 3; jj < 12; jj++) {
+                            term *= -x / jj * (double)(jj - 1) / (double)(jj - 2);
+                            acc += term;
+                        }
+                        num = acc;
+                    } else {
+                        num = 1.0 - exp(-x) * (1.0 + x);
+                    }
+                    double fd = (ss > 0) ? num / (fp * ss * ss * l * l * l) : 0.0;
+                    Asum += J * wt * ws * fa;
+                    Dsum += J * wt * ws * fd;
+                }
+            }
+        }
+    }
+    o[0] = Asum;
+    o[1] = 0.0;
+    o[2] = 0.0;
+    o[3] = Dsum / c->ebar;
+}
+
+int orc_is_near(const orc_ctx *c, int64_t p, int64_t t) {
+    if (p == t) return 1;
+    return dist3(c->xyz + 3*p, c->xyz + 3*t) < c->c_near * (c->rho[p] + c->rho[t]);
+}
+
+/* Public coefficient access. rule: 0 = far (point) rule, 1 = near rule (self if t == p),
+ * 2 = the rule the definition selects for the pair. */
+void orc_coeffs(const orc_ctx *c, int64_t m, const int64_t *p, const int64_t *t, int rule,
+                double *out4) {
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t i = 0; i < m; i++) {
+        int64_t pp = p[i], tt = t[i];
+        int near = (rule == 1) || (rule == 2 && orc_is_near(c, pp, tt));
+        if (pp == tt) {
+            if (near) self_coeffs(c, pp, out4 + 4*i);
+            else { out4[4*i] = out4[4*i+1] = out4[4*i+2] = out4[4*i+3] = 0; }
+        } else if (near) quad_coeffs(c, pp, tt, out4 + 4*i);
+        else point_coeffs(c, pp, tt, out4 + 4*i);
+    }
+}
+
+/* Near rule over an arbitrary triangle (exposes R4 for pins): integrates the four Eq. 6
+ * integrands over triangle (a,b,q) with source normal ns for target x with normal n0. */
+void orc_tri_quad(const orc_ctx *c, const double *x, const double *n0, const double *a,
+                  const double *b, const double *q, const double *ns, double *out4) {
+    out4[0] = out4[1] = out4[2] = out4[3] = 0;
+    tri_quad_rec(c, x, n0, a, b, q, ns, 0, out4);
+}
+
+/* Same rule applied to every patch piece of the whole surface for an off-surface point x
+ * (target normal n0): the surface integral of the four integrands. */
+void orc_surface_quad(const orc_ctx *c, int64_t m, const double *x, const double *n0, double *out4) {
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t i = 0; i < m; i++) {
+        double acc[4] = {0, 0, 0, 0};
+        for (int64_t v = 0; v < c->n; v++)
+            for (int64_t j = c->inc_ptr[v]; j < c->inc_ptr[v+1]; j++) {
+                int32_t T = c->inc_tri[j];
+                double s[2][3][3];
+                patch_pieces(c, v, T, s);
+                for (int q = 0; q < 2; q++)
+                    tri_quad_rec(c, x + 3*i, n0 + 3*i, s[q][0], s[q][1], s[q][2], c->tri_nrm + 3*T, 0, acc);
+            }
+        for (int k = 0; k < 4; k++) out4[4*i+k] = acc[k];
+    }
+}
+
+/* Kernel values for pin tests: out8 per pair as in kernels8 (d = x - y). */
+void orc_kernel_eval(double kappa, int64_t m, const double *x, const double *n0, const double *y,
+                     const double *n, double *out8) {
+    for (int64_t i = 0; i < m; i++) {
+        double d[3];
+        sub3(x + 3*i, y + 3*i, d);
+        kernels8(kappa, d, n0 + 3*i, n + 3*i, out8 + 8*i);
+    }
+}
+
+/* ------------------------------------------------------------------------------ */
+/* near set and coefficients (brute force over all pairs)                           */
+/* ------------------------------------------------------------------------------ */
+int64_t orc_build_near(orc_ctx *c) {
+    if (c->nptr) return c->nnz;
+    int64_t n = c->n;
+    int64_t *cnt = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
+#pragma omp parallel for schedule(static)
+    for (int64_t p = 0; p < n; p++) {
+        int64_t k = 0;
+        for (int64_t t = 0; t < n; t++) k += orc_is_near(c, p, t);
+        cnt[p + 1] = k;
+    }
+    for (int64_t p = 0; p < n; p++) cnt[p + 1] += cnt[p];
+    c->nnz = cnt[n];
+    c->nptr = cnt;
+    c->ncol = (int32_t *)malloc(sizeof(int32_t) * (size_t)c->nnz);
+    c->ncoef = (double *)malloc(sizeof(double) * 4 * (size_t)c->nnz);
+#pragma omp parallel for schedule(dynamic, 8)
+    for (int64_t p = 0; p < n; p++) {
+        int64_t k = c->nptr[p];
+        for (int64_t t = 0; t < n; t++) {
+            if (!orc_is_near(c, p, t)) continue;
+            c->ncol[k] = (int32_t)t;
+            if (t == p) self_coeffs(c, p, c->ncoef + 4*k);
+            else quad_coeffs(c, p, t, c->ncoef + 4*k);
+            k++;
+        }
+    }
+    return c->nnz;
+}
+
+void orc_get_near(const orc_ctx *c, int64_t *rowptr, int32_t *col, double *coef) {
+    if (rowptr) memcpy(rowptr, c->nptr, sizeof(int64_t) * ((size_t)c->n + 1));
+    if (col) memcpy(col, c->ncol, sizeof(int32_t) * (size_t)c->nnz);
+    if (coef) memcpy(coef, c->ncoef, sizeof(double) * 4 * (size_t)c->nnz);
+}
+
+/* ------------------------------------------------------------------------------ */
+/* matvec (Eq. 5)                                                                   */
+/* ------------------------------------------------------------------------------ */
+/* mode: 0 = the discrete operator of Eq. 5 (near rule on N(p), far rule elsewhere);
+ *       1 = alpha x + far (point) rule for every t != p (no near rule, no self term). */
+static void matvec_row(const orc_ctx *c, int64_t p, const double *x, int mode, int use_cache,
+                       double *y1, double *y2) {
+    int64_t n = c->n;
+    const double *f = x, *h = x + n;
+    double s1 = c->alpha * f[p], s2 = c->alpha * h[p];
+    int64_t kk = use_cache ? c->nptr[p] : 0, kend = use_cache ? c->nptr[p+1] : 0;
+    for (int64_t t = 0; t < n; t++) {
+        double o[4];
+        if (mode == 1) {
+            if (t == p) continue;
+            point_coeffs(c, p, t, o);
+        } else if (use_cache) {
+            if (kk < kend && c->ncol[kk] == t) { memcpy(o, c->ncoef + 4*kk, sizeof(o)); kk++; }
+            else point_coeffs(c, p, t, o);
+        } else {
+            if (t == p) self_coeffs(c, p, o);
+            else if (orc_is_near(c, p, t)) quad_coeffs(c, p, t, o);
+            else point_coeffs(c, p, t, o);
+        }
+        s1 += o[1] * f[t] - o[0] * h[t];
+        s2 += o[3] * f[t] - o[2] * h[t];
+    }
+    *y1 = s1; *y2 = s2;
+}
+
+/* Full matvec y = L x, x = [f; h], y = [y1; y2] (length 2N each). */
+void orc_matvec(orc_ctx *c, const double *x, double *y, int mode) {
+    if (mode == 0) orc_build_near(c);
+    int64_t n = c->n;
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t p = 0; p < n; p++) matvec_row(c, p, x, mode, mode == 0, y + p, y + n + p);
+}
+
+/* Selected rows: y[2*i], y[2*i+1] = rows p = rows[i] of the two blocks. Computes the near
+ * set of each row on the fly (no cached CSR needed). */
+void orc_matvec_rows(const orc_ctx *c, int64_t m, const int64_t *rows, const double *x,
+                     double *y, int mode) {
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t i = 0; i < m; i++) matvec_row(c, rows[i], x, mode, 0, y + 2*i, y + 2*i + 1);
+}
+
+/* Assemble the 2N x 2N matrix of Eq. 5 (row-major), for small N. */
+void orc_assemble(orc_ctx *c, double *M) {
+    orc_build_near(c);
+    int64_t n = c->n, n2 = 2 * n;
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t p = 0; p < n; p++) {
+        double *r1 = M + p * n2, *r2 = M + (n + p) * n2;
+        int64_t kk = c->nptr[p], kend = c->nptr[p+1];
+        for (int64_t t = 0; t < n; t++) {
+            double o[4];
+            if (kk < kend && c->ncol[kk] == t) { memcpy(o, c->ncoef + 4*kk, sizeof(o)); kk++; }
+            else point_coeffs(c, p, t, o);
+            r1[t] = o[1]; r1[n + t] = -o[0];
+            r2[t] = o[3]; r2[n + t] = -o[2];
+        }
+        r1[p] += c->alpha;
+        r2[n + p] += c->alpha;
+    }
+}
+
+/* ------------------------------------------------------------------------------ */
+/* right-hand side (Eq. 5, reading R6) and energy (R7)                              */
+/* ------------------------------------------------------------------------------ */
+void orc_rhs(const orc_ctx *c, int64_t m, const double *axyz, const double *q, double *b) {
+    int64_t n = c->n;
+    double fp = 4.0 * ORC_PI;
+#pragma omp parallel for schedule(static)
+    for (int64_t p = 0; p < n; p++) {
+        double s1 = 0, s2 = 0;
+        const double *xp = c->xyz + 3*p, *np = c->nrm + 3*p;
+        for (int64_t k = 0; k < m; k++) {
+            double d[3];
+            sub3(xp, axyz + 3*k, d);
+            double r = norm3(d);
+            s1 += q[k] / (fp * r);
+            s2 += q[k] * (-dot3(np, d)) / (fp * r * r * r);
+        }
+        b[p] = s1 / c->eps_out;
+        b[n + p] = s2 / c->eps_out;
+    }
+}
+
+/* Reaction potential at the atoms and the polar solvation energy (kcal/mol). */
+double orc_energy(const orc_ctx *c, int64_t m, const double *axyz, const double *q,
+                  const double *f, const double *h, double *phi_reac) {
+    double fp = 4.0 * ORC_PI, E = 0;
+#pragma omp parallel for schedule(static) reduction(+:E)
+    for (int64_t k = 0; k < m; k++) {
+        double s = 0;
+        for (int64_t t = 0; t < c->n; t++) {
+            double d[3];
+            sub3(axyz + 3*k, c->xyz + 3*t, d);
+            double r = norm3(d);
+            double G = 1.0 / (fp * r);
+            double dGdn = dot3(c->nrm + 3*t, d) / (fp * r * r * r);
+            s += c->area[t] * (c->ebar * h[t] * G - f[t] * dGdn);
+        }
+        if (phi_reac) phi_reac[k] = s;
+        E += 0.5 * q[k] * s;
+    }
+    return E * fp * ORC_KC;
+}
+
+/* ------------------------------------------------------------------------------ */
+/* restarted GMRES (Sec. 3.4, Eq. 7), MGS with DGKS re-orthogonalisation            */
+/* ------------------------------------------------------------------------------ */
+static double vdot(int64_t n, const double *a, const double *b) {
+    double s = 0;
+#pragma omp parallel for reduction(+:s) schedule(static)
+    for (int64_t i = 0; i < n; i++) s += a[i] * b[i];
+    return s;
+}
+
+/* matvec provider: dense matrix M (if given) or the matrix-free operator. */
+static void apply_op(orc_ctx *c, const double *M, const double *x, double *y) {
+    int64_t n2 = 2 * c->n;
+    if (M) {
+#pragma omp parallel for schedule(static)
+        for (int64_t i = 0; i < n2; i++) {
+            double s = 0;
+            const double *r = M + i * n2;
+            for (int64_t j = 0; j < n2; j++) s += r[j] * x[j];
+            y[i] = s;
+        }
+    } else {
+        orc_matvec(c, x, y, 0);
+    }
+}
+
+/* Returns 0 on convergence, 1 if max_restart was exhausted. info[0..4] =
+ * iterations, inner products, restarts, final residual estimate, true relative residual. */
+int orc_gmres(orc_ctx *c, const double *M, const double *b, double *x, int m, int max_restart,
+              double rel_tol, double abs_tol, double eta, double *info) {
+    int64_t n2 = 2 * c->n;
+    double *V = (double *)malloc(sizeof(double) * (size_t)n2 * (size_t)(m + 1));
+    double *H = (double *)calloc((size_t)(m + 1) * (size_t)m, sizeof(double));
+    double *cs = (double *)calloc((size_t)m, sizeof(double));
+    double *sn = (double *)calloc((size_t)m, sizeof(double));
+    double *g = (double *)calloc((size_t)m + 1, sizeof(double));
+    double *r = (double *)malloc(sizeof(double) * (size_t)n2);
+    double *yv = (double *)calloc((size_t)m, sizeof(double));
+    int64_t inner = 0;
+    int iters = 0, restarts = 0, converged = 0;
+    double bnorm = sqrt(vdot(n2, b, b));
+    double tol = rel_tol * bnorm + abs_tol;
+    double res = 0;
+    memset(x, 0, sizeof(double) * (size_t)n2);          /* x0 = 0 (R8) */
+    for (int cycle = 0; cycle <= max_restart && !converged; cycle++) {
+        apply_op(c, M, x, r);
+        for (int64_t i = 0; i < n2; i++) r[i] = b[i] - r[i];
+        double beta = sqrt(vdot(n2, r, r)); inner++;
+        if (beta <= tol) { converged = 1; res = beta; break; }
+        if (cycle > 0) restarts++;
+        for (int64_t i = 0; i < n2; i++) V[i] = r[i] / beta;
+        memset(g, 0, sizeof(double) * (size_t)(m + 1));
+        g[0] = beta;
+        int j;
+        for (j = 0; j < m; j++) {
+            double *w = V + (size_t)(j + 1) * n2;
+            apply_op(c, M, V + (size_t)j * n2, w);
+            double before = sqrt(vdot(n2, w, w));
+            for (int i = 0; i <= j; i++) {
+                double hij = vdot(n2, w, V + (size_t)i * n2); inner++;
+                H[i * m + j] = hij;
+                const double *vi = V + (size_t)i * n2;
+                for (int64_t k = 0; k < n2; k++) w[k] -= hij * vi[k];
+            }
+            double after = sqrt(vdot(n2, w, w)); inner++;
+            if (after < eta * before) {                     /* second Gram-Schmidt pass */
+                for (int i = 0; i <= j; i++) {
+                    double hij = vdot(n2, w, V + (size_t)i * n2); inner++;
+                    H[i * m + j] += hij;
+                    const double *vi = V + (size_t)i * n2;
+                    for (int64_t k = 0; k < n2; k++) w[k] -= hij * vi[k];
+                }
+                after = sqrt(vdot(n2, w, w)); inner++;
+            }
+            H[(j + 1) * m + j] = after;
+            if (after > 0) for (int64_t k = 0; k < n2; k++) w[k] /= after;
+            /* Givens rotations */
+            for (int i = 0; i < j; i++) {
+                double a = H[i * m + j], bb = H[(i + 1) * m + j];
+                H[i * m + j] = cs[i] * a + sn[i] * bb;
+                H[(i + 1) * m + j] = -sn[i] * a + cs[i] * bb;
+            }
+            double a = H[j * m + j], bb = H[(j + 1) * m + j];
+            double den = hypot(a, bb);
+            cs[j] = a / den; sn[j] = bb / den;
+            H[j * m + j] = den; H[(j + 1) * m + j] = 0;
+            g[j + 1] = -sn[j] * g[j];
+            g[j] = cs[j] * g[j];
+            res = fabs(g[j + 1]);
+            iters++;
+            if (res <= tol) { j++; converged = 1; break; }
+        }
+        if (j > m) j = m;
+        /* back substitution H y = g */
+        for (int i = j - 1; i >= 0; i--) {
+            double s = g[i];
+            for (int k = i + 1; k < j; k++) s -= H[i * m + k] * yv[k];
+            yv[i] = s / H[i * m + i];
+        }
+        for (int i = 0; i < j; i++) {
+            const double *vi = V + (size_t)i * n2;
+            for (int64_t k = 0; k < n2; k++) x[k] += yv[i] * vi[k];
+        }
+    }
+    apply_op(c, M, x, r);
+    for (int64_t i = 0; i < n2; i++) r[i] = b[i] - r[i];
+    double rt = sqrt(vdot(n2, r, r));
+    if (info) {
+        info[0] = iters; info[1] = (double)inner; info[2] = restarts; info[3] = res;
+        info[4] = rt / bnorm;
+    }
+    free(V); free(H); free(cs); free(sn); free(g); free(r); free(yv);
+    return converged ? 0 : 1;
+}
+
+int orc_num_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

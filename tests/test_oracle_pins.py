@@ -1,0 +1,420 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by mathematics.
+
+Each test ties one part of the oracle to something other than itself: finite
+differences, exact solid angles, Gauss's law, closed-form Born/Kirkwood solutions, a
+dense LU solve, independent high-order quadrature, and the paper's printed numbers.
+A plausible slip anywhere in the oracle (a dropped term, a sign, a transposed
+operand, a wrong normal) fails at least one of them.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synthetic
+from closed_forms import (K_C, born_energy, born_surface, kirkwood_energy, kirkwood_g,
+                          solid_angle)
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def read_golden(name):
+    d = {}
+    for line in open(os.path.join(GOLDEN, name)):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        k, *v = line.split()
+        d[k] = v
+    return d
+
+
+def unit(v):
+    v = np.asarray(v, float)
+    return v / np.linalg.norm(v, axis=-1, keepdims=True)
+
+
+# ---------------------------------------------------------------------------------
+# kernels (Sec. 2, definitions below Eq. 3)
+# ---------------------------------------------------------------------------------
+@pytest.mark.parametrize("kappa", [0.0, 0.104, 1.3])
+def test_kernel_derivatives_match_finite_differences(kappa):
+    rng = np.random.default_rng(1)
+    m = 40
+    x = rng.uniform(-2, 2, (m, 3))
+    y = x + unit(rng.standard_normal((m, 3))) * rng.uniform(0.5, 3.0, (m, 1))
+    n0 = unit(rng.standard_normal((m, 3)))
+    n = unit(rng.standard_normal((m, 3)))
+    k = oracle.kernel_eval(kappa, x, n0, y, n)
+    eps = 1e-5
+    # d/dn at the source y (columns 1, 5) and d/dn0 at the target x (columns 2, 6)
+    kp = oracle.kernel_eval(kappa, x, n0, y + eps * n, n)
+    km = oracle.kernel_eval(kappa, x, n0, y - eps * n, n)
+    np.testing.assert_allclose((kp[:, 0] - km[:, 0]) / (2 * eps), k[:, 1], rtol=1e-7, atol=1e-12)
+    np.testing.assert_allclose((kp[:, 4] - km[:, 4]) / (2 * eps), k[:, 5], rtol=1e-7, atol=1e-12)
+    kp = oracle.kernel_eval(kappa, x + eps * n0, n0, y, n)
+    km = oracle.kernel_eval(kappa, x - eps * n0, n0, y, n)
+    np.testing.assert_allclose((kp[:, 0] - km[:, 0]) / (2 * eps), k[:, 2], rtol=1e-7, atol=1e-12)
+    np.testing.assert_allclose((kp[:, 4] - km[:, 4]) / (2 * eps), k[:, 6], rtol=1e-7, atol=1e-12)
+    # mixed second derivative: d/dn0 of d/dn
+    np.testing.assert_allclose((kp[:, 1] - km[:, 1]) / (2 * eps), k[:, 3], rtol=1e-6, atol=1e-11)
+    np.testing.assert_allclose((kp[:, 5] - km[:, 5]) / (2 * eps), k[:, 7], rtol=1e-6, atol=1e-11)
+
+
+def test_kernel_symmetry_and_kappa_limit():
+    rng = np.random.default_rng(2)
+    x = rng.uniform(-1, 1, (20, 3))
+    y = rng.uniform(2, 3, (20, 3))
+    n = unit(rng.standard_normal((20, 3)))
+    a = oracle.kernel_eval(0.3, x, n, y, n)
+    b = oracle.kernel_eval(0.3, y, n, x, n)
+    np.testing.assert_allclose(a[:, 0], b[:, 0], rtol=1e-15)      # G symmetric
+    np.testing.assert_allclose(a[:, 4], b[:, 4], rtol=1e-15)      # u symmetric
+    np.testing.assert_allclose(a[:, 3], b[:, 3], rtol=1e-13)      # mixed derivative symmetric
+    z = oracle.kernel_eval(0.0, x, n, y, n)
+    np.testing.assert_array_equal(z[:, 0:4], z[:, 4:8])           # kappa = 0: u == G exactly
+    s = oracle.kernel_eval(1e-7, x, n, y, n)
+    np.testing.assert_allclose(s[:, 4:8], s[:, 0:4], rtol=1e-6)   # O(kappa r) approach
+    # G = 1 / (4 pi r) scaled: r G is constant, 4 pi r G = 1
+    r = np.linalg.norm(x - y, axis=1)
+    np.testing.assert_allclose(4 * np.pi * r * a[:, 0], 1.0, rtol=1e-14)
+
+
+# ---------------------------------------------------------------------------------
+# mesh and geometry (Fig. 1 node patch)
+# ---------------------------------------------------------------------------------
+def test_mesh_check_codes():
+    xyz, tri = synthetic.icosphere(2)
+    code, euler, vol = oracle.mesh_check(xyz, tri)
+    assert code == 0 and euler == 2 and vol > 0
+    bad = tri.copy()
+    bad[0] = bad[0][[0, 2, 1]]                          # one flipped triangle
+    assert oracle.mesh_check(xyz, bad)[0] == 3
+    assert oracle.mesh_check(xyz, tri[1:])[0] == 3      # open surface
+    assert oracle.mesh_check(xyz, tri[:, [0, 2, 1]])[0] == 4   # all inward
+    bad = tri.copy()
+    bad[3, 1] = bad[3, 0]
+    assert oracle.mesh_check(xyz, bad)[0] == 2          # degenerate
+    bad = tri.copy()
+    bad[5, 2] = xyz.shape[0]
+    assert oracle.mesh_check(xyz, bad)[0] == 1          # index out of range
+
+
+def test_patch_geometry():
+    mol = synthetic.born_ion(subdiv=3)
+    o = oracle.Oracle.for_molecule(mol)
+    area, nrm, rho = o.geometry()
+    v = mol.xyz[mol.tri]
+    tri_area = 0.5 * np.linalg.norm(np.cross(v[:, 1] - v[:, 0], v[:, 2] - v[:, 0]), axis=1)
+    # patches tile the surface: sum of patch areas == total triangle area
+    assert abs(area.sum() - tri_area.sum()) < 1e-12 * tri_area.sum()
+    # closed surface: sum of area-weighted facet normals vanishes, so does sum a_v n_v
+    # only approximately; the area-weighted facet sum must vanish exactly
+    fn = np.cross(v[:, 1] - v[:, 0], v[:, 2] - v[:, 0])
+    assert np.abs(fn.sum(0)).max() < 1e-12
+    # node normals of a sphere point radially outward
+    radial = unit(mol.xyz)
+    assert np.einsum("ij,ij->i", nrm, radial).min() > 0.999
+    # rho is at least half of every incident edge and at most the longest edge
+    e = np.concatenate([mol.tri[:, [0, 1]], mol.tri[:, [1, 2]], mol.tri[:, [2, 0]]])
+    le = np.linalg.norm(mol.xyz[e[:, 0]] - mol.xyz[e[:, 1]], axis=1)
+    half = np.zeros(mol.n_nodes)
+    np.maximum.at(half, e[:, 0], 0.5 * le)
+    np.maximum.at(half, e[:, 1], 0.5 * le)
+    assert np.all(rho >= half - 1e-14)
+    assert np.all(rho <= le.max())
+
+
+# ---------------------------------------------------------------------------------
+# near rule (Eq. 6 integrals) against exact and independent integrals
+# ---------------------------------------------------------------------------------
+def _ref_tri_integral(kappa, ebar, x, n0, a, b, c, ns, order=48):
+    """Independent product Gauss rule on the collapsed square (Duffy map at vertex a)
+    using the oracle's kernel values only as point evaluations."""
+    g, w = np.polynomial.legendre.leggauss(order)
+    g = 0.5 * (g + 1)
+    w = 0.5 * w
+    S, T = np.meshgrid(g, g, indexing="ij")
+    W = np.outer(w, w)
+    J = np.linalg.norm(np.cross(b - a, c - a))
+    pts = a + S[..., None] * ((b - a) + T[..., None] * (c - b))
+    wts = (W * S * J).ravel()
+    pts = pts.reshape(-1, 3)
+    m = pts.shape[0]
+    k = oracle.kernel_eval(kappa, np.repeat(x[None], m, 0), np.repeat(n0[None], m, 0), pts,
+                           np.repeat(ns[None], m, 0))
+    A = k[:, 0] - k[:, 4]
+    B = k[:, 1] / ebar - k[:, 5]
+    Cc = k[:, 2] - k[:, 6] / ebar
+    D = (k[:, 3] - k[:, 7]) / ebar
+    return np.array([wts @ A, wts @ B, wts @ Cc, wts @ D])
+
+
+@pytest.mark.parametrize("dist", [0.4, 1.0, 3.0])
+def test_near_rule_matches_independent_quadrature(dist):
+    mol = synthetic.born_ion(subdiv=1, kappa=0.7, eps_in=2.0, eps_out=80.0)
+    o = oracle.Oracle.for_molecule(mol)
+    a = np.array([0.0, 0.0, 0.0])
+    b = np.array([1.0, 0.1, 0.0])
+    c = np.array([0.2, 0.9, 0.05])
+    ns = unit(np.cross(b - a, c - a))
+    cen = (a + b + c) / 3
+    x = cen + dist * unit(np.array([0.3, -0.2, 1.0]))
+    n0 = unit(np.array([0.1, 0.5, 1.0]))
+    got = o.tri_quad(x, n0, a, b, c, ns)
+    ref = _ref_tri_integral(mol.kappa, mol.eps_out / mol.eps_in, x, n0, a, b, c, ns)
+    np.testing.assert_allclose(got, ref, rtol=2e-6, atol=1e-9 * np.abs(ref).max())
+
+
+def test_double_layer_equals_exact_solid_angle():
+    """int_T dG/dn_y dS = -Omega_T / (4 pi) for the signed solid angle (Van Oosterom &
+    Strackee).  With eps_bar = 1 and a huge kappa the B integrand is exactly dG/dn."""
+    xyz, tri = synthetic.icosphere(1, radius=1.0)
+    o = oracle.Oracle(xyz, tri, 1.0, 1.0, 1e6)
+    rng = np.random.default_rng(3)
+    for _ in range(25):
+        t = tri[rng.integers(len(tri))]
+        a, b, c = xyz[t[0]], xyz[t[1]], xyz[t[2]]
+        ns = unit(np.cross(b - a, c - a))
+        x = rng.uniform(-0.7, 0.7, 3) * np.array([1, 1, 1])
+        got = o.tri_quad(x, ns, a, b, c, ns)[1]
+        exact = -solid_angle(x, a, b, c) / (4 * np.pi)
+        assert abs(got - exact) < 1e-7 * max(1.0, abs(exact)), (got, exact)
+
+
+def test_gauss_law_over_whole_patch_surface():
+    """Over the union of all node patches (= the closed surface) the double layer of a
+    unit density is -1 inside and 0 outside, exactly (Gauss)."""
+    xyz, tri = synthetic.icosphere(2, radius=1.0)
+    o = oracle.Oracle(xyz, tri, 1.0, 1.0, 1e6)
+    pts = np.array([[0, 0, 0], [0.3, -0.2, 0.5], [0.0, 0.0, 0.85], [1.5, 0, 0], [0, -2.0, 1.0]])
+    n0 = np.tile([0, 0, 1.0], (len(pts), 1))
+    out = o.surface_quad(pts, n0)[:, 1]
+    np.testing.assert_allclose(out, [-1, -1, -1, 0, 0], atol=2e-6)
+
+
+def test_sphere_row_sums_converge_to_exact_integrals():
+    """On a sphere of radius R, for p on the surface: int dG/dn_t = int dG/dn_p = -1/2 and
+    int G = R.  Laplace-only rows (eps_bar = 1, kappa huge) of the assembled operator
+    converge to these as the mesh is refined (first order: flat patches)."""
+    R = 1.0
+    errs = []
+    for s in (2, 3, 4):
+        xyz, tri = synthetic.icosphere(s, radius=R)
+        o = oracle.Oracle(xyz, tri, 1.0, 1.0, 1e5)
+        n = xyz.shape[0]
+        rows = np.arange(0, n, max(1, n // 40))
+        y1, y2 = o.matvec_rows(rows, np.concatenate([np.ones(n), np.zeros(n)]))
+        sumB = y1 - o.alpha
+        z1, z2 = o.matvec_rows(rows, np.concatenate([np.zeros(n), np.ones(n)]))
+        sumA = -z1
+        sumC = o.alpha - z2
+        errs.append([np.abs(sumB + 0.5).max(), np.abs(sumC + 0.5).max(), np.abs(sumA - R).max()])
+    errs = np.array(errs)
+    # at least first-order convergence (error halves as the edge length halves)
+    assert np.all(errs[1:] < 0.6 * errs[:-1])
+    assert np.all(errs[-1] < [0.025, 0.005, 0.003])
+
+
+def test_kappa_zero_makes_A_and_D_vanish():
+    mol = synthetic.born_ion(subdiv=2, kappa=0.0, eps_in=2.0, eps_out=80.0)
+    o = oracle.Oracle.for_molecule(mol)
+    n = mol.n_nodes
+    rng = np.random.default_rng(4)
+    p = rng.integers(0, n, 300)
+    t = rng.integers(0, n, 300)
+    p = np.concatenate([p, np.arange(n)])
+    t = np.concatenate([t, np.arange(n)])       # includes every self term
+    for rule in (o.FAR, o.NEAR, o.AUTO):
+        c = o.coeffs(p, t, rule=rule)
+        if rule == o.FAR:
+            c = c[p != t]
+        assert np.abs(c[:, 0]).max() == 0.0
+        assert np.abs(c[:, 3]).max() == 0.0
+    # and the decoupled f-block: (alpha I + B) f = b1
+    M = o.assemble()
+    assert np.abs(M[n:, :n]).max() == 0.0   # D block
+    assert np.abs(M[:n, n:]).max() == 0.0   # -A block
+
+
+def test_near_rule_self_convergence():
+    """Refining the near rule (one more split level, larger refinement radius, more
+    Gauss points for the self term) changes the near coefficients by < 1e-6 relative."""
+    mol = synthetic.born_ion(subdiv=2, kappa=0.5, eps_in=2.0, eps_out=80.0)
+    o = oracle.Oracle.for_molecule(mol)
+    rp, col, c0 = o.near_csr()
+    rows = np.repeat(np.arange(mol.n_nodes), np.diff(rp))
+    o.set_quadrature(max_depth=8, refine_ratio=5.0, gl_n=32)
+    c1 = o.coeffs(rows, col, rule=o.NEAR)
+    scale = np.abs(c1).max(axis=0)
+    assert (np.abs(c1 - c0).max(axis=0) / scale).max() < 1e-6
+
+
+def test_near_set_is_symmetric_and_contains_neighbours():
+    mol = synthetic.born_ion(subdiv=3)
+    o = oracle.Oracle.for_molecule(mol)
+    rp, col, _ = o.near_csr()
+    n = mol.n_nodes
+    S = np.zeros((n, n), bool)
+    S[np.repeat(np.arange(n), np.diff(rp)), col] = True
+    assert np.array_equal(S, S.T)
+    assert S.diagonal().all()
+    e = np.concatenate([mol.tri[:, [0, 1]], mol.tri[:, [1, 2]]])
+    assert S[e[:, 0], e[:, 1]].all()             # mesh neighbours are always near
+
+
+# ---------------------------------------------------------------------------------
+# assembled operator, GMRES (Sec. 3.4, Eq. 7)
+# ---------------------------------------------------------------------------------
+def test_matvec_paths_agree_with_assembled_matrix():
+    mol = synthetic.kirkwood_sphere(subdiv=2)
+    o = oracle.Oracle.for_molecule(mol)
+    M = o.assemble()
+    x = synthetic.random_unknowns(mol.n_nodes, 0)
+    y = o.matvec(x)
+    np.testing.assert_allclose(y, M @ x, rtol=1e-12, atol=1e-12 * np.abs(y).max())
+    rows = np.array([0, 5, 17, mol.n_nodes - 1])
+    y1, y2 = o.matvec_rows(rows, x)
+    np.testing.assert_allclose(y1, y[rows], rtol=1e-12)
+    np.testing.assert_allclose(y2, y[mol.n_nodes + rows], rtol=1e-12)
+
+
+def test_gmres_matches_dense_lu():
+    mol = synthetic.kirkwood_sphere(subdiv=3)
+    o = oracle.Oracle.for_molecule(mol)
+    M = o.assemble()
+    b = o.rhs(mol.atoms, mol.q)
+    x_lu = np.linalg.solve(M, b)
+    for dense in (M, None):
+        x, info, ok = o.gmres(b, rel_tol=1e-8, dense=dense)
+        assert ok
+        assert np.linalg.norm(x - x_lu) / np.linalg.norm(x_lu) < 1e-7
+        assert info["res_true"] < 1e-7
+
+
+def test_gmres_restart_and_inner_product_count():
+    """Restarted GMRES reaches the same solution; with no second Gram-Schmidt pass the
+    inner-product count is 1 + sum_{j=1..k} (j+1) for k iterations -- the count the paper
+    prints for 1K4R (10 iterations, 66 inner products)."""
+    g = read_golden("gmres_counts.txt")
+    k, ip = int(g["1K4R_3digit"][0]), int(g["1K4R_3digit"][1])
+    assert 1 + sum(j + 1 for j in range(1, k + 1)) == ip
+    mol = synthetic.kirkwood_sphere(subdiv=2)
+    o = oracle.Oracle.for_molecule(mol)
+    b = o.rhs(mol.atoms, mol.q)
+    x_full, info, ok = o.gmres(b, rel_tol=1e-9, eta=0.0)
+    assert ok and info["restarts"] == 0
+    it = info["iters"]
+    assert info["inner"] == 1 + sum(j + 1 for j in range(1, it + 1))
+    x_rs, info2, ok2 = o.gmres(b, rel_tol=1e-9, restart=3, max_restart=50)
+    assert ok2 and info2["restarts"] >= 1
+    assert np.linalg.norm(x_rs - x_full) / np.linalg.norm(x_full) < 1e-7
+
+
+# ---------------------------------------------------------------------------------
+# closed forms: Born ion (configs' smallest case) and Kirkwood sphere
+# ---------------------------------------------------------------------------------
+def test_closed_form_helpers_agree_with_each_other_and_the_paper():
+    # Kirkwood n = 0 term is the Born energy with salt; kappa = 0 gives the classical g_n
+    for kappa in (0.0, 0.104, 0.5):
+        e_k = kirkwood_energy(np.zeros((1, 3)), [1.0], 2.0, 1.0, 80.0, kappa)
+        assert abs(e_k - born_energy(1.0, 2.0, 1.0, 80.0, kappa)) < 1e-10
+    g = kirkwood_g(5, 20.0, 2.0, 80.0, 0.0)
+    n = np.arange(6)
+    np.testing.assert_allclose(g, (n + 1) * (2 - 80) / (n * 2 + (n + 1) * 80), rtol=1e-14)
+    g_small = kirkwood_g(5, 20.0, 2.0, 80.0, 1e-9)
+    np.testing.assert_allclose(g_small, g, rtol=1e-6)
+    # paper's sphere case: analytic -4046 kcal/mol, reproduced by eps_in 2 / eps_out 80
+    p = read_golden("paper_sphere.txt")
+    e = born_energy(float(p["charge_e"][0]), float(p["radius_A"][0]), 2.0, 80.0, 0.0)
+    assert abs(e - float(p["analytic_energy_kcal_mol"][0])) / 4046 < 5e-4
+    # and the paper's relative errors are (computed - analytic) / analytic
+    for key, rkey in (("afmpb_3digit_energy_kcal_mol", "afmpb_3digit_rel_error"),
+                      ("afmpb_6digit_energy_kcal_mol", "afmpb_6digit_rel_error")):
+        rel = abs(float(p[key][0]) - float(p["analytic_energy_kcal_mol"][0])) / 4046
+        assert abs(rel - float(p[rkey][0])) < 1e-4
+
+
+@pytest.mark.parametrize("kappa", [0.0, 0.104])
+def test_born_ion_surface_solution_and_energy(kappa):
+    f_ex, h_ex = born_surface(1.0, 2.0, 80.0, kappa)
+    e_ex = born_energy(1.0, 2.0, 1.0, 80.0, kappa)
+    errs = []
+    for s in (2, 3, 4):
+        mol = synthetic.born_ion(subdiv=s, kappa=kappa)
+        o = oracle.Oracle.for_molecule(mol)
+        r = o.solve(mol.atoms, mol.q)
+        assert r["converged"]
+        errs.append([np.abs(r["f"] / f_ex - 1).max(), np.abs(r["h"] / h_ex - 1).max(),
+                     abs(r["energy"] / e_ex - 1)])
+    errs = np.array(errs)
+    assert np.all(errs[1:, :2] < errs[:-1, :2])     # node-wise O(h) convergence
+    assert errs[-1, 0] < 0.03 and errs[-1, 1] < 0.01
+    assert errs[-1, 2] < 0.005
+
+
+def test_kirkwood_sphere_energy():
+    mol = synthetic.kirkwood_sphere(subdiv=4)
+    o = oracle.Oracle.for_molecule(mol)
+    r = o.solve(mol.atoms, mol.q)
+    assert r["converged"]
+    e_ex = kirkwood_energy(mol.atoms, mol.q, 20.0, 2.0, 80.0, 0.104)
+    assert abs(r["energy"] / e_ex - 1) < 0.005
+
+
+def test_reaction_field_reciprocity():
+    """Green reciprocity: the reaction potential at charge i due to charge j equals the
+    one at j due to i.  A transposed operand in RHS / operator / energy breaks it."""
+    mol = synthetic.kirkwood_sphere(subdiv=3)
+    o = oracle.Oracle.for_molecule(mol)
+    ri = np.array([[3.0, -2.0, 5.0]])
+    rj = np.array([[-6.0, 4.0, -1.0]])
+    phis = []
+    for src, tgt in ((ri, rj), (rj, ri)):
+        b = o.rhs(src, [1.0])
+        x, _, ok = o.gmres(b, rel_tol=1e-10)
+        _, phi = o.energy(tgt, [1.0], x[: mol.n_nodes], x[mol.n_nodes:], return_phi=True)
+        phis.append(phi[0])
+    assert abs(phis[0] - phis[1]) < 0.01 * abs(phis[0])
+
+
+def test_self_term_matches_radial_closed_form():
+    """Self term (reading R5): over the node patch projected on the tangent plane,
+    int_0^R (1 - e^{-kr})/(4 pi r) r dr = (R - (1 - e^{-kR})/k) / (4 pi) and
+    int_0^R (1 - e^{-kr}(1+kr))/(4 pi r^3) r dr = (k - k e^{-kR} - phi(R)/R) / (4 pi),
+    phi(R) = 1 - e^{-kR}(1 + kR).  The angular integral is done along each projected
+    sub-triangle's outer edge with a 64-point Gauss rule."""
+    kappa, ei, eo = 0.8, 2.0, 80.0
+    xyz, tri = synthetic.icosphere(2, radius=3.0)
+    o = oracle.Oracle(xyz, tri, ei, eo, kappa)
+    _, nrm, _ = o.geometry()
+    gx, gw = np.polynomial.legendre.leggauss(64)
+    gx, gw = 0.5 * (gx + 1), 0.5 * gw
+
+    def gA(R):
+        return (R - (1 - np.exp(-kappa * R)) / kappa) / (4 * np.pi)
+
+    def gD(R):
+        phi = 1 - np.exp(-kappa * R) * (1 + kappa * R)
+        return (kappa - kappa * np.exp(-kappa * R) - phi / R) / (4 * np.pi)
+
+    for p in (0, 7, 40, 161):
+        xp, n_p = xyz[p], nrm[p]
+        A = D = 0.0
+        for t in tri[(tri == p).any(axis=1)]:
+            k0 = int(np.where(t == p)[0][0])
+            a, b = xyz[t[(k0 + 1) % 3]], xyz[t[(k0 + 2) % 3]]
+            ma, mb, c = 0.5 * (xp + a), 0.5 * (xp + b), (xp + a + b) / 3
+            for u, v in ((ma, c), (c, mb)):
+                u = (u - xp) - np.dot(u - xp, n_p) * n_p
+                v = (v - xp) - np.dot(v - xp, n_p) * n_p
+                P = u[None] + gx[:, None] * (v - u)[None]
+                R = np.linalg.norm(P, axis=1)
+                jac = np.linalg.norm(np.cross(u, v - u)) / R ** 2
+                A += np.sum(gw * jac * gA(R))
+                D += np.sum(gw * jac * gD(R))
+        got = o.coeffs([p], [p], rule=o.NEAR)[0]
+        assert got[1] == 0.0 and got[2] == 0.0
+        assert abs(got[0] - A) < 1e-10 * abs(A)
+        assert abs(got[3] - D / (eo / ei)) < 1e-9 * abs(D / (eo / ei))
