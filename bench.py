@@ -1,0 +1,374 @@
+#!/usr/bin/env python
+"""Benchmark: FMM-accelerated node-patch matvec throughput (Mnode/s) on one GB300.
+
+Workload: the Kirkwood sphere -- radius 20 A, 64 seeded charges uniform in r < 16 A with
+q ~ U(-1, 1), icosphere subdivision 7 (163,842 nodes, 327,680 triangles),
+eps_in = 2, eps_out = 80, kappa = 0.104 / A, Chebyshev FMM order 6.  Synthetic input;
+the paper's molecules (3K1Q, 1K4R) are not available.
+
+A step is one product y = L x of the discretised operator (Eq. 5): gather, P2M, M2M,
+M2L, P2L, L2L, L2P, P2P, near-field correction and assembly, scatter -- the whole
+per-iteration hot path of the solver.  Timing: CUDA events on the launching stream
+around each product; the L2 cache (129 MB) is flushed by writing a 512 MB buffer
+between timed products (outside the events).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+Under torchrun (N > 1) every rank runs an independent replica of the workload on its
+own GPU (the product needs no exchange between GPUs here); value = nodes processed by
+all ranks / max-over-ranks time.  --impl reference times the FP64 CPU oracle (dense
+direct summation, test infrastructure) on row samples of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "FMM matvec Mnode/s; solves/s, p50/p99 latency vs plain GPU at <=1e-4 dG error"
+UNIT = "Mnode/s"
+FLUSH_BYTES = 512 << 20
+CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+def workload(name):
+    import synthetic
+    if name == "kirkwood":
+        return synthetic.kirkwood_sphere()
+    if name == "born":
+        return synthetic.born_ion()
+    if name == "paper_sphere":
+        return synthetic.paper_sphere()
+    raise SystemExit("unknown workload " + name)
+
+
+def workload_desc(mol):
+    return {"workload": "%s: %d nodes, %d triangles, %d charges, eps %g/%g, kappa %g"
+            % (mol.name, mol.n_nodes, mol.n_tris, len(mol.q), mol.eps_in, mol.eps_out, mol.kappa)}
+
+
+# ------------------------------------------------------------------------------------
+# clocks during the timed region
+# ------------------------------------------------------------------------------------
+class ClockSampler:
+    def __init__(self, gpu_index):
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.proc = None
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=" + CLOCK_FIELDS, "--format=csv,noheader,nounits",
+                 "-i", str(gpu_index), "-lms", "100"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        pw = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(pw) if pw else None}
+
+
+# ------------------------------------------------------------------------------------
+# roofline of the dominant stage
+# ------------------------------------------------------------------------------------
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "sm_max_mhz": 2070.0}, "fallback"
+
+
+def fp32_peak_tflops(sm_max_mhz):
+    # 152 SMs x 128 FP32 lanes x 2 flop per FMA x max SM clock
+    return 152 * 128 * 2 * sm_max_mhz * 1e6 / 1e12
+
+
+# FP32 operations per source-target pair in the P2P kernel, counted from its source
+# (an FMA counts 2 flop): distance 9, rsqrt + products 6, dot products 15, Laplace
+# terms 16, Yukawa terms 26.
+P2P_FLOP_PER_PAIR = 72
+
+
+def ncu_traffic(kernel):
+    """Per-launch DRAM bytes from the committed ncu summary, if it is still current."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    if not os.path.exists(p):
+        return None
+    import hashlib
+    src = os.path.join(ROOT, "paper_1710_06316_gb300", "csrc")
+    h = hashlib.sha1()
+    for f in sorted(os.listdir(src)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(src, f), "rb").read())
+    digest = h.hexdigest()[:12]
+    for line in open(p):
+        t = line.split()
+        if len(t) >= 3 and not line.startswith("#") and t[0] == kernel:
+            return float(t[1]) if t[2] == digest else None
+    return None
+
+
+def roofline(prof, info, n, order, peaks, kind):
+    stages = {name: (ms, launches) for name, ms, launches in prof["stages"]}
+    name, (ms, launches) = max(stages.items(), key=lambda kv: kv[1][0])
+    n3 = order ** 3
+    sm_max = peaks.get("sm_max_mhz", 2070.0)
+    if name == "m2l":
+        flop = 2.0 * n3 * n3 * info["n_m2l_pairs"] * 2      # Laplace + Yukawa
+        achieved = flop / (ms * 1e-3) / 1e12
+        peak = fp32_peak_tflops(sm_max)
+        out = {"bound": "alu", "kernel": "k_m2l (FP32 FMA)", "unit": "TFLOP/s",
+               "peak_kind": "FP32 FMA: 152 SM x 128 lanes x 2 x %.0f MHz" % sm_max}
+    elif name == "p2p":
+        flop = float(P2P_FLOP_PER_PAIR) * info["n_p2p_pairs"]
+        achieved = flop / (ms * 1e-3) / 1e12
+        peak = fp32_peak_tflops(sm_max)
+        out = {"bound": "alu", "kernel": "k_p2p (FP32 FMA + MUFU)", "unit": "TFLOP/s",
+               "peak_kind": "FP32 FMA: 152 SM x 128 lanes x 2 x %.0f MHz" % sm_max}
+    else:   # combine / near SpMV and the rest are memory-bound
+        byts = info["nnz_near"] * 20.0 + n * (8 + 16 + 16 + 8)
+        achieved = byts / (ms * 1e-3) / 1e9
+        peak = peaks["hbm_gbs"]
+        out = {"bound": "hbm", "kernel": "k_" + name, "unit": "GB/s",
+               "peak_kind": "measured copy bandwidth"}
+    out.update({"stage": name, "achieved": round(achieved, 3), "peak": round(peak, 3),
+                "frac": round(achieved / peak, 4), "ms_per_launch": round(ms, 5),
+                "traffic": ncu_traffic(name), "peak_source": kind,
+                "stage_ms": {k: round(v[0], 5) for k, v in stages.items()}})
+    return out
+
+
+# ------------------------------------------------------------------------------------
+# oracle timing (CPU)
+# ------------------------------------------------------------------------------------
+def oracle_rows_rate(mol, rows_target_s=12.0, max_rows=200000):
+    """Oracle product rows per second on the host cores: (rows/s, cores, sample text)."""
+    import numpy as np
+
+    import oracle
+    import synthetic
+    o = oracle.Oracle.for_molecule(mol)
+    x = synthetic.smooth_unknowns(mol.xyz, 1)
+    rng = np.random.default_rng(0)
+    rows = rng.choice(mol.n_nodes, 16, replace=False)
+    t = time.perf_counter()
+    o.matvec_rows(rows, x)
+    dt = time.perf_counter() - t
+    nrow = int(min(max_rows, max(16, rows_target_s / max(dt / 16, 1e-9))))
+    rows = rng.choice(mol.n_nodes, nrow, replace=False)
+    t = time.perf_counter()
+    o.matvec_rows(rows, x)
+    dt = time.perf_counter() - t
+    return nrow / dt, oracle.num_threads(), nrow, dt
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import numpy as np
+
+    import oracle
+    import synthetic
+    mol = workload(args.workload)
+    o = oracle.Oracle.for_molecule(mol)
+    x = synthetic.smooth_unknowns(mol.xyz, 1)
+    rng = np.random.default_rng(0)
+    rows_per_step = args.ref_rows
+    for _ in range(args.warmup):
+        o.matvec_rows(rng.choice(mol.n_nodes, rows_per_step, replace=False), x)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.matvec_rows(rng.choice(mol.n_nodes, rows_per_step, replace=False), x)
+    dt = time.perf_counter() - t0
+    value = rows_per_step * args.steps / dt / 1e6
+    cores = oracle.num_threads()
+    sample = ("%d random rows of the %d-node product per step (FP64 direct sum over all %d "
+              "sources per row, near rule on the fly); value = rows/s = full-product Mnode/s"
+              % (rows_per_step, mol.n_nodes, mol.n_nodes))
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_desc(mol), "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------------------------
+# GPU arm
+# ------------------------------------------------------------------------------------
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    import paper_1710_06316_gb300 as pb
+    import synthetic
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    # a real (non-legacy) stream: the library queues all its work on it, so the CUDA
+    # events below bracket the product itself
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+
+    mol = workload(args.workload)
+    h = pb.Handle.for_molecule(mol, order=args.order, tol=1e-6, leaf_cap=args.leaf_cap,
+                               precision=args.precision, stream=stream.cuda_stream)
+    info = h.info()
+    n = mol.n_nodes
+    x = torch.tensor(synthetic.smooth_unknowns(mol.xyz, 1).astype(np.float32), device=dev)
+    y = torch.empty_like(x)
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    for _ in range(max(args.warmup, 3)):
+        h.matvec(x, y)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device())
+    time.sleep(0.25)
+    t_wall = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        ev[i][0].record(stream)
+        h.matvec(x, y)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    if dist:
+        dist.barrier()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    ms_step = sum(ms) / len(ms)
+    if dist:
+        t = torch.tensor([ms_step], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    value = world * n / (ms_step * 1e-3) / 1e6
+
+    # end to end through the C ABI with pinned host buffers (H2D + product + D2H)
+    xh = x.cpu().pin_memory()
+    yh = torch.empty(2 * n, dtype=torch.float32).pin_memory()
+    for _ in range(3):
+        h.matvec_host(xh, yh)
+    e2e_steps = max(5, min(args.steps, 200))
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        h.matvec_host(xh, yh)
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    if dist:
+        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": world * n / e2e_s / 1e6, "unit": UNIT, "h2d_bytes_per_step": 2 * n * 4,
+           "d2h_bytes_per_step": 2 * n * 4, "ms_per_step": e2e_s * 1e3}
+
+    prof = h.profile(reps=5, flush=flush, flush_bytes=FLUSH_BYTES)
+    peaks, kind = measured_peaks()
+    roof = roofline(prof, info, n, args.order, peaks, kind)
+
+    # one full solve + energy (outside the timed region): time to solution
+    f, hh, sinfo = h.solve(raise_on_noconv=False)
+    energy = h.energy() if sinfo["status"] in ("OK", "ENOCONV") else None
+
+    line = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 5),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.precision == 0 else "f32+bf16x3", "data": "synthetic",
+            "config": dict(workload_desc(mol), fmm_order=args.order, leaf_cap=info.get("n_leaves") and args.leaf_cap or 0,
+                           precision=["fp32", "mixed-tc"][args.precision],
+                           l2="flushed between timed products (512 MB write)",
+                           parallelism="replicas" if world > 1 else "single"),
+            "e2e": {k: (round(v, 4) if isinstance(v, float) else v) for k, v in e2e.items()},
+            "roofline": roof,
+            "gpu_launches": int(prof["kernels_per_product"]) * args.steps,
+            "clocks": clk,
+            "ms_graph_profile": round(prof["ms_graph"], 5),
+            "tree": {"boxes": info["n_boxes"], "leaves": info["n_leaves"], "levels": info["n_levels"],
+                     "nnz_near": info["nnz_near"], "p2p_pairs": info["n_p2p_pairs"],
+                     "m2l_pairs": info["n_m2l_pairs"]},
+            "solve": {"status": sinfo["status"], "iters": sinfo["iters"], "ms_setup": round(sinfo["ms_setup"], 2),
+                      "ms_gmres": round(sinfo["ms_gmres"], 2), "res_true": sinfo["res_true"],
+                      "energy_kcal_mol": energy}}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, cores, nrow, dt = oracle_rows_rate(mol, rows_target_s=args.cpu_seconds)
+        line["cpu_baseline"] = {"value": round(rate / 1e6, 6), "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": "%d random rows of the product in %.1f s (FP64 direct sum, O(N) per "
+                                          "row, near rule on the fly); rows/s = full-product Mnode/s" % (nrow, dt)}
+    h.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="kirkwood", choices=["kirkwood", "born", "paper_sphere"])
+    ap.add_argument("--order", type=int, default=6)
+    ap.add_argument("--leaf-cap", type=int, default=0)
+    ap.add_argument("--precision", type=int, default=0, choices=[0, 1])
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-rows", type=int, default=48)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

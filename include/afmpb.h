@@ -1,0 +1,230 @@
+/*
+ * afmpb.h -- C ABI of the GB300 node-patch Poisson-Boltzmann boundary-integral library.
+ *
+ * The library solves the linearized Poisson-Boltzmann equation (paper Sec. 2, Eq. 2) in
+ * its second-kind boundary-integral form (Eq. 3), discretised by the node-patch scheme
+ * (Eq. 4-6, Fig. 1):
+ *
+ *      [ alpha I + B      -A        ] [f]     1   [ sum_k q_k G(x_p, r_k)        ]
+ *      [ D           alpha I - C    ] [h]  = ---- [ sum_k q_k dG/dn0(x_p, r_k)   ]     (Eq. 5)
+ *                                           eps_out
+ *
+ * with alpha = 1/(2 eps_bar) + 1/2, eps_bar = eps_out / eps_in, G = 1/(4 pi r),
+ * u = exp(-kappa r)/(4 pi r), f = exterior potential and h = its outward normal
+ * derivative on the surface nodes.  A, B, C, D are the patch integrals of Eq. 6: near
+ * pairs are integrated over the patch detail once at create time, far pairs use the
+ * node values (integrand constant over the patch), and the far sums are evaluated with
+ * an adaptive fast multipole method that carries the Laplace and Yukawa single- and
+ * double-layer potentials and their normal derivatives in one tree pass (the four FMM
+ * calls of the solution flow in Sec. 2, step 3b).  The linear system is solved by
+ * restarted GMRES (Sec. 3.4) with the stop test of Eq. 7.
+ *
+ * Conventions
+ *  - Every call returns an afmpb_status and never aborts.  On failure the handle's
+ *    afmpb_last_error() string says why (thread-local string when the handle is NULL).
+ *  - Lengths are in Angstrom, charges in units of e, kappa in 1/Angstrom, energies in
+ *    kcal/mol.
+ *  - "Caller order" is the node order of the mesh passed to afmpb_create.  The
+ *    unknown vector is x = [f; h] (length 2N), the product y = [y1; y2] (length 2N).
+ *  - Host pointers are read during the call only; the library copies what it keeps.
+ *    Device pointers must stay valid until the work queued on the handle's stream has
+ *    completed.
+ *  - A handle is not thread-safe.  Use one handle per host thread.
+ *  - All GPU work of a handle runs on its stream (afmpb_options.stream, or a stream the
+ *    handle creates when that field is NULL).  The handle owns all device memory it
+ *    allocates until afmpb_destroy.
+ */
+#ifndef AFMPB_H
+#define AFMPB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct afmpb_t afmpb_t;
+
+typedef enum {
+    AFMPB_OK = 0,
+    AFMPB_EINVAL = 1,    /* invalid argument (NULL pointer, size, parameter range)   */
+    AFMPB_EMESH = 2,     /* mesh not closed, not edge-manifold, mis-oriented,
+                            degenerate triangle, or index out of range               */
+    AFMPB_ENOMEM = 3,    /* device or host allocation failed                         */
+    AFMPB_ECUDA = 4,     /* a CUDA runtime call failed (message has the CUDA error)  */
+    AFMPB_ENOCONV = 5,   /* GMRES did not converge within max_restart; best iterate kept */
+    AFMPB_ETIMEOUT = 6,  /* a bounded device wait expired                            */
+    AFMPB_EBUSY = 7,     /* operation refused while other work owns the handle       */
+    AFMPB_ESTATE = 8     /* call out of order (e.g. energy before a successful solve) */
+} afmpb_status;
+
+/* Surface mesh (host memory).  Triangles are counter-clockwise when seen from the
+ * solvent, so that (b - a) x (c - a) points outward (Eq. 2: n points to the solvent). */
+typedef struct {
+    int64_t n_nodes;
+    int64_t n_tris;
+    const double *xyz;      /* [n_nodes * 3] node positions                          */
+    const int32_t *tri;     /* [n_tris * 3] node indices, 0-based                     */
+    const double *normals;  /* optional [n_nodes * 3] unit outward node normals; NULL =
+                               normalised area-weighted mean of incident facet normals */
+} afmpb_mesh;
+
+/* Point charges of the molecule (host memory), Eq. 1-2: q_k at r_k. */
+typedef struct {
+    int64_t n;
+    const double *xyz;      /* [n * 3] */
+    const double *q;        /* [n]     */
+} afmpb_charges;
+
+/* Options; a zero-initialised struct selects every default. */
+typedef struct {
+    int leaf_cap;        /* most nodes in a leaf box of the octree (default 48)          */
+    int restart;         /* GMRES Krylov dimension m (default 80, Sec. 5)                */
+    int max_restart;     /* GMRES restarts allowed (default 5, Sec. 5)                   */
+    double abs_tol;      /* eps_abs of Eq. 7 (default 0)                                 */
+    int precision;       /* 0 = FP32 FMM; 1 = mixed: M2L on the tensor cores (BF16 split
+                            into three products, FP32 accumulation)                      */
+    double near_c;       /* near-set factor c: t is near p when
+                            |x_p - x_t| < c (rho_p + rho_t), rho = patch radius (default 2) */
+    void *stream;        /* cudaStream_t to run on, or NULL                              */
+    int max_level;       /* deepest octree level (default and maximum 20)                */
+} afmpb_options;
+
+/* Solve report. */
+typedef struct {
+    int iters;             /* Arnoldi steps over all cycles                             */
+    int restarts;          /* restart cycles after the first                            */
+    double res_est;        /* final Givens residual estimate |g_{j+1}|                  */
+    double res_true;       /* ||b - L x|| / ||b|| with one more product                 */
+    double bnorm;          /* ||b||_2                                                    */
+    double ms_setup;       /* time spent in afmpb_create (host clock)                   */
+    double ms_matvec_total;/* time inside products during the solve (CUDA events)       */
+    double ms_gmres;       /* time of the whole solve (CUDA events)                     */
+    int64_t nnz_near;      /* stored near-field pairs (incl. the diagonal)              */
+    int64_t n_boxes;       /* octree boxes                                               */
+} afmpb_solve_info;
+
+/* Structure sizes (for tests, tooling and the memory estimator). */
+typedef struct {
+    int64_t n_nodes, n_tris, n_atoms;
+    int64_t n_boxes, n_leaves, n_levels;
+    int64_t nnz_near;
+    int64_t n_list_u, n_list_v, n_list_w, n_list_x;   /* total entries of lists 1-4    */
+    int64_t n_p2p_pairs;       /* sum over targets of their P2P sources (lists 1 and 3)  */
+    int64_t n_m2l_pairs;       /* V-list (list 2) translations per product              */
+    int order;                 /* Chebyshev points per dimension of each expansion      */
+    int precision;
+    int64_t device_bytes;      /* device memory held by the handle                     */
+    double root_center[3];
+    double root_half_width;
+} afmpb_info;
+
+/* Per-stage timing of one product (afmpb_profile_product). */
+#define AFMPB_MAX_STAGES 16
+typedef struct {
+    int n_stages;
+    char name[AFMPB_MAX_STAGES][16];   /* "gather", "p2m", "m2m", "m2l", "p2l", "l2l", "l2p",
+                                          "p2p", "combine", "scatter"                    */
+    double ms[AFMPB_MAX_STAGES];       /* mean duration of the stage (CUDA events)        */
+    int launches[AFMPB_MAX_STAGES];    /* kernel launches of the stage per product       */
+    double ms_graph;                   /* mean duration of the captured product (graph)   */
+    int kernels_per_product;           /* kernel launches of one afmpb_matvec call       */
+} afmpb_profile;
+
+/* Select parts of the product for testing (afmpb_matvec_parts). */
+#define AFMPB_PART_DIAG 1  /* alpha x                                                 */
+#define AFMPB_PART_FAR 2   /* point (far-rule) sums over every t != p: FMM + P2P     */
+#define AFMPB_PART_NEAR 4  /* near correction: near rule minus far rule on N(p), plus
+                              the self patch                                           */
+#define AFMPB_PART_ALL 7
+
+/* Build the handle: validate the mesh, compute node-patch geometry (Fig. 1), sort the
+ * nodes along a Morton curve, build the adaptive octree and its four interaction lists
+ * (Sec. 3.2: list 3 is evaluated point to point like list 1), integrate the near-field
+ * patch coefficients of Eq. 6 once (Sec. 2, step 2), build the FMM operators, and, when
+ * charges are given, the right-hand side of Eq. 5 (step 1).
+ *   mesh       required; checked (EMESH on failure)
+ *   charges    may be NULL (then afmpb_solve / afmpb_energy return ESTATE)
+ *   eps_in, eps_out > 0; kappa >= 0; fmm_order in [2, 8] Chebyshev points per dimension;
+ *   tol = eps_rel of Eq. 7 (> 0); options may be NULL.
+ * On success *out receives the handle. */
+afmpb_status afmpb_create(const afmpb_mesh *mesh, const afmpb_charges *charges,
+                          double eps_in, double eps_out, double kappa, int fmm_order,
+                          double tol, const afmpb_options *options, afmpb_t **out);
+
+/* y = L x for the operator of Eq. 5 (caller order, device pointers, FP32, length 2N).
+ * Queued on the handle's stream; returns before the product completes.  x and y must not
+ * overlap. */
+afmpb_status afmpb_matvec(afmpb_t *h, const float *x_dev, float *y_dev);
+
+/* As afmpb_matvec but only the selected AFMPB_PART_* terms are summed into y. */
+afmpb_status afmpb_matvec_parts(afmpb_t *h, const float *x_dev, float *y_dev, int parts);
+
+/* Host-buffer product: copies x to the device, forms y = L x, copies y back and waits.
+ * x_host, y_host: [2N] caller order. */
+afmpb_status afmpb_matvec_host(afmpb_t *h, const float *x_host, float *y_host);
+
+/* Solve Eq. 5 with restarted GMRES on the device (FP64 basis, Arnoldi with classical
+ * Gram-Schmidt applied twice, Givens rotations, stop test of Eq. 7), starting from x = 0.
+ * f_host / h_host ([N] each, caller order) may be NULL; the solution stays in the handle.
+ * Returns ENOCONV when max_restart cycles did not reach the tolerance (the best iterate
+ * is still stored and returned).  info may be NULL. */
+afmpb_status afmpb_solve(afmpb_t *h, double *f_host, double *h_host, afmpb_solve_info *info);
+
+/* Polar solvation energy (kcal/mol) of the last solution:
+ * E = 1/2 sum_k q_k phi_reac(r_k), phi_reac from the interior Green representation of
+ * the surface solution.  Requires a successful (or ENOCONV) afmpb_solve. */
+afmpb_status afmpb_energy(afmpb_t *h, double *kcal_per_mol);
+
+/* The right-hand side of Eq. 5 (caller order, host [2N]). */
+afmpb_status afmpb_rhs(afmpb_t *h, double *b_host);
+
+/* Node-patch geometry in caller order (host buffers, each may be NULL): patch area [N],
+ * node normal [N*3], patch radius rho [N]. */
+afmpb_status afmpb_get_geometry(afmpb_t *h, double *area, double *normals, double *rho);
+
+/* Near-field CSR in caller order.  rowptr [N+1]; col [nnz]; coef [nnz*4] holds
+ * (dA, dB, dC, dD): near rule minus far rule for t != p, the self-patch integrals for
+ * t == p.  Columns of a row are in the octree's Morton order.  Pass NULLs to skip. */
+afmpb_status afmpb_get_near(afmpb_t *h, int64_t *rowptr, int32_t *col, float *coef);
+
+/* Octree export (host buffers sized from afmpb_get_info; any may be NULL):
+ *   box_level [n_boxes], box_anchor [n_boxes*3] (integer cell coordinates at the box's
+ *   level), box_range [n_boxes*2] (node range in Morton order), box_parent [n_boxes],
+ *   perm [n_nodes] (Morton position -> caller index), and the lists as CSR over boxes:
+ *   u/w point-to-point lists are indexed by box (empty for non-leaves), v and x by box.
+ *   *_ptr arrays have n_boxes+1 entries. */
+afmpb_status afmpb_get_tree(afmpb_t *h, int32_t *box_level, int32_t *box_anchor,
+                            int32_t *box_range, int32_t *box_parent, int32_t *perm,
+                            int64_t *u_ptr, int32_t *u_idx, int64_t *v_ptr, int32_t *v_idx,
+                            int64_t *w_ptr, int32_t *w_idx, int64_t *x_ptr, int32_t *x_idx);
+
+afmpb_status afmpb_get_info(const afmpb_t *h, afmpb_info *info);
+
+/* Time the stages of the product on the handle's stream: reps products run stage by
+ * stage (not as a graph, P2P serialised after the far field) with CUDA events between
+ * stages, then reps graph replays.  Before each repetition, flush_bytes of flush_dev
+ * (device memory, may be NULL) are overwritten to evict the L2 cache.  The input is the
+ * handle's last product result (values do not change the timing); results go to scratch
+ * buffers of the handle.  Blocks until done. */
+afmpb_status afmpb_profile_product(afmpb_t *h, int reps, void *flush_dev, size_t flush_bytes,
+                                   afmpb_profile *out);
+
+afmpb_status afmpb_destroy(afmpb_t *h);
+
+/* Last error message of the handle (or of this thread when h is NULL); never NULL. */
+const char *afmpb_last_error(const afmpb_t *h);
+
+/* Upper estimate of the device bytes afmpb_create + afmpb_solve will hold. */
+size_t afmpb_estimate_bytes(int64_t n_nodes, int64_t n_atoms, int fmm_order,
+                            const afmpb_options *options);
+
+/* Library version string. */
+const char *afmpb_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AFMPB_H */

@@ -1,0 +1,296 @@
+"""Python binding of libafmpb (GB300 node-patch Poisson-Boltzmann solver).
+
+Argument marshalling only: every step of the product, the solve and the energy runs in
+the CUDA library behind the C ABI of ``include/afmpb.h``.  Device buffers are passed as
+raw pointers (``int``) or as objects with ``data_ptr()`` (PyTorch tensors); the binding
+never computes anything itself and raises if the native library is missing.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import _build
+
+_lib = None
+
+PART_DIAG, PART_FAR, PART_NEAR, PART_ALL = 1, 2, 4, 7
+STATUS = {0: "OK", 1: "EINVAL", 2: "EMESH", 3: "ENOMEM", 4: "ECUDA", 5: "ENOCONV", 6: "ETIMEOUT",
+          7: "EBUSY", 8: "ESTATE"}
+
+
+class AfmpbError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s: %s" % (STATUS.get(code, code), msg))
+        self.code = code
+        self.status = STATUS.get(code, str(code))
+
+
+class Mesh(C.Structure):
+    _fields_ = [("n_nodes", C.c_int64), ("n_tris", C.c_int64), ("xyz", C.c_void_p),
+                ("tri", C.c_void_p), ("normals", C.c_void_p)]
+
+
+class Charges(C.Structure):
+    _fields_ = [("n", C.c_int64), ("xyz", C.c_void_p), ("q", C.c_void_p)]
+
+
+class Options(C.Structure):
+    _fields_ = [("leaf_cap", C.c_int), ("restart", C.c_int), ("max_restart", C.c_int),
+                ("abs_tol", C.c_double), ("precision", C.c_int), ("near_c", C.c_double),
+                ("stream", C.c_void_p), ("max_level", C.c_int)]
+
+
+class SolveInfo(C.Structure):
+    _fields_ = [("iters", C.c_int), ("restarts", C.c_int), ("res_est", C.c_double),
+                ("res_true", C.c_double), ("bnorm", C.c_double), ("ms_setup", C.c_double),
+                ("ms_matvec_total", C.c_double), ("ms_gmres", C.c_double),
+                ("nnz_near", C.c_int64), ("n_boxes", C.c_int64)]
+
+
+class Info(C.Structure):
+    _fields_ = [("n_nodes", C.c_int64), ("n_tris", C.c_int64), ("n_atoms", C.c_int64),
+                ("n_boxes", C.c_int64), ("n_leaves", C.c_int64), ("n_levels", C.c_int64),
+                ("nnz_near", C.c_int64), ("n_list_u", C.c_int64), ("n_list_v", C.c_int64),
+                ("n_list_w", C.c_int64), ("n_list_x", C.c_int64), ("n_p2p_pairs", C.c_int64),
+                ("n_m2l_pairs", C.c_int64), ("order", C.c_int), ("precision", C.c_int),
+                ("device_bytes", C.c_int64), ("root_center", C.c_double * 3),
+                ("root_half_width", C.c_double)]
+
+
+class Profile(C.Structure):
+    _fields_ = [("n_stages", C.c_int), ("name", (C.c_char * 16) * 16), ("ms", C.c_double * 16),
+                ("launches", C.c_int * 16), ("ms_graph", C.c_double), ("kernels_per_product", C.c_int)]
+
+
+def _struct_dict(s):
+    out = {}
+    for name, _ in s._fields_:
+        v = getattr(s, name)
+        out[name] = list(v) if hasattr(v, "__len__") else v
+    return out
+
+
+EXPORTS = ["afmpb_create", "afmpb_matvec", "afmpb_matvec_parts", "afmpb_matvec_host", "afmpb_solve",
+           "afmpb_energy", "afmpb_rhs", "afmpb_get_geometry", "afmpb_get_near", "afmpb_get_tree",
+           "afmpb_get_info", "afmpb_destroy", "afmpb_last_error", "afmpb_estimate_bytes",
+           "afmpb_version", "afmpb_profile_product"]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build: bool = True):
+    """Load libafmpb.so (building it with nvcc if needed).  Raises if it cannot load."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build:
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError("libafmpb.so is missing; run paper_1710_06316_gb300._build.build()")
+    lib = C.CDLL(_build.LIB)
+    P, I64, I32, D = C.c_void_p, C.c_int64, C.c_int, C.c_double
+    lib.afmpb_create.restype = I32
+    lib.afmpb_create.argtypes = [C.POINTER(Mesh), C.POINTER(Charges), D, D, D, I32, D,
+                                 C.POINTER(Options), C.POINTER(P)]
+    for name in ("afmpb_matvec", "afmpb_matvec_host"):
+        getattr(lib, name).restype = I32
+        getattr(lib, name).argtypes = [P, P, P]
+    lib.afmpb_matvec_parts.restype = I32
+    lib.afmpb_matvec_parts.argtypes = [P, P, P, I32]
+    lib.afmpb_solve.restype = I32
+    lib.afmpb_solve.argtypes = [P, P, P, C.POINTER(SolveInfo)]
+    lib.afmpb_energy.restype = I32
+    lib.afmpb_energy.argtypes = [P, C.POINTER(D)]
+    lib.afmpb_rhs.restype = I32
+    lib.afmpb_rhs.argtypes = [P, P]
+    lib.afmpb_get_geometry.restype = I32
+    lib.afmpb_get_geometry.argtypes = [P, P, P, P]
+    lib.afmpb_get_near.restype = I32
+    lib.afmpb_get_near.argtypes = [P, P, P, P]
+    lib.afmpb_get_tree.restype = I32
+    lib.afmpb_get_tree.argtypes = [P] + [P] * 13
+    lib.afmpb_get_info.restype = I32
+    lib.afmpb_get_info.argtypes = [P, C.POINTER(Info)]
+    lib.afmpb_destroy.restype = I32
+    lib.afmpb_destroy.argtypes = [P]
+    lib.afmpb_last_error.restype = C.c_char_p
+    lib.afmpb_last_error.argtypes = [P]
+    lib.afmpb_estimate_bytes.restype = C.c_size_t
+    lib.afmpb_estimate_bytes.argtypes = [I64, I64, I32, C.POINTER(Options)]
+    lib.afmpb_version.restype = C.c_char_p
+    lib.afmpb_profile_product.restype = I32
+    lib.afmpb_profile_product.argtypes = [P, I32, P, C.c_size_t, C.POINTER(Profile)]
+    _lib = lib
+    return lib
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if isinstance(a, int):
+        return a
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    raise TypeError("expected a device pointer, a tensor or a numpy array")
+
+
+def _np(a, dt):
+    return np.ascontiguousarray(a, dtype=dt)
+
+
+def _check(rc, h=None):
+    if rc != 0:
+        msg = load(build=False).afmpb_last_error(h).decode(errors="replace")
+        raise AfmpbError(rc, msg)
+
+
+def version() -> str:
+    return load().afmpb_version().decode()
+
+
+def estimate_bytes(n_nodes, n_atoms, order=6, leaf_cap=0, restart=0) -> int:
+    o = Options(leaf_cap=leaf_cap, restart=restart)
+    return int(load().afmpb_estimate_bytes(int(n_nodes), int(n_atoms), int(order), C.byref(o)))
+
+
+class Handle:
+    """One molecule on the GPU (afmpb_create ... afmpb_destroy)."""
+
+    def __init__(self, xyz, tri, atoms=None, q=None, eps_in=1.0, eps_out=80.0, kappa=0.0,
+                 order=6, tol=1e-6, leaf_cap=0, restart=0, max_restart=0, abs_tol=0.0,
+                 precision=0, near_c=0.0, stream=None, max_level=0, normals=None):
+        self._lib = load()
+        self._xyz = _np(xyz, np.float64)
+        self._tri = _np(tri, np.int32)
+        self.n = int(self._xyz.shape[0])
+        self._nrm = None if normals is None else _np(normals, np.float64)
+        mesh = Mesh(self.n, int(self._tri.shape[0]), self._xyz.ctypes.data, self._tri.ctypes.data,
+                     None if self._nrm is None else self._nrm.ctypes.data)
+        ch = None
+        if atoms is not None and q is not None:
+            self._atoms = _np(np.atleast_2d(atoms), np.float64)
+            self._q = _np(q, np.float64).ravel()
+            ch = Charges(int(self._q.size), self._atoms.ctypes.data, self._q.ctypes.data)
+        st = stream
+        if st is not None and not isinstance(st, int):
+            st = int(getattr(st, "cuda_stream", st))
+        opt = Options(int(leaf_cap), int(restart), int(max_restart), float(abs_tol), int(precision),
+                      float(near_c), st, int(max_level))
+        h = C.c_void_p()
+        rc = self._lib.afmpb_create(C.byref(mesh), None if ch is None else C.byref(ch),
+                                    float(eps_in), float(eps_out), float(kappa), int(order),
+                                    float(tol), C.byref(opt), C.byref(h))
+        _check(rc, None)
+        self.h = h.value
+
+    @classmethod
+    def for_molecule(cls, mol, **kw):
+        return cls(mol.xyz, mol.tri, mol.atoms, mol.q, mol.eps_in, mol.eps_out, mol.kappa, **kw)
+
+    # -- products ---------------------------------------------------------------------
+    def matvec(self, x_dev, y_dev):
+        _check(self._lib.afmpb_matvec(self.h, _ptr(x_dev), _ptr(y_dev)), self.h)
+
+    def matvec_parts(self, x_dev, y_dev, parts):
+        _check(self._lib.afmpb_matvec_parts(self.h, _ptr(x_dev), _ptr(y_dev), int(parts)), self.h)
+
+    def matvec_host(self, x, y=None):
+        """Host buffers: numpy arrays, or (pinned) CPU tensors / raw host pointers."""
+        if isinstance(x, np.ndarray) or not (hasattr(x, "data_ptr") or isinstance(x, int)):
+            x = _np(x, np.float32)
+        if y is None:
+            y = np.empty(2 * self.n, np.float32)
+        _check(self._lib.afmpb_matvec_host(self.h, _ptr(x), _ptr(y)), self.h)
+        return y
+
+    def profile(self, reps=5, flush=None, flush_bytes=0):
+        """Per-stage product timings (ms) measured with CUDA events in the library."""
+        p = Profile()
+        _check(self._lib.afmpb_profile_product(self.h, int(reps), _ptr(flush), int(flush_bytes),
+                                               C.byref(p)), self.h)
+        stages = [(p.name[i].value.decode(), p.ms[i], p.launches[i]) for i in range(p.n_stages)]
+        return dict(stages=stages, ms_graph=p.ms_graph, kernels_per_product=p.kernels_per_product)
+
+    # -- solve --------------------------------------------------------------------------
+    def solve(self, raise_on_noconv=True):
+        f = np.zeros(self.n)
+        hh = np.zeros(self.n)
+        info = SolveInfo()
+        rc = self._lib.afmpb_solve(self.h, f.ctypes.data, hh.ctypes.data, C.byref(info))
+        d = _struct_dict(info)
+        d["status"] = STATUS.get(rc, rc)
+        if rc != 0 and (rc != 5 or raise_on_noconv):
+            _check(rc, self.h)
+        return f, hh, d
+
+    def energy(self):
+        e = C.c_double()
+        _check(self._lib.afmpb_energy(self.h, C.byref(e)), self.h)
+        return float(e.value)
+
+    def rhs(self):
+        b = np.zeros(2 * self.n)
+        _check(self._lib.afmpb_rhs(self.h, b.ctypes.data), self.h)
+        return b
+
+    # -- exports ------------------------------------------------------------------------
+    def info(self):
+        i = Info()
+        _check(self._lib.afmpb_get_info(self.h, C.byref(i)), self.h)
+        return _struct_dict(i)
+
+    def geometry(self):
+        a = np.zeros(self.n)
+        nrm = np.zeros((self.n, 3))
+        rho = np.zeros(self.n)
+        _check(self._lib.afmpb_get_geometry(self.h, a.ctypes.data, nrm.ctypes.data, rho.ctypes.data), self.h)
+        return a, nrm, rho
+
+    def near(self):
+        nnz = self.info()["nnz_near"]
+        rp = np.zeros(self.n + 1, np.int64)
+        col = np.zeros(nnz, np.int32)
+        coef = np.zeros((nnz, 4), np.float32)
+        _check(self._lib.afmpb_get_near(self.h, rp.ctypes.data, col.ctypes.data, coef.ctypes.data), self.h)
+        return rp, col, coef
+
+    def tree(self):
+        inf = self.info()
+        nb = inf["n_boxes"]
+        t = dict(level=np.zeros(nb, np.int32), anchor=np.zeros((nb, 3), np.int32),
+                 range=np.zeros((nb, 2), np.int32), parent=np.zeros(nb, np.int32),
+                 perm=np.zeros(self.n, np.int32))
+        for k, key in (("u", "n_list_u"), ("v", "n_list_v"), ("w", "n_list_w"), ("x", "n_list_x")):
+            t[k + "_ptr"] = np.zeros(nb + 1, np.int64)
+            t[k + "_idx"] = np.zeros(max(1, inf[key]), np.int32)
+        args = [t["level"], t["anchor"], t["range"], t["parent"], t["perm"],
+                t["u_ptr"], t["u_idx"], t["v_ptr"], t["v_idx"], t["w_ptr"], t["w_idx"],
+                t["x_ptr"], t["x_idx"]]
+        _check(self._lib.afmpb_get_tree(self.h, *[a.ctypes.data for a in args]), self.h)
+        for k, key in (("u", "n_list_u"), ("v", "n_list_v"), ("w", "n_list_w"), ("x", "n_list_x")):
+            t[k + "_idx"] = t[k + "_idx"][: inf[key]]
+        return t
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._lib.afmpb_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -1,0 +1,489 @@
+// capi.cu -- the C ABI declared in include/afmpb.h: handle lifecycle, the captured
+// product graph, solve / energy entry points and the export calls used by tests.
+//
+// The product (one GMRES matvec, Sec. 2 step 3) is captured once per parts mask into a
+// CUDA graph: the far-field chain (P2M, M2M per level, M2L, P2L, L2L per level, L2P) runs
+// on the handle's capture stream while the point-to-point kernel runs beside it on a
+// second stream; the combine kernel (near correction + Eq. 5 assembly) joins them.
+// Replaying the graph replaces the paper's per-iteration DAG execution (Sec. 3.3:
+// create the DAG once, execute it many times).
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+
+#include "internal.cuh"
+
+using namespace afmpb;
+
+namespace {
+
+thread_local std::string g_err;
+
+afmpb_status fail(afmpb_t *h, const Err &e) {
+  if (h) h->err = e.msg;
+  else g_err = e.msg;
+  return e.code;
+}
+
+void destroy_handle(afmpb_t *h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  for (auto &g : h->graph)
+    if (g) cudaGraphExecDestroy(g);
+  h->arena.free_all();
+  if (h->h_pinned) cudaFreeHost(h->h_pinned);
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
+  if (h->ev_t0) cudaEventDestroy(h->ev_t0);
+  if (h->ev_t1) cudaEventDestroy(h->ev_t1);
+  if (h->side) cudaStreamDestroy(h->side);
+  if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+  delete h;
+}
+
+Err capture_product(afmpb_t *h, int parts) {
+  cudaStream_t cap = nullptr;
+  AFMPB_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+  struct StreamGuard { cudaStream_t s; ~StreamGuard() { cudaStreamDestroy(s); } } sg{cap};
+  AFMPB_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+  Err e;
+  if (parts & AFMPB_PART_FAR) {
+    cudaEventRecord(h->ev_fork, cap);
+    cudaStreamWaitEvent(h->side, h->ev_fork, 0);
+    e = enqueue_p2p(h, h->side);
+    cudaEventRecord(h->ev_join, h->side);
+    if (e.ok()) e = enqueue_far(h, cap);
+    cudaStreamWaitEvent(cap, h->ev_join, 0);
+  }
+  if (e.ok()) e = enqueue_combine(h, cap, parts);
+  cudaGraph_t g = nullptr;
+  cudaError_t ce = cudaStreamEndCapture(cap, &g);
+  if (!e.ok()) {
+    if (g) cudaGraphDestroy(g);
+    return e;
+  }
+  if (ce != cudaSuccess) return make_err(AFMPB_ECUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(ce));
+  ce = cudaGraphInstantiate(&h->graph[parts], g, 0);
+  cudaGraphDestroy(g);
+  if (ce != cudaSuccess) return make_err(AFMPB_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(ce));
+  return Err{};
+}
+
+Err check_params(const afmpb_mesh *mesh, double eps_in, double eps_out, double kappa, int order, double tol,
+                 const afmpb_options *o) {
+  if (!mesh) return make_err(AFMPB_EINVAL, "mesh is NULL");
+  if (!(eps_in > 0) || !(eps_out > 0) || !std::isfinite(eps_in) || !std::isfinite(eps_out))
+    return make_err(AFMPB_EINVAL, "eps_in and eps_out must be positive and finite");
+  if (!(kappa >= 0) || !std::isfinite(kappa)) return make_err(AFMPB_EINVAL, "kappa must be >= 0 and finite");
+  if (order < 2 || order > kMaxOrder) return make_err(AFMPB_EINVAL, "fmm_order must be in [2, 8]");
+  if (!(tol > 0) || !std::isfinite(tol)) return make_err(AFMPB_EINVAL, "tol must be positive");
+  if (o) {
+    if (o->leaf_cap < 0 || o->restart < 0 || o->max_restart < 0 || o->max_level < 0 || o->max_level > kMaxLevel)
+      return make_err(AFMPB_EINVAL, "negative option or max_level above 20");
+    if (o->abs_tol < 0 || !(o->near_c >= 0)) return make_err(AFMPB_EINVAL, "abs_tol and near_c must be >= 0");
+    if (o->precision != 0 && o->precision != 1) return make_err(AFMPB_EINVAL, "precision must be 0 or 1");
+    if (o->restart > 4096) return make_err(AFMPB_EINVAL, "restart above 4096");
+  }
+  return Err{};
+}
+
+Err create_impl(afmpb_t *h, const afmpb_mesh *mesh, const afmpb_charges *ch) {
+  auto t0 = std::chrono::steady_clock::now();
+  if (h->opt.stream) {
+    h->stream = (cudaStream_t)h->opt.stream;
+  } else {
+    AFMPB_CUDA(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+    h->own_stream = true;
+  }
+  AFMPB_CUDA(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
+  AFMPB_CUDA(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+  AFMPB_CUDA(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+  AFMPB_CUDA(cudaEventCreate(&h->ev_t0));
+  AFMPB_CUDA(cudaEventCreate(&h->ev_t1));
+  AFMPB_TRY(build_geometry(h, mesh));
+  AFMPB_TRY(build_tree(h));
+  AFMPB_TRY(build_near(h));
+  AFMPB_TRY(build_fmm(h));
+  auto &A = h->arena;
+  AFMPB_TRY(A.alloc(&h->d_xs, h->n, "xs"));
+  AFMPB_TRY(A.alloc(&h->d_ys, 2 * h->n, "ys"));
+  AFMPB_TRY(A.alloc(&h->d_phi_far, h->n, "phi far"));
+  AFMPB_TRY(A.alloc(&h->d_phi_near, h->n, "phi near"));
+  AFMPB_CUDA(cudaMemsetAsync(h->d_xs, 0, sizeof(float2) * h->n, h->stream));
+  if (ch && ch->n > 0) {
+    h->natoms = ch->n;
+    AFMPB_TRY(A.alloc(&h->d_atoms, 3 * ch->n, "atoms"));
+    AFMPB_TRY(A.alloc(&h->d_q, ch->n, "charges"));
+    AFMPB_CUDA(cudaMemcpyAsync(h->d_atoms, ch->xyz, sizeof(double) * 3 * ch->n, cudaMemcpyHostToDevice, h->stream));
+    AFMPB_CUDA(cudaMemcpyAsync(h->d_q, ch->q, sizeof(double) * ch->n, cudaMemcpyHostToDevice, h->stream));
+  }
+  AFMPB_TRY(build_rhs(h));
+  AFMPB_CUDA(cudaStreamSynchronize(h->stream));
+  AFMPB_TRY(capture_product(h, AFMPB_PART_ALL));
+  AFMPB_CUDA(cudaStreamSynchronize(h->stream));
+  h->ms_setup = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  return Err{};
+}
+
+}  // namespace
+
+namespace afmpb {
+Err product_sorted(afmpb_t *h, cudaStream_t s, int parts) {
+  if (parts <= 0 || parts > AFMPB_PART_ALL) return make_err(AFMPB_EINVAL, "parts must be a non-empty AFMPB_PART_* mask");
+  if (!h->graph[parts]) AFMPB_TRY(capture_product(h, parts));
+  AFMPB_CUDA(cudaGraphLaunch(h->graph[parts], s));
+  return Err{};
+}
+}  // namespace afmpb
+
+extern "C" {
+
+afmpb_status afmpb_create(const afmpb_mesh *mesh, const afmpb_charges *charges, double eps_in, double eps_out,
+                          double kappa, int fmm_order, double tol, const afmpb_options *options, afmpb_t **out) {
+  if (!out) return fail(nullptr, make_err(AFMPB_EINVAL, "out is NULL"));
+  *out = nullptr;
+  Err e = check_params(mesh, eps_in, eps_out, kappa, fmm_order, tol, options);
+  if (!e.ok()) return fail(nullptr, e);
+  if (charges && charges->n > 0 && (!charges->xyz || !charges->q))
+    return fail(nullptr, make_err(AFMPB_EINVAL, "charges->xyz and charges->q are required when charges->n > 0"));
+  if (charges && charges->n < 0) return fail(nullptr, make_err(AFMPB_EINVAL, "charges->n < 0"));
+  e = validate_mesh(mesh);
+  if (!e.ok()) return fail(nullptr, e);
+  afmpb_t *h = new (std::nothrow) afmpb_t();
+  if (!h) return fail(nullptr, make_err(AFMPB_ENOMEM, "host allocation of the handle failed"));
+  h->n = mesh->n_nodes;
+  h->nt = mesh->n_tris;
+  h->eps_in = eps_in;
+  h->eps_out = eps_out;
+  h->kappa = kappa;
+  h->ebar = eps_out / eps_in;
+  h->alpha = 0.5 / h->ebar + 0.5;
+  h->tol = tol;
+  h->order = fmm_order;
+  h->ncoef = fmm_order * fmm_order * fmm_order;
+  if (options) h->opt = *options;
+  if (h->opt.leaf_cap == 0) h->opt.leaf_cap = 48;
+  if (h->opt.restart == 0) h->opt.restart = 80;
+  if (h->opt.max_restart == 0 && !(options && options->max_restart == 0 && options->restart != 0)) h->opt.max_restart = 5;
+  if (h->opt.near_c == 0) h->opt.near_c = 2.0;
+  if (h->opt.max_level == 0) h->opt.max_level = kMaxLevel;
+  e = create_impl(h, mesh, charges);
+  if (!e.ok()) {
+    g_err = e.msg;
+    destroy_handle(h);
+    return e.code;
+  }
+  *out = h;
+  return AFMPB_OK;
+}
+
+afmpb_status afmpb_matvec_parts(afmpb_t *h, const float *x, float *y, int parts) {
+  if (!h) return fail(nullptr, make_err(AFMPB_EINVAL, "handle is NULL"));
+  if (!x || !y) return fail(h, make_err(AFMPB_EINVAL, "x and y must be device pointers"));
+  if (x == y) return fail(h, make_err(AFMPB_EINVAL, "x and y must not overlap"));
+  Err e = enqueue_gather(h, h->stream, x);
+  if (e.ok()) e = product_sorted(h, h->stream, parts);
+  if (e.ok()) e = enqueue_scatter(h, h->stream, y);
+  return e.ok() ? AFMPB_OK : fail(h, e);
+}
+
+afmpb_status afmpb_matvec(afmpb_t *h, const float *x, float *y) { return afmpb_matvec_parts(h, x, y, AFMPB_PART_ALL); }
+
+afmpb_status afmpb_matvec_host(afmpb_t *h, const float *x, float *y) {
+  if (!h) return fail(nullptr, make_err(AFMPB_EINVAL, "handle is NULL"));
+  if (!x || !y) return fail(h, make_err(AFMPB_EINVAL, "x and y must be host pointers"));
+  const size_t bytes = sizeof(float) * 2 * h->n;
+  Err e;
+  if (!h->d_xhost_stage) {
+    e = h->arena.alloc(&h->d_xhost_stage, 2 * h->n, "host stage x");
+    if (e.ok()) e = h->arena.alloc(&h->d_yhost_stage, 2 * h->n, "host stage y");
+    if (!e.ok()) return fail(h, e);
+  }
+  cudaError_t ce = cudaMemcpyAsync(h->d_xhost_stage, x, bytes, cudaMemcpyHostToDevice, h->stream);
+  if (ce != cudaSuccess) return fail(h, make_err(AFMPB_ECUDA, std::string("H2D: ") + cudaGetErrorString(ce)));
+  e = enqueue_gather(h, h->stream, h->d_xhost_stage);
+  if (e.ok()) e = product_sorted(h, h->stream, AFMPB_PART_ALL);
+  if (e.ok()) e = enqueue_scatter(h, h->stream, h->d_yhost_stage);
+  if (!e.ok()) return fail(h, e);
+  ce = cudaMemcpyAsync(y, h->d_yhost_stage, bytes, cudaMemcpyDeviceToHost, h->stream);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(h->stream);
+  if (ce != cudaSuccess) return fail(h, make_err(AFMPB_ECUDA, std::string("D2H: ") + cudaGetErrorString(ce)));
+  return AFMPB_OK;
+}
+
+afmpb_status afmpb_solve(afmpb_t *h, double *f, double *hh, afmpb_solve_info *info) {
+  if (!h) return fail(nullptr, make_err(AFMPB_EINVAL, "handle is NULL"));
+  if (h->natoms == 0) return fail(h, make_err(AFMPB_ESTATE, "the handle was created without charges"));
+  Err e = run_solve(h, info);
+  if (!e.ok() && e.code != AFMPB_ENOCONV) return fail(h, e);
+  if (f || hh) {
+    std::vector<double> xs(2 * h->n);
+    std::vector<int32_t> perm(h->n);
+    cudaError_t ce = cudaMemcpyAsync(xs.data(), h->d_sol, sizeof(double) * 2 * h->n, cudaMemcpyDeviceToHost, h->stream);
+    if (ce == cudaSuccess)
+      ce = cudaMemcpyAsync(perm.data(), h->d_perm, sizeof(int32_t) * h->n, cudaMemcpyDeviceToHost, h->stream);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(h->stream);
+    if (ce != cudaSuccess) return fail(h, make_err(AFMPB_ECUDA, cudaGetErrorString(ce)));
+    for (int64_t p = 0; p < h->n; ++p) {
+      if (f) f[perm[p]] = xs[p];
+      if (hh) hh[perm[p]] = xs[h->n + p];
+    }
+  }
+  return e.ok() ? AFMPB_OK : fail(h, e);
+}
+
+afmpb_status afmpb_energy(afmpb_t *h, double *E) {
+  if (!h || !E) return fail(h, make_err(AFMPB_EINVAL, "handle and output are required"));
+  Err e = run_energy(h, E);
+  return e.ok() ? AFMPB_OK : fail(h, e);
+}
+
+afmpb_status afmpb_rhs(afmpb_t *h, double *b) {
+  if (!h || !b) return fail(h, make_err(AFMPB_EINVAL, "handle and output are required"));
+  std::vector<double> bs(2 * h->n);
+  std::vector<int32_t> perm(h->n);
+  cudaError_t ce = cudaMemcpyAsync(bs.data(), h->d_b, sizeof(double) * 2 * h->n, cudaMemcpyDeviceToHost, h->stream);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(perm.data(), h->d_perm, sizeof(int32_t) * h->n, cudaMemcpyDeviceToHost, h->stream);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(h->stream);
+  if (ce != cudaSuccess) return fail(h, make_err(AFMPB_ECUDA, cudaGetErrorString(ce)));
+  for (int64_t p = 0; p < h->n; ++p) {
+    b[perm[p]] = bs[p];
+    b[h->n + perm[p]] = bs[h->n + p];
+  }
+  return AFMPB_OK;
+}
+
+afmpb_status afmpb_get_geometry(afmpb_t *h, double *area, double *normals, double *rho) {
+  if (!h) return fail(nullptr, make_err(AFMPB_EINVAL, "handle is NULL"));
+  cudaError_t ce = cudaSuccess;
+  if (area) ce = cudaMemcpyAsync(area, h->d_area64, sizeof(double) * h->n, cudaMemcpyDeviceToHost, h->stream);
+  if (ce == cudaSuccess && normals)
+    ce = cudaMemcpyAsync(normals, h->d_nrm64, sizeof(double) * 3 * h->n, cudaMemcpyDeviceToHost, h->stream);
+  if (ce == cudaSuccess && rho) ce = cudaMemcpyAsync(rho, h->d_rho64, sizeof(double) * h->n, cudaMemcpyDeviceToHost, h->stream);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(h->stream);
+  if (ce != cudaSuccess) return fail(h, make_err(AFMPB_ECUDA, cudaGetErrorString(ce)));
+  return AFMPB_OK;
+}
+
+afmpb_status afmpb_get_near(afmpb_t *h, int64_t *rowptr, int32_t *col, float *coef) {
+  if (!h) return fail(nullptr, make_err(AFMPB_EINVAL, "handle is NULL"));
+  const int64_t n = h->n;
+  std::vector<int64_t> ptr(n + 1);
+  std::vector<int32_t> c(h->nnz), perm(n);
+  std::vector<float4> cf(h->nnz);
+  cudaError_t ce = cudaMemcpyAsync(ptr.data(), h->d_near_ptr, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost, h->stream);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(c.data(), h->d_near_col, sizeof(int32_t) * h->nnz, cudaMemcpyDeviceToHost, h->stream);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(cf.data(), h->d_near_coef, sizeof(float4) * h->nnz, cudaMemcpyDeviceToHost, h->stream);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(perm.data(), h->d_perm, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, h->stream);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(h->stream);
+  if (ce != cudaSuccess) return fail(h, make_err(AFMPB_ECUDA, cudaGetErrorString(ce)));
+  std::vector<int64_t> iperm(n);
+  for (int64_t p = 0; p < n; ++p) iperm[perm[p]] = p;
+  int64_t k = 0;
+  if (rowptr) rowptr[0] = 0;
+  for (int64_t o = 0; o < n; ++o) {
+    const int64_t p = iperm[o];
+    for (int64_t j = ptr[p]; j < ptr[p + 1]; ++j, ++k) {
+      if (col) col[k] = perm[c[j]];
+      if (coef) {
+        coef[4 * k] = cf[j].x;
+        coef[4 * k + 1] = cf[j].y;
+        coef[4 * k + 2] = cf[j].z;
+        coef[4 * k + 3] = cf[j].w;
+      }
+    }
+    if (rowptr) rowptr[o + 1] = k;
+  }
+  return AFMPB_OK;
+}
+
+afmpb_status afmpb_get_tree(afmpb_t *h, int32_t *box_level, int32_t *box_anchor, int32_t *box_range,
+                            int32_t *box_parent, int32_t *perm, int64_t *u_ptr, int32_t *u_idx, int64_t *v_ptr,
+                            int32_t *v_idx, int64_t *w_ptr, int32_t *w_idx, int64_t *x_ptr, int32_t *x_idx) {
+  if (!h) return fail(nullptr, make_err(AFMPB_EINVAL, "handle is NULL"));
+  const auto &T = h->shape;
+  const int nb = T.nbox;
+  cudaStream_t s = h->stream;
+  cudaError_t ce = cudaSuccess;
+  auto cp = [&](void *dst, const void *src, size_t bytes) {
+    if (dst && ce == cudaSuccess && bytes) ce = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s);
+  };
+  cp(box_level, h->d_box_level, sizeof(int32_t) * nb);
+  cp(box_parent, h->d_box_parent, sizeof(int32_t) * nb);
+  cp(perm, h->d_perm, sizeof(int32_t) * h->n);
+  cp(u_ptr, h->d_u_ptr, sizeof(int64_t) * (nb + 1));
+  cp(u_idx, h->d_u_idx, sizeof(int32_t) * T.n_u);
+  cp(v_ptr, h->d_v_ptr, sizeof(int64_t) * (nb + 1));
+  cp(v_idx, h->d_v_idx, sizeof(int32_t) * T.n_v);
+  cp(w_ptr, h->d_w_ptr, sizeof(int64_t) * (nb + 1));
+  cp(w_idx, h->d_w_idx, sizeof(int32_t) * T.n_w);
+  cp(x_ptr, h->d_x_ptr, sizeof(int64_t) * (nb + 1));
+  cp(x_idx, h->d_x_idx, sizeof(int32_t) * T.n_x);
+  std::vector<int4> anc;
+  std::vector<int32_t> beg, end;
+  if (box_anchor) {
+    anc.resize(nb);
+    cp(anc.data(), h->d_box_anchor, sizeof(int4) * nb);
+  }
+  if (box_range) {
+    beg.resize(nb);
+    end.resize(nb);
+    cp(beg.data(), h->d_box_begin, sizeof(int32_t) * nb);
+    cp(end.data(), h->d_box_end, sizeof(int32_t) * nb);
+  }
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+  if (ce != cudaSuccess) return fail(h, make_err(AFMPB_ECUDA, cudaGetErrorString(ce)));
+  for (int b = 0; b < nb; ++b) {
+    if (box_anchor) {
+      box_anchor[3 * b] = anc[b].x;
+      box_anchor[3 * b + 1] = anc[b].y;
+      box_anchor[3 * b + 2] = anc[b].z;
+    }
+    if (box_range) {
+      box_range[2 * b] = beg[b];
+      box_range[2 * b + 1] = end[b];
+    }
+  }
+  return AFMPB_OK;
+}
+
+afmpb_status afmpb_get_info(const afmpb_t *h, afmpb_info *info) {
+  if (!h || !info) return fail(nullptr, make_err(AFMPB_EINVAL, "handle and info are required"));
+  std::memset(info, 0, sizeof(*info));
+  const auto &T = h->shape;
+  info->n_nodes = h->n;
+  info->n_tris = h->nt;
+  info->n_atoms = h->natoms;
+  info->n_boxes = T.nbox;
+  info->n_leaves = T.nleaf;
+  info->n_levels = T.nlevel;
+  info->nnz_near = h->nnz;
+  info->n_list_u = T.n_u;
+  info->n_list_v = T.n_v;
+  info->n_list_w = T.n_w;
+  info->n_list_x = T.n_x;
+  info->n_p2p_pairs = T.n_p2p_pairs;
+  info->n_m2l_pairs = h->n_m2l_pairs;
+  info->order = h->order;
+  info->precision = h->opt.precision;
+  info->device_bytes = (int64_t)h->arena.bytes;
+  for (int d = 0; d < 3; ++d) info->root_center[d] = T.c0[d];
+  info->root_half_width = T.w0;
+  return AFMPB_OK;
+}
+
+afmpb_status afmpb_profile_product(afmpb_t *h, int reps, void *flush, size_t flush_bytes, afmpb_profile *out) {
+  if (!h || !out || reps <= 0) return fail(h, make_err(AFMPB_EINVAL, "handle, reps > 0 and out are required"));
+  std::memset(out, 0, sizeof(*out));
+  cudaStream_t s = h->stream;
+  if (!h->d_prof_x) {
+    Err e = h->arena.alloc(&h->d_prof_x, 2 * h->n, "profile x");
+    if (e.ok()) e = h->arena.alloc(&h->d_prof_y, 2 * h->n, "profile y");
+    if (!e.ok()) return fail(h, e);
+  }
+  // input: the last product result, in caller order (contents do not change timing)
+  {
+    Err e = enqueue_scatter(h, s, h->d_prof_x);
+    if (!e.ok()) return fail(h, e);
+  }
+  std::vector<double> acc;
+  std::vector<std::string> names;
+  std::vector<int> launches;
+  for (int r = 0; r < reps; ++r) {
+    if (flush && flush_bytes) cudaMemsetAsync(flush, r & 0xff, flush_bytes, s);
+    StageTimer tm;
+    tm.s = s;
+    cudaEvent_t start = nullptr;
+    cudaEventCreate(&start);
+    cudaEventRecord(start, s);
+    Err e = enqueue_gather(h, s, h->d_prof_x);
+    if (e.ok()) tm.mark("gather", 1);
+    if (e.ok()) e = enqueue_far(h, s, &tm);
+    if (e.ok()) e = enqueue_p2p(h, s);
+    if (e.ok()) tm.mark("p2p", 1);
+    if (e.ok()) e = enqueue_combine(h, s, AFMPB_PART_ALL);
+    if (e.ok()) tm.mark("combine", 1);
+    if (e.ok()) e = enqueue_scatter(h, s, h->d_prof_y);
+    if (e.ok()) tm.mark("scatter", 1);
+    cudaError_t ce = cudaStreamSynchronize(s);
+    if (!e.ok() || ce != cudaSuccess) {
+      cudaEventDestroy(start);
+      return fail(h, e.ok() ? make_err(AFMPB_ECUDA, cudaGetErrorString(ce)) : e);
+    }
+    if (r == 0) {
+      names = tm.names;
+      launches = tm.launches;
+      acc.assign(names.size(), 0.0);
+    }
+    cudaEvent_t prev = start;
+    for (size_t i = 0; i < tm.ends.size() && i < acc.size(); ++i) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, prev, tm.ends[i]);
+      acc[i] += ms;
+      prev = tm.ends[i];
+    }
+    cudaEventDestroy(start);
+  }
+  out->n_stages = (int)std::min<size_t>(names.size(), AFMPB_MAX_STAGES);
+  int kernels = 0;
+  for (int i = 0; i < out->n_stages; ++i) {
+    std::strncpy(out->name[i], names[i].c_str(), 15);
+    out->ms[i] = acc[i] / reps;
+    out->launches[i] = launches[i];
+    kernels += launches[i];
+  }
+  out->kernels_per_product = kernels;
+  // graph replays (the path afmpb_matvec takes), same flush between repetitions
+  cudaEvent_t a = nullptr, b = nullptr;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  double tot = 0.0;
+  for (int r = 0; r < reps; ++r) {
+    if (flush && flush_bytes) cudaMemsetAsync(flush, r & 0xff, flush_bytes, s);
+    cudaEventRecord(a, s);
+    Err e = product_sorted(h, s, AFMPB_PART_ALL);
+    cudaEventRecord(b, s);
+    if (!e.ok()) {
+      cudaEventDestroy(a);
+      cudaEventDestroy(b);
+      return fail(h, e);
+    }
+    cudaEventSynchronize(b);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    tot += ms;
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  out->ms_graph = tot / reps;
+  return AFMPB_OK;
+}
+
+afmpb_status afmpb_destroy(afmpb_t *h) {
+  destroy_handle(h);
+  return AFMPB_OK;
+}
+
+const char *afmpb_last_error(const afmpb_t *h) { return h ? h->err.c_str() : g_err.c_str(); }
+
+size_t afmpb_estimate_bytes(int64_t n_nodes, int64_t n_atoms, int fmm_order, const afmpb_options *o) {
+  if (n_nodes <= 0 || fmm_order < 2 || fmm_order > kMaxOrder) return 0;
+  const int cap = (o && o->leaf_cap > 0) ? o->leaf_cap : 48;
+  const int m = (o && o->restart > 0) ? o->restart : 80;
+  const size_t n = (size_t)n_nodes, n3 = (size_t)fmm_order * fmm_order * fmm_order;
+  const size_t nbox = 3 * (n / (size_t)std::max(cap / 2, 1) + 64);
+  size_t b = 0;
+  b += n * (3 * 8 + 8 + 3 * 8 + 8 + 2 * 16 + 8 + 4 + 4 + 2 * 16 + 8 + 2 * 4 + 4 * 16);   // nodes
+  b += 2 * n * (3 * 4 + 3 * 8 + 4);                                                    // triangles
+  b += n * 40 * (4 + 16) + 8 * (n + 1);                                                 // near CSR
+  b += nbox * (2 * 2 * n3 * 4 + 64 + 27 * 4 + 200 * 4 * 2);                             // boxes, lists
+  b += 316 * n3 * n3 * 4 * 14;                                                          // M2L tables
+  b += (size_t)(m + 1) * 2 * n * 8 + 8 * 2 * n * 8;                                     // GMRES
+  b += (size_t)std::max<int64_t>(n_atoms, 0) * 32 * 2;
+  return b + (64u << 20);
+}
+
+const char *afmpb_version(void) { return "afmpb-gb300 0.1.0 (sm_103a)"; }
+
+}  // extern "C"

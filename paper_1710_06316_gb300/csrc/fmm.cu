@@ -1,0 +1,720 @@
+// fmm.cu -- far-field sums of the node-patch operator: adaptive FMM + point-to-point.
+//
+// For x = [f; h] every source node t carries a charge c_t = a_t h_t and a dipole
+// strength g_t = -a_t f_t along its normal n_t (Eq. 6 with the far rule: integrand
+// constant on the patch).  With G = 1/(4 pi r), u = exp(-kappa r)/(4 pi r) and the
+// dipole entering as d . grad_y, the four far sums of the solution flow (Sec. 2,
+// step 3b: single- and double-layer Laplace and Yukawa) are
+//     PhiL(p) = sum_t c_t G + (g_t / eps_bar) n_t . grad_y G
+//     PhiY(p) = sum_t c_t u + g_t n_t . grad_y u
+// and their target normal derivatives n_p . grad_x.  They are evaluated together in one
+// tree pass (the "ViewSet" idea of Sec. 3.1): every box carries one Laplace and one
+// Yukawa expansion.
+//
+// Expansions: tensor-product Chebyshev interpolation of the kernel on each box
+// (n = order points per dimension, n^3 weights per box and kernel).  The same
+// weights serve the single and the double layer (Sec. 3.2 notes the two share their
+// expansion form): the dipole enters P2M through the gradient of the interpolating
+// polynomial, and the normal derivative leaves L2P the same way.  M2L is a dense
+// n^3 x n^3 kernel matrix per (level, offset); the paper's FMM97 plane-wave M2L is
+// replaced by these dense translations, which are contractions suited to the GPU.
+//
+// Lists: 1 and 3 by P2P (Sec. 3.2 modified method), 2 by M2L, 4 by P2L (S_to_L).
+#include <cmath>
+
+#include "internal.cuh"
+
+namespace afmpb {
+
+__constant__ float c_cheb[kMaxOrder * kMaxOrder];          // Cm[m][k] = w_k T_k(x_m)
+__constant__ float c_m2m[2 * kMaxOrder * kMaxOrder];       // S2[c][m][m']
+__constant__ float c_nodes[kMaxOrder];                     // Chebyshev points on [-1, 1]
+
+// s_m(x) and s_m'(x) for the n interpolation polynomials.
+template <int N>
+__device__ __forceinline__ void cheb_basis(float x, float s[N], float ds[N]) {
+  float T[N], dT[N];
+  T[0] = 1.0f;
+  dT[0] = 0.0f;
+  if (N > 1) {
+    T[1] = x;
+    dT[1] = 1.0f;
+  }
+#pragma unroll
+  for (int k = 2; k < N; ++k) {
+    T[k] = 2.0f * x * T[k - 1] - T[k - 2];
+    dT[k] = 2.0f * T[k - 1] + 2.0f * x * dT[k - 1] - dT[k - 2];
+  }
+#pragma unroll
+  for (int m = 0; m < N; ++m) {
+    float a = 0.0f, b = 0.0f;
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      a = fmaf(c_cheb[m * kMaxOrder + k], T[k], a);
+      b = fmaf(c_cheb[m * kMaxOrder + k], dT[k], b);
+    }
+    s[m] = a;
+    ds[m] = b;
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// P2M: leaf sources -> Laplace and Yukawa multipole weights.
+// ------------------------------------------------------------------------------------
+template <int N>
+__global__ void __launch_bounds__(256) k_p2m(int nleaf, const int32_t *__restrict__ leaves,
+                                             const int32_t *__restrict__ bbeg, const int32_t *__restrict__ bend,
+                                             const dbl4 *__restrict__ center, const float4 *__restrict__ pos,
+                                             const float4 *__restrict__ nrm, const float2 *__restrict__ xs,
+                                             float inv_ebar, float *__restrict__ M) {
+  constexpr int N3 = N * N * N;
+  constexpr int CH = 64;
+  __shared__ float sb[CH][6 * N];   // sx, dsx, sy, dsy, sz, dsz
+  __shared__ float sw[CH][4];       // c, g nx / w, g ny / w, g nz / w
+  const int b = leaves[blockIdx.x];
+  const int beg = bbeg[b], end = bend[b];
+  const float invw = (float)(1.0 / center[b].w);
+  float accA[(N3 + 255) / 256], accB[(N3 + 255) / 256];
+#pragma unroll
+  for (int r = 0; r < (N3 + 255) / 256; ++r) accA[r] = accB[r] = 0.0f;
+  for (int c0 = beg; c0 < end; c0 += CH) {
+    const int cnt = min(CH, end - c0);
+    for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
+      float4 p = pos[c0 + j], q = nrm[c0 + j];
+      float2 fh = xs[c0 + j];
+      float s[N], ds[N];
+      cheb_basis<N>(p.x * invw, s, ds);
+#pragma unroll
+      for (int m = 0; m < N; ++m) { sb[j][m] = s[m]; sb[j][N + m] = ds[m]; }
+      cheb_basis<N>(p.y * invw, s, ds);
+#pragma unroll
+      for (int m = 0; m < N; ++m) { sb[j][2 * N + m] = s[m]; sb[j][3 * N + m] = ds[m]; }
+      cheb_basis<N>(p.z * invw, s, ds);
+#pragma unroll
+      for (int m = 0; m < N; ++m) { sb[j][4 * N + m] = s[m]; sb[j][5 * N + m] = ds[m]; }
+      float g = -p.w * fh.x * invw;
+      sw[j][0] = p.w * fh.y;
+      sw[j][1] = g * q.x;
+      sw[j][2] = g * q.y;
+      sw[j][3] = g * q.z;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < (N3 + 255) / 256; ++r) {
+      const int m = threadIdx.x + 256 * r;
+      if (m < N3) {
+        const int i = m / (N * N), jj = (m / N) % N, k = m % N;
+        float a = accA[r], bb = accB[r];
+        for (int t = 0; t < cnt; ++t) {
+          const float sx = sb[t][i], dsx = sb[t][N + i];
+          const float sy = sb[t][2 * N + jj], dsy = sb[t][3 * N + jj];
+          const float sz = sb[t][4 * N + k], dsz = sb[t][5 * N + k];
+          const float syz = sy * sz;
+          a = fmaf(sw[t][0], sx * syz, a);
+          bb = fmaf(sw[t][1], dsx * syz, bb);
+          bb = fmaf(sw[t][2], sx * dsy * sz, bb);
+          bb = fmaf(sw[t][3], sx * sy * dsz, bb);
+        }
+        accA[r] = a;
+        accB[r] = bb;
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int r = 0; r < (N3 + 255) / 256; ++r) {
+    const int m = threadIdx.x + 256 * r;
+    if (m < N3) {
+      M[(size_t)b * 2 * N3 + m] = fmaf(accB[r], inv_ebar, accA[r]);
+      M[(size_t)b * 2 * N3 + N3 + m] = accA[r] + accB[r];
+    }
+  }
+}
+
+// Apply the separable 1-D operator S2[c] along the three axes of a box of weights.
+// transpose == false: out[i,j,k] = sum S[cx][i][i'] S[cy][j][j'] S[cz][k][k'] in[i',j',k']
+// transpose == true : out[i',j',k'] = sum S[cx][i][i'] ... in[i,j,k]
+template <int N>
+__device__ __forceinline__ float apply_axis(const float *in, int m, int axis, int c, bool transpose) {
+  const int i = m / (N * N), j = (m / N) % N, k = m % N;
+  const float *S = c_m2m + c * kMaxOrder * kMaxOrder;
+  float acc = 0.0f;
+#pragma unroll
+  for (int q = 0; q < N; ++q) {
+    int src;
+    int row = axis == 0 ? i : (axis == 1 ? j : k);
+    float w = transpose ? S[q * kMaxOrder + row] : S[row * kMaxOrder + q];
+    if (axis == 0) src = q * N * N + j * N + k;
+    else if (axis == 1) src = i * N * N + q * N + k;
+    else src = i * N * N + j * N + q;
+    acc = fmaf(w, in[src], acc);
+  }
+  return acc;
+}
+
+// M2M: every parent of one level sums its children's translated multipoles.
+template <int N>
+__global__ void k_m2m(int ls, const int32_t *__restrict__ child0, const int32_t *__restrict__ nchild,
+                      const int4 *__restrict__ anchor, float *__restrict__ M) {
+  constexpr int N3 = N * N * N;
+  __shared__ float s0[2 * N3], s1[2 * N3];
+  const int b = ls + blockIdx.x;
+  const int nc = nchild[b];
+  if (nc == 0) return;
+  const int e = threadIdx.x;               // (kernel, m)
+  const bool act = e < 2 * N3;
+  const int kt = e / N3, m = e % N3;
+  float acc = 0.0f;
+  for (int q = 0; q < nc; ++q) {
+    const int c = child0[b] + q;
+    const int4 a = anchor[c];
+    if (act) s0[e] = M[(size_t)c * 2 * N3 + e];
+    __syncthreads();
+    float v = act ? apply_axis<N>(s0 + kt * N3, m, 2, a.z & 1, false) : 0.0f;
+    __syncthreads();
+    if (act) s1[e] = v;
+    __syncthreads();
+    v = act ? apply_axis<N>(s1 + kt * N3, m, 1, a.y & 1, false) : 0.0f;
+    __syncthreads();
+    if (act) s0[e] = v;
+    __syncthreads();
+    v = act ? apply_axis<N>(s0 + kt * N3, m, 0, a.x & 1, false) : 0.0f;
+    acc += v;
+    __syncthreads();
+  }
+  if (act) M[(size_t)b * 2 * N3 + e] = acc;
+}
+
+// L2L: every box of one level adds its parent's local expansion, re-interpolated.
+template <int N>
+__global__ void k_l2l(int ls, const int32_t *__restrict__ parent, const int4 *__restrict__ anchor,
+                      float *__restrict__ L) {
+  constexpr int N3 = N * N * N;
+  __shared__ float s0[2 * N3], s1[2 * N3];
+  const int b = ls + blockIdx.x;
+  const int p = parent[b];
+  const int4 a = anchor[b];
+  const int e = threadIdx.x;
+  const bool act = e < 2 * N3;
+  const int kt = e / N3, m = e % N3;
+  if (act) s0[e] = L[(size_t)p * 2 * N3 + e];
+  __syncthreads();
+  float v = act ? apply_axis<N>(s0 + kt * N3, m, 0, a.x & 1, true) : 0.0f;
+  __syncthreads();
+  if (act) s1[e] = v;
+  __syncthreads();
+  v = act ? apply_axis<N>(s1 + kt * N3, m, 1, a.y & 1, true) : 0.0f;
+  __syncthreads();
+  if (act) s0[e] = v;
+  __syncthreads();
+  v = act ? apply_axis<N>(s0 + kt * N3, m, 2, a.z & 1, true) : 0.0f;
+  if (act) L[(size_t)b * 2 * N3 + e] += v;
+}
+
+// ------------------------------------------------------------------------------------
+// M2L (FP32, CUDA cores).  One CTA per (row tile of 64 target weights, (level, offset)
+// group, kernel); the 64 x n^3 slice of the translation matrix stays in shared memory
+// while the group's pairs stream through in chunks of 32.  Results are added with
+// atomics (several offsets feed the same target box).
+// ------------------------------------------------------------------------------------
+template <int N>
+__global__ void __launch_bounds__(256) k_m2l(const M2LGroup *__restrict__ groups, const int2 *__restrict__ pairs,
+                                             const float *__restrict__ Klap, const float *__restrict__ Kyuk,
+                                             const dbl4 *__restrict__ center, int yuk_min_level,
+                                             const float *__restrict__ M, float *__restrict__ L) {
+  constexpr int N3 = N * N * N;
+  constexpr int RT = 64, PC = 32, LD = N3 + 1;
+  extern __shared__ float smem[];
+  float *Ks = smem;                 // [RT][LD]
+  float *Ms = smem + RT * LD;       // [N3][PC]
+  const M2LGroup g = groups[blockIdx.y];
+  const int kt = blockIdx.z;
+  if (kt == 1 && g.level < yuk_min_level) return;
+  const int r0 = blockIdx.x * RT;
+  const int rows = min(RT, N3 - r0);
+  const size_t N6 = (size_t)N3 * N3;
+  const float *K = kt == 0 ? Klap + (size_t)g.offset * N6 : Kyuk + ((size_t)g.level * kNumOffsets + g.offset) * N6;
+  for (int e = threadIdx.x; e < RT * N3; e += blockDim.x) {
+    int r = e / N3, c = e % N3;
+    Ks[r * LD + c] = r < rows ? K[(size_t)(r0 + r) * N3 + c] : 0.0f;
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int pc = 0; pc < g.count; pc += PC) {
+    const int cnt = min(PC, g.count - pc);
+    __syncthreads();
+    for (int e = threadIdx.x; e < N3 * PC; e += blockDim.x) {
+      int p = e / N3, k = e % N3;
+      float v = 0.0f;
+      if (p < cnt) v = M[((size_t)pairs[g.start + pc + p].y * 2 + kt) * N3 + k];
+      Ms[k * PC + p] = v;
+    }
+    __syncthreads();
+    float acc[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
+    const float *k0 = Ks + lane * LD, *k1 = Ks + (lane + 32) * LD;
+#pragma unroll 4
+    for (int k = 0; k < N3; ++k) {
+      const float a0 = k0[k], a1 = k1[k];
+      const float4 mv = *reinterpret_cast<const float4 *>(Ms + k * PC + warp * 4);
+      acc[0][0] = fmaf(a0, mv.x, acc[0][0]); acc[0][1] = fmaf(a0, mv.y, acc[0][1]);
+      acc[0][2] = fmaf(a0, mv.z, acc[0][2]); acc[0][3] = fmaf(a0, mv.w, acc[0][3]);
+      acc[1][0] = fmaf(a1, mv.x, acc[1][0]); acc[1][1] = fmaf(a1, mv.y, acc[1][1]);
+      acc[1][2] = fmaf(a1, mv.z, acc[1][2]); acc[1][3] = fmaf(a1, mv.w, acc[1][3]);
+    }
+    const float scale = kt == 0 ? (float)(1.0 / center[pairs[g.start].x].w) : 1.0f;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int p = warp * 4 + q;
+      if (p >= cnt) continue;
+      const int tb = pairs[g.start + pc + p].x;
+      float *dst = L + ((size_t)tb * 2 + kt) * N3 + r0;
+      if (lane < rows) atomicAdd(dst + lane, acc[0][q] * scale);
+      if (lane + 32 < rows) atomicAdd(dst + lane + 32, acc[1][q] * scale);
+    }
+  }
+}
+
+// M2L matrices: Laplace for a unit box (scaled by 1/w when used), Yukawa per level.
+__global__ void k_m2l_table(int N, int nslots, const int3 *__restrict__ offs, double kw, double invw,
+                            float *__restrict__ out) {
+  const int N3 = N * N * N;
+  const int64_t tot = (int64_t)nslots * N3 * N3;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    int slot = (int)(e / ((int64_t)N3 * N3));
+    int rem = (int)(e % ((int64_t)N3 * N3));
+    int mt = rem / N3, ms = rem % N3;
+    int3 o = offs[slot];
+    double tx = c_nodes[mt / (N * N)], ty = c_nodes[(mt / N) % N], tz = c_nodes[mt % N];
+    double sx = 2.0 * o.x + c_nodes[ms / (N * N)], sy = 2.0 * o.y + c_nodes[(ms / N) % N],
+           sz = 2.0 * o.z + c_nodes[ms % N];
+    double r = sqrt((tx - sx) * (tx - sx) + (ty - sy) * (ty - sy) + (tz - sz) * (tz - sz));
+    double v = kInv4Pi / r;
+    if (kw >= 0.0) v = exp(-kw * r) * v * invw;
+    out[e] = (float)v;
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// P2L: list-4 sources straight into a box's local weights.
+// ------------------------------------------------------------------------------------
+template <int N>
+__global__ void __launch_bounds__(256) k_p2l(const int32_t *__restrict__ xbox, const int64_t *__restrict__ xptr,
+                                             const int32_t *__restrict__ xidx, const int32_t *__restrict__ bbeg,
+                                             const int32_t *__restrict__ bend, const dbl4 *__restrict__ center,
+                                             const float4 *__restrict__ pos, const float4 *__restrict__ nrm,
+                                             const float2 *__restrict__ xs, float inv_ebar, float kappa,
+                                             float *__restrict__ L) {
+  constexpr int N3 = N * N * N;
+  constexpr int CH = 128;
+  __shared__ float4 sp[CH], sn[CH];
+  const int b = xbox[blockIdx.x];
+  const dbl4 cb = center[b];
+  const float w = (float)cb.w;
+  float accL[(N3 + 255) / 256], accY[(N3 + 255) / 256];
+  float px[(N3 + 255) / 256], py[(N3 + 255) / 256], pz[(N3 + 255) / 256];
+#pragma unroll
+  for (int r = 0; r < (N3 + 255) / 256; ++r) {
+    accL[r] = accY[r] = 0.0f;
+    int m = threadIdx.x + 256 * r;
+    if (m < N3) {
+      px[r] = w * c_nodes[m / (N * N)];
+      py[r] = w * c_nodes[(m / N) % N];
+      pz[r] = w * c_nodes[m % N];
+    }
+  }
+  for (int64_t j = xptr[b]; j < xptr[b + 1]; ++j) {
+    const int c = xidx[j];
+    const dbl4 cc = center[c];
+    const float ox = (float)(cc.x - cb.x), oy = (float)(cc.y - cb.y), oz = (float)(cc.z - cb.z);
+    for (int s0 = bbeg[c]; s0 < bend[c]; s0 += CH) {
+      const int cnt = min(CH, bend[c] - s0);
+      __syncthreads();
+      for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+        float4 p = pos[s0 + t], q = nrm[s0 + t];
+        float2 fh = xs[s0 + t];
+        sp[t] = make_float4(p.x + ox, p.y + oy, p.z + oz, p.w * fh.y);
+        sn[t] = make_float4(q.x, q.y, q.z, -p.w * fh.x);
+      }
+      __syncthreads();
+#pragma unroll
+      for (int r = 0; r < (N3 + 255) / 256; ++r) {
+        if (threadIdx.x + 256 * r >= N3) continue;
+        float aL = accL[r], aY = accY[r];
+        for (int t = 0; t < cnt; ++t) {
+          const float4 y = sp[t], q = sn[t];
+          const float dx = px[r] - y.x, dy = py[r] - y.y, dz = pz[r] - y.z;
+          const float r2 = dx * dx + dy * dy + dz * dz;
+          const float ri = rsqrtf(r2);
+          const float rr = r2 * ri;
+          const float G = ri, G3 = ri * ri * ri;
+          const float ndt = q.x * dx + q.y * dy + q.z * dz;
+          const float e = __expf(-kappa * rr);
+          const float g1 = e * (1.0f + kappa * rr) * G3;
+          aL += y.w * G + q.w * inv_ebar * ndt * G3;
+          aY += y.w * e * G + q.w * ndt * g1;
+        }
+        accL[r] = aL;
+        accY[r] = aY;
+      }
+    }
+  }
+  const float s = (float)kInv4Pi;
+#pragma unroll
+  for (int r = 0; r < (N3 + 255) / 256; ++r) {
+    int m = threadIdx.x + 256 * r;
+    if (m < N3) {
+      L[(size_t)b * 2 * N3 + m] += s * accL[r];
+      L[(size_t)b * 2 * N3 + N3 + m] += s * accY[r];
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// L2P: evaluate both local expansions and their normal derivatives at leaf targets.
+// ------------------------------------------------------------------------------------
+template <int N>
+__global__ void __launch_bounds__(128) k_l2p(const int32_t *__restrict__ leaves, const int32_t *__restrict__ bbeg,
+                                             const int32_t *__restrict__ bend, const dbl4 *__restrict__ center,
+                                             const float4 *__restrict__ pos, const float4 *__restrict__ nrm,
+                                             const float *__restrict__ L, float4 *__restrict__ phi) {
+  constexpr int N3 = N * N * N;
+  __shared__ float sL[2 * N3];
+  const int b = leaves[blockIdx.x];
+  for (int e = threadIdx.x; e < 2 * N3; e += blockDim.x) sL[e] = L[(size_t)b * 2 * N3 + e];
+  __syncthreads();
+  const float invw = (float)(1.0 / center[b].w);
+  for (int t = bbeg[b] + threadIdx.x; t < bend[b]; t += blockDim.x) {
+    const float4 p = pos[t], q = nrm[t];
+    float sx[N], dsx[N], sy[N], dsy[N], sz[N], dsz[N];
+    cheb_basis<N>(p.x * invw, sx, dsx);
+    cheb_basis<N>(p.y * invw, sy, dsy);
+    cheb_basis<N>(p.z * invw, sz, dsz);
+    float out[4];
+#pragma unroll
+    for (int kt = 0; kt < 2; ++kt) {
+      const float *Lk = sL + kt * N3;
+      float phi0 = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        float a = 0.f, bj = 0.f, cj = 0.f;
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+          float u = 0.f, du = 0.f;
+#pragma unroll
+          for (int k = 0; k < N; ++k) {
+            const float l = Lk[(i * N + j) * N + k];
+            u = fmaf(l, sz[k], u);
+            du = fmaf(l, dsz[k], du);
+          }
+          a = fmaf(u, sy[j], a);
+          bj = fmaf(u, dsy[j], bj);
+          cj = fmaf(du, sy[j], cj);
+        }
+        phi0 = fmaf(a, sx[i], phi0);
+        gx = fmaf(a, dsx[i], gx);
+        gy = fmaf(bj, sx[i], gy);
+        gz = fmaf(cj, sx[i], gz);
+      }
+      out[2 * kt] = phi0;
+      out[2 * kt + 1] = (q.x * gx + q.y * gy + q.z * gz) * invw;
+    }
+    phi[t] = make_float4(out[0], out[1], out[2], out[3]);
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// P2P (lists 1 and 3): point (far-rule) sums over t != p, both kernels, both outputs.
+// ------------------------------------------------------------------------------------
+constexpr int kP2PThreads = 64;
+constexpr int kP2PChunk = 256;
+
+__global__ void __launch_bounds__(kP2PThreads) k_p2p(const int32_t *__restrict__ leaves, const int64_t *__restrict__ pptr,
+                                                      const int32_t *__restrict__ pidx, const int32_t *__restrict__ bbeg,
+                                                      const int32_t *__restrict__ bend, const dbl4 *__restrict__ center,
+                                                      const float4 *__restrict__ pos, const float4 *__restrict__ nrm,
+                                                      const float2 *__restrict__ xs, float inv_ebar, float kappa,
+                                                      float4 *__restrict__ phi) {
+  __shared__ float4 sp[kP2PChunk], sn[kP2PChunk];
+  const int leaf = blockIdx.x;
+  const int b = leaves[leaf];
+  const dbl4 cb = center[b];
+  const int tb = bbeg[b], te = bend[b];
+  const float kap3 = kappa * (1.0f / 3.0f);
+  for (int t0 = tb; t0 < te; t0 += kP2PThreads) {
+    const int t = t0 + threadIdx.x;
+    const bool act = t < te;
+    float4 xp = act ? pos[t] : make_float4(0, 0, 0, 0);
+    float4 np = act ? nrm[t] : make_float4(0, 0, 0, 0);
+    float sL = 0.f, dL = 0.f, sY = 0.f, dY = 0.f;
+    for (int64_t j = pptr[leaf]; j < pptr[leaf + 1]; ++j) {
+      const int c = pidx[j];
+      const dbl4 cc = center[c];
+      const float ox = (float)(cc.x - cb.x), oy = (float)(cc.y - cb.y), oz = (float)(cc.z - cb.z);
+      for (int s0 = bbeg[c]; s0 < bend[c]; s0 += kP2PChunk) {
+        const int cnt = min(kP2PChunk, bend[c] - s0);
+        __syncthreads();
+        for (int e = threadIdx.x; e < cnt; e += kP2PThreads) {
+          float4 p = pos[s0 + e], q = nrm[s0 + e];
+          float2 fh = xs[s0 + e];
+          sp[e] = make_float4(p.x + ox, p.y + oy, p.z + oz, p.w * fh.y);
+          sn[e] = make_float4(q.x, q.y, q.z, -p.w * fh.x);
+        }
+        __syncthreads();
+        if (act) {
+          for (int e = 0; e < cnt; ++e) {
+            const float4 y = sp[e], q = sn[e];
+            const float dx = xp.x - y.x, dy = xp.y - y.y, dz = xp.z - y.z;
+            const float r2 = dx * dx + dy * dy + dz * dz;
+            const float ri = r2 > 0.0f ? rsqrtf(r2) : 0.0f;   // t == p contributes nothing
+            const float rr = r2 * ri;
+            const float ri2 = ri * ri;
+            const float G3 = ri * ri2;
+            const float G5 = 3.0f * G3 * ri2;
+            const float ndt = q.x * dx + q.y * dy + q.z * dz;
+            const float npd = np.x * dx + np.y * dy + np.z * dz;
+            const float nn = np.x * q.x + np.y * q.y + np.z * q.z;
+            const float gL = q.w * inv_ebar;
+            sL += y.w * ri + gL * ndt * G3;
+            dL += -y.w * npd * G3 + gL * (nn * G3 - ndt * npd * G5);
+            const float kr = kappa * rr;
+            const float ex = __expf(-kr);
+            const float g1 = ex * (1.0f + kr) * G3;
+            const float g2 = ex * (1.0f + kr + kr * kap3 * rr) * G5;
+            sY += y.w * ex * ri + q.w * ndt * g1;
+            dY += -y.w * npd * g1 + q.w * (nn * g1 - ndt * npd * g2);
+          }
+        }
+      }
+    }
+    if (act) {
+      const float s = (float)kInv4Pi;
+      phi[t] = make_float4(s * sL, s * dL, s * sY, s * dY);
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// Combine (Eq. 5): y1 = alpha f - PhiL + PhiY + sum_near (dB f - dA h)
+//                  y2 = alpha h - dn PhiL + dn PhiY / eps_bar + sum_near (dD f - dC h)
+// Eight lanes per row walk the near-field CSR.
+// ------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_combine(int64_t n, int parts, float alpha, float inv_ebar,
+                                                 const float2 *__restrict__ xs, const float4 *__restrict__ pfar,
+                                                 const float4 *__restrict__ pnear, const int64_t *__restrict__ nptr,
+                                                 const int32_t *__restrict__ ncol, const float4 *__restrict__ ncoef,
+                                                 float *__restrict__ ys) {
+  const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t p = gid >> 3;
+  const int sub = threadIdx.x & 7;
+  const bool row = p < n;           // every lane stays for the shuffles below
+  float a1 = 0.f, a2 = 0.f;
+  if (row && (parts & AFMPB_PART_NEAR)) {
+    for (int64_t j = nptr[p] + sub; j < nptr[p + 1]; j += 8) {
+      const float4 c = ncoef[j];
+      const float2 x = xs[ncol[j]];
+      a1 = fmaf(c.y, x.x, fmaf(-c.x, x.y, a1));
+      a2 = fmaf(c.w, x.x, fmaf(-c.z, x.y, a2));
+    }
+  }
+#pragma unroll
+  for (int o = 4; o > 0; o >>= 1) {
+    a1 += __shfl_xor_sync(0xffffffffu, a1, o, 8);
+    a2 += __shfl_xor_sync(0xffffffffu, a2, o, 8);
+  }
+  if (row && sub == 0) {
+    const float2 x = xs[p];
+    if (parts & AFMPB_PART_DIAG) {
+      a1 += alpha * x.x;
+      a2 += alpha * x.y;
+    }
+    if (parts & AFMPB_PART_FAR) {
+      const float4 u = pfar[p], v = pnear[p];
+      a1 += -(u.x + v.x) + (u.z + v.z);
+      a2 += -(u.y + v.y) + (u.w + v.w) * inv_ebar;
+    }
+    ys[p] = a1;
+    ys[n + p] = a2;
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// host side
+// ------------------------------------------------------------------------------------
+namespace {
+
+double cheb_s(int n, int m, double x) {   // s_m(x) in double (host tables)
+  double xm = std::cos((2.0 * m + 1.0) * kPi / (2.0 * n));
+  double v = 1.0 / n;
+  for (int k = 1; k < n; ++k) v += 2.0 / n * std::cos(k * std::acos(xm)) * std::cos(k * std::acos(std::max(-1.0, std::min(1.0, x))));
+  return v;
+}
+
+template <int N>
+Err launch_far(afmpb_t *h, cudaStream_t s, StageTimer *tm) {
+  constexpr int N3 = N * N * N;
+  const auto &T = h->shape;
+  const float inv_ebar = (float)(1.0 / h->ebar);
+  AFMPB_CUDA(cudaMemsetAsync(h->d_L, 0, sizeof(float) * (size_t)T.nbox * 2 * N3, s));
+  k_p2m<N><<<T.nleaf, 256, 0, s>>>(T.nleaf, h->d_leaves, h->d_box_begin, h->d_box_end, h->d_box_center, h->d_pos,
+                                   h->d_nrm, h->d_xs, inv_ebar, h->d_M);
+  AFMPB_TRY(check_launch("k_p2m"));
+  if (tm) tm->mark("p2m", 1);
+  const int mthreads = ((2 * N3 + 31) / 32) * 32;
+  for (int level = T.nlevel - 2; level >= 2; --level) {
+    int ls = T.lvl_start[level], nl = T.lvl_start[level + 1] - ls;
+    k_m2m<N><<<nl, mthreads, 0, s>>>(ls, h->d_box_child0, h->d_box_nchild, h->d_box_anchor, h->d_M);
+    AFMPB_TRY(check_launch("k_m2m"));
+  }
+  if (tm) tm->mark("m2m", std::max(0, T.nlevel - 3));
+  if (!h->m2l_groups.empty()) {
+    if (h->opt.precision == 1) {
+      AFMPB_TRY(enqueue_m2l_tc(h, s));
+    } else {
+      constexpr int RT = 64, PC = 32;
+      const size_t smem = sizeof(float) * (RT * (N3 + 1) + N3 * PC);
+      dim3 grid((N3 + RT - 1) / RT, (unsigned)h->m2l_groups.size(), 2);
+      k_m2l<N><<<grid, 256, smem, s>>>(h->d_m2l_groups, h->d_m2l_pairs, h->d_K_lap, h->d_K_yuk, h->d_box_center,
+                                       h->m2l_yuk_levels, h->d_M, h->d_L);
+      AFMPB_TRY(check_launch("k_m2l"));
+    }
+  }
+  if (tm) tm->mark("m2l", h->m2l_groups.empty() ? 0 : 1);
+  if (!h->h_xbox.empty()) {
+    k_p2l<N><<<(unsigned)h->h_xbox.size(), 256, 0, s>>>(h->d_xbox, h->d_x_ptr, h->d_x_idx, h->d_box_begin,
+                                                        h->d_box_end, h->d_box_center, h->d_pos, h->d_nrm, h->d_xs,
+                                                        inv_ebar, (float)h->kappa, h->d_L);
+    AFMPB_TRY(check_launch("k_p2l"));
+  }
+  if (tm) tm->mark("p2l", h->h_xbox.empty() ? 0 : 1);
+  for (int level = 3; level < T.nlevel; ++level) {
+    int ls = T.lvl_start[level], nl = T.lvl_start[level + 1] - ls;
+    k_l2l<N><<<nl, mthreads, 0, s>>>(ls, h->d_box_parent, h->d_box_anchor, h->d_L);
+    AFMPB_TRY(check_launch("k_l2l"));
+  }
+  if (tm) tm->mark("l2l", std::max(0, T.nlevel - 3));
+  k_l2p<N><<<T.nleaf, 128, 0, s>>>(h->d_leaves, h->d_box_begin, h->d_box_end, h->d_box_center, h->d_pos, h->d_nrm,
+                                   h->d_L, h->d_phi_far);
+  AFMPB_TRY(check_launch("k_l2p"));
+  if (tm) tm->mark("l2p", 1);
+  return Err{};
+}
+
+template <int N>
+Err set_m2l_smem() {
+  constexpr int N3 = N * N * N;
+  const size_t smem = sizeof(float) * (64 * (N3 + 1) + N3 * 32);
+  AFMPB_CUDA(cudaFuncSetAttribute(k_m2l<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  return Err{};
+}
+
+}  // namespace
+
+Err enqueue_far(afmpb_t *h, cudaStream_t s, StageTimer *tm) {
+  switch (h->order) {
+    case 2: return launch_far<2>(h, s, tm);
+    case 3: return launch_far<3>(h, s, tm);
+    case 4: return launch_far<4>(h, s, tm);
+    case 5: return launch_far<5>(h, s, tm);
+    case 6: return launch_far<6>(h, s, tm);
+    case 7: return launch_far<7>(h, s, tm);
+    case 8: return launch_far<8>(h, s, tm);
+    default: return make_err(AFMPB_EINVAL, "fmm_order must be in [2, 8]");
+  }
+}
+
+Err enqueue_p2p(afmpb_t *h, cudaStream_t s) {
+  const auto &T = h->shape;
+  k_p2p<<<T.nleaf, kP2PThreads, 0, s>>>(h->d_leaves, h->d_p2p_ptr, h->d_p2p_idx, h->d_box_begin, h->d_box_end,
+                                        h->d_box_center, h->d_pos, h->d_nrm, h->d_xs, (float)(1.0 / h->ebar),
+                                        (float)h->kappa, h->d_phi_near);
+  return check_launch("k_p2p");
+}
+
+Err enqueue_combine(afmpb_t *h, cudaStream_t s, int parts) {
+  k_combine<<<div_up(h->n * 8, 256), 256, 0, s>>>(h->n, parts, (float)h->alpha, (float)(1.0 / h->ebar), h->d_xs,
+                                                   h->d_phi_far, h->d_phi_near, h->d_near_ptr, h->d_near_col,
+                                                   h->d_near_coef, h->d_ys);
+  return check_launch("k_combine");
+}
+
+Err build_fmm(afmpb_t *h) {
+  const int n = h->order;
+  const int N3 = n * n * n;
+  cudaStream_t s = h->stream;
+  auto &A = h->arena;
+  const auto &T = h->shape;
+  // Chebyshev tables (host, double -> float)
+  {
+    float cheb[kMaxOrder * kMaxOrder] = {0}, nodes[kMaxOrder] = {0}, m2m[2 * kMaxOrder * kMaxOrder] = {0};
+    for (int m = 0; m < n; ++m) {
+      double xm = std::cos((2.0 * m + 1.0) * kPi / (2.0 * n));
+      nodes[m] = (float)xm;
+      for (int k = 0; k < n; ++k) cheb[m * kMaxOrder + k] = (float)((k == 0 ? 1.0 : 2.0) / n * std::cos(k * (2.0 * m + 1.0) * kPi / (2.0 * n)));
+    }
+    for (int c = 0; c < 2; ++c)
+      for (int m = 0; m < n; ++m)
+        for (int mp = 0; mp < n; ++mp) {
+          double xmp = std::cos((2.0 * mp + 1.0) * kPi / (2.0 * n));
+          double xi = (c == 0 ? -0.5 : 0.5) + 0.5 * xmp;
+          m2m[c * kMaxOrder * kMaxOrder + m * kMaxOrder + mp] = (float)cheb_s(n, m, xi);
+        }
+    AFMPB_CUDA(cudaMemcpyToSymbolAsync(c_cheb, cheb, sizeof(cheb), 0, cudaMemcpyHostToDevice, s));
+    AFMPB_CUDA(cudaMemcpyToSymbolAsync(c_nodes, nodes, sizeof(nodes), 0, cudaMemcpyHostToDevice, s));
+    AFMPB_CUDA(cudaMemcpyToSymbolAsync(c_m2m, m2m, sizeof(m2m), 0, cudaMemcpyHostToDevice, s));
+  }
+  // offset slots: [-3,3]^3 minus [-1,1]^3
+  std::vector<int> code_to_slot(343, -1);
+  std::vector<int3> offs;
+  for (int ox = -3; ox <= 3; ++ox)
+    for (int oy = -3; oy <= 3; ++oy)
+      for (int oz = -3; oz <= 3; ++oz) {
+        if (std::abs(ox) <= 1 && std::abs(oy) <= 1 && std::abs(oz) <= 1) continue;
+        code_to_slot[(ox + 3) * 49 + (oy + 3) * 7 + (oz + 3)] = (int)offs.size();
+        offs.push_back(make_int3(ox, oy, oz));
+      }
+  int3 *d_offs = nullptr;
+  AFMPB_TRY(A.alloc(&d_offs, offs.size(), "m2l offsets"));
+  AFMPB_CUDA(cudaMemcpyAsync(d_offs, offs.data(), sizeof(int3) * offs.size(), cudaMemcpyHostToDevice, s));
+  for (auto &g : h->m2l_groups) g.offset = code_to_slot[g.offset];
+  if (!h->m2l_groups.empty()) {
+    AFMPB_TRY(A.alloc(&h->d_m2l_groups, h->m2l_groups.size(), "m2l groups"));
+    AFMPB_CUDA(cudaMemcpyAsync(h->d_m2l_groups, h->m2l_groups.data(), sizeof(M2LGroup) * h->m2l_groups.size(),
+                               cudaMemcpyHostToDevice, s));
+  }
+  // Yukawa M2L is skipped on coarse levels where the screened kernel across the one-box
+  // gap of a list-2 pair (distance >= 2 w) is below e^-40 of its unscreened value.
+  int maxlev = 0;
+  for (auto &g : h->m2l_groups) maxlev = std::max(maxlev, g.level + 1);
+  h->m2l_yuk_levels = 0;
+  while (h->m2l_yuk_levels < maxlev && h->kappa * 2.0 * std::ldexp(T.w0, -h->m2l_yuk_levels) > 40.0)
+    ++h->m2l_yuk_levels;
+  const size_t N6 = (size_t)N3 * N3;
+  AFMPB_TRY(A.alloc(&h->d_K_lap, kNumOffsets * N6, "K laplace"));
+  AFMPB_TRY(A.alloc(&h->d_K_yuk, (size_t)std::max(maxlev, 1) * kNumOffsets * N6, "K yukawa"));
+  k_m2l_table<<<1024, 256, 0, s>>>(n, kNumOffsets, d_offs, -1.0, 1.0, h->d_K_lap);
+  AFMPB_TRY(check_launch("k_m2l_table lap"));
+  for (int l = std::max(2, h->m2l_yuk_levels); l < maxlev; ++l) {
+    double w = std::ldexp(T.w0, -l);
+    k_m2l_table<<<1024, 256, 0, s>>>(n, kNumOffsets, d_offs, h->kappa * w, 1.0 / w,
+                                     h->d_K_yuk + (size_t)l * kNumOffsets * N6);
+    AFMPB_TRY(check_launch("k_m2l_table yuk"));
+  }
+  AFMPB_CUDA(cudaStreamSynchronize(s));
+  A.release(d_offs);
+  AFMPB_TRY(A.alloc(&h->d_M, (size_t)T.nbox * 2 * N3, "M"));
+  AFMPB_TRY(A.alloc(&h->d_L, (size_t)T.nbox * 2 * N3, "L"));
+  AFMPB_CUDA(cudaMemsetAsync(h->d_M, 0, sizeof(float) * (size_t)T.nbox * 2 * N3, s));
+  switch (n) {
+    case 2: AFMPB_TRY(set_m2l_smem<2>()); break;
+    case 3: AFMPB_TRY(set_m2l_smem<3>()); break;
+    case 4: AFMPB_TRY(set_m2l_smem<4>()); break;
+    case 5: AFMPB_TRY(set_m2l_smem<5>()); break;
+    case 6: AFMPB_TRY(set_m2l_smem<6>()); break;
+    case 7: AFMPB_TRY(set_m2l_smem<7>()); break;
+    case 8: AFMPB_TRY(set_m2l_smem<8>()); break;
+    default: return make_err(AFMPB_EINVAL, "fmm_order must be in [2, 8]");
+  }
+  if (h->opt.precision == 1) AFMPB_TRY(build_m2l_tc(h));
+  return Err{};
+}
+
+}  // namespace afmpb

@@ -1,0 +1,248 @@
+// internal.cuh -- state of an afmpb handle and the internal entry points shared by the
+// translation units of the library (geometry, tree, near field, FMM, solver, C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/afmpb.h"
+
+// Box centre and half width (32-byte aligned, one vector load).
+struct __align__(32) dbl4 {
+  double x, y, z, w;
+};
+
+namespace afmpb {
+
+constexpr int kMaxOrder = 8;        // Chebyshev points per dimension, upper bound
+constexpr int kMaxLevel = 20;       // deepest octree level
+constexpr int kKeyBits = 21;        // Morton bits per dimension (63-bit keys)
+constexpr int kNumOffsets = 316;    // M2L offsets: [-3,3]^3 minus [-1,1]^3
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kInv4Pi = 0.07957747154594767;  // 1 / (4 pi)
+
+// Error carried up the host call chain; every internal function returns one.
+struct Err {
+  afmpb_status code = AFMPB_OK;
+  std::string msg;
+  bool ok() const { return code == AFMPB_OK; }
+};
+inline Err make_err(afmpb_status c, const std::string &m) { return Err{c, m}; }
+
+#define AFMPB_CUDA(call)                                                              \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess)                                                            \
+      return ::afmpb::make_err(AFMPB_ECUDA, std::string(#call) + ": " +               \
+                                                cudaGetErrorString(e_));              \
+  } while (0)
+
+#define AFMPB_TRY(expr)                 \
+  do {                                  \
+    ::afmpb::Err e_ = (expr);           \
+    if (!e_.ok()) return e_;            \
+  } while (0)
+
+// Device allocation registry owned by a handle.
+struct DeviceArena {
+  std::vector<std::pair<void *, size_t>> blocks;
+  size_t bytes = 0;
+  template <class T>
+  Err alloc(T **p, size_t count, const char *what) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    void *q = nullptr;
+    cudaError_t e = cudaMalloc(&q, count * sizeof(T));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return make_err(AFMPB_ENOMEM, std::string("cudaMalloc ") + what + " (" +
+                                        std::to_string(count * sizeof(T)) + " B): " +
+                                        cudaGetErrorString(e));
+    }
+    blocks.push_back({q, count * sizeof(T)});
+    bytes += count * sizeof(T);
+    *p = static_cast<T *>(q);
+    return Err{};
+  }
+  void release(void *p) {
+    for (size_t i = 0; i < blocks.size(); ++i)
+      if (blocks[i].first == p) {
+        cudaFree(p);
+        bytes -= blocks[i].second;
+        blocks.erase(blocks.begin() + i);
+        return;
+      }
+  }
+  void free_all() {
+    for (auto &b : blocks) cudaFree(b.first);
+    blocks.clear();
+    bytes = 0;
+  }
+};
+
+// Host mirror of the octree shape (the device holds the arrays).
+struct TreeShape {
+  int nbox = 0, nleaf = 0, nlevel = 0;     // levels 0 .. nlevel-1
+  std::vector<int> lvl_start;              // [nlevel + 1] box index ranges per level
+  double c0[3] = {0, 0, 0};                // root centre
+  double w0 = 1;                           // root half width (power of two)
+  int64_t n_u = 0, n_v = 0, n_w = 0, n_x = 0, n_p2p_pairs = 0;
+};
+
+// Optional per-stage event marks (afmpb_profile_product); nullptr in normal launches.
+struct StageTimer {
+  cudaStream_t s = nullptr;
+  std::vector<std::string> names;
+  std::vector<cudaEvent_t> ends;
+  std::vector<int> launches;
+  void mark(const char *name, int nlaunch) {
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    cudaEventRecord(e, s);
+    names.push_back(name);
+    ends.push_back(e);
+    launches.push_back(nlaunch);
+  }
+  ~StageTimer() {
+    for (auto e : ends) cudaEventDestroy(e);
+  }
+};
+
+// One M2L work group: all V-list pairs of one level and one offset.
+struct M2LGroup {
+  int level, offset, start, count;
+};
+
+}  // namespace afmpb
+
+struct afmpb_t {
+  // ---- parameters -------------------------------------------------------------------
+  int64_t n = 0, nt = 0, natoms = 0;
+  double eps_in = 1, eps_out = 1, kappa = 0, ebar = 1, alpha = 1, tol = 1e-6;
+  int order = 6, ncoef = 216;
+  afmpb_options opt{};
+  std::string err;
+  double ms_setup = 0;
+
+  // ---- streams / events --------------------------------------------------------------
+  cudaStream_t stream = nullptr;   // handle stream (user's or own)
+  bool own_stream = false;
+  cudaStream_t side = nullptr;     // second stream: P2P beside the far-field chain
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaEvent_t ev_t0 = nullptr, ev_t1 = nullptr;
+
+  afmpb::DeviceArena arena;
+
+  // ---- mesh, caller order ------------------------------------------------------------
+  double *d_xyz = nullptr;         // [3n]
+  int32_t *d_tri = nullptr;        // [3nt]
+  int64_t *d_inc_ptr = nullptr;    // [n+1] node -> incident triangles
+  int32_t *d_inc_tri = nullptr;    // [3nt]
+  double *d_tri_nrm = nullptr;     // [3nt] unit facet normals
+  double *d_area64 = nullptr;      // [n]
+  double *d_nrm64 = nullptr;       // [3n]
+  double *d_rho64 = nullptr;       // [n]
+
+  // ---- octree -----------------------------------------------------------------------
+  afmpb::TreeShape shape;
+  uint64_t *d_key = nullptr;       // [n] sorted Morton keys
+  int32_t *d_perm = nullptr;       // [n] Morton position -> caller index
+  int32_t *d_box_level = nullptr, *d_box_parent = nullptr, *d_box_child0 = nullptr,
+          *d_box_nchild = nullptr, *d_box_begin = nullptr, *d_box_end = nullptr;
+  int4 *d_box_anchor = nullptr;    // x, y, z cell coordinates at the box level, w = level
+  dbl4 *d_box_center = nullptr; // centre, w = half width
+  uint64_t *d_box_key = nullptr;   // Morton prefix at the box level
+  double *d_box_rho = nullptr;     // largest patch radius inside the box
+  int32_t *d_colleague = nullptr;  // [27 nbox]
+  int32_t *d_leaves = nullptr;     // [nleaf] leaf box ids in Morton order
+  int32_t *d_node_leaf = nullptr;  // [n] Morton position -> leaf box
+  // lists (CSR over boxes; u and w non-empty only for leaves)
+  int64_t *d_u_ptr = nullptr, *d_v_ptr = nullptr, *d_w_ptr = nullptr, *d_x_ptr = nullptr;
+  int32_t *d_u_idx = nullptr, *d_v_idx = nullptr, *d_w_idx = nullptr, *d_x_idx = nullptr;
+  int64_t *d_p2p_ptr = nullptr;    // [nleaf+1] lists 1 + 3 per leaf (leaf order)
+  int32_t *d_p2p_idx = nullptr;
+  std::vector<int32_t> h_xbox;     // boxes with a non-empty list 4
+  int32_t *d_xbox = nullptr;
+
+  // ---- Morton-ordered node data -----------------------------------------------------
+  float4 *d_pos = nullptr;         // position relative to the leaf centre, w = patch area
+  float4 *d_nrm = nullptr;         // unit normal, w = 0
+
+  // ---- near field -------------------------------------------------------------------
+  int64_t nnz = 0;
+  int64_t *d_near_ptr = nullptr;   // [n+1]
+  int32_t *d_near_col = nullptr;   // [nnz] Morton positions
+  float4 *d_near_coef = nullptr;   // [nnz] (dA, dB, dC, dD)
+
+  // ---- FMM --------------------------------------------------------------------------
+  float *d_M = nullptr;            // [nbox][2][ncoef] multipole weights (Laplace, Yukawa)
+  float *d_L = nullptr;            // [nbox][2][ncoef] local weights
+  float *d_K_lap = nullptr;        // [316][ncoef][ncoef] unit-box Laplace M2L
+  float *d_K_yuk = nullptr;        // [nlevel][316][ncoef][ncoef] Yukawa M2L per level
+  std::vector<afmpb::M2LGroup> m2l_groups;
+  afmpb::M2LGroup *d_m2l_groups = nullptr;
+  int2 *d_m2l_pairs = nullptr;     // (target, source) boxes grouped by (level, offset)
+  int64_t n_m2l_pairs = 0;
+  int m2l_yuk_levels = 0;          // Yukawa M2L skipped on levels below this one
+
+  // ---- per-product work --------------------------------------------------------------
+  float2 *d_xs = nullptr;          // [n] (f, h) Morton order
+  float *d_ys = nullptr;           // [2n] y Morton order
+  float4 *d_phi_far = nullptr;     // [n] (PhiL, dn PhiL, PhiY, dn PhiY) from L2P
+  float4 *d_phi_near = nullptr;    // [n] same from P2P
+  cudaGraphExec_t graph[8] = {};   // captured product, one per parts mask
+  float *d_xhost_stage = nullptr, *d_yhost_stage = nullptr;   // afmpb_matvec_host staging
+  float *d_prof_x = nullptr, *d_prof_y = nullptr;             // afmpb_profile_product buffers
+
+  // ---- right-hand side, solution, atoms ---------------------------------------------
+  double *d_atoms = nullptr;       // [3 natoms]
+  double *d_q = nullptr;           // [natoms]
+  double *d_b = nullptr;           // [2n] Morton order
+  double bnorm = 0;
+  double *d_sol = nullptr;         // [2n] Morton order
+  bool solved = false;
+  // GMRES work (allocated at first solve)
+  int gm_m = 0;
+  double *d_V = nullptr, *d_w = nullptr, *d_H = nullptr, *d_g = nullptr, *d_cs = nullptr,
+         *d_sn = nullptr, *d_part = nullptr, *d_hcol = nullptr, *d_hcol2 = nullptr, *d_scal = nullptr;
+  double *h_pinned = nullptr;
+};
+
+namespace afmpb {
+
+// geometry.cu
+Err validate_mesh(const afmpb_mesh *mesh);
+Err build_geometry(afmpb_t *h, const afmpb_mesh *mesh);
+// tree.cu
+Err build_tree(afmpb_t *h);
+// near.cu
+Err build_near(afmpb_t *h);
+// fmm.cu
+Err build_fmm(afmpb_t *h);
+Err enqueue_far(afmpb_t *h, cudaStream_t s, StageTimer *tm = nullptr);   // P2M .. L2P into d_phi_far
+Err enqueue_p2p(afmpb_t *h, cudaStream_t s);          // P2P into d_phi_near
+Err enqueue_combine(afmpb_t *h, cudaStream_t s, int parts);
+Err enqueue_m2l_tc(afmpb_t *h, cudaStream_t s);       // tensor-core M2L (precision 1)
+Err build_m2l_tc(afmpb_t *h);
+// solve.cu
+Err build_rhs(afmpb_t *h);
+Err enqueue_gather(afmpb_t *h, cudaStream_t s, const float *x_caller);
+Err enqueue_scatter(afmpb_t *h, cudaStream_t s, float *y_caller);
+Err run_solve(afmpb_t *h, afmpb_solve_info *info);
+Err run_energy(afmpb_t *h, double *E);
+// capi.cu
+Err product_sorted(afmpb_t *h, cudaStream_t s, int parts);  // d_xs -> d_ys
+
+// launch helpers
+inline int div_up(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+inline Err check_launch(const char *what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return make_err(AFMPB_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  return Err{};
+}
+
+}  // namespace afmpb

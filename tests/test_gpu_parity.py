@@ -1,0 +1,225 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Bars (floating point, FP32 GPU arithmetic against the FP64 oracle):
+* geometry (computed in FP64 on the device): 1e-12 relative;
+* near-field coefficients (FP64 quadrature stored as FP32): 2e-6 of the row's largest;
+* products: relative L2 error <= 1e-4 on the whole vector and on each block (the bar
+  the matvec must meet at the configured FMM order);
+* right-hand side: 1e-5; GMRES solution and solvation energy: 1e-4.
+Integer work (near-set membership, tree lists) is compared exactly or checked for
+validity where several answers are correct.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synthetic
+from closed_forms import born_energy
+
+pytestmark = pytest.mark.gpu
+
+TOL_MATVEC = 1e-4
+
+
+def torch_cuda():
+    import torch
+    return torch
+
+
+def relerr(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def gpu_matvec(h, x, parts=7):
+    torch = torch_cuda()
+    xd = torch.tensor(np.asarray(x, np.float32), device="cuda")
+    yd = torch.empty_like(xd)
+    h.matvec_parts(xd, yd, parts)
+    torch.cuda.synchronize()
+    return yd.cpu().numpy().astype(np.float64)
+
+
+@pytest.fixture(scope="module")
+def born():
+    import paper_1710_06316_gb300 as pb
+    mol = synthetic.born_ion()          # 2,562 nodes, order 6
+    h = pb.Handle.for_molecule(mol, order=6, tol=1e-6)
+    o = oracle.Oracle.for_molecule(mol)
+    yield mol, h, o
+    h.close()
+
+
+def test_geometry_matches_oracle(born):
+    mol, h, o = born
+    a, n, r = h.geometry()
+    a0, n0, r0 = o.geometry()
+    np.testing.assert_allclose(a, a0, rtol=1e-12)
+    np.testing.assert_allclose(n, n0, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(r, r0, rtol=1e-12)
+
+
+def test_near_set_and_coefficients_match_oracle(born):
+    mol, h, o = born
+    rp, col, coef = h.near()
+    rp0, col0, coef0 = o.near_csr()
+    n = mol.n_nodes
+    assert rp[-1] == rp0[-1]
+    for p in range(n):
+        g = np.sort(col[rp[p]:rp[p + 1]])
+        assert np.array_equal(g, col0[rp0[p]:rp0[p + 1]]), p
+    # coefficients: GPU stores near - far (t != p) and the self value (t == p)
+    rows = np.repeat(np.arange(n), np.diff(rp))
+    near = o.coeffs(rows, col, rule=o.NEAR)
+    far = o.coeffs(rows, col, rule=o.FAR)
+    ref = np.where((rows == col)[:, None], near, near - far)
+    scale = np.abs(ref).max(axis=0)
+    err = np.abs(coef - ref).max(axis=0) / scale
+    assert err.max() < 2e-6, err
+
+
+def test_tree_lists_cover_every_pair_once(born):
+    mol, h, o = born
+    check_tree_coverage(h)
+
+
+def check_tree_coverage(h):
+    t = h.tree()
+    nb = len(t["level"])
+    n = h.n
+    children = [[] for _ in range(nb)]
+    for b in range(nb):
+        if t["parent"][b] >= 0:
+            children[t["parent"][b]].append(b)
+    leaves = [b for b in range(nb) if not children[b]]
+    rng = t["range"]
+    # leaves tile [0, n)
+    cover = np.zeros(n, int)
+    for b in leaves:
+        cover[rng[b, 0]:rng[b, 1]] += 1
+    assert np.all(cover == 1)
+    anc = t["anchor"]
+    lev = t["level"]
+
+    def adjacent(a, b):
+        if lev[a] > lev[b]:
+            a, b = b, a
+        s = lev[b] - lev[a]
+        lo = anc[a] << s
+        hi = (anc[a] + 1) << s
+        return bool(np.all(anc[b] + 1 >= lo) and np.all(anc[b] <= hi))
+
+    for T in leaves:
+        cnt = np.zeros(n, int)
+        for c in list(t["u_idx"][t["u_ptr"][T]:t["u_ptr"][T + 1]]):
+            assert adjacent(T, c) and not children[c]
+            cnt[rng[c, 0]:rng[c, 1]] += 1
+        for c in t["w_idx"][t["w_ptr"][T]:t["w_ptr"][T + 1]]:
+            assert not adjacent(T, c) and adjacent(T, t["parent"][c])
+            cnt[rng[c, 0]:rng[c, 1]] += 1
+        A = T
+        while A >= 0:
+            for c in t["v_idx"][t["v_ptr"][A]:t["v_ptr"][A + 1]]:
+                assert lev[c] == lev[A] and np.abs(anc[c] - anc[A]).max() >= 2
+                cnt[rng[c, 0]:rng[c, 1]] += 1
+            for c in t["x_idx"][t["x_ptr"][A]:t["x_ptr"][A + 1]]:
+                assert not children[c] and not adjacent(A, c)
+                cnt[rng[c, 0]:rng[c, 1]] += 1
+            A = t["parent"][A]
+        assert np.all(cnt == 1), (T, np.unique(cnt))
+
+
+@pytest.mark.parametrize("kind", ["smooth", "random"])
+def test_matvec_matches_oracle_born(born, kind):
+    mol, h, o = born
+    n = mol.n_nodes
+    x = synthetic.smooth_unknowns(mol.xyz, 0) if kind == "smooth" else synthetic.random_unknowns(n, 0)
+    y_ref = o.matvec(x)
+    y = gpu_matvec(h, x)
+    assert relerr(y, y_ref) < TOL_MATVEC
+    assert relerr(y[:n], y_ref[:n]) < TOL_MATVEC
+    assert relerr(y[n:], y_ref[n:]) < TOL_MATVEC
+    # parts: point sums alone (FMM + P2P) against the oracle's far rule over all t != p
+    y_pt = gpu_matvec(h, x, parts=1 | 2)
+    y_pt_ref = o.matvec(x, mode=1)
+    assert relerr(y_pt, y_pt_ref) < TOL_MATVEC
+    # near correction alone
+    y_nr = gpu_matvec(h, x, parts=4)
+    assert relerr(y_nr, y_ref - y_pt_ref) < 1e-5
+
+
+def test_matvec_host_buffers_equal_device_buffers(born):
+    """Same product through host buffers.  M2L accumulates with float atomics, so two
+    products agree to FP32 rounding, not bit for bit."""
+    mol, h, o = born
+    x = synthetic.random_unknowns(mol.n_nodes, 3).astype(np.float32)
+    y_dev = gpu_matvec(h, x)
+    y_host = h.matvec_host(x).astype(np.float64)
+    assert relerr(y_host, y_dev) < 1e-6
+    np.testing.assert_allclose(y_host, y_dev, rtol=0, atol=2e-5 * np.abs(y_dev).max())
+
+
+def test_rhs_matches_oracle(born):
+    mol, h, o = born
+    np.testing.assert_allclose(h.rhs(), o.rhs(mol.atoms, mol.q), rtol=1e-5)
+
+
+def test_solve_and_energy_match_oracle_and_born(born):
+    mol, h, o = born
+    f, hh, info = h.solve()
+    assert info["status"] == "OK"
+    ref = o.solve(mol.atoms, mol.q)
+    x = np.concatenate([f, hh])
+    x0 = np.concatenate([ref["f"], ref["h"]])
+    assert relerr(x, x0) < 1e-4
+    E = h.energy()
+    assert abs(E / ref["energy"] - 1) < 1e-4
+    E_born = born_energy(1.0, 2.0, 1.0, 80.0, 0.104)
+    assert abs(E / E_born - 1) < 0.005
+    assert info["res_true"] < 1e-5
+
+
+@pytest.mark.parametrize("order", [4, 6, 8])
+@pytest.mark.parametrize("kappa", [0.0, 0.5])
+def test_matvec_orders_and_kappa_kirkwood_small(order, kappa):
+    """Kirkwood geometry at subdivision 5 (10,242 nodes, several tree levels, ragged
+    leaves) with off-centre charges; full comparison against the oracle."""
+    import paper_1710_06316_gb300 as pb
+    mol = synthetic.kirkwood_sphere(subdiv=5, kappa=kappa)
+    o = oracle.Oracle.for_molecule(mol)
+    x = synthetic.random_unknowns(mol.n_nodes, 5)
+    with pb.Handle.for_molecule(mol, order=order, leaf_cap=32) as h:
+        assert h.info()["n_m2l_pairs"] > 0
+        y = gpu_matvec(h, x)
+    y_ref = o.matvec(x)
+    bar = {4: 1e-3, 6: TOL_MATVEC, 8: TOL_MATVEC}[order]
+    assert relerr(y, y_ref) < bar
+
+
+def test_tiny_mesh_without_far_field():
+    """Icosahedron (12 nodes): one leaf, no multipole levels; all pairs by P2P."""
+    import paper_1710_06316_gb300 as pb
+    xyz, tri = synthetic.icosphere(0, radius=1.5)
+    o = oracle.Oracle(xyz, tri, 2.0, 80.0, 0.3)
+    x = synthetic.random_unknowns(12, 1)
+    with pb.Handle(xyz, tri, eps_in=2.0, eps_out=80.0, kappa=0.3) as h:
+        assert h.info()["n_m2l_pairs"] == 0
+        y = gpu_matvec(h, x)
+    assert relerr(y, o.matvec(x)) < 1e-5
+
+
+def test_kirkwood_full_size_sampled_rows():
+    """Kirkwood sphere at full size (163,842 nodes), the bench's launch configuration;
+    4,096 rows sampled and computed one by one by the oracle."""
+    import paper_1710_06316_gb300 as pb
+    mol = synthetic.kirkwood_sphere()
+    o = oracle.Oracle.for_molecule(mol)
+    x = synthetic.smooth_unknowns(mol.xyz, 1)
+    with pb.Handle.for_molecule(mol, order=6) as h:
+        y = gpu_matvec(h, x)
+    rng = np.random.default_rng(7)
+    rows = np.sort(rng.choice(mol.n_nodes, 4096, replace=False))
+    y1, y2 = o.matvec_rows(rows, x)
+    n = mol.n_nodes
+    got = np.concatenate([y[rows], y[n + rows]])
+    ref = np.concatenate([y1, y2])
+    assert relerr(got, ref) < TOL_MATVEC
