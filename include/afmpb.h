@@ -118,6 +118,8 @@ typedef struct {
     int64_t device_bytes;      /* device memory held by the handle                     */
     double root_center[3];
     double root_half_width;
+    double ms_create[6];       /* afmpb_create phases (host clock): geometry, tree and lists,
+                                  near field, FMM operators, right-hand side, graph capture */
 } afmpb_info;
 
 /* Per-stage timing of one product (afmpb_profile_product). */

@@ -57,7 +57,7 @@ class Info(C.Structure):
                 ("n_list_w", C.c_int64), ("n_list_x", C.c_int64), ("n_p2p_pairs", C.c_int64),
                 ("n_m2l_pairs", C.c_int64), ("order", C.c_int), ("precision", C.c_int),
                 ("device_bytes", C.c_int64), ("root_center", C.c_double * 3),
-                ("root_half_width", C.c_double)]
+                ("root_half_width", C.c_double), ("ms_create", C.c_double * 6)]
 
 
 class Profile(C.Structure):

@@ -101,10 +101,21 @@ Err create_impl(afmpb_t *h, const afmpb_mesh *mesh, const afmpb_charges *ch) {
   AFMPB_CUDA(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
   AFMPB_CUDA(cudaEventCreate(&h->ev_t0));
   AFMPB_CUDA(cudaEventCreate(&h->ev_t1));
+  auto lap = [&](int i) {
+    AFMPB_CUDA(cudaStreamSynchronize(h->stream));
+    auto now = std::chrono::steady_clock::now();
+    h->ms_create[i] = std::chrono::duration<double, std::milli>(now - t0).count();
+    for (int k = 0; k < i; ++k) h->ms_create[i] -= h->ms_create[k];
+    return Err{};
+  };
   AFMPB_TRY(build_geometry(h, mesh));
+  AFMPB_TRY(lap(0));
   AFMPB_TRY(build_tree(h));
+  AFMPB_TRY(lap(1));
   AFMPB_TRY(build_near(h));
+  AFMPB_TRY(lap(2));
   AFMPB_TRY(build_fmm(h));
+  AFMPB_TRY(lap(3));
   auto &A = h->arena;
   AFMPB_TRY(A.alloc(&h->d_xs, h->n, "xs"));
   AFMPB_TRY(A.alloc(&h->d_ys, 2 * h->n, "ys"));
@@ -119,9 +130,9 @@ Err create_impl(afmpb_t *h, const afmpb_mesh *mesh, const afmpb_charges *ch) {
     AFMPB_CUDA(cudaMemcpyAsync(h->d_q, ch->q, sizeof(double) * ch->n, cudaMemcpyHostToDevice, h->stream));
   }
   AFMPB_TRY(build_rhs(h));
-  AFMPB_CUDA(cudaStreamSynchronize(h->stream));
+  AFMPB_TRY(lap(4));
   AFMPB_TRY(capture_product(h, AFMPB_PART_ALL));
-  AFMPB_CUDA(cudaStreamSynchronize(h->stream));
+  AFMPB_TRY(lap(5));
   h->ms_setup = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   return Err{};
 }
@@ -370,6 +381,7 @@ afmpb_status afmpb_get_info(const afmpb_t *h, afmpb_info *info) {
   info->device_bytes = (int64_t)h->arena.bytes;
   for (int d = 0; d < 3; ++d) info->root_center[d] = T.c0[d];
   info->root_half_width = T.w0;
+  for (int i = 0; i < 6; ++i) info->ms_create[i] = h->ms_create[i];
   return AFMPB_OK;
 }
 

@@ -117,6 +117,11 @@ struct M2LGroup {
   int level, offset, start, count;
 };
 
+// One tensor-core M2L work item: up to 128 pairs of one group.
+struct TCItem {
+  int group, start, count;
+};
+
 }  // namespace afmpb
 
 struct afmpb_t {
@@ -127,6 +132,7 @@ struct afmpb_t {
   afmpb_options opt{};
   std::string err;
   double ms_setup = 0;
+  double ms_create[6] = {0, 0, 0, 0, 0, 0};
 
   // ---- streams / events --------------------------------------------------------------
   cudaStream_t stream = nullptr;   // handle stream (user's or own)
@@ -188,6 +194,11 @@ struct afmpb_t {
   int2 *d_m2l_pairs = nullptr;     // (target, source) boxes grouped by (level, offset)
   int64_t n_m2l_pairs = 0;
   int m2l_yuk_levels = 0;          // Yukawa M2L skipped on levels below this one
+  // tensor-core M2L (precision 1)
+  int tc_items = 0;
+  afmpb::TCItem *d_tc_items = nullptr;  // work items: (group, first pair, pair count)
+  uint16_t *d_tc_tiles = nullptr;  // BF16 hi/lo translation tiles in the MMA operand layout
+  int *d_tc_level_table = nullptr; // level -> Yukawa tile table
 
   // ---- per-product work --------------------------------------------------------------
   float2 *d_xs = nullptr;          // [n] (f, h) Morton order
@@ -228,6 +239,7 @@ Err enqueue_p2p(afmpb_t *h, cudaStream_t s);          // P2P into d_phi_near
 Err enqueue_combine(afmpb_t *h, cudaStream_t s, int parts);
 Err enqueue_m2l_tc(afmpb_t *h, cudaStream_t s);       // tensor-core M2L (precision 1)
 Err build_m2l_tc(afmpb_t *h);
+Err read_tc_error(int *flag);                          // 1 when a tensor-core wait expired
 // solve.cu
 Err build_rhs(afmpb_t *h);
 Err enqueue_gather(afmpb_t *h, cudaStream_t s, const float *x_caller);

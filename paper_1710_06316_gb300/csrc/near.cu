@@ -3,104 +3,133 @@
 //
 // Near set of node p: t == p, or |x_p - x_t| < c (rho_p + rho_t).  The set is found by a
 // pruned walk of the octree (box distance against c (rho_p + max rho in the box)), so it
-// is exact and independent of the tree.  For each near pair the library stores the
-// correction  X_near - X_far  (t != p) or the self-patch value X_pp, X in {A, B, C, D}:
-// the far-field sums (FMM + P2P) use the point rule for every pair, and the correction
-// turns the near pairs into the near rule.
+// is exact and independent of the tree; the membership test is done in FP64.  For each
+// near pair the library stores the correction  X_near - X_far  (t != p) or the
+// self-patch value X_pp, X in {A, B, C, D}: the far-field sums (FMM + P2P) use the point
+// rule for every pair, and the correction turns the near pairs into the near rule.
 //
 // Near rule over each patch piece of t (two sub-triangles per incident triangle, facet
 // normal as source normal): 7-point degree-5 Radon rule, split 1 -> 4 while the target
 // is closer than 3 times the piece's longest edge to its centroid, at most 6 times.
 // Self patch: the patch projected on the tangent plane of n_p, where the B and C
 // integrands vanish and A, D are weakly singular; polar (Duffy) map about x_p with a
-// 16 x 16 Gauss-Legendre rule.  All in FP64.
+// 16 x 16 Gauss-Legendre rule.
+//
+// Precision: all geometry is first taken relative to the target x_p in FP64 (so no
+// large-coordinate cancellation reaches the quadrature), then the quadrature runs in
+// FP32 (the `Real` template parameter; GB300's FP32 rate is many times its FP64 rate).
 #include <cmath>
 
 #include "internal.cuh"
 
 namespace afmpb {
 
-__constant__ double c_gl_x[16], c_gl_w[16];      // Gauss-Legendre on [0, 1]
-__constant__ double c_rad_b[21], c_rad_w[7];     // Radon 7-point: barycentrics, weights
+__constant__ float c_gl_xf[16], c_gl_wf[16];     // Gauss-Legendre on [0, 1]
+__constant__ float c_rad_bf[21], c_rad_wf[7];    // Radon 7-point: barycentrics, weights
 
 constexpr int kNearStack = 8 * (kMaxLevel + 2);
 constexpr int kQuadDepth = 6;
-constexpr double kRefine = 3.0;
 
 struct KernelParams {
   double kappa, ebar;
 };
 
-// The four Eq. 6 integrands at one point: d = x_target - y_source, n0 target normal,
-// ns source normal.
-__device__ __forceinline__ void abcd_point(const KernelParams &kp, double dx, double dy, double dz,
-                                           const double *n0, const double *ns, double o[4]) {
-  double r2 = dx * dx + dy * dy + dz * dz;
-  double r = sqrt(r2);
-  double ndn = ns[0] * dx + ns[1] * dy + ns[2] * dz;
-  double n0d = n0[0] * dx + n0[1] * dy + n0[2] * dz;
-  double nn0 = ns[0] * n0[0] + ns[1] * n0[1] + ns[2] * n0[2];
-  double G = kInv4Pi / r;
-  double G3 = G / r2;
-  double G5 = 3.0 * G3 / r2;
-  double kr = kp.kappa * r;
-  double e = exp(-kr);
-  double g1 = (e * (1.0 + kr)) * G3;
-  double g2 = (e * (1.0 + kr + kr * kr / 3.0)) * G5;
-  o[0] = G - e * G;
-  o[1] = ndn * G3 / kp.ebar - ndn * g1;
-  o[2] = -n0d * G3 + n0d * g1 / kp.ebar;
-  o[3] = ((nn0 * G3 - ndn * n0d * G5) - (nn0 * g1 - ndn * n0d * g2)) / kp.ebar;
+template <class Real>
+struct V3 {
+  Real x, y, z;
+};
+
+template <class Real>
+__device__ __forceinline__ Real dot(const V3<Real> &a, const V3<Real> &b) {
+  return a.x * b.x + a.y * b.y + a.z * b.z;
 }
 
-// Adaptive Radon quadrature over triangle (v0, v1, v2), stackless walk of the 1 -> 4
-// subdivision tree (path digits), accumulating into acc.
-__device__ void quad_triangle(const KernelParams &kp, const double *x, const double *n0, const double *v0,
-                              const double *v1, const double *v2, const double *ns, double acc[4]) {
+// phi1(x) = 1 - e^{-x}(1 + x) and phi2(x) = 1 - e^{-x}(1 + x + x^2/3): the screened
+// fractions of the Laplace 1/r^3 and 3/r^5 terms.  Below x = 0.5 they are summed from
+// their power series (coefficients of x^j: (-1)^j (j-1) / j! and
+// (-1)^(j+1) (j-1)(j-3) / (3 j!)), which avoids the cancellation of the direct forms.
+template <class Real>
+__device__ __forceinline__ void screened_fractions(Real x, Real &p1, Real &p2) {
+  if (x < Real(0.5)) {
+    Real t = x;            // x^j / j!
+    Real s1 = 0, s2 = 0;
+    for (int j = 2; j < 16; ++j) {
+      t *= x / (Real)j;
+      const Real sg = (j & 1) ? Real(-1) : Real(1);
+      s1 += sg * (Real)(j - 1) * t;
+      s2 -= sg * (Real)((j - 1) * (j - 3)) * t / Real(3);
+    }
+    p1 = s1;
+    p2 = s2;
+  } else {
+    const Real e = exp(-x);
+    p1 = Real(1) - e * (Real(1) + x);
+    p2 = Real(1) - e * (Real(1) + x + x * x / Real(3));
+  }
+}
+
+// The four Eq. 6 integrands at one point: d = x_target - y_source, n0 target normal,
+// ns source normal.  The G - u differences of A and D are formed without cancellation
+// (A through expm1, D through the screened fractions above).
+template <class Real>
+__device__ __forceinline__ void abcd_point(Real kappa, Real ebar, const V3<Real> &d, const V3<Real> &n0,
+                                           const V3<Real> &ns, Real o[4]) {
+  const Real r2 = dot(d, d);
+  const Real r = sqrt(r2);
+  const Real ndn = dot(ns, d), n0d = dot(n0, d), nn0 = dot(ns, n0);
+  const Real G = Real(kInv4Pi) / r;
+  const Real G3 = G / r2;
+  const Real G5 = Real(3) * G3 / r2;
+  const Real kr = kappa * r;
+  const Real e = exp(-kr);
+  const Real g1 = (e * (Real(1) + kr)) * G3;
+  Real p1, p2;
+  screened_fractions(kr, p1, p2);
+  o[0] = -expm1(-kr) * G;                       // G - u
+  o[1] = ndn * G3 / ebar - ndn * g1;
+  o[2] = -n0d * G3 + n0d * g1 / ebar;
+  o[3] = (nn0 * G3 * p1 - ndn * n0d * G5 * p2) / ebar;
+}
+
+// Adaptive Radon quadrature over triangle (v0, v1, v2) for a target at the origin,
+// stackless walk of the 1 -> 4 subdivision tree (path digits), accumulating into acc.
+template <class Real>
+__device__ void quad_triangle(Real kappa, Real ebar, const V3<Real> &n0, const V3<Real> &v0, const V3<Real> &v1,
+                              const V3<Real> &v2, const V3<Real> &ns, Real acc[4]) {
   int dig[kQuadDepth + 1];
   int d = 0;
   dig[0] = 0;
   while (true) {
-    double a[3], b[3], c[3];
-    for (int k = 0; k < 3; ++k) { a[k] = v0[k]; b[k] = v1[k]; c[k] = v2[k]; }
+    V3<Real> a = v0, b = v1, c = v2;
     for (int l = 1; l <= d; ++l) {
-      double mab[3], mbc[3], mca[3];
-      for (int k = 0; k < 3; ++k) {
-        mab[k] = 0.5 * (a[k] + b[k]); mbc[k] = 0.5 * (b[k] + c[k]); mca[k] = 0.5 * (c[k] + a[k]);
-      }
+      const V3<Real> mab{Real(0.5) * (a.x + b.x), Real(0.5) * (a.y + b.y), Real(0.5) * (a.z + b.z)};
+      const V3<Real> mbc{Real(0.5) * (b.x + c.x), Real(0.5) * (b.y + c.y), Real(0.5) * (b.z + c.z)};
+      const V3<Real> mca{Real(0.5) * (c.x + a.x), Real(0.5) * (c.y + a.y), Real(0.5) * (c.z + a.z)};
       switch (dig[l]) {
-        case 0: for (int k = 0; k < 3; ++k) { b[k] = mab[k]; c[k] = mca[k]; } break;
-        case 1: for (int k = 0; k < 3; ++k) { a[k] = mab[k]; c[k] = mbc[k]; } break;
-        case 2: for (int k = 0; k < 3; ++k) { a[k] = mca[k]; b[k] = mbc[k]; } break;
-        default: for (int k = 0; k < 3; ++k) { a[k] = mab[k]; b[k] = mbc[k]; c[k] = mca[k]; } break;
+        case 0: b = mab; c = mca; break;
+        case 1: a = mab; c = mbc; break;
+        case 2: a = mca; b = mbc; break;
+        default: a = mab; b = mbc; c = mca; break;
       }
     }
-    double e01[3], e12[3], e20[3];
-    for (int k = 0; k < 3; ++k) { e01[k] = b[k] - a[k]; e12[k] = c[k] - b[k]; e20[k] = a[k] - c[k]; }
-    double l01 = sqrt(e01[0] * e01[0] + e01[1] * e01[1] + e01[2] * e01[2]);
-    double l12 = sqrt(e12[0] * e12[0] + e12[1] * e12[1] + e12[2] * e12[2]);
-    double l20 = sqrt(e20[0] * e20[0] + e20[1] * e20[1] + e20[2] * e20[2]);
-    double diam = fmax(l01, fmax(l12, l20));
-    double gx = (a[0] + b[0] + c[0]) / 3.0 - x[0], gy = (a[1] + b[1] + c[1]) / 3.0 - x[1],
-           gz = (a[2] + b[2] + c[2]) / 3.0 - x[2];
-    double dist = sqrt(gx * gx + gy * gy + gz * gz);
-    if (d < kQuadDepth && dist < kRefine * diam) {
+    const V3<Real> e01{b.x - a.x, b.y - a.y, b.z - a.z}, e12{c.x - b.x, c.y - b.y, c.z - b.z},
+        e02{c.x - a.x, c.y - a.y, c.z - a.z};
+    const Real diam = sqrt(fmax(dot(e01, e01), fmax(dot(e12, e12), dot(e02, e02))));
+    const V3<Real> g{(a.x + b.x + c.x) / Real(3), (a.y + b.y + c.y) / Real(3), (a.z + b.z + c.z) / Real(3)};
+    if (d < kQuadDepth && sqrt(dot(g, g)) < Real(3) * diam) {
       ++d;
       dig[d] = 0;
       continue;
     }
-    // e02 = c - a = -e20
-    double cr0 = e01[1] * (-e20[2]) - e01[2] * (-e20[1]);
-    double cr1 = e01[2] * (-e20[0]) - e01[0] * (-e20[2]);
-    double cr2 = e01[0] * (-e20[1]) - e01[1] * (-e20[0]);
-    double area = 0.5 * sqrt(cr0 * cr0 + cr1 * cr1 + cr2 * cr2);
+    const V3<Real> cr{e01.y * e02.z - e01.z * e02.y, e01.z * e02.x - e01.x * e02.z, e01.x * e02.y - e01.y * e02.x};
+    const Real area = Real(0.5) * sqrt(dot(cr, cr));
     for (int q = 0; q < 7; ++q) {
-      double y0 = c_rad_b[3 * q] * a[0] + c_rad_b[3 * q + 1] * b[0] + c_rad_b[3 * q + 2] * c[0];
-      double y1 = c_rad_b[3 * q] * a[1] + c_rad_b[3 * q + 1] * b[1] + c_rad_b[3 * q + 2] * c[1];
-      double y2 = c_rad_b[3 * q] * a[2] + c_rad_b[3 * q + 1] * b[2] + c_rad_b[3 * q + 2] * c[2];
-      double o[4];
-      abcd_point(kp, x[0] - y0, x[1] - y1, x[2] - y2, n0, ns, o);
-      double w = area * c_rad_w[q];
+      const Real b0 = c_rad_bf[3 * q], b1 = c_rad_bf[3 * q + 1], b2 = c_rad_bf[3 * q + 2];
+      const V3<Real> dq{-(b0 * a.x + b1 * b.x + b2 * c.x), -(b0 * a.y + b1 * b.y + b2 * c.y),
+                        -(b0 * a.z + b1 * b.z + b2 * c.z)};
+      Real o[4];
+      abcd_point(kappa, ebar, dq, n0, ns, o);
+      const Real w = area * c_rad_wf[q];
       for (int k = 0; k < 4; ++k) acc[k] += w * o[k];
     }
     while (d > 0 && dig[d] == 3) --d;
@@ -109,85 +138,83 @@ __device__ void quad_triangle(const KernelParams &kp, const double *x, const dou
   }
 }
 
-// Corner positions of triangle t rotated so that node v comes first.
-__device__ __forceinline__ void tri_from(const double *xyz, const int32_t *tri, int32_t t, int64_t v, double P[3][3]) {
+// Corners of triangle t rotated so that node v comes first, relative to the point o
+// (difference taken in FP64).
+template <class Real>
+__device__ __forceinline__ void tri_rel(const double *xyz, const int32_t *tri, int32_t t, int64_t v,
+                                        const double *o, V3<Real> P[3]) {
   int k0 = 0;
   for (int k = 0; k < 3; ++k)
     if (tri[3 * t + k] == v) k0 = k;
   for (int j = 0; j < 3; ++j) {
     const double *q = xyz + 3 * (int64_t)tri[3 * t + (k0 + j) % 3];
-    P[j][0] = q[0]; P[j][1] = q[1]; P[j][2] = q[2];
+    P[j] = V3<Real>{(Real)(q[0] - o[0]), (Real)(q[1] - o[1]), (Real)(q[2] - o[2])};
   }
 }
 
-__device__ void near_rule(const KernelParams &kp, const double *xyz, const int32_t *tri, const int64_t *inc_ptr,
-                          const int32_t *inc_tri, const double *tri_nrm, const double *xp, const double *np,
-                          int64_t ot, double acc[4]) {
+template <class Real>
+__device__ void near_rule(Real kappa, Real ebar, const double *xyz, const int32_t *tri, const int64_t *inc_ptr,
+                          const int32_t *inc_tri, const double *tri_nrm, const double *xp, const V3<Real> &np,
+                          int64_t ot, Real acc[4]) {
   for (int64_t j = inc_ptr[ot]; j < inc_ptr[ot + 1]; ++j) {
-    int32_t T = inc_tri[j];
-    double P[3][3];
-    tri_from(xyz, tri, T, ot, P);
-    double ma[3], mb[3], cen[3];
-    for (int k = 0; k < 3; ++k) {
-      ma[k] = 0.5 * (P[0][k] + P[1][k]);
-      mb[k] = 0.5 * (P[0][k] + P[2][k]);
-      cen[k] = (P[0][k] + P[1][k] + P[2][k]) / 3.0;
-    }
-    const double *ns = tri_nrm + 3 * (int64_t)T;
-    quad_triangle(kp, xp, np, P[0], ma, cen, ns, acc);
-    quad_triangle(kp, xp, np, P[0], cen, mb, ns, acc);
+    const int32_t T = inc_tri[j];
+    V3<Real> P[3];
+    tri_rel(xyz, tri, T, ot, xp, P);
+    const V3<Real> ma{Real(0.5) * (P[0].x + P[1].x), Real(0.5) * (P[0].y + P[1].y), Real(0.5) * (P[0].z + P[1].z)};
+    const V3<Real> mb{Real(0.5) * (P[0].x + P[2].x), Real(0.5) * (P[0].y + P[2].y), Real(0.5) * (P[0].z + P[2].z)};
+    const V3<Real> cen{(P[0].x + P[1].x + P[2].x) / Real(3), (P[0].y + P[1].y + P[2].y) / Real(3),
+                       (P[0].z + P[1].z + P[2].z) / Real(3)};
+    const double *tn = tri_nrm + 3 * (int64_t)T;
+    const V3<Real> ns{(Real)tn[0], (Real)tn[1], (Real)tn[2]};
+    quad_triangle(kappa, ebar, np, P[0], ma, cen, ns, acc);
+    quad_triangle(kappa, ebar, np, P[0], cen, mb, ns, acc);
   }
 }
 
-__device__ void self_rule(const KernelParams &kp, const double *xyz, const int32_t *tri, const int64_t *inc_ptr,
-                          const int32_t *inc_tri, int64_t op, const double *np, double o[4]) {
+template <class Real>
+__device__ void self_rule(Real kappa, Real ebar, const double *xyz, const int32_t *tri, const int64_t *inc_ptr,
+                          const int32_t *inc_tri, int64_t op, const V3<Real> &np, Real o[4]) {
   const double *xp = xyz + 3 * op;
-  double As = 0.0, Ds = 0.0;
+  Real As = 0, Ds = 0;
   for (int64_t j = inc_ptr[op]; j < inc_ptr[op + 1]; ++j) {
-    int32_t T = inc_tri[j];
-    double P[3][3];
-    tri_from(xyz, tri, T, op, P);
-    double ma[3], mb[3], cen[3];
-    for (int k = 0; k < 3; ++k) {
-      ma[k] = 0.5 * (P[0][k] + P[1][k]);
-      mb[k] = 0.5 * (P[0][k] + P[2][k]);
-      cen[k] = (P[0][k] + P[1][k] + P[2][k]) / 3.0;
-    }
-    const double *far_pts[2][2] = {{ma, cen}, {cen, mb}};
+    V3<Real> P[3];
+    tri_rel(xyz, tri, inc_tri[j], op, xp, P);   // P[0] = 0 (the node itself)
+    const V3<Real> ma{Real(0.5) * P[1].x, Real(0.5) * P[1].y, Real(0.5) * P[1].z};
+    const V3<Real> mb{Real(0.5) * P[2].x, Real(0.5) * P[2].y, Real(0.5) * P[2].z};
+    const V3<Real> cen{(P[1].x + P[2].x) / Real(3), (P[1].y + P[2].y) / Real(3), (P[1].z + P[2].z) / Real(3)};
+    const V3<Real> far_pts[2][2] = {{ma, cen}, {cen, mb}};
     for (int q = 0; q < 2; ++q) {
-      double e[2][3];
-      for (int v = 0; v < 2; ++v) {
-        double dv[3] = {far_pts[q][v][0] - xp[0], far_pts[q][v][1] - xp[1], far_pts[q][v][2] - xp[2]};
-        double hgt = dv[0] * np[0] + dv[1] * np[1] + dv[2] * np[2];
-        for (int k = 0; k < 3; ++k) e[v][k] = dv[k] - hgt * np[k];
+      V3<Real> e[2];
+      for (int v = 0; v < 2; ++v) {     // project on the tangent plane of n_p
+        const V3<Real> dv = far_pts[q][v];
+        const Real hgt = dot(dv, np);
+        e[v] = V3<Real>{dv.x - hgt * np.x, dv.y - hgt * np.y, dv.z - hgt * np.z};
       }
-      double c0 = e[0][1] * e[1][2] - e[0][2] * e[1][1];
-      double c1 = e[0][2] * e[1][0] - e[0][0] * e[1][2];
-      double c2 = e[0][0] * e[1][1] - e[0][1] * e[1][0];
-      double J = sqrt(c0 * c0 + c1 * c1 + c2 * c2);
+      const V3<Real> cr{e[0].y * e[1].z - e[0].z * e[1].y, e[0].z * e[1].x - e[0].x * e[1].z,
+                        e[0].x * e[1].y - e[0].y * e[1].x};
+      const Real J = sqrt(dot(cr, cr));
       for (int it = 0; it < 16; ++it) {
-        double tt = c_gl_x[it], wt = c_gl_w[it];
-        double w0 = e[0][0] + tt * (e[1][0] - e[0][0]);
-        double w1 = e[0][1] + tt * (e[1][1] - e[0][1]);
-        double w2 = e[0][2] + tt * (e[1][2] - e[0][2]);
-        double l = sqrt(w0 * w0 + w1 * w1 + w2 * w2);
+        const Real tt = c_gl_xf[it], wt = c_gl_wf[it];
+        const V3<Real> w{e[0].x + tt * (e[1].x - e[0].x), e[0].y + tt * (e[1].y - e[0].y),
+                         e[0].z + tt * (e[1].z - e[0].z)};
+        const Real l = sqrt(dot(w, w));
         for (int is = 0; is < 16; ++is) {
-          double ss = c_gl_x[is], ws = c_gl_w[is];
-          double xk = kp.kappa * ss * l;
-          double fa = -expm1(-xk) * kInv4Pi / l;
-          double num;
-          if (xk < 0.05) {
+          const Real ss = c_gl_xf[is], ws = c_gl_wf[is];
+          const Real xk = kappa * ss * l;
+          const Real fa = -expm1(-xk) * Real(kInv4Pi) / l;
+          Real num;
+          if (xk < Real(0.5)) {
             // 1 - e^{-x}(1 + x) = sum_{j>=2} (-1)^j (j - 1) x^j / j!
-            double term = 0.5 * xk * xk, s = term;
-            for (int jj = 3; jj < 12; ++jj) {
-              term *= -xk * (double)(jj - 1) / ((double)jj * (double)(jj - 2));
+            Real term = Real(0.5) * xk * xk, s = term;
+            for (int jj = 3; jj < 14; ++jj) {
+              term *= -xk * (Real)(jj - 1) / ((Real)jj * (Real)(jj - 2));
               s += term;
             }
             num = s;
           } else {
-            num = 1.0 - exp(-xk) * (1.0 + xk);
+            num = Real(1) - exp(-xk) * (Real(1) + xk);
           }
-          double fd = num * kInv4Pi / (ss * ss * l * l * l);
+          const Real fd = num * Real(kInv4Pi) / (ss * ss * l * l * l);
           As += J * wt * ws * fa;
           Ds += J * wt * ws * fd;
         }
@@ -195,9 +222,9 @@ __device__ void self_rule(const KernelParams &kp, const double *xyz, const int32
     }
   }
   o[0] = As;
-  o[1] = 0.0;
-  o[2] = 0.0;
-  o[3] = Ds / kp.ebar;
+  o[1] = 0;
+  o[2] = 0;
+  o[3] = Ds / ebar;
 }
 
 // Near-set walk.  fill == false: count per row; else write the columns.
@@ -242,30 +269,36 @@ __global__ void k_near_search(int64_t n, double cnear, const int32_t *__restrict
 }
 
 // Coefficients, one warp per row.
-__global__ void k_near_coef(int64_t n, KernelParams kp, const int32_t *__restrict__ perm,
-                            const double *__restrict__ xyz, const int32_t *__restrict__ tri,
-                            const int64_t *__restrict__ inc_ptr, const int32_t *__restrict__ inc_tri,
-                            const double *__restrict__ tri_nrm, const double *__restrict__ area,
-                            const double *__restrict__ nrm, const int64_t *__restrict__ ptr,
-                            const int32_t *__restrict__ col, float4 *__restrict__ coef) {
-  int64_t p = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  int lane = threadIdx.x & 31;
+template <class Real>
+__global__ void __launch_bounds__(128) k_near_coef(int64_t n, KernelParams kp, const int32_t *__restrict__ perm,
+                                                   const double *__restrict__ xyz, const int32_t *__restrict__ tri,
+                                                   const int64_t *__restrict__ inc_ptr,
+                                                   const int32_t *__restrict__ inc_tri,
+                                                   const double *__restrict__ tri_nrm, const double *__restrict__ area,
+                                                   const double *__restrict__ nrm, const int64_t *__restrict__ ptr,
+                                                   const int32_t *__restrict__ col, float4 *__restrict__ coef) {
+  const int64_t p = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
   if (p >= n) return;
-  int64_t op = perm[p];
+  const int64_t op = perm[p];
   const double *xp = xyz + 3 * op;
-  const double *np = nrm + 3 * op;
+  const V3<Real> np{(Real)nrm[3 * op], (Real)nrm[3 * op + 1], (Real)nrm[3 * op + 2]};
+  const Real kappa = (Real)kp.kappa, ebar = (Real)kp.ebar;
   for (int64_t j = ptr[p] + lane; j < ptr[p + 1]; j += 32) {
-    int t = col[j];
-    int64_t ot = perm[t];
-    double o[4] = {0, 0, 0, 0};
+    const int t = col[j];
+    const int64_t ot = perm[t];
+    Real o[4] = {0, 0, 0, 0};
     if (t == p) {
-      self_rule(kp, xyz, tri, inc_ptr, inc_tri, op, np, o);
+      self_rule(kappa, ebar, xyz, tri, inc_ptr, inc_tri, op, np, o);
     } else {
-      near_rule(kp, xyz, tri, inc_ptr, inc_tri, tri_nrm, xp, np, ot, o);
-      double f[4];
+      near_rule(kappa, ebar, xyz, tri, inc_ptr, inc_tri, tri_nrm, xp, np, ot, o);
       const double *xt = xyz + 3 * ot;
-      abcd_point(kp, xp[0] - xt[0], xp[1] - xt[1], xp[2] - xt[2], np, nrm + 3 * ot, f);
-      for (int k = 0; k < 4; ++k) o[k] -= area[ot] * f[k];
+      const V3<Real> d{(Real)(xp[0] - xt[0]), (Real)(xp[1] - xt[1]), (Real)(xp[2] - xt[2])};
+      const V3<Real> nt{(Real)nrm[3 * ot], (Real)nrm[3 * ot + 1], (Real)nrm[3 * ot + 2]};
+      Real f[4];
+      abcd_point(kappa, ebar, d, np, nt, f);
+      const Real at = (Real)area[ot];
+      for (int k = 0; k < 4; ++k) o[k] -= at * f[k];
     }
     coef[j] = make_float4((float)o[0], (float)o[1], (float)o[2], (float)o[3]);
   }
@@ -308,18 +341,23 @@ Err build_near(afmpb_t *h) {
   {
     double gx[16], gw[16];
     gauss_legendre_unit(16, gx, gw);
-    AFMPB_CUDA(cudaMemcpyToSymbolAsync(c_gl_x, gx, sizeof(gx), 0, cudaMemcpyHostToDevice, s));
-    AFMPB_CUDA(cudaMemcpyToSymbolAsync(c_gl_w, gw, sizeof(gw), 0, cudaMemcpyHostToDevice, s));
+    float fx[16], fw[16];
+    for (int i = 0; i < 16; ++i) { fx[i] = (float)gx[i]; fw[i] = (float)gw[i]; }
+    AFMPB_CUDA(cudaMemcpyToSymbolAsync(c_gl_xf, fx, sizeof(fx), 0, cudaMemcpyHostToDevice, s));
+    AFMPB_CUDA(cudaMemcpyToSymbolAsync(c_gl_wf, fw, sizeof(fw), 0, cudaMemcpyHostToDevice, s));
     // Radon's 7-point rule (exact for degree 5): centroid and two orbits of three points
     const double r15 = std::sqrt(15.0);
     const double a1 = (6.0 - r15) / 21.0, a2 = (6.0 + r15) / 21.0;
     const double w1 = (155.0 - r15) / 1200.0, w2 = (155.0 + r15) / 1200.0;
-    double b[21] = {1.0 / 3, 1.0 / 3, 1.0 / 3,
-                    a1, a1, 1 - 2 * a1, a1, 1 - 2 * a1, a1, 1 - 2 * a1, a1, a1,
-                    a2, a2, 1 - 2 * a2, a2, 1 - 2 * a2, a2, 1 - 2 * a2, a2, a2};
-    double w[7] = {9.0 / 40, w1, w1, w1, w2, w2, w2};
-    AFMPB_CUDA(cudaMemcpyToSymbolAsync(c_rad_b, b, sizeof(b), 0, cudaMemcpyHostToDevice, s));
-    AFMPB_CUDA(cudaMemcpyToSymbolAsync(c_rad_w, w, sizeof(w), 0, cudaMemcpyHostToDevice, s));
+    const double b[21] = {1.0 / 3, 1.0 / 3, 1.0 / 3,
+                          a1, a1, 1 - 2 * a1, a1, 1 - 2 * a1, a1, 1 - 2 * a1, a1, a1,
+                          a2, a2, 1 - 2 * a2, a2, 1 - 2 * a2, a2, 1 - 2 * a2, a2, a2};
+    const double w[7] = {9.0 / 40, w1, w1, w1, w2, w2, w2};
+    float bf[21], wf[7];
+    for (int i = 0; i < 21; ++i) bf[i] = (float)b[i];
+    for (int i = 0; i < 7; ++i) wf[i] = (float)w[i];
+    AFMPB_CUDA(cudaMemcpyToSymbolAsync(c_rad_bf, bf, sizeof(bf), 0, cudaMemcpyHostToDevice, s));
+    AFMPB_CUDA(cudaMemcpyToSymbolAsync(c_rad_wf, wf, sizeof(wf), 0, cudaMemcpyHostToDevice, s));
   }
   int64_t *d_cnt = nullptr;
   AFMPB_TRY(A.alloc(&d_cnt, n, "near cnt"));
@@ -342,9 +380,9 @@ Err build_near(afmpb_t *h) {
                                                h->d_box_end, nullptr, h->d_near_ptr, h->d_near_col, true);
   AFMPB_TRY(check_launch("k_near_search fill"));
   KernelParams kp{h->kappa, h->ebar};
-  k_near_coef<<<div_up(n * 32, 128), 128, 0, s>>>(n, kp, h->d_perm, h->d_xyz, h->d_tri, h->d_inc_ptr, h->d_inc_tri,
-                                                   h->d_tri_nrm, h->d_area64, h->d_nrm64, h->d_near_ptr,
-                                                   h->d_near_col, h->d_near_coef);
+  k_near_coef<float><<<div_up(n * 32, 128), 128, 0, s>>>(n, kp, h->d_perm, h->d_xyz, h->d_tri, h->d_inc_ptr,
+                                                          h->d_inc_tri, h->d_tri_nrm, h->d_area64, h->d_nrm64,
+                                                          h->d_near_ptr, h->d_near_col, h->d_near_coef);
   AFMPB_TRY(check_launch("k_near_coef"));
   AFMPB_CUDA(cudaStreamSynchronize(s));
   A.release(d_cnt);

@@ -437,6 +437,11 @@ Err run_solve(afmpb_t *h, afmpb_solve_info *info) {
   float ms_all = 0.f;
   AFMPB_CUDA(cudaEventElapsedTime(&ms_all, h->ev_t0, h->ev_t1));
   h->solved = true;
+  if (h->opt.precision == 1) {
+    int flag = 0;
+    AFMPB_TRY(read_tc_error(&flag));
+    if (flag) return make_err(AFMPB_ETIMEOUT, "a tensor-core M2L wait expired; the products are not valid");
+  }
   if (info) {
     info->iters = iters;
     info->restarts = restarts;
