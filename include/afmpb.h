@@ -79,7 +79,7 @@ typedef struct {
 
 /* Options; a zero-initialised struct selects every default. */
 typedef struct {
-    int leaf_cap;        /* most nodes in a leaf box of the octree (default 48)          */
+    int leaf_cap;        /* most nodes in a leaf box of the octree (default 128)         */
     int restart;         /* GMRES Krylov dimension m (default 80, Sec. 5)                */
     int max_restart;     /* GMRES restarts allowed (default 5, Sec. 5)                   */
     double abs_tol;      /* eps_abs of Eq. 7 (default 0)                                 */

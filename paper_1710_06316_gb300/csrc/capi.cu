@@ -174,7 +174,7 @@ afmpb_status afmpb_create(const afmpb_mesh *mesh, const afmpb_charges *charges, 
   h->order = fmm_order;
   h->ncoef = fmm_order * fmm_order * fmm_order;
   if (options) h->opt = *options;
-  if (h->opt.leaf_cap == 0) h->opt.leaf_cap = 48;
+  if (h->opt.leaf_cap == 0) h->opt.leaf_cap = 128;
   if (h->opt.restart == 0) h->opt.restart = 80;
   if (h->opt.max_restart == 0 && !(options && options->max_restart == 0 && options->restart != 0)) h->opt.max_restart = 5;
   if (h->opt.near_c == 0) h->opt.near_c = 2.0;
@@ -481,7 +481,7 @@ const char *afmpb_last_error(const afmpb_t *h) { return h ? h->err.c_str() : g_e
 
 size_t afmpb_estimate_bytes(int64_t n_nodes, int64_t n_atoms, int fmm_order, const afmpb_options *o) {
   if (n_nodes <= 0 || fmm_order < 2 || fmm_order > kMaxOrder) return 0;
-  const int cap = (o && o->leaf_cap > 0) ? o->leaf_cap : 48;
+  const int cap = (o && o->leaf_cap > 0) ? o->leaf_cap : 128;
   const int m = (o && o->restart > 0) ? o->restart : 80;
   const size_t n = (size_t)n_nodes, n3 = (size_t)fmm_order * fmm_order * fmm_order;
   const size_t nbox = 3 * (n / (size_t)std::max(cap / 2, 1) + 64);

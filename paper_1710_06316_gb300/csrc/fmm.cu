@@ -540,6 +540,140 @@ __global__ void __launch_bounds__(kP2PThreads) k_p2p_v2(const int32_t *__restric
   }
 }
 
+// Far-rule sums of one source at one target, without the 1/(4 pi):
+//   PhiL += c/r + (g/eps_bar) (n.d)/r^3
+//   dn PhiL += -c (n0.d)/r^3 + (g/eps_bar) [(n0.n)/r^3 - 3 (n.d)(n0.d)/r^5]
+//   PhiY += c e/r + g (n.d) e1/r^3,           e = exp(-kr), e1 = e (1 + kr)
+//   dn PhiY += e1 [g (n0.n) - c (n0.d)]/r^3 - 3 g e2 (n.d)(n0.d)/r^5,  e2 = e (1 + kr + (kr)^2/3)
+// with d = x_target - y_source; subexpressions are shared between the two kernels.
+__device__ __forceinline__ void p2p_pair(const float4 &xp, const float4 &np, const float4 &y, const float4 &q,
+                                         float inv_ebar, float kappa, float &sL, float &dL, float &sY,
+                                         float &dY) {
+  const float dx = xp.x - y.x, dy = xp.y - y.y, dz = xp.z - y.z;
+  const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+  const float ri = r2 > 0.0f ? rsqrtf(r2) : 0.0f;     // t == p contributes nothing
+  const float ri2 = ri * ri;
+  const float G3 = ri * ri2;
+  const float ndt = fmaf(q.x, dx, fmaf(q.y, dy, q.z * dz));
+  const float npd = fmaf(np.x, dx, fmaf(np.y, dy, np.z * dz));
+  const float nn = fmaf(np.x, q.x, fmaf(np.y, q.y, np.z * q.z));
+  const float kr = kappa * (r2 * ri);
+  const float ex = __expf(-kr);
+  const float e1 = fmaf(ex, kr, ex);
+  const float e2 = fmaf(ex * kr, kr * (1.0f / 3.0f), e1);
+  const float c = y.w, g = q.w;
+  const float cri = c * ri;
+  const float G3n = ndt * G3;
+  const float npG3 = npd * G3;
+  const float nnG3 = nn * G3;
+  const float T = 3.0f * G3n * npd * ri2;
+  const float gL = g * inv_ebar;
+  sL += fmaf(gL, G3n, cri);
+  dL += fmaf(gL, nnG3 - T, -c * npG3);
+  sY = fmaf(ex, cri, fmaf(g * e1, G3n, sY));
+  dY = fmaf(e1, fmaf(g, nnG3, -c * npG3), fmaf(-g * e2, T, dY));
+}
+
+// One CTA per target leaf.  Threads form a (target x source slice) grid with
+// tile = min(targets, 128) targets and floor(128 / tile) slices, so no lane is padded
+// away for leaves whose size is not a power of two.  The leaf's list-1 and list-3 source
+// leaves are described in shared memory 64 at a time (warp prefix scan of their sizes);
+// their nodes are staged 512 at a time, each shifted by its own leaf centre's offset,
+// and every thread sums its target against every slices-th staged source.
+__global__ void __launch_bounds__(kP2PThreads) k_p2p_v3(const int32_t *__restrict__ leaves,
+                                                         const int64_t *__restrict__ pptr,
+                                                         const int32_t *__restrict__ pidx,
+                                                         const int32_t *__restrict__ bbeg,
+                                                         const int32_t *__restrict__ bend,
+                                                         const dbl4 *__restrict__ center,
+                                                         const float4 *__restrict__ pos,
+                                                         const float4 *__restrict__ nrm,
+                                                         const float2 *__restrict__ xs, float inv_ebar,
+                                                         float kappa, float4 *__restrict__ phi) {
+  __shared__ float4 sp[kP2PChunk], sn[kP2PChunk];
+  __shared__ int s_beg[kP2PBoxes], s_pre[kP2PBoxes + 1];
+  __shared__ float s_off[kP2PBoxes][3];
+  __shared__ float4 red[kP2PThreads];
+  const int leaf = blockIdx.x;
+  const int b = leaves[leaf];
+  const dbl4 cb = center[b];
+  const int tb = bbeg[b], te = bend[b];
+  const int tile = min(te - tb, kP2PThreads);
+  const int slices = kP2PThreads / tile;
+  const int ti = threadIdx.x % tile, si = threadIdx.x / tile;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t l0 = pptr[leaf], l1 = pptr[leaf + 1];
+  for (int t0 = tb; t0 < te; t0 += tile) {
+    const int t = t0 + ti;
+    const bool act = si < slices && t < te;
+    const float4 xp = act ? pos[t] : make_float4(0, 0, 0, 0);
+    const float4 np = act ? nrm[t] : make_float4(0, 0, 0, 0);
+    float sL = 0.f, dL = 0.f, sY = 0.f, dY = 0.f;
+    for (int64_t g0 = l0; g0 < l1; g0 += kP2PBoxes) {
+      const int nb = (int)min((int64_t)kP2PBoxes, l1 - g0);
+      __syncthreads();
+      int mycnt = 0;
+      if (threadIdx.x < nb) {
+        const int c = pidx[g0 + threadIdx.x];
+        const dbl4 cc = center[c];
+        s_beg[threadIdx.x] = bbeg[c];
+        mycnt = bend[c] - bbeg[c];
+        s_off[threadIdx.x][0] = (float)(cc.x - cb.x);
+        s_off[threadIdx.x][1] = (float)(cc.y - cb.y);
+        s_off[threadIdx.x][2] = (float)(cc.z - cb.z);
+      }
+      if (warp < 2) {                       // inclusive scan of the (<= 64) box sizes
+        int v = mycnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int u = __shfl_up_sync(0xffffffffu, v, o);
+          if (lane >= o) v += u;
+        }
+        s_pre[threadIdx.x + 1] = v;         // per-warp partial; fixed up below
+      }
+      __syncthreads();
+      if (threadIdx.x >= 32 && threadIdx.x < 64) s_pre[threadIdx.x + 1] += s_pre[32];
+      if (threadIdx.x == 0) s_pre[0] = 0;
+      __syncthreads();
+      const int total = s_pre[nb];
+      for (int c0 = 0; c0 < total; c0 += kP2PChunk) {
+        const int cnt = min(kP2PChunk, total - c0);
+        if (c0 > 0) __syncthreads();
+        for (int e = threadIdx.x; e < cnt; e += kP2PThreads) {
+          const int j = c0 + e;
+          int lo = 0, hi = nb;              // last box with s_pre[box] <= j
+          while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (s_pre[mid] <= j) lo = mid; else hi = mid;
+          }
+          const int sidx = s_beg[lo] + (j - s_pre[lo]);
+          const float4 p = pos[sidx], q = nrm[sidx];
+          const float2 fh = xs[sidx];
+          sp[e] = make_float4(p.x + s_off[lo][0], p.y + s_off[lo][1], p.z + s_off[lo][2], p.w * fh.y);
+          sn[e] = make_float4(q.x, q.y, q.z, -p.w * fh.x);
+        }
+        __syncthreads();
+        if (act) {
+#pragma unroll 4
+          for (int e = si; e < cnt; e += slices) p2p_pair(xp, np, sp[e], sn[e], inv_ebar, kappa, sL, dL, sY, dY);
+        }
+      }
+    }
+    __syncthreads();
+    red[threadIdx.x] = make_float4(sL, dL, sY, dY);
+    __syncthreads();
+    if (si == 0 && t < te) {
+      float4 a = red[ti];
+      for (int k = 1; k < slices; ++k) {
+        const float4 v = red[k * tile + ti];
+        a.x += v.x; a.y += v.y; a.z += v.z; a.w += v.w;
+      }
+      const float s = (float)kInv4Pi;
+      phi[t] = make_float4(s * a.x, s * a.y, s * a.z, s * a.w);
+    }
+  }
+}
+
 constexpr int kP2PThreadsV1 = 64;
 constexpr int kP2PChunkV1 = 256;
 
@@ -739,10 +873,10 @@ Err enqueue_far(afmpb_t *h, cudaStream_t s, StageTimer *tm) {
 
 Err enqueue_p2p(afmpb_t *h, cudaStream_t s) {
   const auto &T = h->shape;
-  k_p2p_v2<<<T.nleaf, kP2PThreads, 0, s>>>(h->d_leaves, h->d_p2p_ptr, h->d_p2p_idx, h->d_box_begin, h->d_box_end,
+  k_p2p_v3<<<T.nleaf, kP2PThreads, 0, s>>>(h->d_leaves, h->d_p2p_ptr, h->d_p2p_idx, h->d_box_begin, h->d_box_end,
                                         h->d_box_center, h->d_pos, h->d_nrm, h->d_xs, (float)(1.0 / h->ebar),
                                         (float)h->kappa, h->d_phi_near);
-  return check_launch("k_p2p_v2");
+  return check_launch("k_p2p_v3");
 }
 
 Err enqueue_combine(afmpb_t *h, cudaStream_t s, int parts) {

@@ -3,19 +3,23 @@
 //
 // Each (level, offset) group of list-2 pairs is a dense product
 //      L[:, targets] += K_o (n^3 x n^3) * M[:, sources]          (Laplace and Yukawa)
-// The CTA takes one 128-row slice of K_o (A operand) and up to 128 pairs (B operand,
-// the gathered source multipole vectors), and runs tcgen05.mma (kind::f16, BF16 inputs,
-// FP32 accumulation in tensor memory).  FP32 accuracy is kept by splitting every value
-// into BF16 high and low parts, x = hi + lo, and summing hi*hi + hi*lo + lo*hi (the lo*lo
-// term is below FP32 rounding of the sum).  The accumulator is read back with tcgen05.ld
-// and added into the target local expansions.
+// A CTA takes one 128-row slice of K_o (A operand) and up to 112 pairs (B operand, the
+// gathered source multipole vectors) and runs tcgen05.mma (kind::f16: BF16 inputs, FP32
+// accumulation in tensor memory).  FP32 accuracy is kept by splitting every value into
+// BF16 high and low parts, x = hi + lo, and summing hi*hi + hi*lo + lo*hi.
 //
-// Shared-memory operands use the canonical K-major layout without swizzle: 8 x 16-byte
-// "core matrices" (8 rows x 8 BF16), the strided (row) direction at 128 B, the leading
-// (K) direction at rows/8 * 128 B.  Translation matrices are converted to this layout
-// once at setup.  All waits on the MMA-completion barrier are bounded: on expiry the
-// kernel records an error flag, skips the epilogue, still frees its tensor memory and
-// returns.
+// The contraction (K = 224 after padding) runs in two halves of 112 so that a CTA needs
+// ~105 KB of shared memory and two CTAs share an SM, overlapping one CTA's loads with the
+// other's MMAs.  The A halves (pre-converted at setup into the MMA operand layout) arrive
+// by bulk asynchronous copy (the TMA engine, completion counted on an mbarrier) while the
+// 256 threads gather and split the B half.  One thread issues the MMAs and commits them
+// to a second mbarrier; the accumulator is read with tcgen05.ld and added into the target
+// local expansions.
+//
+// Operand layout in shared memory: canonical K-major without swizzle -- 8 x 16-byte core
+// matrices (8 rows x 8 BF16), rows strided by 128 B, K strided by rows/8 * 128 B.
+// Every mbarrier wait is bounded: on expiry the kernel records an error flag, waits once
+// more (bounded) for its own operations, frees its tensor memory and returns.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -24,14 +28,17 @@
 
 namespace afmpb {
 
-constexpr int kTcRows = 128;                 // MMA M
-constexpr int kTcPairs = 128;                // MMA N (pairs per CTA, padded to 16)
-constexpr int kTcK = 224;                    // K padded to a multiple of 16 (order <= 6)
-constexpr int kTcTileElems = kTcRows * kTcK; // 28,672 BF16 per A tile (hi or lo)
-constexpr int kTcBElems = kTcPairs * kTcK;
-constexpr uint32_t kTcSpinLimit = 1u << 26;  // bounded mbarrier wait
+constexpr int kTcRows = 128;                   // MMA M
+constexpr int kTcPairs = 112;                  // MMA N upper bound (pairs per CTA)
+constexpr int kTcKHalf = 112;                  // K per half (7 MMA k-steps of 16)
+constexpr int kTcK = 2 * kTcKHalf;             // 224 >= n^3 for order <= 6
+constexpr int kTcAElems = kTcRows * kTcKHalf;  // 14,336 BF16 per A half-tile (hi or lo)
+constexpr int kTcBElems = kTcPairs * kTcKHalf; // 12,544 BF16 per B half-tile
+constexpr int kTcThreads = 256;
+constexpr int kTcTmemCols = 128;
+constexpr uint32_t kTcSpinLimit = 1u << 26;    // bounded mbarrier wait
 
-__device__ int g_tc_error = 0;               // set when a bounded wait expired
+__device__ int g_tc_error = 0;                 // set when a bounded wait expired
 
 // Byte offset of element (row, k) in a canonical K-major no-swizzle tile with `rows` rows.
 __host__ __device__ __forceinline__ uint32_t canon_off(int row, int k, int rows) {
@@ -43,46 +50,59 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
   d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
   d |= (uint64_t)((lbo & 0x3FFFFu) >> 4) << 16;
   d |= (uint64_t)((sbo & 0x3FFFFu) >> 4) << 32;
-  d |= (uint64_t)1 << 46;                     // descriptor version for tcgen05
-  return d;                                   // base offset 0, no swizzle
+  d |= (uint64_t)1 << 46;                       // descriptor version for tcgen05
+  return d;                                     // base offset 0, no swizzle
 }
 
 // kind::f16 instruction descriptor: D = F32, A = B = BF16, both K-major, M x N.
 __host__ __device__ __forceinline__ uint32_t instr_desc(int M, int N) {
   uint32_t d = 0;
-  d |= 1u << 4;                               // D format F32
-  d |= 1u << 7;                               // A format BF16
-  d |= 1u << 10;                              // B format BF16
+  d |= 1u << 4;                                 // D format F32
+  d |= 1u << 7;                                 // A format BF16
+  d |= 1u << 10;                                // B format BF16
   d |= (uint32_t)(N >> 3) << 17;
   d |= (uint32_t)(M >> 4) << 24;
   return d;
 }
 
-__device__ __forceinline__ uint32_t cvta_smem(const void *p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
+__device__ __forceinline__ uint32_t cvta_smem(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 __device__ __forceinline__ void split_bf16(float v, __nv_bfloat16 &hi, __nv_bfloat16 &lo) {
   hi = __float2bfloat16_rn(v);
   lo = __float2bfloat16_rn(v - __bfloat162float(hi));
 }
 
-// Translation matrices -> BF16 hi/lo tiles in the canonical layout.
-// out: [table][slot][row tile][hi, lo][kTcTileElems]
+__device__ __forceinline__ bool mbar_wait(uint32_t mb, uint32_t parity) {
+  for (uint32_t spin = 0; spin < kTcSpinLimit; ++spin) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred P1;\n\tmbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2;\n\t"
+        "selp.b32 %0, 1, 0, P1;\n\t}"
+        : "=r"(ok)
+        : "r"(mb), "r"(parity));
+    if (ok) return true;
+  }
+  return false;
+}
+
+// Translation matrices -> BF16 hi/lo half-tiles in the operand layout.
+// out: [table][slot][row tile][k half][hi, lo][kTcAElems]
 __global__ void k_tc_tables(int N3, int ntables, int nslots, const float *__restrict__ Klap,
                             const float *__restrict__ Kyuk, const int *__restrict__ table_level,
                             __nv_bfloat16 *__restrict__ out) {
   const int rtiles = (N3 + kTcRows - 1) / kTcRows;
-  const int64_t total = (int64_t)ntables * nslots * rtiles * kTcTileElems;
+  const int64_t total = (int64_t)ntables * nslots * rtiles * 2 * kTcAElems;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int within = (int)(e % kTcTileElems);
-    int64_t tile = e / kTcTileElems;
-    const int rt = (int)(tile % rtiles);
-    tile /= rtiles;
-    const int slot = (int)(tile % nslots);
-    const int table = (int)(tile / nslots);
-    const int row = within / kTcK, k = within % kTcK;
-    const int r = rt * kTcRows + row;
+    const int within = (int)(e % kTcAElems);
+    int64_t t = e / kTcAElems;
+    const int kh = (int)(t % 2);
+    t /= 2;
+    const int rt = (int)(t % rtiles);
+    t /= rtiles;
+    const int slot = (int)(t % nslots);
+    const int table = (int)(t / nslots);
+    const int row = within / kTcKHalf, kk = within % kTcKHalf;
+    const int r = rt * kTcRows + row, k = kh * kTcKHalf + kk;
     float v = 0.0f;
     if (r < N3 && k < N3) {
       const float *K = table == 0 ? Klap + (size_t)slot * N3 * N3
@@ -91,151 +111,152 @@ __global__ void k_tc_tables(int N3, int ntables, int nslots, const float *__rest
     }
     __nv_bfloat16 hi, lo;
     split_bf16(v, hi, lo);
-    const int64_t base = (((int64_t)table * nslots + slot) * rtiles + rt) * 2 * kTcTileElems;
-    const uint32_t off = canon_off(row, k, kTcRows) >> 1;
+    const int64_t base = ((((int64_t)table * nslots + slot) * rtiles + rt) * 2 + kh) * 2 * kTcAElems;
+    const uint32_t off = canon_off(row, kk, kTcRows) >> 1;
     out[base + off] = hi;
-    out[base + kTcTileElems + off] = lo;
+    out[base + kTcAElems + off] = lo;
   }
 }
 
-__global__ void __launch_bounds__(128, 1) k_m2l_tc(int N3, const TCItem *__restrict__ items,
-                                                   const M2LGroup *__restrict__ groups,
-                                                   const int2 *__restrict__ pairs,
-                                                   const __nv_bfloat16 *__restrict__ tiles,
-                                                   const int *__restrict__ level_table, int nslots,
-                                                   int yuk_min_level, const dbl4 *__restrict__ center,
-                                                   const float *__restrict__ M, float *__restrict__ L) {
+__global__ void __launch_bounds__(kTcThreads, 2) k_m2l_tc(int N3, const TCItem *__restrict__ items,
+                                                          const M2LGroup *__restrict__ groups,
+                                                          const int2 *__restrict__ pairs,
+                                                          const __nv_bfloat16 *__restrict__ tiles,
+                                                          const int *__restrict__ level_table, int nslots,
+                                                          int yuk_min_level, const dbl4 *__restrict__ center,
+                                                          const float *__restrict__ M, float *__restrict__ L) {
   extern __shared__ __align__(128) uint8_t smem[];
   __nv_bfloat16 *a_hi = reinterpret_cast<__nv_bfloat16 *>(smem);
-  __nv_bfloat16 *a_lo = a_hi + kTcTileElems;
-  __nv_bfloat16 *b_hi = a_lo + kTcTileElems;
+  __nv_bfloat16 *a_lo = a_hi + kTcAElems;
+  __nv_bfloat16 *b_hi = a_lo + kTcAElems;
   __nv_bfloat16 *b_lo = b_hi + kTcBElems;
-  __shared__ uint64_t mbar;
+  __shared__ __align__(8) uint64_t mbar_load, mbar_mma;
   __shared__ uint32_t tmem_base;
-  __shared__ int s_tgt[kTcPairs];
+  __shared__ int s_src[kTcPairs], s_tgt[kTcPairs];
 
   const TCItem it = items[blockIdx.x];
   const M2LGroup g = groups[it.group];
   const int rt = blockIdx.y;
   const int kt = blockIdx.z;
   const int rtiles = (N3 + kTcRows - 1) / kTcRows;
-  if (kt == 1 && g.level < yuk_min_level) return;     // screened away (uniform per CTA)
+  if (kt == 1 && g.level < yuk_min_level) return;       // screened away (uniform per CTA)
   const int table = kt == 0 ? 0 : level_table[g.level];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int cnt = it.count;
+  const int npad = (cnt + 15) & ~15;
+  const uint32_t mb_load = cvta_smem(&mbar_load), mb_mma = cvta_smem(&mbar_mma);
 
-  // tensor memory: 128 columns (one FP32 accumulator column per pair)
   if (warp == 0) {
-    const uint32_t dst = cvta_smem(&tmem_base);
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst), "r"(kTcPairs));
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(cvta_smem(&tmem_base)),
+                 "r"(kTcTmemCols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (threadIdx.x == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(cvta_smem(&mbar)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb_load));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb_mma));
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
-
-  // A: 128 rows of K_o, hi and lo (already in the canonical layout)
-  {
-    const int64_t base = (((int64_t)table * nslots + g.offset) * rtiles + rt) * 2 * kTcTileElems;
-    const uint4 *src = reinterpret_cast<const uint4 *>(tiles + base);
-    uint4 *dst = reinterpret_cast<uint4 *>(a_hi);
-    for (int e = threadIdx.x; e < 2 * kTcTileElems / 8; e += blockDim.x) dst[e] = src[e];
+  if (threadIdx.x < kTcPairs) {
+    const bool v = threadIdx.x < cnt;
+    const int2 pr = v ? pairs[g.start + it.start + threadIdx.x] : make_int2(-1, -1);
+    s_src[threadIdx.x] = pr.y;
+    s_tgt[threadIdx.x] = pr.x;
   }
-  // B: gathered source multipoles, split into hi / lo, canonical layout (rows = pairs)
-  const int cnt = it.count;
-  const int npad = (cnt + 15) & ~15;
-  for (int e = threadIdx.x; e < kTcPairs * (kTcK / 8); e += blockDim.x) {
-    const int p = e / (kTcK / 8), k8 = e % (kTcK / 8);
-    float v[8];
-    if (p < cnt && k8 * 8 < N3) {
-      const int src_box = pairs[g.start + it.start + p].y;
-      const float *m = M + ((size_t)src_box * 2 + kt) * N3 + k8 * 8;
-#pragma unroll
-      for (int q = 0; q < 8; ++q) v[q] = (k8 * 8 + q < N3) ? m[q] : 0.0f;
-    } else {
-#pragma unroll
-      for (int q = 0; q < 8; ++q) v[q] = 0.0f;
-    }
-    __align__(16) __nv_bfloat16 hi[8], lo[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) split_bf16(v[q], hi[q], lo[q]);
-    const uint32_t off = canon_off(p, k8 * 8, kTcPairs);
-    *reinterpret_cast<uint4 *>(reinterpret_cast<uint8_t *>(b_hi) + off) = *reinterpret_cast<const uint4 *>(hi);
-    *reinterpret_cast<uint4 *>(reinterpret_cast<uint8_t *>(b_lo) + off) = *reinterpret_cast<const uint4 *>(lo);
-  }
-  if (threadIdx.x < kTcPairs) s_tgt[threadIdx.x] = threadIdx.x < cnt ? pairs[g.start + it.start + threadIdx.x].x : -1;
-  asm volatile("fence.proxy.async.shared::cta;");
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_base;
+  bool ok = true;
 
-  // MMA issue: one thread
-  if (threadIdx.x == 0) {
-    const uint32_t idesc = instr_desc(kTcRows, npad);
-    const uint32_t lbo_a = (kTcRows / 8) * 128, lbo_b = (kTcPairs / 8) * 128, sbo = 128;
-    const uint32_t sa_hi = cvta_smem(a_hi), sa_lo = cvta_smem(a_lo);
-    const uint32_t sb_hi = cvta_smem(b_hi), sb_lo = cvta_smem(b_lo);
-    const int ksteps = (N3 + 15) / 16;
-    for (int s = 0; s < ksteps; ++s) {
-      const uint32_t ka = 2 * s * lbo_a, kb = 2 * s * lbo_b;
-      const uint64_t dah = smem_desc(sa_hi + ka, lbo_a, sbo), dal = smem_desc(sa_lo + ka, lbo_a, sbo);
-      const uint64_t dbh = smem_desc(sb_hi + kb, lbo_b, sbo), dbl = smem_desc(sb_lo + kb, lbo_b, sbo);
-      const uint32_t acc0 = s > 0 ? 1u : 0u;
+  for (int kh = 0; kh < 2 && ok; ++kh) {
+    // A half: two bulk copies (hi, lo) tracked by mb_load
+    if (threadIdx.x == 0) {
+      const int64_t base = ((((int64_t)table * nslots + g.offset) * rtiles + rt) * 2 + kh) * 2 * kTcAElems;
+      const __nv_bfloat16 *src = tiles + base;
+      const uint32_t bytes = 2 * kTcAElems * 2;
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb_load), "r"(bytes));
       asm volatile(
-          "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-          "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
-          "l"(dah), "l"(dbh), "r"(idesc), "r"(acc0));
+          "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+              cvta_smem(a_hi)),
+          "l"(src), "r"((uint32_t)(kTcAElems * 2)), "r"(mb_load)
+          : "memory");
       asm volatile(
-          "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-          "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
-          "l"(dah), "l"(dbl), "r"(idesc), "r"(1u));
-      asm volatile(
-          "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-          "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
-          "l"(dal), "l"(dbh), "r"(idesc), "r"(1u));
+          "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+              cvta_smem(a_lo)),
+          "l"(src + kTcAElems), "r"((uint32_t)(kTcAElems * 2)), "r"(mb_load)
+          : "memory");
     }
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-        cvta_smem(&mbar)));
-  }
-  // bounded wait for the MMAs (phase 0)
-  bool done = false;
-  {
-    const uint32_t mb = cvta_smem(&mbar);
-    for (uint32_t spin = 0; spin < kTcSpinLimit; ++spin) {
-      uint32_t ok;
-      asm volatile(
-          "{\n\t.reg .pred P1;\n\tmbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2;\n\t"
-          "selp.b32 %0, 1, 0, P1;\n\t}"
-          : "=r"(ok)
-          : "r"(mb), "r"(0u));
-      if (ok) {
-        done = true;
-        break;
+    // B half: gathered source multipoles, split into hi / lo (rows = pairs)
+    constexpr int kG = kTcKHalf / 8;    // 14 groups of 8 along K
+    for (int e = threadIdx.x; e < kTcPairs * kG; e += kTcThreads) {
+      const int p = e / kG, k8 = e % kG;
+      const int k0 = kh * kTcKHalf + k8 * 8;
+      float v[8];
+      if (p < cnt && k0 < N3) {
+        const float *m = M + ((size_t)s_src[p] * 2 + kt) * N3 + k0;
+        if (k0 + 8 <= N3) {
+          const float4 u0 = *reinterpret_cast<const float4 *>(m), u1 = *reinterpret_cast<const float4 *>(m + 4);
+          v[0] = u0.x; v[1] = u0.y; v[2] = u0.z; v[3] = u0.w; v[4] = u1.x; v[5] = u1.y; v[6] = u1.z; v[7] = u1.w;
+        } else {
+#pragma unroll
+          for (int q = 0; q < 8; ++q) v[q] = (k0 + q < N3) ? m[q] : 0.0f;
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) v[q] = 0.0f;
       }
+      __align__(16) __nv_bfloat16 hi[8], lo[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) split_bf16(v[q], hi[q], lo[q]);
+      const uint32_t off = canon_off(p, k8 * 8, kTcPairs);
+      *reinterpret_cast<uint4 *>(reinterpret_cast<uint8_t *>(b_hi) + off) = *reinterpret_cast<const uint4 *>(hi);
+      *reinterpret_cast<uint4 *>(reinterpret_cast<uint8_t *>(b_lo) + off) = *reinterpret_cast<const uint4 *>(lo);
     }
+    asm volatile("fence.proxy.async.shared::cta;");
+    __syncthreads();
+    ok = __syncthreads_and(mbar_wait(mb_load, (uint32_t)kh));   // block-uniform
+    if (ok && threadIdx.x == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const uint32_t idesc = instr_desc(kTcRows, npad);
+      const uint32_t lbo_a = (kTcRows / 8) * 128, lbo_b = (kTcPairs / 8) * 128, sbo = 128;
+      const uint32_t sa_hi = cvta_smem(a_hi), sa_lo = cvta_smem(a_lo);
+      const uint32_t sb_hi = cvta_smem(b_hi), sb_lo = cvta_smem(b_lo);
+      for (int s = 0; s < kTcKHalf / 16; ++s) {
+        const uint32_t ka = 2 * s * lbo_a, kb = 2 * s * lbo_b;
+        const uint64_t dah = smem_desc(sa_hi + ka, lbo_a, sbo), dal = smem_desc(sa_lo + ka, lbo_a, sbo);
+        const uint64_t dbh = smem_desc(sb_hi + kb, lbo_b, sbo), dbl = smem_desc(sb_lo + kb, lbo_b, sbo);
+        const uint32_t acc0 = (kh > 0 || s > 0) ? 1u : 0u;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+            "l"(dah), "l"(dbh), "r"(idesc), "r"(acc0));
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+            "l"(dah), "l"(dbl), "r"(idesc), "r"(1u));
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+            "l"(dal), "l"(dbh), "r"(idesc), "r"(1u));
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mb_mma));
+    }
+    // the MMAs must finish reading A and B before the next half overwrites them
+    ok = __syncthreads_and(ok && mbar_wait(mb_mma, (uint32_t)kh));
   }
   asm volatile("tcgen05.fence::after_thread_sync;");
-  if (!done) {
+  if (!ok) {
     if (lane == 0) atomicExch(&g_tc_error, 1);
-    // give the MMAs a second bounded window to drain before the memory is freed
-    const uint32_t mb = cvta_smem(&mbar);
-    for (uint32_t spin = 0; spin < kTcSpinLimit; ++spin) {
-      uint32_t ok;
-      asm volatile(
-          "{\n\t.reg .pred P1;\n\tmbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2;\n\t"
-          "selp.b32 %0, 1, 0, P1;\n\t}"
-          : "=r"(ok)
-          : "r"(mb), "r"(0u));
-      if (ok) break;
-    }
+    mbar_wait(mb_mma, 0);     // bounded: let any issued MMA drain before freeing memory
+    mbar_wait(mb_mma, 1);
   } else {
-    // epilogue: warp w owns accumulator rows 32w .. 32w + 31
-    const int row = rt * kTcRows + warp * 32 + lane;
-    const float scale = kt == 0 ? (float)(1.0 / center[s_tgt[0] >= 0 ? s_tgt[0] : 0].w) : 1.0f;
-    for (int c0 = 0; c0 < npad; c0 += 16) {
+    // epilogue: warps w and w+4 own accumulator rows 32 (w % 4) .. + 31 and split columns
+    const int quarter = warp & 3, half = warp >> 2;
+    const int row = rt * kTcRows + quarter * 32 + lane;
+    const float scale = kt == 0 ? (float)(1.0 / center[s_tgt[0]].w) : 1.0f;
+    for (int c0 = half * 16; c0 < npad; c0 += 32) {
       uint32_t r[16];
-      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+      const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0;
       asm volatile(
           "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
           : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
@@ -253,7 +274,11 @@ __global__ void __launch_bounds__(128, 1) k_m2l_tc(int N3, const TCItem *__restr
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcPairs));
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcTmemCols));
+}
+
+namespace {
+constexpr int kTcSmem = (2 * kTcAElems + 2 * kTcBElems) * 2;
 }
 
 Err build_m2l_tc(afmpb_t *h) {
@@ -261,7 +286,7 @@ Err build_m2l_tc(afmpb_t *h) {
   if (N3 > kTcK) return make_err(AFMPB_EINVAL, "precision 1 (tensor-core M2L) supports fmm_order <= 6");
   auto &A = h->arena;
   cudaStream_t s = h->stream;
-  // work items: chunks of <= 128 pairs per (level, offset) group
+  // work items: chunks of <= 112 pairs per (level, offset) group
   std::vector<TCItem> items;
   int maxlev = 0;
   for (size_t gi = 0; gi < h->m2l_groups.size(); ++gi) {
@@ -279,7 +304,7 @@ Err build_m2l_tc(afmpb_t *h) {
   }
   const int ntables = (int)table_level.size();
   const int rtiles = (N3 + kTcRows - 1) / kTcRows;
-  const size_t elems = (size_t)ntables * kNumOffsets * rtiles * 2 * kTcTileElems;
+  const size_t elems = (size_t)ntables * kNumOffsets * rtiles * 2 * 2 * kTcAElems;
   AFMPB_TRY(A.alloc(&h->d_tc_tiles, elems, "tensor-core M2L tiles"));
   int *d_table_level = nullptr;
   AFMPB_TRY(A.alloc(&d_table_level, table_level.size(), "table level"));
@@ -294,20 +319,18 @@ Err build_m2l_tc(afmpb_t *h) {
   AFMPB_TRY(check_launch("k_tc_tables"));
   AFMPB_CUDA(cudaStreamSynchronize(s));
   A.release(d_table_level);
-  const int smem = (2 * kTcTileElems + 2 * kTcBElems) * 2;
-  AFMPB_CUDA(cudaFuncSetAttribute(k_m2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  AFMPB_CUDA(cudaFuncSetAttribute(k_m2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem));
   return Err{};
 }
 
 Err enqueue_m2l_tc(afmpb_t *h, cudaStream_t s) {
   if (h->tc_items == 0) return Err{};
   const int N3 = h->ncoef;
-  const int smem = (2 * kTcTileElems + 2 * kTcBElems) * 2;
   dim3 grid((unsigned)h->tc_items, (N3 + kTcRows - 1) / kTcRows, 2);
-  k_m2l_tc<<<grid, 128, smem, s>>>(N3, reinterpret_cast<const TCItem *>(h->d_tc_items), h->d_m2l_groups,
-                                   h->d_m2l_pairs, reinterpret_cast<const __nv_bfloat16 *>(h->d_tc_tiles),
-                                   h->d_tc_level_table, kNumOffsets, h->m2l_yuk_levels, h->d_box_center, h->d_M,
-                                   h->d_L);
+  k_m2l_tc<<<grid, kTcThreads, kTcSmem, s>>>(N3, h->d_tc_items, h->d_m2l_groups, h->d_m2l_pairs,
+                                             reinterpret_cast<const __nv_bfloat16 *>(h->d_tc_tiles),
+                                             h->d_tc_level_table, kNumOffsets, h->m2l_yuk_levels,
+                                             h->d_box_center, h->d_M, h->d_L);
   return check_launch("k_m2l_tc");
 }
 

@@ -530,25 +530,42 @@ Err build_tree(afmpb_t *h) {
   h->d_w_ptr = d_wptr;
   AFMPB_TRY(to_device(h, &h->d_x_ptr, xptr, "xptr"));
   AFMPB_TRY(to_device(h, &h->d_x_idx, xidx, "xidx"));
+  // List 4 of a box is evaluated by P2P at the targets when the box holds no more nodes
+  // than an expansion holds weights (n^3): the direct sum is then the cheaper route.
+  // Otherwise it goes to the box's local expansion (P2L).  Either way each pair once.
+  AFMPB_TRY(to_host(hend, bend, nbox, s));
+  AFMPB_TRY(to_host(hparent, bparent, nbox, s));
+  const int64_t x_direct_max = (int64_t)h->order * h->order * h->order;
+  std::vector<char> x_direct(nbox, 0);
   h->h_xbox.clear();
-  for (int b = 0; b < nbox; ++b)
-    if (xptr[b + 1] > xptr[b]) h->h_xbox.push_back(b);
+  for (int b = 0; b < nbox; ++b) {
+    if (xptr[b + 1] == xptr[b]) continue;
+    if (hend[b] - hbeg[b] <= x_direct_max) x_direct[b] = 1;
+    else h->h_xbox.push_back(b);
+  }
   AFMPB_TRY(to_device(h, &h->d_xbox, h->h_xbox, "xbox"));
 
-  // point-to-point source boxes per leaf: list 1, then the leaves under each list-3 box
-  // (node positions are stored relative to their own leaf, so P2P sources are leaves)
+  // point-to-point source boxes per leaf: list 1, the leaves under each list-3 box
+  // (node positions are stored relative to their own leaf, so P2P sources are leaves),
+  // then the list-4 leaves of itself and its ancestors that are evaluated directly
   std::vector<int32_t> hchild0;
   AFMPB_TRY(to_host(hchild0, bchild0, nbox, s));
   std::vector<int64_t> pptr(T.nleaf + 1, 0);
   std::vector<int32_t> pidx;
   pidx.reserve(uidx.size() + widx.size());
-  AFMPB_TRY(to_host(hend, bend, nbox, s));
   int64_t pairs = 0;
   std::vector<int32_t> stack;
   for (int i = 0; i < T.nleaf; ++i) {
     int b = leaves[i];
     int64_t nt_b = hend[b] - hbeg[b];
     for (int64_t j = uptr[b]; j < uptr[b + 1]; ++j) { pidx.push_back(uidx[j]); pairs += nt_b * (hend[uidx[j]] - hbeg[uidx[j]]); }
+    for (int a = b; a >= 0; a = hparent[a]) {
+      if (!x_direct[a]) continue;
+      for (int64_t j = xptr[a]; j < xptr[a + 1]; ++j) {
+        pidx.push_back(xidx[j]);
+        pairs += nt_b * (hend[xidx[j]] - hbeg[xidx[j]]);
+      }
+    }
     for (int64_t j = wptr[b]; j < wptr[b + 1]; ++j) {
       stack.assign(1, widx[j]);
       while (!stack.empty()) {
