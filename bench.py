@@ -57,6 +57,14 @@ def workload_desc(mol):
             % (mol.name, mol.n_nodes, mol.n_tris, len(mol.q), mol.eps_in, mol.eps_out, mol.kappa)}
 
 
+def run_config(mol, args, world):
+    return dict(workload_desc(mol), fmm_order=args.order,
+                leaf_cap=args.leaf_cap if args.leaf_cap else 128,
+                precision=["fp32", "mixed: tensor-core M2L"][args.precision],
+                l2="flushed between timed products (512 MB write)",
+                parallelism="replicas" if world > 1 else "single")
+
+
 # ------------------------------------------------------------------------------------
 # clocks during the timed region
 # ------------------------------------------------------------------------------------
@@ -116,10 +124,10 @@ def fp32_peak_tflops(sm_max_mhz):
     return 152 * 128 * 2 * sm_max_mhz * 1e6 / 1e12
 
 
-# FP32 operations per source-target pair in the P2P kernel, counted from its source
-# (an FMA counts 2 flop): distance 9, rsqrt + products 6, dot products 15, Laplace
-# terms 16, Yukawa terms 26.
-P2P_FLOP_PER_PAIR = 72
+# FP32 operations per source-target pair in the P2P kernel (p2p_pair), counted from its
+# source with an FMA as 2 flop: 46 FP32 instructions of which 17 are FMAs, plus one
+# rsqrt and one exp2 on the special-function unit.
+P2P_FLOP_PER_PAIR = 63
 
 
 def ncu_traffic(kernel):
@@ -141,12 +149,20 @@ def ncu_traffic(kernel):
     return None
 
 
-def roofline(prof, info, n, order, peaks, kind):
+def roofline(prof, info, n, order, peaks, kind, precision):
     stages = {name: (ms, launches) for name, ms, launches in prof["stages"]}
     name, (ms, launches) = max(stages.items(), key=lambda kv: kv[1][0])
     n3 = order ** 3
     sm_max = peaks.get("sm_max_mhz", 2070.0)
-    if name == "m2l":
+    if name == "m2l" and precision == 1:
+        # three BF16 products (hi*hi, hi*lo, lo*hi) of every n^3 x n^3 translation,
+        # Laplace and Yukawa; the burst BF16 peak, the kernel being timed on its own
+        flop = 3 * 2.0 * n3 * n3 * info["n_m2l_pairs"] * 2
+        achieved = flop / (ms * 1e-3) / 1e12
+        peak = peaks["bf16_tflops"]
+        out = {"bound": "tensor", "kernel": "k_m2l_tc (tcgen05 BF16 x3, FP32 accumulate)",
+               "unit": "TFLOP/s", "peak_kind": "measured dense BF16 GEMM (burst)"}
+    elif name == "m2l":
         flop = 2.0 * n3 * n3 * info["n_m2l_pairs"] * 2      # Laplace + Yukawa
         achieved = flop / (ms * 1e-3) / 1e12
         peak = fp32_peak_tflops(sm_max)
@@ -156,7 +172,7 @@ def roofline(prof, info, n, order, peaks, kind):
         flop = float(P2P_FLOP_PER_PAIR) * info["n_p2p_pairs"]
         achieved = flop / (ms * 1e-3) / 1e12
         peak = fp32_peak_tflops(sm_max)
-        out = {"bound": "alu", "kernel": "k_p2p (FP32 FMA + MUFU)", "unit": "TFLOP/s",
+        out = {"bound": "alu", "kernel": "k_p2p_v3 (FP32 FMA + MUFU)", "unit": "TFLOP/s",
                "peak_kind": "FP32 FMA: 152 SM x 128 lanes x 2 x %.0f MHz" % sm_max}
     else:   # combine / near SpMV and the rest are memory-bound
         byts = info["nnz_near"] * 20.0 + n * (8 + 16 + 16 + 8)
@@ -222,7 +238,7 @@ def run_reference(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_desc(mol), "impl": "reference",
+            "config": run_config(mol, args, int(os.environ.get("WORLD_SIZE", "1"))), "impl": "reference",
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -257,41 +273,63 @@ def run_gpu(args):
     torch.cuda.set_stream(stream)
 
     mol = workload(args.workload)
-    h = pb.Handle.for_molecule(mol, order=args.order, tol=1e-6, leaf_cap=args.leaf_cap,
-                               precision=args.precision, stream=stream.cuda_stream)
-    info = h.info()
     n = mol.n_nodes
     x = torch.tensor(synthetic.smooth_unknowns(mol.xyz, 1).astype(np.float32), device=dev)
     y = torch.empty_like(x)
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
-    for _ in range(max(args.warmup, 3)):
-        h.matvec(x, y)
-    torch.cuda.synchronize()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    clocks = ClockSampler(torch.cuda.current_device())
-    time.sleep(0.25)
-    t_wall = time.perf_counter()
-    for i in range(args.steps):
-        flush.fill_(float(i))
-        ev[i][0].record(stream)
-        h.matvec(x, y)
-        ev[i][1].record(stream)
-    torch.cuda.synchronize()
-    t_wall = time.perf_counter() - t_wall
-    clk = clocks.stop()
-    if dist:
-        dist.barrier()
-    ms = [a.elapsed_time(b) for a, b in ev]
-    ms_step = sum(ms) / len(ms)
-    if dist:
-        t = torch.tensor([ms_step], device=dev, dtype=torch.float64)
+    def max_over_ranks(v):
+        if not dist:
+            return v
+        t = torch.tensor([v], device=dev, dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
+        return float(t.item())
+
+    def timed_products(hh, steps, warmup, sample_clocks=False):
+        """Mean product time (ms, CUDA events on the launching stream), L2 flushed."""
+        for _ in range(max(warmup, 3)):
+            hh.matvec(x, y)
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        clocks = ClockSampler(torch.cuda.current_device()) if sample_clocks else None
+        if clocks:
+            time.sleep(0.25)
+        for i in range(steps):
+            flush.fill_(float(i))
+            ev[i][0].record(stream)
+            hh.matvec(x, y)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        clk = clocks.stop() if clocks else None
+        if dist:
+            dist.barrier()
+        ms = [a.elapsed_time(b) for a, b in ev]
+        return max_over_ranks(sum(ms) / len(ms)), clk
+
+    def solve_latency(hh, reps):
+        """Repeated solves (GMRES + energy) on a resident handle: p50 / p99 / solves/s."""
+        lat = []
+        out = None
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            f, hv, sinfo = hh.solve(raise_on_noconv=False)
+            energy = hh.energy()
+            lat.append((time.perf_counter() - t0) * 1e3)
+            out = (sinfo, energy)
+        lat.sort()
+        p = lambda q: lat[min(len(lat) - 1, int(round(q * (len(lat) - 1))))]
+        return {"n": reps, "p50_ms": round(p(0.5), 3), "p99_ms": round(p(0.99), 3),
+                "solves_per_s": round(1e3 * len(lat) / sum(lat), 3)}, out
+
+    h = pb.Handle.for_molecule(mol, order=args.order, tol=1e-6, leaf_cap=args.leaf_cap,
+                               precision=args.precision, stream=stream.cuda_stream)
+    info = h.info()
+    ms_step, clk = timed_products(h, args.steps, args.warmup, sample_clocks=True)
     value = world * n / (ms_step * 1e-3) / 1e6
 
     # end to end through the C ABI with pinned host buffers (H2D + product + D2H)
@@ -313,20 +351,29 @@ def run_gpu(args):
 
     prof = h.profile(reps=5, flush=flush, flush_bytes=FLUSH_BYTES)
     peaks, kind = measured_peaks()
-    roof = roofline(prof, info, n, args.order, peaks, kind)
+    roof = roofline(prof, info, n, args.order, peaks, kind, args.precision)
 
-    # one full solve + energy (outside the timed region): time to solution
-    f, hh, sinfo = h.solve(raise_on_noconv=False)
-    energy = h.energy() if sinfo["status"] in ("OK", "ENOCONV") else None
+    # solves on the resident handle (outside the timed region): GMRES + energy latency
+    lat, (sinfo, energy) = solve_latency(h, args.solve_reps)
+    h.close()
+
+    # the plain FP32 path (M2L on the CUDA cores) at its own best leaf size, same workload
+    plain = None
+    if args.precision == 1 and not args.no_plain:
+        hp = pb.Handle.for_molecule(mol, order=args.order, tol=1e-6, leaf_cap=args.plain_leaf_cap,
+                                    precision=0, stream=stream.cuda_stream)
+        ms_p, _ = timed_products(hp, max(5, args.steps // 4), args.warmup)
+        lat_p, (sinfo_p, energy_p) = solve_latency(hp, args.solve_reps)
+        plain = {"value": round(world * n / (ms_p * 1e-3) / 1e6, 3), "unit": UNIT, "ms_per_step": round(ms_p, 5),
+                 "leaf_cap": args.plain_leaf_cap, "solve": lat_p, "energy_kcal_mol": energy_p,
+                 "energy_rel_diff_vs_mixed": abs(energy_p / energy - 1) if energy else None}
+        hp.close()
 
     line = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 5),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if args.precision == 0 else "f32+bf16x3", "data": "synthetic",
-            "config": dict(workload_desc(mol), fmm_order=args.order, leaf_cap=info.get("n_leaves") and args.leaf_cap or 0,
-                           precision=["fp32", "mixed-tc"][args.precision],
-                           l2="flushed between timed products (512 MB write)",
-                           parallelism="replicas" if world > 1 else "single"),
+            "config": run_config(mol, args, world),
             "e2e": {k: (round(v, 4) if isinstance(v, float) else v) for k, v in e2e.items()},
             "roofline": roof,
             "gpu_launches": int(prof["kernels_per_product"]) * args.steps,
@@ -334,16 +381,22 @@ def run_gpu(args):
             "ms_graph_profile": round(prof["ms_graph"], 5),
             "tree": {"boxes": info["n_boxes"], "leaves": info["n_leaves"], "levels": info["n_levels"],
                      "nnz_near": info["nnz_near"], "p2p_pairs": info["n_p2p_pairs"],
-                     "m2l_pairs": info["n_m2l_pairs"]},
-            "solve": {"status": sinfo["status"], "iters": sinfo["iters"], "ms_setup": round(sinfo["ms_setup"], 2),
-                      "ms_gmres": round(sinfo["ms_gmres"], 2), "res_true": sinfo["res_true"],
-                      "energy_kcal_mol": energy}}
+                     "m2l_pairs": info["n_m2l_pairs"], "ms_create": [round(v, 1) for v in info["ms_create"]]},
+            "solve": dict(lat, status=sinfo["status"], iters=sinfo["iters"],
+                          ms_gmres=round(sinfo["ms_gmres"], 2), res_true=sinfo["res_true"],
+                          energy_kcal_mol=energy),
+            "plain_fp32": plain}
+    if args.workload == "kirkwood" and energy is not None:
+        sys.path.insert(0, os.path.join(ROOT, "tests"))
+        from closed_forms import kirkwood_energy
+        e_ref = kirkwood_energy(mol.atoms, mol.q, mol.meta["radius"], mol.eps_in, mol.eps_out, mol.kappa)
+        line["solve"]["kirkwood_series_kcal_mol"] = e_ref
+        line["solve"]["energy_rel_err_vs_series"] = abs(energy / e_ref - 1)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, cores, nrow, dt = oracle_rows_rate(mol, rows_target_s=args.cpu_seconds)
         line["cpu_baseline"] = {"value": round(rate / 1e6, 6), "unit": UNIT, "cores": cores, "kind": "oracle",
                                 "sample": "%d random rows of the product in %.1f s (FP64 direct sum, O(N) per "
                                           "row, near rule on the fly); rows/s = full-product Mnode/s" % (nrow, dt)}
-    h.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
@@ -360,8 +413,11 @@ def main():
     ap.add_argument("--workload", default="kirkwood", choices=["kirkwood", "born", "paper_sphere"])
     ap.add_argument("--order", type=int, default=6)
     ap.add_argument("--leaf-cap", type=int, default=0)
-    ap.add_argument("--precision", type=int, default=0, choices=[0, 1])
-    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--precision", type=int, default=1, choices=[0, 1])
+    ap.add_argument("--plain-leaf-cap", type=int, default=256)
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--solve-reps", type=int, default=5)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-rows", type=int, default=48)
     args = ap.parse_args()
