@@ -425,120 +425,8 @@ __global__ void __launch_bounds__(128) k_l2p(const int32_t *__restrict__ leaves,
 // P2P (lists 1 and 3): point (far-rule) sums over t != p, both kernels, both outputs.
 // ------------------------------------------------------------------------------------
 constexpr int kP2PThreads = 128;
-constexpr int kP2PChunk = 512;      // sources staged in shared memory at a time
+constexpr int kP2PChunk = 1024;     // sources staged in shared memory at a time
 constexpr int kP2PBoxes = 64;       // source boxes described in shared memory at a time
-
-// One CTA per target leaf.  The 128 threads form a (target tile x source slice) grid:
-// tile = the smallest power of two >= the leaf's targets (at most 128), and each thread
-// sums its target against every (128 / tile)-th staged source; partial sums are reduced
-// through shared memory.  All sources of the leaf's lists 1 and 3 are staged in chunks,
-// each with the offset of its own leaf centre from the target leaf centre.
-__global__ void __launch_bounds__(kP2PThreads) k_p2p_v2(const int32_t *__restrict__ leaves,
-                                                         const int64_t *__restrict__ pptr,
-                                                         const int32_t *__restrict__ pidx,
-                                                         const int32_t *__restrict__ bbeg,
-                                                         const int32_t *__restrict__ bend,
-                                                         const dbl4 *__restrict__ center,
-                                                         const float4 *__restrict__ pos,
-                                                         const float4 *__restrict__ nrm,
-                                                         const float2 *__restrict__ xs, float inv_ebar,
-                                                         float kappa, float4 *__restrict__ phi) {
-  __shared__ float4 sp[kP2PChunk], sn[kP2PChunk];
-  __shared__ int s_beg[kP2PBoxes], s_pre[kP2PBoxes + 1];
-  __shared__ float s_off[kP2PBoxes][3];
-  __shared__ float4 red[kP2PThreads];
-  const int leaf = blockIdx.x;
-  const int b = leaves[leaf];
-  const dbl4 cb = center[b];
-  const int tb = bbeg[b], te = bend[b];
-  const int ntgt = te - tb;
-  int tile = 1;
-  while (tile < ntgt && tile < kP2PThreads) tile <<= 1;
-  const int slices = kP2PThreads / tile;
-  const int ti = threadIdx.x & (tile - 1), si = threadIdx.x / tile;
-  const float kap3 = kappa * (1.0f / 3.0f);
-  const int64_t l0 = pptr[leaf], l1 = pptr[leaf + 1];
-  for (int t0 = tb; t0 < te; t0 += tile) {
-    const int t = t0 + ti;
-    const bool act = t < te;
-    const float4 xp = act ? pos[t] : make_float4(0, 0, 0, 0);
-    const float4 np = act ? nrm[t] : make_float4(0, 0, 0, 0);
-    float sL = 0.f, dL = 0.f, sY = 0.f, dY = 0.f;
-    for (int64_t g0 = l0; g0 < l1; g0 += kP2PBoxes) {
-      const int nb = (int)min((int64_t)kP2PBoxes, l1 - g0);
-      __syncthreads();
-      if (threadIdx.x < nb) {
-        const int c = pidx[g0 + threadIdx.x];
-        const dbl4 cc = center[c];
-        s_beg[threadIdx.x] = bbeg[c];
-        s_pre[threadIdx.x + 1] = bend[c] - bbeg[c];
-        s_off[threadIdx.x][0] = (float)(cc.x - cb.x);
-        s_off[threadIdx.x][1] = (float)(cc.y - cb.y);
-        s_off[threadIdx.x][2] = (float)(cc.z - cb.z);
-      }
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        s_pre[0] = 0;
-        for (int k = 0; k < nb; ++k) s_pre[k + 1] += s_pre[k];
-      }
-      __syncthreads();
-      const int total = s_pre[nb];
-      for (int c0 = 0; c0 < total; c0 += kP2PChunk) {
-        const int cnt = min(kP2PChunk, total - c0);
-        __syncthreads();
-        for (int e = threadIdx.x; e < cnt; e += kP2PThreads) {
-          const int j = c0 + e;
-          int k = 0;
-          while (s_pre[k + 1] <= j) ++k;          // source box of staged source j
-          const int sidx = s_beg[k] + (j - s_pre[k]);
-          const float4 p = pos[sidx], q = nrm[sidx];
-          const float2 fh = xs[sidx];
-          sp[e] = make_float4(p.x + s_off[k][0], p.y + s_off[k][1], p.z + s_off[k][2], p.w * fh.y);
-          sn[e] = make_float4(q.x, q.y, q.z, -p.w * fh.x);
-        }
-        __syncthreads();
-        if (act) {
-#pragma unroll 2
-          for (int e = si; e < cnt; e += slices) {
-            const float4 y = sp[e], q = sn[e];
-            const float dx = xp.x - y.x, dy = xp.y - y.y, dz = xp.z - y.z;
-            const float r2 = dx * dx + dy * dy + dz * dz;
-            const float ri = r2 > 0.0f ? rsqrtf(r2) : 0.0f;   // t == p contributes nothing
-            const float rr = r2 * ri;
-            const float ri2 = ri * ri;
-            const float G3 = ri * ri2;
-            const float G5 = 3.0f * G3 * ri2;
-            const float ndt = q.x * dx + q.y * dy + q.z * dz;
-            const float npd = np.x * dx + np.y * dy + np.z * dz;
-            const float nn = np.x * q.x + np.y * q.y + np.z * q.z;
-            const float gL = q.w * inv_ebar;
-            sL += y.w * ri + gL * ndt * G3;
-            dL += -y.w * npd * G3 + gL * (nn * G3 - ndt * npd * G5);
-            const float kr = kappa * rr;
-            const float ex = __expf(-kr);
-            const float g1 = ex * (1.0f + kr) * G3;
-            const float g2 = ex * (1.0f + kr + kr * kap3 * rr) * G5;
-            sY += y.w * ex * ri + q.w * ndt * g1;
-            dY += -y.w * npd * g1 + q.w * (nn * g1 - ndt * npd * g2);
-          }
-        }
-      }
-    }
-    // reduce the source slices of each target
-    __syncthreads();
-    red[threadIdx.x] = make_float4(sL, dL, sY, dY);
-    __syncthreads();
-    if (si == 0 && act) {
-      float4 a = red[ti];
-      for (int k = 1; k < slices; ++k) {
-        const float4 v = red[k * tile + ti];
-        a.x += v.x; a.y += v.y; a.z += v.z; a.w += v.w;
-      }
-      const float s = (float)kInv4Pi;
-      phi[t] = make_float4(s * a.x, s * a.y, s * a.z, s * a.w);
-    }
-  }
-}
 
 // Far-rule sums of one source at one target, without the 1/(4 pi):
 //   PhiL += c/r + (g/eps_bar) (n.d)/r^3
@@ -674,74 +562,6 @@ __global__ void __launch_bounds__(kP2PThreads) k_p2p_v3(const int32_t *__restric
   }
 }
 
-constexpr int kP2PThreadsV1 = 64;
-constexpr int kP2PChunkV1 = 256;
-
-__global__ void __launch_bounds__(kP2PThreadsV1) k_p2p(const int32_t *__restrict__ leaves, const int64_t *__restrict__ pptr,
-                                                      const int32_t *__restrict__ pidx, const int32_t *__restrict__ bbeg,
-                                                      const int32_t *__restrict__ bend, const dbl4 *__restrict__ center,
-                                                      const float4 *__restrict__ pos, const float4 *__restrict__ nrm,
-                                                      const float2 *__restrict__ xs, float inv_ebar, float kappa,
-                                                      float4 *__restrict__ phi) {
-  __shared__ float4 sp[kP2PChunkV1], sn[kP2PChunkV1];
-  const int leaf = blockIdx.x;
-  const int b = leaves[leaf];
-  const dbl4 cb = center[b];
-  const int tb = bbeg[b], te = bend[b];
-  const float kap3 = kappa * (1.0f / 3.0f);
-  for (int t0 = tb; t0 < te; t0 += kP2PThreadsV1) {
-    const int t = t0 + threadIdx.x;
-    const bool act = t < te;
-    float4 xp = act ? pos[t] : make_float4(0, 0, 0, 0);
-    float4 np = act ? nrm[t] : make_float4(0, 0, 0, 0);
-    float sL = 0.f, dL = 0.f, sY = 0.f, dY = 0.f;
-    for (int64_t j = pptr[leaf]; j < pptr[leaf + 1]; ++j) {
-      const int c = pidx[j];
-      const dbl4 cc = center[c];
-      const float ox = (float)(cc.x - cb.x), oy = (float)(cc.y - cb.y), oz = (float)(cc.z - cb.z);
-      for (int s0 = bbeg[c]; s0 < bend[c]; s0 += kP2PChunkV1) {
-        const int cnt = min(kP2PChunkV1, bend[c] - s0);
-        __syncthreads();
-        for (int e = threadIdx.x; e < cnt; e += kP2PThreadsV1) {
-          float4 p = pos[s0 + e], q = nrm[s0 + e];
-          float2 fh = xs[s0 + e];
-          sp[e] = make_float4(p.x + ox, p.y + oy, p.z + oz, p.w * fh.y);
-          sn[e] = make_float4(q.x, q.y, q.z, -p.w * fh.x);
-        }
-        __syncthreads();
-        if (act) {
-          for (int e = 0; e < cnt; ++e) {
-            const float4 y = sp[e], q = sn[e];
-            const float dx = xp.x - y.x, dy = xp.y - y.y, dz = xp.z - y.z;
-            const float r2 = dx * dx + dy * dy + dz * dz;
-            const float ri = r2 > 0.0f ? rsqrtf(r2) : 0.0f;   // t == p contributes nothing
-            const float rr = r2 * ri;
-            const float ri2 = ri * ri;
-            const float G3 = ri * ri2;
-            const float G5 = 3.0f * G3 * ri2;
-            const float ndt = q.x * dx + q.y * dy + q.z * dz;
-            const float npd = np.x * dx + np.y * dy + np.z * dz;
-            const float nn = np.x * q.x + np.y * q.y + np.z * q.z;
-            const float gL = q.w * inv_ebar;
-            sL += y.w * ri + gL * ndt * G3;
-            dL += -y.w * npd * G3 + gL * (nn * G3 - ndt * npd * G5);
-            const float kr = kappa * rr;
-            const float ex = __expf(-kr);
-            const float g1 = ex * (1.0f + kr) * G3;
-            const float g2 = ex * (1.0f + kr + kr * kap3 * rr) * G5;
-            sY += y.w * ex * ri + q.w * ndt * g1;
-            dY += -y.w * npd * g1 + q.w * (nn * g1 - ndt * npd * g2);
-          }
-        }
-      }
-    }
-    if (act) {
-      const float s = (float)kInv4Pi;
-      phi[t] = make_float4(s * sL, s * dL, s * sY, s * dY);
-    }
-  }
-}
-
 // ------------------------------------------------------------------------------------
 // Combine (Eq. 5): y1 = alpha f - PhiL + PhiY + sum_near (dB f - dA h)
 //                  y2 = alpha h - dn PhiL + dn PhiY / eps_bar + sum_near (dD f - dC h)
@@ -872,10 +692,9 @@ Err enqueue_far(afmpb_t *h, cudaStream_t s, StageTimer *tm) {
 }
 
 Err enqueue_p2p(afmpb_t *h, cudaStream_t s) {
-  const auto &T = h->shape;
-  k_p2p_v3<<<T.nleaf, kP2PThreads, 0, s>>>(h->d_leaves, h->d_p2p_ptr, h->d_p2p_idx, h->d_box_begin, h->d_box_end,
-                                        h->d_box_center, h->d_pos, h->d_nrm, h->d_xs, (float)(1.0 / h->ebar),
-                                        (float)h->kappa, h->d_phi_near);
+  k_p2p_v3<<<h->shape.nleaf, kP2PThreads, 0, s>>>(h->d_leaves, h->d_p2p_ptr, h->d_p2p_idx, h->d_box_begin,
+                                                  h->d_box_end, h->d_box_center, h->d_pos, h->d_nrm, h->d_xs,
+                                                  (float)(1.0 / h->ebar), (float)h->kappa, h->d_phi_near);
   return check_launch("k_p2p_v3");
 }
 

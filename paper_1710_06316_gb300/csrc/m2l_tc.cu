@@ -186,25 +186,37 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_m2l_tc(int N3, const TCItem *
           "l"(src + kTcAElems), "r"((uint32_t)(kTcAElems * 2)), "r"(mb_load)
           : "memory");
     }
-    // B half: gathered source multipoles, split into hi / lo (rows = pairs)
+    // B half: gathered source multipoles, split into hi / lo (rows = pairs).  Each thread
+    // first issues all of its loads (up to kU units of 8 values), then converts and stores.
     constexpr int kG = kTcKHalf / 8;    // 14 groups of 8 along K
-    for (int e = threadIdx.x; e < kTcPairs * kG; e += kTcThreads) {
+    constexpr int kU = (kTcPairs * kG + kTcThreads - 1) / kTcThreads;
+    float4 u[kU][2];
+#pragma unroll
+    for (int i = 0; i < kU; ++i) {
+      const int e = threadIdx.x + i * kTcThreads;
       const int p = e / kG, k8 = e % kG;
       const int k0 = kh * kTcKHalf + k8 * 8;
-      float v[8];
-      if (p < cnt && k0 < N3) {
+      u[i][0] = u[i][1] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (e < kTcPairs * kG && p < cnt && k0 < N3) {
         const float *m = M + ((size_t)s_src[p] * 2 + kt) * N3 + k0;
         if (k0 + 8 <= N3) {
-          const float4 u0 = *reinterpret_cast<const float4 *>(m), u1 = *reinterpret_cast<const float4 *>(m + 4);
-          v[0] = u0.x; v[1] = u0.y; v[2] = u0.z; v[3] = u0.w; v[4] = u1.x; v[5] = u1.y; v[6] = u1.z; v[7] = u1.w;
+          u[i][0] = __ldg(reinterpret_cast<const float4 *>(m));
+          u[i][1] = __ldg(reinterpret_cast<const float4 *>(m + 4));
         } else {
+          float v[8];
 #pragma unroll
           for (int q = 0; q < 8; ++q) v[q] = (k0 + q < N3) ? m[q] : 0.0f;
+          u[i][0] = make_float4(v[0], v[1], v[2], v[3]);
+          u[i][1] = make_float4(v[4], v[5], v[6], v[7]);
         }
-      } else {
-#pragma unroll
-        for (int q = 0; q < 8; ++q) v[q] = 0.0f;
       }
+    }
+#pragma unroll
+    for (int i = 0; i < kU; ++i) {
+      const int e = threadIdx.x + i * kTcThreads;
+      if (e >= kTcPairs * kG) continue;
+      const int p = e / kG, k8 = e % kG;
+      const float v[8] = {u[i][0].x, u[i][0].y, u[i][0].z, u[i][0].w, u[i][1].x, u[i][1].y, u[i][1].z, u[i][1].w};
       __align__(16) __nv_bfloat16 hi[8], lo[8];
 #pragma unroll
       for (int q = 0; q < 8; ++q) split_bf16(v[q], hi[q], lo[q]);
@@ -250,10 +262,13 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_m2l_tc(int N3, const TCItem *
     mbar_wait(mb_mma, 0);     // bounded: let any issued MMA drain before freeing memory
     mbar_wait(mb_mma, 1);
   } else {
-    // epilogue: warps w and w+4 own accumulator rows 32 (w % 4) .. + 31 and split columns
+    // epilogue: warps w and w+4 read accumulator rows 32 (w % 4) .. + 31 (one row per lane)
+    // and split the columns; the tile is transposed through shared memory (the A buffer,
+    // free once the MMAs completed) so that every thread adds 4 consecutive rows of one
+    // pair with a single 16-byte vector atomic.
+    float *tile = reinterpret_cast<float *>(smem);       // [pair][128 rows]
     const int quarter = warp & 3, half = warp >> 2;
-    const int row = rt * kTcRows + quarter * 32 + lane;
-    const float scale = kt == 0 ? (float)(1.0 / center[s_tgt[0]].w) : 1.0f;
+    const int lrow = quarter * 32 + lane;
     for (int c0 = half * 16; c0 < npad; c0 += 32) {
       uint32_t r[16];
       const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0;
@@ -263,13 +278,18 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_m2l_tc(int N3, const TCItem *
             "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
           : "r"(taddr));
       asm volatile("tcgen05.wait::ld.sync.aligned;");
-      if (row < N3) {
 #pragma unroll
-        for (int q = 0; q < 16; ++q) {
-          const int p = c0 + q;
-          if (p < cnt) atomicAdd(L + ((size_t)s_tgt[p] * 2 + kt) * N3 + row, __uint_as_float(r[q]) * scale);
-        }
-      }
+      for (int q = 0; q < 16; ++q) tile[(c0 + q) * kTcRows + lrow] = __uint_as_float(r[q]);
+    }
+    __syncthreads();
+    const float scale = kt == 0 ? (float)(1.0 / center[s_tgt[0]].w) : 1.0f;
+    const int rows_valid = min(kTcRows, N3 - rt * kTcRows);   // a multiple of 4
+    for (int e = threadIdx.x; e < cnt * (kTcRows / 4); e += kTcThreads) {
+      const int p = e / (kTcRows / 4), g4 = (e % (kTcRows / 4)) * 4;
+      if (g4 >= rows_valid) continue;
+      float4 v = *reinterpret_cast<const float4 *>(tile + p * kTcRows + g4);
+      v.x *= scale; v.y *= scale; v.z *= scale; v.w *= scale;
+      atomicAdd(reinterpret_cast<float4 *>(L + ((size_t)s_tgt[p] * 2 + kt) * N3 + rt * kTcRows + g4), v);
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
@@ -283,7 +303,10 @@ constexpr int kTcSmem = (2 * kTcAElems + 2 * kTcBElems) * 2;
 
 Err build_m2l_tc(afmpb_t *h) {
   const int N3 = h->ncoef;
-  if (N3 > kTcK) return make_err(AFMPB_EINVAL, "precision 1 (tensor-core M2L) supports fmm_order <= 6");
+  // the epilogue adds 4 consecutive weights with one 16-byte atomic: n^3 must be a
+  // multiple of 4 (orders 2, 4, 6) and fit the 224-wide contraction
+  if (N3 > kTcK || N3 % 4 != 0)
+    return make_err(AFMPB_EINVAL, "precision 1 (tensor-core M2L) supports fmm_order 2, 4 or 6");
   auto &A = h->arena;
   cudaStream_t s = h->stream;
   // work items: chunks of <= 112 pairs per (level, offset) group
