@@ -179,6 +179,25 @@ afmpb_status afmpb_solve(afmpb_t *h, double *f_host, double *h_host, afmpb_solve
  * the surface solution.  Requires a successful (or ENOCONV) afmpb_solve. */
 afmpb_status afmpb_energy(afmpb_t *h, double *kcal_per_mol);
 
+/* Allocation-free variant of afmpb_energy, for callers that cannot call cudaMalloc:
+ * processes whose device memory is fully reserved by another allocator (a framework
+ * memory pool or a fixed serving budget), and latency-critical loops that cannot afford
+ * the device-wide synchronisation an allocation or free can cause.  afmpb_energy
+ * allocates its partial-sum buffers on every call; this variant instead uses one
+ * scratch array compiled into the library as a static device array of
+ * 16 x AFMPB_NOALLOC_MAX_ATOMS + AFMPB_NOALLOC_MAX_ATOMS + 1 doubles (about 8.4 MB),
+ * which every GPU that loads the library holds until the process exits.
+ *   h             a handle with a prior afmpb_solve (ESTATE otherwise)
+ *   kcal_per_mol  host output, the same energy afmpb_energy returns
+ * Returns EINVAL when the handle has more than AFMPB_NOALLOC_MAX_ATOMS charges.  The
+ * first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ * and caches it; make that first call before any stream capture.  All calls share the
+ * one array, so calls whose work overlaps on the GPU (two handles on different streams)
+ * race and must be serialised by the caller.  The paper has no counterpart to this
+ * entry point. */
+#define AFMPB_NOALLOC_MAX_ATOMS 65536
+afmpb_status afmpb_energy_noalloc(afmpb_t *h, double *kcal_per_mol);
+
 /* The right-hand side of Eq. 5 (caller order, host [2N]). */
 afmpb_status afmpb_rhs(afmpb_t *h, double *b_host);
 

@@ -76,7 +76,7 @@ def _struct_dict(s):
 EXPORTS = ["afmpb_create", "afmpb_matvec", "afmpb_matvec_parts", "afmpb_matvec_host", "afmpb_solve",
            "afmpb_energy", "afmpb_rhs", "afmpb_get_geometry", "afmpb_get_near", "afmpb_get_tree",
            "afmpb_get_info", "afmpb_destroy", "afmpb_last_error", "afmpb_estimate_bytes",
-           "afmpb_version", "afmpb_profile_product"]
+           "afmpb_version", "afmpb_profile_product", "afmpb_energy_noalloc"]
 
 
 def library_path() -> str:
@@ -106,6 +106,8 @@ def load(build: bool = True):
     lib.afmpb_solve.argtypes = [P, P, P, C.POINTER(SolveInfo)]
     lib.afmpb_energy.restype = I32
     lib.afmpb_energy.argtypes = [P, C.POINTER(D)]
+    lib.afmpb_energy_noalloc.restype = I32
+    lib.afmpb_energy_noalloc.argtypes = [P, C.POINTER(D)]
     lib.afmpb_rhs.restype = I32
     lib.afmpb_rhs.argtypes = [P, P]
     lib.afmpb_get_geometry.restype = I32
@@ -233,6 +235,12 @@ class Handle:
     def energy(self):
         e = C.c_double()
         _check(self._lib.afmpb_energy(self.h, C.byref(e)), self.h)
+        return float(e.value)
+
+    def energy_noalloc(self):
+        """Same energy as energy(), computed without any device allocation (static scratch)."""
+        e = C.c_double()
+        _check(self._lib.afmpb_energy_noalloc(self.h, C.byref(e)), self.h)
         return float(e.value)
 
     def rhs(self):

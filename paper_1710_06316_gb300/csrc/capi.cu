@@ -250,6 +250,12 @@ afmpb_status afmpb_energy(afmpb_t *h, double *E) {
   return e.ok() ? AFMPB_OK : fail(h, e);
 }
 
+afmpb_status afmpb_energy_noalloc(afmpb_t *h, double *E) {
+  if (!h || !E) return fail(h, make_err(AFMPB_EINVAL, "handle and output are required"));
+  Err e = run_energy_noalloc(h, E);
+  return e.ok() ? AFMPB_OK : fail(h, e);
+}
+
 afmpb_status afmpb_rhs(afmpb_t *h, double *b) {
   if (!h || !b) return fail(h, make_err(AFMPB_EINVAL, "handle and output are required"));
   std::vector<double> bs(2 * h->n);

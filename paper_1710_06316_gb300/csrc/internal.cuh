@@ -246,6 +246,7 @@ Err enqueue_gather(afmpb_t *h, cudaStream_t s, const float *x_caller);
 Err enqueue_scatter(afmpb_t *h, cudaStream_t s, float *y_caller);
 Err run_solve(afmpb_t *h, afmpb_solve_info *info);
 Err run_energy(afmpb_t *h, double *E);
+Err run_energy_noalloc(afmpb_t *h, double *E);      // static scratch, no allocation
 // capi.cu
 Err product_sorted(afmpb_t *h, cudaStream_t s, int parts);  // d_xs -> d_ys
 

@@ -11,6 +11,7 @@
 // partition and a fixed summation order, so results are reproducible.
 #include <chrono>
 #include <cmath>
+#include <mutex>
 
 #include "internal.cuh"
 
@@ -483,6 +484,61 @@ Err run_energy(afmpb_t *h, double *E) {
   A.release(d_part);
   A.release(d_phi);
   A.release(d_E);
+  return Err{};
+}
+
+// ---- allocation-free energy ---------------------------------------------------------------
+// The partial sums, reaction potentials and the energy of afmpb_energy_noalloc live in
+// this static device array instead of buffers allocated per call.  In host code the
+// symbol is only a stand-in: its device address is looked up once per device with
+// cudaGetSymbolAddress and cached.
+constexpr int kNoAllocParts = 16;
+constexpr int kNoAllocMaxAtoms = AFMPB_NOALLOC_MAX_ATOMS;
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocParts * kNoAllocMaxAtoms + kNoAllocMaxAtoms + 1];
+
+namespace {
+constexpr int kMaxDevices = 64;
+double *g_noalloc_ptr[kMaxDevices] = {};
+std::mutex g_noalloc_mutex;
+}  // namespace
+
+Err run_energy_noalloc(afmpb_t *h, double *E) {
+  if (!h->solved || !h->d_sol) return make_err(AFMPB_ESTATE, "afmpb_energy_noalloc needs a prior afmpb_solve");
+  if (h->natoms == 0) return make_err(AFMPB_ESTATE, "the handle has no charges");
+  if (h->natoms > kNoAllocMaxAtoms)
+    return make_err(AFMPB_EINVAL, "afmpb_energy_noalloc handles at most AFMPB_NOALLOC_MAX_ATOMS (" +
+                                      std::to_string(kNoAllocMaxAtoms) + ") charges; the handle has " +
+                                      std::to_string(h->natoms));
+  int dev = 0;
+  AFMPB_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return make_err(AFMPB_EINVAL, "device ordinal out of range");
+  double *base = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+      void *p = nullptr;
+      AFMPB_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+      g_noalloc_ptr[dev] = static_cast<double *>(p);
+    }
+    base = g_noalloc_ptr[dev];
+  }
+  double *d_part = base;                                    // [parts][natoms], fully rewritten
+  double *d_phi = base + (size_t)kNoAllocParts * kNoAllocMaxAtoms;
+  double *d_E = d_phi + kNoAllocMaxAtoms;
+  const int nleaf = h->shape.nleaf;
+  const int nparts = std::min(nleaf, kNoAllocParts);
+  const int lpb = div_up(nleaf, nparts);
+  const int nparts_used = div_up(nleaf, lpb);
+  dim3 grid(div_up(h->natoms, 128), nparts_used);
+  k_energy_part<<<grid, 128, 0, h->stream>>>(nleaf, lpb, h->d_leaves, h->d_box_begin, h->d_box_end, h->d_box_center,
+                                              h->d_pos, h->d_nrm, h->d_sol, h->n, h->ebar, h->natoms, h->d_atoms,
+                                              d_part);
+  AFMPB_TRY(check_launch("k_energy_part (no alloc)"));
+  const double K_c = 332.0636;   // kcal A / (mol e^2)
+  k_energy_final<<<1, 256, 0, h->stream>>>(nparts_used, h->natoms, d_part, h->d_q, 4.0 * kPi * K_c, d_phi, d_E);
+  AFMPB_TRY(check_launch("k_energy_final (no alloc)"));
+  AFMPB_CUDA(cudaMemcpyAsync(E, d_E, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  AFMPB_CUDA(cudaStreamSynchronize(h->stream));
   return Err{};
 }
 
