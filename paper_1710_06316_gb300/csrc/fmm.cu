@@ -371,8 +371,10 @@ __global__ void __launch_bounds__(256) k_p2l(const int32_t *__restrict__ xbox, c
 // ------------------------------------------------------------------------------------
 // L2P: evaluate both local expansions and their normal derivatives at leaf targets.
 // ------------------------------------------------------------------------------------
+constexpr int kL2PThreads = 64;   // leaves hold ~cap/3 nodes on surfaces
+
 template <int N>
-__global__ void __launch_bounds__(128) k_l2p(const int32_t *__restrict__ leaves, const int32_t *__restrict__ bbeg,
+__global__ void __launch_bounds__(kL2PThreads, 12) k_l2p(const int32_t *__restrict__ leaves, const int32_t *__restrict__ bbeg,
                                              const int32_t *__restrict__ bend, const dbl4 *__restrict__ center,
                                              const float4 *__restrict__ pos, const float4 *__restrict__ nrm,
                                              const float *__restrict__ L, float4 *__restrict__ phi) {
@@ -389,7 +391,7 @@ __global__ void __launch_bounds__(128) k_l2p(const int32_t *__restrict__ leaves,
     cheb_basis<N>(p.y * invw, sy, dsy);
     cheb_basis<N>(p.z * invw, sz, dsz);
     float out[4];
-#pragma unroll
+#pragma unroll 1
     for (int kt = 0; kt < 2; ++kt) {
       const float *Lk = sL + kt * N3;
       float phi0 = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
@@ -414,8 +416,8 @@ __global__ void __launch_bounds__(128) k_l2p(const int32_t *__restrict__ leaves,
         gy = fmaf(bj, sx[i], gy);
         gz = fmaf(cj, sx[i], gz);
       }
-      out[2 * kt] = phi0;
-      out[2 * kt + 1] = (q.x * gx + q.y * gy + q.z * gz) * invw;
+      const float dn = (q.x * gx + q.y * gy + q.z * gz) * invw;
+      if (kt == 0) { out[0] = phi0; out[1] = dn; } else { out[2] = phi0; out[3] = dn; }
     }
     phi[t] = make_float4(out[0], out[1], out[2], out[3]);
   }
@@ -425,7 +427,7 @@ __global__ void __launch_bounds__(128) k_l2p(const int32_t *__restrict__ leaves,
 // P2P (lists 1 and 3): point (far-rule) sums over t != p, both kernels, both outputs.
 // ------------------------------------------------------------------------------------
 constexpr int kP2PThreads = 128;
-constexpr int kP2PChunk = 1024;     // sources staged in shared memory at a time
+constexpr int kP2PChunk = 768;      // sources staged in shared memory at a time (8 CTAs/SM)
 constexpr int kP2PBoxes = 64;       // source boxes described in shared memory at a time
 
 // Far-rule sums of one source at one target, without the 1/(4 pi):
@@ -468,7 +470,7 @@ __device__ __forceinline__ void p2p_pair(const float4 &xp, const float4 &np, con
 // leaves are described in shared memory 64 at a time (warp prefix scan of their sizes);
 // their nodes are staged 512 at a time, each shifted by its own leaf centre's offset,
 // and every thread sums its target against every slices-th staged source.
-__global__ void __launch_bounds__(kP2PThreads) k_p2p_v3(const int32_t *__restrict__ leaves,
+__global__ void __launch_bounds__(kP2PThreads, 8) k_p2p_v3(const int32_t *__restrict__ leaves,
                                                          const int64_t *__restrict__ pptr,
                                                          const int32_t *__restrict__ pidx,
                                                          const int32_t *__restrict__ bbeg,
@@ -661,7 +663,7 @@ Err launch_far(afmpb_t *h, cudaStream_t s, StageTimer *tm) {
     AFMPB_TRY(check_launch("k_l2l"));
   }
   if (tm) tm->mark("l2l", std::max(0, T.nlevel - 3));
-  k_l2p<N><<<T.nleaf, 128, 0, s>>>(h->d_leaves, h->d_box_begin, h->d_box_end, h->d_box_center, h->d_pos, h->d_nrm,
+  k_l2p<N><<<T.nleaf, kL2PThreads, 0, s>>>(h->d_leaves, h->d_box_begin, h->d_box_end, h->d_box_center, h->d_pos, h->d_nrm,
                                    h->d_L, h->d_phi_far);
   AFMPB_TRY(check_launch("k_l2p"));
   if (tm) tm->mark("l2p", 1);
