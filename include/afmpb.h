@@ -206,9 +206,15 @@ afmpb_status afmpb_rhs(afmpb_t *h, double *b_host);
 afmpb_status afmpb_get_geometry(afmpb_t *h, double *area, double *normals, double *rho);
 
 /* Near-field CSR in caller order.  rowptr [N+1]; col [nnz]; coef [nnz*4] holds
- * (dA, dB, dC, dD): near rule minus far rule for t != p, the self-patch integrals for
- * t == p.  Columns of a row are in the octree's Morton order.  Pass NULLs to skip. */
-afmpb_status afmpb_get_near(afmpb_t *h, int64_t *rowptr, int32_t *col, float *coef);
+ * (dA, dB, dC, dD); whole [nnz] tells which of two values an entry holds.  whole = 0:
+ * near rule minus far (point) rule -- the product's far part already holds the point
+ * rule for that pair.  whole = 1: the whole near-rule value, for the self entry (the
+ * self-patch integrals of Eq. 6) and for the close pairs that the point-to-point pass
+ * leaves out (FP32 distance r <= 0.9 c (rho_p + rho_t), every one of them inside the
+ * near set r < c (rho_p + rho_t)).  Columns of a row are in the octree's Morton order.
+ * Pass NULLs to skip. */
+afmpb_status afmpb_get_near(afmpb_t *h, int64_t *rowptr, int32_t *col, float *coef,
+                            uint8_t *whole);
 
 /* Octree export (host buffers sized from afmpb_get_info; any may be NULL):
  *   box_level [n_boxes], box_anchor [n_boxes*3] (integer cell coordinates at the box's

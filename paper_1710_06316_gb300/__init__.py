@@ -113,7 +113,7 @@ def load(build: bool = True):
     lib.afmpb_get_geometry.restype = I32
     lib.afmpb_get_geometry.argtypes = [P, P, P, P]
     lib.afmpb_get_near.restype = I32
-    lib.afmpb_get_near.argtypes = [P, P, P, P]
+    lib.afmpb_get_near.argtypes = [P, P, P, P, P]
     lib.afmpb_get_tree.restype = I32
     lib.afmpb_get_tree.argtypes = [P] + [P] * 13
     lib.afmpb_get_info.restype = I32
@@ -266,8 +266,10 @@ class Handle:
         rp = np.zeros(self.n + 1, np.int64)
         col = np.zeros(nnz, np.int32)
         coef = np.zeros((nnz, 4), np.float32)
-        _check(self._lib.afmpb_get_near(self.h, rp.ctypes.data, col.ctypes.data, coef.ctypes.data), self.h)
-        return rp, col, coef
+        whole = np.zeros(nnz, np.uint8)
+        _check(self._lib.afmpb_get_near(self.h, rp.ctypes.data, col.ctypes.data, coef.ctypes.data,
+                                        whole.ctypes.data), self.h)
+        return rp, col, coef, whole.astype(bool)
 
     def tree(self):
         inf = self.info()

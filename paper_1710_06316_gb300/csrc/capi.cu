@@ -283,15 +283,17 @@ afmpb_status afmpb_get_geometry(afmpb_t *h, double *area, double *normals, doubl
   return AFMPB_OK;
 }
 
-afmpb_status afmpb_get_near(afmpb_t *h, int64_t *rowptr, int32_t *col, float *coef) {
+afmpb_status afmpb_get_near(afmpb_t *h, int64_t *rowptr, int32_t *col, float *coef, uint8_t *whole) {
   if (!h) return fail(nullptr, make_err(AFMPB_EINVAL, "handle is NULL"));
   const int64_t n = h->n;
   std::vector<int64_t> ptr(n + 1);
   std::vector<int32_t> c(h->nnz), perm(n);
   std::vector<float4> cf(h->nnz);
+  std::vector<uint8_t> fl(h->nnz);
   cudaError_t ce = cudaMemcpyAsync(ptr.data(), h->d_near_ptr, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost, h->stream);
   if (ce == cudaSuccess) ce = cudaMemcpyAsync(c.data(), h->d_near_col, sizeof(int32_t) * h->nnz, cudaMemcpyDeviceToHost, h->stream);
   if (ce == cudaSuccess) ce = cudaMemcpyAsync(cf.data(), h->d_near_coef, sizeof(float4) * h->nnz, cudaMemcpyDeviceToHost, h->stream);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(fl.data(), h->d_near_full, h->nnz, cudaMemcpyDeviceToHost, h->stream);
   if (ce == cudaSuccess) ce = cudaMemcpyAsync(perm.data(), h->d_perm, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, h->stream);
   if (ce == cudaSuccess) ce = cudaStreamSynchronize(h->stream);
   if (ce != cudaSuccess) return fail(h, make_err(AFMPB_ECUDA, cudaGetErrorString(ce)));
@@ -303,6 +305,7 @@ afmpb_status afmpb_get_near(afmpb_t *h, int64_t *rowptr, int32_t *col, float *co
     const int64_t p = iperm[o];
     for (int64_t j = ptr[p]; j < ptr[p + 1]; ++j, ++k) {
       if (col) col[k] = perm[c[j]];
+      if (whole) whole[k] = fl[j];
       if (coef) {
         coef[4 * k] = cf[j].x;
         coef[4 * k + 1] = cf[j].y;
@@ -494,7 +497,7 @@ size_t afmpb_estimate_bytes(int64_t n_nodes, int64_t n_atoms, int fmm_order, con
   size_t b = 0;
   b += n * (3 * 8 + 8 + 3 * 8 + 8 + 2 * 16 + 8 + 4 + 4 + 2 * 16 + 8 + 2 * 4 + 4 * 16);   // nodes
   b += 2 * n * (3 * 4 + 3 * 8 + 4);                                                    // triangles
-  b += n * 40 * (4 + 16) + 8 * (n + 1);                                                 // near CSR
+  b += n * 40 * (4 + 16 + 1) + 8 * (n + 1);                                             // near CSR
   b += nbox * (2 * 2 * n3 * 4 + 64 + 27 * 4 + 200 * 4 * 2);                             // boxes, lists
   b += 316 * n3 * n3 * 4 * 14;                                                          // M2L tables
   b += (size_t)(m + 1) * 2 * n * 8 + 8 * 2 * n * 8;                                     // GMRES

@@ -427,7 +427,7 @@ __global__ void __launch_bounds__(kL2PThreads, 12) k_l2p(const int32_t *__restri
 // P2P (lists 1 and 3): point (far-rule) sums over t != p, both kernels, both outputs.
 // ------------------------------------------------------------------------------------
 constexpr int kP2PThreads = 128;
-constexpr int kP2PChunk = 768;      // sources staged in shared memory at a time (8 CTAs/SM)
+constexpr int kP2PChunk = 704;      // sources staged in shared memory at a time (8 CTAs/SM)
 constexpr int kP2PBoxes = 64;       // source boxes described in shared memory at a time
 
 // Far-rule sums of one source at one target, without the 1/(4 pi):
@@ -436,12 +436,14 @@ constexpr int kP2PBoxes = 64;       // source boxes described in shared memory a
 //   PhiY += c e/r + g (n.d) e1/r^3,           e = exp(-kr), e1 = e (1 + kr)
 //   dn PhiY += e1 [g (n0.n) - c (n0.d)]/r^3 - 3 g e2 (n.d)(n0.d)/r^5,  e2 = e (1 + kr + (kr)^2/3)
 // with d = x_target - y_source; subexpressions are shared between the two kernels.
-__device__ __forceinline__ void p2p_pair(const float4 &xp, const float4 &np, const float4 &y, const float4 &q,
-                                         float inv_ebar, float kappa, float &sL, float &dL, float &sY,
-                                         float &dY) {
+__device__ __forceinline__ void p2p_pair(const float4 &xp, const float4 &np, float rsp, const float4 &y,
+                                         const float4 &q, float rst, float inv_ebar, float kappa, float &sL,
+                                         float &dL, float &sY, float &dY) {
   const float dx = xp.x - y.x, dy = xp.y - y.y, dz = xp.z - y.z;
-  const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-  const float ri = r2 > 0.0f ? rsqrtf(r2) : 0.0f;     // t == p contributes nothing
+  const float r2 = p2p_r2(dx, dy, dz);
+  // Pairs inside the skip radius (t == p among them) contribute nothing here: the near
+  // CSR carries their whole near-rule value.
+  const float ri = p2p_evaluates(r2, rsp, rst) ? rsqrtf(r2) : 0.0f;
   const float ri2 = ri * ri;
   const float G3 = ri * ri2;
   const float ndt = fmaf(q.x, dx, fmaf(q.y, dy, q.z * dz));
@@ -479,11 +481,14 @@ __global__ void __launch_bounds__(kP2PThreads, 8) k_p2p_v3(const int32_t *__rest
                                                          const float4 *__restrict__ pos,
                                                          const float4 *__restrict__ nrm,
                                                          const float2 *__restrict__ xs, float inv_ebar,
-                                                         float kappa, float4 *__restrict__ phi) {
+                                                         float kappa, float skip_scale,
+                                                         float4 *__restrict__ phi) {
+  static_assert(kP2PThreads <= kP2PChunk, "the reduction reuses the staging buffer");
   __shared__ float4 sp[kP2PChunk], sn[kP2PChunk];
+  __shared__ float sr[kP2PChunk];
   __shared__ int s_beg[kP2PBoxes], s_pre[kP2PBoxes + 1];
   __shared__ float s_off[kP2PBoxes][3];
-  __shared__ float4 red[kP2PThreads];
+  float4 *red = sp;
   const int leaf = blockIdx.x;
   const int b = leaves[leaf];
   const dbl4 cb = center[b];
@@ -498,6 +503,7 @@ __global__ void __launch_bounds__(kP2PThreads, 8) k_p2p_v3(const int32_t *__rest
     const bool act = si < slices && t < te;
     const float4 xp = act ? pos[t] : make_float4(0, 0, 0, 0);
     const float4 np = act ? nrm[t] : make_float4(0, 0, 0, 0);
+    const float rsp = p2p_skip_radius(skip_scale, np.w);
     float sL = 0.f, dL = 0.f, sY = 0.f, dY = 0.f;
     for (int64_t g0 = l0; g0 < l1; g0 += kP2PBoxes) {
       const int nb = (int)min((int64_t)kP2PBoxes, l1 - g0);
@@ -539,13 +545,15 @@ __global__ void __launch_bounds__(kP2PThreads, 8) k_p2p_v3(const int32_t *__rest
           const int sidx = s_beg[lo] + (j - s_pre[lo]);
           const float4 p = pos[sidx], q = nrm[sidx];
           const float2 fh = xs[sidx];
-          sp[e] = make_float4(p.x + s_off[lo][0], p.y + s_off[lo][1], p.z + s_off[lo][2], p.w * fh.y);
+          sp[e] = make_float4(__fadd_rn(p.x, s_off[lo][0]), __fadd_rn(p.y, s_off[lo][1]),
+                              __fadd_rn(p.z, s_off[lo][2]), p.w * fh.y);
           sn[e] = make_float4(q.x, q.y, q.z, -p.w * fh.x);
+          sr[e] = p2p_skip_radius(skip_scale, q.w);
         }
         __syncthreads();
         if (act) {
 #pragma unroll 4
-          for (int e = si; e < cnt; e += slices) p2p_pair(xp, np, sp[e], sn[e], inv_ebar, kappa, sL, dL, sY, dY);
+          for (int e = si; e < cnt; e += slices) p2p_pair(xp, np, rsp, sp[e], sn[e], sr[e], inv_ebar, kappa, sL, dL, sY, dY);
         }
       }
     }
@@ -696,7 +704,8 @@ Err enqueue_far(afmpb_t *h, cudaStream_t s, StageTimer *tm) {
 Err enqueue_p2p(afmpb_t *h, cudaStream_t s) {
   k_p2p_v3<<<h->shape.nleaf, kP2PThreads, 0, s>>>(h->d_leaves, h->d_p2p_ptr, h->d_p2p_idx, h->d_box_begin,
                                                   h->d_box_end, h->d_box_center, h->d_pos, h->d_nrm, h->d_xs,
-                                                  (float)(1.0 / h->ebar), (float)h->kappa, h->d_phi_near);
+                                                  (float)(1.0 / h->ebar), (float)h->kappa,
+                                                  (float)(kP2PSkip * h->opt.near_c), h->d_phi_near);
   return check_launch("k_p2p_v3");
 }
 

@@ -24,6 +24,27 @@ constexpr int kKeyBits = 21;        // Morton bits per dimension (63-bit keys)
 constexpr int kNumOffsets = 316;    // M2L offsets: [-3,3]^3 minus [-1,1]^3
 constexpr double kPi = 3.14159265358979323846;
 constexpr double kInv4Pi = 0.07957747154594767;  // 1 / (4 pi)
+constexpr double kP2PSkip = 0.9;    // P2P leaves out pairs closer than kP2PSkip * c * (rho_p + rho_t)
+
+// Pair geometry of the P2P pass in FP32.  Positions are relative to the target's leaf
+// centre; a source is shifted by the rounded difference of the two leaf centres.  Near-field
+// setup calls the same functions to learn, bit for bit, which near pairs the P2P pass
+// leaves out (those pairs then carry the whole near-rule value in the near CSR).  The
+// _rn intrinsics keep the compiler from contracting the products into FMAs differently
+// in the two kernels.
+__device__ __forceinline__ float p2p_shift(float x, double src_centre, double tgt_centre) {
+  return __fadd_rn(x, (float)(src_centre - tgt_centre));
+}
+__device__ __forceinline__ float p2p_r2(float dx, float dy, float dz) {
+  return fmaf(dx, dx, fmaf(dy, dy, __fmul_rn(dz, dz)));
+}
+// Scaled patch radius kP2PSkip * c * rho of one node; `scale` = (float)(kP2PSkip * c).
+__device__ __forceinline__ float p2p_skip_radius(float scale, float rho) { return __fmul_rn(scale, rho); }
+// True when the P2P pass evaluates the pair (squared distance r2, scaled radii sp and st).
+__device__ __forceinline__ bool p2p_evaluates(float r2, float sp, float st) {
+  const float R = __fadd_rn(sp, st);
+  return r2 > __fmul_rn(R, R);
+}
 
 // Error carried up the host call chain; every internal function returns one.
 struct Err {
@@ -166,6 +187,7 @@ struct afmpb_t {
   int32_t *d_colleague = nullptr;  // [27 nbox]
   int32_t *d_leaves = nullptr;     // [nleaf] leaf box ids in Morton order
   int32_t *d_node_leaf = nullptr;  // [n] Morton position -> leaf box
+  int32_t *d_leaf_index = nullptr; // [nbox] leaf box -> position in d_leaves, -1 otherwise
   // lists (CSR over boxes; u and w non-empty only for leaves)
   int64_t *d_u_ptr = nullptr, *d_v_ptr = nullptr, *d_w_ptr = nullptr, *d_x_ptr = nullptr;
   int32_t *d_u_idx = nullptr, *d_v_idx = nullptr, *d_w_idx = nullptr, *d_x_idx = nullptr;
@@ -176,13 +198,14 @@ struct afmpb_t {
 
   // ---- Morton-ordered node data -----------------------------------------------------
   float4 *d_pos = nullptr;         // position relative to the leaf centre, w = patch area
-  float4 *d_nrm = nullptr;         // unit normal, w = 0
+  float4 *d_nrm = nullptr;         // unit normal, w = patch radius rho
 
   // ---- near field -------------------------------------------------------------------
   int64_t nnz = 0;
   int64_t *d_near_ptr = nullptr;   // [n+1]
   int32_t *d_near_col = nullptr;   // [nnz] Morton positions
   float4 *d_near_coef = nullptr;   // [nnz] (dA, dB, dC, dD)
+  uint8_t *d_near_full = nullptr;  // [nnz] 1 where the entry holds the whole near-rule value
 
   // ---- FMM --------------------------------------------------------------------------
   float *d_M = nullptr;            // [nbox][2][ncoef] multipole weights (Laplace, Yukawa)

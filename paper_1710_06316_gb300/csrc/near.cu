@@ -268,7 +268,18 @@ __global__ void k_near_search(int64_t n, double cnear, const int32_t *__restrict
   if (!fill) cnt[p] = k;
 }
 
-// Coefficients, one warp per row.
+// What the P2P pass sees of a pair: its source lists and the FP32 node data.
+struct P2PView {
+  const int32_t *node_leaf, *leaf_index, *pidx;
+  const int64_t *pptr;
+  const dbl4 *center;
+  const float4 *pos, *nrm;
+  float skip_scale;
+};
+
+// Coefficients, one warp per row.  An entry is the near rule minus the point rule, except
+// where the P2P pass leaves the pair out (the self entry among them): there it is the
+// whole near-rule value and `full` is set.
 template <class Real>
 __global__ void __launch_bounds__(128) k_near_coef(int64_t n, KernelParams kp, const int32_t *__restrict__ perm,
                                                    const double *__restrict__ xyz, const int32_t *__restrict__ tri,
@@ -276,7 +287,8 @@ __global__ void __launch_bounds__(128) k_near_coef(int64_t n, KernelParams kp, c
                                                    const int32_t *__restrict__ inc_tri,
                                                    const double *__restrict__ tri_nrm, const double *__restrict__ area,
                                                    const double *__restrict__ nrm, const int64_t *__restrict__ ptr,
-                                                   const int32_t *__restrict__ col, float4 *__restrict__ coef) {
+                                                   const int32_t *__restrict__ col, P2PView pv,
+                                                   float4 *__restrict__ coef, uint8_t *__restrict__ full) {
   const int64_t p = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (p >= n) return;
@@ -284,14 +296,36 @@ __global__ void __launch_bounds__(128) k_near_coef(int64_t n, KernelParams kp, c
   const double *xp = xyz + 3 * op;
   const V3<Real> np{(Real)nrm[3 * op], (Real)nrm[3 * op + 1], (Real)nrm[3 * op + 2]};
   const Real kappa = (Real)kp.kappa, ebar = (Real)kp.ebar;
+  const int lp = pv.node_leaf[p];
+  const dbl4 cp = pv.center[lp];
+  const float4 xp32 = pv.pos[p];
+  const float rsp = p2p_skip_radius(pv.skip_scale, pv.nrm[p].w);
+  const int64_t l0 = pv.pptr[pv.leaf_index[lp]], l1 = pv.pptr[pv.leaf_index[lp] + 1];
   for (int64_t j = ptr[p] + lane; j < ptr[p + 1]; j += 32) {
     const int t = col[j];
     const int64_t ot = perm[t];
     Real o[4] = {0, 0, 0, 0};
+    bool whole = true;
     if (t == p) {
       self_rule(kappa, ebar, xyz, tri, inc_ptr, inc_tri, op, np, o);
     } else {
       near_rule(kappa, ebar, xyz, tri, inc_ptr, inc_tri, tri_nrm, xp, np, ot, o);
+      // Replay the P2P pass's FP32 distance test: when it evaluates this pair, the far
+      // rule is already in the product and the entry is the correction.
+      const int lt = pv.node_leaf[t];
+      bool listed = false;
+      for (int64_t k = l0; k < l1 && !listed; ++k) listed = pv.pidx[k] == lt;
+      if (listed) {
+        const dbl4 ct = pv.center[lt];
+        const float4 y = pv.pos[t];
+        const float dx = xp32.x - p2p_shift(y.x, ct.x, cp.x), dy = xp32.y - p2p_shift(y.y, ct.y, cp.y),
+                    dz = xp32.z - p2p_shift(y.z, ct.z, cp.z);
+        whole = !p2p_evaluates(p2p_r2(dx, dy, dz), rsp, p2p_skip_radius(pv.skip_scale, pv.nrm[t].w));
+      } else {
+        whole = false;                      // a far-field pair (M2L, P2L or L2P side)
+      }
+    }
+    if (!whole) {
       const double *xt = xyz + 3 * ot;
       const V3<Real> d{(Real)(xp[0] - xt[0]), (Real)(xp[1] - xt[1]), (Real)(xp[2] - xt[2])};
       const V3<Real> nt{(Real)nrm[3 * ot], (Real)nrm[3 * ot + 1], (Real)nrm[3 * ot + 2]};
@@ -301,6 +335,7 @@ __global__ void __launch_bounds__(128) k_near_coef(int64_t n, KernelParams kp, c
       for (int k = 0; k < 4; ++k) o[k] -= at * f[k];
     }
     coef[j] = make_float4((float)o[0], (float)o[1], (float)o[2], (float)o[3]);
+    full[j] = whole ? 1 : 0;
   }
 }
 
@@ -380,9 +415,13 @@ Err build_near(afmpb_t *h) {
                                                h->d_box_end, nullptr, h->d_near_ptr, h->d_near_col, true);
   AFMPB_TRY(check_launch("k_near_search fill"));
   KernelParams kp{h->kappa, h->ebar};
+  AFMPB_TRY(A.alloc(&h->d_near_full, h->nnz, "near full"));
+  const P2PView pv{h->d_node_leaf, h->d_leaf_index, h->d_p2p_idx, h->d_p2p_ptr, h->d_box_center,
+                   h->d_pos,       h->d_nrm,        (float)(kP2PSkip * h->opt.near_c)};
   k_near_coef<float><<<div_up(n * 32, 128), 128, 0, s>>>(n, kp, h->d_perm, h->d_xyz, h->d_tri, h->d_inc_ptr,
                                                           h->d_inc_tri, h->d_tri_nrm, h->d_area64, h->d_nrm64,
-                                                          h->d_near_ptr, h->d_near_col, h->d_near_coef);
+                                                          h->d_near_ptr, h->d_near_col, pv, h->d_near_coef,
+                                                          h->d_near_full);
   AFMPB_TRY(check_launch("k_near_coef"));
   AFMPB_CUDA(cudaStreamSynchronize(s));
   A.release(d_cnt);

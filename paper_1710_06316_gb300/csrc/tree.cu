@@ -235,18 +235,18 @@ __global__ void k_node_leaf(int nleaf, const int32_t *__restrict__ leaves, const
 }
 
 // Morton-ordered node data: position relative to the leaf centre (exact box-centre
-// differences keep FP32 relative to the leaf size), patch area, normal.
+// differences keep FP32 relative to the leaf size), patch area; normal and patch radius.
 __global__ void k_node_sorted(int64_t n, const int32_t *__restrict__ perm, const int32_t *__restrict__ node_leaf,
                               const dbl4 *__restrict__ center, const double *__restrict__ xyz,
                               const double *__restrict__ area, const double *__restrict__ nrm,
-                              float4 *__restrict__ pos, float4 *__restrict__ nr) {
+                              const double *__restrict__ rho, float4 *__restrict__ pos, float4 *__restrict__ nr) {
   int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (p >= n) return;
   int64_t o = perm[p];
   dbl4 c = center[node_leaf[p]];
   pos[p] = make_float4((float)(xyz[3 * o] - c.x), (float)(xyz[3 * o + 1] - c.y), (float)(xyz[3 * o + 2] - c.z),
                        (float)area[o]);
-  nr[p] = make_float4((float)nrm[3 * o], (float)nrm[3 * o + 1], (float)nrm[3 * o + 2], 0.0f);
+  nr[p] = make_float4((float)nrm[3 * o], (float)nrm[3 * o + 1], (float)nrm[3 * o + 2], (float)rho[o]);
 }
 
 __global__ void k_box_rho_leaf(int nleaf, const int32_t *__restrict__ leaves, const int32_t *__restrict__ bbeg,
@@ -623,8 +623,13 @@ Err build_tree(afmpb_t *h) {
   AFMPB_TRY(A.alloc(&h->d_pos, n, "pos"));
   AFMPB_TRY(A.alloc(&h->d_nrm, n, "nrm"));
   k_node_sorted<<<div_up(n, 256), 256, 0, s>>>(n, h->d_perm, h->d_node_leaf, h->d_box_center, h->d_xyz,
-                                               h->d_area64, h->d_nrm64, h->d_pos, h->d_nrm);
+                                               h->d_area64, h->d_nrm64, h->d_rho64, h->d_pos, h->d_nrm);
   AFMPB_TRY(check_launch("k_node_sorted"));
+  {
+    std::vector<int32_t> leaf_index(nbox, -1);
+    for (int i = 0; i < T.nleaf; ++i) leaf_index[leaves[i]] = i;
+    AFMPB_TRY(to_device(h, &h->d_leaf_index, leaf_index, "leaf index"));
+  }
   AFMPB_TRY(A.alloc(&h->d_box_rho, nbox, "box_rho"));
   k_box_rho_leaf<<<div_up(T.nleaf, 128), 128, 0, s>>>(T.nleaf, h->d_leaves, bbeg, bend, h->d_perm, h->d_rho64,
                                                       h->d_box_rho);

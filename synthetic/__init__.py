@@ -147,6 +147,180 @@ def kirkwood_sphere(subdiv: int = 7, radius: float = 20.0, n_charges: int = 64,
                     {"radius": radius, "subdiv": subdiv})
 
 
+# ----------------------------------------------------------------------------------
+# synthetic globular molecule: compact self-avoiding walk + Gaussian isosurface
+# ----------------------------------------------------------------------------------
+def compact_walk(rng: np.random.Generator, n_atoms: int, step: float = 1.5, min_dist: float = 1.0,
+                 r_confine: float | None = None, max_reject: int = 50):
+    """Self-avoiding random walk of n_atoms points: isotropic steps of `step`, a step is
+    rejected if it comes within `min_dist` of an earlier point or leaves the confinement
+    sphere; after `max_reject` rejections in a row the walk backtracks one point.
+    The default confinement radius 38.7 (N/20000)^(1/3) A gives a protein-like density."""
+    if r_confine is None:
+        r_confine = 38.7 * (n_atoms / 20000.0) ** (1.0 / 3.0)
+    cell = min_dist
+    grid: dict = {}
+    pts = [np.zeros(3)]
+
+    def key(p):
+        return (int(np.floor(p[0] / cell)), int(np.floor(p[1] / cell)), int(np.floor(p[2] / cell)))
+
+    grid.setdefault(key(pts[0]), []).append(0)
+    fails = 0
+    while len(pts) < n_atoms:
+        d = rng.standard_normal(3)
+        c = pts[-1] + step * d / np.linalg.norm(d)
+        ok = np.dot(c, c) <= r_confine * r_confine
+        if ok:
+            kx, ky, kz = key(c)
+            for dx in (-1, 0, 1):
+                for dy in (-1, 0, 1):
+                    for dz in (-1, 0, 1):
+                        for j in grid.get((kx + dx, ky + dy, kz + dz), ()):
+                            if np.sum((pts[j] - c) ** 2) < min_dist * min_dist:
+                                ok = False
+                                break
+                        if not ok:
+                            break
+                    if not ok:
+                        break
+                if not ok:
+                    break
+        if ok:
+            grid.setdefault(key(c), []).append(len(pts))
+            pts.append(c)
+            fails = 0
+        else:
+            fails += 1
+            if fails >= max_reject and len(pts) > 1:
+                last = pts.pop()
+                grid[key(last)].remove(len(pts))
+                fails = 0
+    return np.array(pts)
+
+
+def gaussian_density(atoms, radii, origin, h, shape, beta=2.3, cutoff=1e-4):
+    """rho(x) = sum_i exp(beta (1 - |x - x_i|^2 / r_i^2)) on a regular grid."""
+    rho = np.zeros(shape)
+    for a, r in zip(atoms, radii):
+        reach = r * np.sqrt(1.0 - np.log(cutoff) / beta)
+        lo = np.maximum(np.floor((a - reach - origin) / h).astype(int), 0)
+        hi = np.minimum(np.ceil((a + reach - origin) / h).astype(int) + 1, np.array(shape))
+        xs = [origin[d] + h * np.arange(lo[d], hi[d]) - a[d] for d in range(3)]
+        d2 = xs[0][:, None, None] ** 2 + xs[1][None, :, None] ** 2 + xs[2][None, None, :] ** 2
+        rho[lo[0]:hi[0], lo[1]:hi[1], lo[2]:hi[2]] += np.exp(beta * (1.0 - d2 / (r * r)))
+    return rho
+
+
+# Kuhn split of the unit cube into 6 tetrahedra along the (0 -> 7) diagonal; corner c has
+# offset (c & 1, (c >> 1) & 1, (c >> 2) & 1).  The split is the same in every cube, so
+# neighbouring tetrahedra share faces and the extracted surface is closed.
+_KUHN = np.array([[0, 1, 3, 7], [0, 1, 5, 7], [0, 2, 3, 7], [0, 2, 6, 7], [0, 4, 5, 7], [0, 4, 6, 7]])
+
+
+def isosurface(values, origin, h, level=1.0, t_clip=0.01):
+    """Marching tetrahedra on a regular grid: the closed surface {values = level} with
+    triangles counter-clockwise seen from the low side (outward when the inside has
+    values > level).  Vertices lie on grid edges and are shared by edge."""
+    v = np.array(values, dtype=np.float64) - level
+    v[np.abs(v) < 1e-9] = 1e-9
+    nx, ny, nz = v.shape
+    inside = v > 0
+    # cubes with mixed signs
+    corners = np.stack([inside[(c & 1):nx - 1 + (c & 1), ((c >> 1) & 1):ny - 1 + ((c >> 1) & 1),
+                               ((c >> 2) & 1):nz - 1 + ((c >> 2) & 1)] for c in range(8)], axis=-1)
+    mixed = corners.any(-1) & ~corners.all(-1)
+    ci, cj, ck = np.nonzero(mixed)
+    off = np.array([[c & 1, (c >> 1) & 1, (c >> 2) & 1] for c in range(8)])
+    tris, keys_all, tpos = [], [], []
+    for tet in _KUHN:
+        gi = ci[:, None] + off[tet][:, 0][None, :]
+        gj = cj[:, None] + off[tet][:, 1][None, :]
+        gk = ck[:, None] + off[tet][:, 2][None, :]
+        gid = (gi * ny + gj) * nz + gk                        # [m, 4] global grid ids
+        val = v[gi, gj, gk]
+        ins = val > 0
+        cnt = ins.sum(1)
+        pos = origin[None, None, :] + h * np.stack([gi, gj, gk], -1)
+        for m_in in (1, 2, 3):
+            sel = np.nonzero(cnt == m_in)[0]
+            if sel.size == 0:
+                continue
+            order = np.argsort(~ins[sel], axis=1, kind="stable")   # inside vertices first
+            ids = np.take_along_axis(gid[sel], order, 1)
+            vals = np.take_along_axis(val[sel], order, 1)
+            ps = np.take_along_axis(pos[sel], order[:, :, None], 1)
+            if m_in == 1:
+                cuts = [[(0, 1), (0, 2), (0, 3)]]
+            elif m_in == 3:
+                cuts = [[(0, 3), (1, 3), (2, 3)]]
+            else:
+                cuts = [[(0, 2), (0, 3), (1, 3)], [(0, 2), (1, 3), (1, 2)]]
+            cin = ps[:, :m_in].mean(1)
+            cout = ps[:, m_in:].mean(1)
+            for tri_cut in cuts:
+                vp, vk = [], []
+                for a, b in tri_cut:
+                    t = np.clip(vals[:, a] / (vals[:, a] - vals[:, b]), t_clip, 1.0 - t_clip)
+                    vp.append(ps[:, a] + t[:, None] * (ps[:, b] - ps[:, a]))
+                    lo_id = np.minimum(ids[:, a], ids[:, b])
+                    hi_id = np.maximum(ids[:, a], ids[:, b])
+                    vk.append(lo_id * (nx * ny * nz) + hi_id)
+                vp = np.stack(vp, 1)
+                vk = np.stack(vk, 1)
+                nrm = np.cross(vp[:, 1] - vp[:, 0], vp[:, 2] - vp[:, 0])
+                flip = np.einsum("ij,ij->i", nrm, cout - cin) < 0
+                vk[flip] = vk[flip][:, [0, 2, 1]]
+                vp[flip] = vp[flip][:, [0, 2, 1]]
+                keys_all.append(vk)
+                tpos.append(vp)
+    keys = np.concatenate(keys_all)
+    vps = np.concatenate(tpos)
+    uniq, first, inv = np.unique(keys.ravel(), return_index=True, return_inverse=True)
+    xyz = vps.reshape(-1, 3)[first]
+    tri = inv.reshape(-1, 3)
+    return xyz, tri
+
+
+def outer_component(xyz, tri):
+    """Keep the connected surface component that contains the vertex of largest x."""
+    from scipy.sparse import coo_matrix
+    from scipy.sparse.csgraph import connected_components
+    n = xyz.shape[0]
+    e = np.concatenate([tri[:, [0, 1]], tri[:, [1, 2]], tri[:, [2, 0]]])
+    g = coo_matrix((np.ones(len(e)), (e[:, 0], e[:, 1])), shape=(n, n))
+    _, lab = connected_components(g, directed=False)
+    keep = lab == lab[np.argmax(xyz[:, 0])]
+    tri = tri[keep[tri[:, 0]]]
+    used = np.unique(tri.ravel())
+    remap = -np.ones(n, dtype=np.int64)
+    remap[used] = np.arange(used.size)
+    return xyz[used], remap[tri].astype(np.int32)
+
+
+def globule(n_atoms: int = 20000, index: int = 2, grid: float = 0.4, beta: float = 2.3,
+            eps_in: float = 2.0, eps_out: float = 80.0, kappa: float = 0.104,
+            r_confine: float | None = None) -> Molecule:
+    """Synthetic globular protein: compact self-avoiding walk (1.5 A steps, 1.0 A exclusion,
+    confinement radius 38.7 (N/20000)^(1/3) A), atomic radii U(1.2, 2.0) A, partial charges
+    N(0, 0.35) e shifted to zero net charge, molecular surface = outer component of the
+    rho = 1 isosurface of the summed-Gaussian density on a `grid`-A lattice."""
+    rng = rng_for(index)
+    atoms = compact_walk(rng, n_atoms, r_confine=r_confine)
+    radii = rng.uniform(1.2, 2.0, n_atoms)
+    q = rng.normal(0.0, 0.35, n_atoms)
+    q -= q.mean()
+    pad = 2.5 * radii.max() + 2 * grid
+    lo = atoms.min(0) - pad
+    hi = atoms.max(0) + pad
+    shape = tuple(int(np.ceil((hi[d] - lo[d]) / grid)) + 1 for d in range(3))
+    rho = gaussian_density(atoms, radii, lo, grid, shape, beta=beta)
+    xyz, tri = isosurface(rho, lo, grid, level=1.0)
+    xyz, tri = outer_component(xyz, tri)
+    return Molecule("globule", xyz, tri, atoms, q, eps_in, eps_out, kappa,
+                    {"n_atoms": n_atoms, "grid": grid, "beta": beta})
+
+
 def random_unknowns(n_nodes: int, seed: int, dtype=np.float64):
     """A seeded test vector x = [f; h] of length 2N with O(1) entries."""
     rng = np.random.Generator(np.random.PCG64(SEED_BASE + 1000 + seed))
