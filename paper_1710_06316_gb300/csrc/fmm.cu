@@ -426,8 +426,7 @@ __global__ void __launch_bounds__(kL2PThreads, 12) k_l2p(const int32_t *__restri
 // ------------------------------------------------------------------------------------
 // P2P (lists 1 and 3): point (far-rule) sums over t != p, both kernels, both outputs.
 // ------------------------------------------------------------------------------------
-constexpr int kP2PThreads = 128;
-constexpr int kP2PChunk = 704;      // sources staged in shared memory at a time (8 CTAs/SM)
+constexpr int kP2PChunk = 768;      // sources staged in shared memory at a time (8 CTAs/SM)
 constexpr int kP2PBoxes = 64;       // source boxes described in shared memory at a time
 
 // Far-rule sums of one source at one target, without the 1/(4 pi):
@@ -435,44 +434,39 @@ constexpr int kP2PBoxes = 64;       // source boxes described in shared memory a
 //   dn PhiL += -c (n0.d)/r^3 + (g/eps_bar) [(n0.n)/r^3 - 3 (n.d)(n0.d)/r^5]
 //   PhiY += c e/r + g (n.d) e1/r^3,           e = exp(-kr), e1 = e (1 + kr)
 //   dn PhiY += e1 [g (n0.n) - c (n0.d)]/r^3 - 3 g e2 (n.d)(n0.d)/r^5,  e2 = e (1 + kr + (kr)^2/3)
-// with d = x_target - y_source; subexpressions are shared between the two kernels.
+// with d = x_target - y_source.  g enters only through the vector g n, which the staging
+// stores in place of n: y = (source position, c), q = (g n, scaled skip radius).
 __device__ __forceinline__ void p2p_pair(const float4 &xp, const float4 &np, float rsp, const float4 &y,
-                                         const float4 &q, float rst, float inv_ebar, float kappa, float &sL,
-                                         float &dL, float &sY, float &dY) {
+                                         const float4 &q, float inv_ebar, float kappa, float &sL, float &dL,
+                                         float &sY, float &dY) {
   const float dx = xp.x - y.x, dy = xp.y - y.y, dz = xp.z - y.z;
   const float r2 = p2p_r2(dx, dy, dz);
   // Pairs inside the skip radius (t == p among them) contribute nothing here: the near
   // CSR carries their whole near-rule value.
-  const float ri = p2p_evaluates(r2, rsp, rst) ? rsqrtf(r2) : 0.0f;
+  const float ri = p2p_evaluates(r2, rsp, q.w) ? rsqrtf(r2) : 0.0f;
   const float ri2 = ri * ri;
   const float G3 = ri * ri2;
-  const float ndt = fmaf(q.x, dx, fmaf(q.y, dy, q.z * dz));
-  const float npd = fmaf(np.x, dx, fmaf(np.y, dy, np.z * dz));
-  const float nn = fmaf(np.x, q.x, fmaf(np.y, q.y, np.z * q.z));
+  const float gnd = fmaf(q.x, dx, fmaf(q.y, dy, q.z * dz));     // g n.d
+  const float npd = fmaf(np.x, dx, fmaf(np.y, dy, np.z * dz));  // n0.d
+  const float gnn = fmaf(np.x, q.x, fmaf(np.y, q.y, np.z * q.z));  // g n0.n
   const float kr = kappa * (r2 * ri);
   const float ex = __expf(-kr);
   const float e1 = fmaf(ex, kr, ex);
   const float e2 = fmaf(ex * kr, kr * (1.0f / 3.0f), e1);
-  const float c = y.w, g = q.w;
+  const float c = y.w;
   const float cri = c * ri;
-  const float G3n = ndt * G3;
-  const float npG3 = npd * G3;
-  const float nnG3 = nn * G3;
-  const float T = 3.0f * G3n * npd * ri2;
-  const float gL = g * inv_ebar;
-  sL += fmaf(gL, G3n, cri);
-  dL += fmaf(gL, nnG3 - T, -c * npG3);
-  sY = fmaf(ex, cri, fmaf(g * e1, G3n, sY));
-  dY = fmaf(e1, fmaf(g, nnG3, -c * npG3), fmaf(-g * e2, T, dY));
+  const float A = gnd * G3;
+  const float B = gnn * G3;
+  const float cnG3 = c * (npd * G3);
+  const float T = 3.0f * A * npd * ri2;
+  sL += fmaf(inv_ebar, A, cri);
+  dL += fmaf(inv_ebar, B - T, -cnG3);
+  sY = fmaf(ex, cri, fmaf(e1, A, sY));
+  dY = fmaf(e1, B - cnG3, fmaf(-e2, T, dY));
 }
 
-// One CTA per target leaf.  Threads form a (target x source slice) grid with
-// tile = min(targets, 128) targets and floor(128 / tile) slices, so no lane is padded
-// away for leaves whose size is not a power of two.  The leaf's list-1 and list-3 source
-// leaves are described in shared memory 64 at a time (warp prefix scan of their sizes);
-// their nodes are staged 512 at a time, each shifted by its own leaf centre's offset,
-// and every thread sums its target against every slices-th staged source.
-__global__ void __launch_bounds__(kP2PThreads, 8) k_p2p_v3(const int32_t *__restrict__ leaves,
+__global__ void __launch_bounds__(kP2PThreads, 8) k_p2p_v3(const int32_t *__restrict__ order,
+                                                         const int32_t *__restrict__ leaves,
                                                          const int64_t *__restrict__ pptr,
                                                          const int32_t *__restrict__ pidx,
                                                          const int32_t *__restrict__ bbeg,
@@ -485,11 +479,10 @@ __global__ void __launch_bounds__(kP2PThreads, 8) k_p2p_v3(const int32_t *__rest
                                                          float4 *__restrict__ phi) {
   static_assert(kP2PThreads <= kP2PChunk, "the reduction reuses the staging buffer");
   __shared__ float4 sp[kP2PChunk], sn[kP2PChunk];
-  __shared__ float sr[kP2PChunk];
   __shared__ int s_beg[kP2PBoxes], s_pre[kP2PBoxes + 1];
   __shared__ float s_off[kP2PBoxes][3];
   float4 *red = sp;
-  const int leaf = blockIdx.x;
+  const int leaf = order[blockIdx.x];
   const int b = leaves[leaf];
   const dbl4 cb = center[b];
   const int tb = bbeg[b], te = bend[b];
@@ -547,13 +540,13 @@ __global__ void __launch_bounds__(kP2PThreads, 8) k_p2p_v3(const int32_t *__rest
           const float2 fh = xs[sidx];
           sp[e] = make_float4(__fadd_rn(p.x, s_off[lo][0]), __fadd_rn(p.y, s_off[lo][1]),
                               __fadd_rn(p.z, s_off[lo][2]), p.w * fh.y);
-          sn[e] = make_float4(q.x, q.y, q.z, -p.w * fh.x);
-          sr[e] = p2p_skip_radius(skip_scale, q.w);
+          const float g = -p.w * fh.x;
+          sn[e] = make_float4(g * q.x, g * q.y, g * q.z, p2p_skip_radius(skip_scale, q.w));
         }
         __syncthreads();
         if (act) {
 #pragma unroll 4
-          for (int e = si; e < cnt; e += slices) p2p_pair(xp, np, rsp, sp[e], sn[e], sr[e], inv_ebar, kappa, sL, dL, sY, dY);
+          for (int e = si; e < cnt; e += slices) p2p_pair(xp, np, rsp, sp[e], sn[e], inv_ebar, kappa, sL, dL, sY, dY);
         }
       }
     }
@@ -702,7 +695,7 @@ Err enqueue_far(afmpb_t *h, cudaStream_t s, StageTimer *tm) {
 }
 
 Err enqueue_p2p(afmpb_t *h, cudaStream_t s) {
-  k_p2p_v3<<<h->shape.nleaf, kP2PThreads, 0, s>>>(h->d_leaves, h->d_p2p_ptr, h->d_p2p_idx, h->d_box_begin,
+  k_p2p_v3<<<h->shape.nleaf, kP2PThreads, 0, s>>>(h->d_p2p_order, h->d_leaves, h->d_p2p_ptr, h->d_p2p_idx, h->d_box_begin,
                                                   h->d_box_end, h->d_box_center, h->d_pos, h->d_nrm, h->d_xs,
                                                   (float)(1.0 / h->ebar), (float)h->kappa,
                                                   (float)(kP2PSkip * h->opt.near_c), h->d_phi_near);

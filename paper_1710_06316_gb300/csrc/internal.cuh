@@ -24,6 +24,7 @@ constexpr int kKeyBits = 21;        // Morton bits per dimension (63-bit keys)
 constexpr int kNumOffsets = 316;    // M2L offsets: [-3,3]^3 minus [-1,1]^3
 constexpr double kPi = 3.14159265358979323846;
 constexpr double kInv4Pi = 0.07957747154594767;  // 1 / (4 pi)
+constexpr int kP2PThreads = 128;   // threads of a P2P block (one block per target leaf)
 constexpr double kP2PSkip = 0.9;    // P2P leaves out pairs closer than kP2PSkip * c * (rho_p + rho_t)
 
 // Pair geometry of the P2P pass in FP32.  Positions are relative to the target's leaf
@@ -193,6 +194,7 @@ struct afmpb_t {
   int32_t *d_u_idx = nullptr, *d_v_idx = nullptr, *d_w_idx = nullptr, *d_x_idx = nullptr;
   int64_t *d_p2p_ptr = nullptr;    // [nleaf+1] lists 1 + 3 per leaf (leaf order)
   int32_t *d_p2p_idx = nullptr;
+  int32_t *d_p2p_order = nullptr;  // [nleaf] P2P blocks, most work first (leaf order)
   std::vector<int32_t> h_xbox;     // boxes with a non-empty list 4
   int32_t *d_xbox = nullptr;
 

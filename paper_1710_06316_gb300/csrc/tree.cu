@@ -555,9 +555,11 @@ Err build_tree(afmpb_t *h) {
   pidx.reserve(uidx.size() + widx.size());
   int64_t pairs = 0;
   std::vector<int32_t> stack;
+  std::vector<double> cost(T.nleaf);
   for (int i = 0; i < T.nleaf; ++i) {
     int b = leaves[i];
     int64_t nt_b = hend[b] - hbeg[b];
+    const int64_t pairs_before = pairs;
     for (int64_t j = uptr[b]; j < uptr[b + 1]; ++j) { pidx.push_back(uidx[j]); pairs += nt_b * (hend[uidx[j]] - hbeg[uidx[j]]); }
     for (int a = b; a >= 0; a = hparent[a]) {
       if (!x_direct[a]) continue;
@@ -580,9 +582,22 @@ Err build_tree(afmpb_t *h) {
       }
     }
     pptr[i + 1] = (int64_t)pidx.size();
+    // Time of the leaf's P2P block: tiles of up to kP2PThreads targets, each thread
+    // slice walking its share of the sources, plus the staging of every source per tile.
+    const int64_t nsrc = nt_b > 0 ? (pairs - pairs_before) / nt_b : 0;
+    const int64_t tile = std::max<int64_t>(1, std::min<int64_t>(nt_b, kP2PThreads));
+    const int64_t slices = kP2PThreads / tile, ntiles = (nt_b + tile - 1) / tile;
+    cost[i] = (double)ntiles * ((double)((nsrc + slices - 1) / slices) + 0.25 * (double)nsrc + 64.0);
   }
   AFMPB_TRY(to_device(h, &h->d_p2p_ptr, pptr, "p2p_ptr"));
   AFMPB_TRY(to_device(h, &h->d_p2p_idx, pidx, "p2p_idx"));
+  {
+    // Longest blocks first: the block scheduler then ends the launch on short blocks.
+    std::vector<int32_t> order(T.nleaf);
+    for (int i = 0; i < T.nleaf; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) { return cost[x] > cost[y]; });
+    AFMPB_TRY(to_device(h, &h->d_p2p_order, order, "p2p_order"));
+  }
   T.n_u = (int64_t)uidx.size();
   T.n_v = (int64_t)vidx.size();
   T.n_w = (int64_t)widx.size();
