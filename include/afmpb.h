@@ -56,7 +56,9 @@ typedef enum {
     AFMPB_ENOCONV = 5,   /* GMRES did not converge within max_restart; best iterate kept */
     AFMPB_ETIMEOUT = 6,  /* a bounded device wait expired                            */
     AFMPB_EBUSY = 7,     /* operation refused while other work owns the handle       */
-    AFMPB_ESTATE = 8     /* call out of order (e.g. energy before a successful solve) */
+    AFMPB_ESTATE = 8,    /* call out of order (e.g. energy before a successful solve) */
+    AFMPB_EINTERNAL = 9  /* an internal numerical step failed (the eigensolver of the
+                            M2L compression did not converge)                        */
 } afmpb_status;
 
 /* Surface mesh (host memory).  Triangles are counter-clockwise when seen from the
@@ -89,6 +91,10 @@ typedef struct {
                             |x_p - x_t| < c (rho_p + rho_t), rho = patch radius (default 2) */
     void *stream;        /* cudaStream_t to run on, or NULL                              */
     int max_level;       /* deepest octree level (default and maximum 20)                */
+    double m2l_tol;      /* list-2 translations are compressed to the singular vectors of
+                            the stacked translation matrices whose singular values exceed
+                            m2l_tol times the largest (default 1e-5 for 0; a negative
+                            value keeps the full n^3 x n^3 translations)                 */
 } afmpb_options;
 
 /* Solve report. */
@@ -120,6 +126,8 @@ typedef struct {
     double root_half_width;
     double ms_create[6];       /* afmpb_create phases (host clock): geometry, tree and lists,
                                   near field, FMM operators, right-hand side, graph capture */
+    int m2l_rank;              /* compressed translation size r (0: full n^3)            */
+    int m2l_tables;            /* compressed bases: Laplace + one Yukawa per level       */
 } afmpb_info;
 
 /* Per-stage timing of one product (afmpb_profile_product). */

@@ -18,7 +18,7 @@ _lib = None
 
 PART_DIAG, PART_FAR, PART_NEAR, PART_ALL = 1, 2, 4, 7
 STATUS = {0: "OK", 1: "EINVAL", 2: "EMESH", 3: "ENOMEM", 4: "ECUDA", 5: "ENOCONV", 6: "ETIMEOUT",
-          7: "EBUSY", 8: "ESTATE"}
+          7: "EBUSY", 8: "ESTATE", 9: "EINTERNAL"}
 
 
 class AfmpbError(RuntimeError):
@@ -40,7 +40,7 @@ class Charges(C.Structure):
 class Options(C.Structure):
     _fields_ = [("leaf_cap", C.c_int), ("restart", C.c_int), ("max_restart", C.c_int),
                 ("abs_tol", C.c_double), ("precision", C.c_int), ("near_c", C.c_double),
-                ("stream", C.c_void_p), ("max_level", C.c_int)]
+                ("stream", C.c_void_p), ("max_level", C.c_int), ("m2l_tol", C.c_double)]
 
 
 class SolveInfo(C.Structure):
@@ -57,7 +57,8 @@ class Info(C.Structure):
                 ("n_list_w", C.c_int64), ("n_list_x", C.c_int64), ("n_p2p_pairs", C.c_int64),
                 ("n_m2l_pairs", C.c_int64), ("order", C.c_int), ("precision", C.c_int),
                 ("device_bytes", C.c_int64), ("root_center", C.c_double * 3),
-                ("root_half_width", C.c_double), ("ms_create", C.c_double * 6)]
+                ("root_half_width", C.c_double), ("ms_create", C.c_double * 6),
+                ("m2l_rank", C.c_int), ("m2l_tables", C.c_int)]
 
 
 class Profile(C.Structure):
@@ -167,7 +168,7 @@ class Handle:
 
     def __init__(self, xyz, tri, atoms=None, q=None, eps_in=1.0, eps_out=80.0, kappa=0.0,
                  order=6, tol=1e-6, leaf_cap=0, restart=0, max_restart=0, abs_tol=0.0,
-                 precision=0, near_c=0.0, stream=None, max_level=0, normals=None):
+                 precision=0, near_c=0.0, stream=None, max_level=0, normals=None, m2l_tol=0.0):
         self._lib = load()
         self._xyz = _np(xyz, np.float64)
         self._tri = _np(tri, np.int32)
@@ -184,7 +185,7 @@ class Handle:
         if st is not None and not isinstance(st, int):
             st = int(getattr(st, "cuda_stream", st))
         opt = Options(int(leaf_cap), int(restart), int(max_restart), float(abs_tol), int(precision),
-                      float(near_c), st, int(max_level))
+                      float(near_c), st, int(max_level), float(m2l_tol))
         h = C.c_void_p()
         rc = self._lib.afmpb_create(C.byref(mesh), None if ch is None else C.byref(ch),
                                     float(eps_in), float(eps_out), float(kappa), int(order),

@@ -179,6 +179,7 @@ afmpb_status afmpb_create(const afmpb_mesh *mesh, const afmpb_charges *charges, 
   if (h->opt.max_restart == 0 && !(options && options->max_restart == 0 && options->restart != 0)) h->opt.max_restart = 5;
   if (h->opt.near_c == 0) h->opt.near_c = 2.0;
   if (h->opt.max_level == 0) h->opt.max_level = kMaxLevel;
+  if (h->opt.m2l_tol == 0) h->opt.m2l_tol = 1e-5;
   e = create_impl(h, mesh, charges);
   if (!e.ok()) {
     g_err = e.msg;
@@ -391,6 +392,8 @@ afmpb_status afmpb_get_info(const afmpb_t *h, afmpb_info *info) {
   for (int d = 0; d < 3; ++d) info->root_center[d] = T.c0[d];
   info->root_half_width = T.w0;
   for (int i = 0; i < 6; ++i) info->ms_create[i] = h->ms_create[i];
+  info->m2l_rank = h->m2l_rank;
+  info->m2l_tables = h->m2l_ntables;
   return AFMPB_OK;
 }
 

@@ -638,7 +638,11 @@ Err launch_far(afmpb_t *h, cudaStream_t s, StageTimer *tm) {
     AFMPB_TRY(check_launch("k_m2m"));
   }
   if (tm) tm->mark("m2m", std::max(0, T.nlevel - 3));
-  if (!h->m2l_groups.empty()) {
+  int m2l_launches = h->m2l_groups.empty() ? 0 : 1;
+  if (!h->m2l_groups.empty() && h->m2l_rank > 0) {
+    AFMPB_TRY(enqueue_m2l_svd(h, s));
+    m2l_launches = 3;
+  } else if (!h->m2l_groups.empty()) {
     if (h->opt.precision == 1) {
       AFMPB_TRY(enqueue_m2l_tc(h, s));
     } else {
@@ -650,7 +654,7 @@ Err launch_far(afmpb_t *h, cudaStream_t s, StageTimer *tm) {
       AFMPB_TRY(check_launch("k_m2l"));
     }
   }
-  if (tm) tm->mark("m2l", h->m2l_groups.empty() ? 0 : 1);
+  if (tm) tm->mark("m2l", m2l_launches);
   if (!h->h_xbox.empty()) {
     k_p2l<N><<<(unsigned)h->h_xbox.size(), 256, 0, s>>>(h->d_xbox, h->d_x_ptr, h->d_x_idx, h->d_box_begin,
                                                         h->d_box_end, h->d_box_center, h->d_pos, h->d_nrm, h->d_xs,
@@ -760,6 +764,16 @@ Err build_fmm(afmpb_t *h) {
   h->m2l_yuk_levels = 0;
   while (h->m2l_yuk_levels < maxlev && h->kappa * 2.0 * std::ldexp(T.w0, -h->m2l_yuk_levels) > 40.0)
     ++h->m2l_yuk_levels;
+  bool compressed = false;
+  AFMPB_TRY(build_m2l_svd(h, &compressed));
+  if (compressed) {
+    A.release(d_offs);
+    AFMPB_TRY(A.alloc(&h->d_M, (size_t)T.nbox * 2 * N3, "M"));
+    AFMPB_TRY(A.alloc(&h->d_L, (size_t)T.nbox * 2 * N3, "L"));
+    AFMPB_CUDA(cudaMemsetAsync(h->d_M, 0, sizeof(float) * (size_t)T.nbox * 2 * N3, s));
+    if (h->opt.precision == 1) AFMPB_TRY(build_m2l_tc(h));
+    return Err{};
+  }
   const size_t N6 = (size_t)N3 * N3;
   AFMPB_TRY(A.alloc(&h->d_K_lap, kNumOffsets * N6, "K laplace"));
   AFMPB_TRY(A.alloc(&h->d_K_yuk, (size_t)std::max(maxlev, 1) * kNumOffsets * N6, "K yukawa"));

@@ -47,6 +47,41 @@ __device__ __forceinline__ bool p2p_evaluates(float r2, float sp, float st) {
   return r2 > __fmul_rn(R, R);
 }
 
+// Global -> shared copies with kCopyILP independent loads in flight per thread (a plain
+// element loop issues each load only after the previous element's store).
+constexpr int kCopyILP = 8;
+__device__ __forceinline__ void copy_g2s(float *dst, const float *__restrict__ src, int n) {
+  for (int e0 = threadIdx.x; e0 < n; e0 += blockDim.x * kCopyILP) {
+    float v[kCopyILP];
+#pragma unroll
+    for (int u = 0; u < kCopyILP; ++u) {
+      const int e = e0 + u * (int)blockDim.x;
+      v[u] = e < n ? __ldg(src + e) : 0.0f;
+    }
+#pragma unroll
+    for (int u = 0; u < kCopyILP; ++u) {
+      const int e = e0 + u * (int)blockDim.x;
+      if (e < n) dst[e] = v[u];
+    }
+  }
+}
+// Same for 16-byte vectors (both pointers 16-byte aligned, n4 vectors).
+__device__ __forceinline__ void copy_g2s4(float4 *dst, const float4 *__restrict__ src, int n4) {
+  for (int e0 = threadIdx.x; e0 < n4; e0 += blockDim.x * kCopyILP) {
+    float4 v[kCopyILP];
+#pragma unroll
+    for (int u = 0; u < kCopyILP; ++u) {
+      const int e = e0 + u * (int)blockDim.x;
+      v[u] = e < n4 ? __ldg(src + e) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < kCopyILP; ++u) {
+      const int e = e0 + u * (int)blockDim.x;
+      if (e < n4) dst[e] = v[u];
+    }
+  }
+}
+
 // Error carried up the host call chain; every internal function returns one.
 struct Err {
   afmpb_status code = AFMPB_OK;
@@ -219,6 +254,19 @@ struct afmpb_t {
   int2 *d_m2l_pairs = nullptr;     // (target, source) boxes grouped by (level, offset)
   int64_t n_m2l_pairs = 0;
   int m2l_yuk_levels = 0;          // Yukawa M2L skipped on levels below this one
+  // compressed M2L (m2l_rank > 0): bases Q per table (0 = Laplace on the unit box,
+  // 1.. = Yukawa per level), translations C_o = Q^T K_o Q, compressed expansions
+  int m2l_rank = 0;                // r, a multiple of 16; 0 = full n^3 translations
+  int m2l_ntables = 0;
+  std::vector<int> h_level_table;  // level -> Yukawa table
+  int *d_level_table = nullptr;
+  float *d_Q = nullptr;            // [table][ncoef][r]
+  float *d_QT = nullptr;           // [table][r][ncoef]
+  float *d_C = nullptr;            // [table][316][r][r]
+  float *d_Mc = nullptr;           // [nbox][2][r] compressed multipole vectors
+  float *d_Lc = nullptr;           // [nbox][2][r] compressed local vectors
+  int4 *d_m2l_chunks = nullptr;    // (first box, count, level) of the compress/expand CTAs
+  int m2l_nchunks = 0;
   // tensor-core M2L (precision 1)
   int tc_items = 0;
   afmpb::TCItem *d_tc_items = nullptr;  // work items: (group, first pair, pair count)
@@ -264,6 +312,9 @@ Err enqueue_p2p(afmpb_t *h, cudaStream_t s);          // P2P into d_phi_near
 Err enqueue_combine(afmpb_t *h, cudaStream_t s, int parts);
 Err enqueue_m2l_tc(afmpb_t *h, cudaStream_t s);       // tensor-core M2L (precision 1)
 Err build_m2l_tc(afmpb_t *h);
+// m2l_svd.cu: compressed translations; *compressed = false leaves the full ones in use
+Err build_m2l_svd(afmpb_t *h, bool *compressed);
+Err enqueue_m2l_svd(afmpb_t *h, cudaStream_t s);      // compress, translate, expand
 Err read_tc_error(int *flag);                          // 1 when a tensor-core wait expired
 // solve.cu
 Err build_rhs(afmpb_t *h);

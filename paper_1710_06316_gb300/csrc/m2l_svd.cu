@@ -1,0 +1,540 @@
+// m2l_svd.cu -- compressed list-2 translations (M2L).
+//
+// The 316 translation matrices K_o of one kernel and level (n^3 x n^3, Chebyshev points
+// of a target box against those of the box at offset o) share one numerically low-rank
+// row space and one column space: with Q the leading eigenvectors of the Gram matrix
+// sum_o K_o K_o^T, C_o = Q^T K_o Q (r x r) stands for K_o, and
+//     L += K_o M   becomes   L += Q (C_o (Q^T M)).
+// Because the offset set is symmetric and the kernels are radial, K_{-o} = K_o^T, so the
+// same Q spans the column space (sum_o K_o^T K_o is the same Gram matrix).
+// The product compresses every multipole vector once (Mc = Q^T M), translates r-vectors,
+// and expands every local vector once (L += Q Lc): the translation work falls by
+// (n^3 / r)^2.  r is the number of singular values of the stacked operators above
+// m2l_tol times the largest, rounded up to a multiple of 16 and shared by all tables.
+//
+// Setup (FP64 on the GPU, eigenproblems on the host): per table, the FP64 matrices K_o,
+// the Gram matrix, its eigen-decomposition, then C_o = Q^T (K_o Q).
+#include <algorithm>
+#include <cmath>
+#include <thread>
+
+#include "internal.cuh"
+#include "symeig.h"
+
+namespace afmpb {
+
+namespace {
+
+constexpr int kGramTile = 32;       // Gram matrix tile (32 x 32 per CTA)
+constexpr int kGramOffsets = 20;    // offsets summed per Gram CTA
+constexpr int kRowsPerCta = 8;      // rows of T = K_o Q (and of C) per CTA
+constexpr int kChunkBoxes = 32;     // boxes per compress / expand CTA (a multiple of 4)
+constexpr int kMaxN3 = kMaxOrder * kMaxOrder * kMaxOrder;
+constexpr int kMaxRank = 192;       // largest compressed size (M2L staging in shared memory)
+
+struct NodesD {
+  double x[kMaxOrder];
+};
+
+// K_o(i, k): kernel between point i of the unit target box and point k of the source box
+// at offset o (centres 2 o apart).  kw < 0: Laplace 1/(4 pi r); else Yukawa
+// exp(-kw r)/(4 pi r) times invw (the box half width w enters as kw = kappa w).
+__device__ __forceinline__ double m2l_entry(const NodesD &nd, int N, int3 o, int i, int k, double kw, double invw) {
+  const double tx = nd.x[i / (N * N)], ty = nd.x[(i / N) % N], tz = nd.x[i % N];
+  const double sx = 2.0 * o.x + nd.x[k / (N * N)], sy = 2.0 * o.y + nd.x[(k / N) % N],
+               sz = 2.0 * o.z + nd.x[k % N];
+  const double r = sqrt((tx - sx) * (tx - sx) + (ty - sy) * (ty - sy) + (tz - sz) * (tz - sz));
+  double v = kInv4Pi / r;
+  if (kw >= 0.0) v = exp(-kw * r) * v * invw;
+  return v;
+}
+
+__global__ void k_table_f64(int N, const int3 *__restrict__ offs, NodesD nd, double kw, double invw,
+                            double *__restrict__ K) {
+  const int N3 = N * N * N;
+  const int64_t tot = (int64_t)kNumOffsets * N3 * N3;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int o = (int)(e / ((int64_t)N3 * N3));
+    const int rem = (int)(e % ((int64_t)N3 * N3));
+    K[e] = m2l_entry(nd, N, offs[o], rem / N3, rem % N3, kw, invw);
+  }
+}
+
+// gram[i][j] += sum over a range of offsets o and all k of K_o(i, k) K_o(j, k)
+__global__ void __launch_bounds__(256) k_gram(int N3, const double *__restrict__ K, double *__restrict__ gram) {
+  __shared__ double Ki[kGramTile][kGramTile + 1], Kj[kGramTile][kGramTile + 1];
+  const int i0 = blockIdx.x * kGramTile, j0 = blockIdx.y * kGramTile;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  double acc[2][2] = {{0, 0}, {0, 0}};
+  const int o0 = blockIdx.z * kGramOffsets, o1 = min(kNumOffsets, o0 + kGramOffsets);
+  for (int o = o0; o < o1; ++o) {
+    const double *Ko = K + (size_t)o * N3 * N3;
+    for (int k0 = 0; k0 < N3; k0 += kGramTile) {
+      __syncthreads();
+      for (int e = threadIdx.x; e < kGramTile * kGramTile; e += blockDim.x) {
+        const int r = e / kGramTile, c = e % kGramTile, k = k0 + c;
+        Ki[r][c] = (i0 + r < N3 && k < N3) ? Ko[(size_t)(i0 + r) * N3 + k] : 0.0;
+        Kj[r][c] = (j0 + r < N3 && k < N3) ? Ko[(size_t)(j0 + r) * N3 + k] : 0.0;
+      }
+      __syncthreads();
+#pragma unroll 8
+      for (int c = 0; c < kGramTile; ++c) {
+        const double a0 = Ki[ty][c], a1 = Ki[ty + 16][c], b0 = Kj[tx][c], b1 = Kj[tx + 16][c];
+        acc[0][0] = fma(a0, b0, acc[0][0]);
+        acc[0][1] = fma(a0, b1, acc[0][1]);
+        acc[1][0] = fma(a1, b0, acc[1][0]);
+        acc[1][1] = fma(a1, b1, acc[1][1]);
+      }
+    }
+  }
+  for (int a = 0; a < 2; ++a)
+    for (int b = 0; b < 2; ++b) {
+      const int i = i0 + ty + 16 * a, j = j0 + tx + 16 * b;
+      if (i < N3 && j < N3) atomicAdd(&gram[(size_t)i * N3 + j], acc[a][b]);
+    }
+}
+
+// T[o][i][b] = sum_k K_o(i, k) Q(k, b)        (Q: [N3][R], FP64)
+__global__ void __launch_bounds__(128) k_kq(int N3, int R, const double *__restrict__ K, const double *__restrict__ Q,
+                                            double *__restrict__ T) {
+  __shared__ double Ks[kRowsPerCta][kMaxN3];
+  const int o = blockIdx.x, i0 = blockIdx.y * kRowsPerCta;
+  const int rows = min(kRowsPerCta, N3 - i0);
+  for (int e = threadIdx.x; e < kRowsPerCta * N3; e += blockDim.x) {
+    const int r = e / N3, k = e % N3;
+    Ks[r][k] = r < rows ? K[((size_t)o * N3 + i0 + r) * N3 + k] : 0.0;
+  }
+  __syncthreads();
+  for (int b = threadIdx.x; b < R; b += blockDim.x) {
+    double acc[kRowsPerCta] = {};
+    for (int k = 0; k < N3; ++k) {
+      const double q = Q[(size_t)k * R + b];
+#pragma unroll
+      for (int r = 0; r < kRowsPerCta; ++r) acc[r] = fma(Ks[r][k], q, acc[r]);
+    }
+    for (int r = 0; r < rows; ++r) T[((size_t)o * N3 + i0 + r) * R + b] = acc[r];
+  }
+}
+
+// C[o][a][b] = sum_i Q(i, a) T[o][i][b], stored FP32
+__global__ void __launch_bounds__(128) k_qtt(int N3, int R, const double *__restrict__ Q, const double *__restrict__ T,
+                                             float *__restrict__ C) {
+  __shared__ double Qs[kRowsPerCta][kMaxN3];
+  const int o = blockIdx.x, a0 = blockIdx.y * kRowsPerCta;
+  const int rows = min(kRowsPerCta, R - a0);
+  for (int e = threadIdx.x; e < kRowsPerCta * N3; e += blockDim.x) {
+    const int r = e / N3, i = e % N3;
+    Qs[r][i] = r < rows ? Q[(size_t)i * R + a0 + r] : 0.0;
+  }
+  __syncthreads();
+  for (int b = threadIdx.x; b < R; b += blockDim.x) {
+    double acc[kRowsPerCta] = {};
+    for (int i = 0; i < N3; ++i) {
+      const double t = T[((size_t)o * N3 + i) * R + b];
+#pragma unroll
+      for (int r = 0; r < kRowsPerCta; ++r) acc[r] = fma(Qs[r][i], t, acc[r]);
+    }
+    for (int r = 0; r < rows; ++r) C[((size_t)o * R + a0 + r) * R + b] = (float)acc[r];
+  }
+}
+
+// Asynchronous global -> shared copies (cp.async); src_bytes = 0 writes zeros.
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void cp_async4(float *dst, const float *src, bool valid) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(valid ? 4 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async16(float *dst, const float *src, bool valid) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(valid ? 16 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+// Per-box basis change for one chunk of up to kChunkBoxes boxes of one level:
+//     Y[b][kt][c] (+)= sum_k A_table[k][c] X[b][kt][k]
+// compress: A = Q (K = n^3, ncol = r), X = M, Y = Mc;  expand: A = Q^T (K = r,
+// ncol = n^3), X = Lc, Y = L (accumulated).  The chunk's X vectors (X[k][box]) and slabs
+// of kSlabRows rows of A reach shared memory by cp.async in a kStages-deep pipeline, so
+// the copy of slab s + 2 overlaps the products of slab s.  A thread owns 4 boxes x 4
+// columns per tile (two 16-byte shared loads per 16 FMAs) and up to TILES tiles; ncol is
+// a multiple of 4.
+constexpr int kSlabRows = 32;
+constexpr int kStages = 3;
+template <int TILES, bool ACCUM>
+__global__ void __launch_bounds__(256) k_box_basis(int K, int ncol, const int4 *__restrict__ chunks,
+                                                   const int *__restrict__ level_table, int yuk_min,
+                                                   const float *__restrict__ A, const float *__restrict__ X,
+                                                   float *__restrict__ Y) {
+  extern __shared__ __align__(16) float sm[];
+  float *Xs = sm;                                      // [K][kChunkBoxes]
+  float *As = sm + (size_t)K * kChunkBoxes;            // [kStages][kSlabRows][ncol]
+  const int4 ch = chunks[blockIdx.x];                  // first box, count, level
+  const int kt = blockIdx.y;
+  if (kt == 1 && ch.z < yuk_min) return;               // no Yukawa translations on this level
+  const int table = kt == 0 ? 0 : level_table[ch.z];
+  const float *At = A + (size_t)table * K * ncol;
+  const int slab_elems = kSlabRows * ncol;
+  const int nslab = (K + kSlabRows - 1) / kSlabRows;
+  // X: the box index runs fastest so that the shared stores hit distinct banks
+  for (int e = threadIdx.x; e < K * kChunkBoxes; e += blockDim.x) {
+    const int j = e % kChunkBoxes, k = e / kChunkBoxes;
+    const bool v = j < ch.y;
+    cp_async4(Xs + e, v ? X + ((size_t)(ch.x + j) * 2 + kt) * K + k : X, v);
+  }
+  auto issue_slab = [&](int sl) {
+    if (sl < nslab) {
+      float *dst = As + (size_t)(sl % kStages) * slab_elems;
+      const int k0 = sl * kSlabRows;
+      const int valid = min(kSlabRows, K - k0) * ncol;     // floats present in A
+      for (int e = threadIdx.x * 4; e < slab_elems; e += blockDim.x * 4) {
+        const bool v = e < valid;
+        cp_async16(dst + e, v ? At + (size_t)k0 * ncol + e : At, v);
+      }
+    }
+    cp_async_commit();                                 // empty groups keep the count
+  };
+  issue_slab(0);                                       // commits X together with slab 0
+  issue_slab(1);
+  const int ncol4 = ncol / 4;
+  const int ntiles = (kChunkBoxes / 4) * ncol4;
+  float acc[TILES][4][4] = {};
+  for (int sl = 0; sl < nslab; ++sl) {
+    cp_async_wait_1();                                 // X and slab sl have landed
+    __syncthreads();
+    issue_slab(sl + 2);                                // its buffer held slab sl - 1
+    const float *as = As + (size_t)(sl % kStages) * slab_elems;
+    const int k0 = sl * kSlabRows, rows = min(kSlabRows, K - k0);
+#pragma unroll
+    for (int t = 0; t < TILES; ++t) {
+      const int tile = threadIdx.x + t * blockDim.x;
+      if (tile >= ntiles) continue;
+      const int c0 = (tile % ncol4) * 4, b0 = (tile / ncol4) * 4;
+#pragma unroll 4
+      for (int kk = 0; kk < rows; ++kk) {
+        const float4 a = *reinterpret_cast<const float4 *>(as + (size_t)kk * ncol + c0);
+        const float4 x = *reinterpret_cast<const float4 *>(Xs + (size_t)(k0 + kk) * kChunkBoxes + b0);
+        const float av[4] = {a.x, a.y, a.z, a.w}, xv[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[t][i][j] = fmaf(xv[i], av[j], acc[t][i][j]);
+      }
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < TILES; ++t) {
+    const int tile = threadIdx.x + t * blockDim.x;
+    if (tile >= ntiles) continue;
+    const int c4 = tile % ncol4, b0 = (tile / ncol4) * 4;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      if (b0 + i >= ch.y) continue;
+      float4 *y = reinterpret_cast<float4 *>(Y + ((size_t)(ch.x + b0 + i) * 2 + kt) * ncol) + c4;
+      float4 v = make_float4(acc[t][i][0], acc[t][i][1], acc[t][i][2], acc[t][i][3]);
+      if (ACCUM) {
+        const float4 o = *y;
+        v.x += o.x; v.y += o.y; v.z += o.z; v.w += o.w;
+      }
+      *y = v;
+    }
+  }
+}
+
+int basis_tiles(int ncol) { return ((kChunkBoxes / 4) * (ncol / 4) + 255) / 256; }
+size_t basis_smem(int K, int ncol) {
+  return sizeof(float) * ((size_t)K * kChunkBoxes + (size_t)kStages * kSlabRows * ncol);
+}
+
+template <bool ACCUM>
+Err launch_box_basis(cudaStream_t s, dim3 grid, int K, int ncol, const int4 *chunks, const int *level_table,
+                     int yuk_min, const float *A, const float *X, float *Y) {
+  const size_t smem = basis_smem(K, ncol);
+  switch (basis_tiles(ncol)) {
+    case 1: k_box_basis<1, ACCUM><<<grid, 256, smem, s>>>(K, ncol, chunks, level_table, yuk_min, A, X, Y); break;
+    case 2: k_box_basis<2, ACCUM><<<grid, 256, smem, s>>>(K, ncol, chunks, level_table, yuk_min, A, X, Y); break;
+    case 3: k_box_basis<3, ACCUM><<<grid, 256, smem, s>>>(K, ncol, chunks, level_table, yuk_min, A, X, Y); break;
+    default: k_box_basis<4, ACCUM><<<grid, 256, smem, s>>>(K, ncol, chunks, level_table, yuk_min, A, X, Y); break;
+  }
+  return check_launch(ACCUM ? "k_box_basis expand" : "k_box_basis compress");
+}
+
+template <bool ACCUM>
+Err set_box_basis_smem(int K, int ncol) {
+  const int smem = (int)basis_smem(K, ncol);
+  switch (basis_tiles(ncol)) {
+    case 1: AFMPB_CUDA(cudaFuncSetAttribute(k_box_basis<1, ACCUM>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)); break;
+    case 2: AFMPB_CUDA(cudaFuncSetAttribute(k_box_basis<2, ACCUM>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)); break;
+    case 3: AFMPB_CUDA(cudaFuncSetAttribute(k_box_basis<3, ACCUM>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)); break;
+    default: AFMPB_CUDA(cudaFuncSetAttribute(k_box_basis<4, ACCUM>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)); break;
+  }
+  return Err{};
+}
+
+// Compressed M2L on the CUDA cores: one CTA per ((level, offset) group, kernel); the
+// R x R operator stays in shared memory while the group's pairs stream through in chunks
+// of 32 (a warp owns 4 pairs, a lane RPL rows).  Results are added with atomics.
+template <int RPL>
+__global__ void __launch_bounds__(256) k_m2l_c(int R, const M2LGroup *__restrict__ groups,
+                                               const int2 *__restrict__ pairs, const float *__restrict__ C,
+                                               const int *__restrict__ level_table, const dbl4 *__restrict__ center,
+                                               int yuk_min, const float *__restrict__ Mc, float *__restrict__ Lc) {
+  extern __shared__ float smem[];
+  const int LD = R + 1;
+  float *Cs = smem;                 // [R][LD]
+  float *Ms = smem + R * LD;        // [R][32]
+  const M2LGroup g = groups[blockIdx.x];
+  const int kt = blockIdx.y;
+  if (kt == 1 && g.level < yuk_min) return;
+  const int table = kt == 0 ? 0 : level_table[g.level];
+  const float *Cg = C + ((size_t)table * kNumOffsets + g.offset) * R * R;
+  for (int e0 = threadIdx.x; e0 < R * R; e0 += blockDim.x * kCopyILP) {
+    float v[kCopyILP];
+#pragma unroll
+    for (int u = 0; u < kCopyILP; ++u) {
+      const int e = e0 + u * (int)blockDim.x;
+      v[u] = e < R * R ? __ldg(Cg + e) : 0.0f;
+    }
+#pragma unroll
+    for (int u = 0; u < kCopyILP; ++u) {
+      const int e = e0 + u * (int)blockDim.x;
+      if (e < R * R) Cs[(e / R) * LD + e % R] = v[u];
+    }
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const float scale = kt == 0 ? (float)(1.0 / center[pairs[g.start].x].w) : 1.0f;
+  __shared__ int s_src[32], s_tgt[32];
+  for (int pc = 0; pc < g.count; pc += 32) {
+    const int cnt = min(32, g.count - pc);
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      const int2 pr = threadIdx.x < cnt ? pairs[g.start + pc + threadIdx.x] : make_int2(0, 0);
+      s_tgt[threadIdx.x] = pr.x;
+      s_src[threadIdx.x] = pr.y;
+    }
+    __syncthreads();
+    for (int e0 = threadIdx.x; e0 < R * 32; e0 += blockDim.x * kCopyILP) {
+      float v[kCopyILP];
+#pragma unroll
+      for (int u = 0; u < kCopyILP; ++u) {
+        const int e = e0 + u * (int)blockDim.x, p = e / R, k = e % R;
+        v[u] = (e < R * 32 && p < cnt) ? __ldg(Mc + ((size_t)s_src[p] * 2 + kt) * R + k) : 0.0f;
+      }
+#pragma unroll
+      for (int u = 0; u < kCopyILP; ++u) {
+        const int e = e0 + u * (int)blockDim.x, p = e / R, k = e % R;
+        if (e < R * 32) Ms[k * 32 + p] = v[u];
+      }
+    }
+    __syncthreads();
+    float acc[RPL][4] = {};
+#pragma unroll 2
+    for (int k = 0; k < R; ++k) {
+      const float4 mv = *reinterpret_cast<const float4 *>(Ms + k * 32 + warp * 4);
+#pragma unroll
+      for (int r = 0; r < RPL; ++r) {
+        const int row = lane + 32 * r;
+        const float a = row < R ? Cs[row * LD + k] : 0.0f;
+        acc[r][0] = fmaf(a, mv.x, acc[r][0]);
+        acc[r][1] = fmaf(a, mv.y, acc[r][1]);
+        acc[r][2] = fmaf(a, mv.z, acc[r][2]);
+        acc[r][3] = fmaf(a, mv.w, acc[r][3]);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int p = warp * 4 + q;
+      if (p >= cnt) continue;
+      float *dst = Lc + ((size_t)s_tgt[p] * 2 + kt) * R;
+#pragma unroll
+      for (int r = 0; r < RPL; ++r) {
+        const int row = lane + 32 * r;
+        if (row < R) atomicAdd(dst + row, acc[r][q] * scale);
+      }
+    }
+  }
+}
+
+template <int RPL>
+Err launch_m2l_c(afmpb_t *h, cudaStream_t s) {
+  const int R = h->m2l_rank;
+  const size_t smem = sizeof(float) * ((size_t)R * (R + 1) + (size_t)R * 32);
+  dim3 grid((unsigned)h->m2l_groups.size(), 2);
+  k_m2l_c<RPL><<<grid, 256, smem, s>>>(R, h->d_m2l_groups, h->d_m2l_pairs, h->d_C, h->d_level_table,
+                                       h->d_box_center, h->m2l_yuk_levels, h->d_Mc, h->d_Lc);
+  return check_launch("k_m2l_c");
+}
+
+template <int RPL>
+Err set_m2l_c_smem(int R) {
+  const size_t smem = sizeof(float) * ((size_t)R * (R + 1) + (size_t)R * 32);
+  AFMPB_CUDA(cudaFuncSetAttribute(k_m2l_c<RPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  return Err{};
+}
+
+}  // namespace
+
+Err build_m2l_svd(afmpb_t *h, bool *compressed) {
+  *compressed = false;
+  const double tol = h->opt.m2l_tol;
+  const int n = h->order, N3 = n * n * n;
+  // the basis kernels move 16-byte vectors of n^3 weights: orders 2, 4, 6, 8
+  if (tol < 0.0 || h->m2l_groups.empty() || N3 % 4 != 0) return Err{};
+  cudaStream_t s = h->stream;
+  auto &A = h->arena;
+  const auto &T = h->shape;
+  // tables: 0 = Laplace on the unit box, then Yukawa per level that translates
+  int maxlev = 0;
+  for (auto &g : h->m2l_groups) maxlev = std::max(maxlev, g.level + 1);
+  std::vector<double> tab_kw(1, -1.0), tab_invw(1, 1.0);
+  std::vector<int> level_table(std::max(maxlev, 1), 0);
+  for (int l = std::max(2, h->m2l_yuk_levels); l < maxlev; ++l) {
+    const double w = std::ldexp(T.w0, -l);
+    level_table[l] = (int)tab_kw.size();
+    tab_kw.push_back(h->kappa * w);
+    tab_invw.push_back(1.0 / w);
+  }
+  const int ntab = (int)tab_kw.size();
+  NodesD nd{};
+  for (int m = 0; m < n; ++m) nd.x[m] = (double)(float)std::cos((2.0 * m + 1.0) * kPi / (2.0 * n));
+  std::vector<int3> offs;
+  for (int ox = -3; ox <= 3; ++ox)
+    for (int oy = -3; oy <= 3; ++oy)
+      for (int oz = -3; oz <= 3; ++oz)
+        if (std::abs(ox) > 1 || std::abs(oy) > 1 || std::abs(oz) > 1) offs.push_back(make_int3(ox, oy, oz));
+  int3 *d_offs = nullptr;
+  double *d_K = nullptr, *d_gram = nullptr;
+  AFMPB_TRY(A.alloc(&d_offs, offs.size(), "svd offsets"));
+  AFMPB_TRY(A.alloc(&d_K, (size_t)kNumOffsets * N3 * N3, "svd K64"));
+  AFMPB_TRY(A.alloc(&d_gram, (size_t)N3 * N3, "svd gram"));
+  AFMPB_CUDA(cudaMemcpyAsync(d_offs, offs.data(), sizeof(int3) * offs.size(), cudaMemcpyHostToDevice, s));
+  // Gram matrices and their eigen-decompositions
+  std::vector<std::vector<double>> gram(ntab, std::vector<double>((size_t)N3 * N3));
+  const dim3 ggrid((N3 + kGramTile - 1) / kGramTile, (N3 + kGramTile - 1) / kGramTile,
+                   (kNumOffsets + kGramOffsets - 1) / kGramOffsets);
+  for (int t = 0; t < ntab; ++t) {
+    k_table_f64<<<1024, 256, 0, s>>>(n, d_offs, nd, tab_kw[t], tab_invw[t], d_K);
+    AFMPB_TRY(check_launch("k_table_f64"));
+    AFMPB_CUDA(cudaMemsetAsync(d_gram, 0, sizeof(double) * N3 * N3, s));
+    k_gram<<<ggrid, 256, 0, s>>>(N3, d_K, d_gram);
+    AFMPB_TRY(check_launch("k_gram"));
+    AFMPB_CUDA(cudaMemcpyAsync(gram[t].data(), d_gram, sizeof(double) * N3 * N3, cudaMemcpyDeviceToHost, s));
+  }
+  AFMPB_CUDA(cudaStreamSynchronize(s));
+  std::vector<std::vector<double>> lam(ntab, std::vector<double>(N3)), zt(ntab, std::vector<double>((size_t)N3 * N3));
+  std::vector<int> rc(ntab, 0);
+  {
+    std::vector<std::thread> pool;
+    for (int t = 0; t < ntab; ++t)
+      pool.emplace_back([&, t] { rc[t] = sym_eig_desc(N3, gram[t].data(), lam[t].data(), zt[t].data()); });
+    for (auto &th : pool) th.join();
+  }
+  int rmax = 1;
+  for (int t = 0; t < ntab; ++t) {
+    if (rc[t] != 0) return make_err(AFMPB_EINTERNAL, "M2L compression: eigensolver did not converge");
+    // singular values of the stacked operators are the square roots of the eigenvalues
+    int r = 0;
+    while (r < N3 && lam[t][r] > 0.0 && std::sqrt(lam[t][r] / lam[t][0]) > tol) ++r;
+    rmax = std::max(rmax, r);
+  }
+  const int R = (rmax + 15) / 16 * 16;
+  if (R > kMaxRank || R >= N3) {       // no gain: keep the full translations
+    A.release(d_gram);
+    A.release(d_K);
+    A.release(d_offs);
+    return Err{};
+  }
+  h->m2l_rank = R;
+  h->m2l_ntables = ntab;
+  h->h_level_table = level_table;
+  AFMPB_TRY(A.alloc(&h->d_level_table, level_table.size(), "svd level table"));
+  AFMPB_CUDA(cudaMemcpyAsync(h->d_level_table, level_table.data(), sizeof(int) * level_table.size(),
+                             cudaMemcpyHostToDevice, s));
+  // bases (FP32 for the product, FP64 for the compressed operators) and C_o = Q^T K_o Q
+  AFMPB_TRY(A.alloc(&h->d_Q, (size_t)ntab * N3 * R, "svd Q"));
+  AFMPB_TRY(A.alloc(&h->d_QT, (size_t)ntab * R * N3, "svd QT"));
+  AFMPB_TRY(A.alloc(&h->d_C, (size_t)ntab * kNumOffsets * R * R, "svd C"));
+  double *d_Q64 = nullptr, *d_T = nullptr;
+  AFMPB_TRY(A.alloc(&d_Q64, (size_t)N3 * R, "svd Q64"));
+  AFMPB_TRY(A.alloc(&d_T, (size_t)kNumOffsets * N3 * R, "svd T"));
+  std::vector<double> q64((size_t)N3 * R);
+  std::vector<float> qf((size_t)ntab * N3 * R), qtf((size_t)ntab * R * N3);
+  for (int t = 0; t < ntab; ++t) {
+    for (int i = 0; i < N3; ++i)
+      for (int a = 0; a < R; ++a) {
+        const double v = zt[t][(size_t)a * N3 + i];
+        q64[(size_t)i * R + a] = v;
+        qf[((size_t)t * N3 + i) * R + a] = (float)v;
+        qtf[((size_t)t * R + a) * N3 + i] = (float)v;
+      }
+    AFMPB_CUDA(cudaMemcpyAsync(d_Q64, q64.data(), sizeof(double) * q64.size(), cudaMemcpyHostToDevice, s));
+    k_table_f64<<<1024, 256, 0, s>>>(n, d_offs, nd, tab_kw[t], tab_invw[t], d_K);
+    AFMPB_TRY(check_launch("k_table_f64"));
+    k_kq<<<dim3(kNumOffsets, (N3 + kRowsPerCta - 1) / kRowsPerCta), 128, 0, s>>>(N3, R, d_K, d_Q64, d_T);
+    AFMPB_TRY(check_launch("k_kq"));
+    k_qtt<<<dim3(kNumOffsets, (R + kRowsPerCta - 1) / kRowsPerCta), 128, 0, s>>>(
+        N3, R, d_Q64, d_T, h->d_C + (size_t)t * kNumOffsets * R * R);
+    AFMPB_TRY(check_launch("k_qtt"));
+    AFMPB_CUDA(cudaStreamSynchronize(s));     // q64 is rewritten for the next table
+  }
+  AFMPB_CUDA(cudaMemcpyAsync(h->d_Q, qf.data(), sizeof(float) * qf.size(), cudaMemcpyHostToDevice, s));
+  AFMPB_CUDA(cudaMemcpyAsync(h->d_QT, qtf.data(), sizeof(float) * qtf.size(), cudaMemcpyHostToDevice, s));
+  // compress / expand work: chunks of up to kChunkBoxes boxes of one level, on the levels
+  // that have list-2 pairs
+  std::vector<int4> chunks;
+  for (int l = 2; l < std::min(T.nlevel, maxlev); ++l)
+    for (int b = T.lvl_start[l]; b < T.lvl_start[l + 1]; b += kChunkBoxes)
+      chunks.push_back(make_int4(b, std::min(kChunkBoxes, T.lvl_start[l + 1] - b), l, 0));
+  h->m2l_nchunks = (int)chunks.size();
+  AFMPB_TRY(A.alloc(&h->d_m2l_chunks, std::max<size_t>(1, chunks.size()), "svd chunks"));
+  if (!chunks.empty())
+    AFMPB_CUDA(cudaMemcpyAsync(h->d_m2l_chunks, chunks.data(), sizeof(int4) * chunks.size(), cudaMemcpyHostToDevice, s));
+  AFMPB_TRY(A.alloc(&h->d_Mc, (size_t)T.nbox * 2 * R, "Mc"));
+  AFMPB_TRY(A.alloc(&h->d_Lc, (size_t)T.nbox * 2 * R, "Lc"));
+  AFMPB_CUDA(cudaMemsetAsync(h->d_Mc, 0, sizeof(float) * (size_t)T.nbox * 2 * R, s));
+  AFMPB_TRY(set_box_basis_smem<false>(N3, R));
+  AFMPB_TRY(set_box_basis_smem<true>(R, N3));
+  const int rpl = (R + 31) / 32;
+  switch (rpl) {
+    case 1: AFMPB_TRY(set_m2l_c_smem<1>(R)); break;
+    case 2: AFMPB_TRY(set_m2l_c_smem<2>(R)); break;
+    case 3: AFMPB_TRY(set_m2l_c_smem<3>(R)); break;
+    case 4: AFMPB_TRY(set_m2l_c_smem<4>(R)); break;
+    case 5: AFMPB_TRY(set_m2l_c_smem<5>(R)); break;
+    default: AFMPB_TRY(set_m2l_c_smem<6>(R)); break;
+  }
+  AFMPB_CUDA(cudaStreamSynchronize(s));
+  A.release(d_T);
+  A.release(d_Q64);
+  A.release(d_gram);
+  A.release(d_K);
+  A.release(d_offs);
+  *compressed = true;
+  return Err{};
+}
+
+Err enqueue_m2l_svd(afmpb_t *h, cudaStream_t s) {
+  const int R = h->m2l_rank, N3 = h->ncoef;
+  const auto &T = h->shape;
+  AFMPB_CUDA(cudaMemsetAsync(h->d_Lc, 0, sizeof(float) * (size_t)T.nbox * 2 * R, s));
+  if (h->m2l_nchunks == 0) return Err{};
+  const dim3 cgrid((unsigned)h->m2l_nchunks, 2);
+  AFMPB_TRY(launch_box_basis<false>(s, cgrid, N3, R, h->d_m2l_chunks, h->d_level_table, h->m2l_yuk_levels,
+                                     h->d_Q, h->d_M, h->d_Mc));
+  if (h->opt.precision == 1) {
+    AFMPB_TRY(enqueue_m2l_tc(h, s));
+  } else {
+    switch ((R + 31) / 32) {
+      case 1: AFMPB_TRY(launch_m2l_c<1>(h, s)); break;
+      case 2: AFMPB_TRY(launch_m2l_c<2>(h, s)); break;
+      case 3: AFMPB_TRY(launch_m2l_c<3>(h, s)); break;
+      case 4: AFMPB_TRY(launch_m2l_c<4>(h, s)); break;
+      case 5: AFMPB_TRY(launch_m2l_c<5>(h, s)); break;
+      default: AFMPB_TRY(launch_m2l_c<6>(h, s)); break;
+    }
+  }
+  return launch_box_basis<true>(s, cgrid, R, N3, h->d_m2l_chunks, h->d_level_table, h->m2l_yuk_levels, h->d_QT,
+                                h->d_Lc, h->d_L);
+}
+
+}  // namespace afmpb

@@ -2,13 +2,14 @@
 // (precision mode 1).
 //
 // Each (level, offset) group of list-2 pairs is a dense product
-//      L[:, targets] += K_o (n^3 x n^3) * M[:, sources]          (Laplace and Yukawa)
-// A CTA takes one 128-row slice of K_o (A operand) and up to 112 pairs (B operand, the
-// gathered source multipole vectors) and runs tcgen05.mma (kind::f16: BF16 inputs, FP32
-// accumulation in tensor memory).  FP32 accuracy is kept by splitting every value into
+//      L[:, targets] += K_o (R x R) * M[:, sources]          (Laplace and Yukawa)
+// with R = n^3 (full translations) or the compressed size r (K_o = C_o, M and L the
+// compressed vectors Mc and Lc).  A CTA takes one 128-row slice of K_o (A operand) and
+// up to 112 pairs (B operand, the gathered source vectors) and runs tcgen05.mma
+// (kind::f16: BF16 inputs, FP32 accumulation in tensor memory).  FP32 accuracy is kept by splitting every value into
 // BF16 high and low parts, x = hi + lo, and summing hi*hi + hi*lo + lo*hi.
 //
-// The contraction (K = 224 after padding) runs in two halves of 112 so that a CTA needs
+// The contraction (R <= 224 after padding to 16) runs in halves of 112 so that a CTA needs
 // ~105 KB of shared memory and two CTAs share an SM, overlapping one CTA's loads with the
 // other's MMAs.  The A halves (pre-converted at setup into the MMA operand layout) arrive
 // by bulk asynchronous copy (the TMA engine, completion counted on an mbarrier) while the
@@ -31,7 +32,7 @@ namespace afmpb {
 constexpr int kTcRows = 128;                   // MMA M
 constexpr int kTcPairs = 112;                  // MMA N upper bound (pairs per CTA)
 constexpr int kTcKHalf = 112;                  // K per half (7 MMA k-steps of 16)
-constexpr int kTcK = 2 * kTcKHalf;             // 224 >= n^3 for order <= 6
+constexpr int kTcK = 2 * kTcKHalf;             // largest contraction: 224 >= n^3 for order <= 6
 constexpr int kTcAElems = kTcRows * kTcKHalf;  // 14,336 BF16 per A half-tile (hi or lo)
 constexpr int kTcBElems = kTcPairs * kTcKHalf; // 12,544 BF16 per B half-tile
 constexpr int kTcThreads = 256;
@@ -86,10 +87,11 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mb, uint32_t parity) {
 }
 
 // Translation matrices -> BF16 hi/lo half-tiles in the operand layout.
-// out: [table][slot][row tile][k half][hi, lo][kTcAElems]
+// out: [table][slot][row tile][k half][hi, lo][kTcAElems].  Sources: compressed tables
+// C [table][slot][R][R] when C is given, else Klap / Kyuk [level][slot] (R = n^3).
 __global__ void k_tc_tables(int N3, int ntables, int nslots, const float *__restrict__ Klap,
-                            const float *__restrict__ Kyuk, const int *__restrict__ table_level,
-                            __nv_bfloat16 *__restrict__ out) {
+                            const float *__restrict__ Kyuk, const float *__restrict__ C,
+                            const int *__restrict__ table_level, __nv_bfloat16 *__restrict__ out) {
   const int rtiles = (N3 + kTcRows - 1) / kTcRows;
   const int64_t total = (int64_t)ntables * nslots * rtiles * 2 * kTcAElems;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
@@ -105,8 +107,9 @@ __global__ void k_tc_tables(int N3, int ntables, int nslots, const float *__rest
     const int r = rt * kTcRows + row, k = kh * kTcKHalf + kk;
     float v = 0.0f;
     if (r < N3 && k < N3) {
-      const float *K = table == 0 ? Klap + (size_t)slot * N3 * N3
-                                  : Kyuk + ((size_t)table_level[table] * kNumOffsets + slot) * N3 * N3;
+      const float *K = C ? C + ((size_t)table * nslots + slot) * N3 * N3
+                         : table == 0 ? Klap + (size_t)slot * N3 * N3
+                                      : Kyuk + ((size_t)table_level[table] * kNumOffsets + slot) * N3 * N3;
       v = K[(size_t)r * N3 + k];
     }
     __nv_bfloat16 hi, lo;
@@ -167,8 +170,12 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_m2l_tc(int N3, const TCItem *
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_base;
   bool ok = true;
+  const int nkh = (N3 + kTcKHalf - 1) / kTcKHalf;     // contraction halves (1 or 2)
+  int issued = 0;                                      // MMA commits made on mb_mma
+  int loads = 0;                                       // A-operand copies started on mb_load
 
-  for (int kh = 0; kh < 2 && ok; ++kh) {
+  for (int kh = 0; kh < nkh && ok; ++kh) {
+    ++loads;
     // A half: two bulk copies (hi, lo) tracked by mb_load
     if (threadIdx.x == 0) {
       const int64_t base = ((((int64_t)table * nslots + g.offset) * rtiles + rt) * 2 + kh) * 2 * kTcAElems;
@@ -233,7 +240,8 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_m2l_tc(int N3, const TCItem *
       const uint32_t lbo_a = (kTcRows / 8) * 128, lbo_b = (kTcPairs / 8) * 128, sbo = 128;
       const uint32_t sa_hi = cvta_smem(a_hi), sa_lo = cvta_smem(a_lo);
       const uint32_t sb_hi = cvta_smem(b_hi), sb_lo = cvta_smem(b_lo);
-      for (int s = 0; s < kTcKHalf / 16; ++s) {
+      const int ksteps = (min(kTcKHalf, N3 - kh * kTcKHalf) + 15) / 16;
+      for (int s = 0; s < ksteps; ++s) {
         const uint32_t ka = 2 * s * lbo_a, kb = 2 * s * lbo_b;
         const uint64_t dah = smem_desc(sa_hi + ka, lbo_a, sbo), dal = smem_desc(sa_lo + ka, lbo_a, sbo);
         const uint64_t dbh = smem_desc(sb_hi + kb, lbo_b, sbo), dbl = smem_desc(sb_lo + kb, lbo_b, sbo);
@@ -253,14 +261,17 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_m2l_tc(int N3, const TCItem *
       }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mb_mma));
     }
+    if (ok) ++issued;                                  // block-uniform
     // the MMAs must finish reading A and B before the next half overwrites them
     ok = __syncthreads_and(ok && mbar_wait(mb_mma, (uint32_t)kh));
   }
   asm volatile("tcgen05.fence::after_thread_sync;");
   if (!ok) {
     if (lane == 0) atomicExch(&g_tc_error, 1);
-    mbar_wait(mb_mma, 0);     // bounded: let any issued MMA drain before freeing memory
-    mbar_wait(mb_mma, 1);
+    // bounded: let the last issued MMA group (they complete in order) drain before the
+    // tensor memory is freed
+    if (issued > 0) mbar_wait(mb_mma, (uint32_t)((issued - 1) & 1));
+    if (loads > 0) mbar_wait(mb_load, (uint32_t)((loads - 1) & 1));    // and the last bulk copy
   } else {
     // epilogue: warps w and w+4 read accumulator rows 32 (w % 4) .. + 31 (one row per lane)
     // and split the columns; the tile is transposed through shared memory (the A buffer,
@@ -302,11 +313,13 @@ constexpr int kTcSmem = (2 * kTcAElems + 2 * kTcBElems) * 2;
 }
 
 Err build_m2l_tc(afmpb_t *h) {
-  const int N3 = h->ncoef;
-  // the epilogue adds 4 consecutive weights with one 16-byte atomic: n^3 must be a
-  // multiple of 4 (orders 2, 4, 6) and fit the 224-wide contraction
+  // R: compressed size (a multiple of 16) or n^3
+  const int N3 = h->m2l_rank > 0 ? h->m2l_rank : h->ncoef;
+  // the epilogue adds 4 consecutive weights with one 16-byte atomic: R must be a
+  // multiple of 4 and fit the 224-wide contraction
   if (N3 > kTcK || N3 % 4 != 0)
-    return make_err(AFMPB_EINVAL, "precision 1 (tensor-core M2L) supports fmm_order 2, 4 or 6");
+    return make_err(AFMPB_EINVAL, "precision 1 (tensor-core M2L) supports fmm_order 2, 4 or 6, "
+                                  "or a compressed rank <= 224");
   auto &A = h->arena;
   cudaStream_t s = h->stream;
   // work items: chunks of <= 112 pairs per (level, offset) group
@@ -337,7 +350,8 @@ Err build_m2l_tc(afmpb_t *h) {
   AFMPB_CUDA(cudaMemcpyAsync(h->d_tc_level_table, level_table.data(), sizeof(int) * level_table.size(),
                              cudaMemcpyHostToDevice, s));
   AFMPB_CUDA(cudaMemcpyAsync(h->d_tc_items, items.data(), sizeof(TCItem) * items.size(), cudaMemcpyHostToDevice, s));
-  k_tc_tables<<<2048, 256, 0, s>>>(N3, ntables, kNumOffsets, h->d_K_lap, h->d_K_yuk, d_table_level,
+  k_tc_tables<<<2048, 256, 0, s>>>(N3, ntables, kNumOffsets, h->d_K_lap, h->d_K_yuk,
+                                   h->m2l_rank > 0 ? h->d_C : nullptr, d_table_level,
                                    reinterpret_cast<__nv_bfloat16 *>(h->d_tc_tiles));
   AFMPB_TRY(check_launch("k_tc_tables"));
   AFMPB_CUDA(cudaStreamSynchronize(s));
@@ -348,12 +362,13 @@ Err build_m2l_tc(afmpb_t *h) {
 
 Err enqueue_m2l_tc(afmpb_t *h, cudaStream_t s) {
   if (h->tc_items == 0) return Err{};
-  const int N3 = h->ncoef;
+  const bool comp = h->m2l_rank > 0;
+  const int N3 = comp ? h->m2l_rank : h->ncoef;
   dim3 grid((unsigned)h->tc_items, (N3 + kTcRows - 1) / kTcRows, 2);
   k_m2l_tc<<<grid, kTcThreads, kTcSmem, s>>>(N3, h->d_tc_items, h->d_m2l_groups, h->d_m2l_pairs,
                                              reinterpret_cast<const __nv_bfloat16 *>(h->d_tc_tiles),
                                              h->d_tc_level_table, kNumOffsets, h->m2l_yuk_levels,
-                                             h->d_box_center, h->d_M, h->d_L);
+                                             h->d_box_center, comp ? h->d_Mc : h->d_M, comp ? h->d_Lc : h->d_L);
   return check_launch("k_m2l_tc");
 }
 

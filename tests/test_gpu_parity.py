@@ -240,6 +240,29 @@ def test_mixed_precision_tensor_core_m2l(kappa):
     assert relerr(y_tc, y_fp) < 1e-5
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_m2l_compression_against_full_translations(precision):
+    """Compressed list-2 translations (the singular vectors of the stacked translation
+    matrices above m2l_tol): the rank grows as the cutoff falls, every setting meets the
+    oracle bar, and at 1e-6 the product agrees with the full n^3 translations to 1e-5."""
+    import paper_1710_06316_gb300 as pb
+    mol = synthetic.kirkwood_sphere(subdiv=5, kappa=0.104)
+    o = oracle.Oracle.for_molecule(mol)
+    x = synthetic.random_unknowns(mol.n_nodes, 11)
+    y_ref = o.matvec(x)
+    res = {}
+    for tol in (-1.0, 1e-4, 1e-6):
+        with pb.Handle.for_molecule(mol, order=6, leaf_cap=32, precision=precision, m2l_tol=tol) as h:
+            assert h.info()["n_m2l_pairs"] > 0
+            res[tol] = (h.info()["m2l_rank"], gpu_matvec(h, x))
+    assert res[-1.0][0] == 0
+    assert 0 < res[1e-4][0] <= res[1e-6][0] < 216
+    assert res[1e-4][0] % 16 == 0 and res[1e-6][0] % 16 == 0
+    for tol, (rank, y) in res.items():
+        assert relerr(y, y_ref) < TOL_MATVEC, (tol, rank)
+    assert relerr(res[1e-6][1], res[-1.0][1]) < 1e-5
+
+
 def test_mixed_precision_solve_and_energy(born):
     """Mixed-precision solve of the Born ion: same solution and energy as the oracle."""
     import paper_1710_06316_gb300 as pb
