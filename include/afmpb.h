@@ -128,6 +128,7 @@ typedef struct {
                                   near field, FMM operators, right-hand side, graph capture */
     int m2l_rank;              /* compressed translation size r (0: full n^3)            */
     int m2l_tables;            /* compressed bases: Laplace + one Yukawa per level       */
+    int64_t device_bytes_peak; /* high-water mark of device_bytes (setup scratch included) */
 } afmpb_info;
 
 /* Per-stage timing of one product (afmpb_profile_product). */
@@ -199,10 +200,10 @@ afmpb_status afmpb_energy(afmpb_t *h, double *kcal_per_mol);
  *   kcal_per_mol  host output, the same energy afmpb_energy returns
  * Returns EINVAL when the handle has more than AFMPB_NOALLOC_MAX_ATOMS charges.  The
  * first call on a device looks up the array's device address (cudaGetSymbolAddress)
- * and caches it; make that first call before any stream capture.  All calls share the
- * one array, so calls whose work overlaps on the GPU (two handles on different streams)
- * race and must be serialised by the caller.  The paper has no counterpart to this
- * entry point. */
+ * and caches it; make that first call before any stream capture.  All calls on one
+ * device share the one array, so the library serialises them: a call holds a process-wide
+ * lock from its first kernel until its result is back on the host.  The paper has no
+ * counterpart to this entry point. */
 #define AFMPB_NOALLOC_MAX_ATOMS 65536
 afmpb_status afmpb_energy_noalloc(afmpb_t *h, double *kcal_per_mol);
 
@@ -257,6 +258,65 @@ size_t afmpb_estimate_bytes(int64_t n_nodes, int64_t n_atoms, int fmm_order,
 
 /* Library version string. */
 const char *afmpb_version(void);
+
+/* ---- Serving: continuous batching of whole solves ------------------------------------
+ * The paper runs one solve at a time; this layer (no counterpart in the paper) serves
+ * many molecules or conformations of uneven size on one GPU.  Each request is one full
+ * afmpb_create + afmpb_solve + afmpb_energy + afmpb_destroy.  The server owns max_slots
+ * slot threads, each with its own CUDA stream; a slot admits the first queued request (in
+ * arrival order) whose device-memory reservation, afmpb_estimate_bytes of the request,
+ * fits under bytes_budget beside the requests already running; once the request's setup is
+ * done its reservation drops to the handle's measured high-water mark or its current bytes
+ * plus the GMRES basis still to come, whichever is larger.  Requests that arrive while
+ * others run are admitted as soon as a slot and memory free up, and their kernels overlap
+ * on the device.  The inputs are copied at submission; the solution, if asked for, is
+ * written into caller buffers that must stay valid until the request completes.  A result
+ * is handed out once (poll or wait); the ticket is invalid afterwards.  All calls are
+ * thread-safe except afmpb_server_destroy, which must not race with other calls on the
+ * same server: it drops queued requests, lets running ones finish and frees the server. */
+typedef struct afmpb_server_t afmpb_server_t;
+
+typedef struct {
+    afmpb_mesh mesh;             /* as for afmpb_create; copied at submission             */
+    afmpb_charges charges;       /* copied at submission                                  */
+    double eps_in, eps_out, kappa;
+    int fmm_order;
+    double tol;
+    afmpb_options options;       /* options.stream is ignored: each slot has its own       */
+    double *f_out, *h_out;       /* optional host buffers [n_nodes] for f and h (caller
+                                    order), written before the request completes           */
+} afmpb_request;
+
+typedef struct {
+    afmpb_status status;         /* AFMPB_OK, or the status of the failing step           */
+    char error[160];             /* its message                                           */
+    double energy_kcal_mol;
+    afmpb_solve_info info;
+    double t_submit, t_admit, t_done;   /* seconds since afmpb_server_create (steady clock) */
+    int64_t bytes_reserved;      /* admission reservation                                 */
+    int64_t bytes_used;          /* the handle's device high-water mark                   */
+    int slot;
+} afmpb_result;
+
+typedef struct {
+    int64_t submitted, completed, failed, running, queued;
+    int64_t bytes_in_use, bytes_high_water, bytes_budget;   /* reservations              */
+    int64_t max_running;         /* most requests running at once so far                  */
+    int slots;
+} afmpb_server_info;
+
+/* bytes_budget > 0; max_slots in [1, 256]. */
+afmpb_status afmpb_server_create(size_t bytes_budget, int max_slots, afmpb_server_t **out);
+/* EINVAL for missing arrays or sizes; ENOMEM when the reservation exceeds the whole budget
+ * (the request could never run); otherwise queues it and returns its ticket. */
+afmpb_status afmpb_server_submit(afmpb_server_t *s, const afmpb_request *req, int64_t *ticket);
+/* OK with *res filled when the request has completed (successfully or not), EBUSY while it
+ * is queued or running, EINVAL for an unknown ticket. */
+afmpb_status afmpb_server_poll(afmpb_server_t *s, int64_t ticket, afmpb_result *res);
+/* As poll but blocks up to timeout_s seconds; ETIMEOUT if the request is still pending. */
+afmpb_status afmpb_server_wait(afmpb_server_t *s, int64_t ticket, double timeout_s, afmpb_result *res);
+afmpb_status afmpb_server_get_info(afmpb_server_t *s, afmpb_server_info *st);
+afmpb_status afmpb_server_destroy(afmpb_server_t *s);
 
 #ifdef __cplusplus
 }

@@ -58,12 +58,32 @@ class Info(C.Structure):
                 ("n_m2l_pairs", C.c_int64), ("order", C.c_int), ("precision", C.c_int),
                 ("device_bytes", C.c_int64), ("root_center", C.c_double * 3),
                 ("root_half_width", C.c_double), ("ms_create", C.c_double * 6),
-                ("m2l_rank", C.c_int), ("m2l_tables", C.c_int)]
+                ("m2l_rank", C.c_int), ("m2l_tables", C.c_int), ("device_bytes_peak", C.c_int64)]
 
 
 class Profile(C.Structure):
     _fields_ = [("n_stages", C.c_int), ("name", (C.c_char * 16) * 16), ("ms", C.c_double * 16),
                 ("launches", C.c_int * 16), ("ms_graph", C.c_double), ("kernels_per_product", C.c_int)]
+
+
+class Request(C.Structure):
+    _fields_ = [("mesh", Mesh), ("charges", Charges), ("eps_in", C.c_double), ("eps_out", C.c_double),
+                ("kappa", C.c_double), ("fmm_order", C.c_int), ("tol", C.c_double), ("options", Options),
+                ("f_out", C.c_void_p), ("h_out", C.c_void_p)]
+
+
+class Result(C.Structure):
+    _fields_ = [("status", C.c_int), ("error", C.c_char * 160), ("energy_kcal_mol", C.c_double),
+                ("info", SolveInfo), ("t_submit", C.c_double), ("t_admit", C.c_double),
+                ("t_done", C.c_double), ("bytes_reserved", C.c_int64), ("bytes_used", C.c_int64),
+                ("slot", C.c_int)]
+
+
+class ServerInfo(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("failed", C.c_int64),
+                ("running", C.c_int64), ("queued", C.c_int64), ("bytes_in_use", C.c_int64),
+                ("bytes_high_water", C.c_int64), ("bytes_budget", C.c_int64),
+                ("max_running", C.c_int64), ("slots", C.c_int)]
 
 
 def _struct_dict(s):
@@ -77,7 +97,9 @@ def _struct_dict(s):
 EXPORTS = ["afmpb_create", "afmpb_matvec", "afmpb_matvec_parts", "afmpb_matvec_host", "afmpb_solve",
            "afmpb_energy", "afmpb_rhs", "afmpb_get_geometry", "afmpb_get_near", "afmpb_get_tree",
            "afmpb_get_info", "afmpb_destroy", "afmpb_last_error", "afmpb_estimate_bytes",
-           "afmpb_version", "afmpb_profile_product", "afmpb_energy_noalloc"]
+           "afmpb_version", "afmpb_profile_product", "afmpb_energy_noalloc",
+           "afmpb_server_create", "afmpb_server_submit", "afmpb_server_poll", "afmpb_server_wait",
+           "afmpb_server_get_info", "afmpb_server_destroy"]
 
 
 def library_path() -> str:
@@ -109,6 +131,18 @@ def load(build: bool = True):
     lib.afmpb_energy.argtypes = [P, C.POINTER(D)]
     lib.afmpb_energy_noalloc.restype = I32
     lib.afmpb_energy_noalloc.argtypes = [P, C.POINTER(D)]
+    lib.afmpb_server_create.restype = I32
+    lib.afmpb_server_create.argtypes = [C.c_size_t, C.c_int, C.POINTER(P)]
+    lib.afmpb_server_submit.restype = I32
+    lib.afmpb_server_submit.argtypes = [P, C.POINTER(Request), C.POINTER(I64)]
+    lib.afmpb_server_poll.restype = I32
+    lib.afmpb_server_poll.argtypes = [P, I64, C.POINTER(Result)]
+    lib.afmpb_server_wait.restype = I32
+    lib.afmpb_server_wait.argtypes = [P, I64, D, C.POINTER(Result)]
+    lib.afmpb_server_get_info.restype = I32
+    lib.afmpb_server_get_info.argtypes = [P, C.POINTER(ServerInfo)]
+    lib.afmpb_server_destroy.restype = I32
+    lib.afmpb_server_destroy.argtypes = [P]
     lib.afmpb_rhs.restype = I32
     lib.afmpb_rhs.argtypes = [P, P]
     lib.afmpb_get_geometry.restype = I32
@@ -305,3 +339,97 @@ class Handle:
 
     def __exit__(self, *a):
         self.close()
+
+
+def _result_dict(r):
+    d = {"status": STATUS.get(r.status, r.status), "error": r.error.decode(errors="replace"),
+         "energy": r.energy_kcal_mol, "info": _struct_dict(r.info), "t_submit": r.t_submit,
+         "t_admit": r.t_admit, "t_done": r.t_done, "bytes_reserved": r.bytes_reserved,
+         "bytes_used": r.bytes_used, "slot": r.slot}
+    d["latency"] = r.t_done - r.t_submit
+    return d
+
+
+class Server:
+    """Continuous-batching solve server (afmpb_server_*): submit whole solves, poll or wait
+    for their results; requests overlap on the GPU as slots and device memory allow."""
+
+    def __init__(self, bytes_budget, max_slots=4):
+        self._lib = load()
+        h = C.c_void_p()
+        rc = self._lib.afmpb_server_create(int(bytes_budget), int(max_slots), C.byref(h))
+        if rc != 0:
+            raise AfmpbError(rc, "afmpb_server_create failed")
+        self.s = h.value
+        self._keep = {}          # ticket -> output buffers that the server writes into
+
+    def submit(self, xyz, tri, atoms, q, eps_in=1.0, eps_out=80.0, kappa=0.0, order=6, tol=1e-6,
+               precision=0, leaf_cap=0, m2l_tol=0.0, want_solution=False):
+        xyz = _np(xyz, np.float64)
+        tri = _np(tri, np.int32)
+        atoms = _np(np.atleast_2d(atoms), np.float64)
+        q = _np(q, np.float64).ravel()
+        n = int(xyz.shape[0])
+        f = np.zeros(n) if want_solution else None
+        hh = np.zeros(n) if want_solution else None
+        req = Request(Mesh(n, int(tri.shape[0]), xyz.ctypes.data, tri.ctypes.data, None),
+                      Charges(int(q.size), atoms.ctypes.data, q.ctypes.data),
+                      float(eps_in), float(eps_out), float(kappa), int(order), float(tol),
+                      Options(int(leaf_cap), 0, 0, 0.0, int(precision), 0.0, None, 0, float(m2l_tol)),
+                      None if f is None else f.ctypes.data, None if hh is None else hh.ctypes.data)
+        t = C.c_int64()
+        rc = self._lib.afmpb_server_submit(self.s, C.byref(req), C.byref(t))
+        if rc != 0:
+            raise AfmpbError(rc, "afmpb_server_submit refused the request")
+        self._keep[t.value] = (f, hh)
+        return t.value
+
+    def submit_molecule(self, mol, **kw):
+        return self.submit(mol.xyz, mol.tri, mol.atoms, mol.q, mol.eps_in, mol.eps_out, mol.kappa, **kw)
+
+    def _finish(self, ticket, r):
+        d = _result_dict(r)
+        f, hh = self._keep.pop(ticket, (None, None))
+        if f is not None:
+            d["f"], d["h"] = f, hh
+        return d
+
+    def poll(self, ticket):
+        """The result dict, or None while the request is pending."""
+        r = Result()
+        rc = self._lib.afmpb_server_poll(self.s, int(ticket), C.byref(r))
+        if rc == 7:
+            return None
+        if rc != 0:
+            raise AfmpbError(rc, "afmpb_server_poll")
+        return self._finish(ticket, r)
+
+    def wait(self, ticket, timeout=600.0):
+        r = Result()
+        rc = self._lib.afmpb_server_wait(self.s, int(ticket), float(timeout), C.byref(r))
+        if rc != 0:
+            raise AfmpbError(rc, "afmpb_server_wait")
+        return self._finish(ticket, r)
+
+    def info(self):
+        i = ServerInfo()
+        _check(self._lib.afmpb_server_get_info(self.s, C.byref(i)))
+        return _struct_dict(i)
+
+    def close(self):
+        if getattr(self, "s", None):
+            self._lib.afmpb_server_destroy(self.s)
+            self.s = None
+            self._keep.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

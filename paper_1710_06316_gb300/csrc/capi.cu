@@ -11,6 +11,8 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <mutex>
 
 #include "internal.cuh"
 
@@ -140,6 +142,19 @@ Err create_impl(afmpb_t *h, const afmpb_mesh *mesh, const afmpb_charges *ch) {
 }  // namespace
 
 namespace afmpb {
+Err raise_smem_limit(const void *func, int bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void *>, int> limit;
+  int dev = 0;
+  AFMPB_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(mu);
+  int &cur = limit[{dev, func}];
+  if (bytes <= cur) return Err{};
+  AFMPB_CUDA(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  cur = bytes;
+  return Err{};
+}
+
 Err product_sorted(afmpb_t *h, cudaStream_t s, int parts) {
   if (parts <= 0 || parts > AFMPB_PART_ALL) return make_err(AFMPB_EINVAL, "parts must be a non-empty AFMPB_PART_* mask");
   if (!h->graph[parts]) AFMPB_TRY(capture_product(h, parts));
@@ -392,6 +407,7 @@ afmpb_status afmpb_get_info(const afmpb_t *h, afmpb_info *info) {
   for (int d = 0; d < 3; ++d) info->root_center[d] = T.c0[d];
   info->root_half_width = T.w0;
   for (int i = 0; i < 6; ++i) info->ms_create[i] = h->ms_create[i];
+  info->device_bytes_peak = (int64_t)h->arena.peak;
   info->m2l_rank = h->m2l_rank;
   info->m2l_tables = h->m2l_ntables;
   return AFMPB_OK;
@@ -500,7 +516,9 @@ size_t afmpb_estimate_bytes(int64_t n_nodes, int64_t n_atoms, int fmm_order, con
   size_t b = 0;
   b += n * (3 * 8 + 8 + 3 * 8 + 8 + 2 * 16 + 8 + 4 + 4 + 2 * 16 + 8 + 2 * 4 + 4 * 16);   // nodes
   b += 2 * n * (3 * 4 + 3 * 8 + 4);                                                    // triangles
-  b += n * 40 * (4 + 16 + 1) + 8 * (n + 1);                                             // near CSR
+  const double c = (o && o->near_c > 0) ? o->near_c : 2.0;
+  const size_t per_row = (size_t)std::ceil(80.0 * (c / 2.0) * (c / 2.0));             // isosurface meshes ~70
+  b += n * per_row * (4 + 16 + 1) + 8 * (n + 1);                                        // near CSR
   b += nbox * (2 * 2 * n3 * 4 + 64 + 27 * 4 + 200 * 4 * 2);                             // boxes, lists
   b += 316 * n3 * n3 * 4 * 14;                                                          // M2L tables
   b += (size_t)(m + 1) * 2 * n * 8 + 8 * 2 * n * 8;                                     // GMRES

@@ -21,14 +21,17 @@
 //
 // Lists: 1 and 3 by P2P (Sec. 3.2 modified method), 2 by M2L, 4 by P2L (S_to_L).
 #include <cmath>
+#include <mutex>
 
 #include "internal.cuh"
 
 namespace afmpb {
 
-__constant__ float c_cheb[kMaxOrder * kMaxOrder];          // Cm[m][k] = w_k T_k(x_m)
-__constant__ float c_m2m[2 * kMaxOrder * kMaxOrder];       // S2[c][m][m']
-__constant__ float c_nodes[kMaxOrder];                     // Chebyshev points on [-1, 1]
+// Per-order tables (index = order n), written once per device before the first handle
+// uses them, so that handles of different orders can run side by side.
+__constant__ float c_cheb[kMaxOrder + 1][kMaxOrder * kMaxOrder];     // Cm[m][k] = w_k T_k(x_m)
+__constant__ float c_m2m[kMaxOrder + 1][2 * kMaxOrder * kMaxOrder];  // S2[c][m][m']
+__constant__ float c_nodes[kMaxOrder + 1][kMaxOrder];                // Chebyshev points on [-1, 1]
 
 // s_m(x) and s_m'(x) for the n interpolation polynomials.
 template <int N>
@@ -50,8 +53,8 @@ __device__ __forceinline__ void cheb_basis(float x, float s[N], float ds[N]) {
     float a = 0.0f, b = 0.0f;
 #pragma unroll
     for (int k = 0; k < N; ++k) {
-      a = fmaf(c_cheb[m * kMaxOrder + k], T[k], a);
-      b = fmaf(c_cheb[m * kMaxOrder + k], dT[k], b);
+      a = fmaf(c_cheb[N][m * kMaxOrder + k], T[k], a);
+      b = fmaf(c_cheb[N][m * kMaxOrder + k], dT[k], b);
     }
     s[m] = a;
     ds[m] = b;
@@ -137,7 +140,7 @@ __global__ void __launch_bounds__(256) k_p2m(int nleaf, const int32_t *__restric
 template <int N>
 __device__ __forceinline__ float apply_axis(const float *in, int m, int axis, int c, bool transpose) {
   const int i = m / (N * N), j = (m / N) % N, k = m % N;
-  const float *S = c_m2m + c * kMaxOrder * kMaxOrder;
+  const float *S = c_m2m[N] + c * kMaxOrder * kMaxOrder;
   float acc = 0.0f;
 #pragma unroll
   for (int q = 0; q < N; ++q) {
@@ -283,9 +286,9 @@ __global__ void k_m2l_table(int N, int nslots, const int3 *__restrict__ offs, do
     int rem = (int)(e % ((int64_t)N3 * N3));
     int mt = rem / N3, ms = rem % N3;
     int3 o = offs[slot];
-    double tx = c_nodes[mt / (N * N)], ty = c_nodes[(mt / N) % N], tz = c_nodes[mt % N];
-    double sx = 2.0 * o.x + c_nodes[ms / (N * N)], sy = 2.0 * o.y + c_nodes[(ms / N) % N],
-           sz = 2.0 * o.z + c_nodes[ms % N];
+    const float *nd = c_nodes[N];
+    double tx = nd[mt / (N * N)], ty = nd[(mt / N) % N], tz = nd[mt % N];
+    double sx = 2.0 * o.x + nd[ms / (N * N)], sy = 2.0 * o.y + nd[(ms / N) % N], sz = 2.0 * o.z + nd[ms % N];
     double r = sqrt((tx - sx) * (tx - sx) + (ty - sy) * (ty - sy) + (tz - sz) * (tz - sz));
     double v = kInv4Pi / r;
     if (kw >= 0.0) v = exp(-kw * r) * v * invw;
@@ -316,9 +319,9 @@ __global__ void __launch_bounds__(256) k_p2l(const int32_t *__restrict__ xbox, c
     accL[r] = accY[r] = 0.0f;
     int m = threadIdx.x + 256 * r;
     if (m < N3) {
-      px[r] = w * c_nodes[m / (N * N)];
-      py[r] = w * c_nodes[(m / N) % N];
-      pz[r] = w * c_nodes[m % N];
+      px[r] = w * c_nodes[N][m / (N * N)];
+      py[r] = w * c_nodes[N][(m / N) % N];
+      pz[r] = w * c_nodes[N][m % N];
     }
   }
   for (int64_t j = xptr[b]; j < xptr[b + 1]; ++j) {
@@ -621,6 +624,38 @@ double cheb_s(int n, int m, double x) {   // s_m(x) in double (host tables)
   return v;
 }
 
+// Chebyshev tables of every order, uploaded once per device (host double -> float).
+Err init_cheb_tables() {
+  static std::mutex mu;
+  static bool done[64] = {};
+  int dev = 0;
+  AFMPB_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return make_err(AFMPB_EINVAL, "device index out of range");
+  std::lock_guard<std::mutex> lock(mu);
+  if (done[dev]) return Err{};
+  static float cheb[kMaxOrder + 1][kMaxOrder * kMaxOrder], nodes[kMaxOrder + 1][kMaxOrder],
+      m2m[kMaxOrder + 1][2 * kMaxOrder * kMaxOrder];
+  for (int n = 2; n <= kMaxOrder; ++n) {
+    for (int m = 0; m < n; ++m) {
+      nodes[n][m] = (float)std::cos((2.0 * m + 1.0) * kPi / (2.0 * n));
+      for (int k = 0; k < n; ++k)
+        cheb[n][m * kMaxOrder + k] = (float)((k == 0 ? 1.0 : 2.0) / n * std::cos(k * (2.0 * m + 1.0) * kPi / (2.0 * n)));
+    }
+    for (int c = 0; c < 2; ++c)
+      for (int m = 0; m < n; ++m)
+        for (int mp = 0; mp < n; ++mp) {
+          const double xmp = std::cos((2.0 * mp + 1.0) * kPi / (2.0 * n));
+          const double xi = (c == 0 ? -0.5 : 0.5) + 0.5 * xmp;
+          m2m[n][c * kMaxOrder * kMaxOrder + m * kMaxOrder + mp] = (float)cheb_s(n, m, xi);
+        }
+  }
+  AFMPB_CUDA(cudaMemcpyToSymbol(c_cheb, cheb, sizeof(cheb)));
+  AFMPB_CUDA(cudaMemcpyToSymbol(c_nodes, nodes, sizeof(nodes)));
+  AFMPB_CUDA(cudaMemcpyToSymbol(c_m2m, m2m, sizeof(m2m)));
+  done[dev] = true;
+  return Err{};
+}
+
 template <int N>
 Err launch_far(afmpb_t *h, cudaStream_t s, StageTimer *tm) {
   constexpr int N3 = N * N * N;
@@ -679,7 +714,7 @@ template <int N>
 Err set_m2l_smem() {
   constexpr int N3 = N * N * N;
   const size_t smem = sizeof(float) * (64 * (N3 + 1) + N3 * 32);
-  AFMPB_CUDA(cudaFuncSetAttribute(k_m2l<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  AFMPB_TRY(raise_smem_limit((const void *)k_m2l<N>, (int)smem));
   return Err{};
 }
 
@@ -719,25 +754,7 @@ Err build_fmm(afmpb_t *h) {
   cudaStream_t s = h->stream;
   auto &A = h->arena;
   const auto &T = h->shape;
-  // Chebyshev tables (host, double -> float)
-  {
-    float cheb[kMaxOrder * kMaxOrder] = {0}, nodes[kMaxOrder] = {0}, m2m[2 * kMaxOrder * kMaxOrder] = {0};
-    for (int m = 0; m < n; ++m) {
-      double xm = std::cos((2.0 * m + 1.0) * kPi / (2.0 * n));
-      nodes[m] = (float)xm;
-      for (int k = 0; k < n; ++k) cheb[m * kMaxOrder + k] = (float)((k == 0 ? 1.0 : 2.0) / n * std::cos(k * (2.0 * m + 1.0) * kPi / (2.0 * n)));
-    }
-    for (int c = 0; c < 2; ++c)
-      for (int m = 0; m < n; ++m)
-        for (int mp = 0; mp < n; ++mp) {
-          double xmp = std::cos((2.0 * mp + 1.0) * kPi / (2.0 * n));
-          double xi = (c == 0 ? -0.5 : 0.5) + 0.5 * xmp;
-          m2m[c * kMaxOrder * kMaxOrder + m * kMaxOrder + mp] = (float)cheb_s(n, m, xi);
-        }
-    AFMPB_CUDA(cudaMemcpyToSymbolAsync(c_cheb, cheb, sizeof(cheb), 0, cudaMemcpyHostToDevice, s));
-    AFMPB_CUDA(cudaMemcpyToSymbolAsync(c_nodes, nodes, sizeof(nodes), 0, cudaMemcpyHostToDevice, s));
-    AFMPB_CUDA(cudaMemcpyToSymbolAsync(c_m2m, m2m, sizeof(m2m), 0, cudaMemcpyHostToDevice, s));
-  }
+  AFMPB_TRY(init_cheb_tables());
   // offset slots: [-3,3]^3 minus [-1,1]^3
   std::vector<int> code_to_slot(343, -1);
   std::vector<int3> offs;

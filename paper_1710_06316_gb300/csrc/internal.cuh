@@ -4,6 +4,7 @@
 
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <cstdio>
 #include <string>
@@ -108,6 +109,7 @@ inline Err make_err(afmpb_status c, const std::string &m) { return Err{c, m}; }
 struct DeviceArena {
   std::vector<std::pair<void *, size_t>> blocks;
   size_t bytes = 0;
+  size_t peak = 0;                 // high-water mark of bytes
   template <class T>
   Err alloc(T **p, size_t count, const char *what) {
     *p = nullptr;
@@ -122,6 +124,7 @@ struct DeviceArena {
     }
     blocks.push_back({q, count * sizeof(T)});
     bytes += count * sizeof(T);
+    peak = std::max(peak, bytes);
     *p = static_cast<T *>(q);
     return Err{};
   }
@@ -272,6 +275,7 @@ struct afmpb_t {
   afmpb::TCItem *d_tc_items = nullptr;  // work items: (group, first pair, pair count)
   uint16_t *d_tc_tiles = nullptr;  // BF16 hi/lo translation tiles in the MMA operand layout
   int *d_tc_level_table = nullptr; // level -> Yukawa tile table
+  int *d_tc_flag = nullptr;        // set by a tensor-core CTA whose bounded wait expired
 
   // ---- per-product work --------------------------------------------------------------
   float2 *d_xs = nullptr;          // [n] (f, h) Morton order
@@ -315,7 +319,7 @@ Err build_m2l_tc(afmpb_t *h);
 // m2l_svd.cu: compressed translations; *compressed = false leaves the full ones in use
 Err build_m2l_svd(afmpb_t *h, bool *compressed);
 Err enqueue_m2l_svd(afmpb_t *h, cudaStream_t s);      // compress, translate, expand
-Err read_tc_error(int *flag);                          // 1 when a tensor-core wait expired
+Err read_tc_error(afmpb_t *h, int *flag);             // 1 when a tensor-core wait expired
 // solve.cu
 Err build_rhs(afmpb_t *h);
 Err enqueue_gather(afmpb_t *h, cudaStream_t s, const float *x_caller);
@@ -328,6 +332,11 @@ Err product_sorted(afmpb_t *h, cudaStream_t s, int parts);  // d_xs -> d_ys
 
 // launch helpers
 inline int div_up(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+// Raise a kernel's dynamic shared-memory limit to at least `bytes` (the attribute is
+// process-wide per kernel and per device, so it is only ever raised: a handle that needs
+// less must not lower it under another handle's launch).
+Err raise_smem_limit(const void *func, int bytes);
+
 inline Err check_launch(const char *what) {
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return make_err(AFMPB_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));

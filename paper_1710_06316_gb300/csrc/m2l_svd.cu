@@ -263,10 +263,10 @@ template <bool ACCUM>
 Err set_box_basis_smem(int K, int ncol) {
   const int smem = (int)basis_smem(K, ncol);
   switch (basis_tiles(ncol)) {
-    case 1: AFMPB_CUDA(cudaFuncSetAttribute(k_box_basis<1, ACCUM>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)); break;
-    case 2: AFMPB_CUDA(cudaFuncSetAttribute(k_box_basis<2, ACCUM>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)); break;
-    case 3: AFMPB_CUDA(cudaFuncSetAttribute(k_box_basis<3, ACCUM>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)); break;
-    default: AFMPB_CUDA(cudaFuncSetAttribute(k_box_basis<4, ACCUM>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)); break;
+    case 1: AFMPB_TRY(raise_smem_limit((const void *)k_box_basis<1, ACCUM>, smem)); break;
+    case 2: AFMPB_TRY(raise_smem_limit((const void *)k_box_basis<2, ACCUM>, smem)); break;
+    case 3: AFMPB_TRY(raise_smem_limit((const void *)k_box_basis<3, ACCUM>, smem)); break;
+    default: AFMPB_TRY(raise_smem_limit((const void *)k_box_basis<4, ACCUM>, smem)); break;
   }
   return Err{};
 }
@@ -368,7 +368,7 @@ Err launch_m2l_c(afmpb_t *h, cudaStream_t s) {
 template <int RPL>
 Err set_m2l_c_smem(int R) {
   const size_t smem = sizeof(float) * ((size_t)R * (R + 1) + (size_t)R * 32);
-  AFMPB_CUDA(cudaFuncSetAttribute(k_m2l_c<RPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  AFMPB_TRY(raise_smem_limit((const void *)k_m2l_c<RPL>, (int)smem));
   return Err{};
 }
 

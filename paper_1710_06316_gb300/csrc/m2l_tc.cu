@@ -39,7 +39,6 @@ constexpr int kTcThreads = 256;
 constexpr int kTcTmemCols = 128;
 constexpr uint32_t kTcSpinLimit = 1u << 26;    // bounded mbarrier wait
 
-__device__ int g_tc_error = 0;                 // set when a bounded wait expired
 
 // Byte offset of element (row, k) in a canonical K-major no-swizzle tile with `rows` rows.
 __host__ __device__ __forceinline__ uint32_t canon_off(int row, int k, int rows) {
@@ -127,7 +126,8 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_m2l_tc(int N3, const TCItem *
                                                           const __nv_bfloat16 *__restrict__ tiles,
                                                           const int *__restrict__ level_table, int nslots,
                                                           int yuk_min_level, const dbl4 *__restrict__ center,
-                                                          const float *__restrict__ M, float *__restrict__ L) {
+                                                          const float *__restrict__ M, float *__restrict__ L,
+                                                          int *__restrict__ err_flag) {
   extern __shared__ __align__(128) uint8_t smem[];
   __nv_bfloat16 *a_hi = reinterpret_cast<__nv_bfloat16 *>(smem);
   __nv_bfloat16 *a_lo = a_hi + kTcAElems;
@@ -267,7 +267,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_m2l_tc(int N3, const TCItem *
   }
   asm volatile("tcgen05.fence::after_thread_sync;");
   if (!ok) {
-    if (lane == 0) atomicExch(&g_tc_error, 1);
+    if (lane == 0) atomicExch(err_flag, 1);      // the handle's flag: set when a bounded wait expired
     // bounded: let the last issued MMA group (they complete in order) drain before the
     // tensor memory is freed
     if (issued > 0) mbar_wait(mb_mma, (uint32_t)((issued - 1) & 1));
@@ -346,6 +346,8 @@ Err build_m2l_tc(afmpb_t *h) {
   AFMPB_TRY(A.alloc(&d_table_level, table_level.size(), "table level"));
   AFMPB_TRY(A.alloc(&h->d_tc_level_table, level_table.size(), "level table"));
   AFMPB_TRY(A.alloc(&h->d_tc_items, items.size(), "tc items"));
+  AFMPB_TRY(A.alloc(&h->d_tc_flag, 1, "tc flag"));
+  AFMPB_CUDA(cudaMemsetAsync(h->d_tc_flag, 0, sizeof(int), s));
   AFMPB_CUDA(cudaMemcpyAsync(d_table_level, table_level.data(), sizeof(int) * table_level.size(), cudaMemcpyHostToDevice, s));
   AFMPB_CUDA(cudaMemcpyAsync(h->d_tc_level_table, level_table.data(), sizeof(int) * level_table.size(),
                              cudaMemcpyHostToDevice, s));
@@ -356,7 +358,7 @@ Err build_m2l_tc(afmpb_t *h) {
   AFMPB_TRY(check_launch("k_tc_tables"));
   AFMPB_CUDA(cudaStreamSynchronize(s));
   A.release(d_table_level);
-  AFMPB_CUDA(cudaFuncSetAttribute(k_m2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem));
+  AFMPB_TRY(raise_smem_limit((const void *)k_m2l_tc, kTcSmem));
   return Err{};
 }
 
@@ -368,12 +370,16 @@ Err enqueue_m2l_tc(afmpb_t *h, cudaStream_t s) {
   k_m2l_tc<<<grid, kTcThreads, kTcSmem, s>>>(N3, h->d_tc_items, h->d_m2l_groups, h->d_m2l_pairs,
                                              reinterpret_cast<const __nv_bfloat16 *>(h->d_tc_tiles),
                                              h->d_tc_level_table, kNumOffsets, h->m2l_yuk_levels,
-                                             h->d_box_center, comp ? h->d_Mc : h->d_M, comp ? h->d_Lc : h->d_L);
+                                             h->d_box_center, comp ? h->d_Mc : h->d_M, comp ? h->d_Lc : h->d_L,
+                                             h->d_tc_flag);
   return check_launch("k_m2l_tc");
 }
 
-Err read_tc_error(int *flag) {
-  AFMPB_CUDA(cudaMemcpyFromSymbol(flag, g_tc_error, sizeof(int)));
+Err read_tc_error(afmpb_t *h, int *flag) {
+  *flag = 0;
+  if (!h->d_tc_flag) return Err{};
+  AFMPB_CUDA(cudaMemcpyAsync(flag, h->d_tc_flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  AFMPB_CUDA(cudaStreamSynchronize(h->stream));
   return Err{};
 }
 

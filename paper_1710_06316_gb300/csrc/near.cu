@@ -20,6 +20,8 @@
 // FP32 (the `Real` template parameter; GB300's FP32 rate is many times its FP64 rate).
 #include <cmath>
 
+#include <mutex>
+
 #include "internal.cuh"
 
 namespace afmpb {
@@ -367,19 +369,22 @@ void gauss_legendre_unit(int n, double *x, double *w) {
     w[i] = 1.0 / ((1.0 - z * z) * dp * dp);
   }
 }
-}  // namespace
-
-Err build_near(afmpb_t *h) {
-  const int64_t n = h->n;
-  cudaStream_t s = h->stream;
-  auto &A = h->arena;
+// Quadrature constants (the same for every handle), uploaded once per device.
+Err init_quadrature_tables() {
+  static std::mutex mu;
+  static bool done[64] = {};
+  int dev = 0;
+  AFMPB_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return make_err(AFMPB_EINVAL, "device index out of range");
+  std::lock_guard<std::mutex> lock(mu);
+  if (done[dev]) return Err{};
   {
     double gx[16], gw[16];
     gauss_legendre_unit(16, gx, gw);
     float fx[16], fw[16];
     for (int i = 0; i < 16; ++i) { fx[i] = (float)gx[i]; fw[i] = (float)gw[i]; }
-    AFMPB_CUDA(cudaMemcpyToSymbolAsync(c_gl_xf, fx, sizeof(fx), 0, cudaMemcpyHostToDevice, s));
-    AFMPB_CUDA(cudaMemcpyToSymbolAsync(c_gl_wf, fw, sizeof(fw), 0, cudaMemcpyHostToDevice, s));
+    AFMPB_CUDA(cudaMemcpyToSymbol(c_gl_xf, fx, sizeof(fx)));
+    AFMPB_CUDA(cudaMemcpyToSymbol(c_gl_wf, fw, sizeof(fw)));
     // Radon's 7-point rule (exact for degree 5): centroid and two orbits of three points
     const double r15 = std::sqrt(15.0);
     const double a1 = (6.0 - r15) / 21.0, a2 = (6.0 + r15) / 21.0;
@@ -391,9 +396,20 @@ Err build_near(afmpb_t *h) {
     float bf[21], wf[7];
     for (int i = 0; i < 21; ++i) bf[i] = (float)b[i];
     for (int i = 0; i < 7; ++i) wf[i] = (float)w[i];
-    AFMPB_CUDA(cudaMemcpyToSymbolAsync(c_rad_bf, bf, sizeof(bf), 0, cudaMemcpyHostToDevice, s));
-    AFMPB_CUDA(cudaMemcpyToSymbolAsync(c_rad_wf, wf, sizeof(wf), 0, cudaMemcpyHostToDevice, s));
+    AFMPB_CUDA(cudaMemcpyToSymbol(c_rad_bf, bf, sizeof(bf)));
+    AFMPB_CUDA(cudaMemcpyToSymbol(c_rad_wf, wf, sizeof(wf)));
   }
+  done[dev] = true;
+  return Err{};
+}
+
+}  // namespace
+
+Err build_near(afmpb_t *h) {
+  const int64_t n = h->n;
+  cudaStream_t s = h->stream;
+  auto &A = h->arena;
+  AFMPB_TRY(init_quadrature_tables());
   int64_t *d_cnt = nullptr;
   AFMPB_TRY(A.alloc(&d_cnt, n, "near cnt"));
   const double cnear = h->opt.near_c;

@@ -1,0 +1,288 @@
+// server.cu -- continuous-batching solve server (afmpb_server_*).
+//
+// Requests (a mesh, its charges and the solver parameters) are copied at submission and
+// queued.  A fixed set of slot threads, each with its own CUDA stream, admits queued
+// requests first-fit in arrival order whenever a slot is idle and the request's device
+// memory reservation (afmpb_estimate_bytes) fits under the budget beside the requests
+// already running.  An admitted request runs its whole life on its slot's stream: handle
+// setup (tree, near field, FMM operators, captured product graph), GMRES solve with the
+// Krylov basis on the device, energy, then the handle is freed and its reservation
+// returned, which may admit the next request at once.  Requests on different slots
+// overlap on the device (their kernels run on separate streams) and on the host (setup
+// work runs on the slot threads).  Results are kept until a poll or wait hands them out.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Job {
+  int64_t ticket = 0;
+  std::vector<double> xyz, normals, atoms, q;
+  std::vector<int32_t> tri;
+  int64_t n_nodes = 0, n_tris = 0, n_atoms = 0;
+  double eps_in = 1, eps_out = 1, kappa = 0, tol = 1e-6;
+  int order = 6;
+  afmpb_options opt{};
+  double *f_out = nullptr, *h_out = nullptr;
+  size_t reserve = 0;
+  double t_submit = 0;
+};
+
+struct Done {
+  afmpb_result res{};
+  bool ready = false;
+};
+
+}  // namespace
+
+struct afmpb_server_t {
+  size_t budget = 0;
+  int max_slots = 0;
+  Clock::time_point t0;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<std::unique_ptr<Job>> queue;
+  std::unordered_map<int64_t, Done> results;
+  std::vector<std::thread> slots;
+  bool stop = false;
+  int64_t next_ticket = 1;
+  size_t in_use = 0, high_water = 0;
+  int64_t submitted = 0, completed = 0, failed = 0, running = 0, max_running = 0;
+  std::string err;
+
+  double now() const { return std::chrono::duration<double>(Clock::now() - t0).count(); }
+};
+
+namespace {
+
+// First queued job (arrival order) whose reservation fits beside the running ones.
+std::unique_ptr<Job> take_admissible(afmpb_server_t *s) {
+  for (auto it = s->queue.begin(); it != s->queue.end(); ++it) {
+    if (s->in_use + (*it)->reserve <= s->budget) {
+      std::unique_ptr<Job> j = std::move(*it);
+      s->queue.erase(it);
+      return j;
+    }
+  }
+  return nullptr;
+}
+
+void run_job(afmpb_server_t *s, Job &j, cudaStream_t stream, afmpb_result &r) {
+  afmpb_mesh mesh{j.n_nodes, j.n_tris, j.xyz.data(), j.tri.data(), j.normals.empty() ? nullptr : j.normals.data()};
+  afmpb_charges ch{j.n_atoms, j.atoms.data(), j.q.data()};
+  afmpb_options opt = j.opt;
+  opt.stream = stream;
+  afmpb_t *h = nullptr;
+  r.status = afmpb_create(&mesh, j.n_atoms > 0 ? &ch : nullptr, j.eps_in, j.eps_out, j.kappa, j.order, j.tol, &opt, &h);
+  if (r.status != AFMPB_OK) {
+    std::strncpy(r.error, afmpb_last_error(nullptr), sizeof(r.error) - 1);
+    return;
+  }
+  // Setup is done: shrink the reservation to what the handle holds at its peak, or now
+  // plus the GMRES basis and work vectors still to come, whichever is larger.
+  afmpb_info pre{};
+  if (afmpb_get_info(h, &pre) == AFMPB_OK) {
+    const size_t m = (size_t)(opt.restart > 0 ? opt.restart : 80);
+    const size_t n2 = 2 * (size_t)j.n_nodes;
+    const size_t gmres = (m + 1) * n2 * 8 + 16 * n2 * 8 + (16u << 20);
+    const size_t need = std::max((size_t)pre.device_bytes_peak, (size_t)pre.device_bytes + gmres);
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      s->in_use = s->in_use - j.reserve + need;
+      s->high_water = std::max(s->high_water, s->in_use);
+      j.reserve = need;
+    }
+    s->cv_work.notify_all();
+  }
+  r.status = afmpb_solve(h, j.f_out, j.h_out, &r.info);
+  if (r.status == AFMPB_OK) r.status = afmpb_energy(h, &r.energy_kcal_mol);
+  if (r.status != AFMPB_OK) std::strncpy(r.error, afmpb_last_error(h), sizeof(r.error) - 1);
+  afmpb_info inf{};
+  if (afmpb_get_info(h, &inf) == AFMPB_OK) r.bytes_used = inf.device_bytes_peak;
+  afmpb_destroy(h);
+}
+
+void slot_main(afmpb_server_t *s, int slot) {
+  cudaStream_t stream = nullptr;
+  const bool have_stream = cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking) == cudaSuccess;
+  for (;;) {
+    std::unique_ptr<Job> j;
+    {
+      std::unique_lock<std::mutex> lk(s->mu);
+      s->cv_work.wait(lk, [&] { return s->stop || (!s->queue.empty() && (j = take_admissible(s)) != nullptr); });
+      if (!j) break;                                    // stopping
+      s->in_use += j->reserve;
+      s->high_water = std::max(s->high_water, s->in_use);
+      ++s->running;
+      s->max_running = std::max(s->max_running, s->running);
+    }
+    afmpb_result r{};
+    r.t_submit = j->t_submit;
+    r.t_admit = s->now();
+    r.slot = slot;
+    r.bytes_reserved = (int64_t)j->reserve;
+    if (have_stream) {
+      run_job(s, *j, stream, r);
+    } else {
+      r.status = AFMPB_ECUDA;
+      std::strncpy(r.error, "slot stream creation failed", sizeof(r.error) - 1);
+    }
+    r.t_done = s->now();
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      s->in_use -= j->reserve;
+      --s->running;
+      ++s->completed;
+      if (r.status != AFMPB_OK) ++s->failed;
+      Done &d = s->results[j->ticket];
+      d.res = r;
+      d.ready = true;
+    }
+    s->cv_done.notify_all();
+    s->cv_work.notify_all();                            // freed memory may admit others
+  }
+  if (stream) cudaStreamDestroy(stream);
+}
+
+bool copy_array(std::vector<double> &dst, const double *src, int64_t n) {
+  if (n < 0 || (n > 0 && !src)) return false;
+  dst.assign(src, src + n);
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+afmpb_status afmpb_server_create(size_t bytes_budget, int max_slots, afmpb_server_t **out) {
+  if (!out || bytes_budget == 0 || max_slots < 1 || max_slots > 256) return AFMPB_EINVAL;
+  *out = nullptr;
+  afmpb_server_t *s = new (std::nothrow) afmpb_server_t();
+  if (!s) return AFMPB_ENOMEM;
+  s->budget = bytes_budget;
+  s->max_slots = max_slots;
+  s->t0 = Clock::now();
+  try {
+    for (int i = 0; i < max_slots; ++i) s->slots.emplace_back(slot_main, s, i);
+  } catch (...) {
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      s->stop = true;
+    }
+    s->cv_work.notify_all();
+    for (auto &t : s->slots) t.join();
+    delete s;
+    return AFMPB_ENOMEM;
+  }
+  *out = s;
+  return AFMPB_OK;
+}
+
+afmpb_status afmpb_server_submit(afmpb_server_t *s, const afmpb_request *req, int64_t *ticket) {
+  if (!s || !req || !ticket) return AFMPB_EINVAL;
+  const afmpb_mesh &m = req->mesh;
+  if (m.n_nodes <= 0 || m.n_tris <= 0 || !m.xyz || !m.tri || req->charges.n < 0) return AFMPB_EINVAL;
+  auto j = std::make_unique<Job>();
+  j->n_nodes = m.n_nodes;
+  j->n_tris = m.n_tris;
+  j->n_atoms = req->charges.n;
+  if (!copy_array(j->xyz, m.xyz, 3 * m.n_nodes)) return AFMPB_EINVAL;
+  j->tri.assign(m.tri, m.tri + 3 * m.n_tris);
+  if (m.normals) copy_array(j->normals, m.normals, 3 * m.n_nodes);
+  if (!copy_array(j->atoms, req->charges.xyz, 3 * req->charges.n) || !copy_array(j->q, req->charges.q, req->charges.n))
+    return AFMPB_EINVAL;
+  j->eps_in = req->eps_in;
+  j->eps_out = req->eps_out;
+  j->kappa = req->kappa;
+  j->tol = req->tol;
+  j->order = req->fmm_order;
+  j->opt = req->options;
+  j->f_out = req->f_out;
+  j->h_out = req->h_out;
+  j->reserve = afmpb_estimate_bytes(m.n_nodes, req->charges.n, req->fmm_order, &req->options);
+  if (j->reserve == 0) return AFMPB_EINVAL;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (s->stop) return AFMPB_ESTATE;
+    if (j->reserve > s->budget) {
+      s->err = "request needs more device memory than the whole budget";
+      return AFMPB_ENOMEM;
+    }
+    j->ticket = s->next_ticket++;
+    j->t_submit = s->now();
+    *ticket = j->ticket;
+    s->results[j->ticket];                              // pending entry
+    s->queue.push_back(std::move(j));
+    ++s->submitted;
+  }
+  s->cv_work.notify_one();
+  return AFMPB_OK;
+}
+
+afmpb_status afmpb_server_poll(afmpb_server_t *s, int64_t ticket, afmpb_result *res) {
+  if (!s || !res) return AFMPB_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->results.find(ticket);
+  if (it == s->results.end()) return AFMPB_EINVAL;
+  if (!it->second.ready) return AFMPB_EBUSY;
+  *res = it->second.res;
+  s->results.erase(it);
+  return AFMPB_OK;
+}
+
+afmpb_status afmpb_server_wait(afmpb_server_t *s, int64_t ticket, double timeout_s, afmpb_result *res) {
+  if (!s || !res || !(timeout_s >= 0)) return AFMPB_EINVAL;
+  std::unique_lock<std::mutex> lk(s->mu);
+  auto it = s->results.find(ticket);
+  if (it == s->results.end()) return AFMPB_EINVAL;
+  const auto limit = Clock::now() + std::chrono::duration_cast<Clock::duration>(std::chrono::duration<double>(timeout_s));
+  if (!s->cv_done.wait_until(lk, limit, [&] { return s->results[ticket].ready; })) return AFMPB_ETIMEOUT;
+  it = s->results.find(ticket);
+  *res = it->second.res;
+  s->results.erase(it);
+  return AFMPB_OK;
+}
+
+afmpb_status afmpb_server_get_info(afmpb_server_t *s, afmpb_server_info *st) {
+  if (!s || !st) return AFMPB_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  st->submitted = s->submitted;
+  st->completed = s->completed;
+  st->failed = s->failed;
+  st->running = s->running;
+  st->queued = (int64_t)s->queue.size();
+  st->bytes_in_use = (int64_t)s->in_use;
+  st->bytes_high_water = (int64_t)s->high_water;
+  st->bytes_budget = (int64_t)s->budget;
+  st->max_running = s->max_running;
+  st->slots = s->max_slots;
+  return AFMPB_OK;
+}
+
+afmpb_status afmpb_server_destroy(afmpb_server_t *s) {
+  if (!s) return AFMPB_EINVAL;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop = true;
+    s->queue.clear();                                   // queued requests are dropped
+  }
+  s->cv_work.notify_all();
+  for (auto &t : s->slots) t.join();                    // running requests finish first
+  delete s;
+  return AFMPB_OK;
+}
+
+}  // extern "C"

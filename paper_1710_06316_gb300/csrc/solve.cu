@@ -440,7 +440,7 @@ Err run_solve(afmpb_t *h, afmpb_solve_info *info) {
   h->solved = true;
   if (h->opt.precision == 1) {
     int flag = 0;
-    AFMPB_TRY(read_tc_error(&flag));
+    AFMPB_TRY(read_tc_error(h, &flag));
     if (flag) return make_err(AFMPB_ETIMEOUT, "a tensor-core M2L wait expired; the products are not valid");
   }
   if (info) {
@@ -512,16 +512,15 @@ Err run_energy_noalloc(afmpb_t *h, double *E) {
   int dev = 0;
   AFMPB_CUDA(cudaGetDevice(&dev));
   if (dev < 0 || dev >= kMaxDevices) return make_err(AFMPB_EINVAL, "device ordinal out of range");
-  double *base = nullptr;
-  {
-    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-    if (!g_noalloc_ptr[dev]) {
-      void *p = nullptr;
-      AFMPB_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
-      g_noalloc_ptr[dev] = static_cast<double *>(p);
-    }
-    base = g_noalloc_ptr[dev];
+  // One scratch array per device: calls on different handles of the same device take
+  // turns (the lock is held until the result has been copied back).
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_ptr[dev]) {
+    void *p = nullptr;
+    AFMPB_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    g_noalloc_ptr[dev] = static_cast<double *>(p);
   }
+  double *base = g_noalloc_ptr[dev];
   double *d_part = base;                                    // [parts][natoms], fully rewritten
   double *d_phi = base + (size_t)kNoAllocParts * kNoAllocMaxAtoms;
   double *d_E = d_phi + kNoAllocMaxAtoms;
