@@ -79,9 +79,13 @@ typedef struct {
     const double *q;        /* [n]     */
 } afmpb_charges;
 
+/* afmpb_options.leaf_cap: choose the leaf capacity by measurement (afmpb_get_autotune). */
+#define AFMPB_LEAF_CAP_AUTO (-1)
+
 /* Options; a zero-initialised struct selects every default. */
 typedef struct {
-    int leaf_cap;        /* most nodes in a leaf box of the octree (default 128)         */
+    int leaf_cap;        /* most nodes in a leaf box of the octree (default 80 with
+                            precision 1, 192 with precision 0); AFMPB_LEAF_CAP_AUTO tunes it */
     int restart;         /* GMRES Krylov dimension m (default 80, Sec. 5)                */
     int max_restart;     /* GMRES restarts allowed (default 5, Sec. 5)                   */
     double abs_tol;      /* eps_abs of Eq. 7 (default 0)                                 */
@@ -129,7 +133,30 @@ typedef struct {
     int m2l_rank;              /* compressed translation size r (0: full n^3)            */
     int m2l_tables;            /* compressed bases: Laplace + one Yukawa per level       */
     int64_t device_bytes_peak; /* high-water mark of device_bytes (setup scratch included) */
+    int leaf_cap;              /* leaf capacity the octree was built with                */
+    int autotuned;             /* 1 when AFMPB_LEAF_CAP_AUTO ran the tuner for this handle */
 } afmpb_info;
+
+/* Leaf-capacity autotuner report (AFMPB_LEAF_CAP_AUTO; no counterpart in the paper, which
+ * fixes the leaf size by hand).  The handle is first built at start_cap; its product's
+ * stage times calibrate the cost of one list-2 translation (ms_per_m2l_pair) and of one
+ * box in the other tree passes (ms_per_box); for each candidate capacity the octree and
+ * lists alone are rebuilt over the same geometry and the P2P kernel is timed on them
+ * (p2p_ms); predicted_ms = p2p_ms + ms_per_m2l_pair * list-2 pairs + ms_per_box * boxes +
+ * ms_rest.  The handle is rebuilt at best_cap when that predicts a product at least 3%
+ * faster.  The choice is cached per size class (device, precision, order, kappa > 0,
+ * floor(log2 N)); later handles of the class start at it and skip the tuning. */
+#define AFMPB_AUTOTUNE_MAX 16
+typedef struct {
+    int n_candidates;
+    int cap[AFMPB_AUTOTUNE_MAX];
+    double p2p_ms[AFMPB_AUTOTUNE_MAX];
+    double predicted_ms[AFMPB_AUTOTUNE_MAX];
+    int start_cap, best_cap;
+    double predicted_start_ms, predicted_best_ms;
+    double ms_per_m2l_pair, ms_per_box, ms_rest;
+    double ms_tuning;          /* host time of the calibration and the candidate trees   */
+} afmpb_autotune_report;
 
 /* Per-stage timing of one product (afmpb_profile_product). */
 #define AFMPB_MAX_STAGES 16
@@ -237,6 +264,10 @@ afmpb_status afmpb_get_tree(afmpb_t *h, int32_t *box_level, int32_t *box_anchor,
                             int64_t *w_ptr, int32_t *w_idx, int64_t *x_ptr, int32_t *x_idx);
 
 afmpb_status afmpb_get_info(const afmpb_t *h, afmpb_info *info);
+
+/* The tuner's report; ESTATE when the handle was not built with AFMPB_LEAF_CAP_AUTO or its
+ * size class was already tuned (then info.autotuned = 0). */
+afmpb_status afmpb_get_autotune(const afmpb_t *h, afmpb_autotune_report *report);
 
 /* Time the stages of the product on the handle's stream: reps products run stage by
  * stage (not as a graph, P2P serialised after the far field) with CUDA events between

@@ -58,7 +58,20 @@ class Info(C.Structure):
                 ("n_m2l_pairs", C.c_int64), ("order", C.c_int), ("precision", C.c_int),
                 ("device_bytes", C.c_int64), ("root_center", C.c_double * 3),
                 ("root_half_width", C.c_double), ("ms_create", C.c_double * 6),
-                ("m2l_rank", C.c_int), ("m2l_tables", C.c_int), ("device_bytes_peak", C.c_int64)]
+                ("m2l_rank", C.c_int), ("m2l_tables", C.c_int), ("device_bytes_peak", C.c_int64),
+                ("leaf_cap", C.c_int), ("autotuned", C.c_int)]
+
+
+AUTOTUNE_MAX = 16
+LEAF_CAP_AUTO = -1
+
+
+class AutotuneReport(C.Structure):
+    _fields_ = [("n_candidates", C.c_int), ("cap", C.c_int * AUTOTUNE_MAX),
+                ("p2p_ms", C.c_double * AUTOTUNE_MAX), ("predicted_ms", C.c_double * AUTOTUNE_MAX),
+                ("start_cap", C.c_int), ("best_cap", C.c_int), ("predicted_start_ms", C.c_double),
+                ("predicted_best_ms", C.c_double), ("ms_per_m2l_pair", C.c_double),
+                ("ms_per_box", C.c_double), ("ms_rest", C.c_double), ("ms_tuning", C.c_double)]
 
 
 class Profile(C.Structure):
@@ -99,7 +112,7 @@ EXPORTS = ["afmpb_create", "afmpb_matvec", "afmpb_matvec_parts", "afmpb_matvec_h
            "afmpb_get_info", "afmpb_destroy", "afmpb_last_error", "afmpb_estimate_bytes",
            "afmpb_version", "afmpb_profile_product", "afmpb_energy_noalloc",
            "afmpb_server_create", "afmpb_server_submit", "afmpb_server_poll", "afmpb_server_wait",
-           "afmpb_server_get_info", "afmpb_server_destroy"]
+           "afmpb_server_get_info", "afmpb_server_destroy", "afmpb_get_autotune"]
 
 
 def library_path() -> str:
@@ -131,6 +144,8 @@ def load(build: bool = True):
     lib.afmpb_energy.argtypes = [P, C.POINTER(D)]
     lib.afmpb_energy_noalloc.restype = I32
     lib.afmpb_energy_noalloc.argtypes = [P, C.POINTER(D)]
+    lib.afmpb_get_autotune.restype = I32
+    lib.afmpb_get_autotune.argtypes = [P, C.POINTER(AutotuneReport)]
     lib.afmpb_server_create.restype = I32
     lib.afmpb_server_create.argtypes = [C.c_size_t, C.c_int, C.POINTER(P)]
     lib.afmpb_server_submit.restype = I32
@@ -288,6 +303,19 @@ class Handle:
         i = Info()
         _check(self._lib.afmpb_get_info(self.h, C.byref(i)), self.h)
         return _struct_dict(i)
+
+    def autotune(self):
+        """The leaf-capacity tuner's report (None unless this handle ran the tuner)."""
+        r = AutotuneReport()
+        rc = self._lib.afmpb_get_autotune(self.h, C.byref(r))
+        if rc == 8:
+            return None
+        _check(rc, self.h)
+        k = r.n_candidates
+        d = _struct_dict(r)
+        for key in ("cap", "p2p_ms", "predicted_ms"):
+            d[key] = d[key][:k]
+        return d
 
     def geometry(self):
         a = np.zeros(self.n)

@@ -81,7 +81,7 @@ Err check_params(const afmpb_mesh *mesh, double eps_in, double eps_out, double k
   if (order < 2 || order > kMaxOrder) return make_err(AFMPB_EINVAL, "fmm_order must be in [2, 8]");
   if (!(tol > 0) || !std::isfinite(tol)) return make_err(AFMPB_EINVAL, "tol must be positive");
   if (o) {
-    if (o->leaf_cap < 0 || o->restart < 0 || o->max_restart < 0 || o->max_level < 0 || o->max_level > kMaxLevel)
+    if ((o->leaf_cap < 0 && o->leaf_cap != AFMPB_LEAF_CAP_AUTO) || o->restart < 0 || o->max_restart < 0 || o->max_level < 0 || o->max_level > kMaxLevel)
       return make_err(AFMPB_EINVAL, "negative option or max_level above 20");
     if (o->abs_tol < 0 || !(o->near_c >= 0)) return make_err(AFMPB_EINVAL, "abs_tol and near_c must be >= 0");
     if (o->precision != 0 && o->precision != 1) return make_err(AFMPB_EINVAL, "precision must be 0 or 1");
@@ -163,6 +163,42 @@ Err product_sorted(afmpb_t *h, cudaStream_t s, int parts) {
 }
 }  // namespace afmpb
 
+namespace {
+
+int default_leaf_cap(int precision) { return precision == 1 ? 80 : 192; }
+
+Err build_handle(const afmpb_mesh *mesh, const afmpb_charges *charges, double eps_in, double eps_out, double kappa,
+                 int fmm_order, double tol, const afmpb_options *options, int leaf_cap, afmpb_t **out) {
+  afmpb_t *h = new (std::nothrow) afmpb_t();
+  if (!h) return make_err(AFMPB_ENOMEM, "host allocation of the handle failed");
+  h->n = mesh->n_nodes;
+  h->nt = mesh->n_tris;
+  h->eps_in = eps_in;
+  h->eps_out = eps_out;
+  h->kappa = kappa;
+  h->ebar = eps_out / eps_in;
+  h->alpha = 0.5 / h->ebar + 0.5;
+  h->tol = tol;
+  h->order = fmm_order;
+  h->ncoef = fmm_order * fmm_order * fmm_order;
+  if (options) h->opt = *options;
+  h->opt.leaf_cap = leaf_cap;
+  if (h->opt.restart == 0) h->opt.restart = 80;
+  if (h->opt.max_restart == 0 && !(options && options->max_restart == 0 && options->restart != 0)) h->opt.max_restart = 5;
+  if (h->opt.near_c == 0) h->opt.near_c = 2.0;
+  if (h->opt.max_level == 0) h->opt.max_level = kMaxLevel;
+  if (h->opt.m2l_tol == 0) h->opt.m2l_tol = 1e-5;
+  Err e = create_impl(h, mesh, charges);
+  if (!e.ok()) {
+    destroy_handle(h);
+    return e;
+  }
+  *out = h;
+  return Err{};
+}
+
+}  // namespace
+
 extern "C" {
 
 afmpb_status afmpb_create(const afmpb_mesh *mesh, const afmpb_charges *charges, double eps_in, double eps_out,
@@ -176,30 +212,32 @@ afmpb_status afmpb_create(const afmpb_mesh *mesh, const afmpb_charges *charges, 
   if (charges && charges->n < 0) return fail(nullptr, make_err(AFMPB_EINVAL, "charges->n < 0"));
   e = validate_mesh(mesh);
   if (!e.ok()) return fail(nullptr, e);
-  afmpb_t *h = new (std::nothrow) afmpb_t();
-  if (!h) return fail(nullptr, make_err(AFMPB_ENOMEM, "host allocation of the handle failed"));
-  h->n = mesh->n_nodes;
-  h->nt = mesh->n_tris;
-  h->eps_in = eps_in;
-  h->eps_out = eps_out;
-  h->kappa = kappa;
-  h->ebar = eps_out / eps_in;
-  h->alpha = 0.5 / h->ebar + 0.5;
-  h->tol = tol;
-  h->order = fmm_order;
-  h->ncoef = fmm_order * fmm_order * fmm_order;
-  if (options) h->opt = *options;
-  if (h->opt.leaf_cap == 0) h->opt.leaf_cap = 128;
-  if (h->opt.restart == 0) h->opt.restart = 80;
-  if (h->opt.max_restart == 0 && !(options && options->max_restart == 0 && options->restart != 0)) h->opt.max_restart = 5;
-  if (h->opt.near_c == 0) h->opt.near_c = 2.0;
-  if (h->opt.max_level == 0) h->opt.max_level = kMaxLevel;
-  if (h->opt.m2l_tol == 0) h->opt.m2l_tol = 1e-5;
-  e = create_impl(h, mesh, charges);
-  if (!e.ok()) {
-    g_err = e.msg;
-    destroy_handle(h);
-    return e.code;
+  const int prec = options ? options->precision : 0;
+  const bool tune = options && options->leaf_cap == AFMPB_LEAF_CAP_AUTO;
+  int cap = (options && options->leaf_cap > 0) ? options->leaf_cap : default_leaf_cap(prec);
+  int cached = 0;
+  if (tune) {
+    cached = autotune_cached_cap(prec, fmm_order, kappa, mesh->n_nodes);
+    if (cached) cap = cached;
+  }
+  afmpb_t *h = nullptr;
+  e = build_handle(mesh, charges, eps_in, eps_out, kappa, fmm_order, tol, options, cap, &h);
+  if (!e.ok()) return fail(nullptr, e);
+  if (tune && !cached) {
+    afmpb_autotune_report rep{};
+    e = autotune_leaf_cap(h, &rep);
+    if (!e.ok()) {
+      destroy_handle(h);
+      return fail(nullptr, e);
+    }
+    if (rep.best_cap != cap && rep.predicted_best_ms < 0.97 * rep.predicted_start_ms) {
+      destroy_handle(h);
+      h = nullptr;
+      e = build_handle(mesh, charges, eps_in, eps_out, kappa, fmm_order, tol, options, rep.best_cap, &h);
+      if (!e.ok()) return fail(nullptr, e);
+    }
+    h->autotuned = true;
+    h->tune = rep;
   }
   *out = h;
   return AFMPB_OK;
@@ -408,8 +446,17 @@ afmpb_status afmpb_get_info(const afmpb_t *h, afmpb_info *info) {
   info->root_half_width = T.w0;
   for (int i = 0; i < 6; ++i) info->ms_create[i] = h->ms_create[i];
   info->device_bytes_peak = (int64_t)h->arena.peak;
+  info->leaf_cap = h->opt.leaf_cap;
+  info->autotuned = h->autotuned ? 1 : 0;
   info->m2l_rank = h->m2l_rank;
   info->m2l_tables = h->m2l_ntables;
+  return AFMPB_OK;
+}
+
+afmpb_status afmpb_get_autotune(const afmpb_t *h, afmpb_autotune_report *r) {
+  if (!h || !r) return AFMPB_EINVAL;
+  if (!h->autotuned) return AFMPB_ESTATE;
+  *r = h->tune;
   return AFMPB_OK;
 }
 
@@ -509,7 +556,9 @@ const char *afmpb_last_error(const afmpb_t *h) { return h ? h->err.c_str() : g_e
 
 size_t afmpb_estimate_bytes(int64_t n_nodes, int64_t n_atoms, int fmm_order, const afmpb_options *o) {
   if (n_nodes <= 0 || fmm_order < 2 || fmm_order > kMaxOrder) return 0;
-  const int cap = (o && o->leaf_cap > 0) ? o->leaf_cap : 128;
+  // the smallest candidate of the autotuner gives the most boxes
+  const int cap = (o && o->leaf_cap > 0) ? o->leaf_cap
+                  : (o && o->leaf_cap == AFMPB_LEAF_CAP_AUTO) ? 32 : ((o && o->precision == 1) ? 80 : 192);
   const int m = (o && o->restart > 0) ? o->restart : 80;
   const size_t n = (size_t)n_nodes, n3 = (size_t)fmm_order * fmm_order * fmm_order;
   const size_t nbox = 3 * (n / (size_t)std::max(cap / 2, 1) + 64);

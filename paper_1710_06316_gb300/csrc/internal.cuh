@@ -277,6 +277,10 @@ struct afmpb_t {
   int *d_tc_level_table = nullptr; // level -> Yukawa tile table
   int *d_tc_flag = nullptr;        // set by a tensor-core CTA whose bounded wait expired
 
+  // ---- leaf-capacity autotuner (AFMPB_LEAF_CAP_AUTO) --------------------------------
+  bool autotuned = false;
+  afmpb_autotune_report tune{};
+
   // ---- per-product work --------------------------------------------------------------
   float2 *d_xs = nullptr;          // [n] (f, h) Morton order
   float *d_ys = nullptr;           // [2n] y Morton order
@@ -316,6 +320,9 @@ Err enqueue_p2p(afmpb_t *h, cudaStream_t s);          // P2P into d_phi_near
 Err enqueue_combine(afmpb_t *h, cudaStream_t s, int parts);
 Err enqueue_m2l_tc(afmpb_t *h, cudaStream_t s);       // tensor-core M2L (precision 1)
 Err build_m2l_tc(afmpb_t *h);
+// autotune.cu
+Err autotune_leaf_cap(afmpb_t *h, afmpb_autotune_report *rep);
+int autotune_cached_cap(int precision, int order, double kappa, int64_t n);   // 0 if none
 // m2l_svd.cu: compressed translations; *compressed = false leaves the full ones in use
 Err build_m2l_svd(afmpb_t *h, bool *compressed);
 Err enqueue_m2l_svd(afmpb_t *h, cudaStream_t s);      // compress, translate, expand
