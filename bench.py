@@ -57,12 +57,78 @@ def workload_desc(mol):
             % (mol.name, mol.n_nodes, mol.n_tris, len(mol.q), mol.eps_in, mol.eps_out, mol.kappa)}
 
 
-def run_config(mol, args, world):
+def run_config(mol, args, world, leaf_cap=None):
     return dict(workload_desc(mol), fmm_order=args.order,
-                leaf_cap=args.leaf_cap if args.leaf_cap else 128,
+                leaf_cap=leaf_cap if leaf_cap else (args.leaf_cap or "library default"),
                 precision=["fp32", "mixed: tensor-core M2L"][args.precision],
                 l2="flushed between timed products (512 MB write)",
                 parallelism="replicas" if world > 1 else "single")
+
+
+# ------------------------------------------------------------------------------------
+# serving: many molecules of uneven size through the continuous-batching server
+# ------------------------------------------------------------------------------------
+def serving_leg(args):
+    """Solve requests on synthetic globules (atom counts log-uniform in [40, 1200], so
+    meshes of ~5k-120k nodes; kappa ~ U(0.03, 0.3)), drawn from a pool of seeded
+    molecules.  Three runs: the plain FP32 path one solve at a time (closed loop: each
+    request is submitted when the previous one has finished); the mixed path served with
+    all requests submitted at once (capacity); the mixed path served under Poisson
+    arrivals at 0.9x the plain capacity (latency, queueing included)."""
+    import numpy as np
+
+    import paper_1710_06316_gb300 as pb
+    import synthetic
+
+    rng = np.random.default_rng(synthetic.SEED_BASE + 3)
+    counts = np.exp(rng.uniform(np.log(40), np.log(1200), args.serve_pool)).astype(int)
+    t0 = time.perf_counter()
+    pool = [synthetic.globule(n_atoms=int(c), index=100 + i) for i, c in enumerate(counts)]
+    t_gen = time.perf_counter() - t0
+    reqs = [(int(rng.integers(len(pool))), float(rng.uniform(0.03, 0.3))) for _ in range(args.serve_requests)]
+    arrivals = np.cumsum(rng.exponential(1.0, len(reqs)))      # unit-rate gaps, scaled below
+
+    def run(precision, slots, rate=None, closed_loop=False):
+        with pb.Server(bytes_budget=int(args.serve_budget_gb * (1 << 30)), max_slots=slots) as srv:
+            start = time.perf_counter()
+            tickets, res = [], []
+            for k, (i, kap) in enumerate(reqs):
+                if rate:
+                    delay = start + arrivals[k] / rate - time.perf_counter()
+                    if delay > 0:
+                        time.sleep(delay)
+                m = pool[i]
+                tickets.append(srv.submit(m.xyz, m.tri, m.atoms, m.q, m.eps_in, m.eps_out, kap,
+                                          order=args.order, tol=1e-6, precision=precision,
+                                          restart=args.serve_restart, max_restart=5))
+                if closed_loop:
+                    res.append(srv.wait(tickets[-1], 3600))
+            if not closed_loop:
+                res = [srv.wait(t, 3600) for t in tickets]
+            wall = time.perf_counter() - start
+            info = srv.info()
+        bad = [(r["status"], r["error"]) for r in res if r["status"] != "OK"]
+        lat = sorted(1e3 * r["latency"] for r in res)
+        pq = lambda q: lat[min(len(lat) - 1, int(round(q * (len(lat) - 1))))]
+        return {"solves_per_s": round(len(res) / wall, 3), "p50_ms": round(pq(0.5), 1),
+                "p99_ms": round(pq(0.99), 1), "wall_s": round(wall, 2), "failed": len(bad), "failures": bad[:3],
+                "iters_max": max(r["info"]["iters"] for r in res),
+                "max_running": info["max_running"], "reserved_high_water_gb": round(info["bytes_high_water"] / 2**30, 2),
+                "slots": slots}, [r["energy"] for r in res]
+
+    plain, e_plain = run(0, 1, closed_loop=True)
+    burst, e_mixed = run(1, args.serve_slots)
+    rate = 0.9 * plain["solves_per_s"]
+    poisson, _ = run(1, args.serve_slots, rate=rate)
+    poisson["arrival_rate_per_s"] = round(rate, 3)
+    diff = max((abs(a / b - 1) for a, b in zip(e_mixed, e_plain) if a and b), default=None)
+    return {"workload": "%d requests over %d synthetic globules (%d-%d nodes), kappa U(0.03, 0.3), order %d, "
+                        "GMRES(%d) tol 1e-6, each request = setup + solve + energy" % (
+                            len(reqs), len(pool), min(m.n_nodes for m in pool), max(m.n_nodes for m in pool), args.order,
+                            args.serve_restart),
+            "pool_nodes": [m.n_nodes for m in pool], "pool_generation_s": round(t_gen, 1),
+            "plain_fp32_one_at_a_time": plain, "mixed_served_burst": burst, "mixed_served_poisson": poisson,
+            "energy_max_rel_diff_mixed_vs_plain": diff}
 
 
 # ------------------------------------------------------------------------------------
@@ -365,7 +431,7 @@ def run_gpu(args):
         ms_p, _ = timed_products(hp, max(5, args.steps // 4), args.warmup)
         lat_p, (sinfo_p, energy_p) = solve_latency(hp, args.solve_reps)
         plain = {"value": round(world * n / (ms_p * 1e-3) / 1e6, 3), "unit": UNIT, "ms_per_step": round(ms_p, 5),
-                 "leaf_cap": args.plain_leaf_cap, "solve": lat_p, "energy_kcal_mol": energy_p,
+                 "leaf_cap": hp.info()["leaf_cap"], "solve": lat_p, "energy_kcal_mol": energy_p,
                  "energy_rel_diff_vs_mixed": abs(energy_p / energy - 1) if energy else None}
         hp.close()
 
@@ -373,7 +439,7 @@ def run_gpu(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 5),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if args.precision == 0 else "f32+bf16x3", "data": "synthetic",
-            "config": run_config(mol, args, world),
+            "config": run_config(mol, args, world, info["leaf_cap"]),
             "e2e": {k: (round(v, 4) if isinstance(v, float) else v) for k, v in e2e.items()},
             "roofline": roof,
             "gpu_launches": int(prof["kernels_per_product"]) * args.steps,
@@ -392,6 +458,8 @@ def run_gpu(args):
         e_ref = kirkwood_energy(mol.atoms, mol.q, mol.meta["radius"], mol.eps_in, mol.eps_out, mol.kappa)
         line["solve"]["kirkwood_series_kcal_mol"] = e_ref
         line["solve"]["energy_rel_err_vs_series"] = abs(energy / e_ref - 1)
+    if rank == 0 and world == 1 and not args.no_serving:
+        line["serving"] = serving_leg(args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, cores, nrow, dt = oracle_rows_rate(mol, rows_target_s=args.cpu_seconds)
         line["cpu_baseline"] = {"value": round(rate / 1e6, 6), "unit": UNIT, "cores": cores, "kind": "oracle",
@@ -414,7 +482,13 @@ def main():
     ap.add_argument("--order", type=int, default=6)
     ap.add_argument("--leaf-cap", type=int, default=0)
     ap.add_argument("--precision", type=int, default=1, choices=[0, 1])
-    ap.add_argument("--plain-leaf-cap", type=int, default=256)
+    ap.add_argument("--plain-leaf-cap", type=int, default=0)
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serve-pool", type=int, default=8)
+    ap.add_argument("--serve-requests", type=int, default=24)
+    ap.add_argument("--serve-slots", type=int, default=4)
+    ap.add_argument("--serve-budget-gb", type=float, default=96.0)
+    ap.add_argument("--serve-restart", type=int, default=200)
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--solve-reps", type=int, default=5)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)

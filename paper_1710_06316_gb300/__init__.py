@@ -392,7 +392,7 @@ class Server:
         self._keep = {}          # ticket -> output buffers that the server writes into
 
     def submit(self, xyz, tri, atoms, q, eps_in=1.0, eps_out=80.0, kappa=0.0, order=6, tol=1e-6,
-               precision=0, leaf_cap=0, m2l_tol=0.0, want_solution=False):
+               precision=0, leaf_cap=0, m2l_tol=0.0, restart=0, max_restart=0, want_solution=False):
         xyz = _np(xyz, np.float64)
         tri = _np(tri, np.int32)
         atoms = _np(np.atleast_2d(atoms), np.float64)
@@ -403,7 +403,8 @@ class Server:
         req = Request(Mesh(n, int(tri.shape[0]), xyz.ctypes.data, tri.ctypes.data, None),
                       Charges(int(q.size), atoms.ctypes.data, q.ctypes.data),
                       float(eps_in), float(eps_out), float(kappa), int(order), float(tol),
-                      Options(int(leaf_cap), 0, 0, 0.0, int(precision), 0.0, None, 0, float(m2l_tol)),
+                      Options(int(leaf_cap), int(restart), int(max_restart), 0.0, int(precision), 0.0, None, 0,
+                              float(m2l_tol)),
                       None if f is None else f.ctypes.data, None if hh is None else hh.ctypes.data)
         t = C.c_int64()
         rc = self._lib.afmpb_server_submit(self.s, C.byref(req), C.byref(t))
