@@ -15,9 +15,15 @@
 // integrands vanish and A, D are weakly singular; polar (Duffy) map about x_p with a
 // 16 x 16 Gauss-Legendre rule.
 //
+// Scheduling: self entries take one thread per node.  Off-diagonal entries are handed to
+// lanes by a global counter, and each lane's adaptive walk is split into a cheap
+// advance-to-next-leaf phase and a leaf-evaluation phase that the whole warp runs
+// together (a lane per row with each lane walking its own tree left ~3 of 32 lanes busy).
+//
 // Precision: all geometry is first taken relative to the target x_p in FP64 (so no
 // large-coordinate cancellation reaches the quadrature), then the quadrature runs in
 // FP32 (the `Real` template parameter; GB300's FP32 rate is many times its FP64 rate).
+#include <algorithm>
 #include <cmath>
 
 #include <mutex>
@@ -93,53 +99,6 @@ __device__ __forceinline__ void abcd_point(Real kappa, Real ebar, const V3<Real>
   o[3] = (nn0 * G3 * p1 - ndn * n0d * G5 * p2) / ebar;
 }
 
-// Adaptive Radon quadrature over triangle (v0, v1, v2) for a target at the origin,
-// stackless walk of the 1 -> 4 subdivision tree (path digits), accumulating into acc.
-template <class Real>
-__device__ void quad_triangle(Real kappa, Real ebar, const V3<Real> &n0, const V3<Real> &v0, const V3<Real> &v1,
-                              const V3<Real> &v2, const V3<Real> &ns, Real acc[4]) {
-  int dig[kQuadDepth + 1];
-  int d = 0;
-  dig[0] = 0;
-  while (true) {
-    V3<Real> a = v0, b = v1, c = v2;
-    for (int l = 1; l <= d; ++l) {
-      const V3<Real> mab{Real(0.5) * (a.x + b.x), Real(0.5) * (a.y + b.y), Real(0.5) * (a.z + b.z)};
-      const V3<Real> mbc{Real(0.5) * (b.x + c.x), Real(0.5) * (b.y + c.y), Real(0.5) * (b.z + c.z)};
-      const V3<Real> mca{Real(0.5) * (c.x + a.x), Real(0.5) * (c.y + a.y), Real(0.5) * (c.z + a.z)};
-      switch (dig[l]) {
-        case 0: b = mab; c = mca; break;
-        case 1: a = mab; c = mbc; break;
-        case 2: a = mca; b = mbc; break;
-        default: a = mab; b = mbc; c = mca; break;
-      }
-    }
-    const V3<Real> e01{b.x - a.x, b.y - a.y, b.z - a.z}, e12{c.x - b.x, c.y - b.y, c.z - b.z},
-        e02{c.x - a.x, c.y - a.y, c.z - a.z};
-    const Real diam = sqrt(fmax(dot(e01, e01), fmax(dot(e12, e12), dot(e02, e02))));
-    const V3<Real> g{(a.x + b.x + c.x) / Real(3), (a.y + b.y + c.y) / Real(3), (a.z + b.z + c.z) / Real(3)};
-    if (d < kQuadDepth && sqrt(dot(g, g)) < Real(3) * diam) {
-      ++d;
-      dig[d] = 0;
-      continue;
-    }
-    const V3<Real> cr{e01.y * e02.z - e01.z * e02.y, e01.z * e02.x - e01.x * e02.z, e01.x * e02.y - e01.y * e02.x};
-    const Real area = Real(0.5) * sqrt(dot(cr, cr));
-    for (int q = 0; q < 7; ++q) {
-      const Real b0 = c_rad_bf[3 * q], b1 = c_rad_bf[3 * q + 1], b2 = c_rad_bf[3 * q + 2];
-      const V3<Real> dq{-(b0 * a.x + b1 * b.x + b2 * c.x), -(b0 * a.y + b1 * b.y + b2 * c.y),
-                        -(b0 * a.z + b1 * b.z + b2 * c.z)};
-      Real o[4];
-      abcd_point(kappa, ebar, dq, n0, ns, o);
-      const Real w = area * c_rad_wf[q];
-      for (int k = 0; k < 4; ++k) acc[k] += w * o[k];
-    }
-    while (d > 0 && dig[d] == 3) --d;
-    if (d == 0) break;
-    ++dig[d];
-  }
-}
-
 // Corners of triangle t rotated so that node v comes first, relative to the point o
 // (difference taken in FP64).
 template <class Real>
@@ -151,25 +110,6 @@ __device__ __forceinline__ void tri_rel(const double *xyz, const int32_t *tri, i
   for (int j = 0; j < 3; ++j) {
     const double *q = xyz + 3 * (int64_t)tri[3 * t + (k0 + j) % 3];
     P[j] = V3<Real>{(Real)(q[0] - o[0]), (Real)(q[1] - o[1]), (Real)(q[2] - o[2])};
-  }
-}
-
-template <class Real>
-__device__ void near_rule(Real kappa, Real ebar, const double *xyz, const int32_t *tri, const int64_t *inc_ptr,
-                          const int32_t *inc_tri, const double *tri_nrm, const double *xp, const V3<Real> &np,
-                          int64_t ot, Real acc[4]) {
-  for (int64_t j = inc_ptr[ot]; j < inc_ptr[ot + 1]; ++j) {
-    const int32_t T = inc_tri[j];
-    V3<Real> P[3];
-    tri_rel(xyz, tri, T, ot, xp, P);
-    const V3<Real> ma{Real(0.5) * (P[0].x + P[1].x), Real(0.5) * (P[0].y + P[1].y), Real(0.5) * (P[0].z + P[1].z)};
-    const V3<Real> mb{Real(0.5) * (P[0].x + P[2].x), Real(0.5) * (P[0].y + P[2].y), Real(0.5) * (P[0].z + P[2].z)};
-    const V3<Real> cen{(P[0].x + P[1].x + P[2].x) / Real(3), (P[0].y + P[1].y + P[2].y) / Real(3),
-                       (P[0].z + P[1].z + P[2].z) / Real(3)};
-    const double *tn = tri_nrm + 3 * (int64_t)T;
-    const V3<Real> ns{(Real)tn[0], (Real)tn[1], (Real)tn[2]};
-    quad_triangle(kappa, ebar, np, P[0], ma, cen, ns, acc);
-    quad_triangle(kappa, ebar, np, P[0], cen, mb, ns, acc);
   }
 }
 
@@ -270,7 +210,31 @@ __global__ void k_near_search(int64_t n, double cnear, const int32_t *__restrict
   if (!fill) cnt[p] = k;
 }
 
-// What the P2P pass sees of a pair: its source lists and the FP32 node data.
+// Self entries (t == p): one thread per node; the fixed 16 x 16 rule keeps the lanes
+// of a warp together.  Columns of a row are in ascending Morton order.
+__global__ void __launch_bounds__(128) k_near_self(int64_t n, KernelParams kp, const int32_t *__restrict__ perm,
+                                                   const double *__restrict__ xyz, const int32_t *__restrict__ tri,
+                                                   const int64_t *__restrict__ inc_ptr,
+                                                   const int32_t *__restrict__ inc_tri, const double *__restrict__ nrm,
+                                                   const int64_t *__restrict__ ptr, const int32_t *__restrict__ col,
+                                                   float4 *__restrict__ coef, uint8_t *__restrict__ full) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  int64_t lo = ptr[p], hi = ptr[p + 1] - 1;
+  while (lo < hi) {                           // the diagonal entry
+    const int64_t mid = (lo + hi) >> 1;
+    if (col[mid] < p) lo = mid + 1; else hi = mid;
+  }
+  const int64_t op = perm[p];
+  const V3<float> np{(float)nrm[3 * op], (float)nrm[3 * op + 1], (float)nrm[3 * op + 2]};
+  float o[4] = {0, 0, 0, 0};
+  self_rule((float)kp.kappa, (float)kp.ebar, xyz, tri, inc_ptr, inc_tri, op, np, o);
+  coef[lo] = make_float4(o[0], o[1], o[2], o[3]);
+  full[lo] = 1;
+}
+
+// What the P2P pass sees of a pair: its source lists (ascending per leaf) and the FP32
+// node data.
 struct P2PView {
   const int32_t *node_leaf, *leaf_index, *pidx;
   const int64_t *pptr;
@@ -279,66 +243,172 @@ struct P2PView {
   float skip_scale;
 };
 
-// Coefficients, one warp per row.  An entry is the near rule minus the point rule, except
-// where the P2P pass leaves the pair out (the self entry among them): there it is the
-// whole near-rule value and `full` is set.
-template <class Real>
-__global__ void __launch_bounds__(128) k_near_coef(int64_t n, KernelParams kp, const int32_t *__restrict__ perm,
-                                                   const double *__restrict__ xyz, const int32_t *__restrict__ tri,
-                                                   const int64_t *__restrict__ inc_ptr,
-                                                   const int32_t *__restrict__ inc_tri,
-                                                   const double *__restrict__ tri_nrm, const double *__restrict__ area,
-                                                   const double *__restrict__ nrm, const int64_t *__restrict__ ptr,
-                                                   const int32_t *__restrict__ col, P2PView pv,
-                                                   float4 *__restrict__ coef, uint8_t *__restrict__ full) {
-  const int64_t p = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (p >= n) return;
-  const int64_t op = perm[p];
-  const double *xp = xyz + 3 * op;
-  const V3<Real> np{(Real)nrm[3 * op], (Real)nrm[3 * op + 1], (Real)nrm[3 * op + 2]};
-  const Real kappa = (Real)kp.kappa, ebar = (Real)kp.ebar;
-  const int lp = pv.node_leaf[p];
-  const dbl4 cp = pv.center[lp];
-  const float4 xp32 = pv.pos[p];
-  const float rsp = p2p_skip_radius(pv.skip_scale, pv.nrm[p].w);
-  const int64_t l0 = pv.pptr[pv.leaf_index[lp]], l1 = pv.pptr[pv.leaf_index[lp] + 1];
-  for (int64_t j = ptr[p] + lane; j < ptr[p + 1]; j += 32) {
-    const int t = col[j];
-    const int64_t ot = perm[t];
-    Real o[4] = {0, 0, 0, 0};
-    bool whole = true;
-    if (t == p) {
-      self_rule(kappa, ebar, xyz, tri, inc_ptr, inc_tri, op, np, o);
-    } else {
-      near_rule(kappa, ebar, xyz, tri, inc_ptr, inc_tri, tri_nrm, xp, np, ot, o);
-      // Replay the P2P pass's FP32 distance test: when it evaluates this pair, the far
-      // rule is already in the product and the entry is the correction.
-      const int lt = pv.node_leaf[t];
-      bool listed = false;
-      for (int64_t k = l0; k < l1 && !listed; ++k) listed = pv.pidx[k] == lt;
-      if (listed) {
-        const dbl4 ct = pv.center[lt];
-        const float4 y = pv.pos[t];
-        const float dx = xp32.x - p2p_shift(y.x, ct.x, cp.x), dy = xp32.y - p2p_shift(y.y, ct.y, cp.y),
-                    dz = xp32.z - p2p_shift(y.z, ct.z, cp.z);
-        whole = !p2p_evaluates(p2p_r2(dx, dy, dz), rsp, p2p_skip_radius(pv.skip_scale, pv.nrm[t].w));
+// Replays the P2P pass's FP32 distance test for target p and source t: true when the
+// pass leaves the pair out (then the entry holds the whole near-rule value).
+__device__ __forceinline__ bool p2p_leaves_out(const P2PView &pv, int p, int t) {
+  const int lp = pv.node_leaf[p], lt = pv.node_leaf[t];
+  const int li = pv.leaf_index[lp];
+  int64_t lo = pv.pptr[li], hi = pv.pptr[li + 1];
+  while (lo < hi) {                           // is leaf lt a P2P source of leaf lp?
+    const int64_t mid = (lo + hi) >> 1;
+    if (pv.pidx[mid] < lt) lo = mid + 1; else hi = mid;
+  }
+  if (lo == pv.pptr[li + 1] || pv.pidx[lo] != lt) return false;   // far-field pair
+  const dbl4 cp = pv.center[lp], ct = pv.center[lt];
+  const float4 xp = pv.pos[p], y = pv.pos[t];
+  const float dx = xp.x - p2p_shift(y.x, ct.x, cp.x), dy = xp.y - p2p_shift(y.y, ct.y, cp.y),
+              dz = xp.z - p2p_shift(y.z, ct.z, cp.z);
+  return !p2p_evaluates(p2p_r2(dx, dy, dz), p2p_skip_radius(pv.skip_scale, pv.nrm[p].w),
+                        p2p_skip_radius(pv.skip_scale, pv.nrm[t].w));
+}
+
+// Off-diagonal entries (t != p).  An entry is the near rule minus the point rule, except
+// where the P2P pass leaves the pair out: there it is the whole near-rule value and `full`
+// is set.  Lanes take entries from a global counter.  For its entry a lane walks the
+// adaptive subdivision tree of every patch piece of t (the same rule and order as a
+// recursive walk: pieces by incident triangle, depth first), but the walk is split in two
+// phases per step so that the warp stays together where the work is: every lane first
+// advances its own walk to its next leaf sub-triangle (cheap, divergent), then all lanes
+// evaluate their leaves' 7 quadrature points at once.  The path of the walk is kept as
+// 2-bit digits in a register.
+__global__ void __launch_bounds__(128) k_near_pairs(int64_t nnz, const int32_t *__restrict__ row,
+                                                    unsigned long long *__restrict__ counter, KernelParams kp,
+                                                    const int32_t *__restrict__ perm, const double *__restrict__ xyz,
+                                                    const int32_t *__restrict__ tri,
+                                                    const int64_t *__restrict__ inc_ptr,
+                                                    const int32_t *__restrict__ inc_tri,
+                                                    const double *__restrict__ tri_nrm, const double *__restrict__ area,
+                                                    const double *__restrict__ nrm, const int32_t *__restrict__ col,
+                                                    P2PView pv, float4 *__restrict__ coef,
+                                                    uint8_t *__restrict__ full) {
+  const float kappa = (float)kp.kappa, ebar = (float)kp.ebar;
+  bool done = false, in_pair = false, in_piece = false, have = false, whole = false;
+  int64_t e = 0, tj = 0, tend = 0, op = 0, ot = 0;
+  int half = 0, d = 0;
+  uint32_t path = 0;                          // digit of level l in bits 2(l-1) .. 2l-1
+  V3<float> np{0, 0, 0}, ns{0, 0, 0}, R0{0, 0, 0}, R1{0, 0, 0}, R2{0, 0, 0};
+  V3<float> la{0, 0, 0}, lb{0, 0, 0}, lc{0, 0, 0};
+  float larea = 0.f, acc[4] = {0, 0, 0, 0};
+  while (true) {
+    // phase 1: advance to the next leaf (or the next entry)
+    while (!have && !done) {
+      if (!in_pair) {
+        e = (int64_t)atomicAdd(counter, 1ULL);
+        if (e >= nnz) {
+          done = true;
+          break;
+        }
+        const int p = row[e], t = col[e];
+        if (t == p) continue;                 // diagonal: k_near_self
+        op = perm[p];
+        ot = perm[t];
+        np = V3<float>{(float)nrm[3 * op], (float)nrm[3 * op + 1], (float)nrm[3 * op + 2]};
+        whole = p2p_leaves_out(pv, p, t);
+        tj = inc_ptr[ot];
+        tend = inc_ptr[ot + 1];
+        half = 0;
+        in_piece = false;
+        acc[0] = acc[1] = acc[2] = acc[3] = 0.f;
+        in_pair = true;
+      }
+      if (!in_piece) {
+        if (tj >= tend) {                     // entry finished
+          float o[4] = {acc[0], acc[1], acc[2], acc[3]};
+          if (!whole) {
+            const double *xp = xyz + 3 * op, *xt = xyz + 3 * ot;
+            const V3<float> dd{(float)(xp[0] - xt[0]), (float)(xp[1] - xt[1]), (float)(xp[2] - xt[2])};
+            const V3<float> nt{(float)nrm[3 * ot], (float)nrm[3 * ot + 1], (float)nrm[3 * ot + 2]};
+            float f[4];
+            abcd_point(kappa, ebar, dd, np, nt, f);
+            const float at = (float)area[ot];
+            for (int k = 0; k < 4; ++k) o[k] -= at * f[k];
+          }
+          coef[e] = make_float4(o[0], o[1], o[2], o[3]);
+          full[e] = whole ? 1 : 0;
+          in_pair = false;
+          continue;
+        }
+        const int32_t T = inc_tri[tj];
+        V3<float> P[3];
+        tri_rel(xyz, tri, T, ot, xyz + 3 * op, P);
+        const V3<float> ma{0.5f * (P[0].x + P[1].x), 0.5f * (P[0].y + P[1].y), 0.5f * (P[0].z + P[1].z)};
+        const V3<float> mb{0.5f * (P[0].x + P[2].x), 0.5f * (P[0].y + P[2].y), 0.5f * (P[0].z + P[2].z)};
+        const V3<float> cen{(P[0].x + P[1].x + P[2].x) / 3.0f, (P[0].y + P[1].y + P[2].y) / 3.0f,
+                            (P[0].z + P[1].z + P[2].z) / 3.0f};
+        const double *tn = tri_nrm + 3 * (int64_t)T;
+        ns = V3<float>{(float)tn[0], (float)tn[1], (float)tn[2]};
+        R0 = P[0];
+        R1 = half == 0 ? ma : cen;
+        R2 = half == 0 ? cen : mb;
+        d = 0;
+        path = 0;
+        in_piece = true;
+      }
+      // the node at (d, path)
+      V3<float> a = R0, b = R1, c = R2;
+      for (int l = 1; l <= d; ++l) {
+        const V3<float> mab{0.5f * (a.x + b.x), 0.5f * (a.y + b.y), 0.5f * (a.z + b.z)};
+        const V3<float> mbc{0.5f * (b.x + c.x), 0.5f * (b.y + c.y), 0.5f * (b.z + c.z)};
+        const V3<float> mca{0.5f * (c.x + a.x), 0.5f * (c.y + a.y), 0.5f * (c.z + a.z)};
+        switch ((path >> (2 * (l - 1))) & 3u) {
+          case 0: b = mab; c = mca; break;
+          case 1: a = mab; c = mbc; break;
+          case 2: a = mca; b = mbc; break;
+          default: a = mab; b = mbc; c = mca; break;
+        }
+      }
+      const V3<float> e01{b.x - a.x, b.y - a.y, b.z - a.z}, e12{c.x - b.x, c.y - b.y, c.z - b.z},
+          e02{c.x - a.x, c.y - a.y, c.z - a.z};
+      const float diam = sqrtf(fmaxf(dot(e01, e01), fmaxf(dot(e12, e12), dot(e02, e02))));
+      const V3<float> g{(a.x + b.x + c.x) / 3.0f, (a.y + b.y + c.y) / 3.0f, (a.z + b.z + c.z) / 3.0f};
+      if (d < kQuadDepth && sqrtf(dot(g, g)) < 3.0f * diam) {
+        ++d;                                  // first child (its digit is 0)
+        continue;
+      }
+      const V3<float> cr{e01.y * e02.z - e01.z * e02.y, e01.z * e02.x - e01.x * e02.z, e01.x * e02.y - e01.y * e02.x};
+      la = a;
+      lb = b;
+      lc = c;
+      larea = 0.5f * sqrtf(dot(cr, cr));
+      have = true;
+      // next node of the walk: the next sibling, climbing past last children
+      while (d > 0 && ((path >> (2 * (d - 1))) & 3u) == 3u) {
+        path &= ~(3u << (2 * (d - 1)));
+        --d;
+      }
+      if (d > 0) {
+        path += 1u << (2 * (d - 1));
       } else {
-        whole = false;                      // a far-field pair (M2L, P2L or L2P side)
+        in_piece = false;                     // piece done: the other half, or the next triangle
+        if (half == 0) {
+          half = 1;
+        } else {
+          half = 0;
+          ++tj;
+        }
       }
     }
-    if (!whole) {
-      const double *xt = xyz + 3 * ot;
-      const V3<Real> d{(Real)(xp[0] - xt[0]), (Real)(xp[1] - xt[1]), (Real)(xp[2] - xt[2])};
-      const V3<Real> nt{(Real)nrm[3 * ot], (Real)nrm[3 * ot + 1], (Real)nrm[3 * ot + 2]};
-      Real f[4];
-      abcd_point(kappa, ebar, d, np, nt, f);
-      const Real at = (Real)area[ot];
-      for (int k = 0; k < 4; ++k) o[k] -= at * f[k];
+    if (__all_sync(0xffffffffu, !have)) break; // every lane has run out of entries
+    // phase 2: the lanes' leaves together
+    if (have) {
+      for (int q = 0; q < 7; ++q) {
+        const float b0 = c_rad_bf[3 * q], b1 = c_rad_bf[3 * q + 1], b2 = c_rad_bf[3 * q + 2];
+        const V3<float> dq{-(b0 * la.x + b1 * lb.x + b2 * lc.x), -(b0 * la.y + b1 * lb.y + b2 * lc.y),
+                           -(b0 * la.z + b1 * lb.z + b2 * lc.z)};
+        float o[4];
+        abcd_point(kappa, ebar, dq, np, ns, o);
+        const float w = larea * c_rad_wf[q];
+        for (int k = 0; k < 4; ++k) acc[k] += w * o[k];
+      }
+      have = false;
     }
-    coef[j] = make_float4((float)o[0], (float)o[1], (float)o[2], (float)o[3]);
-    full[j] = whole ? 1 : 0;
   }
+}
+
+__global__ void k_near_rows(int64_t n, const int64_t *__restrict__ ptr, int32_t *__restrict__ row) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  for (int64_t j = ptr[p]; j < ptr[p + 1]; ++j) row[j] = (int32_t)p;
 }
 
 namespace {
@@ -432,14 +502,31 @@ Err build_near(afmpb_t *h) {
   AFMPB_TRY(check_launch("k_near_search fill"));
   KernelParams kp{h->kappa, h->ebar};
   AFMPB_TRY(A.alloc(&h->d_near_full, h->nnz, "near full"));
+  k_near_self<<<div_up(n, 128), 128, 0, s>>>(n, kp, h->d_perm, h->d_xyz, h->d_tri, h->d_inc_ptr, h->d_inc_tri,
+                                              h->d_nrm64, h->d_near_ptr, h->d_near_col, h->d_near_coef,
+                                              h->d_near_full);
+  AFMPB_TRY(check_launch("k_near_self"));
+  int32_t *d_row = nullptr;
+  unsigned long long *d_counter = nullptr;
+  AFMPB_TRY(A.alloc(&d_row, h->nnz, "near rows"));
+  AFMPB_TRY(A.alloc(&d_counter, 1, "near counter"));
+  AFMPB_CUDA(cudaMemsetAsync(d_counter, 0, sizeof(unsigned long long), s));
+  k_near_rows<<<div_up(n, 256), 256, 0, s>>>(n, h->d_near_ptr, d_row);
+  AFMPB_TRY(check_launch("k_near_rows"));
   const P2PView pv{h->d_node_leaf, h->d_leaf_index, h->d_p2p_idx, h->d_p2p_ptr, h->d_box_center,
                    h->d_pos,       h->d_nrm,        (float)(kP2PSkip * h->opt.near_c)};
-  k_near_coef<float><<<div_up(n * 32, 128), 128, 0, s>>>(n, kp, h->d_perm, h->d_xyz, h->d_tri, h->d_inc_ptr,
-                                                          h->d_inc_tri, h->d_tri_nrm, h->d_area64, h->d_nrm64,
-                                                          h->d_near_ptr, h->d_near_col, pv, h->d_near_coef,
-                                                          h->d_near_full);
-  AFMPB_TRY(check_launch("k_near_coef"));
+  int dev = 0, sms = 0;
+  AFMPB_CUDA(cudaGetDevice(&dev));
+  AFMPB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int64_t want = div_up(h->nnz, 128);   // lanes take entries dynamically; cap the grid
+  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sms * 16));
+  k_near_pairs<<<grid, 128, 0, s>>>(h->nnz, d_row, d_counter, kp, h->d_perm, h->d_xyz, h->d_tri, h->d_inc_ptr,
+                                    h->d_inc_tri, h->d_tri_nrm, h->d_area64, h->d_nrm64, h->d_near_col, pv,
+                                    h->d_near_coef, h->d_near_full);
+  AFMPB_TRY(check_launch("k_near_pairs"));
   AFMPB_CUDA(cudaStreamSynchronize(s));
+  A.release(d_counter);
+  A.release(d_row);
   A.release(d_cnt);
   return Err{};
 }

@@ -582,6 +582,8 @@ Err build_tree(afmpb_t *h) {
       }
     }
     pptr[i + 1] = (int64_t)pidx.size();
+    // ascending source boxes: near-field setup looks a box up by binary search
+    std::sort(pidx.begin() + pptr[i], pidx.end());
     // Time of the leaf's P2P block: tiles of up to kP2PThreads targets, each thread
     // slice walking its share of the sources, plus the staging of every source per tile.
     const int64_t nsrc = nt_b > 0 ? (pairs - pairs_before) / nt_b : 0;
