@@ -220,16 +220,17 @@ def roofline(prof, info, n, order, peaks, kind, precision):
     name, (ms, launches) = max(stages.items(), key=lambda kv: kv[1][0])
     n3 = order ** 3
     sm_max = peaks.get("sm_max_mhz", 2070.0)
+    r = info.get("m2l_rank") or n3                 # compressed translation size, or n^3
     if name == "m2l" and precision == 1:
-        # three BF16 products (hi*hi, hi*lo, lo*hi) of every n^3 x n^3 translation,
-        # Laplace and Yukawa; the burst BF16 peak, the kernel being timed on its own
-        flop = 3 * 2.0 * n3 * n3 * info["n_m2l_pairs"] * 2
+        # three BF16 products (hi*hi, hi*lo, lo*hi) of every r x r translation, Laplace and
+        # Yukawa; the burst BF16 peak, the kernel being timed on its own
+        flop = 3 * 2.0 * r * r * info["n_m2l_pairs"] * 2
         achieved = flop / (ms * 1e-3) / 1e12
         peak = peaks["bf16_tflops"]
         out = {"bound": "tensor", "kernel": "k_m2l_tc (tcgen05 BF16 x3, FP32 accumulate)",
                "unit": "TFLOP/s", "peak_kind": "measured dense BF16 GEMM (burst)"}
     elif name == "m2l":
-        flop = 2.0 * n3 * n3 * info["n_m2l_pairs"] * 2      # Laplace + Yukawa
+        flop = 2.0 * r * r * info["n_m2l_pairs"] * 2        # Laplace + Yukawa
         achieved = flop / (ms * 1e-3) / 1e12
         peak = fp32_peak_tflops(sm_max)
         out = {"bound": "alu", "kernel": "k_m2l (FP32 FMA)", "unit": "TFLOP/s",

@@ -5,7 +5,7 @@
 //   1. calibrates the far field on the handle just built at a starting capacity s0: the
 //      per-stage times of its product give the cost of one list-2 translation (the M2L
 //      stage over its pair count) and of one box in the other tree passes (P2M, M2M, P2L,
-//      L2L, L2P over the box count);
+//      L2L, L2P and the compressed-basis changes over the box count);
 //   2. for every candidate s, builds only the octree and its lists over the same
 //      geometry, and times the real P2P kernel on them;
 //   3. predicts the product time  t(s) = t_P2P(s) + b * pairs_V(s) + c * boxes(s) + t_rest
@@ -106,7 +106,9 @@ Err autotune_leaf_cap(afmpb_t *h, afmpb_autotune_report *rep) {
   for (int i = 0; i < prof.n_stages; ++i) {
     const std::string nm = prof.name[i];
     if (nm == "m2l") m2l_ms += prof.ms[i];
-    else if (nm == "p2m" || nm == "m2m" || nm == "p2l" || nm == "l2l" || nm == "l2p") box_ms += prof.ms[i];
+    else if (nm == "p2m" || nm == "m2m" || nm == "p2l" || nm == "l2l" || nm == "l2p" || nm == "compress" ||
+             nm == "expand")
+      box_ms += prof.ms[i];
     else if (nm == "p2p") p2p_ms += prof.ms[i];
     else rest_ms += prof.ms[i];
   }

@@ -673,10 +673,9 @@ Err launch_far(afmpb_t *h, cudaStream_t s, StageTimer *tm) {
     AFMPB_TRY(check_launch("k_m2m"));
   }
   if (tm) tm->mark("m2m", std::max(0, T.nlevel - 3));
-  int m2l_launches = h->m2l_groups.empty() ? 0 : 1;
-  if (!h->m2l_groups.empty() && h->m2l_rank > 0) {
-    AFMPB_TRY(enqueue_m2l_svd(h, s));
-    m2l_launches = 3;
+  const bool compressed = !h->m2l_groups.empty() && h->m2l_rank > 0;
+  if (compressed) {
+    AFMPB_TRY(enqueue_m2l_svd(h, s, tm));        // marks compress, m2l, expand itself
   } else if (!h->m2l_groups.empty()) {
     if (h->opt.precision == 1) {
       AFMPB_TRY(enqueue_m2l_tc(h, s));
@@ -689,7 +688,7 @@ Err launch_far(afmpb_t *h, cudaStream_t s, StageTimer *tm) {
       AFMPB_TRY(check_launch("k_m2l"));
     }
   }
-  if (tm) tm->mark("m2l", m2l_launches);
+  if (tm && !compressed) tm->mark("m2l", h->m2l_groups.empty() ? 0 : 1);
   if (!h->h_xbox.empty()) {
     k_p2l<N><<<(unsigned)h->h_xbox.size(), 256, 0, s>>>(h->d_xbox, h->d_x_ptr, h->d_x_idx, h->d_box_begin,
                                                         h->d_box_end, h->d_box_center, h->d_pos, h->d_nrm, h->d_xs,

@@ -325,7 +325,7 @@ Err autotune_leaf_cap(afmpb_t *h, afmpb_autotune_report *rep);
 int autotune_cached_cap(int precision, int order, double kappa, int64_t n);   // 0 if none
 // m2l_svd.cu: compressed translations; *compressed = false leaves the full ones in use
 Err build_m2l_svd(afmpb_t *h, bool *compressed);
-Err enqueue_m2l_svd(afmpb_t *h, cudaStream_t s);      // compress, translate, expand
+Err enqueue_m2l_svd(afmpb_t *h, cudaStream_t s, StageTimer *tm = nullptr);   // compress, translate, expand
 Err read_tc_error(afmpb_t *h, int *flag);             // 1 when a tensor-core wait expired
 // solve.cu
 Err build_rhs(afmpb_t *h);

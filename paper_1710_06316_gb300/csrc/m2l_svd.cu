@@ -513,7 +513,7 @@ Err build_m2l_svd(afmpb_t *h, bool *compressed) {
   return Err{};
 }
 
-Err enqueue_m2l_svd(afmpb_t *h, cudaStream_t s) {
+Err enqueue_m2l_svd(afmpb_t *h, cudaStream_t s, StageTimer *tm) {
   const int R = h->m2l_rank, N3 = h->ncoef;
   const auto &T = h->shape;
   AFMPB_CUDA(cudaMemsetAsync(h->d_Lc, 0, sizeof(float) * (size_t)T.nbox * 2 * R, s));
@@ -521,6 +521,7 @@ Err enqueue_m2l_svd(afmpb_t *h, cudaStream_t s) {
   const dim3 cgrid((unsigned)h->m2l_nchunks, 2);
   AFMPB_TRY(launch_box_basis<false>(s, cgrid, N3, R, h->d_m2l_chunks, h->d_level_table, h->m2l_yuk_levels,
                                      h->d_Q, h->d_M, h->d_Mc));
+  if (tm) tm->mark("compress", 2);             // Lc memset + basis change
   if (h->opt.precision == 1) {
     AFMPB_TRY(enqueue_m2l_tc(h, s));
   } else {
@@ -533,8 +534,11 @@ Err enqueue_m2l_svd(afmpb_t *h, cudaStream_t s) {
       default: AFMPB_TRY(launch_m2l_c<6>(h, s)); break;
     }
   }
-  return launch_box_basis<true>(s, cgrid, R, N3, h->d_m2l_chunks, h->d_level_table, h->m2l_yuk_levels, h->d_QT,
-                                h->d_Lc, h->d_L);
+  if (tm) tm->mark("m2l", 1);
+  AFMPB_TRY(launch_box_basis<true>(s, cgrid, R, N3, h->d_m2l_chunks, h->d_level_table, h->m2l_yuk_levels, h->d_QT,
+                                   h->d_Lc, h->d_L));
+  if (tm) tm->mark("expand", 1);
+  return Err{};
 }
 
 }  // namespace afmpb
