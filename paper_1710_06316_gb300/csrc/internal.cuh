@@ -286,7 +286,12 @@ struct afmpb_t {
   float *d_ys = nullptr;           // [2n] y Morton order
   float4 *d_phi_far = nullptr;     // [n] (PhiL, dn PhiL, PhiY, dn PhiY) from L2P
   float4 *d_phi_near = nullptr;    // [n] same from P2P
-  cudaGraphExec_t graph[8] = {};   // captured product, one per parts mask
+  cudaGraphExec_t graph[8] = {};   // captured product (Morton-ordered d_xs -> d_ys), per parts mask
+  cudaGraphExec_t graph_io[8] = {};          // the same with gather and scatter of caller buffers
+  cudaGraph_t graph_io_tmpl[8] = {};         // templates of graph_io (their nodes are updated)
+  cudaGraphNode_t io_gather[8] = {}, io_scatter[8] = {};
+  const float *io_x[8] = {};                 // buffers the io graphs currently point at
+  float *io_y[8] = {};
   float *d_xhost_stage = nullptr, *d_yhost_stage = nullptr;   // afmpb_matvec_host staging
   float *d_prof_x = nullptr, *d_prof_y = nullptr;             // afmpb_profile_product buffers
 
@@ -330,6 +335,8 @@ Err read_tc_error(afmpb_t *h, int *flag);             // 1 when a tensor-core wa
 // solve.cu
 Err build_rhs(afmpb_t *h);
 Err enqueue_gather(afmpb_t *h, cudaStream_t s, const float *x_caller);
+const void *gather_kernel();                           // k_gather, to find its graph node
+const void *scatter_kernel();
 Err enqueue_scatter(afmpb_t *h, cudaStream_t s, float *y_caller);
 Err run_solve(afmpb_t *h, afmpb_solve_info *info);
 Err run_energy(afmpb_t *h, double *E);

@@ -40,6 +40,9 @@ Err enqueue_gather(afmpb_t *h, cudaStream_t s, const float *x) {
   return check_launch("k_gather");
 }
 
+const void *gather_kernel() { return (const void *)k_gather; }
+const void *scatter_kernel() { return (const void *)k_scatter; }
+
 Err enqueue_scatter(afmpb_t *h, cudaStream_t s, float *y) {
   k_scatter<<<div_up(h->n, 256), 256, 0, s>>>(h->n, h->d_perm, h->d_ys, y);
   return check_launch("k_scatter");
