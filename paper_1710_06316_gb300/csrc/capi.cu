@@ -37,6 +37,8 @@ void destroy_handle(afmpb_t *h) {
     if (g) cudaGraphExecDestroy(g);
   for (auto &g : h->graph_io_tmpl)
     if (g) cudaGraphDestroy(g);
+  if (h->graph_gm) cudaGraphExecDestroy(h->graph_gm);
+  if (h->graph_gm_tmpl) cudaGraphDestroy(h->graph_gm_tmpl);
   h->arena.free_all();
   if (h->h_pinned) cudaFreeHost(h->h_pinned);
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
@@ -231,6 +233,68 @@ Err raise_smem_limit(const void *func, int bytes) {
   if (bytes <= cur) return Err{};
   AFMPB_CUDA(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
   cur = bytes;
+  return Err{};
+}
+
+// The product for the solver: a graph that converts the FP64 Krylov vector v (Morton
+// order) to the FP32 input itself, so that no separate launch precedes the graph.  The
+// pointer argument of the conversion node is patched when v changes.
+Err product_from64(afmpb_t *h, cudaStream_t s, const double *v) {
+  if (!h->graph_gm) {
+    int lo = 0, hi = 0;
+    AFMPB_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+    cudaStream_t cap = nullptr;
+    AFMPB_CUDA(cudaStreamCreateWithPriority(&cap, cudaStreamNonBlocking, hi));
+    struct StreamGuard { cudaStream_t s; ~StreamGuard() { cudaStreamDestroy(s); } } sg{cap};
+    AFMPB_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+    Err e = enqueue_to_xs(h, cap, v);
+    if (e.ok()) {
+      cudaEventRecord(h->ev_fork, cap);
+      cudaStreamWaitEvent(h->side, h->ev_fork, 0);
+      e = enqueue_p2p(h, h->side);
+      cudaEventRecord(h->ev_join, h->side);
+      if (e.ok()) e = enqueue_far(h, cap);
+      cudaStreamWaitEvent(cap, h->ev_join, 0);
+    }
+    if (e.ok()) e = enqueue_combine(h, cap, AFMPB_PART_ALL);
+    cudaGraph_t g = nullptr;
+    cudaError_t ce = cudaStreamEndCapture(cap, &g);
+    if (!e.ok() || ce != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return e.ok() ? make_err(AFMPB_ECUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(ce)) : e;
+    }
+    ce = cudaGraphInstantiate(&h->graph_gm, g, 0);
+    if (ce != cudaSuccess) {
+      cudaGraphDestroy(g);
+      return make_err(AFMPB_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(ce));
+    }
+    h->graph_gm_tmpl = g;
+    size_t nn = 0;
+    AFMPB_CUDA(cudaGraphGetNodes(g, nullptr, &nn));
+    std::vector<cudaGraphNode_t> nodes(nn);
+    AFMPB_CUDA(cudaGraphGetNodes(g, nodes.data(), &nn));
+    for (auto nd : nodes) {
+      cudaGraphNodeType ty;
+      AFMPB_CUDA(cudaGraphNodeGetType(nd, &ty));
+      if (ty != cudaGraphNodeTypeKernel) continue;
+      cudaKernelNodeParams kp{};
+      AFMPB_CUDA(cudaGraphKernelNodeGetParams(nd, &kp));
+      if (kp.func == to_xs_kernel()) h->gm_to_xs = nd;
+    }
+    if (!h->gm_to_xs) return make_err(AFMPB_ECUDA, "captured solver product: conversion node missing");
+    h->gm_src = v;
+  } else if (v != h->gm_src) {
+    cudaKernelNodeParams kp{};
+    AFMPB_CUDA(cudaGraphKernelNodeGetParams(h->gm_to_xs, &kp));
+    int64_t n = h->n;
+    float2 *xs = h->d_xs;
+    void *args[] = {&n, (void *)&v, &xs};
+    kp.kernelParams = args;
+    kp.extra = nullptr;
+    AFMPB_CUDA(cudaGraphExecKernelNodeSetParams(h->graph_gm, h->gm_to_xs, &kp));
+    h->gm_src = v;
+  }
+  AFMPB_CUDA(cudaGraphLaunch(h->graph_gm, s));
   return Err{};
 }
 

@@ -292,6 +292,10 @@ struct afmpb_t {
   cudaGraphNode_t io_gather[8] = {}, io_scatter[8] = {};
   const float *io_x[8] = {};                 // buffers the io graphs currently point at
   float *io_y[8] = {};
+  cudaGraphExec_t graph_gm = nullptr;        // solver product: FP64 Krylov vector -> d_ys
+  cudaGraph_t graph_gm_tmpl = nullptr;
+  cudaGraphNode_t gm_to_xs = nullptr;
+  const double *gm_src = nullptr;
   float *d_xhost_stage = nullptr, *d_yhost_stage = nullptr;   // afmpb_matvec_host staging
   float *d_prof_x = nullptr, *d_prof_y = nullptr;             // afmpb_profile_product buffers
 
@@ -337,6 +341,9 @@ Err build_rhs(afmpb_t *h);
 Err enqueue_gather(afmpb_t *h, cudaStream_t s, const float *x_caller);
 const void *gather_kernel();                           // k_gather, to find its graph node
 const void *scatter_kernel();
+const void *to_xs_kernel();
+Err enqueue_to_xs(afmpb_t *h, cudaStream_t s, const double *v);   // FP64 Morton vector -> d_xs
+Err product_from64(afmpb_t *h, cudaStream_t s, const double *v);  // d_ys = L v (one graph launch)
 Err enqueue_scatter(afmpb_t *h, cudaStream_t s, float *y_caller);
 Err run_solve(afmpb_t *h, afmpb_solve_info *info);
 Err run_energy(afmpb_t *h, double *E);

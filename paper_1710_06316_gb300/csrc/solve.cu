@@ -160,13 +160,19 @@ __global__ void k_normalize(int64_t n, const double *__restrict__ w, const doubl
   const double a = w[p] * inv, b = w[n + p] * inv;
   v[p] = a;
   v[n + p] = b;
-  xs[p] = make_float2((float)a, (float)b);
+  if (xs) xs[p] = make_float2((float)a, (float)b);
 }
 
 __global__ void k_to_xs(int64_t n, const double *__restrict__ v, float2 *__restrict__ xs) {
   int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (p >= n) return;
   xs[p] = make_float2((float)v[p], (float)v[n + p]);
+}
+
+const void *to_xs_kernel() { return (const void *)k_to_xs; }
+Err enqueue_to_xs(afmpb_t *h, cudaStream_t s, const double *v) {
+  k_to_xs<<<div_up(h->n, 256), 256, 0, s>>>(h->n, v, h->d_xs);
+  return check_launch("k_to_xs");
 }
 
 // w = ys (FP32 -> FP64), optionally w = b - ys
@@ -352,9 +358,9 @@ Err run_solve(afmpb_t *h, afmpb_solve_info *info) {
   AFMPB_CUDA(cudaEventCreate(&e1));
   struct EvGuard { cudaEvent_t a, b; ~EvGuard() { cudaEventDestroy(a); cudaEventDestroy(b); } } guard{e0, e1};
   AFMPB_CUDA(cudaEventRecord(h->ev_t0, s));
-  auto timed_product = [&]() -> Err {   // d_xs -> d_ys
+  auto timed_product = [&](const double *v) -> Err {   // d_ys = L v (one graph launch)
     AFMPB_CUDA(cudaEventRecord(e0, s));
-    AFMPB_TRY(product_sorted(h, s, AFMPB_PART_ALL));
+    AFMPB_TRY(product_from64(h, s, v));
     AFMPB_CUDA(cudaEventRecord(e1, s));
     return Err{};
   };
@@ -384,8 +390,7 @@ Err run_solve(afmpb_t *h, afmpb_solve_info *info) {
       AFMPB_CUDA(cudaMemcpyAsync(h->d_w, h->d_b, sizeof(double) * n2, cudaMemcpyDeviceToDevice, s));
     } else {
       ++restarts;
-      k_to_xs<<<nb_el, 256, 0, s>>>(n, x, h->d_xs);
-      AFMPB_TRY(timed_product());
+      AFMPB_TRY(timed_product(x));
       k_from_ys<<<nb_el2, 256, 0, s>>>(n2, h->d_ys, h->d_b, h->d_w);
       AFMPB_TRY(check_launch("residual"));
     }
@@ -397,12 +402,12 @@ Err run_solve(afmpb_t *h, afmpb_solve_info *info) {
       converged = !std::isnan(res);
       break;
     }
-    k_normalize<<<nb_el, 256, 0, s>>>(n, h->d_w, h->d_scal + 1, h->d_V, h->d_xs);
+    k_normalize<<<nb_el, 256, 0, s>>>(n, h->d_w, h->d_scal + 1, h->d_V, nullptr);
     k_set_beta<<<1, 1, 0, s>>>(h->d_g, m, h->d_scal + 1);
     AFMPB_TRY(check_launch("gmres start"));
     int k = 0;
     for (int j = 0; j < m; ++j) {
-      AFMPB_TRY(timed_product());   // d_xs holds v_j
+      AFMPB_TRY(timed_product(h->d_V + (size_t)j * n2));
       k_from_ys<<<nb_el2, 256, 0, s>>>(n2, h->d_ys, nullptr, h->d_w);
       // classical Gram-Schmidt applied twice
       AFMPB_TRY(multidot(h, n2, j + 1, h->d_V, n2, h->d_w, h->d_hcol, 0));
@@ -411,7 +416,7 @@ Err run_solve(afmpb_t *h, afmpb_solve_info *info) {
       k_sub_combo<<<nb_comb, 256, 0, s>>>(n2, j + 1, h->d_V, n2, h->d_hcol2, -1.0, h->d_w);
       k_add_small<<<1, 128, 0, s>>>(j + 1, h->d_hcol2, h->d_hcol);
       AFMPB_TRY(norm2(h, n2, h->d_w, h->d_hcol + j + 1));
-      k_normalize<<<nb_el, 256, 0, s>>>(n, h->d_w, h->d_hcol + j + 1, h->d_V + (size_t)(j + 1) * n2, h->d_xs);
+      k_normalize<<<nb_el, 256, 0, s>>>(n, h->d_w, h->d_hcol + j + 1, h->d_V + (size_t)(j + 1) * n2, nullptr);
       k_givens<<<1, 1, 0, s>>>(j, m, h->d_hcol, h->d_H, h->d_cs, h->d_sn, h->d_g, h->d_scal + 2);
       AFMPB_TRY(check_launch("arnoldi"));
       AFMPB_TRY(read_scalar(h->d_scal + 2, 2));
@@ -430,8 +435,7 @@ Err run_solve(afmpb_t *h, afmpb_solve_info *info) {
     AFMPB_TRY(check_launch("gmres update"));
   }
   // true residual with one more product
-  k_to_xs<<<nb_el, 256, 0, s>>>(n, x, h->d_xs);
-  AFMPB_TRY(timed_product());
+  AFMPB_TRY(timed_product(x));
   k_from_ys<<<nb_el2, 256, 0, s>>>(n2, h->d_ys, h->d_b, h->d_w);
   AFMPB_TRY(norm2(h, n2, h->d_w, h->d_scal + 3));
   AFMPB_TRY(read_scalar(h->d_scal + 3, 3));
