@@ -259,7 +259,9 @@ struct afmpb_t {
   int m2l_yuk_levels = 0;          // Yukawa M2L skipped on levels below this one
   // compressed M2L (m2l_rank > 0): bases Q per table (0 = Laplace on the unit box,
   // 1.. = Yukawa per level), translations C_o = Q^T K_o Q, compressed expansions
-  int m2l_rank = 0;                // r, a multiple of 16; 0 = full n^3 translations
+  int m2l_rank = 0;                // storage stride r (largest table rank, multiple of 16); 0 = full n^3
+  std::vector<int> h_table_rank;   // each table's own rank (<= r; columns beyond it are zero)
+  int *d_table_rank = nullptr;
   int m2l_ntables = 0;
   std::vector<int> h_level_table;  // level -> Yukawa table
   int *d_level_table = nullptr;

@@ -163,7 +163,8 @@ constexpr int kSlabRows = 32;
 constexpr int kStages = 3;
 template <int TILES, bool ACCUM>
 __global__ void __launch_bounds__(256) k_box_basis(int K, int ncol, const int4 *__restrict__ chunks,
-                                                   const int *__restrict__ level_table, int yuk_min,
+                                                   const int *__restrict__ level_table,
+                                                   const int *__restrict__ table_rank, int yuk_min,
                                                    const float *__restrict__ A, const float *__restrict__ X,
                                                    float *__restrict__ Y) {
   extern __shared__ __align__(16) float sm[];
@@ -174,10 +175,13 @@ __global__ void __launch_bounds__(256) k_box_basis(int K, int ncol, const int4 *
   if (kt == 1 && ch.z < yuk_min) return;               // no Yukawa translations on this level
   const int table = kt == 0 ? 0 : level_table[ch.z];
   const float *At = A + (size_t)table * K * ncol;
+  // the table's own rank bounds the output columns (compress) or the contraction (expand)
+  const int Keff = ACCUM ? table_rank[table] : K;
+  const int ceff = ACCUM ? ncol : table_rank[table];
   const int slab_elems = kSlabRows * ncol;
-  const int nslab = (K + kSlabRows - 1) / kSlabRows;
+  const int nslab = (Keff + kSlabRows - 1) / kSlabRows;
   // X: the box index runs fastest so that the shared stores hit distinct banks
-  for (int e = threadIdx.x; e < K * kChunkBoxes; e += blockDim.x) {
+  for (int e = threadIdx.x; e < Keff * kChunkBoxes; e += blockDim.x) {
     const int j = e % kChunkBoxes, k = e / kChunkBoxes;
     const bool v = j < ch.y;
     cp_async4(Xs + e, v ? X + ((size_t)(ch.x + j) * 2 + kt) * K + k : X, v);
@@ -186,17 +190,18 @@ __global__ void __launch_bounds__(256) k_box_basis(int K, int ncol, const int4 *
     if (sl < nslab) {
       float *dst = As + (size_t)(sl % kStages) * slab_elems;
       const int k0 = sl * kSlabRows;
-      const int valid = min(kSlabRows, K - k0) * ncol;     // floats present in A
-      for (int e = threadIdx.x * 4; e < slab_elems; e += blockDim.x * 4) {
-        const bool v = e < valid;
-        cp_async16(dst + e, v ? At + (size_t)k0 * ncol + e : At, v);
+      const int rows = min(kSlabRows, Keff - k0), c4n = ceff / 4;
+      for (int g = threadIdx.x; g < kSlabRows * c4n; g += blockDim.x) {   // 16-byte groups used
+        const int r = g / c4n, c = 4 * (g % c4n);
+        const bool v = r < rows;
+        cp_async16(dst + r * ncol + c, v ? At + (size_t)(k0 + r) * ncol + c : At, v);
       }
     }
     cp_async_commit();                                 // empty groups keep the count
   };
   issue_slab(0);                                       // commits X together with slab 0
   issue_slab(1);
-  const int ncol4 = ncol / 4;
+  const int ncol4 = ceff / 4;
   const int ntiles = (kChunkBoxes / 4) * ncol4;
   float acc[TILES][4][4] = {};
   for (int sl = 0; sl < nslab; ++sl) {
@@ -204,7 +209,7 @@ __global__ void __launch_bounds__(256) k_box_basis(int K, int ncol, const int4 *
     __syncthreads();
     issue_slab(sl + 2);                                // its buffer held slab sl - 1
     const float *as = As + (size_t)(sl % kStages) * slab_elems;
-    const int k0 = sl * kSlabRows, rows = min(kSlabRows, K - k0);
+    const int k0 = sl * kSlabRows, rows = min(kSlabRows, Keff - k0);
 #pragma unroll
     for (int t = 0; t < TILES; ++t) {
       const int tile = threadIdx.x + t * blockDim.x;
@@ -248,13 +253,13 @@ size_t basis_smem(int K, int ncol) {
 
 template <bool ACCUM>
 Err launch_box_basis(cudaStream_t s, dim3 grid, int K, int ncol, const int4 *chunks, const int *level_table,
-                     int yuk_min, const float *A, const float *X, float *Y) {
+                     const int *table_rank, int yuk_min, const float *A, const float *X, float *Y) {
   const size_t smem = basis_smem(K, ncol);
   switch (basis_tiles(ncol)) {
-    case 1: k_box_basis<1, ACCUM><<<grid, 256, smem, s>>>(K, ncol, chunks, level_table, yuk_min, A, X, Y); break;
-    case 2: k_box_basis<2, ACCUM><<<grid, 256, smem, s>>>(K, ncol, chunks, level_table, yuk_min, A, X, Y); break;
-    case 3: k_box_basis<3, ACCUM><<<grid, 256, smem, s>>>(K, ncol, chunks, level_table, yuk_min, A, X, Y); break;
-    default: k_box_basis<4, ACCUM><<<grid, 256, smem, s>>>(K, ncol, chunks, level_table, yuk_min, A, X, Y); break;
+    case 1: k_box_basis<1, ACCUM><<<grid, 256, smem, s>>>(K, ncol, chunks, level_table, table_rank, yuk_min, A, X, Y); break;
+    case 2: k_box_basis<2, ACCUM><<<grid, 256, smem, s>>>(K, ncol, chunks, level_table, table_rank, yuk_min, A, X, Y); break;
+    case 3: k_box_basis<3, ACCUM><<<grid, 256, smem, s>>>(K, ncol, chunks, level_table, table_rank, yuk_min, A, X, Y); break;
+    default: k_box_basis<4, ACCUM><<<grid, 256, smem, s>>>(K, ncol, chunks, level_table, table_rank, yuk_min, A, X, Y); break;
   }
   return check_launch(ACCUM ? "k_box_basis expand" : "k_box_basis compress");
 }
@@ -275,25 +280,27 @@ Err set_box_basis_smem(int K, int ncol) {
 // R x R operator stays in shared memory while the group's pairs stream through in chunks
 // of 32 (a warp owns 4 pairs, a lane RPL rows).  Results are added with atomics.
 template <int RPL>
-__global__ void __launch_bounds__(256) k_m2l_c(int R, const M2LGroup *__restrict__ groups,
+__global__ void __launch_bounds__(256) k_m2l_c(int Rs, const M2LGroup *__restrict__ groups,
                                                const int2 *__restrict__ pairs, const float *__restrict__ C,
-                                               const int *__restrict__ level_table, const dbl4 *__restrict__ center,
+                                               const int *__restrict__ level_table,
+                                               const int *__restrict__ table_rank, const dbl4 *__restrict__ center,
                                                int yuk_min, const float *__restrict__ Mc, float *__restrict__ Lc) {
   extern __shared__ float smem[];
-  const int LD = R + 1;
-  float *Cs = smem;                 // [R][LD]
-  float *Ms = smem + R * LD;        // [R][32]
+  const int LD = Rs + 1;
+  float *Cs = smem;                 // [Rs][LD], the table's R x R block used
+  float *Ms = smem + Rs * LD;       // [R][32]
   const M2LGroup g = groups[blockIdx.x];
   const int kt = blockIdx.y;
   if (kt == 1 && g.level < yuk_min) return;
   const int table = kt == 0 ? 0 : level_table[g.level];
-  const float *Cg = C + ((size_t)table * kNumOffsets + g.offset) * R * R;
+  const int R = table_rank[table];            // this table's rank (stride Rs in memory)
+  const float *Cg = C + ((size_t)table * kNumOffsets + g.offset) * Rs * Rs;
   for (int e0 = threadIdx.x; e0 < R * R; e0 += blockDim.x * kCopyILP) {
     float v[kCopyILP];
 #pragma unroll
     for (int u = 0; u < kCopyILP; ++u) {
       const int e = e0 + u * (int)blockDim.x;
-      v[u] = e < R * R ? __ldg(Cg + e) : 0.0f;
+      v[u] = e < R * R ? __ldg(Cg + (size_t)(e / R) * Rs + e % R) : 0.0f;
     }
 #pragma unroll
     for (int u = 0; u < kCopyILP; ++u) {
@@ -318,7 +325,7 @@ __global__ void __launch_bounds__(256) k_m2l_c(int R, const M2LGroup *__restrict
 #pragma unroll
       for (int u = 0; u < kCopyILP; ++u) {
         const int e = e0 + u * (int)blockDim.x, p = e / R, k = e % R;
-        v[u] = (e < R * 32 && p < cnt) ? __ldg(Mc + ((size_t)s_src[p] * 2 + kt) * R + k) : 0.0f;
+        v[u] = (e < R * 32 && p < cnt) ? __ldg(Mc + ((size_t)s_src[p] * 2 + kt) * Rs + k) : 0.0f;
       }
 #pragma unroll
       for (int u = 0; u < kCopyILP; ++u) {
@@ -345,7 +352,7 @@ __global__ void __launch_bounds__(256) k_m2l_c(int R, const M2LGroup *__restrict
     for (int q = 0; q < 4; ++q) {
       const int p = warp * 4 + q;
       if (p >= cnt) continue;
-      float *dst = Lc + ((size_t)s_tgt[p] * 2 + kt) * R;
+      float *dst = Lc + ((size_t)s_tgt[p] * 2 + kt) * Rs;
 #pragma unroll
       for (int r = 0; r < RPL; ++r) {
         const int row = lane + 32 * r;
@@ -361,7 +368,7 @@ Err launch_m2l_c(afmpb_t *h, cudaStream_t s) {
   const size_t smem = sizeof(float) * ((size_t)R * (R + 1) + (size_t)R * 32);
   dim3 grid((unsigned)h->m2l_groups.size(), 2);
   k_m2l_c<RPL><<<grid, 256, smem, s>>>(R, h->d_m2l_groups, h->d_m2l_pairs, h->d_C, h->d_level_table,
-                                       h->d_box_center, h->m2l_yuk_levels, h->d_Mc, h->d_Lc);
+                                       h->d_table_rank, h->d_box_center, h->m2l_yuk_levels, h->d_Mc, h->d_Lc);
   return check_launch("k_m2l_c");
 }
 
@@ -430,14 +437,16 @@ Err build_m2l_svd(afmpb_t *h, bool *compressed) {
     for (auto &th : pool) th.join();
   }
   int rmax = 1;
+  std::vector<int> rank(ntab);
   for (int t = 0; t < ntab; ++t) {
     if (rc[t] != 0) return make_err(AFMPB_EINTERNAL, "M2L compression: eigensolver did not converge");
     // singular values of the stacked operators are the square roots of the eigenvalues
     int r = 0;
     while (r < N3 && lam[t][r] > 0.0 && std::sqrt(lam[t][r] / lam[t][0]) > tol) ++r;
-    rmax = std::max(rmax, r);
+    rank[t] = std::min(N3, std::max(16, (r + 15) / 16 * 16));   // own rank, a multiple of 16
+    rmax = std::max(rmax, rank[t]);
   }
-  const int R = (rmax + 15) / 16 * 16;
+  const int R = rmax;                  // storage stride; table t uses its first rank[t] columns
   if (R > kMaxRank || R >= N3) {       // no gain: keep the full translations
     A.release(d_gram);
     A.release(d_K);
@@ -447,6 +456,9 @@ Err build_m2l_svd(afmpb_t *h, bool *compressed) {
   h->m2l_rank = R;
   h->m2l_ntables = ntab;
   h->h_level_table = level_table;
+  h->h_table_rank = rank;
+  AFMPB_TRY(A.alloc(&h->d_table_rank, rank.size(), "svd table ranks"));
+  AFMPB_CUDA(cudaMemcpyAsync(h->d_table_rank, rank.data(), sizeof(int) * rank.size(), cudaMemcpyHostToDevice, s));
   AFMPB_TRY(A.alloc(&h->d_level_table, level_table.size(), "svd level table"));
   AFMPB_CUDA(cudaMemcpyAsync(h->d_level_table, level_table.data(), sizeof(int) * level_table.size(),
                              cudaMemcpyHostToDevice, s));
@@ -462,7 +474,7 @@ Err build_m2l_svd(afmpb_t *h, bool *compressed) {
   for (int t = 0; t < ntab; ++t) {
     for (int i = 0; i < N3; ++i)
       for (int a = 0; a < R; ++a) {
-        const double v = zt[t][(size_t)a * N3 + i];
+        const double v = a < rank[t] ? zt[t][(size_t)a * N3 + i] : 0.0;   // zero beyond the rank
         q64[(size_t)i * R + a] = v;
         qf[((size_t)t * N3 + i) * R + a] = (float)v;
         qtf[((size_t)t * R + a) * N3 + i] = (float)v;
@@ -519,8 +531,8 @@ Err enqueue_m2l_svd(afmpb_t *h, cudaStream_t s, StageTimer *tm) {
   AFMPB_CUDA(cudaMemsetAsync(h->d_Lc, 0, sizeof(float) * (size_t)T.nbox * 2 * R, s));
   if (h->m2l_nchunks == 0) return Err{};
   const dim3 cgrid((unsigned)h->m2l_nchunks, 2);
-  AFMPB_TRY(launch_box_basis<false>(s, cgrid, N3, R, h->d_m2l_chunks, h->d_level_table, h->m2l_yuk_levels,
-                                     h->d_Q, h->d_M, h->d_Mc));
+  AFMPB_TRY(launch_box_basis<false>(s, cgrid, N3, R, h->d_m2l_chunks, h->d_level_table, h->d_table_rank,
+                                     h->m2l_yuk_levels, h->d_Q, h->d_M, h->d_Mc));
   if (tm) tm->mark("compress", 2);             // Lc memset + basis change
   if (h->opt.precision == 1) {
     AFMPB_TRY(enqueue_m2l_tc(h, s));
@@ -535,8 +547,8 @@ Err enqueue_m2l_svd(afmpb_t *h, cudaStream_t s, StageTimer *tm) {
     }
   }
   if (tm) tm->mark("m2l", 1);
-  AFMPB_TRY(launch_box_basis<true>(s, cgrid, R, N3, h->d_m2l_chunks, h->d_level_table, h->m2l_yuk_levels, h->d_QT,
-                                   h->d_Lc, h->d_L));
+  AFMPB_TRY(launch_box_basis<true>(s, cgrid, R, N3, h->d_m2l_chunks, h->d_level_table, h->d_table_rank,
+                                   h->m2l_yuk_levels, h->d_QT, h->d_Lc, h->d_L));
   if (tm) tm->mark("expand", 1);
   return Err{};
 }

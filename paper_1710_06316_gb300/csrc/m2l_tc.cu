@@ -127,7 +127,8 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_m2l_tc(int N3, const TCItem *
                                                           const int *__restrict__ level_table, int nslots,
                                                           int yuk_min_level, const dbl4 *__restrict__ center,
                                                           const float *__restrict__ M, float *__restrict__ L,
-                                                          int *__restrict__ err_flag) {
+                                                          int *__restrict__ err_flag,
+                                                          const int *__restrict__ table_rank) {
   extern __shared__ __align__(128) uint8_t smem[];
   __nv_bfloat16 *a_hi = reinterpret_cast<__nv_bfloat16 *>(smem);
   __nv_bfloat16 *a_lo = a_hi + kTcAElems;
@@ -144,6 +145,9 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_m2l_tc(int N3, const TCItem *
   const int rtiles = (N3 + kTcRows - 1) / kTcRows;
   if (kt == 1 && g.level < yuk_min_level) return;       // screened away (uniform per CTA)
   const int table = kt == 0 ? 0 : level_table[g.level];
+  // compressed tables: the table's own rank bounds rows and contraction (N3 is the stride)
+  const int Rt = table_rank ? table_rank[table] : N3;
+  if (rt * kTcRows >= Rt) return;                       // no rows of this tile (uniform)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int cnt = it.count;
   const int npad = (cnt + 15) & ~15;
@@ -170,7 +174,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_m2l_tc(int N3, const TCItem *
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_base;
   bool ok = true;
-  const int nkh = (N3 + kTcKHalf - 1) / kTcKHalf;     // contraction halves (1 or 2)
+  const int nkh = (Rt + kTcKHalf - 1) / kTcKHalf;     // contraction halves (1 or 2)
   int issued = 0;                                      // MMA commits made on mb_mma
   int loads = 0;                                       // A-operand copies started on mb_load
 
@@ -204,15 +208,15 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_m2l_tc(int N3, const TCItem *
       const int p = e / kG, k8 = e % kG;
       const int k0 = kh * kTcKHalf + k8 * 8;
       u[i][0] = u[i][1] = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (e < kTcPairs * kG && p < cnt && k0 < N3) {
+      if (e < kTcPairs * kG && p < cnt && k0 < Rt) {
         const float *m = M + ((size_t)s_src[p] * 2 + kt) * N3 + k0;
-        if (k0 + 8 <= N3) {
+        if (k0 + 8 <= Rt) {
           u[i][0] = __ldg(reinterpret_cast<const float4 *>(m));
           u[i][1] = __ldg(reinterpret_cast<const float4 *>(m + 4));
         } else {
           float v[8];
 #pragma unroll
-          for (int q = 0; q < 8; ++q) v[q] = (k0 + q < N3) ? m[q] : 0.0f;
+          for (int q = 0; q < 8; ++q) v[q] = (k0 + q < Rt) ? m[q] : 0.0f;
           u[i][0] = make_float4(v[0], v[1], v[2], v[3]);
           u[i][1] = make_float4(v[4], v[5], v[6], v[7]);
         }
@@ -240,7 +244,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_m2l_tc(int N3, const TCItem *
       const uint32_t lbo_a = (kTcRows / 8) * 128, lbo_b = (kTcPairs / 8) * 128, sbo = 128;
       const uint32_t sa_hi = cvta_smem(a_hi), sa_lo = cvta_smem(a_lo);
       const uint32_t sb_hi = cvta_smem(b_hi), sb_lo = cvta_smem(b_lo);
-      const int ksteps = (min(kTcKHalf, N3 - kh * kTcKHalf) + 15) / 16;
+      const int ksteps = (min(kTcKHalf, Rt - kh * kTcKHalf) + 15) / 16;
       for (int s = 0; s < ksteps; ++s) {
         const uint32_t ka = 2 * s * lbo_a, kb = 2 * s * lbo_b;
         const uint64_t dah = smem_desc(sa_hi + ka, lbo_a, sbo), dal = smem_desc(sa_lo + ka, lbo_a, sbo);
@@ -294,7 +298,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_m2l_tc(int N3, const TCItem *
     }
     __syncthreads();
     const float scale = kt == 0 ? (float)(1.0 / center[s_tgt[0]].w) : 1.0f;
-    const int rows_valid = min(kTcRows, N3 - rt * kTcRows);   // a multiple of 4
+    const int rows_valid = min(kTcRows, Rt - rt * kTcRows);   // a multiple of 4
     for (int e = threadIdx.x; e < cnt * (kTcRows / 4); e += kTcThreads) {
       const int p = e / (kTcRows / 4), g4 = (e % (kTcRows / 4)) * 4;
       if (g4 >= rows_valid) continue;
@@ -371,7 +375,7 @@ Err enqueue_m2l_tc(afmpb_t *h, cudaStream_t s) {
                                              reinterpret_cast<const __nv_bfloat16 *>(h->d_tc_tiles),
                                              h->d_tc_level_table, kNumOffsets, h->m2l_yuk_levels,
                                              h->d_box_center, comp ? h->d_Mc : h->d_M, comp ? h->d_Lc : h->d_L,
-                                             h->d_tc_flag);
+                                             h->d_tc_flag, comp ? h->d_table_rank : nullptr);
   return check_launch("k_m2l_tc");
 }
 
