@@ -269,6 +269,7 @@ struct afmpb_t {
   float *d_QT = nullptr;           // [table][r][ncoef]
   float *d_C = nullptr;            // [table][316][r][r]
   float *d_Mc = nullptr;           // [nbox][2][r] compressed multipole vectors
+  uint16_t *d_Mc16 = nullptr;      // [nbox][2][hi, lo][r] the same split into BF16 (precision 1)
   float *d_Lc = nullptr;           // [nbox][2][r] compressed local vectors
   int4 *d_m2l_chunks = nullptr;    // (first box, count, level) of the compress/expand CTAs
   int m2l_nchunks = 0;
@@ -278,6 +279,9 @@ struct afmpb_t {
   uint16_t *d_tc_tiles = nullptr;  // BF16 hi/lo translation tiles in the MMA operand layout
   int *d_tc_level_table = nullptr; // level -> Yukawa tile table
   int *d_tc_flag = nullptr;        // set by a tensor-core CTA whose bounded wait expired
+  bool tc_pipelined = false;       // the warp-specialized persistent kernel is used
+  int tc_nunits = 0;
+  int2 *d_tc_units = nullptr;      // (item, kernel) work units of the pipelined kernel
 
   // ---- leaf-capacity autotuner (AFMPB_LEAF_CAP_AUTO) --------------------------------
   bool autotuned = false;

@@ -14,6 +14,8 @@
 //
 // Setup (FP64 on the GPU, eigenproblems on the host): per table, the FP64 matrices K_o,
 // the Gram matrix, its eigen-decomposition, then C_o = Q^T (K_o Q).
+#include <cuda_bf16.h>
+
 #include <algorithm>
 #include <cmath>
 #include <thread>
@@ -166,7 +168,7 @@ __global__ void __launch_bounds__(256) k_box_basis(int K, int ncol, const int4 *
                                                    const int *__restrict__ level_table,
                                                    const int *__restrict__ table_rank, int yuk_min,
                                                    const float *__restrict__ A, const float *__restrict__ X,
-                                                   float *__restrict__ Y) {
+                                                   float *__restrict__ Y, __nv_bfloat16 *__restrict__ Y16) {
   extern __shared__ __align__(16) float sm[];
   float *Xs = sm;                                      // [K][kChunkBoxes]
   float *As = sm + (size_t)K * kChunkBoxes;            // [kStages][kSlabRows][ncol]
@@ -242,6 +244,18 @@ __global__ void __launch_bounds__(256) k_box_basis(int K, int ncol, const int4 *
         v.x += o.x; v.y += o.y; v.z += o.z; v.w += o.w;
       }
       *y = v;
+      if (!ACCUM && Y16) {   // the same vector split into BF16 hi / lo for the tensor-core M2L
+        const float w[4] = {v.x, v.y, v.z, v.w};
+        __align__(8) __nv_bfloat16 hi[4], lo[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          hi[j] = __float2bfloat16_rn(w[j]);
+          lo[j] = __float2bfloat16_rn(w[j] - __bfloat162float(hi[j]));
+        }
+        __nv_bfloat16 *y16 = Y16 + ((size_t)(ch.x + b0 + i) * 2 + kt) * 2 * ncol + 4 * c4;
+        *reinterpret_cast<uint2 *>(y16) = *reinterpret_cast<const uint2 *>(hi);
+        *reinterpret_cast<uint2 *>(y16 + ncol) = *reinterpret_cast<const uint2 *>(lo);
+      }
     }
   }
 }
@@ -253,13 +267,14 @@ size_t basis_smem(int K, int ncol) {
 
 template <bool ACCUM>
 Err launch_box_basis(cudaStream_t s, dim3 grid, int K, int ncol, const int4 *chunks, const int *level_table,
-                     const int *table_rank, int yuk_min, const float *A, const float *X, float *Y) {
+                     const int *table_rank, int yuk_min, const float *A, const float *X, float *Y,
+                     __nv_bfloat16 *Y16 = nullptr) {
   const size_t smem = basis_smem(K, ncol);
   switch (basis_tiles(ncol)) {
-    case 1: k_box_basis<1, ACCUM><<<grid, 256, smem, s>>>(K, ncol, chunks, level_table, table_rank, yuk_min, A, X, Y); break;
-    case 2: k_box_basis<2, ACCUM><<<grid, 256, smem, s>>>(K, ncol, chunks, level_table, table_rank, yuk_min, A, X, Y); break;
-    case 3: k_box_basis<3, ACCUM><<<grid, 256, smem, s>>>(K, ncol, chunks, level_table, table_rank, yuk_min, A, X, Y); break;
-    default: k_box_basis<4, ACCUM><<<grid, 256, smem, s>>>(K, ncol, chunks, level_table, table_rank, yuk_min, A, X, Y); break;
+    case 1: k_box_basis<1, ACCUM><<<grid, 256, smem, s>>>(K, ncol, chunks, level_table, table_rank, yuk_min, A, X, Y, Y16); break;
+    case 2: k_box_basis<2, ACCUM><<<grid, 256, smem, s>>>(K, ncol, chunks, level_table, table_rank, yuk_min, A, X, Y, Y16); break;
+    case 3: k_box_basis<3, ACCUM><<<grid, 256, smem, s>>>(K, ncol, chunks, level_table, table_rank, yuk_min, A, X, Y, Y16); break;
+    default: k_box_basis<4, ACCUM><<<grid, 256, smem, s>>>(K, ncol, chunks, level_table, table_rank, yuk_min, A, X, Y, Y16); break;
   }
   return check_launch(ACCUM ? "k_box_basis expand" : "k_box_basis compress");
 }
@@ -502,6 +517,10 @@ Err build_m2l_svd(afmpb_t *h, bool *compressed) {
   if (!chunks.empty())
     AFMPB_CUDA(cudaMemcpyAsync(h->d_m2l_chunks, chunks.data(), sizeof(int4) * chunks.size(), cudaMemcpyHostToDevice, s));
   AFMPB_TRY(A.alloc(&h->d_Mc, (size_t)T.nbox * 2 * R, "Mc"));
+  if (h->opt.precision == 1) {                     // BF16 hi / lo copy for the tensor-core M2L
+    AFMPB_TRY(A.alloc(&h->d_Mc16, (size_t)T.nbox * 2 * 2 * R, "Mc bf16"));
+    AFMPB_CUDA(cudaMemsetAsync(h->d_Mc16, 0, sizeof(uint16_t) * (size_t)T.nbox * 2 * 2 * R, s));
+  }
   AFMPB_TRY(A.alloc(&h->d_Lc, (size_t)T.nbox * 2 * R, "Lc"));
   AFMPB_CUDA(cudaMemsetAsync(h->d_Mc, 0, sizeof(float) * (size_t)T.nbox * 2 * R, s));
   AFMPB_TRY(set_box_basis_smem<false>(N3, R));
@@ -532,7 +551,8 @@ Err enqueue_m2l_svd(afmpb_t *h, cudaStream_t s, StageTimer *tm) {
   if (h->m2l_nchunks == 0) return Err{};
   const dim3 cgrid((unsigned)h->m2l_nchunks, 2);
   AFMPB_TRY(launch_box_basis<false>(s, cgrid, N3, R, h->d_m2l_chunks, h->d_level_table, h->d_table_rank,
-                                     h->m2l_yuk_levels, h->d_Q, h->d_M, h->d_Mc));
+                                     h->m2l_yuk_levels, h->d_Q, h->d_M, h->d_Mc,
+                                     reinterpret_cast<__nv_bfloat16 *>(h->d_Mc16)));
   if (tm) tm->mark("compress", 2);             // Lc memset + basis change
   if (h->opt.precision == 1) {
     AFMPB_TRY(enqueue_m2l_tc(h, s));

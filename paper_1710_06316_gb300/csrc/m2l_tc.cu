@@ -312,6 +312,243 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_m2l_tc(int N3, const TCItem *
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcTmemCols));
 }
 
+// ------------------------------------------------------------------------------------
+// Pipelined form for compressed translations whose ranks all fit one contraction block
+// (r <= 112): persistent CTAs (two per SM) walk a contiguous range of work units
+// (item, kernel), ordered so that consecutive units share their translation tile.
+// Warps 0-3 produce: wait until the previous unit's MMAs have read the operands, load the
+// A tile when it changes (bulk copy), gather and split the B operand, and thread 0 issues
+// the MMAs into one of two TMEM accumulators.  Warps 4-7 consume: wait for a unit's
+// accumulator, read it with tcgen05.ld (warp w reads lanes 32 (w - 4) .. +31, one output
+// row per lane) and add each pair's column into the target's compressed local vector with
+// coalesced atomics, then release the accumulator.  So the gather of unit k + 1, the MMAs
+// of unit k and the epilogue of unit k - 1 overlap.  Every wait is bounded; on expiry the
+// CTA records the error flag, drains its own MMAs (bounded) and frees its TMEM.
+// ------------------------------------------------------------------------------------
+__device__ __forceinline__ void producer_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+__device__ __forceinline__ void cp_async16_zfill(uint32_t dst, const void *src, bool valid) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(valid ? 16 : 0) : "memory");
+}
+__device__ __forceinline__ bool producer_all(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 q, %1, 0;\n\tbar.red.and.pred p, 1, 128, q;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(r)
+      : "r"((uint32_t)v)
+      : "memory");
+  return r != 0;
+}
+
+__global__ void __launch_bounds__(kTcThreads, 2) k_m2l_tcp(int R, int nunits, const int2 *__restrict__ units,
+                                                           const __nv_bfloat16 *__restrict__ Mc16,
+                                                           const TCItem *__restrict__ items,
+                                                           const M2LGroup *__restrict__ groups,
+                                                           const int2 *__restrict__ pairs,
+                                                           const __nv_bfloat16 *__restrict__ tiles,
+                                                           const int *__restrict__ level_table, int nslots,
+                                                           const int *__restrict__ table_rank,
+                                                           const dbl4 *__restrict__ center,
+                                                           const float *__restrict__ Mc, float *__restrict__ Lc,
+                                                           int *__restrict__ err_flag) {
+  extern __shared__ __align__(128) uint8_t smem[];
+  __nv_bfloat16 *a_hi = reinterpret_cast<__nv_bfloat16 *>(smem);
+  __nv_bfloat16 *a_lo = a_hi + kTcAElems;
+  __nv_bfloat16 *b_hi = a_lo + kTcAElems;
+  __nv_bfloat16 *b_lo = b_hi + kTcBElems;
+  __shared__ __align__(8) uint64_t bar_a, bar_full[2], bar_empty[2];
+  __shared__ uint32_t tmem_base;
+  __shared__ int s_src[kTcPairs];
+  __shared__ int s_etgt[4][kTcPairs];                     // per epilogue warp: the unit's targets
+  __shared__ int s_issued;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int per = (nunits + (int)gridDim.x - 1) / (int)gridDim.x;
+  const int u0 = (int)blockIdx.x * per, u1 = min(nunits, u0 + per);
+  if (u0 >= u1) return;                                   // uniform per CTA
+  const int nk = u1 - u0;
+  const uint32_t mb_a = cvta_smem(&bar_a);
+  const uint32_t mb_full[2] = {cvta_smem(&bar_full[0]), cvta_smem(&bar_full[1])};
+  const uint32_t mb_empty[2] = {cvta_smem(&bar_empty[0]), cvta_smem(&bar_empty[1])};
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(cvta_smem(&tmem_base)),
+                 "r"(2 * kTcTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb_a));
+    for (int b = 0; b < 2; ++b) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb_full[b]));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(mb_empty[b]));   // one arrival per epilogue warp
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;");
+    s_issued = 0;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_base;
+  bool failed = false;
+
+  if (warp < 4) {
+    // ---- producers -------------------------------------------------------------------
+    int a_key = -1, a_loads = 0, issued = 0;
+    for (int k = 0; k < nk; ++k) {
+      const int2 un = units[u0 + k];
+      const TCItem it = items[un.x];
+      const M2LGroup g = groups[it.group];
+      const int kt = un.y;
+      const int table = kt == 0 ? 0 : level_table[g.level];
+      const int Rt = table_rank[table];
+      const int cnt = it.count, npad = (cnt + 15) & ~15;
+      // operands free: the previous unit's MMAs have completed
+      bool ok = true;
+      if (k >= 1) ok = mbar_wait(mb_full[(k - 1) & 1], (uint32_t)(((k - 1) >> 1) & 1));
+      if (!producer_all(ok)) {
+        failed = true;
+        break;
+      }
+      if (threadIdx.x < kTcPairs) s_src[threadIdx.x] = threadIdx.x < cnt ? pairs[g.start + it.start + threadIdx.x].y : 0;
+      const int key = table * nslots + g.offset;
+      const bool load_a = key != a_key;
+      if (load_a) {
+        if (threadIdx.x == 0) {
+          const __nv_bfloat16 *src = tiles + (size_t)key * 2 * 2 * kTcAElems;   // row tile 0, K half 0
+          const uint32_t bytes = 2 * kTcAElems * 2;
+          asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb_a), "r"(bytes));
+          asm volatile(
+              "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                  cvta_smem(a_hi)),
+              "l"(src), "r"((uint32_t)(kTcAElems * 2)), "r"(mb_a)
+              : "memory");
+          asm volatile(
+              "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                  cvta_smem(a_lo)),
+              "l"(src + kTcAElems), "r"((uint32_t)(kTcAElems * 2)), "r"(mb_a)
+              : "memory");
+        }
+        a_key = key;
+        ++a_loads;
+      }
+      producer_sync();                                   // s_src visible
+      // B: npad pairs x Rt weights, already split into BF16 hi / lo by the compression:
+      // 16-byte asynchronous copies straight into the canonical K-major layout (rows of
+      // padding pairs are zero-filled)
+      const int kg = Rt / 8;                             // groups of 8 along K
+      const int nunit = npad * kg;
+      const uint32_t sb_hi0 = cvta_smem(b_hi), sb_lo0 = cvta_smem(b_lo);
+      for (int e = threadIdx.x; e < nunit; e += 128) {
+        const int p = e / kg, k8 = e % kg;
+        const bool v = p < cnt;
+        const __nv_bfloat16 *src = Mc16 + ((size_t)(v ? s_src[p] : 0) * 2 + kt) * 2 * R + k8 * 8;
+        const uint32_t off = canon_off(p, k8 * 8, kTcPairs);
+        cp_async16_zfill(sb_hi0 + off, src, v);
+        cp_async16_zfill(sb_lo0 + off, src + R, v);
+      }
+      asm volatile("cp.async.commit_group;" ::: "memory");
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
+      asm volatile("fence.proxy.async.shared::cta;");
+      producer_sync();
+      const int b = k & 1;
+      bool ok0 = true;
+      if (threadIdx.x == 0) {
+        if (load_a) ok0 = mbar_wait(mb_a, (uint32_t)((a_loads - 1) & 1));
+        if (ok0 && k >= 2) ok0 = mbar_wait(mb_empty[b], (uint32_t)(((k - 2) >> 1) & 1));   // accumulator drained
+        if (ok0) {
+          asm volatile("tcgen05.fence::after_thread_sync;");
+          const uint32_t idesc = instr_desc(kTcRows, npad);
+          const uint32_t lbo_a = (kTcRows / 8) * 128, lbo_b = (kTcPairs / 8) * 128, sbo = 128;
+          const uint32_t sa_hi = cvta_smem(a_hi), sa_lo = cvta_smem(a_lo);
+          const uint32_t sb_hi = cvta_smem(b_hi), sb_lo = cvta_smem(b_lo);
+          const uint32_t acc = tmem + (uint32_t)(b * kTcTmemCols);
+          for (int st = 0; st < Rt / 16; ++st) {
+            const uint32_t ka = 2 * st * lbo_a, kb = 2 * st * lbo_b;
+            const uint64_t dah = smem_desc(sa_hi + ka, lbo_a, sbo), dal = smem_desc(sa_lo + ka, lbo_a, sbo);
+            const uint64_t dbh = smem_desc(sb_hi + kb, lbo_b, sbo), dbl = smem_desc(sb_lo + kb, lbo_b, sbo);
+            const uint32_t acc0 = st > 0 ? 1u : 0u;
+            asm volatile(
+                "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(acc),
+                "l"(dah), "l"(dbh), "r"(idesc), "r"(acc0));
+            asm volatile(
+                "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(acc),
+                "l"(dah), "l"(dbl), "r"(idesc), "r"(1u));
+            asm volatile(
+                "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(acc),
+                "l"(dal), "l"(dbh), "r"(idesc), "r"(1u));
+          }
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+              mb_full[b]));
+          ++issued;
+        }
+      }
+      if (!producer_all(ok0)) {
+        failed = true;
+        break;
+      }
+    }
+    if (threadIdx.x == 0) s_issued = issued;
+  } else {
+    // ---- epilogue --------------------------------------------------------------------
+    const int ew = warp - 4;
+    const int row = 32 * ew + lane;
+    for (int k = 0; k < nk; ++k) {
+      const int2 un = units[u0 + k];
+      const TCItem it = items[un.x];
+      const M2LGroup g = groups[it.group];
+      const int kt = un.y;
+      const int table = kt == 0 ? 0 : level_table[g.level];
+      const int Rt = table_rank[table];
+      const int cnt = it.count, npad = (cnt + 15) & ~15;
+      const int b = k & 1;
+      // the unit's targets and scale, loaded while its MMAs may still be running
+      const int2 *pr = pairs + g.start + it.start;
+      for (int p = lane; p < cnt; p += 32) s_etgt[ew][p] = pr[p].x;
+      const float scale = kt == 0 ? (float)(1.0 / center[pairs[g.start].x].w) : 1.0f;
+      __syncwarp();
+      const bool ok = __all_sync(0xffffffffu, mbar_wait(mb_full[b], (uint32_t)((k >> 1) & 1)));
+      if (!ok) {
+        failed = true;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      for (int c0 = 0; c0 < npad; c0 += 16) {
+        uint32_t r[16];
+        const uint32_t taddr = tmem + ((uint32_t)(32 * ew) << 16) + (uint32_t)(b * kTcTmemCols + c0);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;");
+        if (row < Rt) {
+#pragma unroll
+          for (int q = 0; q < 16; ++q) {
+            const int p = c0 + q;
+            if (p < cnt) atomicAdd(Lc + ((size_t)s_etgt[ew][p] * 2 + kt) * R + row, __uint_as_float(r[q]) * scale);
+          }
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      __syncwarp();                                      // also: s_etgt reads done before the next unit
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mb_empty[b]) : "memory");
+    }
+  }
+  if (failed && lane == 0) atomicExch(err_flag, 1);
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (threadIdx.x == 0 && failed) {
+    // bounded: let this CTA's last MMA group drain before the tensor memory is freed
+    const int issued = s_issued;
+    if (issued > 0) mbar_wait(mb_full[(issued - 1) & 1], (uint32_t)(((issued - 1) >> 1) & 1));
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kTcTmemCols));
+}
+
 namespace {
 constexpr int kTcSmem = (2 * kTcAElems + 2 * kTcBElems) * 2;
 }
@@ -360,6 +597,24 @@ Err build_m2l_tc(afmpb_t *h) {
                                    h->m2l_rank > 0 ? h->d_C : nullptr, d_table_level,
                                    reinterpret_cast<__nv_bfloat16 *>(h->d_tc_tiles));
   AFMPB_TRY(check_launch("k_tc_tables"));
+  // pipelined kernel: compressed tables whose ranks all fit one contraction block
+  int rmax = 0;
+  for (int r : h->h_table_rank) rmax = std::max(rmax, r);
+  h->tc_pipelined = h->m2l_rank > 0 && rmax <= kTcKHalf && N3 <= kTcRows && h->d_Mc16;
+  if (h->tc_pipelined) {
+    std::vector<int2> units;                           // (item, kernel), kernel-major
+    for (int kt = 0; kt < 2; ++kt)
+      for (int i = 0; i < (int)items.size(); ++i) {
+        const auto &g = h->m2l_groups[items[i].group];
+        if (kt == 1 && g.level < h->m2l_yuk_levels) continue;   // screened away
+        units.push_back(make_int2(i, kt));
+      }
+    h->tc_nunits = (int)units.size();
+    AFMPB_TRY(A.alloc(&h->d_tc_units, std::max<size_t>(1, units.size()), "tc units"));
+    if (!units.empty())
+      AFMPB_CUDA(cudaMemcpyAsync(h->d_tc_units, units.data(), sizeof(int2) * units.size(), cudaMemcpyHostToDevice, s));
+    AFMPB_TRY(raise_smem_limit((const void *)k_m2l_tcp, kTcSmem));
+  }
   AFMPB_CUDA(cudaStreamSynchronize(s));
   A.release(d_table_level);
   AFMPB_TRY(raise_smem_limit((const void *)k_m2l_tc, kTcSmem));
@@ -369,6 +624,20 @@ Err build_m2l_tc(afmpb_t *h) {
 Err enqueue_m2l_tc(afmpb_t *h, cudaStream_t s) {
   if (h->tc_items == 0) return Err{};
   const bool comp = h->m2l_rank > 0;
+  if (h->tc_pipelined) {
+    if (h->tc_nunits == 0) return Err{};
+    int dev = 0, sms = 0;
+    AFMPB_CUDA(cudaGetDevice(&dev));
+    AFMPB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const unsigned grid = (unsigned)std::min(h->tc_nunits, 2 * sms);   // two CTAs per SM
+    k_m2l_tcp<<<grid, kTcThreads, kTcSmem, s>>>(h->m2l_rank, h->tc_nunits, h->d_tc_units,
+                                                reinterpret_cast<const __nv_bfloat16 *>(h->d_Mc16), h->d_tc_items,
+                                                h->d_m2l_groups, h->d_m2l_pairs,
+                                                reinterpret_cast<const __nv_bfloat16 *>(h->d_tc_tiles),
+                                                h->d_tc_level_table, kNumOffsets, h->d_table_rank,
+                                                h->d_box_center, h->d_Mc, h->d_Lc, h->d_tc_flag);
+    return check_launch("k_m2l_tcp");
+  }
   const int N3 = comp ? h->m2l_rank : h->ncoef;
   dim3 grid((unsigned)h->tc_items, (N3 + kTcRows - 1) / kTcRows, 2);
   k_m2l_tc<<<grid, kTcThreads, kTcSmem, s>>>(N3, h->d_tc_items, h->d_m2l_groups, h->d_m2l_pairs,
