@@ -99,7 +99,13 @@ typedef struct {
                             the stacked translation matrices whose singular values exceed
                             m2l_tol times the largest (default 1e-5 for 0; a negative
                             value keeps the full n^3 x n^3 translations)                 */
+    int charge_fmm;      /* charge-surface sums of the right-hand side and the energy:
+                            0 = by FMM when n_nodes x n_charges > AFMPB_CHARGE_FMM_PAIRS,
+                            else direct; 1 = always direct; 2 = always by FMM            */
 } afmpb_options;
+
+/* afmpb_options.charge_fmm = 0 switches to the FMM above this many charge-node pairs. */
+#define AFMPB_CHARGE_FMM_PAIRS 5.0e11
 
 /* Solve report. */
 typedef struct {
@@ -135,6 +141,8 @@ typedef struct {
     int64_t device_bytes_peak; /* high-water mark of device_bytes (setup scratch included) */
     int leaf_cap;              /* leaf capacity the octree was built with                */
     int autotuned;             /* 1 when AFMPB_LEAF_CAP_AUTO ran the tuner for this handle */
+    int charge_fmm;            /* 1 when the right-hand side and energy use the FMM      */
+    int64_t charge_fmm_boxes;  /* boxes of that FMM's octree over nodes and charges      */
 } afmpb_info;
 
 /* Leaf-capacity autotuner report (AFMPB_LEAF_CAP_AUTO; no counterpart in the paper, which

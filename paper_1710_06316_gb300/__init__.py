@@ -40,7 +40,8 @@ class Charges(C.Structure):
 class Options(C.Structure):
     _fields_ = [("leaf_cap", C.c_int), ("restart", C.c_int), ("max_restart", C.c_int),
                 ("abs_tol", C.c_double), ("precision", C.c_int), ("near_c", C.c_double),
-                ("stream", C.c_void_p), ("max_level", C.c_int), ("m2l_tol", C.c_double)]
+                ("stream", C.c_void_p), ("max_level", C.c_int), ("m2l_tol", C.c_double),
+                ("charge_fmm", C.c_int)]
 
 
 class SolveInfo(C.Structure):
@@ -59,7 +60,8 @@ class Info(C.Structure):
                 ("device_bytes", C.c_int64), ("root_center", C.c_double * 3),
                 ("root_half_width", C.c_double), ("ms_create", C.c_double * 6),
                 ("m2l_rank", C.c_int), ("m2l_tables", C.c_int), ("device_bytes_peak", C.c_int64),
-                ("leaf_cap", C.c_int), ("autotuned", C.c_int)]
+                ("leaf_cap", C.c_int), ("autotuned", C.c_int), ("charge_fmm", C.c_int),
+                ("charge_fmm_boxes", C.c_int64)]
 
 
 AUTOTUNE_MAX = 16
@@ -207,8 +209,8 @@ def version() -> str:
     return load().afmpb_version().decode()
 
 
-def estimate_bytes(n_nodes, n_atoms, order=6, leaf_cap=0, restart=0) -> int:
-    o = Options(leaf_cap=leaf_cap, restart=restart)
+def estimate_bytes(n_nodes, n_atoms, order=6, leaf_cap=0, restart=0, charge_fmm=0) -> int:
+    o = Options(leaf_cap=leaf_cap, restart=restart, charge_fmm=charge_fmm)
     return int(load().afmpb_estimate_bytes(int(n_nodes), int(n_atoms), int(order), C.byref(o)))
 
 
@@ -217,7 +219,8 @@ class Handle:
 
     def __init__(self, xyz, tri, atoms=None, q=None, eps_in=1.0, eps_out=80.0, kappa=0.0,
                  order=6, tol=1e-6, leaf_cap=0, restart=0, max_restart=0, abs_tol=0.0,
-                 precision=0, near_c=0.0, stream=None, max_level=0, normals=None, m2l_tol=0.0):
+                 precision=0, near_c=0.0, stream=None, max_level=0, normals=None, m2l_tol=0.0,
+                 charge_fmm=0):
         self._lib = load()
         self._xyz = _np(xyz, np.float64)
         self._tri = _np(tri, np.int32)
@@ -234,7 +237,7 @@ class Handle:
         if st is not None and not isinstance(st, int):
             st = int(getattr(st, "cuda_stream", st))
         opt = Options(int(leaf_cap), int(restart), int(max_restart), float(abs_tol), int(precision),
-                      float(near_c), st, int(max_level), float(m2l_tol))
+                      float(near_c), st, int(max_level), float(m2l_tol), int(charge_fmm))
         h = C.c_void_p()
         rc = self._lib.afmpb_create(C.byref(mesh), None if ch is None else C.byref(ch),
                                     float(eps_in), float(eps_out), float(kappa), int(order),
@@ -392,7 +395,8 @@ class Server:
         self._keep = {}          # ticket -> output buffers that the server writes into
 
     def submit(self, xyz, tri, atoms, q, eps_in=1.0, eps_out=80.0, kappa=0.0, order=6, tol=1e-6,
-               precision=0, leaf_cap=0, m2l_tol=0.0, restart=0, max_restart=0, want_solution=False):
+               precision=0, leaf_cap=0, m2l_tol=0.0, restart=0, max_restart=0, want_solution=False,
+               charge_fmm=0):
         xyz = _np(xyz, np.float64)
         tri = _np(tri, np.int32)
         atoms = _np(np.atleast_2d(atoms), np.float64)
@@ -404,7 +408,7 @@ class Server:
                       Charges(int(q.size), atoms.ctypes.data, q.ctypes.data),
                       float(eps_in), float(eps_out), float(kappa), int(order), float(tol),
                       Options(int(leaf_cap), int(restart), int(max_restart), 0.0, int(precision), 0.0, None, 0,
-                              float(m2l_tol)),
+                              float(m2l_tol), int(charge_fmm)),
                       None if f is None else f.ctypes.data, None if hh is None else hh.ctypes.data)
         t = C.c_int64()
         rc = self._lib.afmpb_server_submit(self.s, C.byref(req), C.byref(t))

@@ -31,6 +31,7 @@ afmpb_status fail(afmpb_t *h, const Err &e) {
 void destroy_handle(afmpb_t *h) {
   if (!h) return;
   if (h->stream) cudaStreamSynchronize(h->stream);
+  if (h->cf) destroy_handle(h->cf);                   // shares h's stream, owns no stream
   for (auto &g : h->graph)
     if (g) cudaGraphExecDestroy(g);
   for (auto &g : h->graph_io)
@@ -163,6 +164,7 @@ Err check_params(const afmpb_mesh *mesh, double eps_in, double eps_out, double k
     if (o->abs_tol < 0 || !(o->near_c >= 0)) return make_err(AFMPB_EINVAL, "abs_tol and near_c must be >= 0");
     if (o->precision != 0 && o->precision != 1) return make_err(AFMPB_EINVAL, "precision must be 0 or 1");
     if (o->restart > 4096) return make_err(AFMPB_EINVAL, "restart above 4096");
+    if (o->charge_fmm < 0 || o->charge_fmm > 2) return make_err(AFMPB_EINVAL, "charge_fmm must be 0, 1 or 2");
   }
   return Err{};
 }
@@ -590,6 +592,13 @@ afmpb_status afmpb_get_info(const afmpb_t *h, afmpb_info *info) {
   info->autotuned = h->autotuned ? 1 : 0;
   info->m2l_rank = h->m2l_rank;
   info->m2l_tables = h->m2l_ntables;
+  if (h->cf) {
+    // the charge FMM is built after the handle's own setup scratch is released
+    info->charge_fmm = 1;
+    info->charge_fmm_boxes = h->cf->shape.nbox;
+    info->device_bytes += (int64_t)h->cf->arena.bytes;
+    info->device_bytes_peak = std::max(info->device_bytes_peak, (int64_t)(h->arena.bytes + h->cf->arena.peak));
+  }
   return AFMPB_OK;
 }
 
@@ -712,6 +721,12 @@ size_t afmpb_estimate_bytes(int64_t n_nodes, int64_t n_atoms, int fmm_order, con
   b += 316 * n3 * n3 * 4 * 14;                                                          // M2L tables
   b += (size_t)(m + 1) * 2 * n * 8 + 8 * 2 * n * 8;                                     // GMRES
   b += (size_t)std::max<int64_t>(n_atoms, 0) * 32 * 2;
+  const int cfm = o ? o->charge_fmm : 0;
+  if (n_atoms > 0 && (cfm == 2 || (cfm == 0 && (double)n_nodes * (double)n_atoms > AFMPB_CHARGE_FMM_PAIRS))) {
+    const size_t nu = n + (size_t)n_atoms;                                             // charge FMM
+    const size_t nbu = 3 * (nu / (size_t)std::max(cap / 2, 1) + 64);
+    b += nu * 160 + nbu * (2 * 2 * n3 * 4 + 64 + 27 * 4 + 200 * 4 * 2) + 316 * n3 * n3 * 4 * 14;
+  }
   return b + (64u << 20);
 }
 

@@ -780,6 +780,7 @@ Err build_fmm(afmpb_t *h) {
   h->m2l_yuk_levels = 0;
   while (h->m2l_yuk_levels < maxlev && h->kappa * 2.0 * std::ldexp(T.w0, -h->m2l_yuk_levels) > 40.0)
     ++h->m2l_yuk_levels;
+  if (h->laplace_only) h->m2l_yuk_levels = maxlev;
   bool compressed = false;
   AFMPB_TRY(build_m2l_svd(h, &compressed));
   if (compressed) {
@@ -792,7 +793,7 @@ Err build_fmm(afmpb_t *h) {
   }
   const size_t N6 = (size_t)N3 * N3;
   AFMPB_TRY(A.alloc(&h->d_K_lap, kNumOffsets * N6, "K laplace"));
-  AFMPB_TRY(A.alloc(&h->d_K_yuk, (size_t)std::max(maxlev, 1) * kNumOffsets * N6, "K yukawa"));
+  AFMPB_TRY(A.alloc(&h->d_K_yuk, h->laplace_only ? 1 : (size_t)std::max(maxlev, 1) * kNumOffsets * N6, "K yukawa"));
   k_m2l_table<<<1024, 256, 0, s>>>(n, kNumOffsets, d_offs, -1.0, 1.0, h->d_K_lap);
   AFMPB_TRY(check_launch("k_m2l_table lap"));
   for (int l = std::max(2, h->m2l_yuk_levels); l < maxlev; ++l) {

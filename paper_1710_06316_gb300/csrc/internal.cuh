@@ -257,6 +257,7 @@ struct afmpb_t {
   int2 *d_m2l_pairs = nullptr;     // (target, source) boxes grouped by (level, offset)
   int64_t n_m2l_pairs = 0;
   int m2l_yuk_levels = 0;          // Yukawa M2L skipped on levels below this one
+  bool laplace_only = false;       // no Yukawa translations at all (the Yukawa outputs are unused)
   // compressed M2L (m2l_rank > 0): bases Q per table (0 = Laplace on the unit box,
   // 1.. = Yukawa per level), translations C_o = Q^T K_o Q, compressed expansions
   int m2l_rank = 0;                // storage stride r (largest table rank, multiple of 16); 0 = full n^3
@@ -317,6 +318,8 @@ struct afmpb_t {
   double *d_V = nullptr, *d_w = nullptr, *d_H = nullptr, *d_g = nullptr, *d_cs = nullptr,
          *d_sn = nullptr, *d_part = nullptr, *d_hcol = nullptr, *d_hcol2 = nullptr, *d_scal = nullptr;
   double *h_pinned = nullptr;
+  // Laplace FMM over nodes and charges for the right-hand side and the energy (owned)
+  afmpb_t *cf = nullptr;
 };
 
 namespace afmpb {
@@ -353,6 +356,11 @@ Err product_from64(afmpb_t *h, cudaStream_t s, const double *v);  // d_ys = L v 
 Err enqueue_scatter(afmpb_t *h, cudaStream_t s, float *y_caller);
 Err run_solve(afmpb_t *h, afmpb_solve_info *info);
 Err run_energy(afmpb_t *h, double *E);
+// charge_fmm.cu
+bool charge_fmm_wanted(const afmpb_t *h);
+Err build_charge_fmm(afmpb_t *h);
+Err charge_fmm_rhs(afmpb_t *h, double *b);       // b [2n], Morton order
+Err charge_fmm_phi(afmpb_t *h, double *phi);     // reaction potential at the charges (with 1/(4 pi))
 Err run_energy_noalloc(afmpb_t *h, double *E);      // static scratch, no allocation
 // capi.cu
 Err product_sorted(afmpb_t *h, cudaStream_t s, int parts);  // d_xs -> d_ys

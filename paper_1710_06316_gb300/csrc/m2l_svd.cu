@@ -453,11 +453,19 @@ Err build_m2l_svd(afmpb_t *h, bool *compressed) {
   }
   int rmax = 1;
   std::vector<int> rank(ntab);
-  for (int t = 0; t < ntab; ++t) {
+  for (int t = 0; t < ntab; ++t)
     if (rc[t] != 0) return make_err(AFMPB_EINTERNAL, "M2L compression: eigensolver did not converge");
-    // singular values of the stacked operators are the square roots of the eigenvalues
+  for (int t = 0; t < ntab; ++t) {
+    // Singular values of the stacked operators are the square roots of the eigenvalues.
+    // The cut is relative to the larger of the table's own largest singular value and
+    // the Laplace table's at the same level (sigma_0(Laplace) / w): the Yukawa and
+    // Laplace far fields enter each row of Eq. 5 with O(1) weights, so a translation
+    // error counts against the Laplace scale.  On strongly screened levels (kappa w of
+    // several units on large molecules) the screened kernel is orders of magnitude
+    // smaller and needs far fewer vectors than a cut relative to itself would keep.
+    const double ref = std::max(std::sqrt(std::max(lam[t][0], 0.0)), std::sqrt(std::max(lam[0][0], 0.0)) * tab_invw[t]);
     int r = 0;
-    while (r < N3 && lam[t][r] > 0.0 && std::sqrt(lam[t][r] / lam[t][0]) > tol) ++r;
+    while (r < N3 && lam[t][r] > 0.0 && std::sqrt(lam[t][r]) > tol * ref) ++r;
     rank[t] = std::min(N3, std::max(16, (r + 15) / 16 * 16));   // own rank, a multiple of 16
     rmax = std::max(rmax, rank[t]);
   }

@@ -294,6 +294,10 @@ Err build_rhs(afmpb_t *h) {
     AFMPB_CUDA(cudaMemsetAsync(h->d_b, 0, sizeof(double) * 2 * n, h->stream));
     return Err{};
   }
+  if (charge_fmm_wanted(h)) {
+    AFMPB_TRY(build_charge_fmm(h));
+    return charge_fmm_rhs(h, h->d_b);
+  }
   k_rhs<<<h->shape.nleaf, 128, 0, h->stream>>>(h->d_leaves, h->d_box_begin, h->d_box_end, h->d_box_center, h->d_pos,
                                                 h->d_nrm, h->natoms, h->d_atoms, h->d_q, kInv4Pi / h->eps_out, n,
                                                 h->d_b);
@@ -470,19 +474,23 @@ Err run_energy(afmpb_t *h, double *E) {
   if (!h->solved || !h->d_sol) return make_err(AFMPB_ESTATE, "afmpb_energy needs a prior afmpb_solve");
   if (h->natoms == 0) return make_err(AFMPB_ESTATE, "the handle has no charges");
   const int nleaf = h->shape.nleaf;
-  const int nparts = std::min(nleaf, 64);
+  const int nparts = h->cf ? 1 : std::min(nleaf, 64);
   const int lpb = div_up(nleaf, nparts);
-  const int nparts_used = div_up(nleaf, lpb);
+  const int nparts_used = h->cf ? 1 : div_up(nleaf, lpb);
   double *d_part = nullptr, *d_phi = nullptr, *d_E = nullptr;
   auto &A = h->arena;
   AFMPB_TRY(A.alloc(&d_part, (size_t)nparts_used * h->natoms, "energy partials"));
   AFMPB_TRY(A.alloc(&d_phi, h->natoms, "phi reac"));
   AFMPB_TRY(A.alloc(&d_E, 1, "energy"));
-  dim3 grid(div_up(h->natoms, 128), nparts_used);
-  k_energy_part<<<grid, 128, 0, h->stream>>>(nleaf, lpb, h->d_leaves, h->d_box_begin, h->d_box_end, h->d_box_center,
-                                              h->d_pos, h->d_nrm, h->d_sol, h->n, h->ebar, h->natoms, h->d_atoms,
-                                              d_part);
-  AFMPB_TRY(check_launch("k_energy_part"));
+  if (h->cf) {
+    AFMPB_TRY(charge_fmm_phi(h, d_part));
+  } else {
+    dim3 grid(div_up(h->natoms, 128), nparts_used);
+    k_energy_part<<<grid, 128, 0, h->stream>>>(nleaf, lpb, h->d_leaves, h->d_box_begin, h->d_box_end,
+                                                h->d_box_center, h->d_pos, h->d_nrm, h->d_sol, h->n, h->ebar,
+                                                h->natoms, h->d_atoms, d_part);
+    AFMPB_TRY(check_launch("k_energy_part"));
+  }
   const double K_c = 332.0636;   // kcal A / (mol e^2)
   k_energy_final<<<1, 256, 0, h->stream>>>(nparts_used, h->natoms, d_part, h->d_q, 4.0 * kPi * K_c, d_phi, d_E);
   AFMPB_TRY(check_launch("k_energy_final"));
@@ -532,14 +540,18 @@ Err run_energy_noalloc(afmpb_t *h, double *E) {
   double *d_phi = base + (size_t)kNoAllocParts * kNoAllocMaxAtoms;
   double *d_E = d_phi + kNoAllocMaxAtoms;
   const int nleaf = h->shape.nleaf;
-  const int nparts = std::min(nleaf, kNoAllocParts);
+  const int nparts = h->cf ? 1 : std::min(nleaf, kNoAllocParts);
   const int lpb = div_up(nleaf, nparts);
-  const int nparts_used = div_up(nleaf, lpb);
-  dim3 grid(div_up(h->natoms, 128), nparts_used);
-  k_energy_part<<<grid, 128, 0, h->stream>>>(nleaf, lpb, h->d_leaves, h->d_box_begin, h->d_box_end, h->d_box_center,
-                                              h->d_pos, h->d_nrm, h->d_sol, h->n, h->ebar, h->natoms, h->d_atoms,
-                                              d_part);
-  AFMPB_TRY(check_launch("k_energy_part (no alloc)"));
+  const int nparts_used = h->cf ? 1 : div_up(nleaf, lpb);
+  if (h->cf) {
+    AFMPB_TRY(charge_fmm_phi(h, d_part));          // the charge FMM's buffers exist already
+  } else {
+    dim3 grid(div_up(h->natoms, 128), nparts_used);
+    k_energy_part<<<grid, 128, 0, h->stream>>>(nleaf, lpb, h->d_leaves, h->d_box_begin, h->d_box_end,
+                                                h->d_box_center, h->d_pos, h->d_nrm, h->d_sol, h->n, h->ebar,
+                                                h->natoms, h->d_atoms, d_part);
+    AFMPB_TRY(check_launch("k_energy_part (no alloc)"));
+  }
   const double K_c = 332.0636;   // kcal A / (mol e^2)
   k_energy_final<<<1, 256, 0, h->stream>>>(nparts_used, h->natoms, d_part, h->d_q, 4.0 * kPi * K_c, d_phi, d_E);
   AFMPB_TRY(check_launch("k_energy_final (no alloc)"));

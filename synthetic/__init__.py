@@ -151,13 +151,15 @@ def kirkwood_sphere(subdiv: int = 7, radius: float = 20.0, n_charges: int = 64,
 # synthetic globular molecule: compact self-avoiding walk + Gaussian isosurface
 # ----------------------------------------------------------------------------------
 def compact_walk(rng: np.random.Generator, n_atoms: int, step: float = 1.5, min_dist: float = 1.0,
-                 r_confine: float | None = None, max_reject: int = 50):
+                 r_confine: float | None = None, max_reject: int = 50, axes=None):
     """Self-avoiding random walk of n_atoms points: isotropic steps of `step`, a step is
     rejected if it comes within `min_dist` of an earlier point or leaves the confinement
-    sphere; after `max_reject` rejections in a row the walk backtracks one point.
-    The default confinement radius 38.7 (N/20000)^(1/3) A gives a protein-like density."""
+    region; after `max_reject` rejections in a row the walk backtracks one point.
+    The region is the ellipsoid with semi-axes `axes` when given, else a sphere; the
+    default radius 38.7 (N/20000)^(1/3) A gives a protein-like density."""
     if r_confine is None:
         r_confine = 38.7 * (n_atoms / 20000.0) ** (1.0 / 3.0)
+    inv_ax = None if axes is None else 1.0 / np.asarray(axes, dtype=np.float64)
     cell = min_dist
     grid: dict = {}
     pts = [np.zeros(3)]
@@ -170,7 +172,11 @@ def compact_walk(rng: np.random.Generator, n_atoms: int, step: float = 1.5, min_
     while len(pts) < n_atoms:
         d = rng.standard_normal(3)
         c = pts[-1] + step * d / np.linalg.norm(d)
-        ok = np.dot(c, c) <= r_confine * r_confine
+        if inv_ax is None:
+            ok = np.dot(c, c) <= r_confine * r_confine
+        else:
+            u = c * inv_ax
+            ok = np.dot(u, u) <= 1.0
         if ok:
             kx, ky, kz = key(c)
             for dx in (-1, 0, 1):
@@ -282,6 +288,25 @@ def isosurface(values, origin, h, level=1.0, t_clip=0.01):
     return xyz, tri
 
 
+def taubin_smooth(xyz, tri, iters: int = 10, lam: float = 0.5, mu: float = -0.53):
+    """Taubin's lambda/mu smoothing (SIGGRAPH 1995): alternating umbrella steps
+    x += lam (mean of neighbours - x) and x += mu (...), which evens out the triangle
+    shapes of an isosurface without the shrinkage of plain Laplacian smoothing.  The
+    connectivity is unchanged."""
+    from scipy.sparse import coo_matrix, diags
+    n = xyz.shape[0]
+    e = np.concatenate([tri[:, [0, 1]], tri[:, [1, 2]], tri[:, [2, 0]]])
+    e = np.concatenate([e, e[:, ::-1]])
+    A = coo_matrix((np.ones(len(e)), (e[:, 0], e[:, 1])), shape=(n, n)).tocsr()
+    A.data[:] = 1.0
+    W = diags(1.0 / np.asarray(A.sum(1)).ravel()) @ A
+    x = np.array(xyz, dtype=np.float64)
+    for _ in range(iters):
+        x = x + lam * (W @ x - x)
+        x = x + mu * (W @ x - x)
+    return x
+
+
 def outer_component(xyz, tri):
     """Keep the connected surface component that contains the vertex of largest x."""
     from scipy.sparse import coo_matrix
@@ -300,11 +325,14 @@ def outer_component(xyz, tri):
 
 def globule(n_atoms: int = 20000, index: int = 2, grid: float = 0.4, beta: float = 2.3,
             eps_in: float = 2.0, eps_out: float = 80.0, kappa: float = 0.104,
-            r_confine: float | None = None) -> Molecule:
+            r_confine: float | None = None, t_clip: float = 0.2, smooth: int = 10) -> Molecule:
     """Synthetic globular protein: compact self-avoiding walk (1.5 A steps, 1.0 A exclusion,
     confinement radius 38.7 (N/20000)^(1/3) A), atomic radii U(1.2, 2.0) A, partial charges
     N(0, 0.35) e shifted to zero net charge, molecular surface = outer component of the
-    rho = 1 isosurface of the summed-Gaussian density on a `grid`-A lattice."""
+    rho = 1 isosurface of the summed-Gaussian density on a `grid`-A lattice, with edge
+    parameters clipped to [t_clip, 1 - t_clip] and `smooth` Taubin smoothing passes.
+    t_clip = 0.01 and smooth = 0 keep the raw isosurface, whose sliver triangles slow
+    GMRES down by an order of magnitude on large meshes."""
     rng = rng_for(index)
     atoms = compact_walk(rng, n_atoms, r_confine=r_confine)
     radii = rng.uniform(1.2, 2.0, n_atoms)
@@ -315,10 +343,114 @@ def globule(n_atoms: int = 20000, index: int = 2, grid: float = 0.4, beta: float
     hi = atoms.max(0) + pad
     shape = tuple(int(np.ceil((hi[d] - lo[d]) / grid)) + 1 for d in range(3))
     rho = gaussian_density(atoms, radii, lo, grid, shape, beta=beta)
-    xyz, tri = isosurface(rho, lo, grid, level=1.0)
+    xyz, tri = isosurface(rho, lo, grid, level=1.0, t_clip=t_clip)
     xyz, tri = outer_component(xyz, tri)
+    if smooth > 0:
+        xyz = taubin_smooth(xyz, tri, smooth)
     return Molecule("globule", xyz, tri, atoms, q, eps_in, eps_out, kappa,
-                    {"n_atoms": n_atoms, "grid": grid, "beta": beta})
+                    {"n_atoms": n_atoms, "grid": grid, "beta": beta, "t_clip": t_clip, "smooth": smooth})
+
+
+def icosahedral_rotations():
+    """The 60 proper rotations of the icosahedron: the closure of a 72-degree turn about
+    the vertex axis (0, 1, phi) and a 120-degree turn about the face axis (1, 1, 1)."""
+    phi = 0.5 * (1.0 + np.sqrt(5.0))
+
+    def turn(axis, ang):
+        a = np.asarray(axis, dtype=np.float64)
+        a = a / np.linalg.norm(a)
+        K = np.array([[0, -a[2], a[1]], [a[2], 0, -a[0]], [-a[1], a[0], 0]])
+        return np.eye(3) + np.sin(ang) * K + (1.0 - np.cos(ang)) * K @ K
+
+    gens = [turn((0.0, 1.0, phi), 2.0 * np.pi / 5.0), turn((1.0, 1.0, 1.0), 2.0 * np.pi / 3.0)]
+    group = [np.eye(3)]
+    frontier = [np.eye(3)]
+    while frontier:
+        nxt = []
+        for g in frontier:
+            for s in gens:
+                m = s @ g
+                if not any(np.abs(m - e).max() < 1e-9 for e in group):
+                    group.append(m)
+                    nxt.append(m)
+        frontier = nxt
+    return np.array(group)
+
+
+def _spread_direction(rots, samples: int = 4000, seed: int = 7):
+    """A unit vector whose 60 images under `rots` are as far apart as possible (best of a
+    seeded random sample of directions)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    d = rng.standard_normal((samples, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    imgs = np.einsum("gij,sj->sgi", rots, d)                    # [samples, 60, 3]
+    best, best_v = None, -1.0
+    for k in range(samples):
+        p = imgs[k]
+        g = p @ p.T
+        np.fill_diagonal(g, -2.0)
+        v = 1.0 - g.max()                                       # 1 - cos of the smallest angle
+        if v > best_v:
+            best, best_v = d[k], v
+    return best
+
+
+def capsid(n_atoms: int = 20000, copies: int = 60, r_shell: float = 250.0, thickness: float = 40.0,
+           grid: float = 1.2, index: int = 4, beta: float = 2.3, eps_in: float = 2.0, eps_out: float = 80.0,
+           kappa: float = 0.104, t_clip: float = 0.2, smooth: int = 10) -> Molecule:
+    """Virus-capsid stand-in: `copies` (at most 60) copies of one globule placed by the
+    icosahedral rotations on a shell of mean radius r_shell.  The globule is a compact walk
+    confined to an oblate ellipsoid (radial semi-axis thickness/2 + 5 A, tangential semi-axes
+    chosen for a protein-like density), radii U(1.2, 2.0) A, charges N(0, 0.35) e shifted to
+    zero net; its surface is the outer component of the rho = 1 Gaussian isosurface on a
+    `grid`-A lattice (edge parameters clipped to [t_clip, 1 - t_clip], `smooth` Taubin
+    passes, as for the globule), and every copy carries the same mesh, moved rigidly.  The copies are
+    checked to be disjoint (bounding spheres apart), so the surface is `copies` closed
+    components."""
+    rng = rng_for(index)
+    a_r = 0.5 * thickness + 5.0
+    vol = n_atoms * (4.0 / 3.0 * np.pi * 38.7 ** 3 / 20000.0)  # the globule's atom density
+    a_t = np.sqrt(vol / (4.0 / 3.0 * np.pi * a_r))
+    atoms = compact_walk(rng, n_atoms, axes=(a_t, a_t, a_r))
+    radii = rng.uniform(1.2, 2.0, n_atoms)
+    q = rng.normal(0.0, 0.35, n_atoms)
+    q -= q.mean()
+    pad = 2.5 * radii.max() + 2 * grid
+    lo = atoms.min(0) - pad
+    hi = atoms.max(0) + pad
+    shape = tuple(int(np.ceil((hi[d] - lo[d]) / grid)) + 1 for d in range(3))
+    rho = gaussian_density(atoms, radii, lo, grid, shape, beta=beta)
+    xyz, tri = isosurface(rho, lo, grid, level=1.0, t_clip=t_clip)
+    xyz, tri = outer_component(xyz, tri)
+    if smooth > 0:
+        xyz = taubin_smooth(xyz, tri, smooth)
+    rots = icosahedral_rotations()[:copies]
+    d = _spread_direction(icosahedral_rotations())
+    # rotation taking the z axis to d (Rodrigues about z x d)
+    z = np.array([0.0, 0.0, 1.0])
+    v = np.cross(z, d)
+    s_, c_ = np.linalg.norm(v), float(np.dot(z, d))
+    K = np.array([[0, -v[2], v[1]], [v[2], 0, -v[0]], [-v[1], v[0], 0]])
+    R0 = np.eye(3) + K + K @ K * ((1.0 - c_) / max(s_ * s_, 1e-300))
+    shift = np.array([0.0, 0.0, r_shell])
+    base_xyz = (xyz + shift) @ R0.T
+    base_atoms = (atoms + shift) @ R0.T
+    centre = R0 @ shift
+    r_bound = np.linalg.norm(base_xyz - centre, axis=1).max()
+    cs = np.einsum("gij,j->gi", rots, centre)
+    dist = np.linalg.norm(cs[:, None, :] - cs[None, :, :], axis=2)
+    np.fill_diagonal(dist, np.inf)
+    if dist.min() <= 2.0 * r_bound:
+        raise ValueError("capsid copies overlap: centre spacing %.1f A <= 2 x %.1f A"
+                         % (dist.min(), r_bound))
+    nb = xyz.shape[0]
+    all_xyz = np.concatenate([base_xyz @ g.T for g in rots])
+    all_tri = np.concatenate([tri + i * nb for i in range(len(rots))]).astype(np.int32)
+    all_atoms = np.concatenate([base_atoms @ g.T for g in rots])
+    all_q = np.tile(q, len(rots))
+    return Molecule("capsid", all_xyz, all_tri, all_atoms, all_q, eps_in, eps_out, kappa,
+                    {"n_atoms": n_atoms * len(rots), "copies": len(rots), "grid": grid,
+                     "copy_nodes": nb, "r_shell": r_shell, "axes": (a_t, a_t, a_r)})
 
 
 def random_unknowns(n_nodes: int, seed: int, dtype=np.float64):

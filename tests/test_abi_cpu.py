@@ -36,6 +36,11 @@ def test_host_only_entry_points():
     b1 = pb.estimate_bytes(2562, 1)
     b2 = pb.estimate_bytes(163842, 64)
     assert 0 < b1 < b2
+    # the charge FMM (forced, or above the pair threshold) adds its octree to the estimate
+    assert pb.estimate_bytes(163842, 64, charge_fmm=2) > b2
+    assert pb.estimate_bytes(163842, 64, charge_fmm=1) == b2
+    big = pb.estimate_bytes(10_000_000, 1_200_000, charge_fmm=1)
+    assert pb.estimate_bytes(10_000_000, 1_200_000) > big
     lib = pb.load()
     assert lib.afmpb_estimate_bytes(0, 0, 6, None) == 0          # invalid size
     assert lib.afmpb_estimate_bytes(100, 0, 9, None) == 0        # invalid order
@@ -71,6 +76,9 @@ def test_invalid_mesh_is_rejected_on_the_host():
     assert e.value.status == "EINVAL"
     with pytest.raises(pb.AfmpbError) as e:
         pb.Handle(xyz, tri, eps_in=1, eps_out=80, kappa=0.1, order=9)
+    assert e.value.status == "EINVAL"
+    with pytest.raises(pb.AfmpbError) as e:
+        pb.Handle(xyz, tri, eps_in=1, eps_out=80, kappa=0.1, charge_fmm=3)
     assert e.value.status == "EINVAL"
     xyz2 = xyz.copy()
     xyz2[3, 0] = np.nan

@@ -278,7 +278,9 @@ def test_mixed_precision_solve_and_energy(born):
 
 @pytest.fixture(scope="module")
 def small_globule():
-    mol = synthetic.globule(n_atoms=200)      # ~23.6k nodes, isosurface with slivers
+    # ~23.6k nodes; the raw isosurface (t_clip 0.01, no smoothing) keeps its sliver
+    # triangles, a stress case for the near-field quadrature
+    mol = synthetic.globule(n_atoms=200, t_clip=0.01, smooth=0)
     o = oracle.Oracle.for_molecule(mol)
     x = synthetic.random_unknowns(mol.n_nodes, 21)
     return mol, o, x, o.matvec(x)
