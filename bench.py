@@ -69,9 +69,9 @@ def run_config(mol, args, world, leaf_cap=None):
 # serving: many molecules of uneven size through the continuous-batching server
 # ------------------------------------------------------------------------------------
 def serving_leg(args):
-    """Solve requests on synthetic globules (atom counts log-uniform in [40, 1200], so
-    meshes of ~5k-120k nodes; kappa ~ U(0.03, 0.3)), drawn from a pool of seeded
-    molecules.  Three runs: the plain FP32 path one solve at a time (closed loop: each
+    """Solve requests on synthetic globules (atom counts log-uniform in [500, 50,000],
+    surfaces on a 1.2 A lattice, so meshes of ~6k-410k nodes; kappa ~ U(0.03, 0.3)), drawn
+    from a pool of seeded molecules.  Three runs: the plain FP32 path one solve at a time (closed loop: each
     request is submitted when the previous one has finished); the mixed path served with
     all requests submitted at once (capacity); the mixed path served under Poisson
     arrivals at 0.9x the plain capacity (latency, queueing included)."""
@@ -81,9 +81,9 @@ def serving_leg(args):
     import synthetic
 
     rng = np.random.default_rng(synthetic.SEED_BASE + 3)
-    counts = np.exp(rng.uniform(np.log(40), np.log(1200), args.serve_pool)).astype(int)
+    counts = np.exp(rng.uniform(np.log(500), np.log(50000), args.serve_pool)).astype(int)
     t0 = time.perf_counter()
-    pool = [synthetic.globule(n_atoms=int(c), index=100 + i) for i, c in enumerate(counts)]
+    pool = [synthetic.globule(n_atoms=int(c), index=100 + i, grid=1.2) for i, c in enumerate(counts)]
     t_gen = time.perf_counter() - t0
     reqs = [(int(rng.integers(len(pool))), float(rng.uniform(0.03, 0.3))) for _ in range(args.serve_requests)]
     arrivals = np.cumsum(rng.exponential(1.0, len(reqs)))      # unit-rate gaps, scaled below
@@ -129,6 +129,67 @@ def serving_leg(args):
             "pool_nodes": [m.n_nodes for m in pool], "pool_generation_s": round(t_gen, 1),
             "plain_fp32_one_at_a_time": plain, "mixed_served_burst": burst, "mixed_served_poisson": poisson,
             "energy_max_rel_diff_mixed_vs_plain": diff}
+
+
+# ------------------------------------------------------------------------------------
+# capsid scale: one 10M-node solve
+# ------------------------------------------------------------------------------------
+def capsid_leg(args, stream):
+    """Virus-capsid stand-in: 60 icosahedral copies of a 20,000-atom globule (10,455,600
+    nodes, 20,971,440 triangles, 1.2M charges), mixed precision, order 6.  Reports the
+    product throughput (CUDA events; the working set is far above L2) and the wall time of
+    the whole solve: handle setup (geometry, octree, near field, FMM operators, right-hand
+    side by the charge FMM), GMRES to 1e-6, and the energy."""
+    import numpy as np
+    import torch
+
+    import paper_1710_06316_gb300 as pb
+    import synthetic
+
+    t0 = time.perf_counter()
+    mol = synthetic.capsid()
+    t_gen = time.perf_counter() - t0
+    n = mol.n_nodes
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    h = pb.Handle.for_molecule(mol, order=args.order, tol=1e-6, precision=1, stream=stream.cuda_stream)
+    t_setup = time.perf_counter() - t0
+    info = h.info()
+    x = torch.tensor(synthetic.smooth_unknowns(mol.xyz, 1).astype(np.float32), device="cuda")
+    y = torch.empty_like(x)
+    for _ in range(3):
+        h.matvec(x, y)
+    steps = args.capsid_steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    torch.cuda.synchronize()
+    for a, b in ev:
+        a.record(stream)
+        h.matvec(x, y)
+        b.record(stream)
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+    prof = h.profile(reps=3)
+    t0 = time.perf_counter()
+    f, hh, si = h.solve(raise_on_noconv=False)
+    t_solve = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    energy = h.energy()
+    t_energy = time.perf_counter() - t0
+    h.close()
+    return {"workload": "capsid: %d copies of a %d-atom globule, %d nodes, %d triangles, %d charges, eps %g/%g, "
+                        "kappa %g, order %d, mixed precision" % (
+                            mol.meta["copies"], mol.meta["n_atoms"] // mol.meta["copies"], n, mol.n_tris,
+                            len(mol.q), mol.eps_in, mol.eps_out, mol.kappa, args.order),
+            "value": round(n / (ms * 1e-3) / 1e6, 3), "unit": UNIT, "ms_per_product": round(ms, 3),
+            "steps": steps, "stages_ms": {a: round(b, 3) for a, b, _ in prof["stages"]},
+            "full_solve_wall_s": round(t_setup + t_solve + t_energy, 3),
+            "setup_s": round(t_setup, 3), "gmres_s": round(t_solve, 3), "energy_s": round(t_energy, 3),
+            "ms_create": {k: round(v, 1) for k, v in zip(("geometry", "tree", "near", "fmm", "rhs", "graph"),
+                                                         info["ms_create"])},
+            "iters": si["iters"], "status": si["status"], "res_true": si["res_true"],
+            "energy_kcal_mol": energy, "charge_fmm": bool(info["charge_fmm"]),
+            "nnz_near": info["nnz_near"], "boxes": info["n_boxes"], "m2l_rank": info["m2l_rank"],
+            "device_gb": round(info["device_bytes_peak"] / 2**30, 2), "mesh_generation_s": round(t_gen, 1)}
 
 
 # ------------------------------------------------------------------------------------
@@ -461,6 +522,8 @@ def run_gpu(args):
         line["solve"]["energy_rel_err_vs_series"] = abs(energy / e_ref - 1)
     if rank == 0 and world == 1 and not args.no_serving:
         line["serving"] = serving_leg(args)
+    if rank == 0 and world == 1 and not args.no_capsid:
+        line["capsid"] = capsid_leg(args, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, cores, nrow, dt = oracle_rows_rate(mol, rows_target_s=args.cpu_seconds)
         line["cpu_baseline"] = {"value": round(rate / 1e6, 6), "unit": UNIT, "cores": cores, "kind": "oracle",
@@ -489,7 +552,9 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=24)
     ap.add_argument("--serve-slots", type=int, default=4)
     ap.add_argument("--serve-budget-gb", type=float, default=96.0)
-    ap.add_argument("--serve-restart", type=int, default=200)
+    ap.add_argument("--serve-restart", type=int, default=80)
+    ap.add_argument("--no-capsid", action="store_true")
+    ap.add_argument("--capsid-steps", type=int, default=10)
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--solve-reps", type=int, default=5)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)

@@ -64,6 +64,7 @@ def _load():
     lib.orc_matvec_rows.argtypes = [P, i64, P, P, P, i32]
     lib.orc_assemble.argtypes = [P, P]
     lib.orc_rhs.argtypes = [P, i64, P, P, P]
+    lib.orc_rhs_rows.argtypes = [P, i64, P, P, i64, P, P]
     lib.orc_energy.restype = dbl
     lib.orc_energy.argtypes = [P, i64, P, P, P, P, P]
     lib.orc_gmres.restype = i32
@@ -203,6 +204,15 @@ class Oracle:
         b = np.zeros(2 * self.n)
         self._lib.orc_rhs(self._h, q.size, _p(atoms), _p(q), _p(b))
         return b
+
+    def rhs_rows(self, rows, atoms, q):
+        """Rows of b: returns (b1[rows], b2[rows])."""
+        atoms = _f64(np.atleast_2d(atoms))
+        q = _f64(q)
+        rows = np.ascontiguousarray(rows, dtype=np.int64).ravel()
+        b = np.zeros(2 * rows.size)
+        self._lib.orc_rhs_rows(self._h, q.size, _p(atoms), _p(q), rows.size, _p(rows), _p(b))
+        return b[0::2].copy(), b[1::2].copy()
 
     def energy(self, atoms, q, f, h, return_phi=False):
         atoms = _f64(np.atleast_2d(atoms))

@@ -637,23 +637,35 @@ void orc_assemble(orc_ctx *c, double *M) {
 /* ------------------------------------------------------------------------------ */
 /* right-hand side (Eq. 5, reading R6) and energy (R7)                              */
 /* ------------------------------------------------------------------------------ */
+/* Row p of both blocks of the right-hand side: the charges' potential and its normal
+ * derivative at node p, over eps_out. */
+static void rhs_row(const orc_ctx *c, int64_t p, int64_t m, const double *axyz, const double *q,
+                    double *b1, double *b2) {
+    double fp = 4.0 * ORC_PI;
+    double s1 = 0, s2 = 0;
+    const double *xp = c->xyz + 3*p, *np = c->nrm + 3*p;
+    for (int64_t k = 0; k < m; k++) {
+        double d[3];
+        sub3(xp, axyz + 3*k, d);
+        double r = norm3(d);
+        s1 += q[k] / (fp * r);
+        s2 += q[k] * (-dot3(np, d)) / (fp * r * r * r);
+    }
+    *b1 = s1 / c->eps_out;
+    *b2 = s2 / c->eps_out;
+}
+
 void orc_rhs(const orc_ctx *c, int64_t m, const double *axyz, const double *q, double *b) {
     int64_t n = c->n;
-    double fp = 4.0 * ORC_PI;
 #pragma omp parallel for schedule(static)
-    for (int64_t p = 0; p < n; p++) {
-        double s1 = 0, s2 = 0;
-        const double *xp = c->xyz + 3*p, *np = c->nrm + 3*p;
-        for (int64_t k = 0; k < m; k++) {
-            double d[3];
-            sub3(xp, axyz + 3*k, d);
-            double r = norm3(d);
-            s1 += q[k] / (fp * r);
-            s2 += q[k] * (-dot3(np, d)) / (fp * r * r * r);
-        }
-        b[p] = s1 / c->eps_out;
-        b[n + p] = s2 / c->eps_out;
-    }
+    for (int64_t p = 0; p < n; p++) rhs_row(c, p, m, axyz, q, b + p, b + n + p);
+}
+
+/* Selected rows: b[2*i], b[2*i+1] = rows p = rows[i] of the two blocks. */
+void orc_rhs_rows(const orc_ctx *c, int64_t m, const double *axyz, const double *q, int64_t nr,
+                  const int64_t *rows, double *b) {
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t i = 0; i < nr; i++) rhs_row(c, rows[i], m, axyz, q, b + 2*i, b + 2*i + 1);
 }
 
 /* Reaction potential at the atoms and the polar solvation energy (kcal/mol). */

@@ -363,6 +363,17 @@ def test_kirkwood_sphere_energy():
     assert abs(r["energy"] / e_ex - 1) < 0.005
 
 
+def test_rhs_rows_equal_full_rhs():
+    """The row-sampled right-hand side (used at sizes where the full sum is too slow)
+    is the same sum as the full one, row for row, in any row order."""
+    mol = synthetic.kirkwood_sphere(subdiv=3, n_charges=50)
+    o = oracle.Oracle.for_molecule(mol)
+    b = o.rhs(mol.atoms, mol.q)
+    rows = np.array([17, 3, mol.n_nodes - 1, 0, 321])
+    b1, b2 = o.rhs_rows(rows, mol.atoms, mol.q)
+    assert np.array_equal(b1, b[rows]) and np.array_equal(b2, b[mol.n_nodes + rows])
+
+
 def test_reaction_field_reciprocity():
     """Green reciprocity: the reaction potential at charge i due to charge j equals the
     one at j due to i.  A transposed operand in RHS / operator / energy breaks it."""
