@@ -258,21 +258,20 @@ P2P_FLOP_PER_PAIR = 63
 
 
 def ncu_traffic(kernel):
-    """Per-launch DRAM bytes from the committed ncu summary, if it is still current."""
+    """Per-launch DRAM bytes from the committed ncu summary, if the source files of that
+    kernel (listed on its line) are unchanged since the capture."""
     p = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
     if not os.path.exists(p):
         return None
     import hashlib
     src = os.path.join(ROOT, "paper_1710_06316_gb300", "csrc")
-    h = hashlib.sha1()
-    for f in sorted(os.listdir(src)):
-        if f.endswith((".cu", ".cuh")):
-            h.update(open(os.path.join(src, f), "rb").read())
-    digest = h.hexdigest()[:12]
     for line in open(p):
         t = line.split()
-        if len(t) >= 3 and not line.startswith("#") and t[0] == kernel:
-            return float(t[1]) if t[2] == digest else None
+        if len(t) >= 4 and not line.startswith("#") and t[0] == kernel:
+            h = hashlib.sha1()
+            for f in t[3].split(","):
+                h.update(open(os.path.join(src, f), "rb").read())
+            return float(t[1]) if t[2] == h.hexdigest()[:12] else None
     return None
 
 
@@ -288,7 +287,7 @@ def roofline(prof, info, n, order, peaks, kind, precision):
         flop = 3 * 2.0 * r * r * info["n_m2l_pairs"] * 2
         achieved = flop / (ms * 1e-3) / 1e12
         peak = peaks["bf16_tflops"]
-        out = {"bound": "tensor", "kernel": "k_m2l_tc (tcgen05 BF16 x3, FP32 accumulate)",
+        out = {"bound": "tensor", "kernel": "k_m2l_tcp (tcgen05 BF16 x3, FP32 accumulate)",
                "unit": "TFLOP/s", "peak_kind": "measured dense BF16 GEMM (burst)"}
     elif name == "m2l":
         flop = 2.0 * r * r * info["n_m2l_pairs"] * 2        # Laplace + Yukawa
@@ -300,7 +299,7 @@ def roofline(prof, info, n, order, peaks, kind, precision):
         flop = float(P2P_FLOP_PER_PAIR) * info["n_p2p_pairs"]
         achieved = flop / (ms * 1e-3) / 1e12
         peak = fp32_peak_tflops(sm_max)
-        out = {"bound": "alu", "kernel": "k_p2p_v3 (FP32 FMA + MUFU)", "unit": "TFLOP/s",
+        out = {"bound": "alu", "kernel": "k_p2p (packed FP32x2 FMA + MUFU)", "unit": "TFLOP/s",
                "peak_kind": "FP32 FMA: 152 SM x 128 lanes x 2 x %.0f MHz" % sm_max}
     else:   # combine / near SpMV and the rest are memory-bound
         byts = info["nnz_near"] * 20.0 + n * (8 + 16 + 16 + 8)

@@ -430,6 +430,7 @@ __global__ void __launch_bounds__(kL2PThreads, 12) k_l2p(const int32_t *__restri
 // P2P (lists 1 and 3): point (far-rule) sums over t != p, both kernels, both outputs.
 // ------------------------------------------------------------------------------------
 constexpr int kP2PChunk = 768;      // sources staged in shared memory at a time (8 CTAs/SM)
+constexpr int kP2PPairs = kP2PChunk / 2;
 constexpr int kP2PBoxes = 64;       // source boxes described in shared memory at a time
 
 // Far-rule sums of one source at one target, without the 1/(4 pi):
@@ -437,54 +438,86 @@ constexpr int kP2PBoxes = 64;       // source boxes described in shared memory a
 //   dn PhiL += -c (n0.d)/r^3 + (g/eps_bar) [(n0.n)/r^3 - 3 (n.d)(n0.d)/r^5]
 //   PhiY += c e/r + g (n.d) e1/r^3,           e = exp(-kr), e1 = e (1 + kr)
 //   dn PhiY += e1 [g (n0.n) - c (n0.d)]/r^3 - 3 g e2 (n.d)(n0.d)/r^5,  e2 = e (1 + kr + (kr)^2/3)
-// with d = x_target - y_source.  g enters only through the vector g n, which the staging
-// stores in place of n: y = (source position, c), q = (g n, scaled skip radius).
-__device__ __forceinline__ void p2p_pair(const float4 &xp, const float4 &np, float rsp, const float4 &y,
-                                         const float4 &q, float inv_ebar, float kappa, float &sL, float &dL,
-                                         float &sY, float &dY) {
-  const float dx = xp.x - y.x, dy = xp.y - y.y, dz = xp.z - y.z;
-  const float r2 = p2p_r2(dx, dy, dz);
-  // Pairs inside the skip radius (t == p among them) contribute nothing here: the near
-  // CSR carries their whole near-rule value.
-  const float ri = p2p_evaluates(r2, rsp, q.w) ? rsqrtf(r2) : 0.0f;
-  const float ri2 = ri * ri;
-  const float G3 = ri * ri2;
-  const float gnd = fmaf(q.x, dx, fmaf(q.y, dy, q.z * dz));     // g n.d
-  const float npd = fmaf(np.x, dx, fmaf(np.y, dy, np.z * dz));  // n0.d
-  const float gnn = fmaf(np.x, q.x, fmaf(np.y, q.y, np.z * q.z));  // g n0.n
-  const float kr = kappa * (r2 * ri);
-  const float ex = __expf(-kr);
-  const float e1 = fmaf(ex, kr, ex);
-  const float e2 = fmaf(ex * kr, kr * (1.0f / 3.0f), e1);
-  const float c = y.w;
-  const float cri = c * ri;
-  const float A = gnd * G3;
-  const float B = gnn * G3;
-  const float cnG3 = c * (npd * G3);
-  const float T = 3.0f * A * npd * ri2;
-  sL += fmaf(inv_ebar, A, cri);
-  dL += fmaf(inv_ebar, B - T, -cnG3);
-  sY = fmaf(ex, cri, fmaf(e1, A, sY));
-  dY = fmaf(e1, B - cnG3, fmaf(-e2, T, dY));
+// with d = x_target - y_source.  g enters only through the vector g n.
+//
+// The sums run on packed FP32 pairs (sm_100 FFMA2 / FADD2 / FMUL2): each thread takes
+// its target against two sources per instruction, lane 0 an even and lane 1 an odd
+// source of the staged chunk.  The target's coordinates, normal and skip radius sit in
+// both lanes for the whole loop; the staging stores every source component already
+// paired with its neighbour's, so no instruction of the loop packs or broadcasts.
+// Every packed operation rounds each lane as its scalar counterpart does, so the
+// distance and skip test below are the scalar p2p_r2 / p2p_evaluates, bit for bit.
+__device__ __forceinline__ float2 dup2(float a) { return make_float2(a, a); }
+
+// 2^x on the special-function unit (PTX ex2.approx); e^-kr = 2^(-kr log2 e).
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
 }
 
-__global__ void __launch_bounds__(kP2PThreads, 8) k_p2p_v3(const int32_t *__restrict__ order,
-                                                         const int32_t *__restrict__ leaves,
-                                                         const int64_t *__restrict__ pptr,
-                                                         const int32_t *__restrict__ pidx,
-                                                         const int32_t *__restrict__ bbeg,
-                                                         const int32_t *__restrict__ bend,
-                                                         const dbl4 *__restrict__ center,
-                                                         const float4 *__restrict__ pos,
-                                                         const float4 *__restrict__ nrm,
-                                                         const float2 *__restrict__ xs, float inv_ebar,
-                                                         float kappa, float skip_scale,
-                                                         float4 *__restrict__ phi) {
-  static_assert(kP2PThreads <= kP2PChunk, "the reduction reuses the staging buffer");
-  __shared__ float4 sp[kP2PChunk], sn[kP2PChunk];
+struct P2PTarget {
+  float2 x, y, z;        // position in the target leaf's frame, both lanes
+  float2 nx, ny, nz;     // unit normal n0
+  float2 rs;             // scaled skip radius
+};
+
+// sources: a = (-x0, -x1, -y0, -y1), b = (-z0, -z1, c0, c1), c = (gnx0, gnx1, gny0, gny1),
+// d = (gnz0, gnz1, skip0, skip1); positions in the target leaf's frame.
+__device__ __forceinline__ void p2p_pair2(const P2PTarget &t, const float4 &a, const float4 &b, const float4 &c,
+                                          const float4 &d, float2 inv_e, float2 kappa, float2 &sL, float2 &nD,
+                                          float2 &sY, float2 &dY) {
+  const float2 dx = __fadd2_rn(t.x, make_float2(a.x, a.y));
+  const float2 dy = __fadd2_rn(t.y, make_float2(a.z, a.w));
+  const float2 dz = __fadd2_rn(t.z, make_float2(b.x, b.y));
+  const float2 cc = make_float2(b.z, b.w);
+  const float2 gx = make_float2(c.x, c.y), gy = make_float2(c.z, c.w), gz = make_float2(d.x, d.y);
+  const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));   // p2p_r2
+  const float2 R = __fadd2_rn(t.rs, make_float2(d.z, d.w));                        // p2p_evaluates
+  const float2 RR = __fmul2_rn(R, R);
+  // Pairs inside the skip radius (t == p among them) contribute nothing here: the near
+  // CSR carries their whole near-rule value.
+  const float2 ri = make_float2(r2.x > RR.x ? rsqrtf(r2.x) : 0.0f, r2.y > RR.y ? rsqrtf(r2.y) : 0.0f);
+  const float2 ri2 = __fmul2_rn(ri, ri);
+  const float2 G3 = __fmul2_rn(ri, ri2);
+  const float2 gnd = __ffma2_rn(gx, dx, __ffma2_rn(gy, dy, __fmul2_rn(gz, dz)));      // g n.d
+  const float2 npd = __ffma2_rn(t.nx, dx, __ffma2_rn(t.ny, dy, __fmul2_rn(t.nz, dz)));  // n0.d
+  const float2 gnn = __ffma2_rn(t.nx, gx, __ffma2_rn(t.ny, gy, __fmul2_rn(t.nz, gz)));  // g n0.n
+  const float2 kr = __fmul2_rn(kappa, __fmul2_rn(r2, ri));
+  const float2 arg = __fmul2_rn(kr, dup2(-1.4426950408889634f));
+  const float2 ex = make_float2(ex2_approx(arg.x), ex2_approx(arg.y));
+  const float2 e1 = __ffma2_rn(ex, kr, ex);
+  const float2 e2 = __ffma2_rn(__fmul2_rn(ex, kr), __fmul2_rn(kr, dup2(1.0f / 3.0f)), e1);
+  const float2 cri = __fmul2_rn(cc, ri);
+  const float2 A = __fmul2_rn(gnd, G3);
+  const float2 B = __fmul2_rn(gnn, G3);
+  const float2 npdG3 = __fmul2_rn(npd, G3);
+  const float2 Tn = __fmul2_rn(__fmul2_rn(__fmul2_rn(A, dup2(-3.0f)), npd), ri2);     // -T
+  sL = __fadd2_rn(sL, __ffma2_rn(inv_e, A, cri));
+  // nD accumulates -dn PhiL = c (n0.d)/r^3 - (1/eps_bar)(B - T)
+  nD = __ffma2_rn(__fmul2_rn(inv_e, dup2(-1.0f)), __fadd2_rn(B, Tn), __ffma2_rn(cc, npdG3, nD));
+  sY = __ffma2_rn(ex, cri, __ffma2_rn(e1, A, sY));
+  const float2 BmC = __ffma2_rn(__fmul2_rn(cc, dup2(-1.0f)), npdG3, B);             // B - c (n0.d)/r^3
+  dY = __ffma2_rn(e1, BmC, __ffma2_rn(e2, Tn, dY));
+}
+
+__global__ void __launch_bounds__(kP2PThreads, 8) k_p2p(const int32_t *__restrict__ order,
+                                                      const int32_t *__restrict__ leaves,
+                                                      const int64_t *__restrict__ pptr,
+                                                      const int32_t *__restrict__ pidx,
+                                                      const int32_t *__restrict__ bbeg,
+                                                      const int32_t *__restrict__ bend,
+                                                      const dbl4 *__restrict__ center,
+                                                      const float4 *__restrict__ pos,
+                                                      const float4 *__restrict__ nrm,
+                                                      const float2 *__restrict__ xs, float inv_ebar,
+                                                      float kappa, float skip_scale,
+                                                      float4 *__restrict__ phi) {
+  static_assert(kP2PThreads <= kP2PPairs, "the reduction reuses the staging buffer");
+  __shared__ float4 sa[kP2PPairs], sb[kP2PPairs], sc[kP2PPairs], sd[kP2PPairs];
   __shared__ int s_beg[kP2PBoxes], s_pre[kP2PBoxes + 1];
   __shared__ float s_off[kP2PBoxes][3];
-  float4 *red = sp;
+  float4 *red = sa;
   const int leaf = order[blockIdx.x];
   const int b = leaves[leaf];
   const dbl4 cb = center[b];
@@ -494,13 +527,17 @@ __global__ void __launch_bounds__(kP2PThreads, 8) k_p2p_v3(const int32_t *__rest
   const int ti = threadIdx.x % tile, si = threadIdx.x / tile;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t l0 = pptr[leaf], l1 = pptr[leaf + 1];
+  const float2 inv_e = dup2(inv_ebar), kap = dup2(kappa);
   for (int t0 = tb; t0 < te; t0 += tile) {
     const int t = t0 + ti;
     const bool act = si < slices && t < te;
     const float4 xp = act ? pos[t] : make_float4(0, 0, 0, 0);
     const float4 np = act ? nrm[t] : make_float4(0, 0, 0, 0);
-    const float rsp = p2p_skip_radius(skip_scale, np.w);
-    float sL = 0.f, dL = 0.f, sY = 0.f, dY = 0.f;
+    P2PTarget tg;
+    tg.x = dup2(xp.x); tg.y = dup2(xp.y); tg.z = dup2(xp.z);
+    tg.nx = dup2(np.x); tg.ny = dup2(np.y); tg.nz = dup2(np.z);
+    tg.rs = dup2(p2p_skip_radius(skip_scale, np.w));
+    float2 sL = dup2(0.f), nD = dup2(0.f), sY = dup2(0.f), dY = dup2(0.f);
     for (int64_t g0 = l0; g0 < l1; g0 += kP2PBoxes) {
       const int nb = (int)min((int64_t)kP2PBoxes, l1 - g0);
       __syncthreads();
@@ -530,31 +567,46 @@ __global__ void __launch_bounds__(kP2PThreads, 8) k_p2p_v3(const int32_t *__rest
       const int total = s_pre[nb];
       for (int c0 = 0; c0 < total; c0 += kP2PChunk) {
         const int cnt = min(kP2PChunk, total - c0);
+        const int npairs = (cnt + 1) >> 1;
         if (c0 > 0) __syncthreads();
-        for (int e = threadIdx.x; e < cnt; e += kP2PThreads) {
-          const int j = c0 + e;
-          int lo = 0, hi = nb;              // last box with s_pre[box] <= j
-          while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (s_pre[mid] <= j) lo = mid; else hi = mid;
+        for (int e = threadIdx.x; e < 2 * npairs; e += kP2PThreads) {
+          float px = 0.f, py = 0.f, pz = 0.f, cw = 0.f, gx = 0.f, gy = 0.f, gz = 0.f, rs = 3.0e18f;
+          if (e < cnt) {                    // the odd slot past the end stays a never-evaluated pad
+            const int j = c0 + e;
+            int lo = 0, hi = nb;            // last box with s_pre[box] <= j
+            while (hi - lo > 1) {
+              const int mid = (lo + hi) >> 1;
+              if (s_pre[mid] <= j) lo = mid; else hi = mid;
+            }
+            const int sidx = s_beg[lo] + (j - s_pre[lo]);
+            const float4 p = pos[sidx], q = nrm[sidx];
+            const float2 fh = xs[sidx];
+            px = __fadd_rn(p.x, s_off[lo][0]);
+            py = __fadd_rn(p.y, s_off[lo][1]);
+            pz = __fadd_rn(p.z, s_off[lo][2]);
+            cw = p.w * fh.y;
+            const float g = -p.w * fh.x;
+            gx = g * q.x; gy = g * q.y; gz = g * q.z;
+            rs = p2p_skip_radius(skip_scale, q.w);
           }
-          const int sidx = s_beg[lo] + (j - s_pre[lo]);
-          const float4 p = pos[sidx], q = nrm[sidx];
-          const float2 fh = xs[sidx];
-          sp[e] = make_float4(__fadd_rn(p.x, s_off[lo][0]), __fadd_rn(p.y, s_off[lo][1]),
-                              __fadd_rn(p.z, s_off[lo][2]), p.w * fh.y);
-          const float g = -p.w * fh.x;
-          sn[e] = make_float4(g * q.x, g * q.y, g * q.z, p2p_skip_radius(skip_scale, q.w));
+          const int pr = e >> 1, ln = e & 1;
+          float *fa = reinterpret_cast<float *>(sa + pr), *fb = reinterpret_cast<float *>(sb + pr);
+          float *fc = reinterpret_cast<float *>(sc + pr), *fd = reinterpret_cast<float *>(sd + pr);
+          fa[ln] = -px; fa[2 + ln] = -py;
+          fb[ln] = -pz; fb[2 + ln] = cw;
+          fc[ln] = gx; fc[2 + ln] = gy;
+          fd[ln] = gz; fd[2 + ln] = rs;
         }
         __syncthreads();
         if (act) {
-#pragma unroll 4
-          for (int e = si; e < cnt; e += slices) p2p_pair(xp, np, rsp, sp[e], sn[e], inv_ebar, kappa, sL, dL, sY, dY);
+#pragma unroll 2
+          for (int e = si; e < npairs; e += slices)
+            p2p_pair2(tg, sa[e], sb[e], sc[e], sd[e], inv_e, kap, sL, nD, sY, dY);
         }
       }
     }
     __syncthreads();
-    red[threadIdx.x] = make_float4(sL, dL, sY, dY);
+    red[threadIdx.x] = make_float4(sL.x + sL.y, -(nD.x + nD.y), sY.x + sY.y, dY.x + dY.y);
     __syncthreads();
     if (si == 0 && t < te) {
       float4 a = red[ti];
@@ -733,11 +785,11 @@ Err enqueue_far(afmpb_t *h, cudaStream_t s, StageTimer *tm) {
 }
 
 Err enqueue_p2p(afmpb_t *h, cudaStream_t s) {
-  k_p2p_v3<<<h->shape.nleaf, kP2PThreads, 0, s>>>(h->d_p2p_order, h->d_leaves, h->d_p2p_ptr, h->d_p2p_idx, h->d_box_begin,
+  k_p2p<<<h->shape.nleaf, kP2PThreads, 0, s>>>(h->d_p2p_order, h->d_leaves, h->d_p2p_ptr, h->d_p2p_idx, h->d_box_begin,
                                                   h->d_box_end, h->d_box_center, h->d_pos, h->d_nrm, h->d_xs,
                                                   (float)(1.0 / h->ebar), (float)h->kappa,
                                                   (float)(kP2PSkip * h->opt.near_c), h->d_phi_near);
-  return check_launch("k_p2p_v3");
+  return check_launch("k_p2p");
 }
 
 Err enqueue_combine(afmpb_t *h, cudaStream_t s, int parts) {
