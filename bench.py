@@ -508,7 +508,8 @@ def run_gpu(args):
             "ms_graph_profile": round(prof["ms_graph"], 5),
             "tree": {"boxes": info["n_boxes"], "leaves": info["n_leaves"], "levels": info["n_levels"],
                      "nnz_near": info["nnz_near"], "p2p_pairs": info["n_p2p_pairs"],
-                     "m2l_pairs": info["n_m2l_pairs"], "ms_create": [round(v, 1) for v in info["ms_create"]]},
+                     "m2l_pairs": info["n_m2l_pairs"], "m2l_rank": info["m2l_rank"],
+                     "m2l_tables": info["m2l_tables"], "ms_create": [round(v, 1) for v in info["ms_create"]]},
             "solve": dict(lat, status=sinfo["status"], iters=sinfo["iters"],
                           ms_gmres=round(sinfo["ms_gmres"], 2), res_true=sinfo["res_true"],
                           energy_kcal_mol=energy),
