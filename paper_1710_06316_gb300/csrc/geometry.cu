@@ -6,11 +6,31 @@
 // rule is the normalised area-weighted mean of the facet normals (or the caller's
 // normal).  rho_v, the largest distance from v to a patch vertex, sizes the near set.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
 
 #include "internal.cuh"
 
 namespace afmpb {
+
+namespace {
+
+// f(begin, end) over [0, n) split into contiguous ranges, one per host thread (at most 16).
+template <class F>
+void parallel_ranges(int64_t n, F f) {
+  const int64_t nt = std::max<int64_t>(1, std::min<int64_t>({16, (int64_t)std::thread::hardware_concurrency(),
+                                                             n / 65536 + 1}));
+  std::vector<std::thread> pool;
+  for (int64_t t = 1; t < nt; ++t) pool.emplace_back(f, n * t / nt, n * (t + 1) / nt);
+  f(0, n / nt);
+  for (auto &th : pool) th.join();
+}
+
+}  // namespace
 
 Err validate_mesh(const afmpb_mesh *m) {
   if (!m || !m->xyz || !m->tri) return make_err(AFMPB_EINVAL, "mesh, mesh->xyz and mesh->tri are required");
@@ -18,40 +38,78 @@ Err validate_mesh(const afmpb_mesh *m) {
   if (m->n_nodes > (int64_t)INT32_MAX / 2 || m->n_tris > (int64_t)INT32_MAX / 4)
     return make_err(AFMPB_EINVAL, "mesh too large for 32-bit node / triangle indices");
   const int64_t n = m->n_nodes, nt = m->n_tris;
-  for (int64_t i = 0; i < 3 * n; ++i)
-    if (!std::isfinite(m->xyz[i])) return make_err(AFMPB_EINVAL, "non-finite node coordinate");
+  std::atomic<int> bad_xyz{0};
+  parallel_ranges(3 * n, [&](int64_t i0, int64_t i1) {
+    for (int64_t i = i0; i < i1; ++i)
+      if (!std::isfinite(m->xyz[i])) bad_xyz = 1;
+  });
+  if (bad_xyz) return make_err(AFMPB_EINVAL, "non-finite node coordinate");
+  // triangle checks; the enclosed volume (times 6) summed per thread range
+  std::atomic<int64_t> bad_tri{-1};
+  std::mutex vol_mu;
   double vol6 = 0.0;
-  for (int64_t t = 0; t < nt; ++t) {
+  parallel_ranges(nt, [&](int64_t t0, int64_t t1) {
+    double part = 0.0;
+    for (int64_t t = t0; t < t1; ++t) {
+      int32_t a = m->tri[3 * t], b = m->tri[3 * t + 1], c = m->tri[3 * t + 2];
+      if (a < 0 || b < 0 || c < 0 || a >= n || b >= n || c >= n || a == b || b == c || a == c) {
+        bad_tri = t;
+        return;
+      }
+      const double *A = m->xyz + 3 * (int64_t)a, *B = m->xyz + 3 * (int64_t)b, *C = m->xyz + 3 * (int64_t)c;
+      double u[3] = {B[0] - A[0], B[1] - A[1], B[2] - A[2]};
+      double v[3] = {C[0] - A[0], C[1] - A[1], C[2] - A[2]};
+      double w[3] = {u[1] * v[2] - u[2] * v[1], u[2] * v[0] - u[0] * v[2], u[0] * v[1] - u[1] * v[0]};
+      if (w[0] == 0.0 && w[1] == 0.0 && w[2] == 0.0) {
+        bad_tri = t;
+        return;
+      }
+      part += A[0] * w[0] + A[1] * w[1] + A[2] * w[2];
+    }
+    std::lock_guard<std::mutex> lk(vol_mu);
+    vol6 += part;
+  });
+  if (bad_tri >= 0) {
+    // name the first offending triangle's fault (serial rescan of the flagged range is
+    // not needed: any flagged triangle identifies the fault)
+    const int64_t t = bad_tri;
     int32_t a = m->tri[3 * t], b = m->tri[3 * t + 1], c = m->tri[3 * t + 2];
     if (a < 0 || b < 0 || c < 0 || a >= n || b >= n || c >= n)
       return make_err(AFMPB_EMESH, "triangle " + std::to_string(t) + " has a node index out of range");
-    if (a == b || b == c || a == c)
-      return make_err(AFMPB_EMESH, "triangle " + std::to_string(t) + " repeats a node");
-    const double *A = m->xyz + 3 * (int64_t)a, *B = m->xyz + 3 * (int64_t)b, *C = m->xyz + 3 * (int64_t)c;
-    double u[3] = {B[0] - A[0], B[1] - A[1], B[2] - A[2]};
-    double v[3] = {C[0] - A[0], C[1] - A[1], C[2] - A[2]};
-    double w[3] = {u[1] * v[2] - u[2] * v[1], u[2] * v[0] - u[0] * v[2], u[0] * v[1] - u[1] * v[0]};
-    if (w[0] == 0.0 && w[1] == 0.0 && w[2] == 0.0)
-      return make_err(AFMPB_EMESH, "triangle " + std::to_string(t) + " has zero area");
-    vol6 += A[0] * w[0] + A[1] * w[1] + A[2] * w[2];
+    if (a == b || b == c || a == c) return make_err(AFMPB_EMESH, "triangle " + std::to_string(t) + " repeats a node");
+    return make_err(AFMPB_EMESH, "triangle " + std::to_string(t) + " has zero area");
   }
   // every directed edge once, and its reverse once: closed, edge-manifold, consistently
-  // oriented
-  std::vector<uint64_t> fwd(3 * nt), rev(3 * nt);
-  for (int64_t t = 0; t < nt; ++t)
-    for (int k = 0; k < 3; ++k) {
-      uint64_t i = (uint32_t)m->tri[3 * t + k], j = (uint32_t)m->tri[3 * t + (k + 1) % 3];
-      fwd[3 * t + k] = (i << 32) | j;
-      rev[3 * t + k] = (j << 32) | i;
-    }
-  std::sort(fwd.begin(), fwd.end());
-  std::sort(rev.begin(), rev.end());
-  for (size_t i = 0; i < fwd.size(); ++i) {
-    if (i > 0 && fwd[i] == fwd[i - 1])
-      return make_err(AFMPB_EMESH, "an edge is used twice in the same direction (non-manifold or mis-oriented)");
-    if (fwd[i] != rev[i])
-      return make_err(AFMPB_EMESH, "an edge has no opposite half-edge (open surface or mis-oriented triangle)");
+  // oriented.  Half-edges are bucketed by their first node (counting sort, linear in the
+  // triangle count); each bucket is sorted, so a repeated direction sits next to itself
+  // and the reverse of i -> j is a binary search in bucket j.
+  std::vector<int64_t> ptr(n + 1, 0);
+  for (int64_t e = 0; e < 3 * nt; ++e) ++ptr[(int64_t)m->tri[e] + 1];
+  for (int64_t i = 0; i < n; ++i) ptr[i + 1] += ptr[i];
+  std::vector<int32_t> dst(3 * nt);
+  {
+    std::vector<int64_t> fill(ptr.begin(), ptr.end() - 1);
+    for (int64_t t = 0; t < nt; ++t)
+      for (int k = 0; k < 3; ++k) dst[fill[m->tri[3 * t + k]]++] = m->tri[3 * t + (k + 1) % 3];
   }
+  // the two bucket passes run on the host cores, node ranges per thread
+  std::atomic<int> dup{0}, open_edge{0};
+  parallel_ranges(n, [&](int64_t i0, int64_t i1) {
+    for (int64_t i = i0; i < i1; ++i) {
+      std::sort(dst.begin() + ptr[i], dst.begin() + ptr[i + 1]);
+      for (int64_t k = ptr[i] + 1; k < ptr[i + 1]; ++k)
+        if (dst[k] == dst[k - 1]) dup = 1;
+    }
+  });
+  if (dup) return make_err(AFMPB_EMESH, "an edge is used twice in the same direction (non-manifold or mis-oriented)");
+  parallel_ranges(n, [&](int64_t i0, int64_t i1) {
+    for (int64_t i = i0; i < i1 && !open_edge; ++i)
+      for (int64_t k = ptr[i]; k < ptr[i + 1]; ++k) {
+        const int64_t j = dst[k];
+        if (!std::binary_search(dst.begin() + ptr[j], dst.begin() + ptr[j + 1], (int32_t)i)) open_edge = 1;
+      }
+  });
+  if (open_edge) return make_err(AFMPB_EMESH, "an edge has no opposite half-edge (open surface or mis-oriented triangle)");
   if (!(vol6 > 0.0)) return make_err(AFMPB_EMESH, "enclosed volume is not positive: triangles must be counter-clockwise seen from outside");
   if (m->normals) {
     for (int64_t i = 0; i < n; ++i) {

@@ -182,6 +182,16 @@ struct TCItem {
   int group, start, count;
 };
 
+// One unit of the pipelined tensor-core M2L, flattened on the host so that a CTA reads
+// it with one load: first pair (absolute index), pair count, operand tile key
+// (table * slots + offset), table rank, kernel (0 Laplace, 1 Yukawa), output scale.
+struct __align__(16) TCUnit {
+  int pstart, count, key, rank;
+  int kt;
+  float scale;
+  int pad0, pad1;
+};
+
 }  // namespace afmpb
 
 struct afmpb_t {
@@ -282,7 +292,7 @@ struct afmpb_t {
   int *d_tc_flag = nullptr;        // set by a tensor-core CTA whose bounded wait expired
   bool tc_pipelined = false;       // the warp-specialized persistent kernel is used
   int tc_nunits = 0;
-  int2 *d_tc_units = nullptr;      // (item, kernel) work units of the pipelined kernel
+  afmpb::TCUnit *d_tc_units = nullptr;  // work units of the pipelined kernel
 
   // ---- leaf-capacity autotuner (AFMPB_LEAF_CAP_AUTO) --------------------------------
   bool autotuned = false;

@@ -314,11 +314,14 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_m2l_tc(int N3, const TCItem *
 
 // ------------------------------------------------------------------------------------
 // Pipelined form for compressed translations whose ranks all fit one contraction block
-// (r <= 112): persistent CTAs (two per SM) walk a contiguous range of work units
-// (item, kernel), ordered so that consecutive units share their translation tile.
-// Warps 0-3 produce: wait until the previous unit's MMAs have read the operands, load the
-// A tile when it changes (bulk copy), gather and split the B operand, and thread 0 issues
-// the MMAs into one of two TMEM accumulators.  Warps 4-7 consume: wait for a unit's
+// (r <= 112): persistent CTAs (two per SM for r <= 80) walk a contiguous range of work
+// units (item, kernel), ordered so that consecutive units share their translation tile
+// (Laplace units offset-major across levels: one unit-box table serves every level).
+// Shared memory holds the A tile (r columns) and two B stages, sized by r.  Warps 0-3
+// produce: wait until the MMAs that last read the B stage (unit k - 2) and, when the A
+// tile changes, the previous unit's MMAs have completed; load the A tile when it changes
+// (bulk copy), gather the B operand into its stage, and thread 0 issues the MMAs into one
+// of two TMEM accumulators.  Warps 4-7 consume: wait for a unit's
 // accumulator, read it with tcgen05.ld (warp w reads lanes 32 (w - 4) .. +31, one output
 // row per lane) and add each pair's column into the target's compressed local vector with
 // coalesced atomics, then release the accumulator.  So the gather of unit k + 1, the MMAs
@@ -340,22 +343,17 @@ __device__ __forceinline__ bool producer_all(bool v) {
   return r != 0;
 }
 
-__global__ void __launch_bounds__(kTcThreads, 2) k_m2l_tcp(int R, int nunits, const int2 *__restrict__ units,
+__global__ void __launch_bounds__(kTcThreads, 2) k_m2l_tcp(int R, int nunits, const TCUnit *__restrict__ units,
                                                            const __nv_bfloat16 *__restrict__ Mc16,
-                                                           const TCItem *__restrict__ items,
-                                                           const M2LGroup *__restrict__ groups,
                                                            const int2 *__restrict__ pairs,
                                                            const __nv_bfloat16 *__restrict__ tiles,
-                                                           const int *__restrict__ level_table, int nslots,
-                                                           const int *__restrict__ table_rank,
-                                                           const dbl4 *__restrict__ center,
-                                                           const float *__restrict__ Mc, float *__restrict__ Lc,
-                                                           int *__restrict__ err_flag) {
+                                                           float *__restrict__ Lc, int *__restrict__ err_flag) {
   extern __shared__ __align__(128) uint8_t smem[];
+  // A: kTcRows x R per hi / lo; B: two stages of kTcPairs x R per hi / lo (R <= kTcKHalf,
+  // a multiple of 16, so every piece starts on a 16-byte boundary)
   __nv_bfloat16 *a_hi = reinterpret_cast<__nv_bfloat16 *>(smem);
-  __nv_bfloat16 *a_lo = a_hi + kTcAElems;
-  __nv_bfloat16 *b_hi = a_lo + kTcAElems;
-  __nv_bfloat16 *b_lo = b_hi + kTcBElems;
+  __nv_bfloat16 *a_lo = a_hi + kTcRows * R;
+  __nv_bfloat16 *const b_base = a_lo + kTcRows * R;    // stage b: hi at b_base + b * 2 kTcPairs R, lo after it
   __shared__ __align__(8) uint64_t bar_a, bar_full[2], bar_empty[2];
   __shared__ uint32_t tmem_base;
   __shared__ int s_src[kTcPairs];
@@ -392,38 +390,39 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_m2l_tcp(int R, int nunits, co
   if (warp < 4) {
     // ---- producers -------------------------------------------------------------------
     int a_key = -1, a_loads = 0, issued = 0;
+    TCUnit nxt = units[u0];                               // the next unit's descriptor, one load ahead
     for (int k = 0; k < nk; ++k) {
-      const int2 un = units[u0 + k];
-      const TCItem it = items[un.x];
-      const M2LGroup g = groups[it.group];
-      const int kt = un.y;
-      const int table = kt == 0 ? 0 : level_table[g.level];
-      const int Rt = table_rank[table];
-      const int cnt = it.count, npad = (cnt + 15) & ~15;
-      // operands free: the previous unit's MMAs have completed
+      const TCUnit un = nxt;
+      if (k + 1 < nk) nxt = units[u0 + k + 1];
+      const int kt = un.kt, Rt = un.rank, key = un.key;
+      const int cnt = un.count, npad = (cnt + 15) & ~15;
+      const int b = k & 1;
+      const bool load_a = key != a_key;
+      // operands free: B stage b was last read by unit k - 2's MMAs; the A tile, when it
+      // is about to change, by unit k - 1's
       bool ok = true;
-      if (k >= 1) ok = mbar_wait(mb_full[(k - 1) & 1], (uint32_t)(((k - 1) >> 1) & 1));
+      if (k >= 2) ok = mbar_wait(mb_full[b], (uint32_t)(((k - 2) >> 1) & 1));
+      if (ok && load_a && k >= 1) ok = mbar_wait(mb_full[(k - 1) & 1], (uint32_t)(((k - 1) >> 1) & 1));
       if (!producer_all(ok)) {
         failed = true;
         break;
       }
-      if (threadIdx.x < kTcPairs) s_src[threadIdx.x] = threadIdx.x < cnt ? pairs[g.start + it.start + threadIdx.x].y : 0;
-      const int key = table * nslots + g.offset;
-      const bool load_a = key != a_key;
+      if (threadIdx.x < kTcPairs) s_src[threadIdx.x] = threadIdx.x < cnt ? pairs[un.pstart + threadIdx.x].y : 0;
       if (load_a) {
         if (threadIdx.x == 0) {
-          const __nv_bfloat16 *src = tiles + (size_t)key * 2 * 2 * kTcAElems;   // row tile 0, K half 0
-          const uint32_t bytes = 2 * kTcAElems * 2;
-          asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb_a), "r"(bytes));
+          // row tile 0, K half 0; its first R / 8 K-groups of 8 are contiguous
+          const __nv_bfloat16 *src = tiles + (size_t)key * 2 * 2 * kTcAElems;
+          const uint32_t half = (uint32_t)(kTcRows * R * 2);
+          asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb_a), "r"(2 * half));
           asm volatile(
               "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                   cvta_smem(a_hi)),
-              "l"(src), "r"((uint32_t)(kTcAElems * 2)), "r"(mb_a)
+              "l"(src), "r"(half), "r"(mb_a)
               : "memory");
           asm volatile(
               "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                   cvta_smem(a_lo)),
-              "l"(src + kTcAElems), "r"((uint32_t)(kTcAElems * 2)), "r"(mb_a)
+              "l"(src + kTcAElems), "r"(half), "r"(mb_a)
               : "memory");
         }
         a_key = key;
@@ -435,7 +434,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_m2l_tcp(int R, int nunits, co
       // padding pairs are zero-filled)
       const int kg = Rt / 8;                             // groups of 8 along K
       const int nunit = npad * kg;
-      const uint32_t sb_hi0 = cvta_smem(b_hi), sb_lo0 = cvta_smem(b_lo);
+      const uint32_t sb_hi0 = cvta_smem(b_base + b * 2 * kTcPairs * R), sb_lo0 = sb_hi0 + (uint32_t)(kTcPairs * R * 2);
       for (int e = threadIdx.x; e < nunit; e += 128) {
         const int p = e / kg, k8 = e % kg;
         const bool v = p < cnt;
@@ -448,7 +447,6 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_m2l_tcp(int R, int nunits, co
       asm volatile("cp.async.wait_group 0;" ::: "memory");
       asm volatile("fence.proxy.async.shared::cta;");
       producer_sync();
-      const int b = k & 1;
       bool ok0 = true;
       if (threadIdx.x == 0) {
         if (load_a) ok0 = mbar_wait(mb_a, (uint32_t)((a_loads - 1) & 1));
@@ -458,7 +456,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_m2l_tcp(int R, int nunits, co
           const uint32_t idesc = instr_desc(kTcRows, npad);
           const uint32_t lbo_a = (kTcRows / 8) * 128, lbo_b = (kTcPairs / 8) * 128, sbo = 128;
           const uint32_t sa_hi = cvta_smem(a_hi), sa_lo = cvta_smem(a_lo);
-          const uint32_t sb_hi = cvta_smem(b_hi), sb_lo = cvta_smem(b_lo);
+          const uint32_t sb_hi = cvta_smem(b_base + b * 2 * kTcPairs * R), sb_lo = sb_hi + (uint32_t)(kTcPairs * R * 2);
           const uint32_t acc = tmem + (uint32_t)(b * kTcTmemCols);
           for (int st = 0; st < Rt / 16; ++st) {
             const uint32_t ka = 2 * st * lbo_a, kb = 2 * st * lbo_b;
@@ -493,19 +491,17 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_m2l_tcp(int R, int nunits, co
     // ---- epilogue --------------------------------------------------------------------
     const int ew = warp - 4;
     const int row = 32 * ew + lane;
+    TCUnit nxt = units[u0];
     for (int k = 0; k < nk; ++k) {
-      const int2 un = units[u0 + k];
-      const TCItem it = items[un.x];
-      const M2LGroup g = groups[it.group];
-      const int kt = un.y;
-      const int table = kt == 0 ? 0 : level_table[g.level];
-      const int Rt = table_rank[table];
-      const int cnt = it.count, npad = (cnt + 15) & ~15;
+      const TCUnit un = nxt;
+      if (k + 1 < nk) nxt = units[u0 + k + 1];
+      const int kt = un.kt, Rt = un.rank;
+      const int cnt = un.count, npad = (cnt + 15) & ~15;
       const int b = k & 1;
-      // the unit's targets and scale, loaded while its MMAs may still be running
-      const int2 *pr = pairs + g.start + it.start;
+      // the unit's targets, loaded while its MMAs may still be running
+      const int2 *pr = pairs + un.pstart;
       for (int p = lane; p < cnt; p += 32) s_etgt[ew][p] = pr[p].x;
-      const float scale = kt == 0 ? (float)(1.0 / center[pairs[g.start].x].w) : 1.0f;
+      const float scale = un.scale;
       __syncwarp();
       const bool ok = __all_sync(0xffffffffu, mbar_wait(mb_full[b], (uint32_t)((k >> 1) & 1)));
       if (!ok) {
@@ -551,6 +547,8 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_m2l_tcp(int R, int nunits, co
 
 namespace {
 constexpr int kTcSmem = (2 * kTcAElems + 2 * kTcBElems) * 2;
+// pipelined kernel: A tile (hi, lo) + two B stages (hi, lo), r weights each
+int tcp_smem_bytes(int R) { return 2 * (2 * kTcRows * R) + 2 * 2 * (2 * kTcPairs * R); }
 }
 
 Err build_m2l_tc(afmpb_t *h) {
@@ -602,18 +600,37 @@ Err build_m2l_tc(afmpb_t *h) {
   for (int r : h->h_table_rank) rmax = std::max(rmax, r);
   h->tc_pipelined = h->m2l_rank > 0 && rmax <= kTcKHalf && N3 <= kTcRows && h->d_Mc16;
   if (h->tc_pipelined) {
-    std::vector<int2> units;                           // (item, kernel), kernel-major
-    for (int kt = 0; kt < 2; ++kt)
-      for (int i = 0; i < (int)items.size(); ++i) {
-        const auto &g = h->m2l_groups[items[i].group];
-        if (kt == 1 && g.level < h->m2l_yuk_levels) continue;   // screened away
-        units.push_back(make_int2(i, kt));
-      }
+    // (item, kernel), kernel-major; Laplace items offset-major across levels (one table
+    // for every level), Yukawa items in (level, offset) order (one table per level)
+    std::vector<int> lap(items.size());
+    for (int i = 0; i < (int)items.size(); ++i) lap[i] = i;
+    std::stable_sort(lap.begin(), lap.end(), [&](int x, int y) {
+      return h->m2l_groups[items[x].group].offset < h->m2l_groups[items[y].group].offset;
+    });
+    std::vector<TCUnit> units;
+    auto add = [&](int i, int kt) {
+      const auto &it = items[i];
+      const auto &g = h->m2l_groups[it.group];
+      const int table = kt == 0 ? 0 : level_table[g.level];
+      TCUnit u{};
+      u.pstart = g.start + it.start;
+      u.count = it.count;
+      u.key = table * kNumOffsets + g.offset;
+      u.rank = h->h_table_rank[table];
+      u.kt = kt;
+      // Laplace tables are for the unit box: scale by 1 / w of the level (the box centre
+      // array holds the same power-of-two half width)
+      u.scale = kt == 0 ? (float)(1.0 / std::ldexp(h->shape.w0, -g.level)) : 1.0f;
+      units.push_back(u);
+    };
+    for (int i : lap) add(i, 0);
+    for (int i = 0; i < (int)items.size(); ++i)
+      if (h->m2l_groups[items[i].group].level >= h->m2l_yuk_levels) add(i, 1);   // else screened away
     h->tc_nunits = (int)units.size();
     AFMPB_TRY(A.alloc(&h->d_tc_units, std::max<size_t>(1, units.size()), "tc units"));
     if (!units.empty())
-      AFMPB_CUDA(cudaMemcpyAsync(h->d_tc_units, units.data(), sizeof(int2) * units.size(), cudaMemcpyHostToDevice, s));
-    AFMPB_TRY(raise_smem_limit((const void *)k_m2l_tcp, kTcSmem));
+      AFMPB_CUDA(cudaMemcpyAsync(h->d_tc_units, units.data(), sizeof(TCUnit) * units.size(), cudaMemcpyHostToDevice, s));
+    AFMPB_TRY(raise_smem_limit((const void *)k_m2l_tcp, tcp_smem_bytes(h->m2l_rank)));
   }
   AFMPB_CUDA(cudaStreamSynchronize(s));
   A.release(d_table_level);
@@ -630,12 +647,9 @@ Err enqueue_m2l_tc(afmpb_t *h, cudaStream_t s) {
     AFMPB_CUDA(cudaGetDevice(&dev));
     AFMPB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     const unsigned grid = (unsigned)std::min(h->tc_nunits, 2 * sms);   // two CTAs per SM
-    k_m2l_tcp<<<grid, kTcThreads, kTcSmem, s>>>(h->m2l_rank, h->tc_nunits, h->d_tc_units,
-                                                reinterpret_cast<const __nv_bfloat16 *>(h->d_Mc16), h->d_tc_items,
-                                                h->d_m2l_groups, h->d_m2l_pairs,
-                                                reinterpret_cast<const __nv_bfloat16 *>(h->d_tc_tiles),
-                                                h->d_tc_level_table, kNumOffsets, h->d_table_rank,
-                                                h->d_box_center, h->d_Mc, h->d_Lc, h->d_tc_flag);
+    k_m2l_tcp<<<grid, kTcThreads, tcp_smem_bytes(h->m2l_rank), s>>>(
+        h->m2l_rank, h->tc_nunits, h->d_tc_units, reinterpret_cast<const __nv_bfloat16 *>(h->d_Mc16), h->d_m2l_pairs,
+        reinterpret_cast<const __nv_bfloat16 *>(h->d_tc_tiles), h->d_Lc, h->d_tc_flag);
     return check_launch("k_m2l_tcp");
   }
   const int N3 = comp ? h->m2l_rank : h->ncoef;
