@@ -432,6 +432,7 @@ __global__ void __launch_bounds__(kL2PThreads, 12) k_l2p(const int32_t *__restri
 constexpr int kP2PChunk = 768;      // sources staged in shared memory at a time (8 CTAs/SM)
 constexpr int kP2PPairs = kP2PChunk / 2;
 constexpr int kP2PBoxes = 64;       // source boxes described in shared memory at a time
+constexpr int kP2PResident = 6;     // P2P blocks kept resident per SM
 
 // Far-rule sums of one source at one target, without the 1/(4 pi):
 //   PhiL += c/r + (g/eps_bar) (n.d)/r^3
@@ -501,7 +502,7 @@ __device__ __forceinline__ void p2p_pair2(const P2PTarget &t, const float4 &a, c
   dY = __ffma2_rn(e1, BmC, __ffma2_rn(e2, Tn, dY));
 }
 
-__global__ void __launch_bounds__(kP2PThreads, 8) k_p2p(const int32_t *__restrict__ order,
+__global__ void __launch_bounds__(kP2PThreads, 8) k_p2p(int nleaf, const int32_t *__restrict__ order,
                                                       const int32_t *__restrict__ leaves,
                                                       const int64_t *__restrict__ pptr,
                                                       const int32_t *__restrict__ pidx,
@@ -518,7 +519,11 @@ __global__ void __launch_bounds__(kP2PThreads, 8) k_p2p(const int32_t *__restric
   __shared__ int s_beg[kP2PBoxes], s_pre[kP2PBoxes + 1];
   __shared__ float s_off[kP2PBoxes][3];
   float4 *red = sa;
-  const int leaf = order[blockIdx.x];
+  const float2 inv_e = dup2(inv_ebar), kap = dup2(kappa);
+  // a fixed number of resident blocks per SM walk the cost-ordered leaves round robin
+  for (int li = blockIdx.x; li < nleaf; li += gridDim.x) {
+  if (li != (int)blockIdx.x) __syncthreads();           // the previous leaf's reduction read red
+  const int leaf = order[li];
   const int b = leaves[leaf];
   const dbl4 cb = center[b];
   const int tb = bbeg[b], te = bend[b];
@@ -527,7 +532,6 @@ __global__ void __launch_bounds__(kP2PThreads, 8) k_p2p(const int32_t *__restric
   const int ti = threadIdx.x % tile, si = threadIdx.x / tile;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t l0 = pptr[leaf], l1 = pptr[leaf + 1];
-  const float2 inv_e = dup2(inv_ebar), kap = dup2(kappa);
   for (int t0 = tb; t0 < te; t0 += tile) {
     const int t = t0 + ti;
     const bool act = si < slices && t < te;
@@ -617,6 +621,7 @@ __global__ void __launch_bounds__(kP2PThreads, 8) k_p2p(const int32_t *__restric
       const float s = (float)kInv4Pi;
       phi[t] = make_float4(s * a.x, s * a.y, s * a.z, s * a.w);
     }
+  }
   }
 }
 
@@ -785,7 +790,13 @@ Err enqueue_far(afmpb_t *h, cudaStream_t s, StageTimer *tm) {
 }
 
 Err enqueue_p2p(afmpb_t *h, cudaStream_t s) {
-  k_p2p<<<h->shape.nleaf, kP2PThreads, 0, s>>>(h->d_p2p_order, h->d_leaves, h->d_p2p_ptr, h->d_p2p_idx, h->d_box_begin,
+  // Six resident blocks per SM (of the eight that fit) leave registers and shared memory
+  // for the far-field chain's kernels, which run beside P2P at a higher stream priority.
+  int dev = 0, sms = 0;
+  AFMPB_CUDA(cudaGetDevice(&dev));
+  AFMPB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int grid = std::max(1, std::min(h->shape.nleaf, kP2PResident * sms));
+  k_p2p<<<grid, kP2PThreads, 0, s>>>(h->shape.nleaf, h->d_p2p_order, h->d_leaves, h->d_p2p_ptr, h->d_p2p_idx, h->d_box_begin,
                                                   h->d_box_end, h->d_box_center, h->d_pos, h->d_nrm, h->d_xs,
                                                   (float)(1.0 / h->ebar), (float)h->kappa,
                                                   (float)(kP2PSkip * h->opt.near_c), h->d_phi_near);

@@ -317,9 +317,9 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_m2l_tc(int N3, const TCItem *
 // (r <= 112): persistent CTAs (two per SM for r <= 80) walk a contiguous range of work
 // units (item, kernel), ordered so that consecutive units share their translation tile
 // (Laplace units offset-major across levels: one unit-box table serves every level).
-// Shared memory holds the A tile (r columns) and two B stages, sized by r.  Warps 0-3
-// produce: wait until the MMAs that last read the B stage (unit k - 2) and, when the A
-// tile changes, the previous unit's MMAs have completed; load the A tile when it changes
+// Shared memory holds the A tile (r columns) and one or two B stages, sized by r.  Warps
+// 0-3 produce: wait until the MMAs that last read the B stage (unit k - 2, or k - 1 with
+// one stage) and, when the A tile changes, the previous unit's MMAs have completed; load the A tile when it changes
 // (bulk copy), gather the B operand into its stage, and thread 0 issues the MMAs into one
 // of two TMEM accumulators.  Warps 4-7 consume: wait for a unit's
 // accumulator, read it with tcgen05.ld (warp w reads lanes 32 (w - 4) .. +31, one output
@@ -343,7 +343,8 @@ __device__ __forceinline__ bool producer_all(bool v) {
   return r != 0;
 }
 
-__global__ void __launch_bounds__(kTcThreads, 2) k_m2l_tcp(int R, int nunits, const TCUnit *__restrict__ units,
+__global__ void __launch_bounds__(kTcThreads, 2) k_m2l_tcp(int R, int nstages, int nunits,
+                                                           const TCUnit *__restrict__ units,
                                                            const __nv_bfloat16 *__restrict__ Mc16,
                                                            const int2 *__restrict__ pairs,
                                                            const __nv_bfloat16 *__restrict__ tiles,
@@ -400,9 +401,11 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_m2l_tcp(int R, int nunits, co
       const bool load_a = key != a_key;
       // operands free: B stage b was last read by unit k - 2's MMAs; the A tile, when it
       // is about to change, by unit k - 1's
+      const int sb = nstages == 2 ? b : 0;                 // B stage of this unit
       bool ok = true;
-      if (k >= 2) ok = mbar_wait(mb_full[b], (uint32_t)(((k - 2) >> 1) & 1));
-      if (ok && load_a && k >= 1) ok = mbar_wait(mb_full[(k - 1) & 1], (uint32_t)(((k - 1) >> 1) & 1));
+      if (nstages == 2 && k >= 2) ok = mbar_wait(mb_full[b], (uint32_t)(((k - 2) >> 1) & 1));
+      if (ok && (load_a || nstages == 1) && k >= 1)
+        ok = mbar_wait(mb_full[(k - 1) & 1], (uint32_t)(((k - 1) >> 1) & 1));
       if (!producer_all(ok)) {
         failed = true;
         break;
@@ -434,7 +437,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_m2l_tcp(int R, int nunits, co
       // padding pairs are zero-filled)
       const int kg = Rt / 8;                             // groups of 8 along K
       const int nunit = npad * kg;
-      const uint32_t sb_hi0 = cvta_smem(b_base + b * 2 * kTcPairs * R), sb_lo0 = sb_hi0 + (uint32_t)(kTcPairs * R * 2);
+      const uint32_t sb_hi0 = cvta_smem(b_base + sb * 2 * kTcPairs * R), sb_lo0 = sb_hi0 + (uint32_t)(kTcPairs * R * 2);
       for (int e = threadIdx.x; e < nunit; e += 128) {
         const int p = e / kg, k8 = e % kg;
         const bool v = p < cnt;
@@ -456,7 +459,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_m2l_tcp(int R, int nunits, co
           const uint32_t idesc = instr_desc(kTcRows, npad);
           const uint32_t lbo_a = (kTcRows / 8) * 128, lbo_b = (kTcPairs / 8) * 128, sbo = 128;
           const uint32_t sa_hi = cvta_smem(a_hi), sa_lo = cvta_smem(a_lo);
-          const uint32_t sb_hi = cvta_smem(b_base + b * 2 * kTcPairs * R), sb_lo = sb_hi + (uint32_t)(kTcPairs * R * 2);
+          const uint32_t sb_hi = cvta_smem(b_base + sb * 2 * kTcPairs * R), sb_lo = sb_hi + (uint32_t)(kTcPairs * R * 2);
           const uint32_t acc = tmem + (uint32_t)(b * kTcTmemCols);
           for (int st = 0; st < Rt / 16; ++st) {
             const uint32_t ka = 2 * st * lbo_a, kb = 2 * st * lbo_b;
@@ -547,8 +550,12 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_m2l_tcp(int R, int nunits, co
 
 namespace {
 constexpr int kTcSmem = (2 * kTcAElems + 2 * kTcBElems) * 2;
-// pipelined kernel: A tile (hi, lo) + two B stages (hi, lo), r weights each
-int tcp_smem_bytes(int R) { return 2 * (2 * kTcRows * R) + 2 * 2 * (2 * kTcPairs * R); }
+// pipelined kernel: A tile (hi, lo) + B stages (hi, lo), r weights each
+int tcp_smem_bytes(int R, int stages) { return 2 * (2 * kTcRows * R) + stages * 2 * (2 * kTcPairs * R); }
+// Two B stages when they fit beside six P2P blocks on an SM (the P2P kernel runs on six
+// resident blocks per SM beside the far-field chain), else one.
+constexpr int kTcCoresidentSmem = 62 * 1024;
+int tcp_stages(int R) { return tcp_smem_bytes(R, 2) <= kTcCoresidentSmem ? 2 : 1; }
 }
 
 Err build_m2l_tc(afmpb_t *h) {
@@ -630,7 +637,7 @@ Err build_m2l_tc(afmpb_t *h) {
     AFMPB_TRY(A.alloc(&h->d_tc_units, std::max<size_t>(1, units.size()), "tc units"));
     if (!units.empty())
       AFMPB_CUDA(cudaMemcpyAsync(h->d_tc_units, units.data(), sizeof(TCUnit) * units.size(), cudaMemcpyHostToDevice, s));
-    AFMPB_TRY(raise_smem_limit((const void *)k_m2l_tcp, tcp_smem_bytes(h->m2l_rank)));
+    AFMPB_TRY(raise_smem_limit((const void *)k_m2l_tcp, tcp_smem_bytes(h->m2l_rank, tcp_stages(h->m2l_rank))));
   }
   AFMPB_CUDA(cudaStreamSynchronize(s));
   A.release(d_table_level);
@@ -647,8 +654,8 @@ Err enqueue_m2l_tc(afmpb_t *h, cudaStream_t s) {
     AFMPB_CUDA(cudaGetDevice(&dev));
     AFMPB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     const unsigned grid = (unsigned)std::min(h->tc_nunits, 2 * sms);   // two CTAs per SM
-    k_m2l_tcp<<<grid, kTcThreads, tcp_smem_bytes(h->m2l_rank), s>>>(
-        h->m2l_rank, h->tc_nunits, h->d_tc_units, reinterpret_cast<const __nv_bfloat16 *>(h->d_Mc16), h->d_m2l_pairs,
+    k_m2l_tcp<<<grid, kTcThreads, tcp_smem_bytes(h->m2l_rank, tcp_stages(h->m2l_rank)), s>>>(
+        h->m2l_rank, tcp_stages(h->m2l_rank), h->tc_nunits, h->d_tc_units, reinterpret_cast<const __nv_bfloat16 *>(h->d_Mc16), h->d_m2l_pairs,
         reinterpret_cast<const __nv_bfloat16 *>(h->d_tc_tiles), h->d_Lc, h->d_tc_flag);
     return check_launch("k_m2l_tcp");
   }
