@@ -11,7 +11,6 @@
 
 #include <algorithm>
 #include <cmath>
-#include <map>
 
 #include "internal.cuh"
 
@@ -606,30 +605,40 @@ Err build_tree(afmpb_t *h) {
   T.n_x = (int64_t)xidx.size();
   T.n_p2p_pairs = pairs - h->n;     // the diagonal t == p is skipped
 
-  // M2L pairs grouped by (level, offset), each group's targets in box order
+  // M2L pairs grouped by (level, offset), each group's targets in box order: a counting
+  // sort on the key level * 343 + offset code (stable, so target order is kept)
   {
     std::vector<int4> anc;
     AFMPB_TRY(to_host(anc, banchor, nbox, s));
-    std::map<std::pair<int, int>, std::vector<int2>> groups;
+    const int nkey = (T.nlevel + 1) * 343;
+    const int64_t nv = vptr[nbox];
+    std::vector<int32_t> key(nv);
+    std::vector<int64_t> kcount(nkey + 1, 0);
     for (int b = 0; b < nbox; ++b)
       for (int64_t j = vptr[b]; j < vptr[b + 1]; ++j) {
-        int c = vidx[j];
-        int ox = anc[c].x - anc[b].x, oy = anc[c].y - anc[b].y, oz = anc[c].z - anc[b].z;
-        int code = (ox + 3) * 49 + (oy + 3) * 7 + (oz + 3);
-        groups[{anc[b].w, code}].push_back(make_int2(b, c));
+        const int c = vidx[j];
+        const int ox = anc[c].x - anc[b].x, oy = anc[c].y - anc[b].y, oz = anc[c].z - anc[b].z;
+        key[j] = anc[b].w * 343 + (ox + 3) * 49 + (oy + 3) * 7 + (oz + 3);
+        ++kcount[key[j] + 1];
       }
-    std::vector<int2> pairs_v;
-    h->m2l_groups.clear();
-    for (auto &kv : groups) {
-      M2LGroup g;
-      g.level = kv.first.first;
-      g.offset = kv.first.second;       // raw code in [0, 343); mapped to a table slot in fmm.cu
-      g.start = (int)pairs_v.size();
-      g.count = (int)kv.second.size();
-      h->m2l_groups.push_back(g);
-      pairs_v.insert(pairs_v.end(), kv.second.begin(), kv.second.end());
+    for (int k = 0; k < nkey; ++k) kcount[k + 1] += kcount[k];
+    std::vector<int2> pairs_v(nv);
+    {
+      std::vector<int64_t> fill(kcount.begin(), kcount.end() - 1);
+      for (int b = 0; b < nbox; ++b)
+        for (int64_t j = vptr[b]; j < vptr[b + 1]; ++j) pairs_v[fill[key[j]]++] = make_int2(b, vidx[j]);
     }
-    h->n_m2l_pairs = (int64_t)pairs_v.size();
+    h->m2l_groups.clear();
+    for (int k = 0; k < nkey; ++k) {
+      if (kcount[k + 1] == kcount[k]) continue;
+      M2LGroup g;
+      g.level = k / 343;
+      g.offset = k % 343;               // raw code in [0, 343); mapped to a table slot in fmm.cu
+      g.start = (int)kcount[k];
+      g.count = (int)(kcount[k + 1] - kcount[k]);
+      h->m2l_groups.push_back(g);
+    }
+    h->n_m2l_pairs = nv;
     AFMPB_TRY(to_device(h, &h->d_m2l_pairs, pairs_v, "m2l_pairs"));
   }
 
