@@ -52,51 +52,71 @@ __device__ __forceinline__ Real dot(const V3<Real> &a, const V3<Real> &b) {
   return a.x * b.x + a.y * b.y + a.z * b.z;
 }
 
-// phi1(x) = 1 - e^{-x}(1 + x) and phi2(x) = 1 - e^{-x}(1 + x + x^2/3): the screened
-// fractions of the Laplace 1/r^3 and 3/r^5 terms.  Below x = 0.5 they are summed from
-// their power series (coefficients of x^j: (-1)^j (j-1) / j! and
-// (-1)^(j+1) (j-1)(j-3) / (3 j!)), which avoids the cancellation of the direct forms.
+// phi0(x) = 1 - e^{-x}, phi1(x) = 1 - e^{-x}(1 + x) and phi2(x) = 1 - e^{-x}(1 + x + x^2/3):
+// the screened fractions of the Laplace 1/r, 1/r^3 and 3/r^5 terms.  Below x = 0.5 they are
+// summed from their Taylor series through x^10 (coefficients of x^j: (-1)^(j+1) / j!,
+// (-1)^j (j-1) / j! and (-1)^(j+1) (j-1)(j-3) / (3 j!)) by Horner's rule with the
+// coefficients as compile-time constants, which avoids the cancellation of the direct
+// forms and every division; e = e^{-x} serves the direct forms above 0.5.
+template <class Real, int N>
+__device__ __forceinline__ Real horner(const Real (&c)[N], Real x) {
+  Real s = c[N - 1];
+#pragma unroll
+  for (int j = N - 2; j >= 0; --j) s = s * x + c[j];
+  return s;
+}
+
 template <class Real>
-__device__ __forceinline__ void screened_fractions(Real x, Real &p1, Real &p2) {
+__device__ __forceinline__ void screened_fractions(Real x, Real e, Real &p0, Real &p1, Real &p2) {
   if (x < Real(0.5)) {
-    Real t = x;            // x^j / j!
-    Real s1 = 0, s2 = 0;
-    for (int j = 2; j < 16; ++j) {
-      t *= x / (Real)j;
-      const Real sg = (j & 1) ? Real(-1) : Real(1);
-      s1 += sg * (Real)(j - 1) * t;
-      s2 -= sg * (Real)((j - 1) * (j - 3)) * t / Real(3);
-    }
-    p1 = s1;
-    p2 = s2;
+    constexpr Real c0[] = {Real(1),           Real(-1.0 / 2),      Real(1.0 / 6),       Real(-1.0 / 24),
+                           Real(1.0 / 120),   Real(-1.0 / 720),    Real(1.0 / 5040),    Real(-1.0 / 40320),
+                           Real(1.0 / 362880), Real(-1.0 / 3628800)};                  // x^1 .. x^10
+    constexpr Real c1[] = {Real(1.0 / 2),     Real(-1.0 / 3),      Real(1.0 / 8),       Real(-1.0 / 30),
+                           Real(1.0 / 144),   Real(-1.0 / 840),    Real(1.0 / 5760),    Real(-1.0 / 45360),
+                           Real(1.0 / 403200)};                                          // x^2 .. x^10
+    constexpr Real c2[] = {Real(1.0 / 6),     Real(0),             Real(-1.0 / 24),     Real(1.0 / 45),
+                           Real(-1.0 / 144),  Real(1.0 / 630),     Real(-1.0 / 3456),   Real(1.0 / 22680),
+                           Real(-1.0 / 172800)};                                         // x^2 .. x^10
+    const Real x2 = x * x;
+    p0 = x * horner(c0, x);
+    p1 = x2 * horner(c1, x);
+    p2 = x2 * horner(c2, x);
   } else {
-    const Real e = exp(-x);
+    p0 = Real(1) - e;
     p1 = Real(1) - e * (Real(1) + x);
-    p2 = Real(1) - e * (Real(1) + x + x * x / Real(3));
+    p2 = Real(1) - e * (Real(1) + x + x * x * Real(1.0 / 3));
   }
 }
 
+__device__ __forceinline__ float rsqrt_r(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsqrt_r(double x) { return rsqrt(x); }
+__device__ __forceinline__ float exp_r(float x) { return __expf(x); }
+__device__ __forceinline__ double exp_r(double x) { return exp(x); }
+
 // The four Eq. 6 integrands at one point: d = x_target - y_source, n0 target normal,
 // ns source normal.  The G - u differences of A and D are formed without cancellation
-// (A through expm1, D through the screened fractions above).
+// (through the screened fractions above).  No division: 1/r from rsqrt, 1/eps_bar given.
 template <class Real>
-__device__ __forceinline__ void abcd_point(Real kappa, Real ebar, const V3<Real> &d, const V3<Real> &n0,
+__device__ __forceinline__ void abcd_point(Real kappa, Real inv_ebar, const V3<Real> &d, const V3<Real> &n0,
                                            const V3<Real> &ns, Real o[4]) {
   const Real r2 = dot(d, d);
-  const Real r = sqrt(r2);
+  const Real ri = rsqrt_r(r2);
+  const Real r = r2 * ri;
+  const Real ri2 = ri * ri;
   const Real ndn = dot(ns, d), n0d = dot(n0, d), nn0 = dot(ns, n0);
-  const Real G = Real(kInv4Pi) / r;
-  const Real G3 = G / r2;
-  const Real G5 = Real(3) * G3 / r2;
+  const Real G = Real(kInv4Pi) * ri;
+  const Real G3 = G * ri2;
+  const Real G5 = Real(3) * G3 * ri2;
   const Real kr = kappa * r;
-  const Real e = exp(-kr);
+  const Real e = exp_r(-kr);
   const Real g1 = (e * (Real(1) + kr)) * G3;
-  Real p1, p2;
-  screened_fractions(kr, p1, p2);
-  o[0] = -expm1(-kr) * G;                       // G - u
-  o[1] = ndn * G3 / ebar - ndn * g1;
-  o[2] = -n0d * G3 + n0d * g1 / ebar;
-  o[3] = (nn0 * G3 * p1 - ndn * n0d * G5 * p2) / ebar;
+  Real p0, p1, p2;
+  screened_fractions(kr, e, p0, p1, p2);
+  o[0] = p0 * G;                                 // G - u
+  o[1] = ndn * (G3 * inv_ebar - g1);
+  o[2] = n0d * (g1 * inv_ebar - G3);
+  o[3] = (nn0 * G3 * p1 - ndn * n0d * G5 * p2) * inv_ebar;
 }
 
 // Corners of triangle t rotated so that node v comes first, relative to the point o
@@ -281,7 +301,7 @@ __global__ void __launch_bounds__(128) k_near_pairs(int64_t nnz, const int32_t *
                                                     const double *__restrict__ nrm, const int32_t *__restrict__ col,
                                                     P2PView pv, float4 *__restrict__ coef,
                                                     uint8_t *__restrict__ full) {
-  const float kappa = (float)kp.kappa, ebar = (float)kp.ebar;
+  const float kappa = (float)kp.kappa, inv_ebar = (float)(1.0 / kp.ebar);
   bool done = false, in_pair = false, in_piece = false, have = false, whole = false;
   int64_t e = 0, tj = 0, tend = 0, op = 0, ot = 0;
   int half = 0, d = 0;
@@ -319,7 +339,7 @@ __global__ void __launch_bounds__(128) k_near_pairs(int64_t nnz, const int32_t *
             const V3<float> dd{(float)(xp[0] - xt[0]), (float)(xp[1] - xt[1]), (float)(xp[2] - xt[2])};
             const V3<float> nt{(float)nrm[3 * ot], (float)nrm[3 * ot + 1], (float)nrm[3 * ot + 2]};
             float f[4];
-            abcd_point(kappa, ebar, dd, np, nt, f);
+            abcd_point(kappa, inv_ebar, dd, np, nt, f);
             const float at = (float)area[ot];
             for (int k = 0; k < 4; ++k) o[k] -= at * f[k];
           }
@@ -333,8 +353,9 @@ __global__ void __launch_bounds__(128) k_near_pairs(int64_t nnz, const int32_t *
         tri_rel(xyz, tri, T, ot, xyz + 3 * op, P);
         const V3<float> ma{0.5f * (P[0].x + P[1].x), 0.5f * (P[0].y + P[1].y), 0.5f * (P[0].z + P[1].z)};
         const V3<float> mb{0.5f * (P[0].x + P[2].x), 0.5f * (P[0].y + P[2].y), 0.5f * (P[0].z + P[2].z)};
-        const V3<float> cen{(P[0].x + P[1].x + P[2].x) / 3.0f, (P[0].y + P[1].y + P[2].y) / 3.0f,
-                            (P[0].z + P[1].z + P[2].z) / 3.0f};
+        const float third = 1.0f / 3.0f;
+        const V3<float> cen{(P[0].x + P[1].x + P[2].x) * third, (P[0].y + P[1].y + P[2].y) * third,
+                            (P[0].z + P[1].z + P[2].z) * third};
         const double *tn = tri_nrm + 3 * (int64_t)T;
         ns = V3<float>{(float)tn[0], (float)tn[1], (float)tn[2]};
         R0 = P[0];
@@ -359,9 +380,11 @@ __global__ void __launch_bounds__(128) k_near_pairs(int64_t nnz, const int32_t *
       }
       const V3<float> e01{b.x - a.x, b.y - a.y, b.z - a.z}, e12{c.x - b.x, c.y - b.y, c.z - b.z},
           e02{c.x - a.x, c.y - a.y, c.z - a.z};
-      const float diam = sqrtf(fmaxf(dot(e01, e01), fmaxf(dot(e12, e12), dot(e02, e02))));
-      const V3<float> g{(a.x + b.x + c.x) / 3.0f, (a.y + b.y + c.y) / 3.0f, (a.z + b.z + c.z) / 3.0f};
-      if (d < kQuadDepth && sqrtf(dot(g, g)) < 3.0f * diam) {
+      // split while |centroid| < 3 x the longest edge (compared squared)
+      const float diam2 = fmaxf(dot(e01, e01), fmaxf(dot(e12, e12), dot(e02, e02)));
+      const float third = 1.0f / 3.0f;
+      const V3<float> g{(a.x + b.x + c.x) * third, (a.y + b.y + c.y) * third, (a.z + b.z + c.z) * third};
+      if (d < kQuadDepth && dot(g, g) < 9.0f * diam2) {
         ++d;                                  // first child (its digit is 0)
         continue;
       }
@@ -396,7 +419,7 @@ __global__ void __launch_bounds__(128) k_near_pairs(int64_t nnz, const int32_t *
         const V3<float> dq{-(b0 * la.x + b1 * lb.x + b2 * lc.x), -(b0 * la.y + b1 * lb.y + b2 * lc.y),
                            -(b0 * la.z + b1 * lb.z + b2 * lc.z)};
         float o[4];
-        abcd_point(kappa, ebar, dq, np, ns, o);
+        abcd_point(kappa, inv_ebar, dq, np, ns, o);
         const float w = larea * c_rad_wf[q];
         for (int k = 0; k < 4; ++k) acc[k] += w * o[k];
       }
