@@ -17,6 +17,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <thread>
 
@@ -28,7 +29,6 @@ namespace afmpb {
 namespace {
 
 constexpr int kGramTile = 32;       // Gram matrix tile (32 x 32 per CTA)
-constexpr int kGramOffsets = 20;    // offsets summed per Gram CTA
 constexpr int kRowsPerCta = 8;      // rows of T = K_o Q (and of C) per CTA
 constexpr int kChunkBoxes = 32;     // boxes per compress / expand CTA (a multiple of 4)
 constexpr int kMaxN3 = kMaxOrder * kMaxOrder * kMaxOrder;
@@ -51,10 +51,10 @@ __device__ __forceinline__ double m2l_entry(const NodesD &nd, int N, int3 o, int
   return v;
 }
 
-__global__ void k_table_f64(int N, const int3 *__restrict__ offs, NodesD nd, double kw, double invw,
+__global__ void k_table_f64(int N, int noffs, const int3 *__restrict__ offs, NodesD nd, double kw, double invw,
                             double *__restrict__ K) {
   const int N3 = N * N * N;
-  const int64_t tot = (int64_t)kNumOffsets * N3 * N3;
+  const int64_t tot = (int64_t)noffs * N3 * N3;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
     const int o = (int)(e / ((int64_t)N3 * N3));
     const int rem = (int)(e % ((int64_t)N3 * N3));
@@ -63,37 +63,55 @@ __global__ void k_table_f64(int N, const int3 *__restrict__ offs, NodesD nd, dou
 }
 
 // gram[i][j] += sum over a range of offsets o and all k of K_o(i, k) K_o(j, k)
-__global__ void __launch_bounds__(256) k_gram(int N3, const double *__restrict__ K, double *__restrict__ gram) {
+// H_r = K_r K_r^T for one offset per orbit of the cube's symmetry group (blockIdx.z = r).
+__global__ void __launch_bounds__(256) k_gram_rep(int N3, const double *__restrict__ K, double *__restrict__ H) {
   __shared__ double Ki[kGramTile][kGramTile + 1], Kj[kGramTile][kGramTile + 1];
   const int i0 = blockIdx.x * kGramTile, j0 = blockIdx.y * kGramTile;
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
   double acc[2][2] = {{0, 0}, {0, 0}};
-  const int o0 = blockIdx.z * kGramOffsets, o1 = min(kNumOffsets, o0 + kGramOffsets);
-  for (int o = o0; o < o1; ++o) {
-    const double *Ko = K + (size_t)o * N3 * N3;
-    for (int k0 = 0; k0 < N3; k0 += kGramTile) {
-      __syncthreads();
-      for (int e = threadIdx.x; e < kGramTile * kGramTile; e += blockDim.x) {
-        const int r = e / kGramTile, c = e % kGramTile, k = k0 + c;
-        Ki[r][c] = (i0 + r < N3 && k < N3) ? Ko[(size_t)(i0 + r) * N3 + k] : 0.0;
-        Kj[r][c] = (j0 + r < N3 && k < N3) ? Ko[(size_t)(j0 + r) * N3 + k] : 0.0;
-      }
-      __syncthreads();
+  const double *Ko = K + (size_t)blockIdx.z * N3 * N3;
+  for (int k0 = 0; k0 < N3; k0 += kGramTile) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < kGramTile * kGramTile; e += blockDim.x) {
+      const int r = e / kGramTile, c = e % kGramTile, k = k0 + c;
+      Ki[r][c] = (i0 + r < N3 && k < N3) ? Ko[(size_t)(i0 + r) * N3 + k] : 0.0;
+      Kj[r][c] = (j0 + r < N3 && k < N3) ? Ko[(size_t)(j0 + r) * N3 + k] : 0.0;
+    }
+    __syncthreads();
 #pragma unroll 8
-      for (int c = 0; c < kGramTile; ++c) {
-        const double a0 = Ki[ty][c], a1 = Ki[ty + 16][c], b0 = Kj[tx][c], b1 = Kj[tx + 16][c];
-        acc[0][0] = fma(a0, b0, acc[0][0]);
-        acc[0][1] = fma(a0, b1, acc[0][1]);
-        acc[1][0] = fma(a1, b0, acc[1][0]);
-        acc[1][1] = fma(a1, b1, acc[1][1]);
-      }
+    for (int c = 0; c < kGramTile; ++c) {
+      const double a0 = Ki[ty][c], a1 = Ki[ty + 16][c], b0 = Kj[tx][c], b1 = Kj[tx + 16][c];
+      acc[0][0] = fma(a0, b0, acc[0][0]);
+      acc[0][1] = fma(a0, b1, acc[0][1]);
+      acc[1][0] = fma(a1, b0, acc[1][0]);
+      acc[1][1] = fma(a1, b1, acc[1][1]);
     }
   }
+  double *Hr = H + (size_t)blockIdx.z * N3 * N3;
   for (int a = 0; a < 2; ++a)
     for (int b = 0; b < 2; ++b) {
       const int i = i0 + ty + 16 * a, j = j0 + tx + 16 * b;
-      if (i < N3 && j < N3) atomicAdd(&gram[(size_t)i * N3 + j], acc[a][b]);
+      if (i < N3 && j < N3) Hr[(size_t)i * N3 + j] = acc[a][b];
     }
+}
+
+// Gram = sum over all offsets of K_o K_o^T, from the orbit representatives: an offset g.o
+// of the orbit of r has K_{g.o} = P_g K_r P_g^T (the kernel depends on |x - y| only and the
+// Chebyshev grid is symmetric), so the orbit contributes (|orbit| / 48) sum_g P_g H_r P_g^T,
+// entry (i, j) of which is H_r(perm_g(i), perm_g(j)) summed over the 48 elements g.
+__global__ void k_gram_sym(int N3, int nrep, const double *__restrict__ H, const double *__restrict__ wrep,
+                           const int32_t *__restrict__ perm, double *__restrict__ gram) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= (int64_t)N3 * N3) return;
+  const int i = (int)(e / N3), j = (int)(e % N3);
+  double sum = 0.0;
+  for (int r = 0; r < nrep; ++r) {
+    const double *Hr = H + (size_t)r * N3 * N3;
+    double t = 0.0;
+    for (int g = 0; g < 48; ++g) t += Hr[(size_t)perm[g * N3 + i] * N3 + perm[g * N3 + j]];
+    sum += wrep[r] * t;
+  }
+  gram[e] = sum;
 }
 
 // T[o][i][b] = sum_k K_o(i, k) Q(k, b)        (Q: [N3][R], FP64)
@@ -424,25 +442,83 @@ Err build_m2l_svd(afmpb_t *h, bool *compressed) {
     for (int oy = -3; oy <= 3; ++oy)
       for (int oz = -3; oz <= 3; ++oz)
         if (std::abs(ox) > 1 || std::abs(oy) > 1 || std::abs(oz) > 1) offs.push_back(make_int3(ox, oy, oz));
-  int3 *d_offs = nullptr;
-  double *d_K = nullptr, *d_gram = nullptr;
+  // The cube's 48 symmetries g (axis permutation sg, signs sn): offsets fall into 16
+  // orbits; for each g, perm_g maps Chebyshev point i to the point at g applied to it.
+  std::vector<std::array<int, 6>> group;
+  {
+    const int perms3[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+    for (auto &pm : perms3)
+      for (int sg = 0; sg < 8; ++sg)
+        group.push_back({pm[0], pm[1], pm[2], (sg & 1) ? -1 : 1, (sg & 2) ? -1 : 1, (sg & 4) ? -1 : 1});
+  }
+  auto act = [&](const std::array<int, 6> &g, const int v[3], int out[3]) {
+    for (int d = 0; d < 3; ++d) out[d] = g[3 + d] * v[g[d]];
+  };
+  std::vector<int32_t> perm((size_t)48 * N3);
+  for (int gi = 0; gi < 48; ++gi)
+    for (int i = 0; i < N3; ++i) {
+      const int idx[3] = {i / (n * n), (i / n) % n, i % n};
+      int out[3];
+      for (int d = 0; d < 3; ++d) {
+        const int src = idx[group[gi][d]];
+        out[d] = group[gi][3 + d] > 0 ? src : n - 1 - src;   // node n-1-m is -node m
+      }
+      perm[(size_t)gi * N3 + i] = (out[0] * n + out[1]) * n + out[2];
+    }
+  std::vector<int3> reps;
+  std::vector<double> wrep;
+  {
+    std::vector<char> seen(343, 0);
+    for (const int3 &o : offs) {
+      const int code = (o.x + 3) * 49 + (o.y + 3) * 7 + (o.z + 3);
+      if (seen[code]) continue;
+      int orbit = 0;
+      const int v[3] = {o.x, o.y, o.z};
+      for (auto &g : group) {
+        int w[3];
+        act(g, v, w);
+        const int c = (w[0] + 3) * 49 + (w[1] + 3) * 7 + (w[2] + 3);
+        if (!seen[c]) {
+          seen[c] = 1;
+          ++orbit;
+        }
+      }
+      reps.push_back(o);
+      wrep.push_back((double)orbit / 48.0);
+    }
+  }
+  const int nrep = (int)reps.size();
+  int3 *d_offs = nullptr, *d_reps = nullptr;
+  double *d_K = nullptr, *d_gram = nullptr, *d_H = nullptr, *d_wrep = nullptr;
+  int32_t *d_perm = nullptr;
   AFMPB_TRY(A.alloc(&d_offs, offs.size(), "svd offsets"));
+  AFMPB_TRY(A.alloc(&d_reps, reps.size(), "svd orbit offsets"));
+  AFMPB_TRY(A.alloc(&d_wrep, wrep.size(), "svd orbit weights"));
+  AFMPB_TRY(A.alloc(&d_perm, perm.size(), "svd point permutations"));
+  AFMPB_TRY(A.alloc(&d_H, (size_t)nrep * N3 * N3, "svd orbit grams"));
   AFMPB_TRY(A.alloc(&d_K, (size_t)kNumOffsets * N3 * N3, "svd K64"));
   AFMPB_TRY(A.alloc(&d_gram, (size_t)N3 * N3, "svd gram"));
+  AFMPB_CUDA(cudaMemcpyAsync(d_reps, reps.data(), sizeof(int3) * reps.size(), cudaMemcpyHostToDevice, s));
+  AFMPB_CUDA(cudaMemcpyAsync(d_wrep, wrep.data(), sizeof(double) * wrep.size(), cudaMemcpyHostToDevice, s));
+  AFMPB_CUDA(cudaMemcpyAsync(d_perm, perm.data(), sizeof(int32_t) * perm.size(), cudaMemcpyHostToDevice, s));
   AFMPB_CUDA(cudaMemcpyAsync(d_offs, offs.data(), sizeof(int3) * offs.size(), cudaMemcpyHostToDevice, s));
   // Gram matrices and their eigen-decompositions
   std::vector<std::vector<double>> gram(ntab, std::vector<double>((size_t)N3 * N3));
-  const dim3 ggrid((N3 + kGramTile - 1) / kGramTile, (N3 + kGramTile - 1) / kGramTile,
-                   (kNumOffsets + kGramOffsets - 1) / kGramOffsets);
+  const dim3 ggrid((N3 + kGramTile - 1) / kGramTile, (N3 + kGramTile - 1) / kGramTile, nrep);
   for (int t = 0; t < ntab; ++t) {
-    k_table_f64<<<1024, 256, 0, s>>>(n, d_offs, nd, tab_kw[t], tab_invw[t], d_K);
-    AFMPB_TRY(check_launch("k_table_f64"));
-    AFMPB_CUDA(cudaMemsetAsync(d_gram, 0, sizeof(double) * N3 * N3, s));
-    k_gram<<<ggrid, 256, 0, s>>>(N3, d_K, d_gram);
-    AFMPB_TRY(check_launch("k_gram"));
+    k_table_f64<<<256, 256, 0, s>>>(n, nrep, d_reps, nd, tab_kw[t], tab_invw[t], d_K);
+    AFMPB_TRY(check_launch("k_table_f64 orbits"));
+    k_gram_rep<<<ggrid, 256, 0, s>>>(N3, d_K, d_H);
+    AFMPB_TRY(check_launch("k_gram_rep"));
+    k_gram_sym<<<div_up((int64_t)N3 * N3, 256), 256, 0, s>>>(N3, nrep, d_H, d_wrep, d_perm, d_gram);
+    AFMPB_TRY(check_launch("k_gram_sym"));
     AFMPB_CUDA(cudaMemcpyAsync(gram[t].data(), d_gram, sizeof(double) * N3 * N3, cudaMemcpyDeviceToHost, s));
   }
   AFMPB_CUDA(cudaStreamSynchronize(s));
+  A.release(d_H);
+  A.release(d_perm);
+  A.release(d_wrep);
+  A.release(d_reps);
   std::vector<std::vector<double>> lam(ntab, std::vector<double>(N3)), zt(ntab, std::vector<double>((size_t)N3 * N3));
   std::vector<int> rc(ntab, 0);
   {
@@ -503,7 +579,7 @@ Err build_m2l_svd(afmpb_t *h, bool *compressed) {
         qtf[((size_t)t * R + a) * N3 + i] = (float)v;
       }
     AFMPB_CUDA(cudaMemcpyAsync(d_Q64, q64.data(), sizeof(double) * q64.size(), cudaMemcpyHostToDevice, s));
-    k_table_f64<<<1024, 256, 0, s>>>(n, d_offs, nd, tab_kw[t], tab_invw[t], d_K);
+    k_table_f64<<<1024, 256, 0, s>>>(n, kNumOffsets, d_offs, nd, tab_kw[t], tab_invw[t], d_K);
     AFMPB_TRY(check_launch("k_table_f64"));
     k_kq<<<dim3(kNumOffsets, (N3 + kRowsPerCta - 1) / kRowsPerCta), 128, 0, s>>>(N3, R, d_K, d_Q64, d_T);
     AFMPB_TRY(check_launch("k_kq"));
