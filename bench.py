@@ -132,6 +132,64 @@ def serving_leg(args):
 
 
 # ------------------------------------------------------------------------------------
+# globule: FMM order and precision sweep
+# ------------------------------------------------------------------------------------
+def globule_sweep_leg(args, stream):
+    """Synthetic globular protein (2,000-atom compact walk, 0.4 A Gaussian isosurface:
+    ~200k nodes, ~400k triangles), FMM order 4 / 6 / 8 in plain FP32 and mixed precision:
+    product time (CUDA events, L2 flushed) and the product's relative L2 error against
+    the FP64 oracle on 512 sampled rows (smooth x)."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import paper_1710_06316_gb300 as pb
+    import synthetic
+
+    mol = synthetic.globule(n_atoms=2000, index=2)
+    n = mol.n_nodes
+    xh = synthetic.smooth_unknowns(mol.xyz, 3)
+    x = torch.tensor(xh.astype(np.float32), device="cuda")
+    y = torch.empty_like(x)
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    rows = np.sort(np.random.default_rng(5).choice(n, 512, replace=False))
+    y1, y2 = oracle.Oracle.for_molecule(mol).matvec_rows(rows, xh)
+    ref = np.concatenate([y1, y2])
+    out = []
+    for order in (4, 6, 8):
+        for prec in (0, 1):
+            rec = {"order": order, "precision": ["fp32", "mixed"][prec]}
+            try:
+                h = pb.Handle.for_molecule(mol, order=order, precision=prec, stream=stream.cuda_stream)
+            except pb.AfmpbError as e:
+                rec["error"] = str(e)[:120]
+                out.append(rec)
+                continue
+            for _ in range(3):
+                h.matvec(x, y)
+            ev = []
+            for i in range(20):
+                flush.fill_(float(i))
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                h.matvec(x, y)
+                b.record(stream)
+                ev.append((a, b))
+            torch.cuda.synchronize()
+            ms = sum(a.elapsed_time(b) for a, b in ev) / len(ev)
+            yv = y.cpu().numpy().astype(np.float64)
+            got = np.concatenate([yv[rows], yv[n + rows]])
+            info = h.info()
+            rec.update({"ms_per_product": round(ms, 4), "mnode_per_s": round(n / ms / 1e3, 2),
+                        "rel_err_vs_oracle_sampled": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
+                        "m2l_rank": info["m2l_rank"], "leaf_cap": info["leaf_cap"]})
+            h.close()
+            out.append(rec)
+    return {"workload": "globule: 2000 atoms, %d nodes, %d triangles, eps %g/%g, kappa %g" % (
+        n, mol.n_tris, mol.eps_in, mol.eps_out, mol.kappa), "sweep": out}
+
+
+# ------------------------------------------------------------------------------------
 # capsid scale: one 10M-node solve
 # ------------------------------------------------------------------------------------
 def capsid_leg(args, stream):
@@ -522,6 +580,8 @@ def run_gpu(args):
         line["solve"]["energy_rel_err_vs_series"] = abs(energy / e_ref - 1)
     if rank == 0 and world == 1 and not args.no_serving:
         line["serving"] = serving_leg(args)
+    if rank == 0 and world == 1 and not args.no_sweep:
+        line["globule_sweep"] = globule_sweep_leg(args, stream)
     if rank == 0 and world == 1 and not args.no_capsid:
         line["capsid"] = capsid_leg(args, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -554,6 +614,7 @@ def main():
     ap.add_argument("--serve-budget-gb", type=float, default=96.0)
     ap.add_argument("--serve-restart", type=int, default=80)
     ap.add_argument("--no-capsid", action="store_true")
+    ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--capsid-steps", type=int, default=10)
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--solve-reps", type=int, default=5)
