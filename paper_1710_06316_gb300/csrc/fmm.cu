@@ -432,7 +432,8 @@ __global__ void __launch_bounds__(kL2PThreads, 12) k_l2p(const int32_t *__restri
 constexpr int kP2PChunk = 768;      // sources staged in shared memory at a time (8 CTAs/SM)
 constexpr int kP2PPairs = kP2PChunk / 2;
 constexpr int kP2PBoxes = 64;       // source boxes described in shared memory at a time
-constexpr int kP2PResident = 6;     // P2P blocks kept resident per SM
+constexpr int kP2PResident = 6;     // P2P blocks kept resident per SM (<= 80 registers per thread)
+constexpr int kP2PRegBlocks = 6;
 
 // Far-rule sums of one source at one target, without the 1/(4 pi):
 //   PhiL += c/r + (g/eps_bar) (n.d)/r^3
@@ -502,7 +503,7 @@ __device__ __forceinline__ void p2p_pair2(const P2PTarget &t, const float4 &a, c
   dY = __ffma2_rn(e1, BmC, __ffma2_rn(e2, Tn, dY));
 }
 
-__global__ void __launch_bounds__(kP2PThreads, 8) k_p2p(int nleaf, const int32_t *__restrict__ order,
+__global__ void __launch_bounds__(kP2PThreads, kP2PRegBlocks) k_p2p(int nleaf, const int32_t *__restrict__ order,
                                                       const int32_t *__restrict__ leaves,
                                                       const int64_t *__restrict__ pptr,
                                                       const int32_t *__restrict__ pidx,
@@ -514,7 +515,7 @@ __global__ void __launch_bounds__(kP2PThreads, 8) k_p2p(int nleaf, const int32_t
                                                       const float2 *__restrict__ xs, float inv_ebar,
                                                       float kappa, float skip_scale,
                                                       float4 *__restrict__ phi) {
-  static_assert(kP2PThreads <= kP2PPairs, "the reduction reuses the staging buffer");
+  static_assert(2 * kP2PThreads <= kP2PPairs, "the reduction reuses the staging buffer");
   __shared__ float4 sa[kP2PPairs], sb[kP2PPairs], sc[kP2PPairs], sd[kP2PPairs];
   __shared__ int s_beg[kP2PBoxes], s_pre[kP2PBoxes + 1];
   __shared__ float s_off[kP2PBoxes][3];
@@ -527,21 +528,32 @@ __global__ void __launch_bounds__(kP2PThreads, 8) k_p2p(int nleaf, const int32_t
   const int b = leaves[leaf];
   const dbl4 cb = center[b];
   const int tb = bbeg[b], te = bend[b];
-  const int tile = min(te - tb, kP2PThreads);
+  // each thread takes two targets, t and t + tile, against the same sources
+  const int tile = min((te - tb + 1) / 2, kP2PThreads);
   const int slices = kP2PThreads / tile;
   const int ti = threadIdx.x % tile, si = threadIdx.x / tile;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t l0 = pptr[leaf], l1 = pptr[leaf + 1];
-  for (int t0 = tb; t0 < te; t0 += tile) {
-    const int t = t0 + ti;
+  for (int t0 = tb; t0 < te; t0 += 2 * tile) {
+    const int t = t0 + ti, t2 = t + tile;
     const bool act = si < slices && t < te;
-    const float4 xp = act ? pos[t] : make_float4(0, 0, 0, 0);
-    const float4 np = act ? nrm[t] : make_float4(0, 0, 0, 0);
-    P2PTarget tg;
-    tg.x = dup2(xp.x); tg.y = dup2(xp.y); tg.z = dup2(xp.z);
-    tg.nx = dup2(np.x); tg.ny = dup2(np.y); tg.nz = dup2(np.z);
-    tg.rs = dup2(p2p_skip_radius(skip_scale, np.w));
+    const bool act2 = act && t2 < te;
+    P2PTarget tg, tg2;
+    {
+      const float4 xp = act ? pos[t] : make_float4(0, 0, 0, 0);
+      const float4 np = act ? nrm[t] : make_float4(0, 0, 0, 0);
+      tg.x = dup2(xp.x); tg.y = dup2(xp.y); tg.z = dup2(xp.z);
+      tg.nx = dup2(np.x); tg.ny = dup2(np.y); tg.nz = dup2(np.z);
+      tg.rs = dup2(p2p_skip_radius(skip_scale, np.w));
+      // a missing second target repeats the first (its sums are not stored)
+      const float4 xq = act2 ? pos[t2] : xp;
+      const float4 nq = act2 ? nrm[t2] : np;
+      tg2.x = dup2(xq.x); tg2.y = dup2(xq.y); tg2.z = dup2(xq.z);
+      tg2.nx = dup2(nq.x); tg2.ny = dup2(nq.y); tg2.nz = dup2(nq.z);
+      tg2.rs = dup2(p2p_skip_radius(skip_scale, nq.w));
+    }
     float2 sL = dup2(0.f), nD = dup2(0.f), sY = dup2(0.f), dY = dup2(0.f);
+    float2 sL2 = dup2(0.f), nD2 = dup2(0.f), sY2 = dup2(0.f), dY2 = dup2(0.f);
     for (int64_t g0 = l0; g0 < l1; g0 += kP2PBoxes) {
       const int nb = (int)min((int64_t)kP2PBoxes, l1 - g0);
       __syncthreads();
@@ -603,23 +615,34 @@ __global__ void __launch_bounds__(kP2PThreads, 8) k_p2p(int nleaf, const int32_t
         }
         __syncthreads();
         if (act) {
-#pragma unroll 2
-          for (int e = si; e < npairs; e += slices)
-            p2p_pair2(tg, sa[e], sb[e], sc[e], sd[e], inv_e, kap, sL, nD, sY, dY);
+          for (int e = si; e < npairs; e += slices) {
+            const float4 qa = sa[e], qb = sb[e], qc = sc[e], qd = sd[e];
+            p2p_pair2(tg, qa, qb, qc, qd, inv_e, kap, sL, nD, sY, dY);
+            p2p_pair2(tg2, qa, qb, qc, qd, inv_e, kap, sL2, nD2, sY2, dY2);
+          }
         }
       }
     }
     __syncthreads();
     red[threadIdx.x] = make_float4(sL.x + sL.y, -(nD.x + nD.y), sY.x + sY.y, dY.x + dY.y);
+    red[kP2PThreads + threadIdx.x] = make_float4(sL2.x + sL2.y, -(nD2.x + nD2.y), sY2.x + sY2.y, dY2.x + dY2.y);
     __syncthreads();
     if (si == 0 && t < te) {
+      const float s = (float)kInv4Pi;
       float4 a = red[ti];
       for (int k = 1; k < slices; ++k) {
         const float4 v = red[k * tile + ti];
         a.x += v.x; a.y += v.y; a.z += v.z; a.w += v.w;
       }
-      const float s = (float)kInv4Pi;
       phi[t] = make_float4(s * a.x, s * a.y, s * a.z, s * a.w);
+      if (t2 < te) {
+        float4 c = red[kP2PThreads + ti];
+        for (int k = 1; k < slices; ++k) {
+          const float4 v = red[kP2PThreads + k * tile + ti];
+          c.x += v.x; c.y += v.y; c.z += v.z; c.w += v.w;
+        }
+        phi[t2] = make_float4(s * c.x, s * c.y, s * c.z, s * c.w);
+      }
     }
   }
   }
@@ -790,8 +813,8 @@ Err enqueue_far(afmpb_t *h, cudaStream_t s, StageTimer *tm) {
 }
 
 Err enqueue_p2p(afmpb_t *h, cudaStream_t s) {
-  // Six resident blocks per SM (of the eight that fit) leave registers and shared memory
-  // for the far-field chain's kernels, which run beside P2P at a higher stream priority.
+  // Six resident blocks per SM walk the leaves while the far-field chain's kernels run
+  // beside them at a higher stream priority (measured best among four to six).
   int dev = 0, sms = 0;
   AFMPB_CUDA(cudaGetDevice(&dev));
   AFMPB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
