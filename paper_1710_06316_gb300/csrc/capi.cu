@@ -56,6 +56,15 @@ void destroy_handle(afmpb_t *h) {
 // arguments afmpb_matvec_parts updates in place for new buffers), so that a product is a
 // single graph launch: a plain kernel launch right before the far-field graph cost ~0.3 ms
 // of start-up on a 163,842-node product.
+// P2P runs beside the far-field chain (fork onto the low-priority side stream) for meshes
+// up to this size; above it the two run one after the other.  Measured products, mixed
+// precision, overlapped vs serial: 164k nodes 0.65 vs 0.73 ms, 200k 1.11 vs 1.46 ms, 2.1M
+// 13.9 vs 14.3 ms, 10.5M 69.3 vs 62.0 ms (there the concurrent form contends for L2 with
+// working sets far above it).
+constexpr int64_t kOverlapMaxNodes = 4000000;
+
+bool overlap_p2p(const afmpb_t *h) { return h->n <= kOverlapMaxNodes; }
+
 Err capture_product(afmpb_t *h, int parts, bool io = false, const float *x = nullptr, float *y = nullptr) {
   // The far-field chain (a long sequence of short, latency-bound launches) is captured
   // from a high-priority stream and P2P from a low-priority one: the kernel nodes keep the
@@ -69,12 +78,17 @@ Err capture_product(afmpb_t *h, int parts, bool io = false, const float *x = nul
   Err e;
   if (io) e = enqueue_gather(h, cap, x);
   if (e.ok() && (parts & AFMPB_PART_FAR)) {
-    cudaEventRecord(h->ev_fork, cap);
-    cudaStreamWaitEvent(h->side, h->ev_fork, 0);
-    e = enqueue_p2p(h, h->side);
-    cudaEventRecord(h->ev_join, h->side);
-    if (e.ok()) e = enqueue_far(h, cap);
-    cudaStreamWaitEvent(cap, h->ev_join, 0);
+    if (overlap_p2p(h)) {
+      cudaEventRecord(h->ev_fork, cap);
+      cudaStreamWaitEvent(h->side, h->ev_fork, 0);
+      e = enqueue_p2p(h, h->side);
+      cudaEventRecord(h->ev_join, h->side);
+      if (e.ok()) e = enqueue_far(h, cap);
+      cudaStreamWaitEvent(cap, h->ev_join, 0);
+    } else {
+      e = enqueue_p2p(h, cap);
+      if (e.ok()) e = enqueue_far(h, cap);
+    }
   }
   if (e.ok()) e = enqueue_combine(h, cap, parts);
   if (e.ok() && io) e = enqueue_scatter(h, cap, y);
@@ -250,13 +264,16 @@ Err product_from64(afmpb_t *h, cudaStream_t s, const double *v) {
     struct StreamGuard { cudaStream_t s; ~StreamGuard() { cudaStreamDestroy(s); } } sg{cap};
     AFMPB_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
     Err e = enqueue_to_xs(h, cap, v);
-    if (e.ok()) {
+    if (e.ok() && overlap_p2p(h)) {
       cudaEventRecord(h->ev_fork, cap);
       cudaStreamWaitEvent(h->side, h->ev_fork, 0);
       e = enqueue_p2p(h, h->side);
       cudaEventRecord(h->ev_join, h->side);
       if (e.ok()) e = enqueue_far(h, cap);
       cudaStreamWaitEvent(cap, h->ev_join, 0);
+    } else if (e.ok()) {
+      e = enqueue_p2p(h, cap);
+      if (e.ok()) e = enqueue_far(h, cap);
     }
     if (e.ok()) e = enqueue_combine(h, cap, AFMPB_PART_ALL);
     cudaGraph_t g = nullptr;
