@@ -62,7 +62,27 @@ __global__ void k_table_f64(int N, int noffs, const int3 *__restrict__ offs, Nod
   }
 }
 
-// gram[i][j] += sum over a range of offsets o and all k of K_o(i, k) K_o(j, k)
+// The same table in FP32 (for C_o = Q^T K_o Q, which the products use in FP32 and BF16).
+__global__ void k_table_f32(int N, int noffs, const int3 *__restrict__ offs, NodesD nd, double kw, double invw,
+                            float *__restrict__ K) {
+  const int N3 = N * N * N;
+  const int64_t tot = (int64_t)noffs * N3 * N3;
+  const float fkw = (float)kw, finvw = (float)invw, c = (float)kInv4Pi;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int o = (int)(e / ((int64_t)N3 * N3));
+    const int rem = (int)(e % ((int64_t)N3 * N3));
+    const int i = rem / N3, k = rem % N3;
+    const int3 of = offs[o];
+    const float dx = (float)(nd.x[i / (N * N)] - 2.0 * of.x - nd.x[k / (N * N)]);
+    const float dy = (float)(nd.x[(i / N) % N] - 2.0 * of.y - nd.x[(k / N) % N]);
+    const float dz = (float)(nd.x[i % N] - 2.0 * of.z - nd.x[k % N]);
+    const float r = sqrtf(dx * dx + dy * dy + dz * dz);
+    float v = c / r;
+    if (fkw >= 0.0f) v = expf(-fkw * r) * v * finvw;
+    K[e] = v;
+  }
+}
+
 // H_r = K_r K_r^T for one offset per orbit of the cube's symmetry group (blockIdx.z = r).
 __global__ void __launch_bounds__(256) k_gram_rep(int N3, const double *__restrict__ K, double *__restrict__ H) {
   __shared__ double Ki[kGramTile][kGramTile + 1], Kj[kGramTile][kGramTile + 1];
@@ -114,47 +134,48 @@ __global__ void k_gram_sym(int N3, int nrep, const double *__restrict__ H, const
   gram[e] = sum;
 }
 
-// T[o][i][b] = sum_k K_o(i, k) Q(k, b)        (Q: [N3][R], FP64)
-__global__ void __launch_bounds__(128) k_kq(int N3, int R, const double *__restrict__ K, const double *__restrict__ Q,
-                                            double *__restrict__ T) {
-  __shared__ double Ks[kRowsPerCta][kMaxN3];
+// T[o][i][b] = sum_k K_o(i, k) Q(k, b)        (Q: [N3][R]; FP32: the operators C_o are used
+// in FP32 and BF16 by the products, while the basis Q itself comes from the FP64 Gram matrix)
+__global__ void __launch_bounds__(128) k_kq(int N3, int R, const float *__restrict__ K, const float *__restrict__ Q,
+                                            float *__restrict__ T) {
+  __shared__ float Ks[kRowsPerCta][kMaxN3];
   const int o = blockIdx.x, i0 = blockIdx.y * kRowsPerCta;
   const int rows = min(kRowsPerCta, N3 - i0);
   for (int e = threadIdx.x; e < kRowsPerCta * N3; e += blockDim.x) {
     const int r = e / N3, k = e % N3;
-    Ks[r][k] = r < rows ? K[((size_t)o * N3 + i0 + r) * N3 + k] : 0.0;
+    Ks[r][k] = r < rows ? K[((size_t)o * N3 + i0 + r) * N3 + k] : 0.0f;
   }
   __syncthreads();
   for (int b = threadIdx.x; b < R; b += blockDim.x) {
-    double acc[kRowsPerCta] = {};
+    float acc[kRowsPerCta] = {};
     for (int k = 0; k < N3; ++k) {
-      const double q = Q[(size_t)k * R + b];
+      const float q = Q[(size_t)k * R + b];
 #pragma unroll
-      for (int r = 0; r < kRowsPerCta; ++r) acc[r] = fma(Ks[r][k], q, acc[r]);
+      for (int r = 0; r < kRowsPerCta; ++r) acc[r] = fmaf(Ks[r][k], q, acc[r]);
     }
     for (int r = 0; r < rows; ++r) T[((size_t)o * N3 + i0 + r) * R + b] = acc[r];
   }
 }
 
 // C[o][a][b] = sum_i Q(i, a) T[o][i][b], stored FP32
-__global__ void __launch_bounds__(128) k_qtt(int N3, int R, const double *__restrict__ Q, const double *__restrict__ T,
+__global__ void __launch_bounds__(128) k_qtt(int N3, int R, const float *__restrict__ Q, const float *__restrict__ T,
                                              float *__restrict__ C) {
-  __shared__ double Qs[kRowsPerCta][kMaxN3];
+  __shared__ float Qs[kRowsPerCta][kMaxN3];
   const int o = blockIdx.x, a0 = blockIdx.y * kRowsPerCta;
   const int rows = min(kRowsPerCta, R - a0);
   for (int e = threadIdx.x; e < kRowsPerCta * N3; e += blockDim.x) {
     const int r = e / N3, i = e % N3;
-    Qs[r][i] = r < rows ? Q[(size_t)i * R + a0 + r] : 0.0;
+    Qs[r][i] = r < rows ? Q[(size_t)i * R + a0 + r] : 0.0f;
   }
   __syncthreads();
   for (int b = threadIdx.x; b < R; b += blockDim.x) {
-    double acc[kRowsPerCta] = {};
+    float acc[kRowsPerCta] = {};
     for (int i = 0; i < N3; ++i) {
-      const double t = T[((size_t)o * N3 + i) * R + b];
+      const float t = T[((size_t)o * N3 + i) * R + b];
 #pragma unroll
-      for (int r = 0; r < kRowsPerCta; ++r) acc[r] = fma(Qs[r][i], t, acc[r]);
+      for (int r = 0; r < kRowsPerCta; ++r) acc[r] = fmaf(Qs[r][i], t, acc[r]);
     }
-    for (int r = 0; r < rows; ++r) C[((size_t)o * R + a0 + r) * R + b] = (float)acc[r];
+    for (int r = 0; r < rows; ++r) C[((size_t)o * R + a0 + r) * R + b] = acc[r];
   }
 }
 
@@ -561,35 +582,32 @@ Err build_m2l_svd(afmpb_t *h, bool *compressed) {
   AFMPB_TRY(A.alloc(&h->d_level_table, level_table.size(), "svd level table"));
   AFMPB_CUDA(cudaMemcpyAsync(h->d_level_table, level_table.data(), sizeof(int) * level_table.size(),
                              cudaMemcpyHostToDevice, s));
-  // bases (FP32 for the product, FP64 for the compressed operators) and C_o = Q^T K_o Q
+  // bases Q (FP32, from the FP64 eigenvectors) and C_o = Q^T K_o Q (FP32)
   AFMPB_TRY(A.alloc(&h->d_Q, (size_t)ntab * N3 * R, "svd Q"));
   AFMPB_TRY(A.alloc(&h->d_QT, (size_t)ntab * R * N3, "svd QT"));
   AFMPB_TRY(A.alloc(&h->d_C, (size_t)ntab * kNumOffsets * R * R, "svd C"));
-  double *d_Q64 = nullptr, *d_T = nullptr;
-  AFMPB_TRY(A.alloc(&d_Q64, (size_t)N3 * R, "svd Q64"));
+  float *d_Kf = reinterpret_cast<float *>(d_K), *d_T = nullptr;   // the FP64 table buffer is free now
   AFMPB_TRY(A.alloc(&d_T, (size_t)kNumOffsets * N3 * R, "svd T"));
-  std::vector<double> q64((size_t)N3 * R);
   std::vector<float> qf((size_t)ntab * N3 * R), qtf((size_t)ntab * R * N3);
-  for (int t = 0; t < ntab; ++t) {
+  for (int t = 0; t < ntab; ++t)
     for (int i = 0; i < N3; ++i)
       for (int a = 0; a < R; ++a) {
         const double v = a < rank[t] ? zt[t][(size_t)a * N3 + i] : 0.0;   // zero beyond the rank
-        q64[(size_t)i * R + a] = v;
         qf[((size_t)t * N3 + i) * R + a] = (float)v;
         qtf[((size_t)t * R + a) * N3 + i] = (float)v;
       }
-    AFMPB_CUDA(cudaMemcpyAsync(d_Q64, q64.data(), sizeof(double) * q64.size(), cudaMemcpyHostToDevice, s));
-    k_table_f64<<<1024, 256, 0, s>>>(n, kNumOffsets, d_offs, nd, tab_kw[t], tab_invw[t], d_K);
-    AFMPB_TRY(check_launch("k_table_f64"));
-    k_kq<<<dim3(kNumOffsets, (N3 + kRowsPerCta - 1) / kRowsPerCta), 128, 0, s>>>(N3, R, d_K, d_Q64, d_T);
-    AFMPB_TRY(check_launch("k_kq"));
-    k_qtt<<<dim3(kNumOffsets, (R + kRowsPerCta - 1) / kRowsPerCta), 128, 0, s>>>(
-        N3, R, d_Q64, d_T, h->d_C + (size_t)t * kNumOffsets * R * R);
-    AFMPB_TRY(check_launch("k_qtt"));
-    AFMPB_CUDA(cudaStreamSynchronize(s));     // q64 is rewritten for the next table
-  }
   AFMPB_CUDA(cudaMemcpyAsync(h->d_Q, qf.data(), sizeof(float) * qf.size(), cudaMemcpyHostToDevice, s));
   AFMPB_CUDA(cudaMemcpyAsync(h->d_QT, qtf.data(), sizeof(float) * qtf.size(), cudaMemcpyHostToDevice, s));
+  for (int t = 0; t < ntab; ++t) {
+    const float *Qt = h->d_Q + (size_t)t * N3 * R;
+    k_table_f32<<<1024, 256, 0, s>>>(n, kNumOffsets, d_offs, nd, tab_kw[t], tab_invw[t], d_Kf);
+    AFMPB_TRY(check_launch("k_table_f32"));
+    k_kq<<<dim3(kNumOffsets, (N3 + kRowsPerCta - 1) / kRowsPerCta), 128, 0, s>>>(N3, R, d_Kf, Qt, d_T);
+    AFMPB_TRY(check_launch("k_kq"));
+    k_qtt<<<dim3(kNumOffsets, (R + kRowsPerCta - 1) / kRowsPerCta), 128, 0, s>>>(
+        N3, R, Qt, d_T, h->d_C + (size_t)t * kNumOffsets * R * R);
+    AFMPB_TRY(check_launch("k_qtt"));
+  }
   // compress / expand work: chunks of up to kChunkBoxes boxes of one level, on the levels
   // that have list-2 pairs
   std::vector<int4> chunks;
@@ -620,7 +638,6 @@ Err build_m2l_svd(afmpb_t *h, bool *compressed) {
   }
   AFMPB_CUDA(cudaStreamSynchronize(s));
   A.release(d_T);
-  A.release(d_Q64);
   A.release(d_gram);
   A.release(d_K);
   A.release(d_offs);

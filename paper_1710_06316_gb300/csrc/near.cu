@@ -211,14 +211,21 @@ __global__ void k_near_search(int64_t n, double cnear, const int32_t *__restrict
     dbl4 c = center[b];
     double dx = fmax(fabs(x0 - c.x) - c.w, 0.0), dy = fmax(fabs(x1 - c.y) - c.w, 0.0),
            dz = fmax(fabs(x2 - c.z) - c.w, 0.0);
-    double dbox = sqrt(dx * dx + dy * dy + dz * dz);
-    if (dbox >= cnear * (rp + brho[b])) continue;
+    // box pruning: compared squared (a box at the boundary is kept, never wrongly dropped:
+    // the squared test errs by a few ulps and a kept box is only searched)
+    const double bR = cnear * (rp + brho[b]);
+    if (dx * dx + dy * dy + dz * dz >= bR * bR * (1.0 + 1e-12)) continue;
     if (nchild[b] == 0) {
       for (int t = bbeg[b]; t < bend[b]; ++t) {
         int64_t ot = perm[t];
         double ex = x0 - xyz[3 * ot], ey = x1 - xyz[3 * ot + 1], ez = x2 - xyz[3 * ot + 2];
-        double dist = sqrt(ex * ex + ey * ey + ez * ez);
-        if (t == p || dist < cnear * (rp + rho[ot])) {
+        const double d2 = ex * ex + ey * ey + ez * ez;
+        const double R = cnear * (rp + rho[ot]);
+        // dist < R decided on squares, and with the square root (the defining test) only
+        // inside the few-ulp band where the two could disagree
+        bool in = d2 < R * R * (1.0 - 1e-12);
+        if (!in && d2 < R * R * (1.0 + 1e-12)) in = sqrt(d2) < R;
+        if (t == p || in) {
           if (fill) col[base + k] = t;
           ++k;
         }
