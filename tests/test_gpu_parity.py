@@ -353,14 +353,16 @@ def test_tiny_mesh_without_far_field():
     assert relerr(y, o.matvec(x)) < 1e-5
 
 
-def test_kirkwood_full_size_sampled_rows():
-    """Kirkwood sphere at full size (163,842 nodes), the bench's launch configuration;
-    4,096 rows sampled and computed one by one by the oracle."""
+@pytest.mark.parametrize("precision", [0, 1])
+def test_kirkwood_full_size_sampled_rows(precision):
+    """Kirkwood sphere at full size (163,842 nodes); precision 1 with its default leaf
+    capacity is the bench's launch configuration.  4,096 rows sampled and computed one by
+    one by the oracle."""
     import paper_1710_06316_gb300 as pb
     mol = synthetic.kirkwood_sphere()
     o = oracle.Oracle.for_molecule(mol)
     x = synthetic.smooth_unknowns(mol.xyz, 1)
-    with pb.Handle.for_molecule(mol, order=6) as h:
+    with pb.Handle.for_molecule(mol, order=6, precision=precision) as h:
         y = gpu_matvec(h, x)
     rng = np.random.default_rng(7)
     rows = np.sort(rng.choice(mol.n_nodes, 4096, replace=False))
