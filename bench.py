@@ -434,6 +434,24 @@ def run_reference(args):
 # ------------------------------------------------------------------------------------
 # GPU arm
 # ------------------------------------------------------------------------------------
+# ------------------------------------------------------------------------------------
+# replicas: each rank runs the whole workload on its own GPU (no exchange on the data path)
+# ------------------------------------------------------------------------------------
+def reduce_max(v, dist=None, device="cpu"):
+    """The largest of the ranks' values (the slowest replica sets the job's time)."""
+    if dist is None:
+        return float(v)
+    import torch
+    t = torch.tensor([float(v)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_rate(world, n_nodes, seconds):
+    """Whole-job Mnode/s: every rank processed n_nodes in at most `seconds`."""
+    return world * n_nodes / seconds / 1e6
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -464,11 +482,7 @@ def run_gpu(args):
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
     def max_over_ranks(v):
-        if not dist:
-            return v
-        t = torch.tensor([v], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return reduce_max(v, dist, dev)
 
     def timed_products(hh, steps, warmup, sample_clocks=False):
         """Mean product time (ms, CUDA events on the launching stream), L2 flushed."""
@@ -515,7 +529,7 @@ def run_gpu(args):
                                precision=args.precision, stream=stream.cuda_stream)
     info = h.info()
     ms_step, clk = timed_products(h, args.steps, args.warmup, sample_clocks=True)
-    value = world * n / (ms_step * 1e-3) / 1e6
+    value = replica_rate(world, n, ms_step * 1e-3)
 
     # end to end through the C ABI with pinned host buffers (H2D + product + D2H)
     xh = x.cpu().pin_memory()
@@ -527,11 +541,8 @@ def run_gpu(args):
     for _ in range(e2e_steps):
         h.matvec_host(xh, yh)
     e2e_s = (time.perf_counter() - t0) / e2e_steps
-    if dist:
-        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": world * n / e2e_s / 1e6, "unit": UNIT, "h2d_bytes_per_step": 2 * n * 4,
+    e2e_s = max_over_ranks(e2e_s)
+    e2e = {"value": replica_rate(world, n, e2e_s), "unit": UNIT, "h2d_bytes_per_step": 2 * n * 4,
            "d2h_bytes_per_step": 2 * n * 4, "ms_per_step": e2e_s * 1e3}
 
     prof = h.profile(reps=5, flush=flush, flush_bytes=FLUSH_BYTES)
