@@ -33,6 +33,7 @@
 namespace afmpb {
 
 __constant__ float c_gl_xf[16], c_gl_wf[16];     // Gauss-Legendre on [0, 1]
+__constant__ float c_gl_wi2f[16];                 // w_i / x_i^2 of the same rule
 __constant__ float c_rad_bf[21], c_rad_wf[7];    // Radon 7-point: barycentrics, weights
 
 constexpr int kNearStack = 8 * (kMaxLevel + 2);
@@ -134,7 +135,7 @@ __device__ __forceinline__ void tri_rel(const double *xyz, const int32_t *tri, i
 }
 
 template <class Real>
-__device__ void self_rule(Real kappa, Real ebar, const double *xyz, const int32_t *tri, const int64_t *inc_ptr,
+__device__ void self_rule(Real kappa, Real inv_ebar, const double *xyz, const int32_t *tri, const int64_t *inc_ptr,
                           const int32_t *inc_tri, int64_t op, const V3<Real> &np, Real o[4]) {
   const double *xp = xyz + 3 * op;
   Real As = 0, Ds = 0;
@@ -159,34 +160,27 @@ __device__ void self_rule(Real kappa, Real ebar, const double *xyz, const int32_
         const Real tt = c_gl_xf[it], wt = c_gl_wf[it];
         const V3<Real> w{e[0].x + tt * (e[1].x - e[0].x), e[0].y + tt * (e[1].y - e[0].y),
                          e[0].z + tt * (e[1].z - e[0].z)};
-        const Real l = sqrt(dot(w, w));
+        const Real l2 = dot(w, w);
+        const Real il = rsqrt_r(l2), l = l2 * il;
+        const Real ca = J * wt * Real(kInv4Pi) * il;             // A: (1 - e^{-x}) / l
+        const Real cd = ca * il * il;                             // D: phi1(x) / (s^2 l^3)
+        Real sa = 0, sd = 0;
         for (int is = 0; is < 16; ++is) {
-          const Real ss = c_gl_xf[is], ws = c_gl_wf[is];
-          const Real xk = kappa * ss * l;
-          const Real fa = -expm1(-xk) * Real(kInv4Pi) / l;
-          Real num;
-          if (xk < Real(0.5)) {
-            // 1 - e^{-x}(1 + x) = sum_{j>=2} (-1)^j (j - 1) x^j / j!
-            Real term = Real(0.5) * xk * xk, s = term;
-            for (int jj = 3; jj < 14; ++jj) {
-              term *= -xk * (Real)(jj - 1) / ((Real)jj * (Real)(jj - 2));
-              s += term;
-            }
-            num = s;
-          } else {
-            num = Real(1) - exp(-xk) * (Real(1) + xk);
-          }
-          const Real fd = num * Real(kInv4Pi) / (ss * ss * l * l * l);
-          As += J * wt * ws * fa;
-          Ds += J * wt * ws * fd;
+          const Real xk = kappa * c_gl_xf[is] * l;
+          Real p0, p1, p2;
+          screened_fractions(xk, exp_r(-xk), p0, p1, p2);
+          sa += c_gl_wf[is] * p0;
+          sd += c_gl_wi2f[is] * p1;
         }
+        As += ca * sa;
+        Ds += cd * sd;
       }
     }
   }
   o[0] = As;
   o[1] = 0;
   o[2] = 0;
-  o[3] = Ds / ebar;
+  o[3] = Ds * inv_ebar;
 }
 
 // Near-set walk.  fill == false: count per row; else write the columns.
@@ -255,7 +249,7 @@ __global__ void __launch_bounds__(128) k_near_self(int64_t n, KernelParams kp, c
   const int64_t op = perm[p];
   const V3<float> np{(float)nrm[3 * op], (float)nrm[3 * op + 1], (float)nrm[3 * op + 2]};
   float o[4] = {0, 0, 0, 0};
-  self_rule((float)kp.kappa, (float)kp.ebar, xyz, tri, inc_ptr, inc_tri, op, np, o);
+  self_rule((float)kp.kappa, (float)(1.0 / kp.ebar), xyz, tri, inc_ptr, inc_tri, op, np, o);
   coef[lo] = make_float4(o[0], o[1], o[2], o[3]);
   full[lo] = 1;
 }
@@ -485,6 +479,9 @@ Err init_quadrature_tables() {
     for (int i = 0; i < 16; ++i) { fx[i] = (float)gx[i]; fw[i] = (float)gw[i]; }
     AFMPB_CUDA(cudaMemcpyToSymbol(c_gl_xf, fx, sizeof(fx)));
     AFMPB_CUDA(cudaMemcpyToSymbol(c_gl_wf, fw, sizeof(fw)));
+    float fwi2[16];
+    for (int i = 0; i < 16; ++i) fwi2[i] = (float)(gw[i] / (gx[i] * gx[i]));
+    AFMPB_CUDA(cudaMemcpyToSymbol(c_gl_wi2f, fwi2, sizeof(fwi2)));
     // Radon's 7-point rule (exact for degree 5): centroid and two orbits of three points
     const double r15 = std::sqrt(15.0);
     const double a1 = (6.0 - r15) / 21.0, a2 = (6.0 + r15) / 21.0;
