@@ -317,11 +317,12 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_m2l_tc(int N3, const TCItem *
 // (r <= 112): persistent CTAs (two per SM for r <= 80) walk a contiguous range of work
 // units (item, kernel), ordered so that consecutive units share their translation tile
 // (Laplace units offset-major across levels: one unit-box table serves every level).
-// Shared memory holds the A tile (r columns) and one or two B stages, sized by r.  Warps
-// 0-3 produce: wait until the MMAs that last read the B stage (unit k - 2, or k - 1 with
-// one stage) and, when the A tile changes, the previous unit's MMAs have completed; load the A tile when it changes
-// (bulk copy), gather the B operand into its stage, and thread 0 issues the MMAs into one
-// of two TMEM accumulators.  Warps 4-7 consume: wait for a unit's
+// Shared memory holds the A tile (r columns) and two B stages, sized by r.  Warps 0-3
+// produce: the B operand of unit k + 1 is gathered into the other stage (once unit k - 1's
+// MMAs, which read that stage, have completed) before the producers wait for unit k's own
+// gather, and the descriptor and source boxes of unit k + 2 are loaded meanwhile; the A tile
+// is reloaded (bulk copy) when it changes; thread 0 issues the MMAs into one of two TMEM
+// accumulators.  Warps 4-7 consume: wait for a unit's
 // accumulator, read it with tcgen05.ld (warp w reads lanes 32 (w - 4) .. +31, one output
 // row per lane) and add each pair's column into the target's compressed local vector with
 // coalesced atomics, then release the accumulator.  So the gather of unit k + 1, the MMAs
@@ -343,7 +344,7 @@ __device__ __forceinline__ bool producer_all(bool v) {
   return r != 0;
 }
 
-__global__ void __launch_bounds__(kTcThreads, 2) k_m2l_tcp(int R, int nstages, int nunits,
+__global__ void __launch_bounds__(kTcThreads, 2) k_m2l_tcp(int R, int nunits,
                                                            const TCUnit *__restrict__ units,
                                                            const __nv_bfloat16 *__restrict__ Mc16,
                                                            const int2 *__restrict__ pairs,
@@ -357,7 +358,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_m2l_tcp(int R, int nstages, i
   __nv_bfloat16 *const b_base = a_lo + kTcRows * R;    // stage b: hi at b_base + b * 2 kTcPairs R, lo after it
   __shared__ __align__(8) uint64_t bar_a, bar_full[2], bar_empty[2];
   __shared__ uint32_t tmem_base;
-  __shared__ int s_src[kTcPairs];
+  __shared__ int s_src[2][kTcPairs];                      // source boxes of the two B stages
   __shared__ int s_etgt[4][kTcPairs];                     // per epilogue warp: the unit's targets
   __shared__ int s_issued;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -390,27 +391,72 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_m2l_tcp(int R, int nstages, i
 
   if (warp < 4) {
     // ---- producers -------------------------------------------------------------------
+    // The B operand of unit k + 1 is gathered (cp.async, its own commit group) before the
+    // producers wait for unit k's, so one gather is always in flight behind the MMAs.
     int a_key = -1, a_loads = 0, issued = 0;
-    TCUnit nxt = units[u0];                               // the next unit's descriptor, one load ahead
-    for (int k = 0; k < nk; ++k) {
-      const TCUnit un = nxt;
-      if (k + 1 < nk) nxt = units[u0 + k + 1];
-      const int kt = un.kt, Rt = un.rank, key = un.key;
-      const int cnt = un.count, npad = (cnt + 15) & ~15;
-      const int b = k & 1;
-      const bool load_a = key != a_key;
-      // operands free: B stage b was last read by unit k - 2's MMAs; the A tile, when it
-      // is about to change, by unit k - 1's
-      const int sb = nstages == 2 ? b : 0;                 // B stage of this unit
-      bool ok = true;
-      if (nstages == 2 && k >= 2) ok = mbar_wait(mb_full[b], (uint32_t)(((k - 2) >> 1) & 1));
-      if (ok && (load_a || nstages == 1) && k >= 1)
-        ok = mbar_wait(mb_full[(k - 1) & 1], (uint32_t)(((k - 1) >> 1) & 1));
-      if (!producer_all(ok)) {
-        failed = true;
-        break;
+    const uint32_t sb_base = cvta_smem(b_base);
+    const uint32_t stage_bytes = (uint32_t)(2 * kTcPairs * R * 2);   // hi + lo of one stage
+    // gather unit u's B operand into stage st (s_src[st] holds its source boxes)
+    auto gather = [&](const TCUnit &u, int st) {
+      const int kg = u.rank / 8;                         // groups of 8 along K
+      const int np = (u.count + 15) & ~15;
+      const uint32_t hi0 = sb_base + (uint32_t)st * stage_bytes, lo0 = hi0 + (uint32_t)(kTcPairs * R * 2);
+      for (int e = threadIdx.x; e < np * kg; e += 128) {
+        const int p = e / kg, k8 = e % kg;
+        const bool v = p < u.count;
+        const __nv_bfloat16 *src = Mc16 + ((size_t)(v ? s_src[st][p] : 0) * 2 + u.kt) * 2 * R + k8 * 8;
+        const uint32_t off = canon_off(p, k8 * 8, kTcPairs);
+        cp_async16_zfill(hi0 + off, src, v);
+        cp_async16_zfill(lo0 + off, src + R, v);
       }
-      if (threadIdx.x < kTcPairs) s_src[threadIdx.x] = threadIdx.x < cnt ? pairs[un.pstart + threadIdx.x].y : 0;
+      asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    // a unit's descriptor and this thread's source box, fetched one unit ahead of use
+    auto src_of = [&](const TCUnit &u) {
+      return (threadIdx.x < kTcPairs && threadIdx.x < u.count) ? pairs[u.pstart + threadIdx.x].y : 0;
+    };
+    TCUnit un = units[u0];
+    if (threadIdx.x < kTcPairs) s_src[0][threadIdx.x] = src_of(un);
+    producer_sync();
+    gather(un, 0);
+    TCUnit nx{};
+    int nx_src = 0;
+    if (nk > 1) {
+      nx = units[u0 + 1];
+      nx_src = src_of(nx);
+    }
+    for (int k = 0; k < nk; ++k) {
+      const int b = k & 1;
+      const int Rt = un.rank, key = un.key;
+      const int npad = (un.count + 15) & ~15;
+      const bool load_a = key != a_key;
+      TCUnit nx2{};
+      int nx2_src = 0;
+      bool ok = true;
+      if (k + 1 < nk) {
+        if (k + 2 < nk) {                                // two units ahead: in flight during this one
+          nx2 = units[u0 + k + 2];
+          nx2_src = src_of(nx2);
+        }
+        // stage (k + 1) & 1 was last read by unit k - 1's MMAs
+        if (k >= 1) ok = mbar_wait(mb_full[(k - 1) & 1], (uint32_t)(((k - 1) >> 1) & 1));
+        if (!producer_all(ok)) {
+          failed = true;
+          break;
+        }
+        if (threadIdx.x < kTcPairs) s_src[(k + 1) & 1][threadIdx.x] = nx_src;
+        producer_sync();                                 // s_src visible
+        gather(nx, (k + 1) & 1);
+        asm volatile("cp.async.wait_group 1;" ::: "memory");   // unit k's gather has landed
+      } else {
+        // the last unit: its A tile, when it changes, must wait for unit k - 1's MMAs
+        if (load_a && k >= 1) ok = mbar_wait(mb_full[(k - 1) & 1], (uint32_t)(((k - 1) >> 1) & 1));
+        if (!producer_all(ok)) {
+          failed = true;
+          break;
+        }
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+      }
       if (load_a) {
         if (threadIdx.x == 0) {
           // row tile 0, K half 0; its first R / 8 K-groups of 8 are contiguous
@@ -431,23 +477,6 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_m2l_tcp(int R, int nstages, i
         a_key = key;
         ++a_loads;
       }
-      producer_sync();                                   // s_src visible
-      // B: npad pairs x Rt weights, already split into BF16 hi / lo by the compression:
-      // 16-byte asynchronous copies straight into the canonical K-major layout (rows of
-      // padding pairs are zero-filled)
-      const int kg = Rt / 8;                             // groups of 8 along K
-      const int nunit = npad * kg;
-      const uint32_t sb_hi0 = cvta_smem(b_base + sb * 2 * kTcPairs * R), sb_lo0 = sb_hi0 + (uint32_t)(kTcPairs * R * 2);
-      for (int e = threadIdx.x; e < nunit; e += 128) {
-        const int p = e / kg, k8 = e % kg;
-        const bool v = p < cnt;
-        const __nv_bfloat16 *src = Mc16 + ((size_t)(v ? s_src[p] : 0) * 2 + kt) * 2 * R + k8 * 8;
-        const uint32_t off = canon_off(p, k8 * 8, kTcPairs);
-        cp_async16_zfill(sb_hi0 + off, src, v);
-        cp_async16_zfill(sb_lo0 + off, src + R, v);
-      }
-      asm volatile("cp.async.commit_group;" ::: "memory");
-      asm volatile("cp.async.wait_group 0;" ::: "memory");
       asm volatile("fence.proxy.async.shared::cta;");
       producer_sync();
       bool ok0 = true;
@@ -459,7 +488,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_m2l_tcp(int R, int nstages, i
           const uint32_t idesc = instr_desc(kTcRows, npad);
           const uint32_t lbo_a = (kTcRows / 8) * 128, lbo_b = (kTcPairs / 8) * 128, sbo = 128;
           const uint32_t sa_hi = cvta_smem(a_hi), sa_lo = cvta_smem(a_lo);
-          const uint32_t sb_hi = cvta_smem(b_base + sb * 2 * kTcPairs * R), sb_lo = sb_hi + (uint32_t)(kTcPairs * R * 2);
+          const uint32_t sb_hi = sb_base + (uint32_t)b * stage_bytes, sb_lo = sb_hi + (uint32_t)(kTcPairs * R * 2);
           const uint32_t acc = tmem + (uint32_t)(b * kTcTmemCols);
           for (int st = 0; st < Rt / 16; ++st) {
             const uint32_t ka = 2 * st * lbo_a, kb = 2 * st * lbo_b;
@@ -488,7 +517,11 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_m2l_tcp(int R, int nstages, i
         failed = true;
         break;
       }
+      un = nx;
+      nx = nx2;
+      nx_src = nx2_src;
     }
+    asm volatile("cp.async.wait_all;" ::: "memory");     // no copy outlives the loop (also on failure)
     if (threadIdx.x == 0) s_issued = issued;
   } else {
     // ---- epilogue --------------------------------------------------------------------
@@ -551,11 +584,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_m2l_tcp(int R, int nstages, i
 namespace {
 constexpr int kTcSmem = (2 * kTcAElems + 2 * kTcBElems) * 2;
 // pipelined kernel: A tile (hi, lo) + B stages (hi, lo), r weights each
-int tcp_smem_bytes(int R, int stages) { return 2 * (2 * kTcRows * R) + stages * 2 * (2 * kTcPairs * R); }
-// Two B stages when they fit beside six P2P blocks on an SM (the P2P kernel runs on six
-// resident blocks per SM beside the far-field chain), else one.
-constexpr int kTcCoresidentSmem = 62 * 1024;
-int tcp_stages(int R) { return tcp_smem_bytes(R, 2) <= kTcCoresidentSmem ? 2 : 1; }
+int tcp_smem_bytes(int R) { return 2 * (2 * kTcRows * R) + 2 * 2 * (2 * kTcPairs * R); }   // two B stages
 }
 
 Err build_m2l_tc(afmpb_t *h) {
@@ -637,7 +666,7 @@ Err build_m2l_tc(afmpb_t *h) {
     AFMPB_TRY(A.alloc(&h->d_tc_units, std::max<size_t>(1, units.size()), "tc units"));
     if (!units.empty())
       AFMPB_CUDA(cudaMemcpyAsync(h->d_tc_units, units.data(), sizeof(TCUnit) * units.size(), cudaMemcpyHostToDevice, s));
-    AFMPB_TRY(raise_smem_limit((const void *)k_m2l_tcp, tcp_smem_bytes(h->m2l_rank, tcp_stages(h->m2l_rank))));
+    AFMPB_TRY(raise_smem_limit((const void *)k_m2l_tcp, tcp_smem_bytes(h->m2l_rank)));
   }
   AFMPB_CUDA(cudaStreamSynchronize(s));
   A.release(d_table_level);
@@ -654,8 +683,8 @@ Err enqueue_m2l_tc(afmpb_t *h, cudaStream_t s) {
     AFMPB_CUDA(cudaGetDevice(&dev));
     AFMPB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     const unsigned grid = (unsigned)std::min(h->tc_nunits, 2 * sms);   // two CTAs per SM
-    k_m2l_tcp<<<grid, kTcThreads, tcp_smem_bytes(h->m2l_rank, tcp_stages(h->m2l_rank)), s>>>(
-        h->m2l_rank, tcp_stages(h->m2l_rank), h->tc_nunits, h->d_tc_units, reinterpret_cast<const __nv_bfloat16 *>(h->d_Mc16), h->d_m2l_pairs,
+    k_m2l_tcp<<<grid, kTcThreads, tcp_smem_bytes(h->m2l_rank), s>>>(
+        h->m2l_rank, h->tc_nunits, h->d_tc_units, reinterpret_cast<const __nv_bfloat16 *>(h->d_Mc16), h->d_m2l_pairs,
         reinterpret_cast<const __nv_bfloat16 *>(h->d_tc_tiles), h->d_Lc, h->d_tc_flag);
     return check_launch("k_m2l_tcp");
   }
