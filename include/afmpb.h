@@ -298,6 +298,18 @@ size_t afmpb_estimate_bytes(int64_t n_nodes, int64_t n_atoms, int fmm_order,
 /* Library version string. */
 const char *afmpb_version(void);
 
+/* Self-test of the bounded device waits (no counterpart in the paper).  Every wait of the
+ * library's kernels on an mbarrier gives up after a fixed number of polls, records an error
+ * flag that the host turns into AFMPB_ETIMEOUT, and lets the kernel return, so that the
+ * context stays usable.  This call runs that mechanism on purpose: one thread waits, with
+ * at most spin_limit polls (1 .. 2^26), on a shared-memory mbarrier that nothing ever
+ * arrives at, on the current device and its own stream.
+ *   expired  host output: 1 when the wait gave up and the flag reached the host (the
+ *            expected outcome), 0 otherwise
+ * Returns EINVAL for a spin_limit out of range or a NULL expired, ECUDA on a launch or
+ * copy failure, else OK. */
+afmpb_status afmpb_selftest_bounded_wait(int spin_limit, int *expired);
+
 /* ---- Serving: continuous batching of whole solves ------------------------------------
  * The paper runs one solve at a time; this layer (no counterpart in the paper) serves
  * many molecules or conformations of uneven size on one GPU.  Each request is one full

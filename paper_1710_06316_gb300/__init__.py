@@ -114,7 +114,8 @@ EXPORTS = ["afmpb_create", "afmpb_matvec", "afmpb_matvec_parts", "afmpb_matvec_h
            "afmpb_get_info", "afmpb_destroy", "afmpb_last_error", "afmpb_estimate_bytes",
            "afmpb_version", "afmpb_profile_product", "afmpb_energy_noalloc",
            "afmpb_server_create", "afmpb_server_submit", "afmpb_server_poll", "afmpb_server_wait",
-           "afmpb_server_get_info", "afmpb_server_destroy", "afmpb_get_autotune"]
+           "afmpb_server_get_info", "afmpb_server_destroy", "afmpb_get_autotune",
+           "afmpb_selftest_bounded_wait"]
 
 
 def library_path() -> str:
@@ -148,6 +149,8 @@ def load(build: bool = True):
     lib.afmpb_energy_noalloc.argtypes = [P, C.POINTER(D)]
     lib.afmpb_get_autotune.restype = I32
     lib.afmpb_get_autotune.argtypes = [P, C.POINTER(AutotuneReport)]
+    lib.afmpb_selftest_bounded_wait.restype = I32
+    lib.afmpb_selftest_bounded_wait.argtypes = [C.c_int, C.POINTER(C.c_int)]
     lib.afmpb_server_create.restype = I32
     lib.afmpb_server_create.argtypes = [C.c_size_t, C.c_int, C.POINTER(P)]
     lib.afmpb_server_submit.restype = I32
@@ -207,6 +210,14 @@ def _check(rc, h=None):
 
 def version() -> str:
     return load().afmpb_version().decode()
+
+
+def selftest_bounded_wait(spin_limit=1000) -> bool:
+    """Runs a device wait that nothing satisfies with a bounded poll count; True when the
+    wait gave up and reported it (the library's failure path for expired waits)."""
+    e = C.c_int(0)
+    _check(load().afmpb_selftest_bounded_wait(int(spin_limit), C.byref(e)), None)
+    return bool(e.value)
 
 
 def estimate_bytes(n_nodes, n_atoms, order=6, leaf_cap=0, restart=0, charge_fmm=0) -> int:

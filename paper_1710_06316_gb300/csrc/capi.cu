@@ -749,4 +749,12 @@ size_t afmpb_estimate_bytes(int64_t n_nodes, int64_t n_atoms, int fmm_order, con
 
 const char *afmpb_version(void) { return "afmpb-gb300 0.1.0 (sm_103a)"; }
 
+afmpb_status afmpb_selftest_bounded_wait(int spin_limit, int *expired) {
+  if (!expired || spin_limit < 1 || spin_limit > (1 << 26))
+    return fail(nullptr, make_err(AFMPB_EINVAL, "spin_limit must be in [1, 2^26] and expired non-NULL"));
+  *expired = 0;
+  Err e = selftest_bounded_wait(spin_limit, expired);
+  return e.ok() ? AFMPB_OK : fail(nullptr, e);
+}
+
 }  // extern "C"

@@ -354,7 +354,8 @@ int autotune_cached_cap(int precision, int order, double kappa, int64_t n);   //
 // m2l_svd.cu: compressed translations; *compressed = false leaves the full ones in use
 Err build_m2l_svd(afmpb_t *h, bool *compressed);
 Err enqueue_m2l_svd(afmpb_t *h, cudaStream_t s, StageTimer *tm = nullptr);   // compress, translate, expand
-Err read_tc_error(afmpb_t *h, int *flag);             // 1 when a tensor-core wait expired
+Err read_tc_error(afmpb_t *h, int *flag);
+Err selftest_bounded_wait(int spin_limit, int *expired);   // m2l_tc.cu             // 1 when a tensor-core wait expired
 // solve.cu
 Err build_rhs(afmpb_t *h);
 Err enqueue_gather(afmpb_t *h, cudaStream_t s, const float *x_caller);

@@ -72,8 +72,8 @@ __device__ __forceinline__ void split_bf16(float v, __nv_bfloat16 &hi, __nv_bflo
   lo = __float2bfloat16_rn(v - __bfloat162float(hi));
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t mb, uint32_t parity) {
-  for (uint32_t spin = 0; spin < kTcSpinLimit; ++spin) {
+__device__ __forceinline__ bool mbar_wait(uint32_t mb, uint32_t parity, uint32_t limit = kTcSpinLimit) {
+  for (uint32_t spin = 0; spin < limit; ++spin) {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred P1;\n\tmbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2;\n\t"
@@ -696,6 +696,36 @@ Err enqueue_m2l_tc(afmpb_t *h, cudaStream_t s) {
                                              h->d_box_center, comp ? h->d_Mc : h->d_M, comp ? h->d_Lc : h->d_L,
                                              h->d_tc_flag, comp ? h->d_table_rank : nullptr);
   return check_launch("k_m2l_tc");
+}
+
+// The bounded wait run on purpose: an mbarrier expecting one arrival that never comes.
+__global__ void k_wait_selftest(uint32_t limit, int *flag) {
+  __shared__ __align__(8) uint64_t bar;
+  const uint32_t mb = cvta_smem(&bar);
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb));
+  asm volatile("fence.mbarrier_init.release.cluster;");
+  if (!mbar_wait(mb, 0, limit)) atomicExch(flag, 1);
+  asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(mb));
+}
+
+Err selftest_bounded_wait(int spin_limit, int *expired) {
+  cudaStream_t s = nullptr;
+  AFMPB_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+  struct Guard {
+    cudaStream_t s;
+    int *d = nullptr;
+    ~Guard() {
+      if (d) cudaFree(d);
+      cudaStreamDestroy(s);
+    }
+  } g{s};
+  AFMPB_CUDA(cudaMalloc(&g.d, sizeof(int)));
+  AFMPB_CUDA(cudaMemsetAsync(g.d, 0, sizeof(int), s));
+  k_wait_selftest<<<1, 1, 0, s>>>((uint32_t)spin_limit, g.d);
+  AFMPB_TRY(check_launch("k_wait_selftest"));
+  AFMPB_CUDA(cudaMemcpyAsync(expired, g.d, sizeof(int), cudaMemcpyDeviceToHost, s));
+  AFMPB_CUDA(cudaStreamSynchronize(s));
+  return Err{};
 }
 
 Err read_tc_error(afmpb_t *h, int *flag) {

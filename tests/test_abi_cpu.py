@@ -85,3 +85,13 @@ def test_invalid_mesh_is_rejected_on_the_host():
     with pytest.raises(pb.AfmpbError) as e:
         pb.Handle(xyz2, tri, eps_in=1, eps_out=80, kappa=0.1)
     assert e.value.status == "EINVAL"
+
+
+def test_selftest_arguments_are_checked_on_the_host():
+    import ctypes
+    import paper_1710_06316_gb300 as pb
+    lib = pb.load()
+    e = ctypes.c_int(7)
+    assert lib.afmpb_selftest_bounded_wait(0, ctypes.byref(e)) == 1        # EINVAL
+    assert lib.afmpb_selftest_bounded_wait(100, None) == 1
+    assert lib.afmpb_selftest_bounded_wait((1 << 26) + 1, ctypes.byref(e)) == 1

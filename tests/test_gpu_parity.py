@@ -371,3 +371,16 @@ def test_kirkwood_full_size_sampled_rows(precision):
     got = np.concatenate([y[rows], y[n + rows]])
     ref = np.concatenate([y1, y2])
     assert relerr(got, ref) < TOL_MATVEC
+
+
+def test_bounded_wait_expires_and_the_context_stays_usable():
+    """Failure path of the device waits, triggered on purpose: a wait on an mbarrier that
+    nothing arrives at gives up after its poll limit and reports it; a product on the same
+    context afterwards still matches the oracle."""
+    import paper_1710_06316_gb300 as pb
+    assert pb.selftest_bounded_wait(2000) is True
+    mol = synthetic.born_ion(subdiv=3)
+    x = synthetic.random_unknowns(mol.n_nodes, 4)
+    with pb.Handle.for_molecule(mol, order=6, precision=1) as h:
+        y = gpu_matvec(h, x)
+    assert relerr(y, oracle.Oracle.for_molecule(mol).matvec(x)) < TOL_MATVEC
