@@ -220,7 +220,10 @@ afmpb_status afmpb_solve(afmpb_t *h, double *f_host, double *h_host, afmpb_solve
 
 /* Polar solvation energy (kcal/mol) of the last solution:
  * E = 1/2 sum_k q_k phi_reac(r_k), phi_reac from the interior Green representation of
- * the surface solution.  Requires a successful (or ENOCONV) afmpb_solve. */
+ * the surface solution.  Requires a successful (or ENOCONV) afmpb_solve.  phi_reac is
+ * summed directly, or, when the handle uses the charge FMM (afmpb_options.charge_fmm,
+ * afmpb_info.charge_fmm), by a Laplace FMM over the nodes and the charges (~1e-5
+ * relative to the direct sum). */
 afmpb_status afmpb_energy(afmpb_t *h, double *kcal_per_mol);
 
 /* Allocation-free variant of afmpb_energy, for callers that cannot call cudaMalloc:
@@ -242,7 +245,8 @@ afmpb_status afmpb_energy(afmpb_t *h, double *kcal_per_mol);
 #define AFMPB_NOALLOC_MAX_ATOMS 65536
 afmpb_status afmpb_energy_noalloc(afmpb_t *h, double *kcal_per_mol);
 
-/* The right-hand side of Eq. 5 (caller order, host [2N]). */
+/* The right-hand side of Eq. 5 (caller order, host [2N]), formed at create time directly
+ * or by the charge FMM (afmpb_options.charge_fmm; ~1e-5 relative L2 per block). */
 afmpb_status afmpb_rhs(afmpb_t *h, double *b_host);
 
 /* Node-patch geometry in caller order (host buffers, each may be NULL): patch area [N],
