@@ -186,6 +186,7 @@ __device__ void self_rule(Real kappa, Real inv_ebar, const double *xyz, const in
 // Near-set walk.  fill == false: count per row; else write the columns.
 __global__ void k_near_search(int64_t n, double cnear, const int32_t *__restrict__ perm,
                               const double *__restrict__ xyz, const double *__restrict__ rho,
+                              const float4 *__restrict__ pos, const float4 *__restrict__ nrm,
                               const dbl4 *__restrict__ center, const double *__restrict__ brho,
                               const int32_t *__restrict__ child0, const int32_t *__restrict__ nchild,
                               const int32_t *__restrict__ bbeg, const int32_t *__restrict__ bend,
@@ -210,15 +211,36 @@ __global__ void k_near_search(int64_t n, double cnear, const int32_t *__restrict
     const double bR = cnear * (rp + brho[b]);
     if (dx * dx + dy * dy + dz * dz >= bR * bR * (1.0 + 1e-12)) continue;
     if (nchild[b] == 0) {
+      // FP32 pre-test on the leaf-relative positions.  The FP32 distance carries an
+      // absolute error below 2^-22 (|o| + |q|) per component (|o|, |q|: the offsets it is
+      // formed from), so d^2 is off by less than 5e-7 R S + 1e-6 R^2 near the boundary
+      // (S = sum of the |o| and |q| components); the FP64 test decides inside twice that.
+      const float ox = (float)(x0 - c.x), oy = (float)(x1 - c.y), oz = (float)(x2 - c.z);
+      const float so = fabsf(ox) + fabsf(oy) + fabsf(oz);
+      const float frp = (float)(cnear * rp), fc = (float)cnear;
       for (int t = bbeg[b]; t < bend[b]; ++t) {
-        int64_t ot = perm[t];
-        double ex = x0 - xyz[3 * ot], ey = x1 - xyz[3 * ot + 1], ez = x2 - xyz[3 * ot + 2];
-        const double d2 = ex * ex + ey * ey + ez * ez;
-        const double R = cnear * (rp + rho[ot]);
-        // dist < R decided on squares, and with the square root (the defining test) only
-        // inside the few-ulp band where the two could disagree
-        bool in = d2 < R * R * (1.0 - 1e-12);
-        if (!in && d2 < R * R * (1.0 + 1e-12)) in = sqrt(d2) < R;
+        const float4 q = pos[t];
+        const float fx = ox - q.x, fy = oy - q.y, fz = oz - q.z;
+        const float fd2 = fx * fx + fy * fy + fz * fz;
+        const float fR = fmaf(fc, nrm[t].w, frp);
+        const float fR2 = fR * fR;
+        const float S = so + fabsf(q.x) + fabsf(q.y) + fabsf(q.z);
+        const float margin = 1e-6f * fR * S + 1e-5f * fR2;
+        bool in;
+        if (fd2 < fR2 - margin) {
+          in = true;
+        } else if (fd2 > fR2 + margin) {
+          in = false;
+        } else {
+          int64_t ot = perm[t];
+          double ex = x0 - xyz[3 * ot], ey = x1 - xyz[3 * ot + 1], ez = x2 - xyz[3 * ot + 2];
+          const double d2 = ex * ex + ey * ey + ez * ez;
+          const double R = cnear * (rp + rho[ot]);
+          // dist < R decided on squares, and with the square root (the defining test)
+          // only inside the few-ulp band where the two could disagree
+          in = d2 < R * R * (1.0 - 1e-12);
+          if (!in && d2 < R * R * (1.0 + 1e-12)) in = sqrt(d2) < R;
+        }
         if (t == p || in) {
           if (fill) col[base + k] = t;
           ++k;
@@ -510,9 +532,9 @@ Err build_near(afmpb_t *h) {
   int64_t *d_cnt = nullptr;
   AFMPB_TRY(A.alloc(&d_cnt, n, "near cnt"));
   const double cnear = h->opt.near_c;
-  k_near_search<<<div_up(n, 128), 128, 0, s>>>(n, cnear, h->d_perm, h->d_xyz, h->d_rho64, h->d_box_center,
-                                               h->d_box_rho, h->d_box_child0, h->d_box_nchild, h->d_box_begin,
-                                               h->d_box_end, d_cnt, nullptr, nullptr, false);
+  k_near_search<<<div_up(n, 128), 128, 0, s>>>(n, cnear, h->d_perm, h->d_xyz, h->d_rho64, h->d_pos, h->d_nrm,
+                                               h->d_box_center, h->d_box_rho, h->d_box_child0, h->d_box_nchild,
+                                               h->d_box_begin, h->d_box_end, d_cnt, nullptr, nullptr, false);
   AFMPB_TRY(check_launch("k_near_search count"));
   std::vector<int64_t> cnt(n), ptr(n + 1, 0);
   AFMPB_CUDA(cudaMemcpyAsync(cnt.data(), d_cnt, sizeof(int64_t) * n, cudaMemcpyDeviceToHost, s));
@@ -523,9 +545,10 @@ Err build_near(afmpb_t *h) {
   AFMPB_TRY(A.alloc(&h->d_near_col, h->nnz, "near col"));
   AFMPB_TRY(A.alloc(&h->d_near_coef, h->nnz, "near coef"));
   AFMPB_CUDA(cudaMemcpyAsync(h->d_near_ptr, ptr.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, s));
-  k_near_search<<<div_up(n, 128), 128, 0, s>>>(n, cnear, h->d_perm, h->d_xyz, h->d_rho64, h->d_box_center,
-                                               h->d_box_rho, h->d_box_child0, h->d_box_nchild, h->d_box_begin,
-                                               h->d_box_end, nullptr, h->d_near_ptr, h->d_near_col, true);
+  k_near_search<<<div_up(n, 128), 128, 0, s>>>(n, cnear, h->d_perm, h->d_xyz, h->d_rho64, h->d_pos, h->d_nrm,
+                                               h->d_box_center, h->d_box_rho, h->d_box_child0, h->d_box_nchild,
+                                               h->d_box_begin, h->d_box_end, nullptr, h->d_near_ptr, h->d_near_col,
+                                               true);
   AFMPB_TRY(check_launch("k_near_search fill"));
   KernelParams kp{h->kappa, h->ebar};
   AFMPB_TRY(A.alloc(&h->d_near_full, h->nnz, "near full"));
