@@ -120,28 +120,57 @@ __device__ __forceinline__ void abcd_point(Real kappa, Real inv_ebar, const V3<R
   o[3] = (nn0 * G3 * p1 - ndn * n0d * G5 * p2) * inv_ebar;
 }
 
-// Corners of triangle t rotated so that node v comes first, relative to the point o
-// (difference taken in FP64).
-template <class Real>
-__device__ __forceinline__ void tri_rel(const double *xyz, const int32_t *tri, int32_t t, int64_t v,
-                                        const double *o, V3<Real> P[3]) {
+// FP32 geometry for the quadrature (caller order): each coordinate x split into
+// hi = fl32(x) and lo = fl32(x - hi), so that a difference of two points formed as
+// (hi_a - hi_b) + (lo_a - lo_b) carries the same ~1e-7 relative error as the FP64
+// difference rounded to FP32, without FP64 arithmetic; normals with the patch area,
+// facet normals.
+struct GeomF32 {
+  const float4 *hi, *lo;      // [n] position split, w unused
+  const float4 *nrm_area;     // [n] node normal, w = patch area
+  const float4 *tri_nrm;      // [nt] unit facet normal
+};
+
+__global__ void k_geom_f32(int64_t n, int64_t nt, const double *__restrict__ xyz, const double *__restrict__ nrm,
+                           const double *__restrict__ area, const double *__restrict__ tri_nrm,
+                           float4 *__restrict__ hi, float4 *__restrict__ lo, float4 *__restrict__ nrm_area,
+                           float4 *__restrict__ tnrm) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) {
+    float h[3], l[3];
+    for (int d = 0; d < 3; ++d) {
+      h[d] = (float)xyz[3 * i + d];
+      l[d] = (float)(xyz[3 * i + d] - (double)h[d]);
+    }
+    hi[i] = make_float4(h[0], h[1], h[2], 0.f);
+    lo[i] = make_float4(l[0], l[1], l[2], 0.f);
+    nrm_area[i] = make_float4((float)nrm[3 * i], (float)nrm[3 * i + 1], (float)nrm[3 * i + 2], (float)area[i]);
+  }
+  if (i < nt) tnrm[i] = make_float4((float)tri_nrm[3 * i], (float)tri_nrm[3 * i + 1], (float)tri_nrm[3 * i + 2], 0.f);
+}
+
+__device__ __forceinline__ V3<float> diff_f32(const GeomF32 &g, int64_t a, const float4 &ho, const float4 &lo) {
+  const float4 ha = g.hi[a], la = g.lo[a];
+  return V3<float>{(ha.x - ho.x) + (la.x - lo.x), (ha.y - ho.y) + (la.y - lo.y), (ha.z - ho.z) + (la.z - lo.z)};
+}
+
+// Corners of triangle t rotated so that node v comes first, relative to node o.
+__device__ __forceinline__ void tri_rel_f32(const GeomF32 &g, const int32_t *tri, int32_t t, int64_t v, int64_t o,
+                                            V3<float> P[3]) {
   int k0 = 0;
   for (int k = 0; k < 3; ++k)
     if (tri[3 * t + k] == v) k0 = k;
-  for (int j = 0; j < 3; ++j) {
-    const double *q = xyz + 3 * (int64_t)tri[3 * t + (k0 + j) % 3];
-    P[j] = V3<Real>{(Real)(q[0] - o[0]), (Real)(q[1] - o[1]), (Real)(q[2] - o[2])};
-  }
+  const float4 ho = g.hi[o], lo = g.lo[o];
+  for (int j = 0; j < 3; ++j) P[j] = diff_f32(g, tri[3 * t + (k0 + j) % 3], ho, lo);
 }
 
 template <class Real>
-__device__ void self_rule(Real kappa, Real inv_ebar, const double *xyz, const int32_t *tri, const int64_t *inc_ptr,
+__device__ void self_rule(Real kappa, Real inv_ebar, const GeomF32 &gf, const int32_t *tri, const int64_t *inc_ptr,
                           const int32_t *inc_tri, int64_t op, const V3<Real> &np, Real o[4]) {
-  const double *xp = xyz + 3 * op;
   Real As = 0, Ds = 0;
   for (int64_t j = inc_ptr[op]; j < inc_ptr[op + 1]; ++j) {
     V3<Real> P[3];
-    tri_rel(xyz, tri, inc_tri[j], op, xp, P);   // P[0] = 0 (the node itself)
+    tri_rel_f32(gf, tri, inc_tri[j], op, op, P);   // P[0] = 0 (the node itself)
     const V3<Real> ma{Real(0.5) * P[1].x, Real(0.5) * P[1].y, Real(0.5) * P[1].z};
     const V3<Real> mb{Real(0.5) * P[2].x, Real(0.5) * P[2].y, Real(0.5) * P[2].z};
     const V3<Real> cen{(P[1].x + P[2].x) / Real(3), (P[1].y + P[2].y) / Real(3), (P[1].z + P[2].z) / Real(3)};
@@ -256,9 +285,9 @@ __global__ void k_near_search(int64_t n, double cnear, const int32_t *__restrict
 // Self entries (t == p): one thread per node; the fixed 16 x 16 rule keeps the lanes
 // of a warp together.  Columns of a row are in ascending Morton order.
 __global__ void __launch_bounds__(128) k_near_self(int64_t n, KernelParams kp, const int32_t *__restrict__ perm,
-                                                   const double *__restrict__ xyz, const int32_t *__restrict__ tri,
+                                                   GeomF32 gf, const int32_t *__restrict__ tri,
                                                    const int64_t *__restrict__ inc_ptr,
-                                                   const int32_t *__restrict__ inc_tri, const double *__restrict__ nrm,
+                                                   const int32_t *__restrict__ inc_tri,
                                                    const int64_t *__restrict__ ptr, const int32_t *__restrict__ col,
                                                    float4 *__restrict__ coef, uint8_t *__restrict__ full) {
   const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -269,9 +298,10 @@ __global__ void __launch_bounds__(128) k_near_self(int64_t n, KernelParams kp, c
     if (col[mid] < p) lo = mid + 1; else hi = mid;
   }
   const int64_t op = perm[p];
-  const V3<float> np{(float)nrm[3 * op], (float)nrm[3 * op + 1], (float)nrm[3 * op + 2]};
+  const float4 na = gf.nrm_area[op];
+  const V3<float> np{na.x, na.y, na.z};
   float o[4] = {0, 0, 0, 0};
-  self_rule((float)kp.kappa, (float)(1.0 / kp.ebar), xyz, tri, inc_ptr, inc_tri, op, np, o);
+  self_rule((float)kp.kappa, (float)(1.0 / kp.ebar), gf, tri, inc_ptr, inc_tri, op, np, o);
   coef[lo] = make_float4(o[0], o[1], o[2], o[3]);
   full[lo] = 1;
 }
@@ -316,12 +346,11 @@ __device__ __forceinline__ bool p2p_leaves_out(const P2PView &pv, int p, int t) 
 // 2-bit digits in a register.
 __global__ void __launch_bounds__(128) k_near_pairs(int64_t nnz, const int32_t *__restrict__ row,
                                                     unsigned long long *__restrict__ counter, KernelParams kp,
-                                                    const int32_t *__restrict__ perm, const double *__restrict__ xyz,
+                                                    const int32_t *__restrict__ perm, GeomF32 gf,
                                                     const int32_t *__restrict__ tri,
                                                     const int64_t *__restrict__ inc_ptr,
                                                     const int32_t *__restrict__ inc_tri,
-                                                    const double *__restrict__ tri_nrm, const double *__restrict__ area,
-                                                    const double *__restrict__ nrm, const int32_t *__restrict__ col,
+                                                    const int32_t *__restrict__ col,
                                                     P2PView pv, float4 *__restrict__ coef,
                                                     uint8_t *__restrict__ full) {
   const float kappa = (float)kp.kappa, inv_ebar = (float)(1.0 / kp.ebar);
@@ -345,7 +374,10 @@ __global__ void __launch_bounds__(128) k_near_pairs(int64_t nnz, const int32_t *
         if (t == p) continue;                 // diagonal: k_near_self
         op = perm[p];
         ot = perm[t];
-        np = V3<float>{(float)nrm[3 * op], (float)nrm[3 * op + 1], (float)nrm[3 * op + 2]};
+        {
+          const float4 na = gf.nrm_area[op];
+          np = V3<float>{na.x, na.y, na.z};
+        }
         whole = p2p_leaves_out(pv, p, t);
         tj = inc_ptr[ot];
         tend = inc_ptr[ot + 1];
@@ -358,12 +390,12 @@ __global__ void __launch_bounds__(128) k_near_pairs(int64_t nnz, const int32_t *
         if (tj >= tend) {                     // entry finished
           float o[4] = {acc[0], acc[1], acc[2], acc[3]};
           if (!whole) {
-            const double *xp = xyz + 3 * op, *xt = xyz + 3 * ot;
-            const V3<float> dd{(float)(xp[0] - xt[0]), (float)(xp[1] - xt[1]), (float)(xp[2] - xt[2])};
-            const V3<float> nt{(float)nrm[3 * ot], (float)nrm[3 * ot + 1], (float)nrm[3 * ot + 2]};
+            const V3<float> dd = diff_f32(gf, op, gf.hi[ot], gf.lo[ot]);
+            const float4 na = gf.nrm_area[ot];
+            const V3<float> nt{na.x, na.y, na.z};
             float f[4];
             abcd_point(kappa, inv_ebar, dd, np, nt, f);
-            const float at = (float)area[ot];
+            const float at = na.w;
             for (int k = 0; k < 4; ++k) o[k] -= at * f[k];
           }
           coef[e] = make_float4(o[0], o[1], o[2], o[3]);
@@ -373,14 +405,16 @@ __global__ void __launch_bounds__(128) k_near_pairs(int64_t nnz, const int32_t *
         }
         const int32_t T = inc_tri[tj];
         V3<float> P[3];
-        tri_rel(xyz, tri, T, ot, xyz + 3 * op, P);
+        tri_rel_f32(gf, tri, T, ot, op, P);
         const V3<float> ma{0.5f * (P[0].x + P[1].x), 0.5f * (P[0].y + P[1].y), 0.5f * (P[0].z + P[1].z)};
         const V3<float> mb{0.5f * (P[0].x + P[2].x), 0.5f * (P[0].y + P[2].y), 0.5f * (P[0].z + P[2].z)};
         const float third = 1.0f / 3.0f;
         const V3<float> cen{(P[0].x + P[1].x + P[2].x) * third, (P[0].y + P[1].y + P[2].y) * third,
                             (P[0].z + P[1].z + P[2].z) * third};
-        const double *tn = tri_nrm + 3 * (int64_t)T;
-        ns = V3<float>{(float)tn[0], (float)tn[1], (float)tn[2]};
+        {
+          const float4 tn = gf.tri_nrm[T];
+          ns = V3<float>{tn.x, tn.y, tn.z};
+        }
         R0 = P[0];
         R1 = half == 0 ? ma : cen;
         R2 = half == 0 ? cen : mb;
@@ -552,9 +586,17 @@ Err build_near(afmpb_t *h) {
   AFMPB_TRY(check_launch("k_near_search fill"));
   KernelParams kp{h->kappa, h->ebar};
   AFMPB_TRY(A.alloc(&h->d_near_full, h->nnz, "near full"));
-  k_near_self<<<div_up(n, 128), 128, 0, s>>>(n, kp, h->d_perm, h->d_xyz, h->d_tri, h->d_inc_ptr, h->d_inc_tri,
-                                              h->d_nrm64, h->d_near_ptr, h->d_near_col, h->d_near_coef,
-                                              h->d_near_full);
+  float4 *g_hi = nullptr, *g_lo = nullptr, *g_na = nullptr, *g_tn = nullptr;
+  AFMPB_TRY(A.alloc(&g_hi, n, "near geometry hi"));
+  AFMPB_TRY(A.alloc(&g_lo, n, "near geometry lo"));
+  AFMPB_TRY(A.alloc(&g_na, n, "near normals"));
+  AFMPB_TRY(A.alloc(&g_tn, h->nt, "near facet normals"));
+  k_geom_f32<<<div_up(std::max<int64_t>(n, h->nt), 256), 256, 0, s>>>(n, h->nt, h->d_xyz, h->d_nrm64, h->d_area64,
+                                                                      h->d_tri_nrm, g_hi, g_lo, g_na, g_tn);
+  AFMPB_TRY(check_launch("k_geom_f32"));
+  const GeomF32 gf{g_hi, g_lo, g_na, g_tn};
+  k_near_self<<<div_up(n, 128), 128, 0, s>>>(n, kp, h->d_perm, gf, h->d_tri, h->d_inc_ptr, h->d_inc_tri,
+                                              h->d_near_ptr, h->d_near_col, h->d_near_coef, h->d_near_full);
   AFMPB_TRY(check_launch("k_near_self"));
   int32_t *d_row = nullptr;
   unsigned long long *d_counter = nullptr;
@@ -570,11 +612,14 @@ Err build_near(afmpb_t *h) {
   AFMPB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   const int64_t want = div_up(h->nnz, 128);   // lanes take entries dynamically; cap the grid
   const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sms * 16));
-  k_near_pairs<<<grid, 128, 0, s>>>(h->nnz, d_row, d_counter, kp, h->d_perm, h->d_xyz, h->d_tri, h->d_inc_ptr,
-                                    h->d_inc_tri, h->d_tri_nrm, h->d_area64, h->d_nrm64, h->d_near_col, pv,
-                                    h->d_near_coef, h->d_near_full);
+  k_near_pairs<<<grid, 128, 0, s>>>(h->nnz, d_row, d_counter, kp, h->d_perm, gf, h->d_tri, h->d_inc_ptr,
+                                    h->d_inc_tri, h->d_near_col, pv, h->d_near_coef, h->d_near_full);
   AFMPB_TRY(check_launch("k_near_pairs"));
   AFMPB_CUDA(cudaStreamSynchronize(s));
+  A.release(g_tn);
+  A.release(g_na);
+  A.release(g_lo);
+  A.release(g_hi);
   A.release(d_counter);
   A.release(d_row);
   A.release(d_cnt);
