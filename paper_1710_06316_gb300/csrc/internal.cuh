@@ -8,6 +8,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/afmpb.h"
@@ -378,6 +379,27 @@ Err product_sorted(afmpb_t *h, cudaStream_t s, int parts);  // d_xs -> d_ys
 
 // launch helpers
 inline int div_up(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+// Host: f(part, begin, end) over [0, n) split into contiguous ranges, one per host thread
+// (at most 16, and at most one per 4,096 items); returns the number of parts.  Part p
+// covers [n p / parts, n (p + 1) / parts), so results written per part and concatenated
+// in part order equal a sequential pass.
+template <class F>
+int host_parallel(int64_t n, F f) {
+  const int parts = (int)std::max<int64_t>(
+      1, std::min<int64_t>({16, (int64_t)std::max(1u, std::thread::hardware_concurrency()), n / 4096 + 1}));
+  std::vector<std::thread> pool;
+  for (int p = 1; p < parts; ++p) pool.emplace_back(f, p, n * p / parts, n * (p + 1) / parts);
+  f(0, (int64_t)0, n / parts);
+  for (auto &t : pool) t.join();
+  return parts;
+}
+
+// The number of parts host_parallel will use for n items (to size per-part buffers).
+inline int host_parts(int64_t n) {
+  return (int)std::max<int64_t>(
+      1, std::min<int64_t>({16, (int64_t)std::max(1u, std::thread::hardware_concurrency()), n / 4096 + 1}));
+}
 // Raise a kernel's dynamic shared-memory limit to at least `bytes` (the attribute is
 // process-wide per kernel and per device, so it is only ever raised: a handle that needs
 // less must not lower it under another handle's launch).
