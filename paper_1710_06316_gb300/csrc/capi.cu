@@ -730,7 +730,8 @@ size_t afmpb_estimate_bytes(int64_t n_nodes, int64_t n_atoms, int fmm_order, con
   const size_t nbox = 3 * (n / (size_t)std::max(cap / 2, 1) + 64);
   size_t b = 0;
   b += n * (3 * 8 + 8 + 3 * 8 + 8 + 2 * 16 + 8 + 4 + 4 + 2 * 16 + 8 + 2 * 4 + 4 * 16);   // nodes
-  b += 2 * n * (3 * 4 + 3 * 8 + 4);                                                    // triangles
+  b += n * 3 * 16;                                          // near-field setup: hi/lo coordinates, normals
+  b += 2 * n * (3 * 4 + 3 * 8 + 4 + 16);                    // triangles (+ FP32 facet normals at setup)
   const double c = (o && o->near_c > 0) ? o->near_c : 2.0;
   const size_t per_row = (size_t)std::ceil(80.0 * (c / 2.0) * (c / 2.0));             // isosurface meshes ~70
   b += n * per_row * (4 + 16 + 1) + 8 * (n + 1);                                        // near CSR
