@@ -24,22 +24,33 @@ _lib = None
 K_C = 332.0636  # kcal A / (mol e^2); reading R7
 
 
+def compile_source(src: str, out: str) -> str:
+    """gcc (-O2, OpenMP, portable flags only) of one oracle source into a shared library."""
+    subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11",
+                           src, "-o", out, "-lm"])
+    return out
+
+
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (-O2, OpenMP).  Portable flags only."""
+    """Compile the oracle into ``liborc.so`` beside its source when the source is newer."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + ".tmp%d" % os.getpid()
-        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11",
-                               _SRC, "-o", tmp, "-lm"])
+        compile_source(_SRC, tmp)
         os.replace(tmp, _LIB)
     return _LIB
 
 
 def _load():
     global _lib
-    if _lib is not None:
-        return _lib
-    build()
-    lib = C.CDLL(_LIB)
+    if _lib is None:
+        build()
+        _lib = configure(C.CDLL(_LIB))
+    return _lib
+
+
+def configure(lib):
+    """Declare the argument and return types of the oracle's entry points on a loaded
+    copy of the library (the tests also load copies compiled from altered sources)."""
     P = C.c_void_p
     i64, dbl, i32 = C.c_int64, C.c_double, C.c_int
     lib.orc_create.restype = P
@@ -70,7 +81,6 @@ def _load():
     lib.orc_gmres.restype = i32
     lib.orc_gmres.argtypes = [P, P, P, P, i32, i32, dbl, dbl, dbl, P]
     lib.orc_num_threads.restype = i32
-    _lib = lib
     return lib
 
 
