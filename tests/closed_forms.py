@@ -9,6 +9,7 @@
     rho_n = x k_n'(x)/k_n(x) = n - x R_n, R_n = k_{n+1}/k_n, x = kappa a,
     R_0 = (1 + x)/x,  R_n = 1/R_{n-1} + (2n+1)/x   (k_n modified spherical Bessel),
   and rho_n = -(n+1) at kappa = 0.
+The surface values f, h of the same series solution are given node-wise too.
 These are the standard textbook solutions; the tests check the series against itself
 in two limits (n = 0 is the Born energy with salt; kappa = 0 gives the classical
 (n+1)(eps_in - eps_out)/(n eps_in + (n+1) eps_out)).
@@ -48,6 +49,57 @@ def kirkwood_g(n_max, a, eps_in, eps_out, kappa):
         rho = n - x * R
         g[n] = (eps_in * (n + 1) + eps_out * rho) / (eps_in * n - eps_out * rho)
     return g
+
+
+def kirkwood_rho(n_max, a, kappa):
+    """rho_n = a phi_n'(a) / phi_n(a) for the decaying exterior solution phi_n of order n:
+    n - x R_n with the upward ratio recurrence above, or -(n+1) at kappa = 0."""
+    if kappa == 0.0:
+        return -(np.arange(n_max + 1) + 1.0)
+    x = kappa * a
+    rho = np.zeros(n_max + 1)
+    R = (1.0 + x) / x
+    for n in range(n_max + 1):
+        if n > 0:
+            R = 1.0 / R + (2 * n + 1) / x
+        rho[n] = n - x * R
+    return rho
+
+
+def _terms(atoms, a, tol, n_max):
+    """Terms of the surface series: its n-th term scales as (r_max / a)^n."""
+    r = np.linalg.norm(atoms, axis=1)
+    ratio = r.max() / a if r.size else 0.0
+    if ratio > 0:
+        return min(n_max, int(np.ceil(np.log(tol) / np.log(ratio))) + 2)
+    return n_max
+
+
+def kirkwood_surface(atoms, q, pts, a, eps_in, eps_out, kappa, tol=1e-14, n_max=400):
+    """Exact f (potential) and h (exterior normal derivative) at points pts on the sphere
+    |x| = a.  With c_n = q_j r_j^n / (4 pi eps_in) the Coulomb part inside is
+    c_n r^-(n+1) P_n, the reaction part g_n c_n r^n / a^(2n+1) P_n (the g_n of the energy),
+    and continuity at r = a makes the exterior coefficient (1 + g_n) c_n a^-(n+1):
+      f = sum_j q_j / (4 pi eps_in a)   sum_n (1 + g_n)       (r_j / a)^n P_n(cos g_j)
+      h = sum_j q_j / (4 pi eps_in a^2) sum_n (1 + g_n) rho_n (r_j / a)^n P_n(cos g_j)."""
+    atoms = np.asarray(atoms, dtype=np.float64)
+    q = np.asarray(q, dtype=np.float64)
+    pts = np.asarray(pts, dtype=np.float64)
+    n_use = _terms(atoms, a, tol, n_max)
+    g = kirkwood_g(n_use, a, eps_in, eps_out, kappa)
+    rho = kirkwood_rho(n_use, a, kappa)
+    r = np.linalg.norm(atoms, axis=1)
+    u = pts / np.linalg.norm(pts, axis=1, keepdims=True)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        cosg = (u @ atoms.T) / np.maximum(r, 1e-300)[None, :]
+    cosg = np.clip(np.where(r[None, :] > 0, cosg, 1.0), -1.0, 1.0)
+    f = np.zeros(pts.shape[0])
+    h = np.zeros(pts.shape[0])
+    for n in range(n_use + 1):
+        t = (eval_legendre(n, cosg) * ((r / a) ** n * q)[None, :]).sum(axis=1)
+        f += (1.0 + g[n]) * t
+        h += (1.0 + g[n]) * rho[n] * t
+    return f / (4 * np.pi * eps_in * a), h / (4 * np.pi * eps_in * a * a)
 
 
 def kirkwood_energy(atoms, q, a, eps_in, eps_out, kappa, tol=1e-14, n_max=400):
