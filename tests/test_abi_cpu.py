@@ -95,3 +95,70 @@ def test_selftest_arguments_are_checked_on_the_host():
     assert lib.afmpb_selftest_bounded_wait(0, ctypes.byref(e)) == 1        # EINVAL
     assert lib.afmpb_selftest_bounded_wait(100, None) == 1
     assert lib.afmpb_selftest_bounded_wait((1 << 26) + 1, ctypes.byref(e)) == 1
+
+
+_GOOD = dict(eps_in=2.0, eps_out=80.0, kappa=0.1, order=6, tol=1e-6)
+_BAD_ARGS = [
+    ("eps_in zero", dict(eps_in=0.0), b"eps_in"),
+    ("eps_out infinite", dict(eps_out=float("inf")), b"eps_in"),
+    ("kappa negative", dict(kappa=-0.1), b"kappa"),
+    ("kappa NaN", dict(kappa=float("nan")), b"kappa"),
+    ("order 1", dict(order=1), b"fmm_order"),
+    ("tol zero", dict(tol=0.0), b"tol"),
+    ("tol NaN", dict(tol=float("nan")), b"tol"),
+]
+_BAD_OPTIONS = [
+    ("negative restart", dict(restart=-1), b"negative option"),
+    ("restart above 4096", dict(restart=4097), b"restart"),
+    ("negative max_restart", dict(max_restart=-2), b"negative option"),
+    ("negative leaf cap", dict(leaf_cap=-5), b"negative option"),
+    ("max_level 21", dict(max_level=21), b"max_level"),
+    ("negative abs_tol", dict(abs_tol=-1e-9), b"abs_tol"),
+    ("NaN near_c", dict(near_c=float("nan")), b"near_c"),
+    ("precision 2", dict(precision=2), b"precision"),
+    ("charge_fmm -1", dict(charge_fmm=-1), b"charge_fmm"),
+]
+
+
+def _create(args=None, options=None, charges=None):
+    import numpy as np
+    import paper_1710_06316_gb300 as pb
+    import synthetic
+    lib = pb.load()
+    xyz, tri = synthetic.icosphere(1)
+    xyz = np.ascontiguousarray(xyz, np.float64)
+    tri = np.ascontiguousarray(tri, np.int32)
+    mesh = pb.Mesh(xyz.shape[0], tri.shape[0], xyz.ctypes.data, tri.ctypes.data, None)
+    a = dict(_GOOD, **(args or {}))
+    opt = None
+    if options is not None:
+        opt = pb.Options()
+        for k, v in options.items():
+            setattr(opt, k, v)
+    out = ctypes.c_void_p()
+    rc = lib.afmpb_create(ctypes.byref(mesh), None if charges is None else ctypes.byref(charges),
+                          a["eps_in"], a["eps_out"], a["kappa"], a["order"], a["tol"],
+                          None if opt is None else ctypes.byref(opt), ctypes.byref(out))
+    return rc, out.value, lib.afmpb_last_error(None)
+
+
+@pytest.mark.parametrize("what,args,word", _BAD_ARGS, ids=[b[0] for b in _BAD_ARGS])
+def test_invalid_scalar_arguments_are_rejected_on_the_host(what, args, word):
+    rc, handle, msg = _create(args=args)
+    assert rc == 1 and handle is None      # EINVAL, no handle, before any CUDA call
+    assert word in msg, msg
+
+
+@pytest.mark.parametrize("what,opts,word", _BAD_OPTIONS, ids=[b[0] for b in _BAD_OPTIONS])
+def test_invalid_options_are_rejected_on_the_host(what, opts, word):
+    rc, handle, msg = _create(options=opts)
+    assert rc == 1 and handle is None
+    assert word in msg, msg
+
+
+def test_invalid_charges_are_rejected_on_the_host():
+    import paper_1710_06316_gb300 as pb
+    rc, handle, msg = _create(charges=pb.Charges(3, None, None))
+    assert rc == 1 and handle is None and b"charges" in msg
+    rc, handle, msg = _create(charges=pb.Charges(-1, None, None))
+    assert rc == 1 and handle is None and b"charges" in msg
