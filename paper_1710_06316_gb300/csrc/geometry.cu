@@ -8,11 +8,13 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <memory>
 #include <mutex>
 #include <string>
 #include <thread>
 #include <vector>
 
+#include "corner_csr.h"
 #include "internal.cuh"
 
 namespace afmpb {
@@ -80,33 +82,30 @@ Err validate_mesh(const afmpb_mesh *m) {
     return make_err(AFMPB_EMESH, "triangle " + std::to_string(t) + " has zero area");
   }
   // every directed edge once, and its reverse once: closed, edge-manifold, consistently
-  // oriented.  Half-edges are bucketed by their first node (counting sort, linear in the
-  // triangle count); each bucket is sorted, so a repeated direction sits next to itself
-  // and the reverse of i -> j is a binary search in bucket j.
-  std::vector<int64_t> ptr(n + 1, 0);
-  for (int64_t e = 0; e < 3 * nt; ++e) ++ptr[(int64_t)m->tri[e] + 1];
-  for (int64_t i = 0; i < n; ++i) ptr[i + 1] += ptr[i];
-  std::vector<int32_t> dst(3 * nt);
-  {
-    std::vector<int64_t> fill(ptr.begin(), ptr.end() - 1);
-    for (int64_t t = 0; t < nt; ++t)
-      for (int k = 0; k < 3; ++k) dst[fill[m->tri[3 * t + k]]++] = m->tri[3 * t + (k + 1) % 3];
-  }
+  // oriented.  Half-edges are bucketed by their first node (parallel counting sort,
+  // linear in the triangle count); each bucket is sorted, so a repeated direction sits
+  // next to itself and the reverse of i -> j is a binary search in bucket j.
+  std::unique_ptr<int64_t[]> ptr;
+  std::unique_ptr<int32_t[]> dst;
+  corner_csr(n, nt, m->tri, corner_csr_threads(nt), ptr, dst,
+             [m](int64_t t, int k) { return m->tri[3 * t + (k + 1) % 3]; });
   // the two bucket passes run on the host cores, node ranges per thread
   std::atomic<int> dup{0}, open_edge{0};
+  int32_t *const d = dst.get();
+  const int64_t *const pp = ptr.get();
   parallel_ranges(n, [&](int64_t i0, int64_t i1) {
     for (int64_t i = i0; i < i1; ++i) {
-      std::sort(dst.begin() + ptr[i], dst.begin() + ptr[i + 1]);
-      for (int64_t k = ptr[i] + 1; k < ptr[i + 1]; ++k)
-        if (dst[k] == dst[k - 1]) dup = 1;
+      std::sort(d + pp[i], d + pp[i + 1]);
+      for (int64_t k = pp[i] + 1; k < pp[i + 1]; ++k)
+        if (d[k] == d[k - 1]) dup = 1;
     }
   });
   if (dup) return make_err(AFMPB_EMESH, "an edge is used twice in the same direction (non-manifold or mis-oriented)");
   parallel_ranges(n, [&](int64_t i0, int64_t i1) {
     for (int64_t i = i0; i < i1 && !open_edge; ++i)
-      for (int64_t k = ptr[i]; k < ptr[i + 1]; ++k) {
-        const int64_t j = dst[k];
-        if (!std::binary_search(dst.begin() + ptr[j], dst.begin() + ptr[j + 1], (int32_t)i)) open_edge = 1;
+      for (int64_t k = pp[i]; k < pp[i + 1]; ++k) {
+        const int64_t j = d[k];
+        if (!std::binary_search(d + pp[j], d + pp[j + 1], (int32_t)i)) open_edge = 1;
       }
   });
   if (open_edge) return make_err(AFMPB_EMESH, "an edge has no opposite half-edge (open surface or mis-oriented triangle)");
@@ -183,16 +182,11 @@ __global__ void k_node_patch(int64_t n, const double *__restrict__ xyz, const in
 
 Err build_geometry(afmpb_t *h, const afmpb_mesh *m) {
   const int64_t n = h->n, nt = h->nt;
-  // node -> incident triangle CSR (counting sort; triangles of a node in index order)
-  std::vector<int64_t> inc_ptr(n + 1, 0);
-  for (int64_t i = 0; i < 3 * nt; ++i) inc_ptr[m->tri[i] + 1]++;
-  for (int64_t v = 0; v < n; ++v) inc_ptr[v + 1] += inc_ptr[v];
-  std::vector<int32_t> inc_tri(3 * nt);
-  {
-    std::vector<int64_t> fill(inc_ptr.begin(), inc_ptr.end() - 1);
-    for (int64_t t = 0; t < nt; ++t)
-      for (int k = 0; k < 3; ++k) inc_tri[fill[m->tri[3 * t + k]]++] = (int32_t)t;
-  }
+  // node -> incident triangle CSR (parallel counting sort; triangles of a node in index
+  // order)
+  std::unique_ptr<int64_t[]> inc_ptr;
+  std::unique_ptr<int32_t[]> inc_tri;
+  corner_csr(n, nt, m->tri, corner_csr_threads(nt), inc_ptr, inc_tri, [](int64_t t, int) { return (int32_t)t; });
   auto &A = h->arena;
   AFMPB_TRY(A.alloc(&h->d_xyz, 3 * n, "xyz"));
   AFMPB_TRY(A.alloc(&h->d_tri, 3 * nt, "tri"));
@@ -205,8 +199,8 @@ Err build_geometry(afmpb_t *h, const afmpb_mesh *m) {
   cudaStream_t s = h->stream;
   AFMPB_CUDA(cudaMemcpyAsync(h->d_xyz, m->xyz, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, s));
   AFMPB_CUDA(cudaMemcpyAsync(h->d_tri, m->tri, sizeof(int32_t) * 3 * nt, cudaMemcpyHostToDevice, s));
-  AFMPB_CUDA(cudaMemcpyAsync(h->d_inc_ptr, inc_ptr.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, s));
-  AFMPB_CUDA(cudaMemcpyAsync(h->d_inc_tri, inc_tri.data(), sizeof(int32_t) * 3 * nt, cudaMemcpyHostToDevice, s));
+  AFMPB_CUDA(cudaMemcpyAsync(h->d_inc_ptr, inc_ptr.get(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, s));
+  AFMPB_CUDA(cudaMemcpyAsync(h->d_inc_tri, inc_tri.get(), sizeof(int32_t) * 3 * nt, cudaMemcpyHostToDevice, s));
   double *d_user = nullptr;
   if (m->normals) {
     AFMPB_TRY(A.alloc(&d_user, 3 * n, "user normals"));

@@ -329,11 +329,28 @@ Err build_tree(afmpb_t *h) {
   AFMPB_CUDA(cudaMemcpyAsync(xyz.data(), h->d_xyz, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, s));
   AFMPB_CUDA(cudaStreamSynchronize(s));
   double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
-  for (int64_t i = 0; i < n; ++i)
-    for (int d = 0; d < 3; ++d) {
-      lo[d] = std::min(lo[d], xyz[3 * i + d]);
-      hi[d] = std::max(hi[d], xyz[3 * i + d]);
-    }
+  {
+    // per-part extents on the host cores, then the extent of the parts (min / max are
+    // exact, so the result does not depend on the split)
+    std::vector<double> part_ext(6 * (size_t)host_parts(n));
+    const int parts = host_parallel(n, [&](int p, int64_t i0, int64_t i1) {
+      double l[3] = {1e300, 1e300, 1e300}, u[3] = {-1e300, -1e300, -1e300};
+      for (int64_t i = i0; i < i1; ++i)
+        for (int d = 0; d < 3; ++d) {
+          l[d] = std::min(l[d], xyz[3 * i + d]);
+          u[d] = std::max(u[d], xyz[3 * i + d]);
+        }
+      for (int d = 0; d < 3; ++d) {
+        part_ext[6 * p + d] = l[d];
+        part_ext[6 * p + 3 + d] = u[d];
+      }
+    });
+    for (int p = 0; p < parts; ++p)
+      for (int d = 0; d < 3; ++d) {
+        lo[d] = std::min(lo[d], part_ext[6 * p + d]);
+        hi[d] = std::max(hi[d], part_ext[6 * p + 3 + d]);
+      }
+  }
   double ext = 0;
   for (int d = 0; d < 3; ++d) {
     T.c0[d] = 0.5 * (lo[d] + hi[d]);
