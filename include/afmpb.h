@@ -22,6 +22,9 @@
  * Conventions
  *  - Every call returns an afmpb_status and never aborts.  On failure the handle's
  *    afmpb_last_error() string says why (thread-local string when the handle is NULL).
+ *    Host failures inside the library (a host allocation or a host thread that could
+ *    not be created) return AFMPB_ENOMEM; any other internal host failure returns
+ *    AFMPB_EINTERNAL.  A create that fails frees whatever it had built.
  *  - Lengths are in Angstrom, charges in units of e, kappa in 1/Angstrom, energies in
  *    kcal/mol.
  *  - "Caller order" is the node order of the mesh passed to afmpb_create.  The

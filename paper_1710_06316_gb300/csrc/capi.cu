@@ -28,6 +28,13 @@ afmpb_status fail(afmpb_t *h, const Err &e) {
   return e.code;
 }
 
+// Closes the try block that wraps the body of every C entry point: a host exception
+// becomes a status (ENOMEM or EINTERNAL) with its message for afmpb_last_error.
+#define AFMPB_CATCH(handle) \
+  catch (...) {             \
+    return fail((handle), current_exception_err()); \
+  }
+
 void destroy_handle(afmpb_t *h) {
   if (!h) return;
   if (h->stream) cudaStreamSynchronize(h->stream);
@@ -350,7 +357,12 @@ Err build_handle(const afmpb_mesh *mesh, const afmpb_charges *charges, double ep
   if (h->opt.near_c == 0) h->opt.near_c = 2.0;
   if (h->opt.max_level == 0) h->opt.max_level = kMaxLevel;
   if (h->opt.m2l_tol == 0) h->opt.m2l_tol = 1e-5;
-  Err e = create_impl(h, mesh, charges);
+  Err e;
+  try {
+    e = create_impl(h, mesh, charges);
+  } catch (...) {                                      // free what was built, then report
+    e = current_exception_err();
+  }
   if (!e.ok()) {
     destroy_handle(h);
     return e;
@@ -365,357 +377,389 @@ extern "C" {
 
 afmpb_status afmpb_create(const afmpb_mesh *mesh, const afmpb_charges *charges, double eps_in, double eps_out,
                           double kappa, int fmm_order, double tol, const afmpb_options *options, afmpb_t **out) {
-  if (!out) return fail(nullptr, make_err(AFMPB_EINVAL, "out is NULL"));
-  *out = nullptr;
-  Err e = check_params(mesh, eps_in, eps_out, kappa, fmm_order, tol, options);
-  if (!e.ok()) return fail(nullptr, e);
-  if (charges && charges->n > 0 && (!charges->xyz || !charges->q))
-    return fail(nullptr, make_err(AFMPB_EINVAL, "charges->xyz and charges->q are required when charges->n > 0"));
-  if (charges && charges->n < 0) return fail(nullptr, make_err(AFMPB_EINVAL, "charges->n < 0"));
-  e = validate_mesh(mesh);
-  if (!e.ok()) return fail(nullptr, e);
-  const int prec = options ? options->precision : 0;
-  const bool tune = options && options->leaf_cap == AFMPB_LEAF_CAP_AUTO;
-  int cap = (options && options->leaf_cap > 0) ? options->leaf_cap : default_leaf_cap(prec);
-  int cached = 0;
-  if (tune) {
-    cached = autotune_cached_cap(prec, fmm_order, kappa, mesh->n_nodes);
-    if (cached) cap = cached;
-  }
-  afmpb_t *h = nullptr;
-  e = build_handle(mesh, charges, eps_in, eps_out, kappa, fmm_order, tol, options, cap, &h);
-  if (!e.ok()) return fail(nullptr, e);
-  if (tune && !cached) {
-    afmpb_autotune_report rep{};
-    e = autotune_leaf_cap(h, &rep);
-    if (!e.ok()) {
-      destroy_handle(h);
-      return fail(nullptr, e);
+  try {
+    if (!out) return fail(nullptr, make_err(AFMPB_EINVAL, "out is NULL"));
+    *out = nullptr;
+    Err e = check_params(mesh, eps_in, eps_out, kappa, fmm_order, tol, options);
+    if (!e.ok()) return fail(nullptr, e);
+    if (charges && charges->n > 0 && (!charges->xyz || !charges->q))
+      return fail(nullptr, make_err(AFMPB_EINVAL, "charges->xyz and charges->q are required when charges->n > 0"));
+    if (charges && charges->n < 0) return fail(nullptr, make_err(AFMPB_EINVAL, "charges->n < 0"));
+    e = validate_mesh(mesh);
+    if (!e.ok()) return fail(nullptr, e);
+    const int prec = options ? options->precision : 0;
+    const bool tune = options && options->leaf_cap == AFMPB_LEAF_CAP_AUTO;
+    int cap = (options && options->leaf_cap > 0) ? options->leaf_cap : default_leaf_cap(prec);
+    int cached = 0;
+    if (tune) {
+      cached = autotune_cached_cap(prec, fmm_order, kappa, mesh->n_nodes);
+      if (cached) cap = cached;
     }
-    if (rep.best_cap != cap && rep.predicted_best_ms < 0.97 * rep.predicted_start_ms) {
-      destroy_handle(h);
-      h = nullptr;
-      e = build_handle(mesh, charges, eps_in, eps_out, kappa, fmm_order, tol, options, rep.best_cap, &h);
-      if (!e.ok()) return fail(nullptr, e);
+    afmpb_t *h = nullptr;
+    e = build_handle(mesh, charges, eps_in, eps_out, kappa, fmm_order, tol, options, cap, &h);
+    if (!e.ok()) return fail(nullptr, e);
+    if (tune && !cached) {
+      afmpb_autotune_report rep{};
+      try {
+        e = autotune_leaf_cap(h, &rep);
+      } catch (...) {
+        e = current_exception_err();
+      }
+      if (!e.ok()) {
+        destroy_handle(h);
+        return fail(nullptr, e);
+      }
+      if (rep.best_cap != cap && rep.predicted_best_ms < 0.97 * rep.predicted_start_ms) {
+        destroy_handle(h);
+        h = nullptr;
+        e = build_handle(mesh, charges, eps_in, eps_out, kappa, fmm_order, tol, options, rep.best_cap, &h);
+        if (!e.ok()) return fail(nullptr, e);
+      }
+      h->autotuned = true;
+      h->tune = rep;
     }
-    h->autotuned = true;
-    h->tune = rep;
-  }
-  *out = h;
-  return AFMPB_OK;
+    *out = h;
+    return AFMPB_OK;
+  } AFMPB_CATCH(nullptr)
 }
 
 afmpb_status afmpb_matvec_parts(afmpb_t *h, const float *x, float *y, int parts) {
-  if (!h) return fail(nullptr, make_err(AFMPB_EINVAL, "handle is NULL"));
-  if (!x || !y) return fail(h, make_err(AFMPB_EINVAL, "x and y must be device pointers"));
-  if (x == y) return fail(h, make_err(AFMPB_EINVAL, "x and y must not overlap"));
-  if (parts <= 0 || parts > AFMPB_PART_ALL) return fail(h, make_err(AFMPB_EINVAL, "parts must be a non-empty AFMPB_PART_* mask"));
-  Err e = product_io(h, parts, x, y);
-  return e.ok() ? AFMPB_OK : fail(h, e);
+  try {
+    if (!h) return fail(nullptr, make_err(AFMPB_EINVAL, "handle is NULL"));
+    if (!x || !y) return fail(h, make_err(AFMPB_EINVAL, "x and y must be device pointers"));
+    if (x == y) return fail(h, make_err(AFMPB_EINVAL, "x and y must not overlap"));
+    if (parts <= 0 || parts > AFMPB_PART_ALL) return fail(h, make_err(AFMPB_EINVAL, "parts must be a non-empty AFMPB_PART_* mask"));
+    Err e = product_io(h, parts, x, y);
+    return e.ok() ? AFMPB_OK : fail(h, e);
+  } AFMPB_CATCH(h)
 }
 
 afmpb_status afmpb_matvec(afmpb_t *h, const float *x, float *y) { return afmpb_matvec_parts(h, x, y, AFMPB_PART_ALL); }
 
 afmpb_status afmpb_matvec_host(afmpb_t *h, const float *x, float *y) {
-  if (!h) return fail(nullptr, make_err(AFMPB_EINVAL, "handle is NULL"));
-  if (!x || !y) return fail(h, make_err(AFMPB_EINVAL, "x and y must be host pointers"));
-  const size_t bytes = sizeof(float) * 2 * h->n;
-  Err e;
-  if (!h->d_xhost_stage) {
-    e = h->arena.alloc(&h->d_xhost_stage, 2 * h->n, "host stage x");
-    if (e.ok()) e = h->arena.alloc(&h->d_yhost_stage, 2 * h->n, "host stage y");
+  try {
+    if (!h) return fail(nullptr, make_err(AFMPB_EINVAL, "handle is NULL"));
+    if (!x || !y) return fail(h, make_err(AFMPB_EINVAL, "x and y must be host pointers"));
+    const size_t bytes = sizeof(float) * 2 * h->n;
+    Err e;
+    if (!h->d_xhost_stage) {
+      e = h->arena.alloc(&h->d_xhost_stage, 2 * h->n, "host stage x");
+      if (e.ok()) e = h->arena.alloc(&h->d_yhost_stage, 2 * h->n, "host stage y");
+      if (!e.ok()) return fail(h, e);
+    }
+    cudaError_t ce = cudaMemcpyAsync(h->d_xhost_stage, x, bytes, cudaMemcpyHostToDevice, h->stream);
+    if (ce != cudaSuccess) return fail(h, make_err(AFMPB_ECUDA, std::string("H2D: ") + cudaGetErrorString(ce)));
+    e = product_io(h, AFMPB_PART_ALL, h->d_xhost_stage, h->d_yhost_stage);
     if (!e.ok()) return fail(h, e);
-  }
-  cudaError_t ce = cudaMemcpyAsync(h->d_xhost_stage, x, bytes, cudaMemcpyHostToDevice, h->stream);
-  if (ce != cudaSuccess) return fail(h, make_err(AFMPB_ECUDA, std::string("H2D: ") + cudaGetErrorString(ce)));
-  e = product_io(h, AFMPB_PART_ALL, h->d_xhost_stage, h->d_yhost_stage);
-  if (!e.ok()) return fail(h, e);
-  ce = cudaMemcpyAsync(y, h->d_yhost_stage, bytes, cudaMemcpyDeviceToHost, h->stream);
-  if (ce == cudaSuccess) ce = cudaStreamSynchronize(h->stream);
-  if (ce != cudaSuccess) return fail(h, make_err(AFMPB_ECUDA, std::string("D2H: ") + cudaGetErrorString(ce)));
-  return AFMPB_OK;
+    ce = cudaMemcpyAsync(y, h->d_yhost_stage, bytes, cudaMemcpyDeviceToHost, h->stream);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(h->stream);
+    if (ce != cudaSuccess) return fail(h, make_err(AFMPB_ECUDA, std::string("D2H: ") + cudaGetErrorString(ce)));
+    return AFMPB_OK;
+  } AFMPB_CATCH(h)
 }
 
 afmpb_status afmpb_solve(afmpb_t *h, double *f, double *hh, afmpb_solve_info *info) {
-  if (!h) return fail(nullptr, make_err(AFMPB_EINVAL, "handle is NULL"));
-  if (h->natoms == 0) return fail(h, make_err(AFMPB_ESTATE, "the handle was created without charges"));
-  Err e = run_solve(h, info);
-  if (!e.ok() && e.code != AFMPB_ENOCONV) return fail(h, e);
-  if (f || hh) {
-    std::vector<double> xs(2 * h->n);
-    std::vector<int32_t> perm(h->n);
-    cudaError_t ce = cudaMemcpyAsync(xs.data(), h->d_sol, sizeof(double) * 2 * h->n, cudaMemcpyDeviceToHost, h->stream);
-    if (ce == cudaSuccess)
-      ce = cudaMemcpyAsync(perm.data(), h->d_perm, sizeof(int32_t) * h->n, cudaMemcpyDeviceToHost, h->stream);
-    if (ce == cudaSuccess) ce = cudaStreamSynchronize(h->stream);
-    if (ce != cudaSuccess) return fail(h, make_err(AFMPB_ECUDA, cudaGetErrorString(ce)));
-    for (int64_t p = 0; p < h->n; ++p) {
-      if (f) f[perm[p]] = xs[p];
-      if (hh) hh[perm[p]] = xs[h->n + p];
+  try {
+    if (!h) return fail(nullptr, make_err(AFMPB_EINVAL, "handle is NULL"));
+    if (h->natoms == 0) return fail(h, make_err(AFMPB_ESTATE, "the handle was created without charges"));
+    Err e = run_solve(h, info);
+    if (!e.ok() && e.code != AFMPB_ENOCONV) return fail(h, e);
+    if (f || hh) {
+      std::vector<double> xs(2 * h->n);
+      std::vector<int32_t> perm(h->n);
+      cudaError_t ce = cudaMemcpyAsync(xs.data(), h->d_sol, sizeof(double) * 2 * h->n, cudaMemcpyDeviceToHost, h->stream);
+      if (ce == cudaSuccess)
+        ce = cudaMemcpyAsync(perm.data(), h->d_perm, sizeof(int32_t) * h->n, cudaMemcpyDeviceToHost, h->stream);
+      if (ce == cudaSuccess) ce = cudaStreamSynchronize(h->stream);
+      if (ce != cudaSuccess) return fail(h, make_err(AFMPB_ECUDA, cudaGetErrorString(ce)));
+      for (int64_t p = 0; p < h->n; ++p) {
+        if (f) f[perm[p]] = xs[p];
+        if (hh) hh[perm[p]] = xs[h->n + p];
+      }
     }
-  }
-  return e.ok() ? AFMPB_OK : fail(h, e);
+    return e.ok() ? AFMPB_OK : fail(h, e);
+  } AFMPB_CATCH(h)
 }
 
 afmpb_status afmpb_energy(afmpb_t *h, double *E) {
-  if (!h || !E) return fail(h, make_err(AFMPB_EINVAL, "handle and output are required"));
-  Err e = run_energy(h, E);
-  return e.ok() ? AFMPB_OK : fail(h, e);
+  try {
+    if (!h || !E) return fail(h, make_err(AFMPB_EINVAL, "handle and output are required"));
+    Err e = run_energy(h, E);
+    return e.ok() ? AFMPB_OK : fail(h, e);
+  } AFMPB_CATCH(h)
 }
 
 afmpb_status afmpb_energy_noalloc(afmpb_t *h, double *E) {
-  if (!h || !E) return fail(h, make_err(AFMPB_EINVAL, "handle and output are required"));
-  Err e = run_energy_noalloc(h, E);
-  return e.ok() ? AFMPB_OK : fail(h, e);
+  try {
+    if (!h || !E) return fail(h, make_err(AFMPB_EINVAL, "handle and output are required"));
+    Err e = run_energy_noalloc(h, E);
+    return e.ok() ? AFMPB_OK : fail(h, e);
+  } AFMPB_CATCH(h)
 }
 
 afmpb_status afmpb_rhs(afmpb_t *h, double *b) {
-  if (!h || !b) return fail(h, make_err(AFMPB_EINVAL, "handle and output are required"));
-  std::vector<double> bs(2 * h->n);
-  std::vector<int32_t> perm(h->n);
-  cudaError_t ce = cudaMemcpyAsync(bs.data(), h->d_b, sizeof(double) * 2 * h->n, cudaMemcpyDeviceToHost, h->stream);
-  if (ce == cudaSuccess) ce = cudaMemcpyAsync(perm.data(), h->d_perm, sizeof(int32_t) * h->n, cudaMemcpyDeviceToHost, h->stream);
-  if (ce == cudaSuccess) ce = cudaStreamSynchronize(h->stream);
-  if (ce != cudaSuccess) return fail(h, make_err(AFMPB_ECUDA, cudaGetErrorString(ce)));
-  for (int64_t p = 0; p < h->n; ++p) {
-    b[perm[p]] = bs[p];
-    b[h->n + perm[p]] = bs[h->n + p];
-  }
-  return AFMPB_OK;
+  try {
+    if (!h || !b) return fail(h, make_err(AFMPB_EINVAL, "handle and output are required"));
+    std::vector<double> bs(2 * h->n);
+    std::vector<int32_t> perm(h->n);
+    cudaError_t ce = cudaMemcpyAsync(bs.data(), h->d_b, sizeof(double) * 2 * h->n, cudaMemcpyDeviceToHost, h->stream);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(perm.data(), h->d_perm, sizeof(int32_t) * h->n, cudaMemcpyDeviceToHost, h->stream);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(h->stream);
+    if (ce != cudaSuccess) return fail(h, make_err(AFMPB_ECUDA, cudaGetErrorString(ce)));
+    for (int64_t p = 0; p < h->n; ++p) {
+      b[perm[p]] = bs[p];
+      b[h->n + perm[p]] = bs[h->n + p];
+    }
+    return AFMPB_OK;
+  } AFMPB_CATCH(h)
 }
 
 afmpb_status afmpb_get_geometry(afmpb_t *h, double *area, double *normals, double *rho) {
-  if (!h) return fail(nullptr, make_err(AFMPB_EINVAL, "handle is NULL"));
-  cudaError_t ce = cudaSuccess;
-  if (area) ce = cudaMemcpyAsync(area, h->d_area64, sizeof(double) * h->n, cudaMemcpyDeviceToHost, h->stream);
-  if (ce == cudaSuccess && normals)
-    ce = cudaMemcpyAsync(normals, h->d_nrm64, sizeof(double) * 3 * h->n, cudaMemcpyDeviceToHost, h->stream);
-  if (ce == cudaSuccess && rho) ce = cudaMemcpyAsync(rho, h->d_rho64, sizeof(double) * h->n, cudaMemcpyDeviceToHost, h->stream);
-  if (ce == cudaSuccess) ce = cudaStreamSynchronize(h->stream);
-  if (ce != cudaSuccess) return fail(h, make_err(AFMPB_ECUDA, cudaGetErrorString(ce)));
-  return AFMPB_OK;
+  try {
+    if (!h) return fail(nullptr, make_err(AFMPB_EINVAL, "handle is NULL"));
+    cudaError_t ce = cudaSuccess;
+    if (area) ce = cudaMemcpyAsync(area, h->d_area64, sizeof(double) * h->n, cudaMemcpyDeviceToHost, h->stream);
+    if (ce == cudaSuccess && normals)
+      ce = cudaMemcpyAsync(normals, h->d_nrm64, sizeof(double) * 3 * h->n, cudaMemcpyDeviceToHost, h->stream);
+    if (ce == cudaSuccess && rho) ce = cudaMemcpyAsync(rho, h->d_rho64, sizeof(double) * h->n, cudaMemcpyDeviceToHost, h->stream);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(h->stream);
+    if (ce != cudaSuccess) return fail(h, make_err(AFMPB_ECUDA, cudaGetErrorString(ce)));
+    return AFMPB_OK;
+  } AFMPB_CATCH(h)
 }
 
 afmpb_status afmpb_get_near(afmpb_t *h, int64_t *rowptr, int32_t *col, float *coef, uint8_t *whole) {
-  if (!h) return fail(nullptr, make_err(AFMPB_EINVAL, "handle is NULL"));
-  const int64_t n = h->n;
-  std::vector<int64_t> ptr(n + 1);
-  std::vector<int32_t> c(h->nnz), perm(n);
-  std::vector<float4> cf(h->nnz);
-  std::vector<uint8_t> fl(h->nnz);
-  cudaError_t ce = cudaMemcpyAsync(ptr.data(), h->d_near_ptr, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost, h->stream);
-  if (ce == cudaSuccess) ce = cudaMemcpyAsync(c.data(), h->d_near_col, sizeof(int32_t) * h->nnz, cudaMemcpyDeviceToHost, h->stream);
-  if (ce == cudaSuccess) ce = cudaMemcpyAsync(cf.data(), h->d_near_coef, sizeof(float4) * h->nnz, cudaMemcpyDeviceToHost, h->stream);
-  if (ce == cudaSuccess) ce = cudaMemcpyAsync(fl.data(), h->d_near_full, h->nnz, cudaMemcpyDeviceToHost, h->stream);
-  if (ce == cudaSuccess) ce = cudaMemcpyAsync(perm.data(), h->d_perm, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, h->stream);
-  if (ce == cudaSuccess) ce = cudaStreamSynchronize(h->stream);
-  if (ce != cudaSuccess) return fail(h, make_err(AFMPB_ECUDA, cudaGetErrorString(ce)));
-  std::vector<int64_t> iperm(n);
-  for (int64_t p = 0; p < n; ++p) iperm[perm[p]] = p;
-  int64_t k = 0;
-  if (rowptr) rowptr[0] = 0;
-  for (int64_t o = 0; o < n; ++o) {
-    const int64_t p = iperm[o];
-    for (int64_t j = ptr[p]; j < ptr[p + 1]; ++j, ++k) {
-      if (col) col[k] = perm[c[j]];
-      if (whole) whole[k] = fl[j];
-      if (coef) {
-        coef[4 * k] = cf[j].x;
-        coef[4 * k + 1] = cf[j].y;
-        coef[4 * k + 2] = cf[j].z;
-        coef[4 * k + 3] = cf[j].w;
+  try {
+    if (!h) return fail(nullptr, make_err(AFMPB_EINVAL, "handle is NULL"));
+    const int64_t n = h->n;
+    std::vector<int64_t> ptr(n + 1);
+    std::vector<int32_t> c(h->nnz), perm(n);
+    std::vector<float4> cf(h->nnz);
+    std::vector<uint8_t> fl(h->nnz);
+    cudaError_t ce = cudaMemcpyAsync(ptr.data(), h->d_near_ptr, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost, h->stream);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(c.data(), h->d_near_col, sizeof(int32_t) * h->nnz, cudaMemcpyDeviceToHost, h->stream);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(cf.data(), h->d_near_coef, sizeof(float4) * h->nnz, cudaMemcpyDeviceToHost, h->stream);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(fl.data(), h->d_near_full, h->nnz, cudaMemcpyDeviceToHost, h->stream);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(perm.data(), h->d_perm, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, h->stream);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(h->stream);
+    if (ce != cudaSuccess) return fail(h, make_err(AFMPB_ECUDA, cudaGetErrorString(ce)));
+    std::vector<int64_t> iperm(n);
+    for (int64_t p = 0; p < n; ++p) iperm[perm[p]] = p;
+    int64_t k = 0;
+    if (rowptr) rowptr[0] = 0;
+    for (int64_t o = 0; o < n; ++o) {
+      const int64_t p = iperm[o];
+      for (int64_t j = ptr[p]; j < ptr[p + 1]; ++j, ++k) {
+        if (col) col[k] = perm[c[j]];
+        if (whole) whole[k] = fl[j];
+        if (coef) {
+          coef[4 * k] = cf[j].x;
+          coef[4 * k + 1] = cf[j].y;
+          coef[4 * k + 2] = cf[j].z;
+          coef[4 * k + 3] = cf[j].w;
+        }
       }
+      if (rowptr) rowptr[o + 1] = k;
     }
-    if (rowptr) rowptr[o + 1] = k;
-  }
-  return AFMPB_OK;
+    return AFMPB_OK;
+  } AFMPB_CATCH(h)
 }
 
 afmpb_status afmpb_get_tree(afmpb_t *h, int32_t *box_level, int32_t *box_anchor, int32_t *box_range,
                             int32_t *box_parent, int32_t *perm, int64_t *u_ptr, int32_t *u_idx, int64_t *v_ptr,
                             int32_t *v_idx, int64_t *w_ptr, int32_t *w_idx, int64_t *x_ptr, int32_t *x_idx) {
-  if (!h) return fail(nullptr, make_err(AFMPB_EINVAL, "handle is NULL"));
-  const auto &T = h->shape;
-  const int nb = T.nbox;
-  cudaStream_t s = h->stream;
-  cudaError_t ce = cudaSuccess;
-  auto cp = [&](void *dst, const void *src, size_t bytes) {
-    if (dst && ce == cudaSuccess && bytes) ce = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s);
-  };
-  cp(box_level, h->d_box_level, sizeof(int32_t) * nb);
-  cp(box_parent, h->d_box_parent, sizeof(int32_t) * nb);
-  cp(perm, h->d_perm, sizeof(int32_t) * h->n);
-  cp(u_ptr, h->d_u_ptr, sizeof(int64_t) * (nb + 1));
-  cp(u_idx, h->d_u_idx, sizeof(int32_t) * T.n_u);
-  cp(v_ptr, h->d_v_ptr, sizeof(int64_t) * (nb + 1));
-  cp(v_idx, h->d_v_idx, sizeof(int32_t) * T.n_v);
-  cp(w_ptr, h->d_w_ptr, sizeof(int64_t) * (nb + 1));
-  cp(w_idx, h->d_w_idx, sizeof(int32_t) * T.n_w);
-  cp(x_ptr, h->d_x_ptr, sizeof(int64_t) * (nb + 1));
-  cp(x_idx, h->d_x_idx, sizeof(int32_t) * T.n_x);
-  std::vector<int4> anc;
-  std::vector<int32_t> beg, end;
-  if (box_anchor) {
-    anc.resize(nb);
-    cp(anc.data(), h->d_box_anchor, sizeof(int4) * nb);
-  }
-  if (box_range) {
-    beg.resize(nb);
-    end.resize(nb);
-    cp(beg.data(), h->d_box_begin, sizeof(int32_t) * nb);
-    cp(end.data(), h->d_box_end, sizeof(int32_t) * nb);
-  }
-  if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
-  if (ce != cudaSuccess) return fail(h, make_err(AFMPB_ECUDA, cudaGetErrorString(ce)));
-  for (int b = 0; b < nb; ++b) {
+  try {
+    if (!h) return fail(nullptr, make_err(AFMPB_EINVAL, "handle is NULL"));
+    const auto &T = h->shape;
+    const int nb = T.nbox;
+    cudaStream_t s = h->stream;
+    cudaError_t ce = cudaSuccess;
+    auto cp = [&](void *dst, const void *src, size_t bytes) {
+      if (dst && ce == cudaSuccess && bytes) ce = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s);
+    };
+    cp(box_level, h->d_box_level, sizeof(int32_t) * nb);
+    cp(box_parent, h->d_box_parent, sizeof(int32_t) * nb);
+    cp(perm, h->d_perm, sizeof(int32_t) * h->n);
+    cp(u_ptr, h->d_u_ptr, sizeof(int64_t) * (nb + 1));
+    cp(u_idx, h->d_u_idx, sizeof(int32_t) * T.n_u);
+    cp(v_ptr, h->d_v_ptr, sizeof(int64_t) * (nb + 1));
+    cp(v_idx, h->d_v_idx, sizeof(int32_t) * T.n_v);
+    cp(w_ptr, h->d_w_ptr, sizeof(int64_t) * (nb + 1));
+    cp(w_idx, h->d_w_idx, sizeof(int32_t) * T.n_w);
+    cp(x_ptr, h->d_x_ptr, sizeof(int64_t) * (nb + 1));
+    cp(x_idx, h->d_x_idx, sizeof(int32_t) * T.n_x);
+    std::vector<int4> anc;
+    std::vector<int32_t> beg, end;
     if (box_anchor) {
-      box_anchor[3 * b] = anc[b].x;
-      box_anchor[3 * b + 1] = anc[b].y;
-      box_anchor[3 * b + 2] = anc[b].z;
+      anc.resize(nb);
+      cp(anc.data(), h->d_box_anchor, sizeof(int4) * nb);
     }
     if (box_range) {
-      box_range[2 * b] = beg[b];
-      box_range[2 * b + 1] = end[b];
+      beg.resize(nb);
+      end.resize(nb);
+      cp(beg.data(), h->d_box_begin, sizeof(int32_t) * nb);
+      cp(end.data(), h->d_box_end, sizeof(int32_t) * nb);
     }
-  }
-  return AFMPB_OK;
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+    if (ce != cudaSuccess) return fail(h, make_err(AFMPB_ECUDA, cudaGetErrorString(ce)));
+    for (int b = 0; b < nb; ++b) {
+      if (box_anchor) {
+        box_anchor[3 * b] = anc[b].x;
+        box_anchor[3 * b + 1] = anc[b].y;
+        box_anchor[3 * b + 2] = anc[b].z;
+      }
+      if (box_range) {
+        box_range[2 * b] = beg[b];
+        box_range[2 * b + 1] = end[b];
+      }
+    }
+    return AFMPB_OK;
+  } AFMPB_CATCH(h)
 }
 
 afmpb_status afmpb_get_info(const afmpb_t *h, afmpb_info *info) {
-  if (!h || !info) return fail(nullptr, make_err(AFMPB_EINVAL, "handle and info are required"));
-  std::memset(info, 0, sizeof(*info));
-  const auto &T = h->shape;
-  info->n_nodes = h->n;
-  info->n_tris = h->nt;
-  info->n_atoms = h->natoms;
-  info->n_boxes = T.nbox;
-  info->n_leaves = T.nleaf;
-  info->n_levels = T.nlevel;
-  info->nnz_near = h->nnz;
-  info->n_list_u = T.n_u;
-  info->n_list_v = T.n_v;
-  info->n_list_w = T.n_w;
-  info->n_list_x = T.n_x;
-  info->n_p2p_pairs = T.n_p2p_pairs;
-  info->n_m2l_pairs = h->n_m2l_pairs;
-  info->order = h->order;
-  info->precision = h->opt.precision;
-  info->device_bytes = (int64_t)h->arena.bytes;
-  for (int d = 0; d < 3; ++d) info->root_center[d] = T.c0[d];
-  info->root_half_width = T.w0;
-  for (int i = 0; i < 6; ++i) info->ms_create[i] = h->ms_create[i];
-  info->device_bytes_peak = (int64_t)h->arena.peak;
-  info->leaf_cap = h->opt.leaf_cap;
-  info->autotuned = h->autotuned ? 1 : 0;
-  info->m2l_rank = h->m2l_rank;
-  info->m2l_tables = h->m2l_ntables;
-  if (h->cf) {
-    // the charge FMM is built after the handle's own setup scratch is released
-    info->charge_fmm = 1;
-    info->charge_fmm_boxes = h->cf->shape.nbox;
-    info->device_bytes += (int64_t)h->cf->arena.bytes;
-    info->device_bytes_peak = std::max(info->device_bytes_peak, (int64_t)(h->arena.bytes + h->cf->arena.peak));
-  }
-  return AFMPB_OK;
+  try {
+    if (!h || !info) return fail(nullptr, make_err(AFMPB_EINVAL, "handle and info are required"));
+    std::memset(info, 0, sizeof(*info));
+    const auto &T = h->shape;
+    info->n_nodes = h->n;
+    info->n_tris = h->nt;
+    info->n_atoms = h->natoms;
+    info->n_boxes = T.nbox;
+    info->n_leaves = T.nleaf;
+    info->n_levels = T.nlevel;
+    info->nnz_near = h->nnz;
+    info->n_list_u = T.n_u;
+    info->n_list_v = T.n_v;
+    info->n_list_w = T.n_w;
+    info->n_list_x = T.n_x;
+    info->n_p2p_pairs = T.n_p2p_pairs;
+    info->n_m2l_pairs = h->n_m2l_pairs;
+    info->order = h->order;
+    info->precision = h->opt.precision;
+    info->device_bytes = (int64_t)h->arena.bytes;
+    for (int d = 0; d < 3; ++d) info->root_center[d] = T.c0[d];
+    info->root_half_width = T.w0;
+    for (int i = 0; i < 6; ++i) info->ms_create[i] = h->ms_create[i];
+    info->device_bytes_peak = (int64_t)h->arena.peak;
+    info->leaf_cap = h->opt.leaf_cap;
+    info->autotuned = h->autotuned ? 1 : 0;
+    info->m2l_rank = h->m2l_rank;
+    info->m2l_tables = h->m2l_ntables;
+    if (h->cf) {
+      // the charge FMM is built after the handle's own setup scratch is released
+      info->charge_fmm = 1;
+      info->charge_fmm_boxes = h->cf->shape.nbox;
+      info->device_bytes += (int64_t)h->cf->arena.bytes;
+      info->device_bytes_peak = std::max(info->device_bytes_peak, (int64_t)(h->arena.bytes + h->cf->arena.peak));
+    }
+    return AFMPB_OK;
+  } AFMPB_CATCH(nullptr)
 }
 
 afmpb_status afmpb_get_autotune(const afmpb_t *h, afmpb_autotune_report *r) {
-  if (!h || !r) return AFMPB_EINVAL;
-  if (!h->autotuned) return AFMPB_ESTATE;
-  *r = h->tune;
-  return AFMPB_OK;
+  try {
+    if (!h || !r) return AFMPB_EINVAL;
+    if (!h->autotuned) return AFMPB_ESTATE;
+    *r = h->tune;
+    return AFMPB_OK;
+  } AFMPB_CATCH(nullptr)
 }
 
 afmpb_status afmpb_profile_product(afmpb_t *h, int reps, void *flush, size_t flush_bytes, afmpb_profile *out) {
-  if (!h || !out || reps <= 0) return fail(h, make_err(AFMPB_EINVAL, "handle, reps > 0 and out are required"));
-  std::memset(out, 0, sizeof(*out));
-  cudaStream_t s = h->stream;
-  if (!h->d_prof_x) {
-    Err e = h->arena.alloc(&h->d_prof_x, 2 * h->n, "profile x");
-    if (e.ok()) e = h->arena.alloc(&h->d_prof_y, 2 * h->n, "profile y");
-    if (!e.ok()) return fail(h, e);
-  }
-  // input: the last product result, in caller order (contents do not change timing)
-  {
-    Err e = enqueue_scatter(h, s, h->d_prof_x);
-    if (!e.ok()) return fail(h, e);
-  }
-  std::vector<double> acc;
-  std::vector<std::string> names;
-  std::vector<int> launches;
-  for (int r = 0; r < reps; ++r) {
-    if (flush && flush_bytes) cudaMemsetAsync(flush, r & 0xff, flush_bytes, s);
-    StageTimer tm;
-    tm.s = s;
-    cudaEvent_t start = nullptr;
-    cudaEventCreate(&start);
-    cudaEventRecord(start, s);
-    Err e = enqueue_gather(h, s, h->d_prof_x);
-    if (e.ok()) tm.mark("gather", 1);
-    if (e.ok()) e = enqueue_far(h, s, &tm);
-    if (e.ok()) e = enqueue_p2p(h, s);
-    if (e.ok()) tm.mark("p2p", 1);
-    if (e.ok()) e = enqueue_combine(h, s, AFMPB_PART_ALL);
-    if (e.ok()) tm.mark("combine", 1);
-    if (e.ok()) e = enqueue_scatter(h, s, h->d_prof_y);
-    if (e.ok()) tm.mark("scatter", 1);
-    cudaError_t ce = cudaStreamSynchronize(s);
-    if (!e.ok() || ce != cudaSuccess) {
+  try {
+    if (!h || !out || reps <= 0) return fail(h, make_err(AFMPB_EINVAL, "handle, reps > 0 and out are required"));
+    std::memset(out, 0, sizeof(*out));
+    cudaStream_t s = h->stream;
+    if (!h->d_prof_x) {
+      Err e = h->arena.alloc(&h->d_prof_x, 2 * h->n, "profile x");
+      if (e.ok()) e = h->arena.alloc(&h->d_prof_y, 2 * h->n, "profile y");
+      if (!e.ok()) return fail(h, e);
+    }
+    // input: the last product result, in caller order (contents do not change timing)
+    {
+      Err e = enqueue_scatter(h, s, h->d_prof_x);
+      if (!e.ok()) return fail(h, e);
+    }
+    std::vector<double> acc;
+    std::vector<std::string> names;
+    std::vector<int> launches;
+    for (int r = 0; r < reps; ++r) {
+      if (flush && flush_bytes) cudaMemsetAsync(flush, r & 0xff, flush_bytes, s);
+      StageTimer tm;
+      tm.s = s;
+      cudaEvent_t start = nullptr;
+      cudaEventCreate(&start);
+      cudaEventRecord(start, s);
+      Err e = enqueue_gather(h, s, h->d_prof_x);
+      if (e.ok()) tm.mark("gather", 1);
+      if (e.ok()) e = enqueue_far(h, s, &tm);
+      if (e.ok()) e = enqueue_p2p(h, s);
+      if (e.ok()) tm.mark("p2p", 1);
+      if (e.ok()) e = enqueue_combine(h, s, AFMPB_PART_ALL);
+      if (e.ok()) tm.mark("combine", 1);
+      if (e.ok()) e = enqueue_scatter(h, s, h->d_prof_y);
+      if (e.ok()) tm.mark("scatter", 1);
+      cudaError_t ce = cudaStreamSynchronize(s);
+      if (!e.ok() || ce != cudaSuccess) {
+        cudaEventDestroy(start);
+        return fail(h, e.ok() ? make_err(AFMPB_ECUDA, cudaGetErrorString(ce)) : e);
+      }
+      if (r == 0) {
+        names = tm.names;
+        launches = tm.launches;
+        acc.assign(names.size(), 0.0);
+      }
+      cudaEvent_t prev = start;
+      for (size_t i = 0; i < tm.ends.size() && i < acc.size(); ++i) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, prev, tm.ends[i]);
+        acc[i] += ms;
+        prev = tm.ends[i];
+      }
       cudaEventDestroy(start);
-      return fail(h, e.ok() ? make_err(AFMPB_ECUDA, cudaGetErrorString(ce)) : e);
     }
-    if (r == 0) {
-      names = tm.names;
-      launches = tm.launches;
-      acc.assign(names.size(), 0.0);
+    out->n_stages = (int)std::min<size_t>(names.size(), AFMPB_MAX_STAGES);
+    int kernels = 0;
+    for (int i = 0; i < out->n_stages; ++i) {
+      std::strncpy(out->name[i], names[i].c_str(), 15);
+      out->ms[i] = acc[i] / reps;
+      out->launches[i] = launches[i];
+      kernels += launches[i];
     }
-    cudaEvent_t prev = start;
-    for (size_t i = 0; i < tm.ends.size() && i < acc.size(); ++i) {
+    out->kernels_per_product = kernels;
+    // graph replays (the path afmpb_matvec takes), same flush between repetitions
+    cudaEvent_t a = nullptr, b = nullptr;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    double tot = 0.0;
+    for (int r = 0; r < reps; ++r) {
+      if (flush && flush_bytes) cudaMemsetAsync(flush, r & 0xff, flush_bytes, s);
+      cudaEventRecord(a, s);
+      Err e = product_sorted(h, s, AFMPB_PART_ALL);
+      cudaEventRecord(b, s);
+      if (!e.ok()) {
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+        return fail(h, e);
+      }
+      cudaEventSynchronize(b);
       float ms = 0.f;
-      cudaEventElapsedTime(&ms, prev, tm.ends[i]);
-      acc[i] += ms;
-      prev = tm.ends[i];
+      cudaEventElapsedTime(&ms, a, b);
+      tot += ms;
     }
-    cudaEventDestroy(start);
-  }
-  out->n_stages = (int)std::min<size_t>(names.size(), AFMPB_MAX_STAGES);
-  int kernels = 0;
-  for (int i = 0; i < out->n_stages; ++i) {
-    std::strncpy(out->name[i], names[i].c_str(), 15);
-    out->ms[i] = acc[i] / reps;
-    out->launches[i] = launches[i];
-    kernels += launches[i];
-  }
-  out->kernels_per_product = kernels;
-  // graph replays (the path afmpb_matvec takes), same flush between repetitions
-  cudaEvent_t a = nullptr, b = nullptr;
-  cudaEventCreate(&a);
-  cudaEventCreate(&b);
-  double tot = 0.0;
-  for (int r = 0; r < reps; ++r) {
-    if (flush && flush_bytes) cudaMemsetAsync(flush, r & 0xff, flush_bytes, s);
-    cudaEventRecord(a, s);
-    Err e = product_sorted(h, s, AFMPB_PART_ALL);
-    cudaEventRecord(b, s);
-    if (!e.ok()) {
-      cudaEventDestroy(a);
-      cudaEventDestroy(b);
-      return fail(h, e);
-    }
-    cudaEventSynchronize(b);
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, a, b);
-    tot += ms;
-  }
-  cudaEventDestroy(a);
-  cudaEventDestroy(b);
-  out->ms_graph = tot / reps;
-  return AFMPB_OK;
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    out->ms_graph = tot / reps;
+    return AFMPB_OK;
+  } AFMPB_CATCH(h)
 }
 
 afmpb_status afmpb_destroy(afmpb_t *h) {
-  destroy_handle(h);
-  return AFMPB_OK;
+  try {
+    destroy_handle(h);
+    return AFMPB_OK;
+  } AFMPB_CATCH(nullptr)
 }
 
 const char *afmpb_last_error(const afmpb_t *h) { return h ? h->err.c_str() : g_err.c_str(); }
@@ -751,11 +795,13 @@ size_t afmpb_estimate_bytes(int64_t n_nodes, int64_t n_atoms, int fmm_order, con
 const char *afmpb_version(void) { return "afmpb-gb300 0.1.0 (sm_103a)"; }
 
 afmpb_status afmpb_selftest_bounded_wait(int spin_limit, int *expired) {
-  if (!expired || spin_limit < 1 || spin_limit > (1 << 26))
-    return fail(nullptr, make_err(AFMPB_EINVAL, "spin_limit must be in [1, 2^26] and expired non-NULL"));
-  *expired = 0;
-  Err e = selftest_bounded_wait(spin_limit, expired);
-  return e.ok() ? AFMPB_OK : fail(nullptr, e);
+  try {
+    if (!expired || spin_limit < 1 || spin_limit > (1 << 26))
+      return fail(nullptr, make_err(AFMPB_EINVAL, "spin_limit must be in [1, 2^26] and expired non-NULL"));
+    *expired = 0;
+    Err e = selftest_bounded_wait(spin_limit, expired);
+    return e.ok() ? AFMPB_OK : fail(nullptr, e);
+  } AFMPB_CATCH(nullptr)
 }
 
 }  // extern "C"

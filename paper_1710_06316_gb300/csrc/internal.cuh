@@ -7,7 +7,10 @@
 #include <algorithm>
 #include <cstdint>
 #include <cstdio>
+#include <exception>
+#include <new>
 #include <string>
+#include <system_error>
 #include <thread>
 #include <vector>
 
@@ -404,6 +407,23 @@ inline int host_parts(int64_t n) {
 // process-wide per kernel and per device, so it is only ever raised: a handle that needs
 // less must not lower it under another handle's launch).
 Err raise_smem_limit(const void *func, int bytes);
+
+// The Err of the exception being handled; call only inside a catch block.  Host
+// allocation and thread-creation failures are ENOMEM, anything else EINTERNAL.  The C
+// entry points use it so that no C++ exception crosses the C boundary.
+inline Err current_exception_err() {
+  try {
+    throw;
+  } catch (const std::bad_alloc &) {
+    return make_err(AFMPB_ENOMEM, "host memory allocation failed");
+  } catch (const std::system_error &e) {
+    return make_err(AFMPB_ENOMEM, std::string("host resources: ") + e.what());
+  } catch (const std::exception &e) {
+    return make_err(AFMPB_EINTERNAL, std::string("host exception: ") + e.what());
+  } catch (...) {
+    return make_err(AFMPB_EINTERNAL, "unknown host exception");
+  }
+}
 
 inline Err check_launch(const char *what) {
   cudaError_t e = cudaGetLastError();

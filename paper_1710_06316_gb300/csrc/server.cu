@@ -135,7 +135,13 @@ void slot_main(afmpb_server_t *s, int slot) {
     r.slot = slot;
     r.bytes_reserved = (int64_t)j->reserve;
     if (have_stream) {
-      run_job(s, *j, stream, r);
+      try {
+        run_job(s, *j, stream, r);
+      } catch (...) {                                   // no exception may end a slot thread
+        const afmpb::Err e = afmpb::current_exception_err();
+        r.status = e.code;
+        std::strncpy(r.error, e.msg.c_str(), sizeof(r.error) - 1);
+      }
     } else {
       r.status = AFMPB_ECUDA;
       std::strncpy(r.error, "slot stream creation failed", sizeof(r.error) - 1);
@@ -156,6 +162,8 @@ void slot_main(afmpb_server_t *s, int slot) {
   }
   if (stream) cudaStreamDestroy(stream);
 }
+
+afmpb_status submit_job(afmpb_server_t *s, const afmpb_request *req, int64_t *ticket);
 
 bool copy_array(std::vector<double> &dst, const double *src, int64_t n) {
   if (n < 0 || (n > 0 && !src)) return false;
@@ -193,6 +201,21 @@ afmpb_status afmpb_server_create(size_t bytes_budget, int max_slots, afmpb_serve
 
 afmpb_status afmpb_server_submit(afmpb_server_t *s, const afmpb_request *req, int64_t *ticket) {
   if (!s || !req || !ticket) return AFMPB_EINVAL;
+  try {
+    return submit_job(s, req, ticket);
+  } catch (...) {                                       // copying the request may run out of memory
+    const afmpb::Err e = afmpb::current_exception_err();
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->err = e.msg;
+    return e.code;
+  }
+}
+
+}  // extern "C"
+
+namespace {
+
+afmpb_status submit_job(afmpb_server_t *s, const afmpb_request *req, int64_t *ticket) {
   const afmpb_mesh &m = req->mesh;
   if (m.n_nodes <= 0 || m.n_tris <= 0 || !m.xyz || !m.tri || req->charges.n < 0) return AFMPB_EINVAL;
   auto j = std::make_unique<Job>();
@@ -231,6 +254,10 @@ afmpb_status afmpb_server_submit(afmpb_server_t *s, const afmpb_request *req, in
   s->cv_work.notify_one();
   return AFMPB_OK;
 }
+
+}  // namespace
+
+extern "C" {
 
 afmpb_status afmpb_server_poll(afmpb_server_t *s, int64_t ticket, afmpb_result *res) {
   if (!s || !res) return AFMPB_EINVAL;
