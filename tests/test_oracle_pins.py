@@ -293,6 +293,26 @@ def test_gmres_matches_dense_lu():
         assert info["res_true"] < 1e-7
 
 
+@pytest.mark.parametrize("case", ["born ion, 2562 nodes", "globule, restart 3"])
+def test_gmres_matches_dense_lu_at_the_solve_tolerance(case):
+    """At the configurations' tolerance (1e-6) GMRES agrees with a dense LU solve of the
+    assembled 2N x 2N system to within 10x that tolerance: the Born ion at its full
+    configuration size (5,124 x 5,124 system) and a small isosurface globule with a Krylov
+    dimension of 3, so that the solve runs through several restarts."""
+    if case.startswith("born"):
+        mol, restart = synthetic.born_ion(subdiv=4), 80
+    else:
+        mol, restart = synthetic.globule(n_atoms=20, index=12, grid=1.0), 3
+    o = oracle.Oracle.for_molecule(mol)
+    M = o.assemble()
+    b = o.rhs(mol.atoms, mol.q)
+    x_lu = np.linalg.solve(M, b)
+    for dense in (M, None):
+        x, info, ok = o.gmres(b, rel_tol=1e-6, restart=restart, max_restart=100, dense=dense)
+        assert ok and (restart == 80 or info["restarts"] >= 1)
+        assert np.linalg.norm(x - x_lu) / np.linalg.norm(x_lu) < 1e-5
+
+
 def test_gmres_restart_and_inner_product_count():
     """Restarted GMRES reaches the same solution; with no second Gram-Schmidt pass the
     inner-product count is 1 + sum_{j=1..k} (j+1) for k iterations -- the count the paper
