@@ -396,6 +396,44 @@ def oracle_rows_rate(mol, rows_target_s=12.0, max_rows=200000):
     return nrow / dt, oracle.num_threads(), nrow, dt
 
 
+def oracle_near_rate(mol, seconds=3.0, c_near=2.0):
+    """The oracle's near-field setup on the host cores, timed on its own: near-rule
+    coefficients (patch quadrature of Eq. 6, self terms included) per second over the
+    near sets of randomly sampled rows.  A row's near set is taken by the rule
+    |x_p - x_t| < c (rho_p + rho_t) with the oracle's patch radii.  Returns
+    (entries/s, rows, entries, seconds)."""
+    import numpy as np
+    from scipy.spatial import cKDTree
+
+    import oracle
+    o = oracle.Oracle.for_molecule(mol, c_near=c_near)
+    _, _, rho = o.geometry()
+    rng = np.random.default_rng(1)
+    kd = cKDTree(mol.xyz)
+
+    def pairs(rows):
+        ps, ts = [], []
+        cand = kd.query_ball_point(mol.xyz[rows], c_near * (rho[rows] + rho.max()))
+        for p, c in zip(rows, cand):
+            c = np.asarray(c, np.int64)
+            d = np.linalg.norm(mol.xyz[c] - mol.xyz[p], axis=1)
+            t = c[d < c_near * (rho[p] + rho[c])]
+            ps.append(np.full(t.size, p, np.int64))
+            ts.append(t)
+        return np.concatenate(ps), np.concatenate(ts)
+
+    p, t = pairs(rng.choice(mol.n_nodes, 8, replace=False))
+    t0 = time.perf_counter()
+    o.coeffs(p, t, rule=o.NEAR)
+    per_row = max((time.perf_counter() - t0) / 8, 1e-6)
+    nrow = int(min(mol.n_nodes, max(8, seconds / per_row)))
+    p, t = pairs(rng.choice(mol.n_nodes, nrow, replace=False))
+    t0 = time.perf_counter()
+    o.coeffs(p, t, rule=o.NEAR)
+    dt = time.perf_counter() - t0
+    return p.size / dt, nrow, int(p.size), dt
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -600,6 +638,15 @@ def run_gpu(args):
         line["cpu_baseline"] = {"value": round(rate / 1e6, 6), "unit": UNIT, "cores": cores, "kind": "oracle",
                                 "sample": "%d random rows of the product in %.1f s (FP64 direct sum, O(N) per "
                                           "row, near rule on the fly); rows/s = full-product Mnode/s" % (nrow, dt)}
+        try:
+            erate, erows, nent, edt = oracle_near_rate(mol)
+            line["cpu_baseline"]["near_setup"] = {
+                "entries_per_s": round(erate, 1), "sample": "near sets of %d random rows, %d entries in %.1f s"
+                                                            % (erows, nent, edt),
+                "full_setup_s_est": round(info["nnz_near"] / erate, 1),
+                "gpu_near_setup_ms": round(info["ms_create"][2], 1)}
+        except Exception as ex:         # the headline line is printed whatever happens here
+            line["cpu_baseline"]["near_setup"] = {"error": repr(ex)[:200]}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

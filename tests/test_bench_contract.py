@@ -43,3 +43,17 @@ def test_reference_arm_other_ranks_exit_quietly():
     r = _run({"RANK": "1", "WORLD_SIZE": "2"})
     assert r.returncode == 0, r.stderr
     assert r.stdout.strip() == ""
+
+
+def test_oracle_near_setup_timing_covers_the_oracle_near_set():
+    """The bench's separately timed oracle near-field setup samples whole near sets: with
+    every row of a small mesh sampled it times exactly the oracle's near CSR entries."""
+    sys.path.insert(0, ROOT)
+    import bench
+    import oracle
+    import synthetic
+    mol = synthetic.born_ion()
+    rate, rows, entries, dt = bench.oracle_near_rate(mol, seconds=60.0)
+    assert rows == mol.n_nodes and rate > 0 and dt > 0
+    rp, _, _ = oracle.Oracle.for_molecule(mol).near_csr()
+    assert entries == rp[-1]
