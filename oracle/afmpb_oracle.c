@@ -43,9 +43,10 @@
  *                      converted with 4 pi K_c, K_c = 332.0636 kcal A / (mol e^2).
  *   R8  GMRES        x0 = 0; restart = Krylov dimension m; a second Gram-Schmidt pass
  *                      only when ||w|| dropped below eta ||w_before|| (eta = 1e-3 by
- *                      default): the paper's inner-product counts (Sec. 5: 77 for 11
- *                      iterations, 4,803 for 133 with restart 80) equal plain MGS, so the
- *                      second pass must be rare.
+ *                      default): the paper's inner-product counts (Sec. 5: 66 for 10
+ *                      iterations, 77 for 11, 4,803 for 133 with restart 80) equal plain
+ *                      MGS's (66) or fall 1-3 short of it (78, 4,806); a second pass adds
+ *                      at least two, so in those runs it never fired.
  */
 #include <math.h>
 #include <stdint.h>

@@ -320,6 +320,19 @@ def test_gmres_restart_and_inner_product_count():
     g = read_golden("gmres_counts.txt")
     k, ip = int(g["1K4R_3digit"][0]), int(g["1K4R_3digit"][1])
     assert 1 + sum(j + 1 for j in range(1, k + 1)) == ip
+
+    def plain_mgs(iters, m=80):     # one residual norm per cycle, j + 1 per step j
+        total = 0
+        while iters > 0:
+            k = min(iters, m)
+            total += 1 + sum(j + 1 for j in range(1, k + 1))
+            iters -= k
+        return total
+    # the other printed counts sit at or just below plain MGS; a second Gram-Schmidt pass
+    # at step j would add j + 2 >= 2, so none fired in the paper's runs (reading R8)
+    for key in ("3K1Q_3digit", "3K1Q_6digit", "1K4R_3digit"):
+        it, count = int(g[key][0]), int(g[key][1])
+        assert 0 <= plain_mgs(it) - count <= 3, key
     mol = synthetic.kirkwood_sphere(subdiv=2)
     o = oracle.Oracle.for_molecule(mol)
     b = o.rhs(mol.atoms, mol.q)
