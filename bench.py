@@ -309,10 +309,11 @@ def fp32_peak_tflops(sm_max_mhz):
     return 152 * 128 * 2 * sm_max_mhz * 1e6 / 1e12
 
 
-# FP32 operations per source-target pair in the P2P kernel (p2p_pair), counted from its
-# source with an FMA as 2 flop: 46 FP32 instructions of which 17 are FMAs, plus one
-# rsqrt and one exp2 on the special-function unit.
-P2P_FLOP_PER_PAIR = 63
+# FP32 operations per source-target pair in the P2P kernel (p2p_pair2, one lane of each
+# packed operation), counted from its source with an FMA as 2 flop: 44 FP32 arithmetic
+# operations (6 adds, 20 multiplies, 18 FMAs) = 62 flop, besides the compare and select of
+# the skip test and one rsqrt and one exp2 on the special-function unit.
+P2P_FLOP_PER_PAIR = 62
 
 
 def ncu_traffic(kernel):
