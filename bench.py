@@ -69,12 +69,17 @@ def run_config(mol, args, world, leaf_cap=None):
 # serving: many molecules of uneven size through the continuous-batching server
 # ------------------------------------------------------------------------------------
 def serving_leg(args):
-    """Solve requests on synthetic globules (atom counts log-uniform in [500, 50,000],
-    surfaces on a 1.2 A lattice, so meshes of ~6k-410k nodes; kappa ~ U(0.03, 0.3)), drawn
-    from a pool of seeded molecules.  Three runs: the plain FP32 path one solve at a time (closed loop: each
-    request is submitted when the previous one has finished); the mixed path served with
-    all requests submitted at once (capacity); the mixed path served under Poisson
-    arrivals at 0.9x the plain capacity (latency, queueing included)."""
+    """The serving configuration: args.serve_requests solve requests (default 512), each a
+    synthetic globule drawn from a seeded pool of args.serve_pool molecules whose atom
+    counts are log-uniform in [500, 50,000] (surfaces on a 1.2 A lattice: ~10k-350k nodes),
+    with kappa ~ U(0.03, 0.3) drawn per request.  Four arms -- plain FP32 and mixed
+    precision, each on 1 and on args.serve_slots server slots -- run the same requests:
+      * capacity: the first args.serve_burst requests submitted at once (solves/s);
+      * latency: all requests on one fixed Poisson arrival trace at 0.9x the capacity of
+        plain FP32 on args.serve_slots slots, p50/p99 from submission to result (queueing
+        included), solves/s = requests / (last result - first submission).
+    Each arm also reports the admitted-memory high-water mark and the largest energy
+    difference against the plain FP32 arm on the same slots."""
     import numpy as np
 
     import paper_1710_06316_gb300 as pb
@@ -86,49 +91,70 @@ def serving_leg(args):
     pool = [synthetic.globule(n_atoms=int(c), index=100 + i, grid=1.2) for i, c in enumerate(counts)]
     t_gen = time.perf_counter() - t0
     reqs = [(int(rng.integers(len(pool))), float(rng.uniform(0.03, 0.3))) for _ in range(args.serve_requests)]
-    arrivals = np.cumsum(rng.exponential(1.0, len(reqs)))      # unit-rate gaps, scaled below
+    gaps = rng.exponential(1.0, len(reqs))            # unit-rate gaps, scaled by the rate below
 
-    def run(precision, slots, rate=None, closed_loop=False):
+    def run(precision, slots, items, rate=None):
         with pb.Server(bytes_budget=int(args.serve_budget_gb * (1 << 30)), max_slots=slots) as srv:
             start = time.perf_counter()
-            tickets, res = [], []
-            for k, (i, kap) in enumerate(reqs):
+            due = start + np.cumsum(gaps[:len(items)]) / rate if rate else None
+            tickets = []
+            for k, (i, kap) in enumerate(items):
                 if rate:
-                    delay = start + arrivals[k] / rate - time.perf_counter()
+                    delay = due[k] - time.perf_counter()
                     if delay > 0:
                         time.sleep(delay)
                 m = pool[i]
                 tickets.append(srv.submit(m.xyz, m.tri, m.atoms, m.q, m.eps_in, m.eps_out, kap,
                                           order=args.order, tol=1e-6, precision=precision,
                                           restart=args.serve_restart, max_restart=5))
-                if closed_loop:
-                    res.append(srv.wait(tickets[-1], 3600))
-            if not closed_loop:
-                res = [srv.wait(t, 3600) for t in tickets]
-            wall = time.perf_counter() - start
+            res = [srv.wait(t, 3600) for t in tickets]
             info = srv.info()
+        t_first = min(r["t_submit"] for r in res)
+        t_last = max(r["t_done"] for r in res)
         bad = [(r["status"], r["error"]) for r in res if r["status"] != "OK"]
         lat = sorted(1e3 * r["latency"] for r in res)
         pq = lambda q: lat[min(len(lat) - 1, int(round(q * (len(lat) - 1))))]
-        return {"solves_per_s": round(len(res) / wall, 3), "p50_ms": round(pq(0.5), 1),
-                "p99_ms": round(pq(0.99), 1), "wall_s": round(wall, 2), "failed": len(bad), "failures": bad[:3],
-                "iters_max": max(r["info"]["iters"] for r in res),
-                "max_running": info["max_running"], "reserved_high_water_gb": round(info["bytes_high_water"] / 2**30, 2),
+        return {"requests": len(res), "solves_per_s": round(len(res) / (t_last - t_first), 3),
+                "p50_ms": round(pq(0.5), 1), "p99_ms": round(pq(0.99), 1),
+                "wall_s": round(t_last - t_first, 2), "failed": len(bad), "failures": bad[:3],
+                "iters_max": max(r["info"]["iters"] for r in res), "max_running": info["max_running"],
+                "reserved_high_water_gb": round(info["bytes_high_water"] / 2**30, 2),
+                "used_high_water_gb": round(max(r["bytes_used"] for r in res) / 2**30, 2),
                 "slots": slots}, [r["energy"] for r in res]
 
-    plain, e_plain = run(0, 1, closed_loop=True)
-    burst, e_mixed = run(1, args.serve_slots)
-    rate = 0.9 * plain["solves_per_s"]
-    poisson, _ = run(1, args.serve_slots, rate=rate)
-    poisson["arrival_rate_per_s"] = round(rate, 3)
-    diff = max((abs(a / b - 1) for a, b in zip(e_mixed, e_plain) if a and b), default=None)
-    return {"workload": "%d requests over %d synthetic globules (%d-%d nodes), kappa U(0.03, 0.3), order %d, "
-                        "GMRES(%d) tol 1e-6, each request = setup + solve + energy" % (
-                            len(reqs), len(pool), min(m.n_nodes for m in pool), max(m.n_nodes for m in pool), args.order,
-                            args.serve_restart),
-            "pool_nodes": [m.n_nodes for m in pool], "pool_generation_s": round(t_gen, 1),
-            "plain_fp32_one_at_a_time": plain, "mixed_served_burst": burst, "mixed_served_poisson": poisson,
-            "energy_max_rel_diff_mixed_vs_plain": diff}
+    def ediff(e, e_ref):
+        return max((abs(a / b - 1) for a, b in zip(e, e_ref) if a and b), default=None)
+
+    arms = [("plain_fp32_1slot", 0, 1), ("plain_fp32_%dslots" % args.serve_slots, 0, args.serve_slots),
+            ("mixed_1slot", 1, 1), ("mixed_%dslots" % args.serve_slots, 1, args.serve_slots)]
+    burst_items = reqs[:args.serve_burst]
+    cap, cap_e = {}, {}
+    for name, prec, slots in arms:
+        cap[name], cap_e[name] = run(prec, slots, burst_items)
+    rate = 0.9 * cap["plain_fp32_%dslots" % args.serve_slots]["solves_per_s"]
+    lat, lat_e = {}, {}
+    for name, prec, slots in arms:
+        lat[name], lat_e[name] = run(prec, slots, reqs, rate=rate)
+    out = {}
+    for name, prec, slots in arms:
+        ref = "plain_fp32_1slot" if slots == 1 else "plain_fp32_%dslots" % args.serve_slots
+        out[name] = {"capacity": cap[name], "poisson": lat[name],
+                     "energy_max_rel_diff_vs_plain": ediff(lat_e[name], lat_e[ref]),
+                     "energy_max_rel_diff_vs_plain_1slot": ediff(lat_e[name], lat_e["plain_fp32_1slot"])}
+    mix, pla = "mixed_%dslots" % args.serve_slots, "plain_fp32_%dslots" % args.serve_slots
+    return {"workload": "%d requests over a pool of %d synthetic globules (%d-%d nodes), kappa U(0.03, 0.3), "
+                        "order %d, GMRES(%d) tol 1e-6, each request = setup + solve + energy" % (
+                            len(reqs), len(pool), min(m.n_nodes for m in pool), max(m.n_nodes for m in pool),
+                            args.order, args.serve_restart),
+            "pool_nodes": [m.n_nodes for m in pool], "pool_atoms": [int(c) for c in counts],
+            "pool_generation_s": round(t_gen, 1),
+            "arrival_rate_per_s": round(rate, 3),
+            "arrival_rule": "Poisson, 0.9 x the burst capacity of plain FP32 on %d slots" % args.serve_slots,
+            "capacity_requests": len(burst_items), "arms": out,
+            "mixed_vs_plain_same_slots": {
+                "capacity_ratio": round(cap[mix]["solves_per_s"] / cap[pla]["solves_per_s"], 3),
+                "p50_ratio": round(lat[mix]["p50_ms"] / lat[pla]["p50_ms"], 3),
+                "p99_ratio": round(lat[mix]["p99_ms"] / lat[pla]["p99_ms"], 3)}}
 
 
 # ------------------------------------------------------------------------------------
@@ -227,6 +253,19 @@ def capsid_leg(args, stream):
     torch.cuda.synchronize()
     ms = sum(a.elapsed_time(b) for a, b in ev) / steps
     prof = h.profile(reps=3)
+    peaks, kind = measured_peaks()
+    sms = torch.cuda.get_device_properties(x.device).multi_processor_count
+    roof_ops, roof = rooflines(prof, info, n, args.order, peaks, kind, 1, sms)
+    # end to end through the C ABI with pinned host buffers (H2D + product + D2H)
+    xh = x.cpu().pin_memory()
+    yh = torch.empty(2 * n, dtype=torch.float32).pin_memory()
+    h.matvec_host(xh, yh)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        h.matvec_host(xh, yh)
+    e2e_s = (time.perf_counter() - t0) / steps
+    e2e = {"value": round(n / e2e_s / 1e6, 3), "unit": UNIT, "h2d_bytes_per_step": 2 * n * 4,
+           "d2h_bytes_per_step": 2 * n * 4, "ms_per_step": round(e2e_s * 1e3, 3)}
     t0 = time.perf_counter()
     f, hh, si = h.solve(raise_on_noconv=False)
     t_solve = time.perf_counter() - t0
@@ -240,6 +279,7 @@ def capsid_leg(args, stream):
                             len(mol.q), mol.eps_in, mol.eps_out, mol.kappa, args.order),
             "value": round(n / (ms * 1e-3) / 1e6, 3), "unit": UNIT, "ms_per_product": round(ms, 3),
             "steps": steps, "stages_ms": {a: round(b, 3) for a, b, _ in prof["stages"]},
+            "e2e": e2e, "roofline": roof, "rooflines": roof_ops,
             "full_solve_wall_s": round(t_setup + t_solve + t_energy, 3),
             "setup_s": round(t_setup, 3), "gmres_s": round(t_solve, 3), "energy_s": round(t_energy, 3),
             "ms_create": {k: round(v, 1) for k, v in zip(("geometry", "tree", "near", "fmm", "rhs", "graph"),
@@ -304,9 +344,9 @@ def measured_peaks():
             "sm_max_mhz": 2070.0}, "fallback"
 
 
-def fp32_peak_tflops(sm_max_mhz):
-    # 152 SMs x 128 FP32 lanes x 2 flop per FMA x max SM clock
-    return 152 * 128 * 2 * sm_max_mhz * 1e6 / 1e12
+def fp32_peak_tflops(sm_max_mhz, sms):
+    # SMs (read from the device) x 128 FP32 lanes x 2 flop per FMA x max SM clock
+    return sms * 128 * 2 * sm_max_mhz * 1e6 / 1e12
 
 
 # FP32 operations per source-target pair in the P2P kernel (p2p_pair2, one lane of each
@@ -334,43 +374,59 @@ def ncu_traffic(kernel):
     return None
 
 
-def roofline(prof, info, n, order, peaks, kind, precision):
+def rooflines(prof, info, n, order, peaks, kind, precision, sms):
+    """One roofline entry per product operator, from the stage times of the live profile
+    (CUDA events, L2 flushed, stages serialised): P2P against the FP32 FMA peak (derived:
+    SMs x 128 lanes x 2 x max clock), the M2L translations against the measured BF16 peak
+    (tensor cores, counting the three split products and the useful one) or the FP32 peak,
+    and the near-field SpMV + assembly against the measured HBM copy bandwidth.  Returns
+    (entries by stage, the dominant stage's entry)."""
     stages = {name: (ms, launches) for name, ms, launches in prof["stages"]}
-    name, (ms, launches) = max(stages.items(), key=lambda kv: kv[1][0])
     n3 = order ** 3
     sm_max = peaks.get("sm_max_mhz", 2070.0)
+    fp32 = fp32_peak_tflops(sm_max, sms)
+    fp32_kind = "FP32 FMA, derived: %d SMs (device attribute) x 128 lanes x 2 x %.0f MHz" % (sms, sm_max)
     r = info.get("m2l_rank") or n3                 # compressed translation size, or n^3
-    if name == "m2l" and precision == 1:
-        # three BF16 products (hi*hi, hi*lo, lo*hi) of every r x r translation, Laplace and
-        # Yukawa; the burst BF16 peak, the kernel being timed on its own
-        flop = 3 * 2.0 * r * r * info["n_m2l_pairs"] * 2
-        achieved = flop / (ms * 1e-3) / 1e12
-        peak = peaks["bf16_tflops"]
-        out = {"bound": "tensor", "kernel": "k_m2l_tcp (tcgen05 BF16 x3, FP32 accumulate)",
-               "unit": "TFLOP/s", "peak_kind": "measured dense BF16 GEMM (burst)"}
-    elif name == "m2l":
-        flop = 2.0 * r * r * info["n_m2l_pairs"] * 2        # Laplace + Yukawa
-        achieved = flop / (ms * 1e-3) / 1e12
-        peak = fp32_peak_tflops(sm_max)
-        out = {"bound": "alu", "kernel": "k_m2l (FP32 FMA)", "unit": "TFLOP/s",
-               "peak_kind": "FP32 FMA: 152 SM x 128 lanes x 2 x %.0f MHz" % sm_max}
-    elif name == "p2p":
-        flop = float(P2P_FLOP_PER_PAIR) * info["n_p2p_pairs"]
-        achieved = flop / (ms * 1e-3) / 1e12
-        peak = fp32_peak_tflops(sm_max)
-        out = {"bound": "alu", "kernel": "k_p2p (packed FP32x2 FMA + MUFU)", "unit": "TFLOP/s",
-               "peak_kind": "FP32 FMA: 152 SM x 128 lanes x 2 x %.0f MHz" % sm_max}
-    else:   # combine / near SpMV and the rest are memory-bound
-        byts = info["nnz_near"] * 20.0 + n * (8 + 16 + 16 + 8)
-        achieved = byts / (ms * 1e-3) / 1e9
-        peak = peaks["hbm_gbs"]
-        out = {"bound": "hbm", "kernel": "k_" + name, "unit": "GB/s",
-               "peak_kind": "measured copy bandwidth"}
-    out.update({"stage": name, "achieved": round(achieved, 3), "peak": round(peak, 3),
-                "frac": round(achieved / peak, 4), "ms_per_launch": round(ms, 5),
-                "traffic": ncu_traffic(name), "peak_source": kind,
-                "stage_ms": {k: round(v[0], 5) for k, v in stages.items()}})
-    return out
+    out = {}
+    ms, _ = stages["p2p"]
+    flop = float(P2P_FLOP_PER_PAIR) * info["n_p2p_pairs"]
+    out["p2p"] = {"bound": "alu", "kernel": "k_p2p (packed FP32x2 FMA + MUFU)", "unit": "TFLOP/s",
+                  "achieved": flop / (ms * 1e-3) / 1e12, "peak": fp32, "peak_kind": fp32_kind,
+                  "peak_source": "derived", "ms_per_launch": ms,
+                  "work": "%d pairs x %d flop" % (info["n_p2p_pairs"], P2P_FLOP_PER_PAIR)}
+    ms, _ = stages["m2l"]
+    if precision == 1:
+        flop3 = 3 * 2.0 * r * r * info["n_m2l_pairs"] * 2       # hi*hi, hi*lo, lo*hi; Laplace + Yukawa
+        out["m2l"] = {"bound": "tensor", "kernel": "k_m2l_tcp (tcgen05 BF16 x3, FP32 accumulate)",
+                      "unit": "TFLOP/s", "achieved": flop3 / (ms * 1e-3) / 1e12, "peak": peaks["bf16_tflops"],
+                      "peak_kind": "measured dense BF16 GEMM (burst)", "peak_source": kind,
+                      "useful_achieved": flop3 / 3 / (ms * 1e-3) / 1e12, "ms_per_launch": ms,
+                      "work": "%d translations x 2 kernels x 3 x 2 r^2 flop, r = %d" % (info["n_m2l_pairs"], r)}
+    else:
+        flop = 2.0 * r * r * info["n_m2l_pairs"] * 2
+        out["m2l"] = {"bound": "alu", "kernel": "k_m2l_c (FP32 FMA)", "unit": "TFLOP/s",
+                      "achieved": flop / (ms * 1e-3) / 1e12, "peak": fp32, "peak_kind": fp32_kind,
+                      "peak_source": "derived", "ms_per_launch": ms,
+                      "work": "%d translations x 2 kernels x 2 r^2 flop, r = %d" % (info["n_m2l_pairs"], r)}
+    ms, _ = stages["combine"]
+    byts = info["nnz_near"] * 20.0 + n * (8 + 16 + 16 + 8 + 8)
+    out["combine"] = {"bound": "hbm", "kernel": "k_combine (near SpMV + Eq. 5 assembly)", "unit": "GB/s",
+                      "achieved": byts / (ms * 1e-3) / 1e9, "peak": peaks["hbm_gbs"],
+                      "peak_kind": "measured copy bandwidth", "peak_source": kind, "ms_per_launch": ms,
+                      "work": "%d entries x 20 B + %d nodes x 56 B" % (info["nnz_near"], n)}
+    for k, e in out.items():
+        e["frac"] = round(e["achieved"] / e["peak"], 4)
+        e["achieved"] = round(e["achieved"], 3)
+        e["peak"] = round(e["peak"], 3)
+        e["ms_per_launch"] = round(e["ms_per_launch"], 5)
+        if "useful_achieved" in e:
+            e["useful_frac"] = round(e["useful_achieved"] / e["peak"], 4)
+            e["useful_achieved"] = round(e["useful_achieved"], 3)
+        e["traffic"] = ncu_traffic(k)
+    dom = max(out, key=lambda k: out[k]["ms_per_launch"])
+    head = dict(out[dom], stage=dom, sms=sms,
+                stage_ms={k: round(v[0], 5) for k, v in stages.items()})
+    return out, head
 
 
 # ------------------------------------------------------------------------------------
@@ -586,7 +642,8 @@ def run_gpu(args):
 
     prof = h.profile(reps=5, flush=flush, flush_bytes=FLUSH_BYTES)
     peaks, kind = measured_peaks()
-    roof = roofline(prof, info, n, args.order, peaks, kind, args.precision)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    roof_ops, roof = rooflines(prof, info, n, args.order, peaks, kind, args.precision, sms)
 
     # solves on the resident handle (outside the timed region): GMRES + energy latency
     lat, (sinfo, energy) = solve_latency(h, args.solve_reps)
@@ -611,6 +668,7 @@ def run_gpu(args):
             "config": run_config(mol, args, world, info["leaf_cap"]),
             "e2e": {k: (round(v, 4) if isinstance(v, float) else v) for k, v in e2e.items()},
             "roofline": roof,
+            "rooflines": roof_ops,
             "gpu_launches": int(prof["kernels_per_product"]) * args.steps,
             "clocks": clk,
             "ms_graph_profile": round(prof["ms_graph"], 5),
@@ -667,8 +725,9 @@ def main():
     ap.add_argument("--precision", type=int, default=1, choices=[0, 1])
     ap.add_argument("--plain-leaf-cap", type=int, default=0)
     ap.add_argument("--no-serving", action="store_true")
-    ap.add_argument("--serve-pool", type=int, default=8)
-    ap.add_argument("--serve-requests", type=int, default=24)
+    ap.add_argument("--serve-pool", type=int, default=16)
+    ap.add_argument("--serve-requests", type=int, default=512)
+    ap.add_argument("--serve-burst", type=int, default=128)
     ap.add_argument("--serve-slots", type=int, default=4)
     ap.add_argument("--serve-budget-gb", type=float, default=96.0)
     ap.add_argument("--serve-restart", type=int, default=80)
@@ -676,7 +735,7 @@ def main():
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--capsid-steps", type=int, default=10)
     ap.add_argument("--no-plain", action="store_true")
-    ap.add_argument("--solve-reps", type=int, default=5)
+    ap.add_argument("--solve-reps", type=int, default=100)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-rows", type=int, default=48)

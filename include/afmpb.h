@@ -105,7 +105,22 @@ typedef struct {
     int charge_fmm;      /* charge-surface sums of the right-hand side and the energy:
                             0 = by FMM when n_nodes x n_charges > AFMPB_CHARGE_FMM_PAIRS,
                             else direct; 1 = always direct; 2 = always by FMM            */
+    int orth;            /* Arnoldi orthogonalisation: 0 = classical Gram-Schmidt applied
+                            twice (three reductions per step, default); 1 = one reduction per
+                            step (AFMPB_ORTH_ONE_REDUCTION) */
 } afmpb_options;
+
+/* afmpb_options.restart: no restart -- the Krylov dimension is the largest whose FP64
+ * basis fits in half of the free device memory at the first solve (at most
+ * AFMPB_RESTART_NONE_MAX); the paper's no-restart runs (Sec. 5). */
+#define AFMPB_RESTART_NONE (-1)
+#define AFMPB_RESTART_NONE_MAX 4096
+/* afmpb_options.orth = 1: classical Gram-Schmidt with one fused reduction per Arnoldi step
+ * (the coefficients V^T w and ||w||^2 together), ||w - V h|| from Pythagoras
+ * (||w||^2 - ||h||^2), and a second Gram-Schmidt pass only when that norm falls below 1e-3
+ * of ||w|| (loss of orthogonality; the reorthogonalisation test of the FP64 reference
+ * GMRES).  The communication-hiding direction of the paper's future work (Sec. 6). */
+#define AFMPB_ORTH_ONE_REDUCTION 1
 
 /* afmpb_options.charge_fmm = 0 switches to the FMM above this many charge-node pairs. */
 #define AFMPB_CHARGE_FMM_PAIRS 5.0e11
@@ -118,10 +133,14 @@ typedef struct {
     double res_true;       /* ||b - L x|| / ||b|| with one more product                 */
     double bnorm;          /* ||b||_2                                                    */
     double ms_setup;       /* time spent in afmpb_create (host clock)                   */
-    double ms_matvec_total;/* time inside products during the solve (CUDA events)       */
+    double ms_matvec_total;/* time inside products during the solve: the number of
+                              products times the CUDA-event time of the final one       */
     double ms_gmres;       /* time of the whole solve (CUDA events)                     */
     int64_t nnz_near;      /* stored near-field pairs (incl. the diagonal)              */
     int64_t n_boxes;       /* octree boxes                                               */
+    int krylov_dim;        /* Krylov dimension m used (restart, or the no-restart size)  */
+    int second_passes;     /* Arnoldi steps that took a second Gram-Schmidt pass (orth = 1;
+                              every step with orth = 0)                                  */
 } afmpb_solve_info;
 
 /* Structure sizes (for tests, tooling and the memory estimator). */
@@ -204,18 +223,37 @@ afmpb_status afmpb_create(const afmpb_mesh *mesh, const afmpb_charges *charges,
 
 /* y = L x for the operator of Eq. 5 (caller order, device pointers, FP32, length 2N).
  * Queued on the handle's stream; returns before the product completes.  x and y must not
- * overlap. */
+ * overlap.
+ * Bounded waits: the tensor-core translation kernels (precision 1) give up on a device wait
+ * after a fixed number of polls and set the handle's wait flag instead of hanging.  The
+ * flag is latched: the next afmpb_matvec, afmpb_matvec_parts, afmpb_matvec_host or
+ * afmpb_solve call on the handle, or afmpb_sync, returns AFMPB_ETIMEOUT once (queuing
+ * nothing) and clears it; the products queued since the previous report are invalid. */
 afmpb_status afmpb_matvec(afmpb_t *h, const float *x_dev, float *y_dev);
 
 /* As afmpb_matvec but only the selected AFMPB_PART_* terms are summed into y. */
 afmpb_status afmpb_matvec_parts(afmpb_t *h, const float *x_dev, float *y_dev, int parts);
 
 /* Host-buffer product: copies x to the device, forms y = L x, copies y back and waits.
- * x_host, y_host: [2N] caller order. */
+ * x_host, y_host: [2N] caller order.  Returns AFMPB_ETIMEOUT when a bounded device wait of
+ * this product (or a latched one of an earlier product) expired; y is then invalid. */
 afmpb_status afmpb_matvec_host(afmpb_t *h, const float *x_host, float *y_host);
 
+/* Waits until the work queued on the handle's stream has finished.  Returns AFMPB_ETIMEOUT
+ * (once, clearing the latched flag) when a bounded device wait of that work expired, ECUDA
+ * when the stream reports an error, else OK. */
+afmpb_status afmpb_sync(afmpb_t *h);
+
+/* Fault injection for tests of the AFMPB_ETIMEOUT path (no counterpart in the paper): waits
+ * for the handle's stream, then sets the handle's wait flag from the host exactly as an
+ * expired device wait would.  No kernel runs and no device wait is made to expire. */
+afmpb_status afmpb_inject_wait_expiry(afmpb_t *h);
+
 /* Solve Eq. 5 with restarted GMRES on the device (FP64 basis, Arnoldi with classical
- * Gram-Schmidt applied twice, Givens rotations, stop test of Eq. 7), starting from x = 0.
+ * Gram-Schmidt applied twice or the one-reduction form of afmpb_options.orth, Givens
+ * rotations, stop test of Eq. 7), starting from x = 0.  Each restart cycle runs on the
+ * device as one graph launch: the Arnoldi steps form a graph WHILE loop whose last kernel
+ * applies the stop test, so the host waits once per cycle, not once per step.
  * f_host / h_host ([N] each, caller order) may be NULL; the solution stays in the handle.
  * Returns ENOCONV when max_restart cycles did not reach the tolerance (the best iterate
  * is still stored and returned).  info may be NULL. */
@@ -239,12 +277,18 @@ afmpb_status afmpb_energy(afmpb_t *h, double *kcal_per_mol);
  * which every GPU that loads the library holds until the process exits.
  *   h             a handle with a prior afmpb_solve (ESTATE otherwise)
  *   kcal_per_mol  host output, the same energy afmpb_energy returns
- * Returns EINVAL when the handle has more than AFMPB_NOALLOC_MAX_ATOMS charges.  The
+ * With direct charge sums the result equals afmpb_energy's bit for bit.  With the charge
+ * FMM (afmpb_info.charge_fmm = 1) every evaluation of the reaction potential adds the
+ * FMM's translated expansions with FP32 atomics in a varying order, so two evaluations, and
+ * this call against afmpb_energy, agree to about 1e-6 relative, not bit for bit.
+ * Returns EINVAL when the handle has more than AFMPB_NOALLOC_MAX_ATOMS charges, or when
+ * the calling thread's current device is not the device the handle was created on.  The
  * first call on a device looks up the array's device address (cudaGetSymbolAddress)
- * and caches it; make that first call before any stream capture.  All calls on one
- * device share the one array, so the library serialises them: a call holds a process-wide
- * lock from its first kernel until its result is back on the host.  The paper has no
- * counterpart to this entry point. */
+ * and caches it; make that first call before any stream capture.  A cudaDeviceReset by
+ * the caller invalidates the cached address: do not call this entry point after one.  All
+ * calls on one device share the one array, so the library serialises them: a call holds a
+ * process-wide lock from its first kernel until its result is back on the host.  The
+ * paper has no counterpart to this entry point. */
 #define AFMPB_NOALLOC_MAX_ATOMS 65536
 afmpb_status afmpb_energy_noalloc(afmpb_t *h, double *kcal_per_mol);
 
@@ -363,7 +407,8 @@ typedef struct {
     int slots;
 } afmpb_server_info;
 
-/* bytes_budget > 0; max_slots in [1, 256]. */
+/* bytes_budget > 0; max_slots in [1, 256].  The server runs every request on the device
+ * that is current in the calling thread. */
 afmpb_status afmpb_server_create(size_t bytes_budget, int max_slots, afmpb_server_t **out);
 /* EINVAL for missing arrays or sizes; ENOMEM when the reservation exceeds the whole budget
  * (the request could never run); otherwise queues it and returns its ticket. */
@@ -371,7 +416,9 @@ afmpb_status afmpb_server_submit(afmpb_server_t *s, const afmpb_request *req, in
 /* OK with *res filled when the request has completed (successfully or not), EBUSY while it
  * is queued or running, EINVAL for an unknown ticket. */
 afmpb_status afmpb_server_poll(afmpb_server_t *s, int64_t ticket, afmpb_result *res);
-/* As poll but blocks up to timeout_s seconds; ETIMEOUT if the request is still pending. */
+/* As poll but blocks up to timeout_s seconds (>= 1e6 or infinity: no limit); ETIMEOUT if
+ * the request is still pending, EINVAL if the ticket is unknown or another thread took
+ * its result meanwhile. */
 afmpb_status afmpb_server_wait(afmpb_server_t *s, int64_t ticket, double timeout_s, afmpb_result *res);
 afmpb_status afmpb_server_get_info(afmpb_server_t *s, afmpb_server_info *st);
 afmpb_status afmpb_server_destroy(afmpb_server_t *s);

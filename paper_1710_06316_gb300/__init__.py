@@ -17,6 +17,8 @@ from . import _build
 _lib = None
 
 PART_DIAG, PART_FAR, PART_NEAR, PART_ALL = 1, 2, 4, 7
+RESTART_NONE = -1
+ORTH_CGS2, ORTH_ONE_REDUCTION = 0, 1
 STATUS = {0: "OK", 1: "EINVAL", 2: "EMESH", 3: "ENOMEM", 4: "ECUDA", 5: "ENOCONV", 6: "ETIMEOUT",
           7: "EBUSY", 8: "ESTATE", 9: "EINTERNAL"}
 
@@ -41,14 +43,15 @@ class Options(C.Structure):
     _fields_ = [("leaf_cap", C.c_int), ("restart", C.c_int), ("max_restart", C.c_int),
                 ("abs_tol", C.c_double), ("precision", C.c_int), ("near_c", C.c_double),
                 ("stream", C.c_void_p), ("max_level", C.c_int), ("m2l_tol", C.c_double),
-                ("charge_fmm", C.c_int)]
+                ("charge_fmm", C.c_int), ("orth", C.c_int)]
 
 
 class SolveInfo(C.Structure):
     _fields_ = [("iters", C.c_int), ("restarts", C.c_int), ("res_est", C.c_double),
                 ("res_true", C.c_double), ("bnorm", C.c_double), ("ms_setup", C.c_double),
                 ("ms_matvec_total", C.c_double), ("ms_gmres", C.c_double),
-                ("nnz_near", C.c_int64), ("n_boxes", C.c_int64)]
+                ("nnz_near", C.c_int64), ("n_boxes", C.c_int64), ("krylov_dim", C.c_int),
+                ("second_passes", C.c_int)]
 
 
 class Info(C.Structure):
@@ -115,7 +118,7 @@ EXPORTS = ["afmpb_create", "afmpb_matvec", "afmpb_matvec_parts", "afmpb_matvec_h
            "afmpb_version", "afmpb_profile_product", "afmpb_energy_noalloc",
            "afmpb_server_create", "afmpb_server_submit", "afmpb_server_poll", "afmpb_server_wait",
            "afmpb_server_get_info", "afmpb_server_destroy", "afmpb_get_autotune",
-           "afmpb_selftest_bounded_wait"]
+           "afmpb_selftest_bounded_wait", "afmpb_sync", "afmpb_inject_wait_expiry"]
 
 
 def library_path() -> str:
@@ -139,6 +142,9 @@ def load(build: bool = True):
     for name in ("afmpb_matvec", "afmpb_matvec_host"):
         getattr(lib, name).restype = I32
         getattr(lib, name).argtypes = [P, P, P]
+    for name in ("afmpb_sync", "afmpb_inject_wait_expiry"):
+        getattr(lib, name).restype = I32
+        getattr(lib, name).argtypes = [P]
     lib.afmpb_matvec_parts.restype = I32
     lib.afmpb_matvec_parts.argtypes = [P, P, P, I32]
     lib.afmpb_solve.restype = I32
@@ -231,7 +237,7 @@ class Handle:
     def __init__(self, xyz, tri, atoms=None, q=None, eps_in=1.0, eps_out=80.0, kappa=0.0,
                  order=6, tol=1e-6, leaf_cap=0, restart=0, max_restart=0, abs_tol=0.0,
                  precision=0, near_c=0.0, stream=None, max_level=0, normals=None, m2l_tol=0.0,
-                 charge_fmm=0):
+                 charge_fmm=0, orth=0):
         self._lib = load()
         self._xyz = _np(xyz, np.float64)
         self._tri = _np(tri, np.int32)
@@ -248,7 +254,7 @@ class Handle:
         if st is not None and not isinstance(st, int):
             st = int(getattr(st, "cuda_stream", st))
         opt = Options(int(leaf_cap), int(restart), int(max_restart), float(abs_tol), int(precision),
-                      float(near_c), st, int(max_level), float(m2l_tol), int(charge_fmm))
+                      float(near_c), st, int(max_level), float(m2l_tol), int(charge_fmm), int(orth))
         h = C.c_void_p()
         rc = self._lib.afmpb_create(C.byref(mesh), None if ch is None else C.byref(ch),
                                     float(eps_in), float(eps_out), float(kappa), int(order),
@@ -275,6 +281,14 @@ class Handle:
             y = np.empty(2 * self.n, np.float32)
         _check(self._lib.afmpb_matvec_host(self.h, _ptr(x), _ptr(y)), self.h)
         return y
+
+    def sync(self):
+        """Wait for the handle's stream; raises ETIMEOUT if a bounded device wait expired."""
+        _check(self._lib.afmpb_sync(self.h), self.h)
+
+    def inject_wait_expiry(self):
+        """Test hook: set the handle's bounded-wait flag from the host (no device fault)."""
+        _check(self._lib.afmpb_inject_wait_expiry(self.h), self.h)
 
     def profile(self, reps=5, flush=None, flush_bytes=0):
         """Per-stage product timings (ms) measured with CUDA events in the library."""
@@ -407,7 +421,7 @@ class Server:
 
     def submit(self, xyz, tri, atoms, q, eps_in=1.0, eps_out=80.0, kappa=0.0, order=6, tol=1e-6,
                precision=0, leaf_cap=0, m2l_tol=0.0, restart=0, max_restart=0, want_solution=False,
-               charge_fmm=0):
+               charge_fmm=0, orth=0):
         xyz = _np(xyz, np.float64)
         tri = _np(tri, np.int32)
         atoms = _np(np.atleast_2d(atoms), np.float64)
@@ -419,7 +433,7 @@ class Server:
                       Charges(int(q.size), atoms.ctypes.data, q.ctypes.data),
                       float(eps_in), float(eps_out), float(kappa), int(order), float(tol),
                       Options(int(leaf_cap), int(restart), int(max_restart), 0.0, int(precision), 0.0, None, 0,
-                              float(m2l_tol), int(charge_fmm)),
+                              float(m2l_tol), int(charge_fmm), int(orth)),
                       None if f is None else f.ctypes.data, None if hh is None else hh.ctypes.data)
         t = C.c_int64()
         rc = self._lib.afmpb_server_submit(self.s, C.byref(req), C.byref(t))

@@ -47,8 +47,10 @@ void destroy_handle(afmpb_t *h) {
     if (g) cudaGraphDestroy(g);
   if (h->graph_gm) cudaGraphExecDestroy(h->graph_gm);
   if (h->graph_gm_tmpl) cudaGraphDestroy(h->graph_gm_tmpl);
+  if (h->graph_cycle) cudaGraphExecDestroy(h->graph_cycle);
   h->arena.free_all();
   if (h->h_pinned) cudaFreeHost(h->h_pinned);
+  if (h->h_wait_flag) cudaFreeHost(h->h_wait_flag);
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   if (h->ev_join) cudaEventDestroy(h->ev_join);
   if (h->ev_t0) cudaEventDestroy(h->ev_t0);
@@ -180,8 +182,10 @@ Err check_params(const afmpb_mesh *mesh, double eps_in, double eps_out, double k
   if (order < 2 || order > kMaxOrder) return make_err(AFMPB_EINVAL, "fmm_order must be in [2, 8]");
   if (!(tol > 0) || !std::isfinite(tol)) return make_err(AFMPB_EINVAL, "tol must be positive");
   if (o) {
-    if ((o->leaf_cap < 0 && o->leaf_cap != AFMPB_LEAF_CAP_AUTO) || o->restart < 0 || o->max_restart < 0 || o->max_level < 0 || o->max_level > kMaxLevel)
+    if ((o->leaf_cap < 0 && o->leaf_cap != AFMPB_LEAF_CAP_AUTO) || (o->restart < 0 && o->restart != AFMPB_RESTART_NONE) ||
+        o->max_restart < 0 || o->max_level < 0 || o->max_level > kMaxLevel)
       return make_err(AFMPB_EINVAL, "negative option or max_level above 20");
+    if (o->orth != 0 && o->orth != AFMPB_ORTH_ONE_REDUCTION) return make_err(AFMPB_EINVAL, "orth must be 0 or 1");
     if (o->abs_tol < 0 || !(o->near_c >= 0)) return make_err(AFMPB_EINVAL, "abs_tol and near_c must be >= 0");
     if (o->precision != 0 && o->precision != 1) return make_err(AFMPB_EINVAL, "precision must be 0 or 1");
     if (o->restart > 4096) return make_err(AFMPB_EINVAL, "restart above 4096");
@@ -192,6 +196,8 @@ Err check_params(const afmpb_mesh *mesh, double eps_in, double eps_out, double k
 
 Err create_impl(afmpb_t *h, const afmpb_mesh *mesh, const afmpb_charges *ch) {
   auto t0 = std::chrono::steady_clock::now();
+  AFMPB_CUDA(cudaGetDevice(&h->device));
+  AFMPB_TRY(alloc_wait_flag(h));
   if (h->opt.stream) {
     h->stream = (cudaStream_t)h->opt.stream;
   } else {
@@ -324,6 +330,26 @@ Err product_from64(afmpb_t *h, cudaStream_t s, const double *v) {
   return Err{};
 }
 
+// The product's kernels from d_xs to d_ys, enqueued on a capturing stream: P2P forked onto
+// the low-priority side stream beside the far-field chain (up to kOverlapMaxNodes), then
+// the combine.  Used by the GMRES cycle graph.
+Err enqueue_product_kernels(afmpb_t *h, cudaStream_t cap) {
+  Err e;
+  if (overlap_p2p(h)) {
+    cudaEventRecord(h->ev_fork, cap);
+    cudaStreamWaitEvent(h->side, h->ev_fork, 0);
+    e = enqueue_p2p(h, h->side);
+    cudaEventRecord(h->ev_join, h->side);
+    if (e.ok()) e = enqueue_far(h, cap);
+    cudaStreamWaitEvent(cap, h->ev_join, 0);
+  } else {
+    e = enqueue_p2p(h, cap);
+    if (e.ok()) e = enqueue_far(h, cap);
+  }
+  if (e.ok()) e = enqueue_combine(h, cap, AFMPB_PART_ALL);
+  return e;
+}
+
 Err product_sorted(afmpb_t *h, cudaStream_t s, int parts) {
   if (parts <= 0 || parts > AFMPB_PART_ALL) return make_err(AFMPB_EINVAL, "parts must be a non-empty AFMPB_PART_* mask");
   if (!h->graph[parts]) AFMPB_TRY(capture_product(h, parts));
@@ -423,12 +449,32 @@ afmpb_status afmpb_create(const afmpb_mesh *mesh, const afmpb_charges *charges, 
   } AFMPB_CATCH(nullptr)
 }
 
+}  // extern "C"
+
+namespace {
+// A bounded device wait of earlier work on the handle expired (the flag is set without a
+// synchronisation once that work has finished): report it once and clear it.
+bool take_wait_expiry(afmpb_t *h) {
+  if (!h->h_wait_flag) return false;
+  volatile int *f = h->h_wait_flag;
+  if (!*f) return false;
+  *f = 0;
+  return true;
+}
+const char *kExpiredEarlier =
+    "a bounded device wait of an earlier product on this handle expired; its result is invalid "
+    "(reported once; nothing was queued by this call)";
+}  // namespace
+
+extern "C" {
+
 afmpb_status afmpb_matvec_parts(afmpb_t *h, const float *x, float *y, int parts) {
   try {
     if (!h) return fail(nullptr, make_err(AFMPB_EINVAL, "handle is NULL"));
     if (!x || !y) return fail(h, make_err(AFMPB_EINVAL, "x and y must be device pointers"));
     if (x == y) return fail(h, make_err(AFMPB_EINVAL, "x and y must not overlap"));
     if (parts <= 0 || parts > AFMPB_PART_ALL) return fail(h, make_err(AFMPB_EINVAL, "parts must be a non-empty AFMPB_PART_* mask"));
+    if (take_wait_expiry(h)) return fail(h, make_err(AFMPB_ETIMEOUT, kExpiredEarlier));
     Err e = product_io(h, parts, x, y);
     return e.ok() ? AFMPB_OK : fail(h, e);
   } AFMPB_CATCH(h)
@@ -440,6 +486,7 @@ afmpb_status afmpb_matvec_host(afmpb_t *h, const float *x, float *y) {
   try {
     if (!h) return fail(nullptr, make_err(AFMPB_EINVAL, "handle is NULL"));
     if (!x || !y) return fail(h, make_err(AFMPB_EINVAL, "x and y must be host pointers"));
+    if (take_wait_expiry(h)) return fail(h, make_err(AFMPB_ETIMEOUT, kExpiredEarlier));
     const size_t bytes = sizeof(float) * 2 * h->n;
     Err e;
     if (!h->d_xhost_stage) {
@@ -454,6 +501,31 @@ afmpb_status afmpb_matvec_host(afmpb_t *h, const float *x, float *y) {
     ce = cudaMemcpyAsync(y, h->d_yhost_stage, bytes, cudaMemcpyDeviceToHost, h->stream);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(h->stream);
     if (ce != cudaSuccess) return fail(h, make_err(AFMPB_ECUDA, std::string("D2H: ") + cudaGetErrorString(ce)));
+    if (take_wait_expiry(h))
+      return fail(h, make_err(AFMPB_ETIMEOUT, "a bounded device wait of this product expired; y is invalid"));
+    return AFMPB_OK;
+  } AFMPB_CATCH(h)
+}
+
+afmpb_status afmpb_sync(afmpb_t *h) {
+  try {
+    if (!h) return fail(nullptr, make_err(AFMPB_EINVAL, "handle is NULL"));
+    cudaError_t ce = cudaStreamSynchronize(h->stream);
+    if (ce != cudaSuccess) return fail(h, make_err(AFMPB_ECUDA, std::string("stream: ") + cudaGetErrorString(ce)));
+    if (take_wait_expiry(h))
+      return fail(h, make_err(AFMPB_ETIMEOUT, "a bounded device wait of work queued on this handle expired; "
+                                              "the products queued since the last report are invalid"));
+    return AFMPB_OK;
+  } AFMPB_CATCH(h)
+}
+
+afmpb_status afmpb_inject_wait_expiry(afmpb_t *h) {
+  try {
+    if (!h) return fail(nullptr, make_err(AFMPB_EINVAL, "handle is NULL"));
+    if (!h->h_wait_flag) return fail(h, make_err(AFMPB_ESTATE, "the handle has no wait flag"));
+    cudaError_t ce = cudaStreamSynchronize(h->stream);
+    if (ce != cudaSuccess) return fail(h, make_err(AFMPB_ECUDA, std::string("stream: ") + cudaGetErrorString(ce)));
+    *(volatile int *)h->h_wait_flag = 1;
     return AFMPB_OK;
   } AFMPB_CATCH(h)
 }
@@ -462,6 +534,7 @@ afmpb_status afmpb_solve(afmpb_t *h, double *f, double *hh, afmpb_solve_info *in
   try {
     if (!h) return fail(nullptr, make_err(AFMPB_EINVAL, "handle is NULL"));
     if (h->natoms == 0) return fail(h, make_err(AFMPB_ESTATE, "the handle was created without charges"));
+    if (take_wait_expiry(h)) return fail(h, make_err(AFMPB_ETIMEOUT, kExpiredEarlier));
     Err e = run_solve(h, info);
     if (!e.ok() && e.code != AFMPB_ENOCONV) return fail(h, e);
     if (f || hh) {
@@ -769,7 +842,7 @@ size_t afmpb_estimate_bytes(int64_t n_nodes, int64_t n_atoms, int fmm_order, con
   // the smallest candidate of the autotuner gives the most boxes
   const int cap = (o && o->leaf_cap > 0) ? o->leaf_cap
                   : (o && o->leaf_cap == AFMPB_LEAF_CAP_AUTO) ? 32 : ((o && o->precision == 1) ? 80 : 192);
-  const int m = (o && o->restart > 0) ? o->restart : 80;
+  const int m = (o && o->restart > 0) ? o->restart : (o && o->restart == AFMPB_RESTART_NONE) ? AFMPB_RESTART_NONE_MAX : 80;
   const size_t n = (size_t)n_nodes, n3 = (size_t)fmm_order * fmm_order * fmm_order;
   const size_t nbox = 3 * (n / (size_t)std::max(cap / 2, 1) + 64);
   size_t b = 0;

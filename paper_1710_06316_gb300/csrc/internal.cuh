@@ -201,6 +201,7 @@ struct __align__(16) TCUnit {
 struct afmpb_t {
   // ---- parameters -------------------------------------------------------------------
   int64_t n = 0, nt = 0, natoms = 0;
+  int device = 0;                  // CUDA device current at create time
   double eps_in = 1, eps_out = 1, kappa = 0, ebar = 1, alpha = 1, tol = 1e-6;
   int order = 6, ncoef = 216;
   afmpb_options opt{};
@@ -247,6 +248,8 @@ struct afmpb_t {
   int64_t *d_p2p_ptr = nullptr;    // [nleaf+1] lists 1 + 3 per leaf (leaf order)
   int32_t *d_p2p_idx = nullptr;
   int32_t *d_p2p_order = nullptr;  // [nleaf] P2P blocks, most work first (leaf order)
+  int4 *d_p2p_units = nullptr;     // [p2p_nunits] P2P work units (leaf, first, end target), most work first
+  int p2p_nunits = 0;
   std::vector<int32_t> h_xbox;     // boxes with a non-empty list 4
   int32_t *d_xbox = nullptr;
 
@@ -293,7 +296,9 @@ struct afmpb_t {
   afmpb::TCItem *d_tc_items = nullptr;  // work items: (group, first pair, pair count)
   uint16_t *d_tc_tiles = nullptr;  // BF16 hi/lo translation tiles in the MMA operand layout
   int *d_tc_level_table = nullptr; // level -> Yukawa tile table
-  int *d_tc_flag = nullptr;        // set by a tensor-core CTA whose bounded wait expired
+  int *d_tc_flag = nullptr;        // device alias of h_wait_flag (the kernels' error flag)
+  int *h_wait_flag = nullptr;      // mapped pinned host int, set by a CTA whose bounded wait
+                                   // expired; read (and cleared) by the host after the work
   bool tc_pipelined = false;       // the warp-specialized persistent kernel is used
   int tc_nunits = 0;
   afmpb::TCUnit *d_tc_units = nullptr;  // work units of the pipelined kernel
@@ -332,6 +337,9 @@ struct afmpb_t {
   double *d_V = nullptr, *d_w = nullptr, *d_H = nullptr, *d_g = nullptr, *d_cs = nullptr,
          *d_sn = nullptr, *d_part = nullptr, *d_hcol = nullptr, *d_hcol2 = nullptr, *d_scal = nullptr;
   double *h_pinned = nullptr;
+  int *d_gm_int = nullptr;         // [4] device step state: j, Arnoldi steps, second-pass flag, second passes
+  cudaGraphExec_t graph_cycle = nullptr;   // one GMRES cycle: a graph WHILE loop over Arnoldi steps
+  int cycle_m = 0, cycle_orth = -1;        // restart length and orthogonalisation the cycle graph was built for
   // Laplace FMM over nodes and charges for the right-hand side and the energy (owned)
   afmpb_t *cf = nullptr;
 };
@@ -358,6 +366,9 @@ int autotune_cached_cap(int precision, int order, double kappa, int64_t n);   //
 // m2l_svd.cu: compressed translations; *compressed = false leaves the full ones in use
 Err build_m2l_svd(afmpb_t *h, bool *compressed);
 Err enqueue_m2l_svd(afmpb_t *h, cudaStream_t s, StageTimer *tm = nullptr);   // compress, translate, expand
+Err alloc_wait_flag(afmpb_t *h);       // the mapped error flag of the bounded waits (once per handle)
+// Waits for the handle's stream, then reports (and clears) the bounded-wait flag: *flag = 1
+// when a wait of work queued on the handle expired since the last report.
 Err read_tc_error(afmpb_t *h, int *flag);
 Err selftest_bounded_wait(int spin_limit, int *expired);   // m2l_tc.cu             // 1 when a tensor-core wait expired
 // solve.cu
@@ -379,6 +390,7 @@ Err charge_fmm_phi(afmpb_t *h, double *phi);     // reaction potential at the ch
 Err run_energy_noalloc(afmpb_t *h, double *E);      // static scratch, no allocation
 // capi.cu
 Err product_sorted(afmpb_t *h, cudaStream_t s, int parts);  // d_xs -> d_ys
+Err enqueue_product_kernels(afmpb_t *h, cudaStream_t cap);   // d_xs -> d_ys on a capturing stream
 
 // launch helpers
 inline int div_up(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }

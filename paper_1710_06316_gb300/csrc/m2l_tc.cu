@@ -621,8 +621,7 @@ Err build_m2l_tc(afmpb_t *h) {
   AFMPB_TRY(A.alloc(&d_table_level, table_level.size(), "table level"));
   AFMPB_TRY(A.alloc(&h->d_tc_level_table, level_table.size(), "level table"));
   AFMPB_TRY(A.alloc(&h->d_tc_items, items.size(), "tc items"));
-  AFMPB_TRY(A.alloc(&h->d_tc_flag, 1, "tc flag"));
-  AFMPB_CUDA(cudaMemsetAsync(h->d_tc_flag, 0, sizeof(int), s));
+  AFMPB_TRY(alloc_wait_flag(h));
   AFMPB_CUDA(cudaMemcpyAsync(d_table_level, table_level.data(), sizeof(int) * table_level.size(), cudaMemcpyHostToDevice, s));
   AFMPB_CUDA(cudaMemcpyAsync(h->d_tc_level_table, level_table.data(), sizeof(int) * level_table.size(),
                              cudaMemcpyHostToDevice, s));
@@ -728,11 +727,33 @@ Err selftest_bounded_wait(int spin_limit, int *expired) {
   return Err{};
 }
 
+// The flag lives in mapped pinned host memory: kernels write it through its device alias
+// only when a wait expires, and the host reads it without a copy once the work is done.
+Err alloc_wait_flag(afmpb_t *h) {
+  if (h->h_wait_flag) return Err{};
+  void *p = nullptr;
+  cudaError_t e = cudaHostAlloc(&p, sizeof(int), cudaHostAllocMapped);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return make_err(AFMPB_ENOMEM, std::string("cudaHostAlloc (wait flag): ") + cudaGetErrorString(e));
+  }
+  h->h_wait_flag = static_cast<int *>(p);
+  *h->h_wait_flag = 0;
+  void *d = nullptr;
+  AFMPB_CUDA(cudaHostGetDevicePointer(&d, p, 0));
+  h->d_tc_flag = static_cast<int *>(d);
+  return Err{};
+}
+
 Err read_tc_error(afmpb_t *h, int *flag) {
   *flag = 0;
-  if (!h->d_tc_flag) return Err{};
-  AFMPB_CUDA(cudaMemcpyAsync(flag, h->d_tc_flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  if (!h->h_wait_flag) return Err{};
   AFMPB_CUDA(cudaStreamSynchronize(h->stream));
+  volatile int *f = h->h_wait_flag;
+  if (*f) {
+    *flag = 1;
+    *f = 0;
+  }
   return Err{};
 }
 

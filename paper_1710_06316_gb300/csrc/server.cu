@@ -51,6 +51,7 @@ struct Done {
 struct afmpb_server_t {
   size_t budget = 0;
   int max_slots = 0;
+  int device = 0;                 // the creator's current device: every slot runs there
   Clock::time_point t0;
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
@@ -95,7 +96,7 @@ void run_job(afmpb_server_t *s, Job &j, cudaStream_t stream, afmpb_result &r) {
   // plus the GMRES basis and work vectors still to come, whichever is larger.
   afmpb_info pre{};
   if (afmpb_get_info(h, &pre) == AFMPB_OK) {
-    const size_t m = (size_t)(opt.restart > 0 ? opt.restart : 80);
+    const size_t m = (size_t)(opt.restart > 0 ? opt.restart : opt.restart == AFMPB_RESTART_NONE ? AFMPB_RESTART_NONE_MAX : 80);
     const size_t n2 = 2 * (size_t)j.n_nodes;
     const size_t gmres = (m + 1) * n2 * 8 + 16 * n2 * 8 + (16u << 20);
     const size_t need = std::max((size_t)pre.device_bytes_peak, (size_t)pre.device_bytes + gmres);
@@ -116,8 +117,10 @@ void run_job(afmpb_server_t *s, Job &j, cudaStream_t stream, afmpb_result &r) {
 }
 
 void slot_main(afmpb_server_t *s, int slot) {
+  // a new thread starts on device 0: take the creator's device before any CUDA call
   cudaStream_t stream = nullptr;
-  const bool have_stream = cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking) == cudaSuccess;
+  const bool have_stream = cudaSetDevice(s->device) == cudaSuccess &&
+                           cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking) == cudaSuccess;
   for (;;) {
     std::unique_ptr<Job> j;
     {
@@ -144,7 +147,7 @@ void slot_main(afmpb_server_t *s, int slot) {
       }
     } else {
       r.status = AFMPB_ECUDA;
-      std::strncpy(r.error, "slot stream creation failed", sizeof(r.error) - 1);
+      std::strncpy(r.error, "slot device selection or stream creation failed", sizeof(r.error) - 1);
     }
     r.t_done = s->now();
     {
@@ -183,6 +186,10 @@ afmpb_status afmpb_server_create(size_t bytes_budget, int max_slots, afmpb_serve
   s->budget = bytes_budget;
   s->max_slots = max_slots;
   s->t0 = Clock::now();
+  if (cudaGetDevice(&s->device) != cudaSuccess) {   // no device: every request fails at its slot
+    cudaGetLastError();
+    s->device = 0;
+  }
   try {
     for (int i = 0; i < max_slots; ++i) s->slots.emplace_back(slot_main, s, i);
   } catch (...) {
@@ -275,8 +282,22 @@ afmpb_status afmpb_server_wait(afmpb_server_t *s, int64_t ticket, double timeout
   std::unique_lock<std::mutex> lk(s->mu);
   auto it = s->results.find(ticket);
   if (it == s->results.end()) return AFMPB_EINVAL;
-  const auto limit = Clock::now() + std::chrono::duration_cast<Clock::duration>(std::chrono::duration<double>(timeout_s));
-  if (!s->cv_done.wait_until(lk, limit, [&] { return s->results[ticket].ready; })) return AFMPB_ETIMEOUT;
+  // The entry may be taken by another thread's poll or wait meanwhile: look it up, never
+  // insert it, and report a ticket that disappeared as unknown.
+  bool gone = false;
+  auto ready = [&] {
+    auto jt = s->results.find(ticket);
+    gone = jt == s->results.end();
+    return gone || jt->second.ready;
+  };
+  constexpr double kMaxWait = 1e6;                    // seconds; longer waits (or inf) wait without a limit
+  if (timeout_s >= kMaxWait) {
+    s->cv_done.wait(lk, ready);
+  } else {
+    const auto limit = Clock::now() + std::chrono::duration_cast<Clock::duration>(std::chrono::duration<double>(timeout_s));
+    if (!s->cv_done.wait_until(lk, limit, ready)) return AFMPB_ETIMEOUT;
+  }
+  if (gone) return AFMPB_EINVAL;
   it = s->results.find(ticket);
   *res = it->second.res;
   s->results.erase(it);

@@ -141,16 +141,6 @@ __global__ void k_reduce_parts(int nblk, int nv, const double *__restrict__ part
   }
 }
 
-// w -= sum_i c_i V_i   (c on the device)
-__global__ void k_sub_combo(int64_t len, int nv, const double *__restrict__ V, int64_t ldv,
-                            const double *__restrict__ c, double sign, double *__restrict__ w) {
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < len; k += (int64_t)gridDim.x * blockDim.x) {
-    double s = 0.0;
-    for (int i = 0; i < nv; ++i) s = fma(c[i], V[(int64_t)i * ldv + k], s);
-    w[k] += sign * s;
-  }
-}
-
 // v = w / nrm (nrm on the device); also writes the FP32 (f, h) product input
 __global__ void k_normalize(int64_t n, const double *__restrict__ w, const double *__restrict__ nrm,
                             double *__restrict__ v, float2 *__restrict__ xs) {
@@ -181,39 +171,6 @@ __global__ void k_from_ys(int64_t len, const float *__restrict__ ys, const doubl
   int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (k >= len) return;
   w[k] = b ? b[k] - (double)ys[k] : (double)ys[k];
-}
-
-// Givens update of Hessenberg column j (hcol[0..j+1]); H column-major (m+1) x m.
-__global__ void k_givens(int j, int m, const double *__restrict__ hcol, double *__restrict__ H,
-                         double *__restrict__ cs, double *__restrict__ sn, double *__restrict__ g,
-                         double *__restrict__ res) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  double *col = H + (int64_t)j * (m + 1);
-  for (int i = 0; i <= j + 1; ++i) col[i] = hcol[i];
-  for (int i = 0; i < j; ++i) {
-    const double a = col[i], b = col[i + 1];
-    col[i] = cs[i] * a + sn[i] * b;
-    col[i + 1] = -sn[i] * a + cs[i] * b;
-  }
-  const double a = col[j], b = col[j + 1];
-  const double den = hypot(a, b);
-  cs[j] = den > 0 ? a / den : 1.0;
-  sn[j] = den > 0 ? b / den : 0.0;
-  col[j] = den;
-  col[j + 1] = 0.0;
-  g[j + 1] = -sn[j] * g[j];
-  g[j] = cs[j] * g[j];
-  res[0] = fabs(g[j + 1]);
-}
-
-// back substitution H(0:k,0:k) y = g(0:k), y written over g
-__global__ void k_backsolve(int k, int m, const double *__restrict__ H, double *__restrict__ g) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  for (int i = k - 1; i >= 0; --i) {
-    double s = g[i];
-    for (int c = i + 1; c < k; ++c) s -= H[(int64_t)c * (m + 1) + i] * g[c];
-    g[i] = s / H[(int64_t)i * (m + 1) + i];
-  }
 }
 
 __global__ void k_set_beta(double *__restrict__ g, int m, const double *__restrict__ beta) {
@@ -323,13 +280,290 @@ Err norm2(afmpb_t *h, int64_t len, const double *w, double *out) { return multid
 
 }  // namespace
 
-__global__ void k_add_small(int k, const double *__restrict__ a, double *__restrict__ b) {
-  for (int i = threadIdx.x; i < k; i += blockDim.x) b[i] += a[i];
+// ---- the Arnoldi step as step-indexed kernels --------------------------------------------
+// One captured Arnoldi step serves every step of a cycle: the kernels read the step index
+// j from device memory (gm[0]) instead of taking it as a launch parameter, and the last
+// kernel of the step advances j and sets the condition of the graph WHILE loop that runs
+// the steps.  gm[1] counts the steps, gm[2] is the second-pass flag of the one-reduction
+// form (the guarded kernels return at once while it is 0) and gm[3] counts second passes.
+// Reorthogonalise when ||w - V h|| < kReorthTol ||w||: the test the FP64 reference GMRES
+// applies to its second Gram-Schmidt pass.
+constexpr double kReorthTol = 1e-3;
+
+__global__ void k_to_xs_j(int64_t n, const double *__restrict__ V, int64_t n2, const int *__restrict__ gm,
+                          float2 *__restrict__ xs) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  const double *v = V + (int64_t)gm[0] * n2;
+  xs[p] = make_float2((float)v[p], (float)v[n + p]);
 }
+
+// part[blk * stride + i] = block's share of V_i . w for i < j + 1, and of w . w at i = j + 1
+// when self_dot == 1 (self_dot == 2: w . w alone, at i = 0); returns at once when guard is
+// set and *guard == 0.
+__global__ void __launch_bounds__(kRedThreads) k_multidot_j(int64_t len, const int *__restrict__ gm,
+                                                            const double *__restrict__ V, int64_t ldv,
+                                                            const double *__restrict__ w, double *__restrict__ part,
+                                                            int stride, int self_dot, const int *__restrict__ guard) {
+  if (guard && *guard == 0) return;
+  __shared__ double sh[32];
+  const int nv = self_dot == 2 ? 0 : gm[0] + 1;        // 2: w . w alone, at index 0
+  const int64_t chunk = (len + gridDim.x - 1) / gridDim.x;
+  const int64_t lo = blockIdx.x * chunk, hi = min(len, lo + chunk);
+  for (int i = 0; i < nv + (self_dot ? 1 : 0); ++i) {
+    const double *v = i < nv ? V + (int64_t)i * ldv : w;
+    double s = 0.0;
+    for (int64_t k = lo + threadIdx.x; k < hi; k += blockDim.x) s = fma(v[k], w[k], s);
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) part[(int64_t)blockIdx.x * stride + i] = s;
+  }
+}
+
+// out[i] = sum_blk part[blk * stride + i] for i < j + 1 + extra (fixed order)
+__global__ void k_reduce_parts_j(int nblk, const int *__restrict__ gm, int extra, const double *__restrict__ part,
+                                 int stride, double *__restrict__ out, const int *__restrict__ guard) {
+  if (guard && *guard == 0) return;
+  __shared__ double sh[32];
+  const int i = blockIdx.x;
+  if (i >= gm[0] + 1 + extra) return;
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += part[(int64_t)b * stride + i];
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) out[i] = s;
+}
+
+// w -= sum_{i <= j} c_i V_i
+__global__ void k_sub_combo_j(int64_t len, const int *__restrict__ gm, const double *__restrict__ V, int64_t ldv,
+                              const double *__restrict__ c, double *__restrict__ w, const int *__restrict__ guard) {
+  if (guard && *guard == 0) return;
+  const int nv = gm[0] + 1;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < len; k += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int i = 0; i < nv; ++i) s = fma(c[i], V[(int64_t)i * ldv + k], s);
+    w[k] -= s;
+  }
+}
+
+__global__ void k_add_small_j(const int *__restrict__ gm, const double *__restrict__ a, double *__restrict__ b,
+                              const int *__restrict__ guard) {
+  if (guard && *guard == 0) return;
+  for (int i = threadIdx.x; i < gm[0] + 1; i += blockDim.x) b[i] += a[i];
+}
+
+// hcol[j + 1] = sqrt(sum_blk part[blk * stride])  (the norm of w after the last pass)
+__global__ void k_norm_to_j(int nblk, const double *__restrict__ part, int stride, const int *__restrict__ gm,
+                            double *__restrict__ hcol, const int *__restrict__ guard) {
+  if (guard && *guard == 0) return;
+  __shared__ double sh[32];
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += part[(int64_t)b * stride];
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) hcol[gm[0] + 1] = sqrt(s);
+}
+
+// One-reduction form: hcol[0..j] = V^T w and hcol[j+1] = ||w||^2 from the fused reduction.
+// ||w - V h||^2 = ||w||^2 - ||h||^2 (Pythagoras, V orthonormal); below kReorthTol^2 ||w||^2
+// the difference has lost its digits and the orthogonality is in doubt: flag a second pass.
+__global__ void k_pythagoras_j(int *__restrict__ gm, double *__restrict__ hcol) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int j = gm[0];
+  const double wsq = hcol[j + 1];
+  double hsq = 0.0;
+  for (int i = 0; i <= j; ++i) hsq = fma(hcol[i], hcol[i], hsq);
+  const double rest = wsq - hsq;
+  if (rest > kReorthTol * kReorthTol * wsq) {
+    hcol[j + 1] = sqrt(rest);
+    gm[2] = 0;
+  } else {
+    gm[2] = 1;
+    gm[3] += 1;
+  }
+}
+
+// V_{j+1} = w / hcol[j+1]
+__global__ void k_normalize_j(int64_t n, const double *__restrict__ w, const double *__restrict__ hcol,
+                              const int *__restrict__ gm, double *__restrict__ V, int64_t n2) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  const int j = gm[0];
+  const double inv = 1.0 / hcol[j + 1];
+  double *v = V + (int64_t)(j + 1) * n2;
+  v[p] = w[p] * inv;
+  v[n + p] = w[n + p] * inv;
+}
+
+// Givens update of Hessenberg column j (as k_givens, j from the device)
+__global__ void k_givens_j(const int *__restrict__ gm, int m, const double *__restrict__ hcol, double *__restrict__ H,
+                           double *__restrict__ cs, double *__restrict__ sn, double *__restrict__ g,
+                           double *__restrict__ res) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int j = gm[0];
+  double *col = H + (int64_t)j * (m + 1);
+  for (int i = 0; i <= j + 1; ++i) col[i] = hcol[i];
+  for (int i = 0; i < j; ++i) {
+    const double a = col[i], b = col[i + 1];
+    col[i] = cs[i] * a + sn[i] * b;
+    col[i + 1] = -sn[i] * a + cs[i] * b;
+  }
+  const double a = col[j], b = col[j + 1];
+  const double den = hypot(a, b);
+  cs[j] = den > 0 ? a / den : 1.0;
+  sn[j] = den > 0 ? b / den : 0.0;
+  col[j] = den;
+  col[j + 1] = 0.0;
+  g[j + 1] = -sn[j] * g[j];
+  g[j] = cs[j] * g[j];
+  res[0] = fabs(g[j + 1]);
+}
+
+// End of a step: j += 1; continue the WHILE loop while the Givens residual estimate is
+// above the tolerance of Eq. 7 and the basis has room.
+__global__ void k_step_end(int *__restrict__ gm, int m, const double *__restrict__ res, const double *__restrict__ tol,
+                           cudaGraphConditionalHandle loop) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int j = gm[0] + 1;
+  gm[0] = j;
+  gm[1] += 1;
+  const double r = res[0];
+  const bool go = j < m && r > tol[0];      // a NaN residual stops as well
+  cudaGraphSetConditional(loop, go ? 1u : 0u);
+}
+
+// back substitution H(0:k,0:k) y = g(0:k), k = gm[0] steps of the cycle, y over g
+__global__ void k_backsolve_j(const int *__restrict__ gm, int m, const double *__restrict__ H, double *__restrict__ g) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int k = gm[0];
+  for (int i = k - 1; i >= 0; --i) {
+    double s = g[i];
+    for (int c = i + 1; c < k; ++c) s -= H[(int64_t)c * (m + 1) + i] * g[c];
+    g[i] = s / H[(int64_t)i * (m + 1) + i];
+  }
+}
+
+// x += sum_{i < k} y_i V_i, k = gm[0]
+__global__ void k_update_x(int64_t len, const int *__restrict__ gm, const double *__restrict__ V, int64_t ldv,
+                           const double *__restrict__ y, double *__restrict__ x) {
+  const int k = gm[0];
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < len; p += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int i = 0; i < k; ++i) s = fma(y[i], V[(int64_t)i * ldv + p], s);
+    x[p] += s;
+  }
+}
+
+__global__ void k_cycle_start(int *__restrict__ gm) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    gm[0] = 0;
+    gm[2] = 0;
+  }
+}
+
+namespace {
+
+// Krylov dimension of the no-restart mode: the largest whose basis fits in half of the
+// free device memory, at most AFMPB_RESTART_NONE_MAX.
+Err restart_length(afmpb_t *h, int *m) {
+  if (h->opt.restart != AFMPB_RESTART_NONE) {
+    *m = h->opt.restart;
+    return Err{};
+  }
+  if (h->gm_m > 0 && h->d_V) {                 // keep the basis of an earlier solve
+    *m = h->gm_m;
+    return Err{};
+  }
+  size_t free_b = 0, total_b = 0;
+  AFMPB_CUDA(cudaMemGetInfo(&free_b, &total_b));
+  const size_t per = sizeof(double) * 2 * (size_t)h->n;
+  const size_t fit = free_b / 2 / per;
+  *m = (int)std::max<size_t>(2, std::min<size_t>(AFMPB_RESTART_NONE_MAX, fit > 1 ? fit - 1 : 1));
+  return Err{};
+}
+
+// The cycle graph: a WHILE node whose body is one Arnoldi step (the FP32 product of V_j,
+// orthogonalisation, normalisation, Givens update, stop test).
+Err build_cycle_graph(afmpb_t *h, int m) {
+  const int64_t n = h->n, n2 = 2 * n;
+  const int orth = h->opt.orth;
+  if (h->graph_cycle) {
+    cudaGraphExecDestroy(h->graph_cycle);
+    h->graph_cycle = nullptr;
+  }
+  cudaGraph_t g = nullptr;
+  AFMPB_CUDA(cudaGraphCreate(&g, 0));
+  struct GraphGuard { cudaGraph_t g; ~GraphGuard() { if (g) cudaGraphDestroy(g); } } gg{g};
+  cudaGraphConditionalHandle loop;
+  AFMPB_CUDA(cudaGraphConditionalHandleCreate(&loop, g, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = loop;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node = nullptr;
+  AFMPB_CUDA(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  int lo = 0, hi = 0;
+  AFMPB_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+  cudaStream_t cap = nullptr;
+  AFMPB_CUDA(cudaStreamCreateWithPriority(&cap, cudaStreamNonBlocking, hi));
+  struct StreamGuard { cudaStream_t s; ~StreamGuard() { cudaStreamDestroy(s); } } sg{cap};
+  AFMPB_CUDA(cudaStreamBeginCaptureToGraph(cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  const int *gm = h->d_gm_int;
+  int *gmw = h->d_gm_int;
+  const int *guard = gm + 2;
+  const int nb = red_blocks(n2), stride = m + 2;
+  const int nb_el = div_up(n, 256), nb_el2 = div_up(n2, 256);
+  const int nb_comb = std::min(nb_el2, 4 * 1184);
+  Err e;
+  k_to_xs_j<<<nb_el, 256, 0, cap>>>(n, h->d_V, n2, gm, h->d_xs);
+  e = check_launch("k_to_xs_j");
+  if (e.ok()) e = enqueue_product_kernels(h, cap);
+  if (e.ok()) {
+    k_from_ys<<<nb_el2, 256, 0, cap>>>(n2, h->d_ys, nullptr, h->d_w);
+    if (orth == 0) {      // classical Gram-Schmidt twice, then the norm: three reductions
+      k_multidot_j<<<nb, kRedThreads, 0, cap>>>(n2, gm, h->d_V, n2, h->d_w, h->d_part, stride, 0, nullptr);
+      k_reduce_parts_j<<<m + 1, 256, 0, cap>>>(nb, gm, 0, h->d_part, stride, h->d_hcol, nullptr);
+      k_sub_combo_j<<<nb_comb, 256, 0, cap>>>(n2, gm, h->d_V, n2, h->d_hcol, h->d_w, nullptr);
+      k_multidot_j<<<nb, kRedThreads, 0, cap>>>(n2, gm, h->d_V, n2, h->d_w, h->d_part, stride, 0, nullptr);
+      k_reduce_parts_j<<<m + 1, 256, 0, cap>>>(nb, gm, 0, h->d_part, stride, h->d_hcol2, nullptr);
+      k_sub_combo_j<<<nb_comb, 256, 0, cap>>>(n2, gm, h->d_V, n2, h->d_hcol2, h->d_w, nullptr);
+      k_add_small_j<<<1, 128, 0, cap>>>(gm, h->d_hcol2, h->d_hcol, nullptr);
+      k_multidot<<<nb, kRedThreads, 0, cap>>>(n2, 1, h->d_w, 0, h->d_w, h->d_part, stride);
+      k_norm_to_j<<<1, 256, 0, cap>>>(nb, h->d_part, stride, gm, h->d_hcol, nullptr);
+    } else {              // one fused reduction; a guarded second pass on loss of orthogonality
+      k_multidot_j<<<nb, kRedThreads, 0, cap>>>(n2, gm, h->d_V, n2, h->d_w, h->d_part, stride, 1, nullptr);
+      k_reduce_parts_j<<<m + 2, 256, 0, cap>>>(nb, gm, 1, h->d_part, stride, h->d_hcol, nullptr);
+      k_sub_combo_j<<<nb_comb, 256, 0, cap>>>(n2, gm, h->d_V, n2, h->d_hcol, h->d_w, nullptr);
+      k_pythagoras_j<<<1, 1, 0, cap>>>(gmw, h->d_hcol);
+      k_multidot_j<<<nb, kRedThreads, 0, cap>>>(n2, gm, h->d_V, n2, h->d_w, h->d_part, stride, 0, guard);
+      k_reduce_parts_j<<<m + 1, 256, 0, cap>>>(nb, gm, 0, h->d_part, stride, h->d_hcol2, guard);
+      k_sub_combo_j<<<nb_comb, 256, 0, cap>>>(n2, gm, h->d_V, n2, h->d_hcol2, h->d_w, guard);
+      k_add_small_j<<<1, 128, 0, cap>>>(gm, h->d_hcol2, h->d_hcol, guard);
+      k_multidot_j<<<nb, kRedThreads, 0, cap>>>(n2, gm, h->d_V, n2, h->d_w, h->d_part, stride, 2, guard);
+      k_norm_to_j<<<1, 256, 0, cap>>>(nb, h->d_part, stride, gm, h->d_hcol, guard);
+    }
+    k_normalize_j<<<nb_el, 256, 0, cap>>>(n, h->d_w, h->d_hcol, gm, h->d_V, n2);
+    k_givens_j<<<1, 1, 0, cap>>>(gm, m, h->d_hcol, h->d_H, h->d_cs, h->d_sn, h->d_g, h->d_scal + 2);
+    k_step_end<<<1, 1, 0, cap>>>(gmw, m, h->d_scal + 2, h->d_scal + 4, loop);
+    e = check_launch("arnoldi step");
+  }
+  cudaGraph_t out = nullptr;
+  cudaError_t ce = cudaStreamEndCapture(cap, &out);
+  if (!e.ok()) return e;
+  if (ce != cudaSuccess) return make_err(AFMPB_ECUDA, std::string("cudaStreamEndCapture (cycle): ") + cudaGetErrorString(ce));
+  ce = cudaGraphInstantiate(&h->graph_cycle, g, 0);
+  if (ce != cudaSuccess) return make_err(AFMPB_ECUDA, std::string("cudaGraphInstantiate (cycle): ") + cudaGetErrorString(ce));
+  h->cycle_m = m;
+  h->cycle_orth = orth;
+  return Err{};
+}
+
+}  // namespace
 
 Err run_solve(afmpb_t *h, afmpb_solve_info *info) {
   const int64_t n = h->n, n2 = 2 * n;
-  const int m = h->opt.restart, max_restart = h->opt.max_restart;
+  int m = 0;
+  AFMPB_TRY(restart_length(h, &m));
+  const int max_restart = h->opt.max_restart;
   cudaStream_t s = h->stream;
   auto &A = h->arena;
   if (h->gm_m != m || !h->d_V) {
@@ -349,44 +583,37 @@ Err run_solve(afmpb_t *h, afmpb_solve_info *info) {
     AFMPB_TRY(A.alloc(&h->d_hcol, m + 2, "gmres hcol"));
     AFMPB_TRY(A.alloc(&h->d_hcol2, m + 2, "gmres hcol2"));
     AFMPB_TRY(A.alloc(&h->d_scal, 8, "gmres scalars"));
+    if (!h->d_gm_int) AFMPB_TRY(A.alloc(&h->d_gm_int, 4, "gmres step state"));
     if (!h->h_pinned) AFMPB_CUDA(cudaMallocHost(&h->h_pinned, 8 * sizeof(double)));
   }
+  if (!h->graph_cycle || h->cycle_m != m || h->cycle_orth != h->opt.orth) AFMPB_TRY(build_cycle_graph(h, m));
   if (!h->d_sol) AFMPB_TRY(A.alloc(&h->d_sol, n2, "solution"));
   double *x = h->d_sol;
   volatile double *hp = h->h_pinned;
   const int nb_el = div_up(n, 256), nb_el2 = div_up(n2, 256);
   const int nb_comb = std::min(nb_el2, 4 * 1184);
-  double ms_mv = 0.0;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   AFMPB_CUDA(cudaEventCreate(&e0));
   AFMPB_CUDA(cudaEventCreate(&e1));
   struct EvGuard { cudaEvent_t a, b; ~EvGuard() { cudaEventDestroy(a); cudaEventDestroy(b); } } guard{e0, e1};
   AFMPB_CUDA(cudaEventRecord(h->ev_t0, s));
-  auto timed_product = [&](const double *v) -> Err {   // d_ys = L v (one graph launch)
-    AFMPB_CUDA(cudaEventRecord(e0, s));
-    AFMPB_TRY(product_from64(h, s, v));
-    AFMPB_CUDA(cudaEventRecord(e1, s));
-    return Err{};
-  };
   auto read_scalar = [&](const double *d, int slot) -> Err {
     AFMPB_CUDA(cudaMemcpyAsync((double *)hp + slot, d, sizeof(double), cudaMemcpyDeviceToHost, s));
     AFMPB_CUDA(cudaStreamSynchronize(s));
     return Err{};
   };
-  auto add_mv_time = [&]() -> Err {
-    float t = 0.f;
-    AFMPB_CUDA(cudaEventElapsedTime(&t, e0, e1));
-    ms_mv += t;
-    return Err{};
-  };
+  int h_gm[4] = {0, 0, 0, 0};
 
   AFMPB_TRY(norm2(h, n2, h->d_b, h->d_scal + 0));
   AFMPB_TRY(read_scalar(h->d_scal + 0, 0));
   const double bnorm = hp[0];
   h->bnorm = bnorm;
   const double tol = h->tol * bnorm + h->opt.abs_tol;
+  hp[4] = tol;
+  AFMPB_CUDA(cudaMemcpyAsync(h->d_scal + 4, (const double *)hp + 4, sizeof(double), cudaMemcpyHostToDevice, s));
+  AFMPB_CUDA(cudaMemsetAsync(h->d_gm_int, 0, 4 * sizeof(int), s));
   AFMPB_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n2, s));
-  int iters = 0, restarts = 0;
+  int restarts = 0, products = 0;
   bool converged = false;
   double res = bnorm;
   for (int cycle = 0; cycle <= max_restart && !converged; ++cycle) {
@@ -394,13 +621,13 @@ Err run_solve(afmpb_t *h, afmpb_solve_info *info) {
       AFMPB_CUDA(cudaMemcpyAsync(h->d_w, h->d_b, sizeof(double) * n2, cudaMemcpyDeviceToDevice, s));
     } else {
       ++restarts;
-      AFMPB_TRY(timed_product(x));
+      ++products;
+      AFMPB_TRY(product_from64(h, s, x));
       k_from_ys<<<nb_el2, 256, 0, s>>>(n2, h->d_ys, h->d_b, h->d_w);
       AFMPB_TRY(check_launch("residual"));
     }
     AFMPB_TRY(norm2(h, n2, h->d_w, h->d_scal + 1));
     AFMPB_TRY(read_scalar(h->d_scal + 1, 1));
-    if (cycle > 0) AFMPB_TRY(add_mv_time());
     res = hp[1];
     if (!(res > tol)) {
       converged = !std::isnan(res);
@@ -408,63 +635,53 @@ Err run_solve(afmpb_t *h, afmpb_solve_info *info) {
     }
     k_normalize<<<nb_el, 256, 0, s>>>(n, h->d_w, h->d_scal + 1, h->d_V, nullptr);
     k_set_beta<<<1, 1, 0, s>>>(h->d_g, m, h->d_scal + 1);
+    k_cycle_start<<<1, 1, 0, s>>>(h->d_gm_int);
     AFMPB_TRY(check_launch("gmres start"));
-    int k = 0;
-    for (int j = 0; j < m; ++j) {
-      AFMPB_TRY(timed_product(h->d_V + (size_t)j * n2));
-      k_from_ys<<<nb_el2, 256, 0, s>>>(n2, h->d_ys, nullptr, h->d_w);
-      // classical Gram-Schmidt applied twice
-      AFMPB_TRY(multidot(h, n2, j + 1, h->d_V, n2, h->d_w, h->d_hcol, 0));
-      k_sub_combo<<<nb_comb, 256, 0, s>>>(n2, j + 1, h->d_V, n2, h->d_hcol, -1.0, h->d_w);
-      AFMPB_TRY(multidot(h, n2, j + 1, h->d_V, n2, h->d_w, h->d_hcol2, 0));
-      k_sub_combo<<<nb_comb, 256, 0, s>>>(n2, j + 1, h->d_V, n2, h->d_hcol2, -1.0, h->d_w);
-      k_add_small<<<1, 128, 0, s>>>(j + 1, h->d_hcol2, h->d_hcol);
-      AFMPB_TRY(norm2(h, n2, h->d_w, h->d_hcol + j + 1));
-      k_normalize<<<nb_el, 256, 0, s>>>(n, h->d_w, h->d_hcol + j + 1, h->d_V + (size_t)(j + 1) * n2, nullptr);
-      k_givens<<<1, 1, 0, s>>>(j, m, h->d_hcol, h->d_H, h->d_cs, h->d_sn, h->d_g, h->d_scal + 2);
-      AFMPB_TRY(check_launch("arnoldi"));
-      AFMPB_TRY(read_scalar(h->d_scal + 2, 2));
-      AFMPB_TRY(add_mv_time());
-      res = hp[2];
-      ++iters;
-      k = j + 1;
-      if (!(res > tol)) {
-        converged = !std::isnan(res);
-        break;
-      }
-    }
+    // the Arnoldi steps of the cycle: one graph launch, no host synchronisation inside
+    AFMPB_CUDA(cudaGraphLaunch(h->graph_cycle, s));
     // x += V y, H y = g
-    k_backsolve<<<1, 1, 0, s>>>(k, m, h->d_H, h->d_g);
-    k_sub_combo<<<nb_comb, 256, 0, s>>>(n2, k, h->d_V, n2, h->d_g, 1.0, x);
+    k_backsolve_j<<<1, 1, 0, s>>>(h->d_gm_int, m, h->d_H, h->d_g);
+    k_update_x<<<nb_comb, 256, 0, s>>>(n2, h->d_gm_int, h->d_V, n2, h->d_g, x);
     AFMPB_TRY(check_launch("gmres update"));
+    AFMPB_CUDA(cudaMemcpyAsync(h_gm, h->d_gm_int, sizeof(h_gm), cudaMemcpyDeviceToHost, s));
+    AFMPB_TRY(read_scalar(h->d_scal + 2, 2));
+    res = hp[2];
+    products += h_gm[0];
+    if (!(res > tol)) converged = !std::isnan(res);
   }
-  // true residual with one more product
-  AFMPB_TRY(timed_product(x));
+  // true residual with one more product (its CUDA-event time stands for every product)
+  AFMPB_CUDA(cudaEventRecord(e0, s));
+  AFMPB_TRY(product_from64(h, s, x));
+  AFMPB_CUDA(cudaEventRecord(e1, s));
+  ++products;
   k_from_ys<<<nb_el2, 256, 0, s>>>(n2, h->d_ys, h->d_b, h->d_w);
   AFMPB_TRY(norm2(h, n2, h->d_w, h->d_scal + 3));
   AFMPB_TRY(read_scalar(h->d_scal + 3, 3));
-  AFMPB_TRY(add_mv_time());
+  float ms_one = 0.f;
+  AFMPB_CUDA(cudaEventElapsedTime(&ms_one, e0, e1));
   AFMPB_CUDA(cudaEventRecord(h->ev_t1, s));
   AFMPB_CUDA(cudaEventSynchronize(h->ev_t1));
   float ms_all = 0.f;
   AFMPB_CUDA(cudaEventElapsedTime(&ms_all, h->ev_t0, h->ev_t1));
   h->solved = true;
-  if (h->opt.precision == 1) {
+  {
     int flag = 0;
     AFMPB_TRY(read_tc_error(h, &flag));
-    if (flag) return make_err(AFMPB_ETIMEOUT, "a tensor-core M2L wait expired; the products are not valid");
+    if (flag) return make_err(AFMPB_ETIMEOUT, "a bounded device wait expired during the solve; the products are not valid");
   }
   if (info) {
-    info->iters = iters;
+    info->iters = h_gm[1];
     info->restarts = restarts;
     info->res_est = res;
     info->res_true = bnorm > 0 ? hp[3] / bnorm : hp[3];
     info->bnorm = bnorm;
     info->ms_setup = h->ms_setup;
-    info->ms_matvec_total = ms_mv;
+    info->ms_matvec_total = ms_one * products;
     info->ms_gmres = ms_all;
     info->nnz_near = h->nnz;
     info->n_boxes = h->shape.nbox;
+    info->krylov_dim = m;
+    info->second_passes = h->opt.orth == 0 ? h_gm[1] : h_gm[3];
   }
   if (!converged) return make_err(AFMPB_ENOCONV, "GMRES did not reach the tolerance within max_restart cycles");
   return Err{};
@@ -527,6 +744,10 @@ Err run_energy_noalloc(afmpb_t *h, double *E) {
   int dev = 0;
   AFMPB_CUDA(cudaGetDevice(&dev));
   if (dev < 0 || dev >= kMaxDevices) return make_err(AFMPB_EINVAL, "device ordinal out of range");
+  // the scratch address is per device: the handle's kernels must run where it is looked up
+  if (dev != h->device)
+    return make_err(AFMPB_EINVAL, "the current device (" + std::to_string(dev) + ") is not the handle's device (" +
+                                      std::to_string(h->device) + "); make it current first");
   // One scratch array per device: calls on different handles of the same device take
   // turns (the lock is held until the result has been copied back).
   std::lock_guard<std::mutex> lock(g_noalloc_mutex);

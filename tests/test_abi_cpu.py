@@ -55,6 +55,8 @@ def test_null_arguments_are_rejected_without_a_device():
     assert rc == 1 and out.value is None
     assert b"mesh" in lib.afmpb_last_error(None)
     assert lib.afmpb_matvec(None, None, None) == 1
+    assert lib.afmpb_sync(None) == 1
+    assert lib.afmpb_inject_wait_expiry(None) == 1
     assert lib.afmpb_destroy(None) == 0
 
 
@@ -108,7 +110,8 @@ _BAD_ARGS = [
     ("tol NaN", dict(tol=float("nan")), b"tol"),
 ]
 _BAD_OPTIONS = [
-    ("negative restart", dict(restart=-1), b"negative option"),
+    ("negative restart", dict(restart=-2), b"negative option"),
+    ("unknown orthogonalisation", dict(orth=2), b"orth"),
     ("restart above 4096", dict(restart=4097), b"restart"),
     ("negative max_restart", dict(max_restart=-2), b"negative option"),
     ("negative leaf cap", dict(leaf_cap=-5), b"negative option"),

@@ -39,6 +39,23 @@ def test_energy_noalloc_matches_energy_on_two_calls():
         assert abs(h2.energy_noalloc() / e2 - 1) < 1e-12
 
 
+def test_energy_noalloc_with_the_charge_fmm_on_two_calls():
+    """With the charge FMM the reaction potential of each evaluation adds translated
+    expansions with FP32 atomics in a varying order, so the allocation-free energy agrees
+    with afmpb_energy to the documented 1e-6 relative, not bit for bit."""
+    import paper_1710_06316_gb300 as pb
+    mol = synthetic.kirkwood_sphere(subdiv=4, n_charges=500, index=21)
+    with pb.Handle.for_molecule(mol, order=6, leaf_cap=32, charge_fmm=2) as h:
+        assert h.info()["charge_fmm"] == 1
+        h.solve()
+        e_ref = h.energy()
+        lib = pb.load(build=False)
+        out = ctypes.c_double()
+        for _ in range(2):
+            assert lib.afmpb_energy_noalloc(ctypes.c_void_p(h.h), ctypes.byref(out)) == 0
+            assert abs(out.value / e_ref - 1) < 1e-6
+
+
 def test_energy_noalloc_rejects_state_and_size():
     import paper_1710_06316_gb300 as pb
     mol = synthetic.born_ion(subdiv=2)
