@@ -786,13 +786,13 @@ Err launch_far(afmpb_t *h, cudaStream_t s, StageTimer *tm) {
     }
   }
   if (tm && !compressed) tm->mark("m2l", h->m2l_groups.empty() ? 0 : 1);
-  if (!h->h_xbox.empty()) {
-    k_p2l<N><<<(unsigned)h->h_xbox.size(), 256, 0, s>>>(h->d_xbox, h->d_x_ptr, h->d_x_idx, h->d_box_begin,
+  if (h->n_xbox > 0) {
+    k_p2l<N><<<(unsigned)h->n_xbox, 256, 0, s>>>(h->d_xbox, h->d_x_ptr, h->d_x_idx, h->d_box_begin,
                                                         h->d_box_end, h->d_box_center, h->d_pos, h->d_nrm, h->d_xs,
                                                         inv_ebar, (float)h->kappa, h->d_L);
     AFMPB_TRY(check_launch("k_p2l"));
   }
-  if (tm) tm->mark("p2l", h->h_xbox.empty() ? 0 : 1);
+  if (tm) tm->mark("p2l", h->n_xbox > 0 ? 1 : 0);
   for (int level = 3; level < T.nlevel; ++level) {
     int ls = T.lvl_start[level], nl = T.lvl_start[level + 1] - ls;
     k_l2l<N><<<nl, mthreads, 0, s>>>(ls, h->d_box_parent, h->d_box_anchor, h->d_L);

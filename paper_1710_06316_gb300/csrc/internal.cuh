@@ -250,8 +250,8 @@ struct afmpb_t {
   int32_t *d_p2p_order = nullptr;  // [nleaf] P2P blocks, most work first (leaf order)
   int4 *d_p2p_units = nullptr;     // [p2p_nunits] P2P work units (leaf, first, end target), most work first
   int p2p_nunits = 0;
-  std::vector<int32_t> h_xbox;     // boxes with a non-empty list 4
-  int32_t *d_xbox = nullptr;
+  int n_xbox = 0;                  // boxes whose list 4 goes to their local expansion (P2L)
+  int32_t *d_xbox = nullptr;       // those boxes
 
   // ---- Morton-ordered node data -----------------------------------------------------
   float4 *d_pos = nullptr;         // position relative to the leaf centre, w = patch area

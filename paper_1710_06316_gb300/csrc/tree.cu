@@ -270,6 +270,217 @@ __global__ void k_box_rho_up(int ls, int nl, const int32_t *__restrict__ child0,
   brho[b] = r;
 }
 
+// ---- device passes that turn the box arrays into lists (no host loop over boxes) ---------
+
+// Extent of the node cloud: per-block minima and maxima, then one block folds the parts
+// (min / max are exact, so the result does not depend on the partition).
+constexpr int kExtThreads = 256;
+__global__ void __launch_bounds__(kExtThreads) k_extent_part(int64_t n, const double *__restrict__ xyz,
+                                                             double *__restrict__ part) {
+  __shared__ double sh[6][kExtThreads];
+  double l[3] = {1e300, 1e300, 1e300}, u[3] = {-1e300, -1e300, -1e300};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    for (int d = 0; d < 3; ++d) {
+      const double v = xyz[3 * i + d];
+      l[d] = fmin(l[d], v);
+      u[d] = fmax(u[d], v);
+    }
+  for (int d = 0; d < 3; ++d) {
+    sh[d][threadIdx.x] = l[d];
+    sh[3 + d][threadIdx.x] = u[d];
+  }
+  __syncthreads();
+  for (int s = kExtThreads / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s)
+      for (int d = 0; d < 3; ++d) {
+        sh[d][threadIdx.x] = fmin(sh[d][threadIdx.x], sh[d][threadIdx.x + s]);
+        sh[3 + d][threadIdx.x] = fmax(sh[3 + d][threadIdx.x], sh[3 + d][threadIdx.x + s]);
+      }
+    __syncthreads();
+  }
+  if (threadIdx.x < 6) part[6 * blockIdx.x + threadIdx.x] = sh[threadIdx.x][0];
+}
+
+__global__ void k_extent_final(int nblk, const double *__restrict__ part, double *__restrict__ out) {
+  if (threadIdx.x >= 6 || blockIdx.x != 0) return;
+  const int d = threadIdx.x;
+  double v = d < 3 ? 1e300 : -1e300;
+  for (int b = 0; b < nblk; ++b) v = d < 3 ? fmin(v, part[6 * b + d]) : fmax(v, part[6 * b + d]);
+  out[d] = v;
+}
+
+__global__ void k_iota(int n, int32_t *__restrict__ v) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) v[i] = i;
+}
+
+// total[0] = off[nl - 1] + cnt[nl - 1] (the children of one level after the exclusive scan)
+__global__ void k_level_total(int nl, const int32_t *__restrict__ off, const int32_t *__restrict__ cnt,
+                              int64_t *__restrict__ total) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) total[0] = nl > 0 ? (int64_t)off[nl - 1] + cnt[nl - 1] : 0;
+}
+
+__global__ void k_leaf_flags(int nbox, const int32_t *__restrict__ nchild, const int32_t *__restrict__ bbeg,
+                             uint8_t *__restrict__ flag, int32_t *__restrict__ key) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nbox) return;
+  flag[b] = nchild[b] == 0;
+  key[b] = bbeg[b];
+}
+
+__global__ void k_gather_i32(int n, const int32_t *__restrict__ idx, const int32_t *__restrict__ src,
+                             int32_t *__restrict__ dst) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = src[idx[i]];
+}
+
+// Coarse half of list 1 and list 4, counted: a leaf b in list 1 of a finer leaf c puts c in
+// b's list 1 as well (adjacency is symmetric); every box d in list 3 of a leaf b puts b in
+// d's list 4 (the dual of list 3).
+__global__ void k_dual_count(int nleaf, const int32_t *__restrict__ leaves, const int32_t *__restrict__ level,
+                             const int64_t *__restrict__ u1ptr, const int32_t *__restrict__ u1idx,
+                             const int64_t *__restrict__ wptr, const int32_t *__restrict__ widx,
+                             int64_t *__restrict__ ucnt, int64_t *__restrict__ xcnt) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nleaf) return;
+  const int b = leaves[i];
+  for (int64_t j = u1ptr[b]; j < u1ptr[b + 1]; ++j) {
+    const int c = u1idx[j];
+    if (level[c] > level[b]) atomicAdd((unsigned long long *)&ucnt[c], 1ull);
+  }
+  for (int64_t j = wptr[b]; j < wptr[b + 1]; ++j) atomicAdd((unsigned long long *)&xcnt[widx[j]], 1ull);
+}
+
+// own list-1 entries first (their order kept); cursors of the coarse part start behind them
+__global__ void k_u_own(int nbox, const int64_t *__restrict__ u1ptr, const int32_t *__restrict__ u1idx,
+                        const int64_t *__restrict__ uptr, int32_t *__restrict__ uidx, int64_t *__restrict__ seg_beg,
+                        int64_t *__restrict__ cur) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nbox) return;
+  const int64_t own = u1ptr[b + 1] - u1ptr[b];
+  for (int64_t j = 0; j < own; ++j) uidx[uptr[b] + j] = u1idx[u1ptr[b] + j];
+  seg_beg[b] = uptr[b] + own;
+  cur[b] = uptr[b] + own;
+}
+
+__global__ void k_dual_fill(int nleaf, const int32_t *__restrict__ leaves, const int32_t *__restrict__ level,
+                            const int64_t *__restrict__ u1ptr, const int32_t *__restrict__ u1idx,
+                            const int64_t *__restrict__ wptr, const int32_t *__restrict__ widx,
+                            int64_t *__restrict__ ucur, int32_t *__restrict__ uidx, int64_t *__restrict__ xcur,
+                            int32_t *__restrict__ xidx) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nleaf) return;
+  const int b = leaves[i];
+  for (int64_t j = u1ptr[b]; j < u1ptr[b + 1]; ++j) {
+    const int c = u1idx[j];
+    if (level[c] > level[b]) uidx[atomicAdd((unsigned long long *)&ucur[c], 1ull)] = b;
+  }
+  for (int64_t j = wptr[b]; j < wptr[b + 1]; ++j) {
+    const int d = widx[j];
+    xidx[atomicAdd((unsigned long long *)&xcur[d], 1ull)] = b;
+  }
+}
+
+__global__ void k_copy_i64(int64_t n, const int64_t *__restrict__ src, int64_t *__restrict__ dst) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = src[i];
+}
+
+// whole list-1 row sizes: own entries (from the scanned pointers) + coarse entries; 0 at nbox
+__global__ void k_u_rowsize(int nbox, const int64_t *__restrict__ u1ptr, const int64_t *__restrict__ coarse,
+                            int64_t *__restrict__ out) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < nbox) out[b] = (u1ptr[b + 1] - u1ptr[b]) + coarse[b];
+  else if (b == nbox) out[b] = 0;
+}
+
+// List 4 of a box goes point to point at the targets when the box holds no more nodes than
+// an expansion holds weights (n^3): the direct sum is then the cheaper route; otherwise to
+// the box's local expansion (P2L).
+__global__ void k_x_route(int nbox, const int64_t *__restrict__ xptr, const int32_t *__restrict__ bbeg,
+                          const int32_t *__restrict__ bend, int direct_max, uint8_t *__restrict__ direct,
+                          uint8_t *__restrict__ p2l) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nbox) return;
+  const bool has = xptr[b + 1] > xptr[b];
+  const bool dir = has && bend[b] - bbeg[b] <= direct_max;
+  direct[b] = dir;
+  p2l[b] = has && !dir;
+}
+
+// Point-to-point source boxes of a leaf: list 1, the list-4 boxes of itself and its
+// ancestors that are summed directly, and the leaves under each list-3 box (node positions
+// are stored relative to their own leaf, so P2P sources are leaves).  fill == false counts
+// boxes, source nodes, pairs and the block's relative cost (tiles of up to kP2PThreads
+// targets, each thread slice walking its share of the sources, plus the staging of every
+// source per tile, in quarter units).
+__global__ void k_p2p_lists(int nleaf, const int32_t *__restrict__ leaves, const int32_t *__restrict__ bbeg,
+                            const int32_t *__restrict__ bend, const int32_t *__restrict__ parent,
+                            const int32_t *__restrict__ child0, const int32_t *__restrict__ nchild,
+                            const int64_t *__restrict__ uptr, const int32_t *__restrict__ uidx,
+                            const int64_t *__restrict__ xptr, const int32_t *__restrict__ xidx,
+                            const uint8_t *__restrict__ x_direct, const int64_t *__restrict__ wptr,
+                            const int32_t *__restrict__ widx, int64_t *__restrict__ cnt, int64_t *__restrict__ pairs,
+                            uint64_t *__restrict__ cost, const int64_t *__restrict__ pptr, int32_t *__restrict__ pidx,
+                            bool fill) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nleaf) return;
+  const int b = leaves[i];
+  int64_t k = fill ? pptr[i] : 0, nb = 0, src = 0;
+  auto put = [&](int c) {
+    if (fill) pidx[k + nb] = c;
+    ++nb;
+    src += bend[c] - bbeg[c];
+  };
+  for (int64_t j = uptr[b]; j < uptr[b + 1]; ++j) put(uidx[j]);
+  for (int a = b; a >= 0; a = parent[a]) {
+    if (!x_direct[a]) continue;
+    for (int64_t j = xptr[a]; j < xptr[a + 1]; ++j) put(xidx[j]);
+  }
+  int stack[kStack];
+  for (int64_t j = wptr[b]; j < wptr[b + 1]; ++j) {
+    int sp = 0;
+    stack[sp++] = widx[j];
+    while (sp > 0) {
+      const int d = stack[--sp];
+      if (nchild[d] == 0) put(d);
+      else
+        for (int q = nchild[d] - 1; q >= 0 && sp < kStack; --q) stack[sp++] = child0[d] + q;
+    }
+  }
+  if (fill) return;
+  const int64_t nt = bend[b] - bbeg[b];
+  cnt[i] = nb;
+  pairs[i] = nt * src;
+  const int64_t tile = max((int64_t)1, min(nt, (int64_t)kP2PThreads));
+  const int64_t slices = kP2PThreads / tile, ntiles = (nt + tile - 1) / tile;
+  cost[i] = (uint64_t)(ntiles * (4 * ((src + slices - 1) / slices) + src + 256));
+}
+
+// (level, offset) key and (target, source) pair of every list-2 entry, in box order
+__global__ void k_m2l_keys(int nbox, const int64_t *__restrict__ vptr, const int32_t *__restrict__ vidx,
+                           const int4 *__restrict__ anchor, uint32_t *__restrict__ key, uint64_t *__restrict__ pair) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nbox) return;
+  const int4 ab = anchor[b];
+  for (int64_t j = vptr[b]; j < vptr[b + 1]; ++j) {
+    const int c = vidx[j];
+    const int4 ac = anchor[c];
+    key[j] = (uint32_t)(ab.w * 343 + (ac.x - ab.x + 3) * 49 + (ac.y - ab.y + 3) * 7 + (ac.z - ab.z + 3));
+    pair[j] = ((uint64_t)(uint32_t)b << 32) | (uint32_t)c;
+  }
+}
+
+__global__ void k_unpack_pairs(int64_t n, const uint64_t *__restrict__ pk, int2 *__restrict__ out) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) out[i] = make_int2((int)(pk[i] >> 32), (int)(pk[i] & 0xffffffffu));
+}
+
+__global__ void k_leaf_index(int nleaf, const int32_t *__restrict__ leaves, int32_t *__restrict__ leaf_index) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < nleaf) leaf_index[leaves[i]] = i;
+}
+
 namespace {
 
 template <class T>
@@ -305,11 +516,61 @@ Err to_device(afmpb_t *h, T **d, const std::vector<T> &v, const char *what) {
   return Err{};
 }
 
-// exclusive scan of counts (host) into a CSR pointer array with a leading 0
-std::vector<int64_t> csr_from_counts(const std::vector<int64_t> &cnt) {
-  std::vector<int64_t> ptr(cnt.size() + 1, 0);
-  for (size_t i = 0; i < cnt.size(); ++i) ptr[i + 1] = ptr[i] + cnt[i];
-  return ptr;
+
+}  // namespace
+
+namespace {
+
+// Runs one CUB device algorithm: the size query, scratch from the handle's arena, the
+// call, and the scratch released once the stream has caught up.
+template <class F>
+Err cub_call(afmpb_t *h, const char *what, F f) {
+  size_t bytes = 0;
+  cudaError_t e = f(nullptr, bytes);
+  if (e != cudaSuccess) return make_err(AFMPB_ECUDA, std::string(what) + " (size): " + cudaGetErrorString(e));
+  uint8_t *tmp = nullptr;
+  AFMPB_TRY(h->arena.alloc(&tmp, std::max<size_t>(bytes, 16), what));
+  e = f(tmp, bytes);
+  if (e != cudaSuccess) return make_err(AFMPB_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  AFMPB_CUDA(cudaStreamSynchronize(h->stream));
+  h->arena.release(tmp);
+  return Err{};
+}
+
+template <class T>
+Err read_one(T *out, const T *d, cudaStream_t s) {
+  AFMPB_CUDA(cudaMemcpyAsync(out, d, sizeof(T), cudaMemcpyDeviceToHost, s));
+  AFMPB_CUDA(cudaStreamSynchronize(s));
+  return Err{};
+}
+
+// CSR pointers from per-row counts: cnt has rows + 1 entries with cnt[rows] = 0, ptr gets
+// rows + 1 entries (exclusive scan); *total = ptr[rows].
+Err csr_ptr(afmpb_t *h, const int64_t *cnt, int64_t rows, int64_t **ptr, int64_t *total, const char *what) {
+  AFMPB_TRY(h->arena.alloc(ptr, rows + 1, what));
+  int64_t *out = *ptr;
+  AFMPB_TRY(cub_call(h, what, [&](void *t, size_t &bytes) {
+    return cub::DeviceScan::ExclusiveSum(t, bytes, cnt, out, rows + 1, h->stream);
+  }));
+  return read_one(total, out + rows, h->stream);
+}
+
+// Sorts every row segment [beg[r], end[r]) of idx ascending, in place (rows of a few to a
+// few hundred entries); entries outside the segments keep their place.
+Err sort_rows(afmpb_t *h, int32_t *idx, int64_t nnz, const int64_t *beg, const int64_t *end, int64_t rows,
+              const char *what) {
+  if (nnz == 0 || rows == 0) return Err{};
+  int32_t *tmp = nullptr;
+  AFMPB_TRY(h->arena.alloc(&tmp, nnz, what));
+  // entries outside every row segment are not written by the sort: start from a copy
+  AFMPB_CUDA(cudaMemcpyAsync(tmp, idx, sizeof(int32_t) * nnz, cudaMemcpyDeviceToDevice, h->stream));
+  AFMPB_TRY(cub_call(h, what, [&](void *t, size_t &bytes) {
+    return cub::DeviceSegmentedSort::SortKeys(t, bytes, idx, tmp, nnz, rows, beg, end, h->stream);
+  }));
+  AFMPB_CUDA(cudaMemcpyAsync(idx, tmp, sizeof(int32_t) * nnz, cudaMemcpyDeviceToDevice, h->stream));
+  AFMPB_CUDA(cudaStreamSynchronize(h->stream));
+  h->arena.release(tmp);
+  return Err{};
 }
 
 }  // namespace
@@ -325,31 +586,24 @@ Err build_tree(afmpb_t *h) {
   // ---- root cube: the tight bounding cube (a little padding so no node sits on the far
   //      face).  Node positions are stored relative to their leaf centre, so FP32 error
   //      scales with the leaf size, not with the root.
-  std::vector<double> xyz(3 * n);
-  AFMPB_CUDA(cudaMemcpyAsync(xyz.data(), h->d_xyz, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, s));
-  AFMPB_CUDA(cudaStreamSynchronize(s));
-  double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+  double lo[3], hi[3];
   {
-    // per-part extents on the host cores, then the extent of the parts (min / max are
-    // exact, so the result does not depend on the split)
-    std::vector<double> part_ext(6 * (size_t)host_parts(n));
-    const int parts = host_parallel(n, [&](int p, int64_t i0, int64_t i1) {
-      double l[3] = {1e300, 1e300, 1e300}, u[3] = {-1e300, -1e300, -1e300};
-      for (int64_t i = i0; i < i1; ++i)
-        for (int d = 0; d < 3; ++d) {
-          l[d] = std::min(l[d], xyz[3 * i + d]);
-          u[d] = std::max(u[d], xyz[3 * i + d]);
-        }
-      for (int d = 0; d < 3; ++d) {
-        part_ext[6 * p + d] = l[d];
-        part_ext[6 * p + 3 + d] = u[d];
-      }
-    });
-    for (int p = 0; p < parts; ++p)
-      for (int d = 0; d < 3; ++d) {
-        lo[d] = std::min(lo[d], part_ext[6 * p + d]);
-        hi[d] = std::max(hi[d], part_ext[6 * p + 3 + d]);
-      }
+    const int nblk = (int)std::max<int64_t>(1, std::min<int64_t>(1024, (n + kExtThreads - 1) / kExtThreads));
+    double *d_part = nullptr, *d_ext = nullptr;
+    AFMPB_TRY(A.alloc(&d_part, 6 * (size_t)nblk, "extent parts"));
+    AFMPB_TRY(A.alloc(&d_ext, 6, "extent"));
+    k_extent_part<<<nblk, kExtThreads, 0, s>>>(n, h->d_xyz, d_part);
+    k_extent_final<<<1, 32, 0, s>>>(nblk, d_part, d_ext);
+    AFMPB_TRY(check_launch("k_extent"));
+    double ext6[6];
+    AFMPB_CUDA(cudaMemcpyAsync(ext6, d_ext, sizeof(ext6), cudaMemcpyDeviceToHost, s));
+    AFMPB_CUDA(cudaStreamSynchronize(s));
+    A.release(d_part);
+    A.release(d_ext);
+    for (int d = 0; d < 3; ++d) {
+      lo[d] = ext6[d];
+      hi[d] = ext6[3 + d];
+    }
   }
   double ext = 0;
   for (int d = 0; d < 3; ++d) {
@@ -370,21 +624,15 @@ Err build_tree(afmpb_t *h) {
   k_morton<<<div_up(n, 256), 256, 0, s>>>(n, h->d_xyz, lox, loy, loz, std::ldexp(1.0, kKeyBits) / (2.0 * w0),
                                           d_key_in, d_idx_in);
   AFMPB_TRY(check_launch("k_morton"));
-  {
-    size_t tmp_bytes = 0;
-    AFMPB_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, tmp_bytes, d_key_in, h->d_key, d_idx_in, h->d_perm,
-                                               (int)n, 0, 3 * kKeyBits, s));
-    uint8_t *tmp = nullptr;
-    AFMPB_TRY(A.alloc(&tmp, tmp_bytes, "sort tmp"));
-    AFMPB_CUDA(cub::DeviceRadixSort::SortPairs(tmp, tmp_bytes, d_key_in, h->d_key, d_idx_in, h->d_perm, (int)n,
-                                               0, 3 * kKeyBits, s));
-    AFMPB_CUDA(cudaStreamSynchronize(s));
-    A.release(tmp);
-  }
+  AFMPB_TRY(cub_call(h, "morton sort", [&](void *t, size_t &bytes) {
+    return cub::DeviceRadixSort::SortPairs(t, bytes, d_key_in, h->d_key, d_idx_in, h->d_perm, (int)n, 0,
+                                           3 * kKeyBits, s);
+  }));
   A.release(d_key_in);
   A.release(d_idx_in);
 
-  // ---- level-by-level adaptive split
+  // ---- level-by-level adaptive split (child offsets by a device scan; the host reads one
+  //      count per level to size the box arrays)
   size_t capb = std::max<size_t>(1024, (size_t)(8 * (n / std::max(cap, 1) + 1)));
   int32_t *blevel = nullptr, *bparent = nullptr, *bchild0 = nullptr, *bnchild = nullptr, *bbeg = nullptr,
           *bend = nullptr;
@@ -418,6 +666,8 @@ Err build_tree(afmpb_t *h) {
   }
   T.lvl_start = {0, 1};
   int32_t *d_bnd = nullptr, *d_nch = nullptr, *d_off = nullptr;
+  int64_t *d_total = nullptr;
+  AFMPB_TRY(A.alloc(&d_total, 1, "level total"));
   size_t cap_lvl = 0;
   for (int level = 0;; ++level) {
     int ls = T.lvl_start[level], le = T.lvl_start[level + 1], nl = le - ls;
@@ -432,45 +682,63 @@ Err build_tree(afmpb_t *h) {
     k_split_count<<<div_up(nl, 128), 128, 0, s>>>(ls, nl, level, cap, maxL, h->d_key, bbeg, bend, bkey, d_bnd,
                                                    d_nch);
     AFMPB_TRY(check_launch("k_split_count"));
-    std::vector<int32_t> nch;
-    AFMPB_TRY(to_host(nch, d_nch, nl, s));
-    std::vector<int32_t> off(nl);
+    AFMPB_TRY(cub_call(h, "level scan", [&](void *t, size_t &bytes) {
+      return cub::DeviceScan::ExclusiveSum(t, bytes, d_nch, d_off, nl, s);
+    }));
+    k_level_total<<<1, 1, 0, s>>>(nl, d_off, d_nch, d_total);
     int64_t total = 0;
-    for (int i = 0; i < nl; ++i) { off[i] = (int32_t)total; total += nch[i]; }
+    AFMPB_TRY(read_one(&total, d_total, s));
     if (total == 0) break;
     if ((size_t)(le + total) > capb) {
       size_t nc = std::max<size_t>(2 * capb, (size_t)(le + total) + 1024);
       AFMPB_TRY(grow_all((size_t)le, nc));
       capb = nc;
     }
-    AFMPB_CUDA(cudaMemcpyAsync(d_off, off.data(), sizeof(int32_t) * nl, cudaMemcpyHostToDevice, s));
     k_split_write<<<div_up(nl, 128), 128, 0, s>>>(ls, nl, le, level, d_bnd, d_nch, d_off, blevel, bparent, bchild0,
                                                    bnchild, bbeg, bend, banchor, bkey);
     AFMPB_TRY(check_launch("k_split_write"));
     T.lvl_start.push_back(le + (int)total);
   }
   if (d_bnd) { A.release(d_bnd); A.release(d_nch); A.release(d_off); }
+  A.release(d_total);
   T.nlevel = (int)T.lvl_start.size() - 1;
   T.nbox = T.lvl_start.back();
   const int nbox = T.nbox;
   h->d_box_level = blevel; h->d_box_parent = bparent; h->d_box_child0 = bchild0; h->d_box_nchild = bnchild;
   h->d_box_begin = bbeg; h->d_box_end = bend; h->d_box_anchor = banchor; h->d_box_key = bkey;
 
-  // ---- box geometry, leaves, colleagues
+  // ---- box geometry; leaves (selected, then put in Morton order of their node ranges);
+  //      colleagues
   AFMPB_TRY(A.alloc(&h->d_box_center, nbox, "box_center"));
   k_box_geometry<<<div_up(nbox, 256), 256, 0, s>>>(nbox, banchor, lox, loy, loz, w0, h->d_box_center);
   AFMPB_TRY(check_launch("k_box_geometry"));
-  std::vector<int32_t> hn_child, hlevel, hparent, hbeg, hend;
-  AFMPB_TRY(to_host(hn_child, bnchild, nbox, s));
-  AFMPB_TRY(to_host(hlevel, blevel, nbox, s));
-  std::vector<int32_t> leaves;
-  for (int b = 0; b < nbox; ++b)
-    if (hn_child[b] == 0) leaves.push_back(b);
-  // leaves in Morton order of their node ranges
-  AFMPB_TRY(to_host(hbeg, bbeg, nbox, s));
-  std::sort(leaves.begin(), leaves.end(), [&](int a, int b) { return hbeg[a] < hbeg[b]; });
-  T.nleaf = (int)leaves.size();
-  AFMPB_TRY(to_device(h, &h->d_leaves, leaves, "leaves"));
+  {
+    uint8_t *flag = nullptr;
+    int32_t *iota = nullptr, *sel = nullptr, *key = nullptr, *selkey = nullptr, *d_nsel = nullptr;
+    AFMPB_TRY(A.alloc(&flag, nbox, "leaf flags"));
+    AFMPB_TRY(A.alloc(&iota, nbox, "box iota"));
+    AFMPB_TRY(A.alloc(&sel, nbox, "leaves unsorted"));
+    AFMPB_TRY(A.alloc(&key, nbox, "leaf keys"));
+    AFMPB_TRY(A.alloc(&selkey, nbox, "leaf keys selected"));
+    AFMPB_TRY(A.alloc(&d_nsel, 1, "leaf count"));
+    k_leaf_flags<<<div_up(nbox, 256), 256, 0, s>>>(nbox, bnchild, bbeg, flag, key);
+    k_iota<<<div_up(nbox, 256), 256, 0, s>>>(nbox, iota);
+    AFMPB_TRY(check_launch("k_leaf_flags"));
+    AFMPB_TRY(cub_call(h, "leaf select", [&](void *t, size_t &bytes) {
+      return cub::DeviceSelect::Flagged(t, bytes, iota, flag, sel, d_nsel, nbox, s);
+    }));
+    int32_t nleaf = 0;
+    AFMPB_TRY(read_one(&nleaf, d_nsel, s));
+    T.nleaf = nleaf;
+    k_gather_i32<<<div_up(nleaf, 256), 256, 0, s>>>(nleaf, sel, key, selkey);
+    AFMPB_TRY(check_launch("k_gather_i32"));
+    AFMPB_TRY(A.alloc(&h->d_leaves, nleaf, "leaves"));
+    int32_t *keys_out = key;                    // reused as the sorted-key output
+    AFMPB_TRY(cub_call(h, "leaf sort", [&](void *t, size_t &bytes) {
+      return cub::DeviceRadixSort::SortPairs(t, bytes, selkey, keys_out, sel, h->d_leaves, nleaf, 0, 32, s);
+    }));
+    for (void *q : {(void *)flag, (void *)iota, (void *)sel, (void *)key, (void *)selkey, (void *)d_nsel}) A.release(q);
+  }
   int *d_lvl_start = nullptr;
   AFMPB_TRY(to_device(h, &d_lvl_start, T.lvl_start, "lvl_start"));
   AFMPB_TRY(A.alloc(&h->d_colleague, 27 * (size_t)nbox, "colleague"));
@@ -479,217 +747,203 @@ Err build_tree(afmpb_t *h) {
 
   // ---- lists 1 (same level + finer) and 3 for leaves; list 2 for all boxes
   int64_t *d_cnt1 = nullptr, *d_cnt2 = nullptr;
-  AFMPB_TRY(A.alloc(&d_cnt1, nbox, "cnt1"));
-  AFMPB_TRY(A.alloc(&d_cnt2, nbox, "cnt2"));
-  AFMPB_CUDA(cudaMemsetAsync(d_cnt1, 0, sizeof(int64_t) * nbox, s));
-  AFMPB_CUDA(cudaMemsetAsync(d_cnt2, 0, sizeof(int64_t) * nbox, s));
+  AFMPB_TRY(A.alloc(&d_cnt1, nbox + 1, "cnt1"));
+  AFMPB_TRY(A.alloc(&d_cnt2, nbox + 1, "cnt2"));
+  AFMPB_CUDA(cudaMemsetAsync(d_cnt1, 0, sizeof(int64_t) * (nbox + 1), s));
+  AFMPB_CUDA(cudaMemsetAsync(d_cnt2, 0, sizeof(int64_t) * (nbox + 1), s));
   k_list_uw<<<div_up(T.nleaf, 64), 64, 0, s>>>(T.nleaf, h->d_leaves, h->d_colleague, bchild0, bnchild, banchor,
                                                 d_cnt1, d_cnt2, nullptr, nullptr, nullptr, nullptr, false);
   AFMPB_TRY(check_launch("k_list_uw count"));
-  std::vector<int64_t> ucnt, wcnt;
-  AFMPB_TRY(to_host(ucnt, d_cnt1, nbox, s));
-  AFMPB_TRY(to_host(wcnt, d_cnt2, nbox, s));
-  std::vector<int64_t> u1ptr = csr_from_counts(ucnt), wptr = csr_from_counts(wcnt);
   int64_t *d_u1ptr = nullptr, *d_wptr = nullptr;
+  int64_t n_u1 = 0, n_w = 0;
+  AFMPB_TRY(csr_ptr(h, d_cnt1, nbox, &d_u1ptr, &n_u1, "u1ptr"));
+  AFMPB_TRY(csr_ptr(h, d_cnt2, nbox, &d_wptr, &n_w, "wptr"));
   int32_t *d_u1idx = nullptr;
-  AFMPB_TRY(to_device(h, &d_u1ptr, u1ptr, "u1ptr"));
-  AFMPB_TRY(to_device(h, &d_wptr, wptr, "wptr"));
-  AFMPB_TRY(A.alloc(&d_u1idx, u1ptr.back(), "u1idx"));
-  AFMPB_TRY(A.alloc(&h->d_w_idx, wptr.back(), "widx"));
+  AFMPB_TRY(A.alloc(&d_u1idx, n_u1, "u1idx"));
+  AFMPB_TRY(A.alloc(&h->d_w_idx, n_w, "widx"));
   k_list_uw<<<div_up(T.nleaf, 64), 64, 0, s>>>(T.nleaf, h->d_leaves, h->d_colleague, bchild0, bnchild, banchor,
                                                 nullptr, nullptr, d_u1ptr, d_wptr, d_u1idx, h->d_w_idx, true);
   AFMPB_TRY(check_launch("k_list_uw fill"));
+  h->d_w_ptr = d_wptr;
+  AFMPB_CUDA(cudaMemsetAsync(d_cnt1, 0, sizeof(int64_t) * (nbox + 1), s));
   k_list_v<<<div_up(nbox, 128), 128, 0, s>>>(nbox, bparent, h->d_colleague, bchild0, bnchild, banchor, d_cnt1,
                                              nullptr, nullptr, false);
   AFMPB_TRY(check_launch("k_list_v count"));
-  std::vector<int64_t> vcnt;
-  AFMPB_TRY(to_host(vcnt, d_cnt1, nbox, s));
-  std::vector<int64_t> vptr = csr_from_counts(vcnt);
-  AFMPB_TRY(to_device(h, &h->d_v_ptr, vptr, "vptr"));
-  AFMPB_TRY(A.alloc(&h->d_v_idx, vptr.back(), "vidx"));
+  int64_t n_v = 0;
+  AFMPB_TRY(csr_ptr(h, d_cnt1, nbox, &h->d_v_ptr, &n_v, "vptr"));
+  AFMPB_TRY(A.alloc(&h->d_v_idx, n_v, "vidx"));
   k_list_v<<<div_up(nbox, 128), 128, 0, s>>>(nbox, bparent, h->d_colleague, bchild0, bnchild, banchor, nullptr,
                                              h->d_v_ptr, h->d_v_idx, true);
   AFMPB_TRY(check_launch("k_list_v fill"));
 
-  // ---- host: complete list 1 with its coarser half (transpose), list 4 = transpose of
-  //      list 3, point-to-point list per leaf, M2L groups by (level, offset)
-  std::vector<int32_t> u1idx, widx, vidx;
-  AFMPB_TRY(to_host(u1idx, d_u1idx, u1ptr.back(), s));
-  AFMPB_TRY(to_host(widx, h->d_w_idx, wptr.back(), s));
-  AFMPB_TRY(to_host(vidx, h->d_v_idx, vptr.back(), s));
+  // ---- list 1 completed with its coarser half, list 4 as the dual of list 3: counts,
+  //      CSR pointers, fill by atomic cursors, then every row's dual part sorted ascending
+  //      (the result does not depend on the order the cursors were taken in)
+  AFMPB_CUDA(cudaMemsetAsync(d_cnt1, 0, sizeof(int64_t) * (nbox + 1), s));
+  AFMPB_CUDA(cudaMemsetAsync(d_cnt2, 0, sizeof(int64_t) * (nbox + 1), s));
+  k_dual_count<<<div_up(T.nleaf, 128), 128, 0, s>>>(T.nleaf, h->d_leaves, blevel, d_u1ptr, d_u1idx, d_wptr,
+                                                    h->d_w_idx, d_cnt1, d_cnt2);
+  AFMPB_TRY(check_launch("k_dual_count"));
+  int64_t *d_uptr = nullptr, *d_xptr = nullptr;
+  int64_t n_uall = 0, n_x = 0;
+  {
+    // u row sizes: own (from u1ptr) + coarse (d_cnt1)
+    int64_t *d_ucount = nullptr;
+    AFMPB_TRY(A.alloc(&d_ucount, nbox + 1, "u counts"));
+    k_u_rowsize<<<div_up(nbox + 1, 256), 256, 0, s>>>(nbox, d_u1ptr, d_cnt1, d_ucount);
+    AFMPB_TRY(check_launch("k_u_rowsize"));
+    AFMPB_TRY(csr_ptr(h, d_ucount, nbox, &d_uptr, &n_uall, "uptr"));
+    A.release(d_ucount);
+  }
+  AFMPB_TRY(csr_ptr(h, d_cnt2, nbox, &d_xptr, &n_x, "xptr"));
+  h->d_u_ptr = d_uptr;
+  h->d_x_ptr = d_xptr;
+  AFMPB_TRY(A.alloc(&h->d_u_idx, n_uall, "uidx"));
+  AFMPB_TRY(A.alloc(&h->d_x_idx, n_x, "xidx"));
+  {
+    int64_t *seg_beg = nullptr, *ucur = nullptr, *xcur = nullptr;
+    AFMPB_TRY(A.alloc(&seg_beg, nbox, "u coarse begin"));
+    AFMPB_TRY(A.alloc(&ucur, nbox, "u cursor"));
+    AFMPB_TRY(A.alloc(&xcur, nbox, "x cursor"));
+    k_u_own<<<div_up(nbox, 128), 128, 0, s>>>(nbox, d_u1ptr, d_u1idx, d_uptr, h->d_u_idx, seg_beg, ucur);
+    k_copy_i64<<<div_up(nbox, 256), 256, 0, s>>>(nbox, d_xptr, xcur);
+    AFMPB_TRY(check_launch("k_u_own"));
+    k_dual_fill<<<div_up(T.nleaf, 128), 128, 0, s>>>(T.nleaf, h->d_leaves, blevel, d_u1ptr, d_u1idx, d_wptr,
+                                                     h->d_w_idx, ucur, h->d_u_idx, xcur, h->d_x_idx);
+    AFMPB_TRY(check_launch("k_dual_fill"));
+    AFMPB_TRY(sort_rows(h, h->d_u_idx, n_uall, seg_beg, d_uptr + 1, nbox, "u coarse sort"));
+    AFMPB_TRY(sort_rows(h, h->d_x_idx, n_x, d_xptr, d_xptr + 1, nbox, "x sort"));
+    A.release(seg_beg);
+    A.release(ucur);
+    A.release(xcur);
+  }
   A.release(d_u1idx);
   A.release(d_u1ptr);
-  std::vector<std::vector<int32_t>> ucoarse(nbox), xl(nbox);
-  for (int b = 0; b < nbox; ++b) {
-    for (int64_t j = u1ptr[b]; j < u1ptr[b + 1]; ++j) {
-      int c = u1idx[j];
-      if (hlevel[c] > hlevel[b]) ucoarse[c].push_back(b);   // b is a coarser leaf adjacent to c
-    }
-    for (int64_t j = wptr[b]; j < wptr[b + 1]; ++j) xl[widx[j]].push_back(b);
-  }
-  std::vector<int64_t> uptr(nbox + 1, 0), xptr(nbox + 1, 0);
-  for (int b = 0; b < nbox; ++b) {
-    uptr[b + 1] = uptr[b] + (u1ptr[b + 1] - u1ptr[b]) + (int64_t)ucoarse[b].size();
-    std::sort(xl[b].begin(), xl[b].end());
-    xptr[b + 1] = xptr[b] + (int64_t)xl[b].size();
-  }
-  std::vector<int32_t> uidx(uptr.back()), xidx(xptr.back());
-  for (int b = 0; b < nbox; ++b) {
-    int64_t k = uptr[b];
-    for (int64_t j = u1ptr[b]; j < u1ptr[b + 1]; ++j) uidx[k++] = u1idx[j];
-    std::sort(ucoarse[b].begin(), ucoarse[b].end());
-    for (int c : ucoarse[b]) uidx[k++] = c;
-    std::copy(xl[b].begin(), xl[b].end(), xidx.begin() + xptr[b]);
-  }
-  AFMPB_TRY(to_device(h, &h->d_u_ptr, uptr, "uptr"));
-  AFMPB_TRY(to_device(h, &h->d_u_idx, uidx, "uidx"));
-  h->d_w_ptr = d_wptr;
-  AFMPB_TRY(to_device(h, &h->d_x_ptr, xptr, "xptr"));
-  AFMPB_TRY(to_device(h, &h->d_x_idx, xidx, "xidx"));
-  // List 4 of a box is evaluated by P2P at the targets when the box holds no more nodes
-  // than an expansion holds weights (n^3): the direct sum is then the cheaper route.
-  // Otherwise it goes to the box's local expansion (P2L).  Either way each pair once.
-  AFMPB_TRY(to_host(hend, bend, nbox, s));
-  AFMPB_TRY(to_host(hparent, bparent, nbox, s));
-  const int64_t x_direct_max = (int64_t)h->order * h->order * h->order;
-  std::vector<char> x_direct(nbox, 0);
-  h->h_xbox.clear();
-  for (int b = 0; b < nbox; ++b) {
-    if (xptr[b + 1] == xptr[b]) continue;
-    if (hend[b] - hbeg[b] <= x_direct_max) x_direct[b] = 1;
-    else h->h_xbox.push_back(b);
-  }
-  AFMPB_TRY(to_device(h, &h->d_xbox, h->h_xbox, "xbox"));
 
-  // point-to-point source boxes per leaf: list 1, the leaves under each list-3 box
-  // (node positions are stored relative to their own leaf, so P2P sources are leaves),
-  // then the list-4 leaves of itself and its ancestors that are evaluated directly
-  std::vector<int32_t> hchild0;
-  AFMPB_TRY(to_host(hchild0, bchild0, nbox, s));
-  std::vector<int64_t> pptr(T.nleaf + 1, 0);
-  std::vector<int32_t> pidx;
-  std::vector<double> cost(T.nleaf);
-  int64_t pairs = 0;
+  // ---- list 4 routes: direct at the targets for small boxes, else P2L
+  uint8_t *d_xdirect = nullptr;
+  AFMPB_TRY(A.alloc(&d_xdirect, nbox, "x direct"));
   {
-    // leaves in contiguous parts on the host threads, concatenated in order
-    const int nparts = host_parts(T.nleaf);
-    std::vector<std::vector<int32_t>> part(nparts);
-    std::vector<int64_t> part_pairs(nparts, 0);
-    host_parallel(T.nleaf, [&](int pt, int64_t i0, int64_t i1) {
-      std::vector<int32_t> &px = part[pt];
-      std::vector<int32_t> stack;
-      int64_t pp = 0;
-      for (int64_t i = i0; i < i1; ++i) {
-        const int b = leaves[i];
-        const int64_t nt_b = hend[b] - hbeg[b];
-        const size_t start = px.size();
-        int64_t src = 0;
-        for (int64_t j = uptr[b]; j < uptr[b + 1]; ++j) { px.push_back(uidx[j]); src += hend[uidx[j]] - hbeg[uidx[j]]; }
-        for (int a = b; a >= 0; a = hparent[a]) {
-          if (!x_direct[a]) continue;
-          for (int64_t j = xptr[a]; j < xptr[a + 1]; ++j) {
-            px.push_back(xidx[j]);
-            src += hend[xidx[j]] - hbeg[xidx[j]];
-          }
-        }
-        for (int64_t j = wptr[b]; j < wptr[b + 1]; ++j) {
-          stack.assign(1, widx[j]);
-          while (!stack.empty()) {
-            const int d = stack.back();
-            stack.pop_back();
-            if (hn_child[d] == 0) {
-              px.push_back(d);
-              src += hend[d] - hbeg[d];
-            } else {
-              for (int k = hn_child[d] - 1; k >= 0; --k) stack.push_back(hchild0[d] + k);
-            }
-          }
-        }
-        pptr[i + 1] = (int64_t)(px.size() - start);     // count; prefix-summed below
-        // ascending source boxes: near-field setup looks a box up by binary search
-        std::sort(px.begin() + start, px.end());
-        pp += nt_b * src;
-        // Relative time of the leaf's P2P block, for the longest-first order: tiles of up to
-        // kP2PThreads targets, each thread slice walking its share of the sources, plus the
-        // staging of every source per tile.  (A model of the two-targets-per-thread tiling
-        // ordered the blocks worse: 0.335 vs 0.320 ms on the Kirkwood sphere.)
-        const int64_t tile = std::max<int64_t>(1, std::min<int64_t>(nt_b, kP2PThreads));
-        const int64_t slices = kP2PThreads / tile, ntiles = (nt_b + tile - 1) / tile;
-        cost[i] = (double)ntiles * ((double)((src + slices - 1) / slices) + 0.25 * (double)src + 64.0);
-      }
-      part_pairs[pt] = pp;
-    });
-    for (int i = 0; i < T.nleaf; ++i) pptr[i + 1] += pptr[i];
-    pidx.reserve(pptr[T.nleaf]);
-    for (int pt = 0; pt < nparts; ++pt) {
-      pidx.insert(pidx.end(), part[pt].begin(), part[pt].end());
-      pairs += part_pairs[pt];
-    }
+    uint8_t *p2l = nullptr;
+    int32_t *iota = nullptr, *d_nsel = nullptr;
+    AFMPB_TRY(A.alloc(&p2l, nbox, "x p2l"));
+    AFMPB_TRY(A.alloc(&iota, nbox, "box iota"));
+    AFMPB_TRY(A.alloc(&d_nsel, 1, "x box count"));
+    AFMPB_TRY(A.alloc(&h->d_xbox, nbox, "xbox"));
+    k_x_route<<<div_up(nbox, 256), 256, 0, s>>>(nbox, d_xptr, bbeg, bend, h->order * h->order * h->order, d_xdirect,
+                                                  p2l);
+    k_iota<<<div_up(nbox, 256), 256, 0, s>>>(nbox, iota);
+    AFMPB_TRY(check_launch("k_x_route"));
+    AFMPB_TRY(cub_call(h, "x box select", [&](void *t, size_t &bytes) {
+      return cub::DeviceSelect::Flagged(t, bytes, iota, p2l, h->d_xbox, d_nsel, nbox, s);
+    }));
+    AFMPB_TRY(read_one(&h->n_xbox, d_nsel, s));
+    A.release(p2l);
+    A.release(iota);
+    A.release(d_nsel);
   }
-  AFMPB_TRY(to_device(h, &h->d_p2p_ptr, pptr, "p2p_ptr"));
-  AFMPB_TRY(to_device(h, &h->d_p2p_idx, pidx, "p2p_idx"));
-  {
-    // Longest blocks first: the block scheduler then ends the launch on short blocks.
-    std::vector<int32_t> order(T.nleaf);
-    for (int i = 0; i < T.nleaf; ++i) order[i] = i;
-    std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) { return cost[x] > cost[y]; });
-    AFMPB_TRY(to_device(h, &h->d_p2p_order, order, "p2p_order"));
-  }
-  T.n_u = (int64_t)uidx.size();
-  T.n_v = (int64_t)vidx.size();
-  T.n_w = (int64_t)widx.size();
-  T.n_x = (int64_t)xidx.size();
-  T.n_p2p_pairs = pairs - h->n;     // the diagonal t == p is skipped
 
-  // M2L pairs grouped by (level, offset), each group's targets in box order: a counting
-  // sort on the key level * 343 + offset code (stable, so target order is kept)
+  // ---- point-to-point source boxes per leaf (ascending: near-field setup looks a box up
+  //      by binary search), the P2P pair count and the blocks' longest-first order
   {
-    std::vector<int4> anc;
-    AFMPB_TRY(to_host(anc, banchor, nbox, s));
+    const int nl = T.nleaf;
+    int64_t *cnt = nullptr, *pairs_l = nullptr, *d_pairs = nullptr;
+    uint64_t *cost = nullptr, *cost_sorted = nullptr;
+    int32_t *iota = nullptr;
+    AFMPB_TRY(A.alloc(&cnt, nl + 1, "p2p counts"));
+    AFMPB_TRY(A.alloc(&pairs_l, nl, "p2p pairs"));
+    AFMPB_TRY(A.alloc(&d_pairs, 1, "p2p pair total"));
+    AFMPB_TRY(A.alloc(&cost, nl, "p2p cost"));
+    AFMPB_TRY(A.alloc(&cost_sorted, nl, "p2p cost sorted"));
+    AFMPB_TRY(A.alloc(&iota, nl, "leaf iota"));
+    AFMPB_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int64_t) * (nl + 1), s));
+    k_p2p_lists<<<div_up(nl, 64), 64, 0, s>>>(nl, h->d_leaves, bbeg, bend, bparent, bchild0, bnchild, d_uptr,
+                                              h->d_u_idx, d_xptr, h->d_x_idx, d_xdirect, d_wptr, h->d_w_idx, cnt,
+                                              pairs_l, cost, nullptr, nullptr, false);
+    AFMPB_TRY(check_launch("k_p2p_lists count"));
+    int64_t n_p = 0;
+    AFMPB_TRY(csr_ptr(h, cnt, nl, &h->d_p2p_ptr, &n_p, "p2p_ptr"));
+    AFMPB_TRY(A.alloc(&h->d_p2p_idx, n_p, "p2p_idx"));
+    k_p2p_lists<<<div_up(nl, 64), 64, 0, s>>>(nl, h->d_leaves, bbeg, bend, bparent, bchild0, bnchild, d_uptr,
+                                              h->d_u_idx, d_xptr, h->d_x_idx, d_xdirect, d_wptr, h->d_w_idx, nullptr,
+                                              nullptr, nullptr, h->d_p2p_ptr, h->d_p2p_idx, true);
+    AFMPB_TRY(check_launch("k_p2p_lists fill"));
+    AFMPB_TRY(sort_rows(h, h->d_p2p_idx, n_p, h->d_p2p_ptr, h->d_p2p_ptr + 1, nl, "p2p sort"));
+    AFMPB_TRY(cub_call(h, "p2p pairs", [&](void *t, size_t &bytes) {
+      return cub::DeviceReduce::Sum(t, bytes, pairs_l, d_pairs, nl, s);
+    }));
+    int64_t pairs = 0;
+    AFMPB_TRY(read_one(&pairs, d_pairs, s));
+    T.n_p2p_pairs = pairs - h->n;     // the diagonal t == p is skipped
+    // Longest blocks first (a stable sort: equal costs keep leaf order), so that the
+    // block scheduler ends the launch on short blocks.  (A model of the two-targets-per-
+    // thread tiling ordered the blocks worse: 0.335 vs 0.320 ms on the Kirkwood sphere.)
+    k_iota<<<div_up(nl, 256), 256, 0, s>>>(nl, iota);
+    AFMPB_TRY(check_launch("k_iota"));
+    AFMPB_TRY(A.alloc(&h->d_p2p_order, nl, "p2p_order"));
+    AFMPB_TRY(cub_call(h, "p2p order", [&](void *t, size_t &bytes) {
+      return cub::DeviceRadixSort::SortPairsDescending(t, bytes, cost, cost_sorted, iota, h->d_p2p_order, nl, 0, 64, s);
+    }));
+    for (void *q : {(void *)cnt, (void *)pairs_l, (void *)d_pairs, (void *)cost, (void *)cost_sorted, (void *)iota})
+      A.release(q);
+  }
+  A.release(d_xdirect);
+  T.n_u = n_uall;
+  T.n_v = n_v;
+  T.n_w = n_w;
+  T.n_x = n_x;
+
+  // ---- M2L pairs grouped by (level, offset), each group's targets in box order: a stable
+  //      radix sort of the entries by key, then the runs of equal keys
+  {
     const int nkey = (T.nlevel + 1) * 343;
-    const int64_t nv = vptr[nbox];
-    std::vector<int32_t> key(nv);
-    const int nparts = host_parts(nbox);
-    std::vector<std::vector<int64_t>> pcount(nparts, std::vector<int64_t>(nkey, 0));
-    host_parallel(nbox, [&](int pt, int64_t b0, int64_t b1) {
-      std::vector<int64_t> &c = pcount[pt];
-      for (int64_t b = b0; b < b1; ++b)
-        for (int64_t j = vptr[b]; j < vptr[b + 1]; ++j) {
-          const int cb = vidx[j];
-          const int ox = anc[cb].x - anc[b].x, oy = anc[cb].y - anc[b].y, oz = anc[cb].z - anc[b].z;
-          key[j] = anc[b].w * 343 + (ox + 3) * 49 + (oy + 3) * 7 + (oz + 3);
-          ++c[key[j]];
-        }
-    });
-    // start of (key, part): keys in order, parts in box order within a key
-    std::vector<int64_t> kcount(nkey + 1, 0);
-    std::vector<std::vector<int64_t>> pstart(nparts, std::vector<int64_t>(nkey, 0));
-    for (int k = 0; k < nkey; ++k) {
-      int64_t run = kcount[k];
-      for (int pt = 0; pt < nparts; ++pt) {
-        pstart[pt][k] = run;
-        run += pcount[pt][k];
-      }
-      kcount[k + 1] = run;
-    }
-    std::vector<int2> pairs_v(nv);
-    host_parallel(nbox, [&](int pt, int64_t b0, int64_t b1) {
-      std::vector<int64_t> &f = pstart[pt];
-      for (int64_t b = b0; b < b1; ++b)
-        for (int64_t j = vptr[b]; j < vptr[b + 1]; ++j) pairs_v[f[key[j]]++] = make_int2((int)b, vidx[j]);
-    });
+    uint32_t *key = nullptr, *key_sorted = nullptr, *uniq = nullptr;
+    uint64_t *pk = nullptr, *pk_sorted = nullptr;
+    int32_t *runs = nullptr, *d_nruns = nullptr;
+    const int64_t nv = std::max<int64_t>(n_v, 1);
+    AFMPB_TRY(A.alloc(&key, nv, "m2l keys"));
+    AFMPB_TRY(A.alloc(&key_sorted, nv, "m2l keys sorted"));
+    AFMPB_TRY(A.alloc(&pk, nv, "m2l pairs packed"));
+    AFMPB_TRY(A.alloc(&pk_sorted, nv, "m2l pairs sorted"));
+    AFMPB_TRY(A.alloc(&uniq, nv, "m2l group keys"));
+    AFMPB_TRY(A.alloc(&runs, nv, "m2l group sizes"));
+    AFMPB_TRY(A.alloc(&d_nruns, 1, "m2l group count"));
+    AFMPB_TRY(A.alloc(&h->d_m2l_pairs, nv, "m2l_pairs"));
     h->m2l_groups.clear();
-    for (int k = 0; k < nkey; ++k) {
-      if (kcount[k + 1] == kcount[k]) continue;
-      M2LGroup g;
-      g.level = k / 343;
-      g.offset = k % 343;               // raw code in [0, 343); mapped to a table slot in fmm.cu
-      g.start = (int)kcount[k];
-      g.count = (int)(kcount[k + 1] - kcount[k]);
-      h->m2l_groups.push_back(g);
+    h->n_m2l_pairs = n_v;
+    if (n_v > 0) {
+      k_m2l_keys<<<div_up(nbox, 128), 128, 0, s>>>(nbox, h->d_v_ptr, h->d_v_idx, banchor, key, pk);
+      AFMPB_TRY(check_launch("k_m2l_keys"));
+      int bits = 1;
+      while ((1 << bits) < nkey) ++bits;
+      AFMPB_TRY(cub_call(h, "m2l key sort", [&](void *t, size_t &bytes) {
+        return cub::DeviceRadixSort::SortPairs(t, bytes, key, key_sorted, pk, pk_sorted, n_v, 0, bits, s);
+      }));
+      AFMPB_TRY(cub_call(h, "m2l groups", [&](void *t, size_t &bytes) {
+        return cub::DeviceRunLengthEncode::Encode(t, bytes, key_sorted, uniq, runs, d_nruns, n_v, s);
+      }));
+      k_unpack_pairs<<<div_up(n_v, 256), 256, 0, s>>>(n_v, pk_sorted, h->d_m2l_pairs);
+      AFMPB_TRY(check_launch("k_unpack_pairs"));
+      int32_t ng = 0;
+      AFMPB_TRY(read_one(&ng, d_nruns, s));
+      std::vector<uint32_t> gkey(ng);
+      std::vector<int32_t> gcnt(ng);
+      AFMPB_TRY(to_host(gkey, uniq, ng, s));
+      AFMPB_TRY(to_host(gcnt, runs, ng, s));
+      int start = 0;
+      for (int g = 0; g < ng; ++g) {                    // one entry per (level, offset) group
+        M2LGroup gr;
+        gr.level = (int)(gkey[g] / 343);
+        gr.offset = (int)(gkey[g] % 343);               // raw code in [0, 343); mapped to a table slot in fmm.cu
+        gr.start = start;
+        gr.count = gcnt[g];
+        start += gcnt[g];
+        h->m2l_groups.push_back(gr);
+      }
     }
-    h->n_m2l_pairs = nv;
-    AFMPB_TRY(to_device(h, &h->d_m2l_pairs, pairs_v, "m2l_pairs"));
+    for (void *q : {(void *)key, (void *)key_sorted, (void *)pk, (void *)pk_sorted, (void *)uniq, (void *)runs,
+                    (void *)d_nruns})
+      A.release(q);
   }
 
   // ---- Morton-ordered node arrays and box patch radii
@@ -701,11 +955,10 @@ Err build_tree(afmpb_t *h) {
   k_node_sorted<<<div_up(n, 256), 256, 0, s>>>(n, h->d_perm, h->d_node_leaf, h->d_box_center, h->d_xyz,
                                                h->d_area64, h->d_nrm64, h->d_rho64, h->d_pos, h->d_nrm);
   AFMPB_TRY(check_launch("k_node_sorted"));
-  {
-    std::vector<int32_t> leaf_index(nbox, -1);
-    for (int i = 0; i < T.nleaf; ++i) leaf_index[leaves[i]] = i;
-    AFMPB_TRY(to_device(h, &h->d_leaf_index, leaf_index, "leaf index"));
-  }
+  AFMPB_TRY(A.alloc(&h->d_leaf_index, nbox, "leaf index"));
+  AFMPB_CUDA(cudaMemsetAsync(h->d_leaf_index, 0xff, sizeof(int32_t) * nbox, s));
+  k_leaf_index<<<div_up(T.nleaf, 256), 256, 0, s>>>(T.nleaf, h->d_leaves, h->d_leaf_index);
+  AFMPB_TRY(check_launch("k_leaf_index"));
   AFMPB_TRY(A.alloc(&h->d_box_rho, nbox, "box_rho"));
   k_box_rho_leaf<<<div_up(T.nleaf, 128), 128, 0, s>>>(T.nleaf, h->d_leaves, bbeg, bend, h->d_perm, h->d_rho64,
                                                       h->d_box_rho);
