@@ -186,14 +186,15 @@ struct TCItem {
   int group, start, count;
 };
 
-// One unit of the pipelined tensor-core M2L, flattened on the host so that a CTA reads
-// it with one load: first pair (absolute index), pair count, operand tile key
-// (table * slots + offset), table rank, kernel (0 Laplace, 1 Yukawa), output scale.
-struct __align__(16) TCUnit {
-  int pstart, count, key, rank;
-  int kt;
+// One item of the target-stationary tensor-core M2L: a block of up to 128 target boxes
+// [base, end) of one level, the runs [run0, run1) of its (offset, pairs) work and their
+// entries [ent0, ent1), the kernel (0 Laplace, 1 Yukawa), its compressed table and rank,
+// and the output scale.
+struct __align__(16) TSItem {
+  int base, end, run0, run1;
+  int kt, table, rank;
   float scale;
-  int pad0, pad1;
+  int ent0, ent1, pad0, pad1;   // the item's entries [ent0, ent1) (its runs are consecutive)
 };
 
 }  // namespace afmpb
@@ -299,9 +300,13 @@ struct afmpb_t {
   int *d_tc_flag = nullptr;        // device alias of h_wait_flag (the kernels' error flag)
   int *h_wait_flag = nullptr;      // mapped pinned host int, set by a CTA whose bounded wait
                                    // expired; read (and cleared) by the host after the work
-  bool tc_pipelined = false;       // the warp-specialized persistent kernel is used
-  int tc_nunits = 0;
-  afmpb::TCUnit *d_tc_units = nullptr;  // work units of the pipelined kernel
+  // target-stationary tensor-core M2L (compressed ranks <= 112): list-2 entries sorted by
+  // (target block, offset), their runs, and the work items
+  int ts_nitems = 0;
+  afmpb::TSItem *d_ts_items = nullptr;
+  int4 *d_ts_runs = nullptr;       // (offset slot, first entry, end entry, -)
+  uint64_t *d_ts_ent = nullptr;    // row in the block << 32 | source box
+  uint16_t *d_ts_tiles = nullptr;  // C_o as BF16 hi/lo B-operand tiles [table][slot][2][R x R]
 
   // ---- leaf-capacity autotuner (AFMPB_LEAF_CAP_AUTO) --------------------------------
   bool autotuned = false;
@@ -360,6 +365,10 @@ Err enqueue_p2p(afmpb_t *h, cudaStream_t s);          // P2P into d_phi_near
 Err enqueue_combine(afmpb_t *h, cudaStream_t s, int parts);
 Err enqueue_m2l_tc(afmpb_t *h, cudaStream_t s);       // tensor-core M2L (precision 1)
 Err build_m2l_tc(afmpb_t *h);
+// m2l_ts.cu: the target-stationary tensor-core M2L
+bool m2l_ts_applies(const afmpb_t *h);
+Err build_m2l_ts(afmpb_t *h);
+Err enqueue_m2l_ts(afmpb_t *h, cudaStream_t s);
 // autotune.cu
 Err autotune_leaf_cap(afmpb_t *h, afmpb_autotune_report *rep);
 int autotune_cached_cap(int precision, int order, double kappa, int64_t n);   // 0 if none

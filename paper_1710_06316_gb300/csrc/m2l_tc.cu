@@ -26,6 +26,7 @@
 #include <algorithm>
 
 #include "internal.cuh"
+#include "tcgen05.cuh"
 
 namespace afmpb {
 
@@ -37,53 +38,8 @@ constexpr int kTcAElems = kTcRows * kTcKHalf;  // 14,336 BF16 per A half-tile (h
 constexpr int kTcBElems = kTcPairs * kTcKHalf; // 12,544 BF16 per B half-tile
 constexpr int kTcThreads = 256;
 constexpr int kTcTmemCols = 128;
-constexpr uint32_t kTcSpinLimit = 1u << 26;    // bounded mbarrier wait
 
 
-// Byte offset of element (row, k) in a canonical K-major no-swizzle tile with `rows` rows.
-__host__ __device__ __forceinline__ uint32_t canon_off(int row, int k, int rows) {
-  return (uint32_t)((((k >> 3) * (rows >> 3) + (row >> 3)) << 7) + ((row & 7) << 4) + ((k & 7) << 1));
-}
-
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
-  d |= (uint64_t)((lbo & 0x3FFFFu) >> 4) << 16;
-  d |= (uint64_t)((sbo & 0x3FFFFu) >> 4) << 32;
-  d |= (uint64_t)1 << 46;                       // descriptor version for tcgen05
-  return d;                                     // base offset 0, no swizzle
-}
-
-// kind::f16 instruction descriptor: D = F32, A = B = BF16, both K-major, M x N.
-__host__ __device__ __forceinline__ uint32_t instr_desc(int M, int N) {
-  uint32_t d = 0;
-  d |= 1u << 4;                                 // D format F32
-  d |= 1u << 7;                                 // A format BF16
-  d |= 1u << 10;                                // B format BF16
-  d |= (uint32_t)(N >> 3) << 17;
-  d |= (uint32_t)(M >> 4) << 24;
-  return d;
-}
-
-__device__ __forceinline__ uint32_t cvta_smem(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void split_bf16(float v, __nv_bfloat16 &hi, __nv_bfloat16 &lo) {
-  hi = __float2bfloat16_rn(v);
-  lo = __float2bfloat16_rn(v - __bfloat162float(hi));
-}
-
-__device__ __forceinline__ bool mbar_wait(uint32_t mb, uint32_t parity, uint32_t limit = kTcSpinLimit) {
-  for (uint32_t spin = 0; spin < limit; ++spin) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred P1;\n\tmbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2;\n\t"
-        "selp.b32 %0, 1, 0, P1;\n\t}"
-        : "=r"(ok)
-        : "r"(mb), "r"(parity));
-    if (ok) return true;
-  }
-  return false;
-}
 
 // Translation matrices -> BF16 hi/lo half-tiles in the operand layout.
 // out: [table][slot][row tile][k half][hi, lo][kTcAElems].  Sources: compressed tables
@@ -312,279 +268,8 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_m2l_tc(int N3, const TCItem *
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcTmemCols));
 }
 
-// ------------------------------------------------------------------------------------
-// Pipelined form for compressed translations whose ranks all fit one contraction block
-// (r <= 112): persistent CTAs (two per SM for r <= 80) walk a contiguous range of work
-// units (item, kernel), ordered so that consecutive units share their translation tile
-// (Laplace units offset-major across levels: one unit-box table serves every level).
-// Shared memory holds the A tile (r columns) and two B stages, sized by r.  Warps 0-3
-// produce: the B operand of unit k + 1 is gathered into the other stage (once unit k - 1's
-// MMAs, which read that stage, have completed) before the producers wait for unit k's own
-// gather, and the descriptor and source boxes of unit k + 2 are loaded meanwhile; the A tile
-// is reloaded (bulk copy) when it changes; thread 0 issues the MMAs into one of two TMEM
-// accumulators.  Warps 4-7 consume: wait for a unit's
-// accumulator, read it with tcgen05.ld (warp w reads lanes 32 (w - 4) .. +31, one output
-// row per lane) and add each pair's column into the target's compressed local vector with
-// coalesced atomics, then release the accumulator.  So the gather of unit k + 1, the MMAs
-// of unit k and the epilogue of unit k - 1 overlap.  Every wait is bounded; on expiry the
-// CTA records the error flag, drains its own MMAs (bounded) and frees its TMEM.
-// ------------------------------------------------------------------------------------
-__device__ __forceinline__ void producer_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
-__device__ __forceinline__ void cp_async16_zfill(uint32_t dst, const void *src, bool valid) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(valid ? 16 : 0) : "memory");
-}
-__device__ __forceinline__ bool producer_all(bool v) {
-  uint32_t r;
-  asm volatile(
-      "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 q, %1, 0;\n\tbar.red.and.pred p, 1, 128, q;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(r)
-      : "r"((uint32_t)v)
-      : "memory");
-  return r != 0;
-}
-
-__global__ void __launch_bounds__(kTcThreads, 2) k_m2l_tcp(int R, int nunits,
-                                                           const TCUnit *__restrict__ units,
-                                                           const __nv_bfloat16 *__restrict__ Mc16,
-                                                           const int2 *__restrict__ pairs,
-                                                           const __nv_bfloat16 *__restrict__ tiles,
-                                                           float *__restrict__ Lc, int *__restrict__ err_flag) {
-  extern __shared__ __align__(128) uint8_t smem[];
-  // A: kTcRows x R per hi / lo; B: two stages of kTcPairs x R per hi / lo (R <= kTcKHalf,
-  // a multiple of 16, so every piece starts on a 16-byte boundary)
-  __nv_bfloat16 *a_hi = reinterpret_cast<__nv_bfloat16 *>(smem);
-  __nv_bfloat16 *a_lo = a_hi + kTcRows * R;
-  __nv_bfloat16 *const b_base = a_lo + kTcRows * R;    // stage b: hi at b_base + b * 2 kTcPairs R, lo after it
-  __shared__ __align__(8) uint64_t bar_a, bar_full[2], bar_empty[2];
-  __shared__ uint32_t tmem_base;
-  __shared__ int s_src[2][kTcPairs];                      // source boxes of the two B stages
-  __shared__ int s_etgt[4][kTcPairs];                     // per epilogue warp: the unit's targets
-  __shared__ int s_issued;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int per = (nunits + (int)gridDim.x - 1) / (int)gridDim.x;
-  const int u0 = (int)blockIdx.x * per, u1 = min(nunits, u0 + per);
-  if (u0 >= u1) return;                                   // uniform per CTA
-  const int nk = u1 - u0;
-  const uint32_t mb_a = cvta_smem(&bar_a);
-  const uint32_t mb_full[2] = {cvta_smem(&bar_full[0]), cvta_smem(&bar_full[1])};
-  const uint32_t mb_empty[2] = {cvta_smem(&bar_empty[0]), cvta_smem(&bar_empty[1])};
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(cvta_smem(&tmem_base)),
-                 "r"(2 * kTcTmemCols));
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-  }
-  if (threadIdx.x == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb_a));
-    for (int b = 0; b < 2; ++b) {
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb_full[b]));
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(mb_empty[b]));   // one arrival per epilogue warp
-    }
-    asm volatile("fence.mbarrier_init.release.cluster;");
-    s_issued = 0;
-  }
-  asm volatile("tcgen05.fence::before_thread_sync;");
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;");
-  const uint32_t tmem = tmem_base;
-  bool failed = false;
-
-  if (warp < 4) {
-    // ---- producers -------------------------------------------------------------------
-    // The B operand of unit k + 1 is gathered (cp.async, its own commit group) before the
-    // producers wait for unit k's, so one gather is always in flight behind the MMAs.
-    int a_key = -1, a_loads = 0, issued = 0;
-    const uint32_t sb_base = cvta_smem(b_base);
-    const uint32_t stage_bytes = (uint32_t)(2 * kTcPairs * R * 2);   // hi + lo of one stage
-    // gather unit u's B operand into stage st (s_src[st] holds its source boxes)
-    auto gather = [&](const TCUnit &u, int st) {
-      const int kg = u.rank / 8;                         // groups of 8 along K
-      const int np = (u.count + 15) & ~15;
-      const uint32_t hi0 = sb_base + (uint32_t)st * stage_bytes, lo0 = hi0 + (uint32_t)(kTcPairs * R * 2);
-      for (int e = threadIdx.x; e < np * kg; e += 128) {
-        const int p = e / kg, k8 = e % kg;
-        const bool v = p < u.count;
-        const __nv_bfloat16 *src = Mc16 + ((size_t)(v ? s_src[st][p] : 0) * 2 + u.kt) * 2 * R + k8 * 8;
-        const uint32_t off = canon_off(p, k8 * 8, kTcPairs);
-        cp_async16_zfill(hi0 + off, src, v);
-        cp_async16_zfill(lo0 + off, src + R, v);
-      }
-      asm volatile("cp.async.commit_group;" ::: "memory");
-    };
-    // a unit's descriptor and this thread's source box, fetched one unit ahead of use
-    auto src_of = [&](const TCUnit &u) {
-      return (threadIdx.x < kTcPairs && threadIdx.x < u.count) ? pairs[u.pstart + threadIdx.x].y : 0;
-    };
-    TCUnit un = units[u0];
-    if (threadIdx.x < kTcPairs) s_src[0][threadIdx.x] = src_of(un);
-    producer_sync();
-    gather(un, 0);
-    TCUnit nx{};
-    int nx_src = 0;
-    if (nk > 1) {
-      nx = units[u0 + 1];
-      nx_src = src_of(nx);
-    }
-    for (int k = 0; k < nk; ++k) {
-      const int b = k & 1;
-      const int Rt = un.rank, key = un.key;
-      const int npad = (un.count + 15) & ~15;
-      const bool load_a = key != a_key;
-      TCUnit nx2{};
-      int nx2_src = 0;
-      bool ok = true;
-      if (k + 1 < nk) {
-        if (k + 2 < nk) {                                // two units ahead: in flight during this one
-          nx2 = units[u0 + k + 2];
-          nx2_src = src_of(nx2);
-        }
-        // stage (k + 1) & 1 was last read by unit k - 1's MMAs
-        if (k >= 1) ok = mbar_wait(mb_full[(k - 1) & 1], (uint32_t)(((k - 1) >> 1) & 1));
-        if (!producer_all(ok)) {
-          failed = true;
-          break;
-        }
-        if (threadIdx.x < kTcPairs) s_src[(k + 1) & 1][threadIdx.x] = nx_src;
-        producer_sync();                                 // s_src visible
-        gather(nx, (k + 1) & 1);
-        asm volatile("cp.async.wait_group 1;" ::: "memory");   // unit k's gather has landed
-      } else {
-        // the last unit: its A tile, when it changes, must wait for unit k - 1's MMAs
-        if (load_a && k >= 1) ok = mbar_wait(mb_full[(k - 1) & 1], (uint32_t)(((k - 1) >> 1) & 1));
-        if (!producer_all(ok)) {
-          failed = true;
-          break;
-        }
-        asm volatile("cp.async.wait_group 0;" ::: "memory");
-      }
-      if (load_a) {
-        if (threadIdx.x == 0) {
-          // row tile 0, K half 0; its first R / 8 K-groups of 8 are contiguous
-          const __nv_bfloat16 *src = tiles + (size_t)key * 2 * 2 * kTcAElems;
-          const uint32_t half = (uint32_t)(kTcRows * R * 2);
-          asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb_a), "r"(2 * half));
-          asm volatile(
-              "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                  cvta_smem(a_hi)),
-              "l"(src), "r"(half), "r"(mb_a)
-              : "memory");
-          asm volatile(
-              "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                  cvta_smem(a_lo)),
-              "l"(src + kTcAElems), "r"(half), "r"(mb_a)
-              : "memory");
-        }
-        a_key = key;
-        ++a_loads;
-      }
-      asm volatile("fence.proxy.async.shared::cta;");
-      producer_sync();
-      bool ok0 = true;
-      if (threadIdx.x == 0) {
-        if (load_a) ok0 = mbar_wait(mb_a, (uint32_t)((a_loads - 1) & 1));
-        if (ok0 && k >= 2) ok0 = mbar_wait(mb_empty[b], (uint32_t)(((k - 2) >> 1) & 1));   // accumulator drained
-        if (ok0) {
-          asm volatile("tcgen05.fence::after_thread_sync;");
-          const uint32_t idesc = instr_desc(kTcRows, npad);
-          const uint32_t lbo_a = (kTcRows / 8) * 128, lbo_b = (kTcPairs / 8) * 128, sbo = 128;
-          const uint32_t sa_hi = cvta_smem(a_hi), sa_lo = cvta_smem(a_lo);
-          const uint32_t sb_hi = sb_base + (uint32_t)b * stage_bytes, sb_lo = sb_hi + (uint32_t)(kTcPairs * R * 2);
-          const uint32_t acc = tmem + (uint32_t)(b * kTcTmemCols);
-          for (int st = 0; st < Rt / 16; ++st) {
-            const uint32_t ka = 2 * st * lbo_a, kb = 2 * st * lbo_b;
-            const uint64_t dah = smem_desc(sa_hi + ka, lbo_a, sbo), dal = smem_desc(sa_lo + ka, lbo_a, sbo);
-            const uint64_t dbh = smem_desc(sb_hi + kb, lbo_b, sbo), dbl = smem_desc(sb_lo + kb, lbo_b, sbo);
-            const uint32_t acc0 = st > 0 ? 1u : 0u;
-            asm volatile(
-                "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(acc),
-                "l"(dah), "l"(dbh), "r"(idesc), "r"(acc0));
-            asm volatile(
-                "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(acc),
-                "l"(dah), "l"(dbl), "r"(idesc), "r"(1u));
-            asm volatile(
-                "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(acc),
-                "l"(dal), "l"(dbh), "r"(idesc), "r"(1u));
-          }
-          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-              mb_full[b]));
-          ++issued;
-        }
-      }
-      if (!producer_all(ok0)) {
-        failed = true;
-        break;
-      }
-      un = nx;
-      nx = nx2;
-      nx_src = nx2_src;
-    }
-    asm volatile("cp.async.wait_all;" ::: "memory");     // no copy outlives the loop (also on failure)
-    if (threadIdx.x == 0) s_issued = issued;
-  } else {
-    // ---- epilogue --------------------------------------------------------------------
-    const int ew = warp - 4;
-    const int row = 32 * ew + lane;
-    TCUnit nxt = units[u0];
-    for (int k = 0; k < nk; ++k) {
-      const TCUnit un = nxt;
-      if (k + 1 < nk) nxt = units[u0 + k + 1];
-      const int kt = un.kt, Rt = un.rank;
-      const int cnt = un.count, npad = (cnt + 15) & ~15;
-      const int b = k & 1;
-      // the unit's targets, loaded while its MMAs may still be running
-      const int2 *pr = pairs + un.pstart;
-      for (int p = lane; p < cnt; p += 32) s_etgt[ew][p] = pr[p].x;
-      const float scale = un.scale;
-      __syncwarp();
-      const bool ok = __all_sync(0xffffffffu, mbar_wait(mb_full[b], (uint32_t)((k >> 1) & 1)));
-      if (!ok) {
-        failed = true;
-        break;
-      }
-      asm volatile("tcgen05.fence::after_thread_sync;");
-      for (int c0 = 0; c0 < npad; c0 += 16) {
-        uint32_t r[16];
-        const uint32_t taddr = tmem + ((uint32_t)(32 * ew) << 16) + (uint32_t)(b * kTcTmemCols + c0);
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-            : "r"(taddr));
-        asm volatile("tcgen05.wait::ld.sync.aligned;");
-        if (row < Rt) {
-#pragma unroll
-          for (int q = 0; q < 16; ++q) {
-            const int p = c0 + q;
-            if (p < cnt) atomicAdd(Lc + ((size_t)s_etgt[ew][p] * 2 + kt) * R + row, __uint_as_float(r[q]) * scale);
-          }
-        }
-      }
-      asm volatile("tcgen05.fence::before_thread_sync;");
-      __syncwarp();                                      // also: s_etgt reads done before the next unit
-      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mb_empty[b]) : "memory");
-    }
-  }
-  if (failed && lane == 0) atomicExch(err_flag, 1);
-  asm volatile("tcgen05.fence::before_thread_sync;");
-  __syncthreads();
-  if (threadIdx.x == 0 && failed) {
-    // bounded: let this CTA's last MMA group drain before the tensor memory is freed
-    const int issued = s_issued;
-    if (issued > 0) mbar_wait(mb_full[(issued - 1) & 1], (uint32_t)(((issued - 1) >> 1) & 1));
-  }
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;");
-  if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kTcTmemCols));
-}
-
 namespace {
 constexpr int kTcSmem = (2 * kTcAElems + 2 * kTcBElems) * 2;
-// pipelined kernel: A tile (hi, lo) + B stages (hi, lo), r weights each
-int tcp_smem_bytes(int R) { return 2 * (2 * kTcRows * R) + 2 * 2 * (2 * kTcPairs * R); }   // two B stages
 }
 
 Err build_m2l_tc(afmpb_t *h) {
@@ -595,6 +280,8 @@ Err build_m2l_tc(afmpb_t *h) {
   if (N3 > kTcK || N3 % 4 != 0)
     return make_err(AFMPB_EINVAL, "precision 1 (tensor-core M2L) supports fmm_order 2, 4 or 6, "
                                   "or a compressed rank <= 224");
+  // compressed ranks <= 112: the target-stationary kernel (m2l_ts.cu) takes the whole M2L
+  if (m2l_ts_applies(h)) return build_m2l_ts(h);
   auto &A = h->arena;
   cudaStream_t s = h->stream;
   // work items: chunks of <= 112 pairs per (level, offset) group
@@ -630,43 +317,6 @@ Err build_m2l_tc(afmpb_t *h) {
                                    h->m2l_rank > 0 ? h->d_C : nullptr, d_table_level,
                                    reinterpret_cast<__nv_bfloat16 *>(h->d_tc_tiles));
   AFMPB_TRY(check_launch("k_tc_tables"));
-  // pipelined kernel: compressed tables whose ranks all fit one contraction block
-  int rmax = 0;
-  for (int r : h->h_table_rank) rmax = std::max(rmax, r);
-  h->tc_pipelined = h->m2l_rank > 0 && rmax <= kTcKHalf && N3 <= kTcRows && h->d_Mc16;
-  if (h->tc_pipelined) {
-    // (item, kernel), kernel-major; Laplace items offset-major across levels (one table
-    // for every level), Yukawa items in (level, offset) order (one table per level)
-    std::vector<int> lap(items.size());
-    for (int i = 0; i < (int)items.size(); ++i) lap[i] = i;
-    std::stable_sort(lap.begin(), lap.end(), [&](int x, int y) {
-      return h->m2l_groups[items[x].group].offset < h->m2l_groups[items[y].group].offset;
-    });
-    std::vector<TCUnit> units;
-    auto add = [&](int i, int kt) {
-      const auto &it = items[i];
-      const auto &g = h->m2l_groups[it.group];
-      const int table = kt == 0 ? 0 : level_table[g.level];
-      TCUnit u{};
-      u.pstart = g.start + it.start;
-      u.count = it.count;
-      u.key = table * kNumOffsets + g.offset;
-      u.rank = h->h_table_rank[table];
-      u.kt = kt;
-      // Laplace tables are for the unit box: scale by 1 / w of the level (the box centre
-      // array holds the same power-of-two half width)
-      u.scale = kt == 0 ? (float)(1.0 / std::ldexp(h->shape.w0, -g.level)) : 1.0f;
-      units.push_back(u);
-    };
-    for (int i : lap) add(i, 0);
-    for (int i = 0; i < (int)items.size(); ++i)
-      if (h->m2l_groups[items[i].group].level >= h->m2l_yuk_levels) add(i, 1);   // else screened away
-    h->tc_nunits = (int)units.size();
-    AFMPB_TRY(A.alloc(&h->d_tc_units, std::max<size_t>(1, units.size()), "tc units"));
-    if (!units.empty())
-      AFMPB_CUDA(cudaMemcpyAsync(h->d_tc_units, units.data(), sizeof(TCUnit) * units.size(), cudaMemcpyHostToDevice, s));
-    AFMPB_TRY(raise_smem_limit((const void *)k_m2l_tcp, tcp_smem_bytes(h->m2l_rank)));
-  }
   AFMPB_CUDA(cudaStreamSynchronize(s));
   A.release(d_table_level);
   AFMPB_TRY(raise_smem_limit((const void *)k_m2l_tc, kTcSmem));
@@ -674,19 +324,9 @@ Err build_m2l_tc(afmpb_t *h) {
 }
 
 Err enqueue_m2l_tc(afmpb_t *h, cudaStream_t s) {
+  if (m2l_ts_applies(h)) return enqueue_m2l_ts(h, s);
   if (h->tc_items == 0) return Err{};
   const bool comp = h->m2l_rank > 0;
-  if (h->tc_pipelined) {
-    if (h->tc_nunits == 0) return Err{};
-    int dev = 0, sms = 0;
-    AFMPB_CUDA(cudaGetDevice(&dev));
-    AFMPB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const unsigned grid = (unsigned)std::min(h->tc_nunits, 2 * sms);   // two CTAs per SM
-    k_m2l_tcp<<<grid, kTcThreads, tcp_smem_bytes(h->m2l_rank), s>>>(
-        h->m2l_rank, h->tc_nunits, h->d_tc_units, reinterpret_cast<const __nv_bfloat16 *>(h->d_Mc16), h->d_m2l_pairs,
-        reinterpret_cast<const __nv_bfloat16 *>(h->d_tc_tiles), h->d_Lc, h->d_tc_flag);
-    return check_launch("k_m2l_tcp");
-  }
   const int N3 = comp ? h->m2l_rank : h->ncoef;
   dim3 grid((unsigned)h->tc_items, (N3 + kTcRows - 1) / kTcRows, 2);
   k_m2l_tc<<<grid, kTcThreads, kTcSmem, s>>>(N3, h->d_tc_items, h->d_m2l_groups, h->d_m2l_pairs,
