@@ -432,8 +432,7 @@ __global__ void __launch_bounds__(kL2PThreads, 12) k_l2p(const int32_t *__restri
 constexpr int kP2PChunk = 768;      // sources staged in shared memory at a time (8 CTAs/SM)
 constexpr int kP2PPairs = kP2PChunk / 2;
 constexpr int kP2PBoxes = 64;       // source boxes described in shared memory at a time
-constexpr int kP2PResident = 6;     // P2P blocks kept resident per SM (<= 80 registers per thread)
-constexpr int kP2PRegBlocks = 6;
+constexpr int kP2PRegBlocks = kP2PResident;
 
 // Far-rule sums of one source at one target, without the 1/(4 pi):
 //   PhiL += c/r + (g/eps_bar) (n.d)/r^3
@@ -513,7 +512,13 @@ __device__ __forceinline__ void p2p_pair2(const P2PTarget &t, const float4 &a, c
   dY = __ffma2_rn(e1, BmC, __ffma2_rn(e2, Tn, dY));
 }
 
-__global__ void __launch_bounds__(kP2PThreads, kP2PRegBlocks) k_p2p(int nleaf, const int32_t *__restrict__ order,
+// A unit that covers its leaf's whole source list stores; a part of a split leaf adds.
+__device__ __forceinline__ void store_or_add(float4 *p, float4 v, bool whole) {
+  if (whole) *p = v;
+  else asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w) : "memory");
+}
+
+__global__ void __launch_bounds__(kP2PThreads, kP2PRegBlocks) k_p2p(int nunits, const int4 *__restrict__ units,
                                                       const int32_t *__restrict__ leaves,
                                                       const int64_t *__restrict__ pptr,
                                                       const int32_t *__restrict__ pidx,
@@ -531,17 +536,18 @@ __global__ void __launch_bounds__(kP2PThreads, kP2PRegBlocks) k_p2p(int nleaf, c
   __shared__ float s_off[kP2PBoxes][3];
   float4 *red = sa;
   const float2 inv_e = dup2(inv_ebar), kap = dup2(kappa);
-  // The resident blocks walk the cost-ordered leaves in boustrophedon order: in round k
-  // block b takes leaf k G + b for even k and k G + G - 1 - b for odd k (G blocks), so the
-  // block that drew the costliest leaf of one round draws the cheapest of the next
-  // (round robin in one direction: 0.294 ms, boustrophedon 0.287 ms on the 163,842-node
-  // sphere).
+  // The resident blocks walk the cost-ordered work units in boustrophedon order: in round
+  // k block b takes unit k G + b for even k and k G + G - 1 - b for odd k (G blocks), so
+  // the block that drew the costliest unit of one round draws the cheapest of the next.  A
+  // unit is one leaf's targets against a range of its source boxes; leaves with more pairs
+  // than the unit budget are split, and their units add into the (zeroed) output.
   const int G = gridDim.x;
-  for (int k = 0; k * G < nleaf; ++k) {
+  for (int k = 0; k * G < nunits; ++k) {
   const int li = k * G + ((k & 1) ? (G - 1 - (int)blockIdx.x) : (int)blockIdx.x);
-  if (li >= nleaf) continue;
-  if (k > 0) __syncthreads();                           // the previous leaf's reduction read red
-  const int leaf = order[li];
+  if (li >= nunits) continue;
+  if (k > 0) __syncthreads();                           // the previous unit's reduction read red
+  const int4 unit = units[li];
+  const int leaf = unit.x;
   const int b = leaves[leaf];
   const dbl4 cb = center[b];
   const int tb = bbeg[b], te = bend[b];
@@ -550,7 +556,8 @@ __global__ void __launch_bounds__(kP2PThreads, kP2PRegBlocks) k_p2p(int nleaf, c
   const int slices = kP2PThreads / tile;
   const int ti = threadIdx.x % tile, si = threadIdx.x / tile;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int64_t l0 = pptr[leaf], l1 = pptr[leaf + 1];
+  const int64_t l0 = unit.y, l1 = unit.z;               // this unit's source boxes
+  const bool whole = l0 == pptr[leaf] && l1 == pptr[leaf + 1];
   for (int t0 = tb; t0 < te; t0 += 2 * tile) {
     const int t = t0 + ti, t2 = t + tile;
     const bool act = si < slices && t < te;
@@ -651,14 +658,14 @@ __global__ void __launch_bounds__(kP2PThreads, kP2PRegBlocks) k_p2p(int nleaf, c
         const float4 v = red[k * tile + ti];
         a.x += v.x; a.y += v.y; a.z += v.z; a.w += v.w;
       }
-      phi[t] = make_float4(s * a.x, s * a.y, s * a.z, s * a.w);
+      store_or_add(phi + t, make_float4(s * a.x, s * a.y, s * a.z, s * a.w), whole);
       if (t2 < te) {
         float4 c = red[kP2PThreads + ti];
         for (int k = 1; k < slices; ++k) {
           const float4 v = red[kP2PThreads + k * tile + ti];
           c.x += v.x; c.y += v.y; c.z += v.z; c.w += v.w;
         }
-        phi[t2] = make_float4(s * c.x, s * c.y, s * c.z, s * c.w);
+        store_or_add(phi + t2, make_float4(s * c.x, s * c.y, s * c.z, s * c.w), whole);
       }
     }
   }
@@ -835,8 +842,9 @@ Err enqueue_p2p(afmpb_t *h, cudaStream_t s) {
   int dev = 0, sms = 0;
   AFMPB_CUDA(cudaGetDevice(&dev));
   AFMPB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  const int grid = std::max(1, std::min(h->shape.nleaf, kP2PResident * sms));
-  k_p2p<<<grid, kP2PThreads, 0, s>>>(h->shape.nleaf, h->d_p2p_order, h->d_leaves, h->d_p2p_ptr, h->d_p2p_idx, h->d_box_begin,
+  const int grid = std::max(1, std::min(h->p2p_nunits, kP2PResident * sms));
+  AFMPB_CUDA(cudaMemsetAsync(h->d_phi_near, 0, sizeof(float4) * h->n, s));   // split leaves add into it
+  k_p2p<<<grid, kP2PThreads, 0, s>>>(h->p2p_nunits, h->d_p2p_units, h->d_leaves, h->d_p2p_ptr, h->d_p2p_idx, h->d_box_begin,
                                                   h->d_box_end, h->d_box_center, h->d_pos, h->d_nrm, h->d_xs,
                                                   (float)(1.0 / h->ebar), (float)h->kappa,
                                                   (float)(kP2PSkip * h->opt.near_c), h->d_phi_near);

@@ -29,7 +29,9 @@ constexpr int kKeyBits = 21;        // Morton bits per dimension (63-bit keys)
 constexpr int kNumOffsets = 316;    // M2L offsets: [-3,3]^3 minus [-1,1]^3
 constexpr double kPi = 3.14159265358979323846;
 constexpr double kInv4Pi = 0.07957747154594767;  // 1 / (4 pi)
-constexpr int kP2PThreads = 128;   // threads of a P2P block (one block per target leaf)
+constexpr int kP2PThreads = 128;   // threads of a P2P block (one work unit of one target leaf at a time)
+constexpr int kP2PResident = 6;    // P2P blocks kept resident per SM (<= 80 registers per thread)
+constexpr int kP2PUnitsPerBlock = 3;   // P2P work units per resident block (sets the unit size; 2-3 best of 1-32)
 constexpr double kP2PSkip = 0.9;    // P2P leaves out pairs closer than kP2PSkip * c * (rho_p + rho_t)
 
 // Pair geometry of the P2P pass in FP32.  Positions are relative to the target's leaf
@@ -248,9 +250,8 @@ struct afmpb_t {
   int32_t *d_u_idx = nullptr, *d_v_idx = nullptr, *d_w_idx = nullptr, *d_x_idx = nullptr;
   int64_t *d_p2p_ptr = nullptr;    // [nleaf+1] lists 1 + 3 per leaf (leaf order)
   int32_t *d_p2p_idx = nullptr;
-  int32_t *d_p2p_order = nullptr;  // [nleaf] P2P blocks, most work first (leaf order)
-  int4 *d_p2p_units = nullptr;     // [p2p_nunits] P2P work units (leaf, first, end target), most work first
-  int p2p_nunits = 0;
+  int4 *d_p2p_units = nullptr;     // [p2p_nunits] P2P work units (leaf, first and end entry of its
+  int p2p_nunits = 0;              // source boxes in p2p_idx, -), most pairs first
   int n_xbox = 0;                  // boxes whose list 4 goes to their local expansion (P2L)
   int32_t *d_xbox = nullptr;       // those boxes
 

@@ -457,6 +457,49 @@ __global__ void k_p2p_lists(int nleaf, const int32_t *__restrict__ leaves, const
   cost[i] = (uint64_t)(ntiles * (4 * ((src + slices - 1) / slices) + src + 256));
 }
 
+// P2P work units: a leaf's source boxes cut into consecutive ranges of at most `budget`
+// target-source pairs (a range holds at least one box), so that blocks of comparable cost
+// can be dealt out statically.  fill == false counts the units of each leaf.
+// unit = (leaf, first box entry, end box entry, pairs)
+__global__ void k_p2p_units(int nleaf, const int32_t *__restrict__ leaves, const int32_t *__restrict__ bbeg,
+                            const int32_t *__restrict__ bend, const int64_t *__restrict__ pptr,
+                            const int32_t *__restrict__ pidx, int64_t budget, int64_t *__restrict__ cnt,
+                            const int64_t *__restrict__ uptr, int4 *__restrict__ units, uint64_t *__restrict__ ucost,
+                            bool fill) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nleaf) return;
+  const int b = leaves[i];
+  const int64_t nt = bend[b] - bbeg[b];
+  int64_t k = fill ? uptr[i] : 0, nu = 0, acc = 0;
+  int64_t start = pptr[i];
+  for (int64_t j = pptr[i]; j < pptr[i + 1]; ++j) {
+    const int c = pidx[j];
+    const int64_t add = nt * (bend[c] - bbeg[c]);
+    if (j > start && acc + add > budget) {
+      if (fill) {
+        units[k + nu] = make_int4(i, (int)start, (int)j, 0);
+        ucost[k + nu] = (uint64_t)acc;
+      }
+      ++nu;
+      start = j;
+      acc = 0;
+    }
+    acc += add;
+  }
+  if (fill) {
+    units[k + nu] = make_int4(i, (int)start, (int)pptr[i + 1], 0);
+    ucost[k + nu] = (uint64_t)acc;
+  }
+  ++nu;
+  if (!fill) cnt[i] = nu;
+}
+
+__global__ void k_gather_int4(int64_t n, const int32_t *__restrict__ idx, const int4 *__restrict__ src,
+                              int4 *__restrict__ dst) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = src[idx[i]];
+}
+
 // (level, offset) key and (target, source) pair of every list-2 entry, in box order
 __global__ void k_m2l_keys(int nbox, const int64_t *__restrict__ vptr, const int32_t *__restrict__ vidx,
                            const int4 *__restrict__ anchor, uint32_t *__restrict__ key, uint64_t *__restrict__ pair) {
@@ -875,16 +918,41 @@ Err build_tree(afmpb_t *h) {
     int64_t pairs = 0;
     AFMPB_TRY(read_one(&pairs, d_pairs, s));
     T.n_p2p_pairs = pairs - h->n;     // the diagonal t == p is skipped
-    // Longest blocks first (a stable sort: equal costs keep leaf order), so that the
-    // block scheduler ends the launch on short blocks.  (A model of the two-targets-per-
-    // thread tiling ordered the blocks worse: 0.335 vs 0.320 ms on the Kirkwood sphere.)
-    k_iota<<<div_up(nl, 256), 256, 0, s>>>(nl, iota);
+    // Work units of at most `budget` pairs (about eight per resident block, so that a
+    // static deal balances), longest first: a stable sort, equal costs keep leaf order.
+    int dev = 0, sms = 0;
+    AFMPB_CUDA(cudaGetDevice(&dev));
+    AFMPB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int64_t budget = std::max<int64_t>(4096, pairs / ((int64_t)kP2PResident * sms * kP2PUnitsPerBlock));
+    AFMPB_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int64_t) * (nl + 1), s));
+    k_p2p_units<<<div_up(nl, 128), 128, 0, s>>>(nl, h->d_leaves, bbeg, bend, h->d_p2p_ptr, h->d_p2p_idx, budget, cnt,
+                                                nullptr, nullptr, nullptr, false);
+    AFMPB_TRY(check_launch("k_p2p_units count"));
+    int64_t *d_uptr = nullptr, nunits = 0;
+    AFMPB_TRY(csr_ptr(h, cnt, nl, &d_uptr, &nunits, "p2p unit ptr"));
+    int4 *units = nullptr;
+    uint64_t *ucost = nullptr, *ucost_sorted = nullptr;
+    int32_t *uiota = nullptr, *uorder = nullptr;
+    AFMPB_TRY(A.alloc(&units, nunits, "p2p units unsorted"));
+    AFMPB_TRY(A.alloc(&ucost, nunits, "p2p unit cost"));
+    AFMPB_TRY(A.alloc(&ucost_sorted, nunits, "p2p unit cost sorted"));
+    AFMPB_TRY(A.alloc(&uiota, nunits, "p2p unit iota"));
+    AFMPB_TRY(A.alloc(&uorder, nunits, "p2p unit order"));
+    k_p2p_units<<<div_up(nl, 128), 128, 0, s>>>(nl, h->d_leaves, bbeg, bend, h->d_p2p_ptr, h->d_p2p_idx, budget,
+                                                nullptr, d_uptr, units, ucost, true);
+    AFMPB_TRY(check_launch("k_p2p_units fill"));
+    k_iota<<<div_up(nunits, 256), 256, 0, s>>>((int)nunits, uiota);
     AFMPB_TRY(check_launch("k_iota"));
-    AFMPB_TRY(A.alloc(&h->d_p2p_order, nl, "p2p_order"));
-    AFMPB_TRY(cub_call(h, "p2p order", [&](void *t, size_t &bytes) {
-      return cub::DeviceRadixSort::SortPairsDescending(t, bytes, cost, cost_sorted, iota, h->d_p2p_order, nl, 0, 64, s);
+    AFMPB_TRY(cub_call(h, "p2p unit order", [&](void *t, size_t &bytes) {
+      return cub::DeviceRadixSort::SortPairsDescending(t, bytes, ucost, ucost_sorted, uiota, uorder, (int)nunits, 0, 64, s);
     }));
-    for (void *q : {(void *)cnt, (void *)pairs_l, (void *)d_pairs, (void *)cost, (void *)cost_sorted, (void *)iota})
+    AFMPB_TRY(A.alloc(&h->d_p2p_units, nunits, "p2p units"));
+    k_gather_int4<<<div_up(nunits, 256), 256, 0, s>>>(nunits, uorder, units, h->d_p2p_units);
+    AFMPB_TRY(check_launch("k_gather_int4"));
+    h->p2p_nunits = (int)nunits;
+    AFMPB_CUDA(cudaStreamSynchronize(s));
+    for (void *q : {(void *)cnt, (void *)pairs_l, (void *)d_pairs, (void *)cost, (void *)cost_sorted, (void *)iota,
+                    (void *)d_uptr, (void *)units, (void *)ucost, (void *)ucost_sorted, (void *)uiota, (void *)uorder})
       A.release(q);
   }
   A.release(d_xdirect);
