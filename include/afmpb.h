@@ -167,15 +167,16 @@ typedef struct {
     int64_t charge_fmm_boxes;  /* boxes of that FMM's octree over nodes and charges      */
 } afmpb_info;
 
-/* Leaf-capacity autotuner report (AFMPB_LEAF_CAP_AUTO; no counterpart in the paper, which
- * fixes the leaf size by hand).  The handle is first built at start_cap; its product's
+/* Leaf-capacity and tile-shape autotuner report (AFMPB_LEAF_CAP_AUTO; no counterpart in
+ * the paper, which fixes the leaf size by hand).  The handle is first built at start_cap; its product's
  * stage times calibrate the cost of one list-2 translation (ms_per_m2l_pair) and of one
  * box in the other tree passes (ms_per_box); for each candidate capacity the octree and
  * lists alone are rebuilt over the same geometry and the P2P kernel is timed on them
  * (p2p_ms); predicted_ms = p2p_ms + ms_per_m2l_pair * list-2 pairs + ms_per_box * boxes +
  * ms_rest.  The handle is rebuilt at best_cap when that predicts a product at least 3%
  * faster.  The choice is cached per size class (device, precision, order, kappa > 0,
- * floor(log2 N)); later handles of the class start at it and skip the tuning. */
+ * floor(log2 N)), tile shapes included; later handles of the class start at it and skip
+ * the tuning. */
 #define AFMPB_AUTOTUNE_MAX 16
 typedef struct {
     int n_candidates;
@@ -186,6 +187,12 @@ typedef struct {
     double predicted_start_ms, predicted_best_ms;
     double ms_per_m2l_pair, ms_per_box, ms_rest;
     double ms_tuning;          /* host time of the calibration and the candidate trees   */
+    /* Tile shapes, chosen on the handle built at best_cap by timing the kernels themselves:
+     * P2P blocks kept resident per SM (4-6) x work units per block (1-6), and the number of
+     * offsets per work item of the tensor-core M2L (8-32; 0 when that kernel is not used). */
+    int p2p_resident, p2p_units_per_block, m2l_runs_per_item;
+    double p2p_ms_default, p2p_ms_tuned;   /* P2P at the library defaults and at the choice  */
+    double m2l_ms_default, m2l_ms_tuned;   /* the same for the M2L translations              */
 } afmpb_autotune_report;
 
 /* Per-stage timing of one product (afmpb_profile_product). */
@@ -422,6 +429,54 @@ afmpb_status afmpb_server_poll(afmpb_server_t *s, int64_t ticket, afmpb_result *
 afmpb_status afmpb_server_wait(afmpb_server_t *s, int64_t ticket, double timeout_s, afmpb_result *res);
 afmpb_status afmpb_server_get_info(afmpb_server_t *s, afmpb_server_info *st);
 afmpb_status afmpb_server_destroy(afmpb_server_t *s);
+
+/* ---- One solve on several GPUs: the partition plan --------------------------------------
+ * The paper distributes one solve over many nodes (Sec. 3.3-3.4): the surface nodes, and
+ * with them the rows of the product and every Krylov vector, are split along the Morton
+ * order.  Each rank evaluates the rows of its nodes and needs from the others (a) the
+ * unknowns (f, h) of the source nodes outside its range that its point-to-point pairs
+ * (lists 1 and 3, list 4) and its near-field rows read -- the halo, exchanged before each
+ * product; (b) the multipole expansions of list-2 source boxes it does not own (a box whose
+ * nodes lie on several ranks is shared: its expansion is the sum of the ranks' partial
+ * ones); (c) global sums of the Krylov inner products.  This host-only call computes (a)
+ * and (b) from the arrays afmpb_get_tree and afmpb_get_near export, with the node ranges
+ * cut between leaves so that the ranks' estimated work (targets x point-to-point sources +
+ * near-field entries) is balanced.  No GPU is touched.  (The multi-GPU product kernels are
+ * not part of this library: every GB300 machine here has one GPU.) */
+typedef struct {
+    int64_t n_nodes, n_boxes;
+    const int32_t *box_range;    /* [n_boxes*2] node range in Morton order (a box's range
+                                    covers its subtree)                                   */
+    const int32_t *box_parent;   /* [n_boxes], -1 for the root                            */
+    const int64_t *u_ptr; const int32_t *u_idx;   /* lists 1-4 as CSR over boxes, as     */
+    const int64_t *v_ptr; const int32_t *v_idx;   /* afmpb_get_tree exports them         */
+    const int64_t *w_ptr; const int32_t *w_idx;
+    const int64_t *x_ptr; const int32_t *x_idx;
+    const int64_t *near_ptr;     /* optional [n_nodes+1] near-field rows in Morton order   */
+    const int32_t *near_col;     /* their columns (Morton positions); NULL with near_ptr   */
+} afmpb_plan_input;
+
+typedef struct {
+    int64_t node_begin, node_end;  /* the rank's Morton range of nodes (rows)             */
+    int64_t n_halo;                /* nodes of other ranks whose unknowns it reads        */
+    int64_t n_send;                /* (node, destination) pairs of its own nodes others read */
+    int64_t n_import_boxes;        /* list-2 source boxes whose expansion it receives     */
+    int64_t n_shared_boxes;        /* boxes touching its range whose nodes span ranks     */
+    double work;                   /* its work estimate                                   */
+} afmpb_plan_rank;
+
+typedef struct afmpb_plan_t afmpb_plan_t;
+/* EINVAL for a NULL array, nranks < 1 or a box range / parent out of bounds. */
+afmpb_status afmpb_plan_create(const afmpb_plan_input *in, int nranks, afmpb_plan_t **out);
+afmpb_status afmpb_plan_get_rank(const afmpb_plan_t *p, int rank, afmpb_plan_rank *info);
+/* halo nodes [n_halo] (ascending) and the rank owning each */
+afmpb_status afmpb_plan_get_halo(const afmpb_plan_t *p, int rank, int64_t *nodes, int32_t *owner);
+/* own nodes sent [n_send] and their destination ranks, grouped by destination */
+afmpb_status afmpb_plan_get_send(const afmpb_plan_t *p, int rank, int64_t *nodes, int32_t *dest);
+/* imported boxes [n_import_boxes] with their owner (-1: shared), shared boxes [n_shared_boxes] */
+afmpb_status afmpb_plan_get_boxes(const afmpb_plan_t *p, int rank, int32_t *imports, int32_t *import_owner,
+                                  int32_t *shared);
+afmpb_status afmpb_plan_destroy(afmpb_plan_t *p);
 
 #ifdef __cplusplus
 }

@@ -76,7 +76,10 @@ class AutotuneReport(C.Structure):
                 ("p2p_ms", C.c_double * AUTOTUNE_MAX), ("predicted_ms", C.c_double * AUTOTUNE_MAX),
                 ("start_cap", C.c_int), ("best_cap", C.c_int), ("predicted_start_ms", C.c_double),
                 ("predicted_best_ms", C.c_double), ("ms_per_m2l_pair", C.c_double),
-                ("ms_per_box", C.c_double), ("ms_rest", C.c_double), ("ms_tuning", C.c_double)]
+                ("ms_per_box", C.c_double), ("ms_rest", C.c_double), ("ms_tuning", C.c_double),
+                ("p2p_resident", C.c_int), ("p2p_units_per_block", C.c_int), ("m2l_runs_per_item", C.c_int),
+                ("p2p_ms_default", C.c_double), ("p2p_ms_tuned", C.c_double),
+                ("m2l_ms_default", C.c_double), ("m2l_ms_tuned", C.c_double)]
 
 
 class Profile(C.Structure):
@@ -104,6 +107,19 @@ class ServerInfo(C.Structure):
                 ("max_running", C.c_int64), ("slots", C.c_int)]
 
 
+class PlanInput(C.Structure):
+    _fields_ = [("n_nodes", C.c_int64), ("n_boxes", C.c_int64), ("box_range", C.c_void_p),
+                ("box_parent", C.c_void_p), ("u_ptr", C.c_void_p), ("u_idx", C.c_void_p),
+                ("v_ptr", C.c_void_p), ("v_idx", C.c_void_p), ("w_ptr", C.c_void_p), ("w_idx", C.c_void_p),
+                ("x_ptr", C.c_void_p), ("x_idx", C.c_void_p), ("near_ptr", C.c_void_p), ("near_col", C.c_void_p)]
+
+
+class PlanRank(C.Structure):
+    _fields_ = [("node_begin", C.c_int64), ("node_end", C.c_int64), ("n_halo", C.c_int64),
+                ("n_send", C.c_int64), ("n_import_boxes", C.c_int64), ("n_shared_boxes", C.c_int64),
+                ("work", C.c_double)]
+
+
 def _struct_dict(s):
     out = {}
     for name, _ in s._fields_:
@@ -118,7 +134,9 @@ EXPORTS = ["afmpb_create", "afmpb_matvec", "afmpb_matvec_parts", "afmpb_matvec_h
            "afmpb_version", "afmpb_profile_product", "afmpb_energy_noalloc",
            "afmpb_server_create", "afmpb_server_submit", "afmpb_server_poll", "afmpb_server_wait",
            "afmpb_server_get_info", "afmpb_server_destroy", "afmpb_get_autotune",
-           "afmpb_selftest_bounded_wait", "afmpb_sync", "afmpb_inject_wait_expiry"]
+           "afmpb_selftest_bounded_wait", "afmpb_sync", "afmpb_inject_wait_expiry",
+           "afmpb_plan_create", "afmpb_plan_get_rank", "afmpb_plan_get_halo", "afmpb_plan_get_send",
+           "afmpb_plan_get_boxes", "afmpb_plan_destroy"]
 
 
 def library_path() -> str:
@@ -145,6 +163,17 @@ def load(build: bool = True):
     for name in ("afmpb_sync", "afmpb_inject_wait_expiry"):
         getattr(lib, name).restype = I32
         getattr(lib, name).argtypes = [P]
+    lib.afmpb_plan_create.restype = I32
+    lib.afmpb_plan_create.argtypes = [C.POINTER(PlanInput), I32, C.POINTER(P)]
+    lib.afmpb_plan_get_rank.restype = I32
+    lib.afmpb_plan_get_rank.argtypes = [P, I32, C.POINTER(PlanRank)]
+    for name in ("afmpb_plan_get_halo", "afmpb_plan_get_send"):
+        getattr(lib, name).restype = I32
+        getattr(lib, name).argtypes = [P, I32, P, P]
+    lib.afmpb_plan_get_boxes.restype = I32
+    lib.afmpb_plan_get_boxes.argtypes = [P, I32, P, P, P]
+    lib.afmpb_plan_destroy.restype = I32
+    lib.afmpb_plan_destroy.argtypes = [P]
     lib.afmpb_matvec_parts.restype = I32
     lib.afmpb_matvec_parts.argtypes = [P, P, P, I32]
     lib.afmpb_solve.restype = I32
@@ -395,6 +424,54 @@ class Handle:
 
     def __exit__(self, *a):
         self.close()
+
+
+def plan_partition(tree, n_nodes, nranks, near_ptr=None, near_col=None):
+    """The multi-GPU partition plan of one solve (afmpb_plan_*): host-side planning only.
+    tree: dict with range [nb, 2], parent [nb] and u/v/w/x _ptr/_idx arrays (the layout of
+    Handle.tree()); near_ptr / near_col: optional near-field CSR over Morton positions.
+    Returns one dict per rank: node range, work, halo nodes and owners, send nodes and
+    destinations, imported list-2 boxes and owners (-1 shared), shared boxes."""
+    lib = load()
+    keep = {}
+
+    def arr(name, a, dt):
+        keep[name] = _np(a, dt)
+        return keep[name].ctypes.data
+
+    nb = int(np.asarray(tree["parent"]).shape[0])
+    pin = PlanInput(int(n_nodes), nb, arr("range", tree["range"], np.int32), arr("parent", tree["parent"], np.int32),
+                    arr("u_ptr", tree["u_ptr"], np.int64), arr("u_idx", tree["u_idx"], np.int32),
+                    arr("v_ptr", tree["v_ptr"], np.int64), arr("v_idx", tree["v_idx"], np.int32),
+                    arr("w_ptr", tree["w_ptr"], np.int64), arr("w_idx", tree["w_idx"], np.int32),
+                    arr("x_ptr", tree["x_ptr"], np.int64), arr("x_idx", tree["x_idx"], np.int32),
+                    None if near_ptr is None else arr("near_ptr", near_ptr, np.int64),
+                    None if near_col is None else arr("near_col", near_col, np.int32))
+    p = C.c_void_p()
+    rc = lib.afmpb_plan_create(C.byref(pin), int(nranks), C.byref(p))
+    if rc != 0:
+        raise AfmpbError(rc, "afmpb_plan_create")
+    out = []
+    try:
+        for r in range(nranks):
+            info = PlanRank()
+            _check(lib.afmpb_plan_get_rank(p, r, C.byref(info)))
+            d = _struct_dict(info)
+            d["halo"] = np.zeros(info.n_halo, np.int64)
+            d["halo_owner"] = np.zeros(info.n_halo, np.int32)
+            d["send"] = np.zeros(info.n_send, np.int64)
+            d["send_dest"] = np.zeros(info.n_send, np.int32)
+            d["imports"] = np.zeros(info.n_import_boxes, np.int32)
+            d["import_owner"] = np.zeros(info.n_import_boxes, np.int32)
+            d["shared"] = np.zeros(info.n_shared_boxes, np.int32)
+            _check(lib.afmpb_plan_get_halo(p, r, d["halo"].ctypes.data, d["halo_owner"].ctypes.data))
+            _check(lib.afmpb_plan_get_send(p, r, d["send"].ctypes.data, d["send_dest"].ctypes.data))
+            _check(lib.afmpb_plan_get_boxes(p, r, d["imports"].ctypes.data, d["import_owner"].ctypes.data,
+                                            d["shared"].ctypes.data))
+            out.append(d)
+    finally:
+        lib.afmpb_plan_destroy(p)
+    return out
 
 
 def _result_dict(r):

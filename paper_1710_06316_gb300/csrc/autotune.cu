@@ -1,4 +1,5 @@
-// autotune.cu -- leaf-capacity autotuner (afmpb_options.leaf_cap = AFMPB_LEAF_CAP_AUTO).
+// autotune.cu -- leaf-capacity and tile-shape autotuner (afmpb_options.leaf_cap =
+// AFMPB_LEAF_CAP_AUTO).
 //
 // The leaf capacity s trades point-to-point work (list 1 and 3 pairs grow roughly like s)
 // against far-field work (boxes and list-2 translations grow roughly like 1/s).  The tuner
@@ -10,8 +11,11 @@
 //      geometry, and times the real P2P kernel on them;
 //   3. predicts the product time  t(s) = t_P2P(s) + b * pairs_V(s) + c * boxes(s) + t_rest
 //      and keeps the smallest.
-// The choice is cached per (precision, order, screened or not, log2 of the node count),
-// so later handles of the same size class skip steps 1-3.
+// Then, on the handle at the chosen capacity, the tile shapes of the two heaviest kernels
+// are picked by timing them: the P2P blocks kept resident per SM and the size of its work
+// units, and the number of offsets per work item of the tensor-core M2L.
+// The choices are cached per (precision, order, screened or not, log2 of the node count),
+// so later handles of the same size class skip the tuning.
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -80,6 +84,30 @@ Err time_candidate(afmpb_t *h, int cap, int reps, double *p2p_ms, int64_t *m2l_p
 
 std::mutex g_cache_mu;
 std::map<std::tuple<int, int, int, int, int>, int> g_cache;
+struct Tiles { int resident, units, runs; };
+std::map<std::tuple<int, int, int, int, int>, Tiles> g_tile_cache;
+
+// Mean time of `reps` launches of one stage on the handle's stream (after one warm-up).
+template <class F>
+Err time_stage(afmpb_t *h, int reps, F launch, double *ms) {
+  AFMPB_TRY(launch());
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  AFMPB_CUDA(cudaEventCreate(&e0));
+  AFMPB_CUDA(cudaEventCreate(&e1));
+  Err err;
+  cudaEventRecord(e0, h->stream);
+  for (int r = 0; r < reps && err.ok(); ++r) err = launch();
+  cudaEventRecord(e1, h->stream);
+  cudaError_t ce = cudaEventSynchronize(e1);
+  float t = 0.f;
+  if (ce == cudaSuccess) ce = cudaEventElapsedTime(&t, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  AFMPB_TRY(err);
+  if (ce != cudaSuccess) return make_err(AFMPB_ECUDA, std::string("autotune timing: ") + cudaGetErrorString(ce));
+  *ms = t / reps;
+  return Err{};
+}
 
 std::tuple<int, int, int, int, int> cache_key(int precision, int order, double kappa, int64_t n) {
   int dev = 0;
@@ -88,6 +116,80 @@ std::tuple<int, int, int, int, int> cache_key(int precision, int order, double k
 }
 
 }  // namespace
+
+// Tile shapes on the finished handle: P2P resident blocks per SM x work units per block,
+// then the M2L offsets per item, each by timing the kernel itself.  The product graphs are
+// captured again afterwards (they hold the launch shapes).
+Err autotune_tiles(afmpb_t *h, afmpb_autotune_report *rep) {
+  constexpr int kReps = 5;
+  auto p2p = [&]() { return enqueue_p2p(h, h->stream); };
+  double ms = 0, best_ms = 0;
+  AFMPB_TRY(time_stage(h, kReps, p2p, &best_ms));
+  rep->p2p_ms_default = best_ms;
+  int best_r = h->p2p_resident, best_u = h->p2p_units_per_block;
+  for (int u : {1, 2, 3, 4, 6}) {
+    h->p2p_units_per_block = u;
+    AFMPB_TRY(build_p2p_units(h));
+    for (int r : {4, 5, 6}) {
+      h->p2p_resident = r;
+      AFMPB_TRY(time_stage(h, kReps, p2p, &ms));
+      if (ms < best_ms) {
+        best_ms = ms;
+        best_r = r;
+        best_u = u;
+      }
+    }
+  }
+  h->p2p_resident = best_r;
+  h->p2p_units_per_block = best_u;
+  AFMPB_TRY(build_p2p_units(h));
+  rep->p2p_resident = best_r;
+  rep->p2p_units_per_block = best_u;
+  rep->p2p_ms_tuned = best_ms;
+  if (m2l_ts_applies(h) && h->ts_nitems > 0) {
+    auto m2l = [&]() { return enqueue_m2l_ts(h, h->stream); };
+    AFMPB_TRY(time_stage(h, kReps, m2l, &best_ms));
+    rep->m2l_ms_default = best_ms;
+    int best_p = h->ts_runs_per_item;
+    for (int per : {8, 16, 24, 32}) {
+      h->ts_runs_per_item = per;
+      AFMPB_TRY(cut_m2l_ts_items(h));
+      AFMPB_TRY(time_stage(h, kReps, m2l, &ms));
+      if (ms < best_ms) {
+        best_ms = ms;
+        best_p = per;
+      }
+    }
+    h->ts_runs_per_item = best_p;
+    AFMPB_TRY(cut_m2l_ts_items(h));
+    rep->m2l_runs_per_item = best_p;
+    rep->m2l_ms_tuned = best_ms;
+  }
+  return recapture_products(h);
+}
+
+void autotune_cache_tiles(const afmpb_t *h) {
+  std::lock_guard<std::mutex> lk(g_cache_mu);
+  g_tile_cache[cache_key(h->opt.precision, h->order, h->kappa, h->n)] =
+      Tiles{h->p2p_resident, h->p2p_units_per_block, h->ts_runs_per_item};
+}
+
+// Applies the cached tile shapes of the handle's size class; false when there are none.
+bool autotune_cached_tiles(afmpb_t *h) {
+  Tiles t{};
+  {
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    auto it = g_tile_cache.find(cache_key(h->opt.precision, h->order, h->kappa, h->n));
+    if (it == g_tile_cache.end()) return false;
+    t = it->second;
+  }
+  h->p2p_resident = t.resident;
+  h->p2p_units_per_block = t.units;
+  h->ts_runs_per_item = t.runs;
+  if (!build_p2p_units(h).ok()) return false;
+  if (m2l_ts_applies(h) && h->ts_nitems > 0 && !cut_m2l_ts_items(h).ok()) return false;
+  return recapture_products(h).ok();
+}
 
 int autotune_cached_cap(int precision, int order, double kappa, int64_t n) {
   std::lock_guard<std::mutex> lk(g_cache_mu);

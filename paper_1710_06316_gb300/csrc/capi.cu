@@ -350,6 +350,34 @@ Err enqueue_product_kernels(afmpb_t *h, cudaStream_t cap) {
   return e;
 }
 
+// Launch shapes and work lists live in the captured graphs: after the tile tuner changes
+// them, every graph is dropped (the solver's and the caller-buffer ones are captured again
+// on their next use) and the full product is captured again.
+Err recapture_products(afmpb_t *h) {
+  AFMPB_CUDA(cudaStreamSynchronize(h->stream));
+  for (int p = 0; p < 8; ++p) {
+    if (h->graph[p]) cudaGraphExecDestroy(h->graph[p]);
+    if (h->graph_io[p]) cudaGraphExecDestroy(h->graph_io[p]);
+    if (h->graph_io_tmpl[p]) cudaGraphDestroy(h->graph_io_tmpl[p]);
+    h->graph[p] = nullptr;
+    h->graph_io[p] = nullptr;
+    h->graph_io_tmpl[p] = nullptr;
+    h->io_gather[p] = h->io_scatter[p] = nullptr;
+    h->io_x[p] = nullptr;
+    h->io_y[p] = nullptr;
+  }
+  if (h->graph_gm) cudaGraphExecDestroy(h->graph_gm);
+  if (h->graph_gm_tmpl) cudaGraphDestroy(h->graph_gm_tmpl);
+  h->graph_gm = nullptr;
+  h->graph_gm_tmpl = nullptr;
+  h->gm_to_xs = nullptr;
+  h->gm_src = nullptr;
+  if (h->graph_cycle) cudaGraphExecDestroy(h->graph_cycle);
+  h->graph_cycle = nullptr;
+  h->cycle_m = 0;
+  return capture_product(h, AFMPB_PART_ALL);
+}
+
 Err product_sorted(afmpb_t *h, cudaStream_t s, int parts) {
   if (parts <= 0 || parts > AFMPB_PART_ALL) return make_err(AFMPB_EINVAL, "parts must be a non-empty AFMPB_PART_* mask");
   if (!h->graph[parts]) AFMPB_TRY(capture_product(h, parts));
@@ -441,8 +469,20 @@ afmpb_status afmpb_create(const afmpb_mesh *mesh, const afmpb_charges *charges, 
         e = build_handle(mesh, charges, eps_in, eps_out, kappa, fmm_order, tol, options, rep.best_cap, &h);
         if (!e.ok()) return fail(nullptr, e);
       }
+      try {
+        e = autotune_tiles(h, &rep);
+      } catch (...) {
+        e = current_exception_err();
+      }
+      if (!e.ok()) {
+        destroy_handle(h);
+        return fail(nullptr, e);
+      }
+      autotune_cache_tiles(h);
       h->autotuned = true;
       h->tune = rep;
+    } else if (tune) {
+      autotune_cached_tiles(h);            // the size class was tuned before: its tile shapes
     }
     *out = h;
     return AFMPB_OK;

@@ -842,7 +842,7 @@ Err enqueue_p2p(afmpb_t *h, cudaStream_t s) {
   int dev = 0, sms = 0;
   AFMPB_CUDA(cudaGetDevice(&dev));
   AFMPB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  const int grid = std::max(1, std::min(h->p2p_nunits, kP2PResident * sms));
+  const int grid = std::max(1, std::min(h->p2p_nunits, std::min(h->p2p_resident, kP2PRegBlocks) * sms));
   AFMPB_CUDA(cudaMemsetAsync(h->d_phi_near, 0, sizeof(float4) * h->n, s));   // split leaves add into it
   k_p2p<<<grid, kP2PThreads, 0, s>>>(h->p2p_nunits, h->d_p2p_units, h->d_leaves, h->d_p2p_ptr, h->d_p2p_idx, h->d_box_begin,
                                                   h->d_box_end, h->d_box_center, h->d_pos, h->d_nrm, h->d_xs,

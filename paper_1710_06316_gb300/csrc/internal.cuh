@@ -252,6 +252,8 @@ struct afmpb_t {
   int32_t *d_p2p_idx = nullptr;
   int4 *d_p2p_units = nullptr;     // [p2p_nunits] P2P work units (leaf, first and end entry of its
   int p2p_nunits = 0;              // source boxes in p2p_idx, -), most pairs first
+  int p2p_resident = afmpb::kP2PResident;            // P2P blocks per SM (tile tuner)
+  int p2p_units_per_block = afmpb::kP2PUnitsPerBlock;   // P2P unit size (tile tuner)
   int n_xbox = 0;                  // boxes whose list 4 goes to their local expansion (P2L)
   int32_t *d_xbox = nullptr;       // those boxes
 
@@ -304,6 +306,9 @@ struct afmpb_t {
   // target-stationary tensor-core M2L (compressed ranks <= 112): list-2 entries sorted by
   // (target block, offset), their runs, and the work items
   int ts_nitems = 0;
+  int ts_runs_per_item = 0;        // most runs per item (0: the default cut; tile tuner)
+  std::vector<uint32_t> ts_rkey;   // host copy of the runs: (block, offset) key and entry count,
+  std::vector<int32_t> ts_rcnt;    // to cut the items again
   afmpb::TSItem *d_ts_items = nullptr;
   int4 *d_ts_runs = nullptr;       // (offset slot, first entry, end entry, -)
   uint64_t *d_ts_ent = nullptr;    // row in the block << 32 | source box
@@ -357,6 +362,7 @@ Err validate_mesh(const afmpb_mesh *mesh);
 Err build_geometry(afmpb_t *h, const afmpb_mesh *mesh);
 // tree.cu
 Err build_tree(afmpb_t *h);
+Err build_p2p_units(afmpb_t *h);       // P2P work units at h->p2p_units_per_block
 // near.cu
 Err build_near(afmpb_t *h);
 // fmm.cu
@@ -370,6 +376,10 @@ Err build_m2l_tc(afmpb_t *h);
 bool m2l_ts_applies(const afmpb_t *h);
 Err build_m2l_ts(afmpb_t *h);
 Err enqueue_m2l_ts(afmpb_t *h, cudaStream_t s);
+Err cut_m2l_ts_items(afmpb_t *h);      // items from the stored runs at h->ts_runs_per_item
+Err autotune_tiles(afmpb_t *h, afmpb_autotune_report *rep);   // autotune.cu: P2P and M2L tile shapes
+void autotune_cache_tiles(const afmpb_t *h);
+bool autotune_cached_tiles(afmpb_t *h);
 // autotune.cu
 Err autotune_leaf_cap(afmpb_t *h, afmpb_autotune_report *rep);
 int autotune_cached_cap(int precision, int order, double kappa, int64_t n);   // 0 if none
@@ -401,6 +411,7 @@ Err run_energy_noalloc(afmpb_t *h, double *E);      // static scratch, no alloca
 // capi.cu
 Err product_sorted(afmpb_t *h, cudaStream_t s, int parts);  // d_xs -> d_ys
 Err enqueue_product_kernels(afmpb_t *h, cudaStream_t cap);   // d_xs -> d_ys on a capturing stream
+Err recapture_products(afmpb_t *h);   // drop the captured product graphs and capture the full one again
 
 // launch helpers
 inline int div_up(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }

@@ -467,18 +467,54 @@ Err build_m2l_ts(afmpb_t *h) {
   for (void *q : {(void *)d_lvl, (void *)d_blk, (void *)key, (void *)key_sorted, (void *)ent, (void *)uniq,
                   (void *)cnt, (void *)d_nruns})
     A.release(q);
-  // runs (offset slot, first entry, end entry); items over the runs of one block
-  std::vector<int4> runs(nruns);
-  int64_t e0 = 0;
-  for (int r = 0; r < nruns; ++r) {
-    runs[r] = make_int4((int)(rkey[r] % kNumOffsets), (int)e0, (int)(e0 + rcnt[r]), 0);
-    e0 += rcnt[r];
+  h->ts_rkey = std::move(rkey);
+  h->ts_rcnt = std::move(rcnt);
+  {
+    // runs (offset slot, first entry, end entry)
+    std::vector<int4> runs(nruns);
+    int64_t e0 = 0;
+    for (int r = 0; r < nruns; ++r) {
+      runs[r] = make_int4((int)(h->ts_rkey[r] % kNumOffsets), (int)e0, (int)(e0 + h->ts_rcnt[r]), 0);
+      e0 += h->ts_rcnt[r];
+    }
+    AFMPB_TRY(A.alloc(&h->d_ts_runs, std::max<size_t>(1, runs.size()), "ts runs"));
+    AFMPB_CUDA(cudaMemcpyAsync(h->d_ts_runs, runs.data(), sizeof(int4) * runs.size(), cudaMemcpyHostToDevice, s));
+    AFMPB_CUDA(cudaStreamSynchronize(s));
   }
+  AFMPB_TRY(cut_m2l_ts_items(h));
+  // B tiles from the compressed FP32 tables
+  const size_t elems = (size_t)h->m2l_ntables * kNumOffsets * 2 * R * R;
+  AFMPB_TRY(A.alloc(&h->d_ts_tiles, elems, "ts translation tiles"));
+  k_ts_tables<<<2048, 256, 0, s>>>(R, h->m2l_ntables, h->d_C, reinterpret_cast<__nv_bfloat16 *>(h->d_ts_tiles));
+  AFMPB_TRY(check_launch("k_ts_tables"));
+  AFMPB_TRY(alloc_wait_flag(h));
+  if (ts_stages(R) == 4) AFMPB_TRY(raise_smem_limit((const void *)k_m2l_ts<4>, ts_smem_bytes(R)));
+  else AFMPB_TRY(raise_smem_limit((const void *)k_m2l_ts<2>, ts_smem_bytes(R)));
+  AFMPB_CUDA(cudaStreamSynchronize(s));
+  return Err{};
+}
+
+// Items over the stored runs: consecutive runs of one target block and one kernel, at most
+// h->ts_runs_per_item runs (0: about four items per SM, at most kTsItemRuns) and kTsItemEnt
+// entries each.  Replaces earlier items; the tile tuner calls it with other sizes.
+Err cut_m2l_ts_items(afmpb_t *h) {
+  auto &A = h->arena;
+  cudaStream_t s = h->stream;
+  const auto &T = h->shape;
+  const std::vector<uint32_t> &rkey = h->ts_rkey;
+  const std::vector<int32_t> &rcnt = h->ts_rcnt;
+  const int nruns = (int)rkey.size();
+  const std::vector<int> &level_table = h->h_level_table;
+  std::vector<int> blk_start(T.nlevel + 1, 0);
+  for (int l = 0; l < T.nlevel; ++l)
+    blk_start[l + 1] = blk_start[l] + (T.lvl_start[l + 1] - T.lvl_start[l] + kTsRows - 1) / kTsRows;
+  std::vector<int64_t> rstart(nruns + 1, 0);
+  for (int r = 0; r < nruns; ++r) rstart[r + 1] = rstart[r] + rcnt[r];
   int dev = 0, sms = 0;
   AFMPB_CUDA(cudaGetDevice(&dev));
   AFMPB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  // enough items for about four per SM (each re-adds its block's accumulator into Lc)
-  const int per_item = std::min(kTsItemRuns, std::max(8, nruns / std::max(1, 4 * sms)));
+  const int per_item = h->ts_runs_per_item > 0 ? std::min(kTsItemRuns, h->ts_runs_per_item)
+                                                : std::min(kTsItemRuns, std::max(8, nruns / std::max(1, 4 * sms)));
   std::vector<TSItem> items;
   auto level_of_block = [&](int blk) {
     int l = 0;
@@ -505,8 +541,8 @@ Err build_m2l_ts(afmpb_t *h) {
           it.end = end;
           it.run0 = q0;
           it.run1 = q1;
-          it.ent0 = runs[q0].y;
-          it.ent1 = runs[q1 - 1].z;
+          it.ent0 = (int)rstart[q0];
+          it.ent1 = (int)rstart[q1];
           it.kt = kt;
           it.table = table;
           it.rank = h->h_table_rank[table];
@@ -520,19 +556,10 @@ Err build_m2l_ts(afmpb_t *h) {
     }
   }
   h->ts_nitems = (int)items.size();
-  AFMPB_TRY(A.alloc(&h->d_ts_runs, std::max<size_t>(1, runs.size()), "ts runs"));
+  if (h->d_ts_items) A.release(h->d_ts_items);
   AFMPB_TRY(A.alloc(&h->d_ts_items, std::max<size_t>(1, items.size()), "ts items"));
-  AFMPB_CUDA(cudaMemcpyAsync(h->d_ts_runs, runs.data(), sizeof(int4) * runs.size(), cudaMemcpyHostToDevice, s));
   if (!items.empty())
     AFMPB_CUDA(cudaMemcpyAsync(h->d_ts_items, items.data(), sizeof(TSItem) * items.size(), cudaMemcpyHostToDevice, s));
-  // B tiles from the compressed FP32 tables
-  const size_t elems = (size_t)h->m2l_ntables * kNumOffsets * 2 * R * R;
-  AFMPB_TRY(A.alloc(&h->d_ts_tiles, elems, "ts translation tiles"));
-  k_ts_tables<<<2048, 256, 0, s>>>(R, h->m2l_ntables, h->d_C, reinterpret_cast<__nv_bfloat16 *>(h->d_ts_tiles));
-  AFMPB_TRY(check_launch("k_ts_tables"));
-  AFMPB_TRY(alloc_wait_flag(h));
-  if (ts_stages(R) == 4) AFMPB_TRY(raise_smem_limit((const void *)k_m2l_ts<4>, ts_smem_bytes(R)));
-  else AFMPB_TRY(raise_smem_limit((const void *)k_m2l_ts<2>, ts_smem_bytes(R)));
   AFMPB_CUDA(cudaStreamSynchronize(s));
   return Err{};
 }

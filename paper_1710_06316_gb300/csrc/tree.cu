@@ -618,6 +618,56 @@ Err sort_rows(afmpb_t *h, int32_t *idx, int64_t nnz, const int64_t *beg, const i
 
 }  // namespace
 
+// P2P work units over the handle's per-leaf source lists: a leaf's source boxes cut into
+// consecutive ranges of at most `budget` pairs, about h->p2p_units_per_block units per
+// resident block, longest first (a stable sort: equal costs keep leaf order).  Replaces
+// earlier units; the tile tuner calls it again with other unit sizes.
+Err build_p2p_units(afmpb_t *h) {
+  auto &A = h->arena;
+  cudaStream_t s = h->stream;
+  const int nl = h->shape.nleaf;
+  int dev = 0, sms = 0;
+  AFMPB_CUDA(cudaGetDevice(&dev));
+  AFMPB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int64_t pairs = h->shape.n_p2p_pairs + h->n;
+  const int64_t budget =
+      std::max<int64_t>(4096, pairs / ((int64_t)h->p2p_resident * sms * std::max(1, h->p2p_units_per_block)));
+  int64_t *cnt = nullptr;
+  AFMPB_TRY(A.alloc(&cnt, nl + 1, "p2p unit counts"));
+  AFMPB_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int64_t) * (nl + 1), s));
+  k_p2p_units<<<div_up(nl, 128), 128, 0, s>>>(nl, h->d_leaves, h->d_box_begin, h->d_box_end, h->d_p2p_ptr,
+                                              h->d_p2p_idx, budget, cnt, nullptr, nullptr, nullptr, false);
+  AFMPB_TRY(check_launch("k_p2p_units count"));
+  int64_t *d_uptr = nullptr, nunits = 0;
+  AFMPB_TRY(csr_ptr(h, cnt, nl, &d_uptr, &nunits, "p2p unit ptr"));
+  int4 *units = nullptr;
+  uint64_t *ucost = nullptr, *ucost_sorted = nullptr;
+  int32_t *uiota = nullptr, *uorder = nullptr;
+  AFMPB_TRY(A.alloc(&units, nunits, "p2p units unsorted"));
+  AFMPB_TRY(A.alloc(&ucost, nunits, "p2p unit cost"));
+  AFMPB_TRY(A.alloc(&ucost_sorted, nunits, "p2p unit cost sorted"));
+  AFMPB_TRY(A.alloc(&uiota, nunits, "p2p unit iota"));
+  AFMPB_TRY(A.alloc(&uorder, nunits, "p2p unit order"));
+  k_p2p_units<<<div_up(nl, 128), 128, 0, s>>>(nl, h->d_leaves, h->d_box_begin, h->d_box_end, h->d_p2p_ptr,
+                                              h->d_p2p_idx, budget, nullptr, d_uptr, units, ucost, true);
+  AFMPB_TRY(check_launch("k_p2p_units fill"));
+  k_iota<<<div_up(nunits, 256), 256, 0, s>>>((int)nunits, uiota);
+  AFMPB_TRY(check_launch("k_iota"));
+  AFMPB_TRY(cub_call(h, "p2p unit order", [&](void *t, size_t &bytes) {
+    return cub::DeviceRadixSort::SortPairsDescending(t, bytes, ucost, ucost_sorted, uiota, uorder, (int)nunits, 0, 64, s);
+  }));
+  if (h->d_p2p_units) A.release(h->d_p2p_units);
+  AFMPB_TRY(A.alloc(&h->d_p2p_units, nunits, "p2p units"));
+  k_gather_int4<<<div_up(nunits, 256), 256, 0, s>>>(nunits, uorder, units, h->d_p2p_units);
+  AFMPB_TRY(check_launch("k_gather_int4"));
+  h->p2p_nunits = (int)nunits;
+  AFMPB_CUDA(cudaStreamSynchronize(s));
+  for (void *q : {(void *)cnt, (void *)d_uptr, (void *)units, (void *)ucost, (void *)ucost_sorted, (void *)uiota,
+                  (void *)uorder})
+    A.release(q);
+  return Err{};
+}
+
 Err build_tree(afmpb_t *h) {
   const int64_t n = h->n;
   cudaStream_t s = h->stream;
@@ -918,41 +968,8 @@ Err build_tree(afmpb_t *h) {
     int64_t pairs = 0;
     AFMPB_TRY(read_one(&pairs, d_pairs, s));
     T.n_p2p_pairs = pairs - h->n;     // the diagonal t == p is skipped
-    // Work units of at most `budget` pairs (about eight per resident block, so that a
-    // static deal balances), longest first: a stable sort, equal costs keep leaf order.
-    int dev = 0, sms = 0;
-    AFMPB_CUDA(cudaGetDevice(&dev));
-    AFMPB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const int64_t budget = std::max<int64_t>(4096, pairs / ((int64_t)kP2PResident * sms * kP2PUnitsPerBlock));
-    AFMPB_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int64_t) * (nl + 1), s));
-    k_p2p_units<<<div_up(nl, 128), 128, 0, s>>>(nl, h->d_leaves, bbeg, bend, h->d_p2p_ptr, h->d_p2p_idx, budget, cnt,
-                                                nullptr, nullptr, nullptr, false);
-    AFMPB_TRY(check_launch("k_p2p_units count"));
-    int64_t *d_uptr = nullptr, nunits = 0;
-    AFMPB_TRY(csr_ptr(h, cnt, nl, &d_uptr, &nunits, "p2p unit ptr"));
-    int4 *units = nullptr;
-    uint64_t *ucost = nullptr, *ucost_sorted = nullptr;
-    int32_t *uiota = nullptr, *uorder = nullptr;
-    AFMPB_TRY(A.alloc(&units, nunits, "p2p units unsorted"));
-    AFMPB_TRY(A.alloc(&ucost, nunits, "p2p unit cost"));
-    AFMPB_TRY(A.alloc(&ucost_sorted, nunits, "p2p unit cost sorted"));
-    AFMPB_TRY(A.alloc(&uiota, nunits, "p2p unit iota"));
-    AFMPB_TRY(A.alloc(&uorder, nunits, "p2p unit order"));
-    k_p2p_units<<<div_up(nl, 128), 128, 0, s>>>(nl, h->d_leaves, bbeg, bend, h->d_p2p_ptr, h->d_p2p_idx, budget,
-                                                nullptr, d_uptr, units, ucost, true);
-    AFMPB_TRY(check_launch("k_p2p_units fill"));
-    k_iota<<<div_up(nunits, 256), 256, 0, s>>>((int)nunits, uiota);
-    AFMPB_TRY(check_launch("k_iota"));
-    AFMPB_TRY(cub_call(h, "p2p unit order", [&](void *t, size_t &bytes) {
-      return cub::DeviceRadixSort::SortPairsDescending(t, bytes, ucost, ucost_sorted, uiota, uorder, (int)nunits, 0, 64, s);
-    }));
-    AFMPB_TRY(A.alloc(&h->d_p2p_units, nunits, "p2p units"));
-    k_gather_int4<<<div_up(nunits, 256), 256, 0, s>>>(nunits, uorder, units, h->d_p2p_units);
-    AFMPB_TRY(check_launch("k_gather_int4"));
-    h->p2p_nunits = (int)nunits;
-    AFMPB_CUDA(cudaStreamSynchronize(s));
-    for (void *q : {(void *)cnt, (void *)pairs_l, (void *)d_pairs, (void *)cost, (void *)cost_sorted, (void *)iota,
-                    (void *)d_uptr, (void *)units, (void *)ucost, (void *)ucost_sorted, (void *)uiota, (void *)uorder})
+    AFMPB_TRY(build_p2p_units(h));
+    for (void *q : {(void *)cnt, (void *)pairs_l, (void *)d_pairs, (void *)cost, (void *)cost_sorted, (void *)iota})
       A.release(q);
   }
   A.release(d_xdirect);

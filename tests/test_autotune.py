@@ -1,5 +1,7 @@
-"""Leaf-capacity autotuner (AFMPB_LEAF_CAP_AUTO): measured P2P per candidate tree plus a
-far-field model calibrated on the handle's own product."""
+"""Leaf-capacity and tile-shape autotuner (AFMPB_LEAF_CAP_AUTO): measured P2P per
+candidate tree plus a far-field model calibrated on the handle's own product, then the P2P
+resident blocks and work-unit size and the tensor-core M2L item size by timing the kernels
+on the finished handle."""
 import numpy as np
 import pytest
 
@@ -25,6 +27,12 @@ def test_autotune_picks_a_measured_candidate_and_caches_it():
         # rebuilt at the best capacity only when it predicts a gain of at least 3%
         rebuilt = rep["best_cap"] != rep["start_cap"] and rep["predicted_best_ms"] < 0.97 * rep["predicted_start_ms"]
         assert info["leaf_cap"] == (rep["best_cap"] if rebuilt else rep["start_cap"])
+        # tile shapes: chosen among the candidates, never slower than the defaults
+        assert rep["p2p_resident"] in (4, 5, 6) and rep["p2p_units_per_block"] in (1, 2, 3, 4, 6)
+        assert 0 < rep["p2p_ms_tuned"] <= rep["p2p_ms_default"]
+        assert rep["m2l_runs_per_item"] in (0, 8, 16, 24, 32)
+        if rep["m2l_runs_per_item"]:
+            assert 0 < rep["m2l_ms_tuned"] <= rep["m2l_ms_default"]
         # the product still meets the bar (sampled rows against the oracle)
         o = oracle.Oracle.for_molecule(mol)
         x = synthetic.random_unknowns(mol.n_nodes, 21)
