@@ -53,6 +53,7 @@ Err time_candidate(afmpb_t *h, int cap, int reps, double *p2p_ms, int64_t *m2l_p
   t->opt = h->opt;
   t->opt.leaf_cap = cap;
   t->stream = h->stream;
+  t->arena.stream = h->stream;
   t->d_xyz = h->d_xyz;
   t->d_rho64 = h->d_rho64;
   t->d_area64 = h->d_area64;

@@ -204,6 +204,8 @@ Err create_impl(afmpb_t *h, const afmpb_mesh *mesh, const afmpb_charges *ch) {
     AFMPB_CUDA(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
     h->own_stream = true;
   }
+  keep_pool_memory();
+  h->arena.stream = h->stream;
   {
     int lo = 0, hi = 0;
     AFMPB_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
@@ -252,6 +254,25 @@ Err create_impl(afmpb_t *h, const afmpb_mesh *mesh, const afmpb_charges *ch) {
 }  // namespace
 
 namespace afmpb {
+void keep_pool_memory() {
+  static std::mutex mu;
+  static std::vector<int> done;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  std::lock_guard<std::mutex> lock(mu);
+  if (std::find(done.begin(), done.end(), dev) != done.end()) return;
+  cudaMemPool_t pool = nullptr;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t keep = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  }
+  cudaGetLastError();
+  done.push_back(dev);
+}
+
 Err raise_smem_limit(const void *func, int bytes) {
   static std::mutex mu;
   static std::map<std::pair<int, const void *>, int> limit;

@@ -150,6 +150,7 @@ Err build_charge_fmm(afmpb_t *h) {
   if (u->opt.m2l_tol > 0) u->opt.m2l_tol = std::min(u->opt.m2l_tol, kChargeFmmTol);
   u->opt.stream = nullptr;
   u->stream = h->stream;
+  u->arena.stream = h->stream;
   u->own_stream = false;
   const int64_t nu = u->n;
   cudaStream_t s = h->stream;

@@ -111,17 +111,25 @@ inline Err make_err(afmpb_status c, const std::string &m) { return Err{c, m}; }
     if (!e_.ok()) return e_;            \
   } while (0)
 
-// Device allocation registry owned by a handle.
+// Makes the device's default memory pool keep freed memory for reuse (stream-ordered
+// allocations of later handles then need no new device memory); once per device.
+void keep_pool_memory();
+
+// Device allocation registry owned by a handle.  With a stream set, memory comes from the
+// device's stream-ordered pool (cudaMallocAsync / cudaFreeAsync on that stream): a free
+// does not synchronise the device, so handles created and destroyed by one server slot do
+// not stall the solves running on the others.
 struct DeviceArena {
   std::vector<std::pair<void *, size_t>> blocks;
   size_t bytes = 0;
   size_t peak = 0;                 // high-water mark of bytes
+  cudaStream_t stream = nullptr;   // stream the allocations and frees are ordered on
   template <class T>
   Err alloc(T **p, size_t count, const char *what) {
     *p = nullptr;
     if (count == 0) count = 1;
     void *q = nullptr;
-    cudaError_t e = cudaMalloc(&q, count * sizeof(T));
+    cudaError_t e = stream ? cudaMallocAsync(&q, count * sizeof(T), stream) : cudaMalloc(&q, count * sizeof(T));
     if (e != cudaSuccess) {
       cudaGetLastError();
       return make_err(AFMPB_ENOMEM, std::string("cudaMalloc ") + what + " (" +
@@ -137,14 +145,18 @@ struct DeviceArena {
   void release(void *p) {
     for (size_t i = 0; i < blocks.size(); ++i)
       if (blocks[i].first == p) {
-        cudaFree(p);
+        if (stream) cudaFreeAsync(p, stream);
+        else cudaFree(p);
         bytes -= blocks[i].second;
         blocks.erase(blocks.begin() + i);
         return;
       }
   }
   void free_all() {
-    for (auto &b : blocks) cudaFree(b.first);
+    for (auto &b : blocks) {
+      if (stream) cudaFreeAsync(b.first, stream);
+      else cudaFree(b.first);
+    }
     blocks.clear();
     bytes = 0;
   }

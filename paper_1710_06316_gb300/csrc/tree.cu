@@ -301,12 +301,29 @@ __global__ void __launch_bounds__(kExtThreads) k_extent_part(int64_t n, const do
   if (threadIdx.x < 6) part[6 * blockIdx.x + threadIdx.x] = sh[threadIdx.x][0];
 }
 
-__global__ void k_extent_final(int nblk, const double *__restrict__ part, double *__restrict__ out) {
-  if (threadIdx.x >= 6 || blockIdx.x != 0) return;
-  const int d = threadIdx.x;
-  double v = d < 3 ? 1e300 : -1e300;
-  for (int b = 0; b < nblk; ++b) v = d < 3 ? fmin(v, part[6 * b + d]) : fmax(v, part[6 * b + d]);
-  out[d] = v;
+__global__ void __launch_bounds__(kExtThreads) k_extent_final(int nblk, const double *__restrict__ part,
+                                                               double *__restrict__ out) {
+  __shared__ double sh[6][kExtThreads];
+  double l[3] = {1e300, 1e300, 1e300}, u[3] = {-1e300, -1e300, -1e300};
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x)
+    for (int d = 0; d < 3; ++d) {
+      l[d] = fmin(l[d], part[6 * b + d]);
+      u[d] = fmax(u[d], part[6 * b + 3 + d]);
+    }
+  for (int d = 0; d < 3; ++d) {
+    sh[d][threadIdx.x] = l[d];
+    sh[3 + d][threadIdx.x] = u[d];
+  }
+  __syncthreads();
+  for (int s = kExtThreads / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s)
+      for (int d = 0; d < 3; ++d) {
+        sh[d][threadIdx.x] = fmin(sh[d][threadIdx.x], sh[d][threadIdx.x + s]);
+        sh[3 + d][threadIdx.x] = fmax(sh[3 + d][threadIdx.x], sh[3 + d][threadIdx.x + s]);
+      }
+    __syncthreads();
+  }
+  if (threadIdx.x < 6) out[threadIdx.x] = sh[threadIdx.x][0];
 }
 
 __global__ void k_iota(int n, int32_t *__restrict__ v) {
@@ -686,7 +703,7 @@ Err build_tree(afmpb_t *h) {
     AFMPB_TRY(A.alloc(&d_part, 6 * (size_t)nblk, "extent parts"));
     AFMPB_TRY(A.alloc(&d_ext, 6, "extent"));
     k_extent_part<<<nblk, kExtThreads, 0, s>>>(n, h->d_xyz, d_part);
-    k_extent_final<<<1, 32, 0, s>>>(nblk, d_part, d_ext);
+    k_extent_final<<<1, kExtThreads, 0, s>>>(nblk, d_part, d_ext);
     AFMPB_TRY(check_launch("k_extent"));
     double ext6[6];
     AFMPB_CUDA(cudaMemcpyAsync(ext6, d_ext, sizeof(ext6), cudaMemcpyDeviceToHost, s));
