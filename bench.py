@@ -397,7 +397,9 @@ def rooflines(prof, info, n, order, peaks, kind, precision, sms):
     ms, _ = stages["m2l"]
     if precision == 1:
         flop3 = 3 * 2.0 * r * r * info["n_m2l_pairs"] * 2       # hi*hi, hi*lo, lo*hi; Laplace + Yukawa
-        out["m2l"] = {"bound": "tensor", "kernel": "k_m2l_tcp (tcgen05 BF16 x3, FP32 accumulate)",
+        kname = ("k_m2l_ts (target-stationary tcgen05 BF16 x3, FP32 accumulate)" if 0 < r <= 112
+                 else "k_m2l_tc (tcgen05 BF16 x3, FP32 accumulate)")
+        out["m2l"] = {"bound": "tensor", "kernel": kname,
                       "unit": "TFLOP/s", "achieved": flop3 / (ms * 1e-3) / 1e12, "peak": peaks["bf16_tflops"],
                       "peak_kind": "measured dense BF16 GEMM (burst)", "peak_source": kind,
                       "useful_achieved": flop3 / 3 / (ms * 1e-3) / 1e12, "ms_per_launch": ms,
