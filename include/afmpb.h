@@ -266,6 +266,35 @@ afmpb_status afmpb_inject_wait_expiry(afmpb_t *h);
  * is still stored and returned).  info may be NULL. */
 afmpb_status afmpb_solve(afmpb_t *h, double *f_host, double *h_host, afmpb_solve_info *info);
 
+/* Batched solve: k problems' GMRES in lockstep, with the products fused across them.
+ * The paper solves one problem at a time (Sec. 5 times single runs) and points to
+ * accelerators for the near field (Sec. 5, Sec. 6); running many small problems together
+ * on one GPU is this library's serving form of that solve.
+ * Each handle keeps its own tree, operators, Krylov basis (afmpb_options restart, orth,
+ * max_restart, tol of its creation) and solution; every Arnoldi step of all running
+ * problems is one pass of one device graph: one P2P launch over the union of their work
+ * units (ordered by cost across problems), one target-stationary tensor-core M2L launch
+ * over all their translation items (when every handle has precision 1 with the same
+ * compressed rank; else each problem's M2L stays in its own chain), and each problem's
+ * remaining product and orthogonalisation kernels on a branch of their own.  A problem
+ * whose Givens residual meets Eq. 7 or whose basis is full stops taking part at once (a
+ * device flag that its kernels and its share of the fused work check); a restart cycle of
+ * the batch is one graph launch and the host waits once per cycle.  The arithmetic of
+ * each problem is that of afmpb_solve; results differ from a lone solve only by the
+ * order of floating-point atomic additions.
+ *   hs          k distinct handles with charges, all on one device; 1 <= k <= AFMPB_BATCH_MAX
+ *   f_host, h_host  NULL, or k pointers each NULL or [N_i] (caller order) receiving the
+ *               surface solution of problem i
+ *   infos       NULL or [k]; ms_gmres is the batch's wall time, the same for all
+ *   statuses    NULL or [k]: OK, ENOCONV (max_restart cycles without the tolerance) or
+ *               ETIMEOUT (a bounded device wait of the batch expired) per problem
+ * Returns OK when every problem converged, else ENOCONV or ETIMEOUT as above, or EINVAL /
+ * ESTATE / ENOMEM / ECUDA for the batch.  The handles must not be used by other threads
+ * during the call. */
+#define AFMPB_BATCH_MAX 64
+afmpb_status afmpb_solve_batch(afmpb_t *const *hs, int k, double *const *f_host, double *const *h_host,
+                               afmpb_solve_info *infos, afmpb_status *statuses);
+
 /* Polar solvation energy (kcal/mol) of the last solution:
  * E = 1/2 sum_k q_k phi_reac(r_k), phi_reac from the interior Green representation of
  * the surface solution.  Requires a successful (or ENOCONV) afmpb_solve.  phi_reac is

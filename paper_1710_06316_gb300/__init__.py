@@ -136,7 +136,7 @@ EXPORTS = ["afmpb_create", "afmpb_matvec", "afmpb_matvec_parts", "afmpb_matvec_h
            "afmpb_server_get_info", "afmpb_server_destroy", "afmpb_get_autotune",
            "afmpb_selftest_bounded_wait", "afmpb_sync", "afmpb_inject_wait_expiry",
            "afmpb_plan_create", "afmpb_plan_get_rank", "afmpb_plan_get_halo", "afmpb_plan_get_send",
-           "afmpb_plan_get_boxes", "afmpb_plan_destroy"]
+           "afmpb_plan_get_boxes", "afmpb_plan_destroy", "afmpb_solve_batch"]
 
 
 def library_path() -> str:
@@ -179,6 +179,9 @@ def load(build: bool = True):
     lib.afmpb_solve.restype = I32
     lib.afmpb_solve.argtypes = [P, P, P, C.POINTER(SolveInfo)]
     lib.afmpb_energy.restype = I32
+    lib.afmpb_solve_batch.restype = I32
+    lib.afmpb_solve_batch.argtypes = [C.POINTER(P), I32, C.POINTER(P), C.POINTER(P), C.POINTER(SolveInfo),
+                                      C.POINTER(I32)]
     lib.afmpb_energy.argtypes = [P, C.POINTER(D)]
     lib.afmpb_energy_noalloc.restype = I32
     lib.afmpb_energy_noalloc.argtypes = [P, C.POINTER(D)]
@@ -424,6 +427,33 @@ class Handle:
 
     def __exit__(self, *a):
         self.close()
+
+
+BATCH_MAX = 64
+
+
+def solve_batch(handles, raise_on_noconv=True):
+    """Solves the problems of several handles together (afmpb_solve_batch): lockstep GMRES
+    with one fused P2P and one fused tensor-core M2L launch per Arnoldi step.  Returns one
+    (f, h, info) per handle, as Handle.solve does, info["status"] per problem."""
+    lib = load(build=False)
+    k = len(handles)
+    hs = (C.c_void_p * k)(*[h.h for h in handles])
+    fs = [np.zeros(h.n) for h in handles]
+    hh = [np.zeros(h.n) for h in handles]
+    fp = (C.c_void_p * k)(*[a.ctypes.data for a in fs])
+    hp = (C.c_void_p * k)(*[a.ctypes.data for a in hh])
+    infos = (SolveInfo * k)()
+    st = (C.c_int * k)()
+    rc = lib.afmpb_solve_batch(hs, k, fp, hp, infos, st)
+    out = []
+    for i in range(k):
+        d = _struct_dict(infos[i])
+        d["status"] = STATUS.get(st[i], st[i]) if rc in (0, 5, 6) else STATUS.get(rc, rc)
+        out.append((fs[i], hh[i], d))
+    if rc != 0 and (rc != 5 or raise_on_noconv):
+        _check(rc, handles[0].h if k else None)
+    return out
 
 
 def plan_partition(tree, n_nodes, nranks, near_ptr=None, near_col=None):

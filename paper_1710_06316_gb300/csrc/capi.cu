@@ -615,6 +615,44 @@ afmpb_status afmpb_solve(afmpb_t *h, double *f, double *hh, afmpb_solve_info *in
   } AFMPB_CATCH(h)
 }
 
+afmpb_status afmpb_solve_batch(afmpb_t *const *hs, int k, double *const *f, double *const *hh,
+                               afmpb_solve_info *infos, afmpb_status *statuses) {
+  afmpb_t *h0 = (hs && k > 0) ? hs[0] : nullptr;
+  try {
+    if (!hs || k < 1 || k > AFMPB_BATCH_MAX)
+      return fail(nullptr, make_err(AFMPB_EINVAL, "a batch takes 1 to AFMPB_BATCH_MAX handles"));
+    for (int i = 0; i < k; ++i) {
+      if (!hs[i]) return fail(nullptr, make_err(AFMPB_EINVAL, "a handle of the batch is NULL"));
+      if (hs[i]->natoms == 0)
+        return fail(hs[i], make_err(AFMPB_ESTATE, "a handle of the batch was created without charges"));
+      if (hs[i]->device != h0->device) return fail(hs[i], make_err(AFMPB_EINVAL, "the handles of a batch share one device"));
+      for (int j = 0; j < i; ++j)
+        if (hs[j] == hs[i]) return fail(hs[i], make_err(AFMPB_EINVAL, "a handle appears twice in the batch"));
+    }
+    for (int i = 0; i < k; ++i)
+      if (take_wait_expiry(hs[i])) return fail(hs[i], make_err(AFMPB_ETIMEOUT, kExpiredEarlier));
+    Err e = run_solve_batch(hs, k, infos, statuses);
+    if (!e.ok() && e.code != AFMPB_ENOCONV) return fail(h0, e);
+    for (int i = 0; i < k; ++i) {
+      afmpb_t *h = hs[i];
+      double *fi = f ? f[i] : nullptr, *hi = hh ? hh[i] : nullptr;
+      if (!fi && !hi) continue;
+      std::vector<double> xs(2 * h->n);
+      std::vector<int32_t> perm(h->n);
+      cudaError_t ce = cudaMemcpyAsync(xs.data(), h->d_sol, sizeof(double) * 2 * h->n, cudaMemcpyDeviceToHost, h->stream);
+      if (ce == cudaSuccess)
+        ce = cudaMemcpyAsync(perm.data(), h->d_perm, sizeof(int32_t) * h->n, cudaMemcpyDeviceToHost, h->stream);
+      if (ce == cudaSuccess) ce = cudaStreamSynchronize(h->stream);
+      if (ce != cudaSuccess) return fail(h, make_err(AFMPB_ECUDA, cudaGetErrorString(ce)));
+      for (int64_t p = 0; p < h->n; ++p) {
+        if (fi) fi[perm[p]] = xs[p];
+        if (hi) hi[perm[p]] = xs[h->n + p];
+      }
+    }
+    return e.ok() ? AFMPB_OK : fail(h0, e);
+  } AFMPB_CATCH(h0)
+}
+
 afmpb_status afmpb_energy(afmpb_t *h, double *E) {
   try {
     if (!h || !E) return fail(h, make_err(AFMPB_EINVAL, "handle and output are required"));

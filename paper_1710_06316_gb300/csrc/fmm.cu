@@ -518,24 +518,27 @@ __device__ __forceinline__ void store_or_add(float4 *p, float4 v, bool whole) {
   else asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w) : "memory");
 }
 
-__global__ void __launch_bounds__(kP2PThreads, kP2PRegBlocks) k_p2p(int nunits, const int4 *__restrict__ units,
-                                                      const int32_t *__restrict__ leaves,
-                                                      const int64_t *__restrict__ pptr,
-                                                      const int32_t *__restrict__ pidx,
-                                                      const int32_t *__restrict__ bbeg,
-                                                      const int32_t *__restrict__ bend,
-                                                      const dbl4 *__restrict__ center,
-                                                      const float4 *__restrict__ pos,
-                                                      const float4 *__restrict__ nrm,
-                                                      const float2 *__restrict__ xs, float inv_ebar,
-                                                      float kappa, float skip_scale,
-                                                      float4 *__restrict__ phi) {
+// A P2P argument: the kernel's own, or (batched) the unit's problem's, read from shared
+// memory where it is used so that no pointer stays live across the loops.
+#define P2P_ARG(name) (kBatch ? s_req.name : name##_1)
+
+// The body of the P2P kernels: with kBatch the work units of several problems share one
+// launch, unit.w naming the problem whose arrays (reqs[unit.w], copied to shared memory
+// per unit) it reads, and units of a problem whose *active flag is 0 are skipped.
+template <bool kBatch>
+__device__ __forceinline__ void p2p_body(int nunits, const int4 *__restrict__ units, const int32_t *__restrict__ leaves_1,
+                                         const int64_t *__restrict__ pptr_1, const int32_t *__restrict__ pidx_1,
+                                         const int32_t *__restrict__ bbeg_1, const int32_t *__restrict__ bend_1,
+                                         const dbl4 *__restrict__ center_1, const float4 *__restrict__ pos_1,
+                                         const float4 *__restrict__ nrm_1, const float2 *__restrict__ xs_1,
+                                         float inv_ebar_1, float kappa_1, float skip_scale_1, float4 *__restrict__ phi_1,
+                                         const P2PReq *__restrict__ reqs) {
   static_assert(2 * kP2PThreads <= kP2PPairs, "the reduction reuses the staging buffer");
   __shared__ float4 sa[kP2PPairs], sb[kP2PPairs], sc[kP2PPairs], sd[kP2PPairs];
   __shared__ int s_beg[kP2PBoxes], s_pre[kP2PBoxes + 1];
   __shared__ float s_off[kP2PBoxes][3];
+  __shared__ __align__(8) P2PReq s_req;
   float4 *red = sa;
-  const float2 inv_e = dup2(inv_ebar), kap = dup2(kappa);
   // The resident blocks walk the cost-ordered work units in boustrophedon order: in round
   // k block b takes unit k G + b for even k and k G + G - 1 - b for odd k (G blocks), so
   // the block that drew the costliest unit of one round draws the cheapest of the next.  A
@@ -547,34 +550,42 @@ __global__ void __launch_bounds__(kP2PThreads, kP2PRegBlocks) k_p2p(int nunits, 
   if (li >= nunits) continue;
   if (k > 0) __syncthreads();                           // the previous unit's reduction read red
   const int4 unit = units[li];
+  if constexpr (kBatch) {
+    static_assert(sizeof(P2PReq) % 8 == 0, "copied as 8-byte words");
+    if (threadIdx.x < sizeof(P2PReq) / 8)
+      reinterpret_cast<uint64_t *>(&s_req)[threadIdx.x] = reinterpret_cast<const uint64_t *>(reqs + unit.w)[threadIdx.x];
+    __syncthreads();
+    if (s_req.active && *s_req.active == 0) continue;  // uniform: the problem has stopped
+  }
+  const float2 inv_e = dup2(kBatch ? s_req.inv_ebar : inv_ebar_1), kap = dup2(kBatch ? s_req.kappa : kappa_1);
   const int leaf = unit.x;
-  const int b = leaves[leaf];
-  const dbl4 cb = center[b];
-  const int tb = bbeg[b], te = bend[b];
+  const int b = P2P_ARG(leaves)[leaf];
+  const dbl4 cb = P2P_ARG(center)[b];
+  const int tb = P2P_ARG(bbeg)[b], te = P2P_ARG(bend)[b];
   // each thread takes two targets, t and t + tile, against the same sources
   const int tile = min((te - tb + 1) / 2, kP2PThreads);
   const int slices = kP2PThreads / tile;
   const int ti = threadIdx.x % tile, si = threadIdx.x / tile;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t l0 = unit.y, l1 = unit.z;               // this unit's source boxes
-  const bool whole = l0 == pptr[leaf] && l1 == pptr[leaf + 1];
+  const bool whole = l0 == P2P_ARG(pptr)[leaf] && l1 == P2P_ARG(pptr)[leaf + 1];
   for (int t0 = tb; t0 < te; t0 += 2 * tile) {
     const int t = t0 + ti, t2 = t + tile;
     const bool act = si < slices && t < te;
     const bool act2 = act && t2 < te;
     P2PTarget tg, tg2;
     {
-      const float4 xp = act ? pos[t] : make_float4(0, 0, 0, 0);
-      const float4 np = act ? nrm[t] : make_float4(0, 0, 0, 0);
+      const float4 xp = act ? P2P_ARG(pos)[t] : make_float4(0, 0, 0, 0);
+      const float4 np = act ? P2P_ARG(nrm)[t] : make_float4(0, 0, 0, 0);
       tg.x = dup2(xp.x); tg.y = dup2(xp.y); tg.z = dup2(xp.z);
       tg.nx = dup2(np.x); tg.ny = dup2(np.y); tg.nz = dup2(np.z);
-      tg.rs = dup2(p2p_skip_radius(skip_scale, np.w));
+      tg.rs = dup2(p2p_skip_radius(P2P_ARG(skip_scale), np.w));
       // a missing second target repeats the first (its sums are not stored)
-      const float4 xq = act2 ? pos[t2] : xp;
-      const float4 nq = act2 ? nrm[t2] : np;
+      const float4 xq = act2 ? P2P_ARG(pos)[t2] : xp;
+      const float4 nq = act2 ? P2P_ARG(nrm)[t2] : np;
       tg2.x = dup2(xq.x); tg2.y = dup2(xq.y); tg2.z = dup2(xq.z);
       tg2.nx = dup2(nq.x); tg2.ny = dup2(nq.y); tg2.nz = dup2(nq.z);
-      tg2.rs = dup2(p2p_skip_radius(skip_scale, nq.w));
+      tg2.rs = dup2(p2p_skip_radius(P2P_ARG(skip_scale), nq.w));
     }
     float2 sL = dup2(0.f), nD = dup2(0.f), sY = dup2(0.f), dY = dup2(0.f);
     float2 sL2 = dup2(0.f), nD2 = dup2(0.f), sY2 = dup2(0.f), dY2 = dup2(0.f);
@@ -583,10 +594,10 @@ __global__ void __launch_bounds__(kP2PThreads, kP2PRegBlocks) k_p2p(int nunits, 
       __syncthreads();
       int mycnt = 0;
       if (threadIdx.x < nb) {
-        const int c = pidx[g0 + threadIdx.x];
-        const dbl4 cc = center[c];
-        s_beg[threadIdx.x] = bbeg[c];
-        mycnt = bend[c] - bbeg[c];
+        const int c = P2P_ARG(pidx)[g0 + threadIdx.x];
+        const dbl4 cc = P2P_ARG(center)[c];
+        s_beg[threadIdx.x] = P2P_ARG(bbeg)[c];
+        mycnt = P2P_ARG(bend)[c] - P2P_ARG(bbeg)[c];
         s_off[threadIdx.x][0] = (float)(cc.x - cb.x);
         s_off[threadIdx.x][1] = (float)(cc.y - cb.y);
         s_off[threadIdx.x][2] = (float)(cc.z - cb.z);
@@ -619,15 +630,15 @@ __global__ void __launch_bounds__(kP2PThreads, kP2PRegBlocks) k_p2p(int nunits, 
               if (s_pre[mid] <= j) lo = mid; else hi = mid;
             }
             const int sidx = s_beg[lo] + (j - s_pre[lo]);
-            const float4 p = pos[sidx], q = nrm[sidx];
-            const float2 fh = xs[sidx];
+            const float4 p = P2P_ARG(pos)[sidx], q = P2P_ARG(nrm)[sidx];
+            const float2 fh = P2P_ARG(xs)[sidx];
             px = __fadd_rn(p.x, s_off[lo][0]);
             py = __fadd_rn(p.y, s_off[lo][1]);
             pz = __fadd_rn(p.z, s_off[lo][2]);
             cw = p.w * fh.y;
             const float g = -p.w * fh.x;
             gx = g * q.x; gy = g * q.y; gz = g * q.z;
-            rs = p2p_skip_radius(skip_scale, q.w);
+            rs = p2p_skip_radius(P2P_ARG(skip_scale), q.w);
           }
           const int pr = e >> 1, ln = e & 1;
           float *fa = reinterpret_cast<float *>(sa + pr), *fb = reinterpret_cast<float *>(sb + pr);
@@ -658,18 +669,41 @@ __global__ void __launch_bounds__(kP2PThreads, kP2PRegBlocks) k_p2p(int nunits, 
         const float4 v = red[k * tile + ti];
         a.x += v.x; a.y += v.y; a.z += v.z; a.w += v.w;
       }
-      store_or_add(phi + t, make_float4(s * a.x, s * a.y, s * a.z, s * a.w), whole);
+      store_or_add(P2P_ARG(phi) + t, make_float4(s * a.x, s * a.y, s * a.z, s * a.w), whole);
       if (t2 < te) {
         float4 c = red[kP2PThreads + ti];
         for (int k = 1; k < slices; ++k) {
           const float4 v = red[kP2PThreads + k * tile + ti];
           c.x += v.x; c.y += v.y; c.z += v.z; c.w += v.w;
         }
-        store_or_add(phi + t2, make_float4(s * c.x, s * c.y, s * c.z, s * c.w), whole);
+        store_or_add(P2P_ARG(phi) + t2, make_float4(s * c.x, s * c.y, s * c.z, s * c.w), whole);
       }
     }
   }
   }
+}
+
+__global__ void __launch_bounds__(kP2PThreads, kP2PRegBlocks) k_p2p(int nunits, const int4 *__restrict__ units,
+                                                      const int32_t *__restrict__ leaves,
+                                                      const int64_t *__restrict__ pptr,
+                                                      const int32_t *__restrict__ pidx,
+                                                      const int32_t *__restrict__ bbeg,
+                                                      const int32_t *__restrict__ bend,
+                                                      const dbl4 *__restrict__ center,
+                                                      const float4 *__restrict__ pos,
+                                                      const float4 *__restrict__ nrm,
+                                                      const float2 *__restrict__ xs, float inv_ebar,
+                                                      float kappa, float skip_scale,
+                                                      float4 *__restrict__ phi) {
+  p2p_body<false>(nunits, units, leaves, pptr, pidx, bbeg, bend, center, pos, nrm, xs, inv_ebar, kappa, skip_scale,
+                  phi, nullptr);
+}
+
+// P2P of several problems in one launch: the units of all of them, cost-ordered together.
+__global__ void __launch_bounds__(kP2PThreads, kP2PRegBlocks) k_p2p_batch(int nunits, const int4 *__restrict__ units,
+                                                                          const P2PReq *__restrict__ reqs) {
+  p2p_body<true>(nunits, units, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0.f,
+                 0.f, 0.f, nullptr, reqs);
 }
 
 // ------------------------------------------------------------------------------------
@@ -761,26 +795,28 @@ Err init_cheb_tables() {
 }
 
 template <int N>
-Err launch_far(afmpb_t *h, cudaStream_t s, StageTimer *tm) {
+Err launch_far(afmpb_t *h, cudaStream_t s, StageTimer *tm, int parts) {
   constexpr int N3 = N * N * N;
   const auto &T = h->shape;
   const float inv_ebar = (float)(1.0 / h->ebar);
+  const int mthreads = ((2 * N3 + 31) / 32) * 32;
+  const bool compressed = !h->m2l_groups.empty() && h->m2l_rank > 0;
+  if (parts & kFarUp) {
   AFMPB_CUDA(cudaMemsetAsync(h->d_L, 0, sizeof(float) * (size_t)T.nbox * 2 * N3, s));
   k_p2m<N><<<T.nleaf, 256, 0, s>>>(T.nleaf, h->d_leaves, h->d_box_begin, h->d_box_end, h->d_box_center, h->d_pos,
                                    h->d_nrm, h->d_xs, inv_ebar, h->d_M);
   AFMPB_TRY(check_launch("k_p2m"));
   if (tm) tm->mark("p2m", 1);
-  const int mthreads = ((2 * N3 + 31) / 32) * 32;
   for (int level = T.nlevel - 2; level >= 2; --level) {
     int ls = T.lvl_start[level], nl = T.lvl_start[level + 1] - ls;
     k_m2m<N><<<nl, mthreads, 0, s>>>(ls, h->d_box_child0, h->d_box_nchild, h->d_box_anchor, h->d_M);
     AFMPB_TRY(check_launch("k_m2m"));
   }
   if (tm) tm->mark("m2m", std::max(0, T.nlevel - 3));
-  const bool compressed = !h->m2l_groups.empty() && h->m2l_rank > 0;
+  }
   if (compressed) {
-    AFMPB_TRY(enqueue_m2l_svd(h, s, tm));        // marks compress, m2l, expand itself
-  } else if (!h->m2l_groups.empty()) {
+    AFMPB_TRY(enqueue_m2l_svd(h, s, tm, parts));  // marks compress, m2l, expand itself
+  } else if (!h->m2l_groups.empty() && (parts & kFarM2L)) {
     if (h->opt.precision == 1) {
       AFMPB_TRY(enqueue_m2l_tc(h, s));
     } else {
@@ -793,6 +829,7 @@ Err launch_far(afmpb_t *h, cudaStream_t s, StageTimer *tm) {
     }
   }
   if (tm && !compressed) tm->mark("m2l", h->m2l_groups.empty() ? 0 : 1);
+  if (!(parts & kFarDown)) return Err{};
   if (h->n_xbox > 0) {
     k_p2l<N><<<(unsigned)h->n_xbox, 256, 0, s>>>(h->d_xbox, h->d_x_ptr, h->d_x_idx, h->d_box_begin,
                                                         h->d_box_end, h->d_box_center, h->d_pos, h->d_nrm, h->d_xs,
@@ -823,15 +860,15 @@ Err set_m2l_smem() {
 
 }  // namespace
 
-Err enqueue_far(afmpb_t *h, cudaStream_t s, StageTimer *tm) {
+Err enqueue_far(afmpb_t *h, cudaStream_t s, StageTimer *tm, int parts) {
   switch (h->order) {
-    case 2: return launch_far<2>(h, s, tm);
-    case 3: return launch_far<3>(h, s, tm);
-    case 4: return launch_far<4>(h, s, tm);
-    case 5: return launch_far<5>(h, s, tm);
-    case 6: return launch_far<6>(h, s, tm);
-    case 7: return launch_far<7>(h, s, tm);
-    case 8: return launch_far<8>(h, s, tm);
+    case 2: return launch_far<2>(h, s, tm, parts);
+    case 3: return launch_far<3>(h, s, tm, parts);
+    case 4: return launch_far<4>(h, s, tm, parts);
+    case 5: return launch_far<5>(h, s, tm, parts);
+    case 6: return launch_far<6>(h, s, tm, parts);
+    case 7: return launch_far<7>(h, s, tm, parts);
+    case 8: return launch_far<8>(h, s, tm, parts);
     default: return make_err(AFMPB_EINVAL, "fmm_order must be in [2, 8]");
   }
 }
@@ -849,6 +886,35 @@ Err enqueue_p2p(afmpb_t *h, cudaStream_t s) {
                                                   (float)(1.0 / h->ebar), (float)h->kappa,
                                                   (float)(kP2PSkip * h->opt.near_c), h->d_phi_near);
   return check_launch("k_p2p");
+}
+
+P2PReq p2p_req_of(const afmpb_t *h, const int *active) {
+  P2PReq q{};
+  q.leaves = h->d_leaves;
+  q.pptr = h->d_p2p_ptr;
+  q.pidx = h->d_p2p_idx;
+  q.bbeg = h->d_box_begin;
+  q.bend = h->d_box_end;
+  q.center = h->d_box_center;
+  q.pos = h->d_pos;
+  q.nrm = h->d_nrm;
+  q.xs = h->d_xs;
+  q.phi = h->d_phi_near;
+  q.active = active;
+  q.inv_ebar = (float)(1.0 / h->ebar);
+  q.kappa = (float)h->kappa;
+  q.skip_scale = (float)(kP2PSkip * h->opt.near_c);
+  return q;
+}
+
+Err enqueue_p2p_batch(const P2PReq *d_reqs, const int4 *d_units, int nunits, int resident, cudaStream_t s) {
+  if (nunits == 0) return Err{};
+  int dev = 0, sms = 0;
+  AFMPB_CUDA(cudaGetDevice(&dev));
+  AFMPB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int grid = std::max(1, std::min(nunits, std::min(resident, kP2PRegBlocks) * sms));
+  k_p2p_batch<<<grid, kP2PThreads, 0, s>>>(nunits, d_units, d_reqs);
+  return check_launch("k_p2p_batch");
 }
 
 Err enqueue_combine(afmpb_t *h, cudaStream_t s, int parts) {

@@ -208,7 +208,32 @@ struct __align__(16) TSItem {
   int base, end, run0, run1;
   int kt, table, rank;
   float scale;
-  int ent0, ent1, pad0, pad1;   // the item's entries [ent0, ent1) (its runs are consecutive)
+  int ent0, ent1, req, pad1;    // the item's entries [ent0, ent1) (its runs are consecutive);
+                                // req: the problem of a batched launch (0 otherwise)
+};
+
+// One problem of a batched P2P launch: the arrays and constants k_p2p takes, and a device
+// flag (nullable) that stops its units when 0.
+struct P2PReq {
+  const int32_t *leaves;
+  const int64_t *pptr;
+  const int32_t *pidx, *bbeg, *bend;
+  const dbl4 *center;
+  const float4 *pos, *nrm;
+  const float2 *xs;
+  float4 *phi;
+  const int *active;
+  float inv_ebar, kappa, skip_scale;
+};
+
+// One problem of a batched target-stationary M2L launch: its runs, entries, compressed
+// multipoles, tables and local expansions, and its stop flag.
+struct TSReq {
+  const int4 *runs;
+  const uint64_t *ent;
+  const void *Mc16, *tiles;
+  float *Lc;
+  const int *active;
 };
 
 }  // namespace afmpb
@@ -360,7 +385,8 @@ struct afmpb_t {
   double *d_V = nullptr, *d_w = nullptr, *d_H = nullptr, *d_g = nullptr, *d_cs = nullptr,
          *d_sn = nullptr, *d_part = nullptr, *d_hcol = nullptr, *d_hcol2 = nullptr, *d_scal = nullptr;
   double *h_pinned = nullptr;
-  int *d_gm_int = nullptr;         // [4] device step state: j, Arnoldi steps, second-pass flag, second passes
+  int *d_gm_int = nullptr;         // [8] device step state: j, Arnoldi steps, second-pass flag, second passes,
+                                   // running flag of a batched solve
   cudaGraphExec_t graph_cycle = nullptr;   // one GMRES cycle: a graph WHILE loop over Arnoldi steps
   int cycle_m = 0, cycle_orth = -1;        // restart length and orthogonalisation the cycle graph was built for
   // Laplace FMM over nodes and charges for the right-hand side and the energy (owned)
@@ -379,8 +405,16 @@ Err build_p2p_units(afmpb_t *h);       // P2P work units at h->p2p_units_per_blo
 Err build_near(afmpb_t *h);
 // fmm.cu
 Err build_fmm(afmpb_t *h);
-Err enqueue_far(afmpb_t *h, cudaStream_t s, StageTimer *tm = nullptr);   // P2M .. L2P into d_phi_far
+// Parts of the far-field chain: the upward pass to the compressed expansions, the M2L,
+// and the downward pass from the local expansions to d_phi_far.
+constexpr int kFarUp = 1, kFarM2L = 2, kFarDown = 4, kFarAll = 7;
+Err enqueue_far(afmpb_t *h, cudaStream_t s, StageTimer *tm = nullptr, int parts = kFarAll);   // P2M .. L2P
 Err enqueue_p2p(afmpb_t *h, cudaStream_t s);          // P2P into d_phi_near
+// The P2P arguments of a handle, with a stop flag for batched launches.
+P2PReq p2p_req_of(const afmpb_t *h, const int *active);
+// One P2P launch over the units of several problems (unit.w names the problem); every
+// problem's d_phi_near must be zeroed before it.
+Err enqueue_p2p_batch(const P2PReq *d_reqs, const int4 *d_units, int nunits, int resident, cudaStream_t s);
 Err enqueue_combine(afmpb_t *h, cudaStream_t s, int parts);
 Err enqueue_m2l_tc(afmpb_t *h, cudaStream_t s);       // tensor-core M2L (precision 1)
 Err build_m2l_tc(afmpb_t *h);
@@ -388,6 +422,10 @@ Err build_m2l_tc(afmpb_t *h);
 bool m2l_ts_applies(const afmpb_t *h);
 Err build_m2l_ts(afmpb_t *h);
 Err enqueue_m2l_ts(afmpb_t *h, cudaStream_t s);
+// One target-stationary M2L launch over the items of several problems (TSItem.req names
+// the problem); the items of stopped problems are compacted away first on the device.
+Err enqueue_m2l_ts_batch(const TSReq *d_reqs, const TSItem *d_items, int nitems, TSItem *d_items_run, int *d_count,
+                         int R, int *err_flag, cudaStream_t s);
 Err cut_m2l_ts_items(afmpb_t *h);      // items from the stored runs at h->ts_runs_per_item
 Err autotune_tiles(afmpb_t *h, afmpb_autotune_report *rep);   // autotune.cu: P2P and M2L tile shapes
 void autotune_cache_tiles(const afmpb_t *h);
@@ -397,7 +435,7 @@ Err autotune_leaf_cap(afmpb_t *h, afmpb_autotune_report *rep);
 int autotune_cached_cap(int precision, int order, double kappa, int64_t n);   // 0 if none
 // m2l_svd.cu: compressed translations; *compressed = false leaves the full ones in use
 Err build_m2l_svd(afmpb_t *h, bool *compressed);
-Err enqueue_m2l_svd(afmpb_t *h, cudaStream_t s, StageTimer *tm = nullptr);   // compress, translate, expand
+Err enqueue_m2l_svd(afmpb_t *h, cudaStream_t s, StageTimer *tm = nullptr, int parts = kFarAll);   // compress, translate, expand
 Err alloc_wait_flag(afmpb_t *h);       // the mapped error flag of the bounded waits (once per handle)
 // Waits for the handle's stream, then reports (and clears) the bounded-wait flag: *flag = 1
 // when a wait of work queued on the handle expired since the last report.
@@ -420,6 +458,33 @@ Err build_charge_fmm(afmpb_t *h);
 Err charge_fmm_rhs(afmpb_t *h, double *b);       // b [2n], Morton order
 Err charge_fmm_phi(afmpb_t *h, double *phi);     // reaction potential at the charges (with 1/(4 pi))
 Err run_energy_noalloc(afmpb_t *h, double *E);      // static scratch, no allocation
+// batch.cu: the merged work lists and descriptors of a batched solve, in stream-ordered
+// device memory freed with the object
+struct BatchLists {
+  cudaStream_t stream = nullptr;
+  std::vector<void *> bufs;
+  P2PReq *d_p2p = nullptr;
+  int **d_gms = nullptr;              // each problem's step state (gm[4]: running)
+  int4 *d_units = nullptr;            // P2P units of all problems, by cost (unit.w = problem)
+  int nunits = 0;
+  TSReq *d_ts = nullptr;
+  TSItem *d_items = nullptr, *d_items_run = nullptr;   // M2L items of all problems; the running ones
+  int *d_count = nullptr;
+  int nitems = 0;
+  BatchLists() = default;
+  BatchLists(const BatchLists &) = delete;
+  BatchLists &operator=(const BatchLists &) = delete;
+  ~BatchLists();
+  Err alloc_bytes(void **p, size_t bytes, const char *what);
+  template <class T>
+  Err alloc(T **p, int64_t n, const char *what) {
+    return alloc_bytes(reinterpret_cast<void **>(p), sizeof(T) * (size_t)(n > 0 ? n : 1), what);
+  }
+};
+Err build_batch_lists(afmpb_t *const *hs, int k, bool fuse_m2l, BatchLists &L);
+// solve.cu: lockstep GMRES of k handles (one graph launch per restart cycle for all)
+Err run_solve_batch(afmpb_t *const *hs, int k, afmpb_solve_info *infos, afmpb_status *statuses);
+
 // capi.cu
 Err product_sorted(afmpb_t *h, cudaStream_t s, int parts);  // d_xs -> d_ys
 Err enqueue_product_kernels(afmpb_t *h, cudaStream_t cap);   // d_xs -> d_ys on a capturing stream

@@ -645,17 +645,20 @@ Err build_m2l_svd(afmpb_t *h, bool *compressed) {
   return Err{};
 }
 
-Err enqueue_m2l_svd(afmpb_t *h, cudaStream_t s, StageTimer *tm) {
+Err enqueue_m2l_svd(afmpb_t *h, cudaStream_t s, StageTimer *tm, int parts) {
   const int R = h->m2l_rank, N3 = h->ncoef;
   const auto &T = h->shape;
-  AFMPB_CUDA(cudaMemsetAsync(h->d_Lc, 0, sizeof(float) * (size_t)T.nbox * 2 * R, s));
+  if (parts & kFarUp) AFMPB_CUDA(cudaMemsetAsync(h->d_Lc, 0, sizeof(float) * (size_t)T.nbox * 2 * R, s));
   if (h->m2l_nchunks == 0) return Err{};
   const dim3 cgrid((unsigned)h->m2l_nchunks, 2);
-  AFMPB_TRY(launch_box_basis<false>(s, cgrid, N3, R, h->d_m2l_chunks, h->d_level_table, h->d_table_rank,
-                                     h->m2l_yuk_levels, h->d_Q, h->d_M, h->d_Mc,
-                                     reinterpret_cast<__nv_bfloat16 *>(h->d_Mc16)));
-  if (tm) tm->mark("compress", 2);             // Lc memset + basis change
-  if (h->opt.precision == 1) {
+  if (parts & kFarUp) {
+    AFMPB_TRY(launch_box_basis<false>(s, cgrid, N3, R, h->d_m2l_chunks, h->d_level_table, h->d_table_rank,
+                                       h->m2l_yuk_levels, h->d_Q, h->d_M, h->d_Mc,
+                                       reinterpret_cast<__nv_bfloat16 *>(h->d_Mc16)));
+    if (tm) tm->mark("compress", 2);             // Lc memset + basis change
+  }
+  if (!(parts & kFarM2L)) {
+  } else if (h->opt.precision == 1) {
     AFMPB_TRY(enqueue_m2l_tc(h, s));
   } else {
     switch ((R + 31) / 32) {
@@ -667,7 +670,8 @@ Err enqueue_m2l_svd(afmpb_t *h, cudaStream_t s, StageTimer *tm) {
       default: AFMPB_TRY(launch_m2l_c<6>(h, s)); break;
     }
   }
-  if (tm) tm->mark("m2l", 1);
+  if (tm && (parts & kFarM2L)) tm->mark("m2l", 1);
+  if (!(parts & kFarDown)) return Err{};
   AFMPB_TRY(launch_box_basis<true>(s, cgrid, R, N3, h->d_m2l_chunks, h->d_level_table, h->d_table_rank,
                                    h->m2l_yuk_levels, h->d_QT, h->d_Lc, h->d_L));
   if (tm) tm->mark("expand", 1);

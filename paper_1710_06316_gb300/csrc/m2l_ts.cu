@@ -85,14 +85,29 @@ __device__ __forceinline__ void red_add_v4(float *addr, float a, float b, float 
                : "memory");
 }
 
-template <int NS>
-__global__ void __launch_bounds__(kTsThreads) k_m2l_ts(int R, int nitems, const TSItem *__restrict__ items,
-                                                      const int4 *__restrict__ runs,
-                                                      const uint64_t *__restrict__ ent,
-                                                      const __nv_bfloat16 *__restrict__ Mc16,
-                                                      const __nv_bfloat16 *__restrict__ tiles,
-                                                      float *__restrict__ Lc, int *__restrict__ err_flag) {
+// With kBatch the items of several problems share the launch: item.req names the problem
+// whose runs, entries, multipoles, tables and local expansions (reqs[item.req]) it uses,
+// and the item count is read from *d_nitems (a list compacted to the running problems).
+template <int NS, bool kBatch>
+__global__ void __launch_bounds__(kTsThreads) k_m2l_ts(int R, int nitems_arg, const TSItem *__restrict__ items,
+                                                      const int4 *__restrict__ runs_1,
+                                                      const uint64_t *__restrict__ ent_1,
+                                                      const __nv_bfloat16 *__restrict__ Mc16_1,
+                                                      const __nv_bfloat16 *__restrict__ tiles_1,
+                                                      float *__restrict__ Lc_1, int *__restrict__ err_flag,
+                                                      const int *__restrict__ d_nitems,
+                                                      const TSReq *__restrict__ reqs) {
   extern __shared__ __align__(128) uint8_t smem[];
+  const int nitems = kBatch ? *d_nitems : nitems_arg;
+  auto runs_of = [&](const TSItem &it) -> const int4 * { return kBatch ? reqs[it.req].runs : runs_1; };
+  auto ent_of = [&](const TSItem &it) -> const uint64_t * { return kBatch ? reqs[it.req].ent : ent_1; };
+  auto mc_of = [&](const TSItem &it) -> const __nv_bfloat16 * {
+    return kBatch ? reinterpret_cast<const __nv_bfloat16 *>(reqs[it.req].Mc16) : Mc16_1;
+  };
+  auto tiles_of = [&](const TSItem &it) -> const __nv_bfloat16 * {
+    return kBatch ? reinterpret_cast<const __nv_bfloat16 *>(reqs[it.req].tiles) : tiles_1;
+  };
+  auto lc_of = [&](const TSItem &it) -> float * { return kBatch ? reqs[it.req].Lc : Lc_1; };
   // stage s: A hi, A lo (kTsRows x R each), B hi, B lo (R x R each)
   const uint32_t a_bytes = (uint32_t)(kTsRows * R * 2), b_bytes = (uint32_t)(R * R * 2);
   const uint32_t stage_bytes = 2 * a_bytes + 2 * b_bytes;
@@ -161,11 +176,11 @@ __global__ void __launch_bounds__(kTsThreads) k_m2l_ts(int R, int nitems, const 
       asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb_item[b]), "r"(rb + eb) : "memory");
       asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                        cvta_smem(&s_runs[b][0])),
-                   "l"(runs + it.run0), "r"(rb), "r"(mb_item[b])
+                   "l"(runs_of(it) + it.run0), "r"(rb), "r"(mb_item[b])
                    : "memory");
       asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                        cvta_smem(&s_ent[b][0])),
-                   "l"(ent + a0), "r"(eb), "r"(mb_item[b])
+                   "l"(ent_of(it) + a0), "r"(eb), "r"(mb_item[b])
                    : "memory");
     };
     int issued = -1, waited = -1;                        // item positions loaded / waited for (thread 0 issues)
@@ -189,7 +204,7 @@ __global__ void __launch_bounds__(kTsThreads) k_m2l_ts(int R, int nitems, const 
       const uint32_t st = s_base + (uint32_t)s * stage_bytes;
       if (threadIdx.x == 0) {
         // C_o of the item's table: hi and lo tiles, counted on the stage's full barrier
-        const __nv_bfloat16 *src = tiles + ((size_t)c_item.table * kNumOffsets + run.x) * 2 * R * R;
+        const __nv_bfloat16 *src = tiles_of(c_item) + ((size_t)c_item.table * kNumOffsets + run.x) * 2 * R * R;
         asm volatile("mbarrier.expect_tx.shared::cta.b64 [%0], %1;" ::"r"(mb_full[s]), "r"(2 * b_bytes) : "memory");
         asm volatile(
             "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
@@ -213,7 +228,7 @@ __global__ void __launch_bounds__(kTsThreads) k_m2l_ts(int R, int nitems, const 
       const bool now = (s_new[s][row >> 5] >> (row & 31)) & 1u;
       if (have) {
         const int kg = c_item.rank / 8;                  // 16-byte groups along K that the MMAs read
-        const __nv_bfloat16 *g = Mc16 + ((size_t)psrc * 2 + c_item.kt) * 2 * R;
+        const __nv_bfloat16 *g = mc_of(c_item) + ((size_t)psrc * 2 + c_item.kt) * 2 * R;
         for (int k8 = 0; k8 < kg; ++k8) {
           const uint32_t off = canon_off(prow, k8 * 8, kTsRows);
           cp_async16_zfill(st + off, g + k8 * 8, true);
@@ -361,7 +376,7 @@ __global__ void __launch_bounds__(kTsThreads) k_m2l_ts(int R, int nitems, const 
       asm volatile("tcgen05.fence::after_thread_sync;");
       const int box = item.base + row;
       const bool valid = box < item.end;
-      float *out = Lc + ((size_t)(valid ? box : 0) * 2 + item.kt) * R;
+      float *out = lc_of(item) + ((size_t)(valid ? box : 0) * 2 + item.kt) * R;
       for (int c0 = 0; c0 < item.rank; c0 += 16) {
         uint32_t v[16];
         const uint32_t taddr = tmem + ((uint32_t)(32 * ew) << 16) + (uint32_t)(a * R + c0);
@@ -488,8 +503,13 @@ Err build_m2l_ts(afmpb_t *h) {
   k_ts_tables<<<2048, 256, 0, s>>>(R, h->m2l_ntables, h->d_C, reinterpret_cast<__nv_bfloat16 *>(h->d_ts_tiles));
   AFMPB_TRY(check_launch("k_ts_tables"));
   AFMPB_TRY(alloc_wait_flag(h));
-  if (ts_stages(R) == 4) AFMPB_TRY(raise_smem_limit((const void *)k_m2l_ts<4>, ts_smem_bytes(R)));
-  else AFMPB_TRY(raise_smem_limit((const void *)k_m2l_ts<2>, ts_smem_bytes(R)));
+  if (ts_stages(R) == 4) {
+    AFMPB_TRY(raise_smem_limit((const void *)k_m2l_ts<4, false>, ts_smem_bytes(R)));
+    AFMPB_TRY(raise_smem_limit((const void *)k_m2l_ts<4, true>, ts_smem_bytes(R)));
+  } else {
+    AFMPB_TRY(raise_smem_limit((const void *)k_m2l_ts<2, false>, ts_smem_bytes(R)));
+    AFMPB_TRY(raise_smem_limit((const void *)k_m2l_ts<2, true>, ts_smem_bytes(R)));
+  }
   AFMPB_CUDA(cudaStreamSynchronize(s));
   return Err{};
 }
@@ -575,12 +595,78 @@ Err enqueue_m2l_ts(afmpb_t *h, cudaStream_t s) {
   const auto *mc = reinterpret_cast<const __nv_bfloat16 *>(h->d_Mc16);
   const auto *tl = reinterpret_cast<const __nv_bfloat16 *>(h->d_ts_tiles);
   if (ts_stages(R) == 4)
-    k_m2l_ts<4><<<grid, kTsThreads, ts_smem_bytes(R), s>>>(R, h->ts_nitems, h->d_ts_items, h->d_ts_runs, h->d_ts_ent,
-                                                           mc, tl, h->d_Lc, h->d_tc_flag);
+    k_m2l_ts<4, false><<<grid, kTsThreads, ts_smem_bytes(R), s>>>(R, h->ts_nitems, h->d_ts_items, h->d_ts_runs,
+                                                                  h->d_ts_ent, mc, tl, h->d_Lc, h->d_tc_flag,
+                                                                  nullptr, nullptr);
   else
-    k_m2l_ts<2><<<grid, kTsThreads, ts_smem_bytes(R), s>>>(R, h->ts_nitems, h->d_ts_items, h->d_ts_runs, h->d_ts_ent,
-                                                           mc, tl, h->d_Lc, h->d_tc_flag);
+    k_m2l_ts<2, false><<<grid, kTsThreads, ts_smem_bytes(R), s>>>(R, h->ts_nitems, h->d_ts_items, h->d_ts_runs,
+                                                                  h->d_ts_ent, mc, tl, h->d_Lc, h->d_tc_flag,
+                                                                  nullptr, nullptr);
   return check_launch("k_m2l_ts");
+}
+
+// The items of the running problems of a batch, in their order: one block scans the
+// flags 1024 items at a time.
+__global__ void __launch_bounds__(1024) k_ts_compact(int n, const TSItem *__restrict__ in, const TSReq *__restrict__ reqs,
+                                                     TSItem *__restrict__ out, int *__restrict__ count) {
+  __shared__ int s_warp[32];
+  __shared__ int s_base;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) s_base = 0;
+  __syncthreads();
+  for (int c0 = 0; c0 < n; c0 += 1024) {
+    const int i = c0 + (int)threadIdx.x;
+    TSItem it{};
+    int keep = 0;
+    if (i < n) {
+      it = in[i];
+      const int *a = reqs[it.req].active;
+      keep = (a == nullptr || *a != 0) ? 1 : 0;
+    }
+    int v = keep;                                        // inclusive scan within the warp
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int u = __shfl_up_sync(0xffffffffu, v, o);
+      if (lane >= o) v += u;
+    }
+    if (lane == 31) s_warp[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+      int w = s_warp[lane];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, w, o);
+        if (lane >= o) w += u;
+      }
+      s_warp[lane] = w;                                  // inclusive over warps
+    }
+    __syncthreads();
+    const int before = s_base + (warp > 0 ? s_warp[warp - 1] : 0) + v - keep;
+    if (keep) out[before] = it;
+    __syncthreads();
+    if (threadIdx.x == 0) s_base += s_warp[31];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *count = s_base;
+}
+
+Err enqueue_m2l_ts_batch(const TSReq *d_reqs, const TSItem *d_items, int nitems, TSItem *d_items_run, int *d_count,
+                         int R, int *err_flag, cudaStream_t s) {
+  if (nitems == 0) return Err{};
+  int dev = 0, sms = 0;
+  AFMPB_CUDA(cudaGetDevice(&dev));
+  AFMPB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  k_ts_compact<<<1, 1024, 0, s>>>(nitems, d_items, d_reqs, d_items_run, d_count);
+  AFMPB_TRY(check_launch("k_ts_compact"));
+  const int per_sm = std::max(1, std::min(2, (227 * 1024) / (ts_smem_bytes(R) + 12 * 1024)));
+  const unsigned grid = (unsigned)std::min(nitems, per_sm * sms);
+  if (ts_stages(R) == 4)
+    k_m2l_ts<4, true><<<grid, kTsThreads, ts_smem_bytes(R), s>>>(R, 0, d_items_run, nullptr, nullptr, nullptr,
+                                                                 nullptr, nullptr, err_flag, d_count, d_reqs);
+  else
+    k_m2l_ts<2, true><<<grid, kTsThreads, ts_smem_bytes(R), s>>>(R, 0, d_items_run, nullptr, nullptr, nullptr,
+                                                                 nullptr, nullptr, err_flag, d_count, d_reqs);
+  return check_launch("k_m2l_ts batch");
 }
 
 }  // namespace afmpb

@@ -165,9 +165,11 @@ Err enqueue_to_xs(afmpb_t *h, cudaStream_t s, const double *v) {
   return check_launch("k_to_xs");
 }
 
-// w = ys (FP32 -> FP64), optionally w = b - ys
+// w = ys (FP32 -> FP64), optionally w = b - ys; returns at once when guard is set and
+// *guard == 0 (a stopped problem of a batch)
 __global__ void k_from_ys(int64_t len, const float *__restrict__ ys, const double *__restrict__ b,
-                          double *__restrict__ w) {
+                          double *__restrict__ w, const int *__restrict__ guard) {
+  if (guard && *guard == 0) return;
   int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (k >= len) return;
   w[k] = b ? b[k] - (double)ys[k] : (double)ys[k];
@@ -291,7 +293,8 @@ Err norm2(afmpb_t *h, int64_t len, const double *w, double *out) { return multid
 constexpr double kReorthTol = 1e-3;
 
 __global__ void k_to_xs_j(int64_t n, const double *__restrict__ V, int64_t n2, const int *__restrict__ gm,
-                          float2 *__restrict__ xs) {
+                          float2 *__restrict__ xs, const int *__restrict__ guard) {
+  if (guard && *guard == 0) return;
   const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (p >= n) return;
   const double *v = V + (int64_t)gm[0] * n2;
@@ -364,8 +367,9 @@ __global__ void k_norm_to_j(int nblk, const double *__restrict__ part, int strid
 // One-reduction form: hcol[0..j] = V^T w and hcol[j+1] = ||w||^2 from the fused reduction.
 // ||w - V h||^2 = ||w||^2 - ||h||^2 (Pythagoras, V orthonormal); below kReorthTol^2 ||w||^2
 // the difference has lost its digits and the orthogonality is in doubt: flag a second pass.
-__global__ void k_pythagoras_j(int *__restrict__ gm, double *__restrict__ hcol) {
+__global__ void k_pythagoras_j(int *__restrict__ gm, double *__restrict__ hcol, const int *__restrict__ guard) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (guard && *guard == 0) return;
   const int j = gm[0];
   const double wsq = hcol[j + 1];
   double hsq = 0.0;
@@ -382,7 +386,9 @@ __global__ void k_pythagoras_j(int *__restrict__ gm, double *__restrict__ hcol) 
 
 // V_{j+1} = w / hcol[j+1]
 __global__ void k_normalize_j(int64_t n, const double *__restrict__ w, const double *__restrict__ hcol,
-                              const int *__restrict__ gm, double *__restrict__ V, int64_t n2) {
+                              const int *__restrict__ gm, double *__restrict__ V, int64_t n2,
+                              const int *__restrict__ guard) {
+  if (guard && *guard == 0) return;
   const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (p >= n) return;
   const int j = gm[0];
@@ -395,8 +401,9 @@ __global__ void k_normalize_j(int64_t n, const double *__restrict__ w, const dou
 // Givens update of Hessenberg column j (as k_givens, j from the device)
 __global__ void k_givens_j(const int *__restrict__ gm, int m, const double *__restrict__ hcol, double *__restrict__ H,
                            double *__restrict__ cs, double *__restrict__ sn, double *__restrict__ g,
-                           double *__restrict__ res) {
+                           double *__restrict__ res, const int *__restrict__ guard) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (guard && *guard == 0) return;
   const int j = gm[0];
   double *col = H + (int64_t)j * (m + 1);
   for (int i = 0; i <= j + 1; ++i) col[i] = hcol[i];
@@ -479,10 +486,57 @@ Err restart_length(afmpb_t *h, int *m) {
   return Err{};
 }
 
+// The Arnoldi step around the product: V_j to the FP32 product input, then (after the
+// product) orthogonalisation, normalisation and the Givens update.  `act` (nullable) is a
+// batch problem's running flag: every kernel returns at once while it is 0.
+Err enqueue_step_head(afmpb_t *h, cudaStream_t cap, const int *act) {
+  const int64_t n = h->n, n2 = 2 * n;
+  k_to_xs_j<<<div_up(n, 256), 256, 0, cap>>>(n, h->d_V, n2, h->d_gm_int, h->d_xs, act);
+  return check_launch("k_to_xs_j");
+}
+
+Err enqueue_step_tail(afmpb_t *h, int m, cudaStream_t cap, const int *act) {
+  const int64_t n = h->n, n2 = 2 * n;
+  const int orth = h->opt.orth;
+  const int *gm = h->d_gm_int;
+  int *gmw = h->d_gm_int;
+  const int *guard = gm + 2;              // second-pass flag: 0 whenever the problem is stopped
+  const int *first = act;                 // the first pass runs while the problem runs
+  const int nb = red_blocks(n2), stride = m + 2;
+  const int nb_el = div_up(n, 256), nb_el2 = div_up(n2, 256);
+  const int nb_comb = std::min(nb_el2, 4 * 1184);
+  k_from_ys<<<nb_el2, 256, 0, cap>>>(n2, h->d_ys, nullptr, h->d_w, act);
+  if (orth == 0) {      // classical Gram-Schmidt twice, then the norm: three reductions
+    k_multidot_j<<<nb, kRedThreads, 0, cap>>>(n2, gm, h->d_V, n2, h->d_w, h->d_part, stride, 0, first);
+    k_reduce_parts_j<<<m + 1, 256, 0, cap>>>(nb, gm, 0, h->d_part, stride, h->d_hcol, first);
+    k_sub_combo_j<<<nb_comb, 256, 0, cap>>>(n2, gm, h->d_V, n2, h->d_hcol, h->d_w, first);
+    k_multidot_j<<<nb, kRedThreads, 0, cap>>>(n2, gm, h->d_V, n2, h->d_w, h->d_part, stride, 0, first);
+    k_reduce_parts_j<<<m + 1, 256, 0, cap>>>(nb, gm, 0, h->d_part, stride, h->d_hcol2, first);
+    k_sub_combo_j<<<nb_comb, 256, 0, cap>>>(n2, gm, h->d_V, n2, h->d_hcol2, h->d_w, first);
+    k_add_small_j<<<1, 128, 0, cap>>>(gm, h->d_hcol2, h->d_hcol, first);
+    if (act) k_multidot_j<<<nb, kRedThreads, 0, cap>>>(n2, gm, h->d_V, n2, h->d_w, h->d_part, stride, 2, act);
+    else k_multidot<<<nb, kRedThreads, 0, cap>>>(n2, 1, h->d_w, 0, h->d_w, h->d_part, stride);
+    k_norm_to_j<<<1, 256, 0, cap>>>(nb, h->d_part, stride, gm, h->d_hcol, first);
+  } else {              // one fused reduction; a guarded second pass on loss of orthogonality
+    k_multidot_j<<<nb, kRedThreads, 0, cap>>>(n2, gm, h->d_V, n2, h->d_w, h->d_part, stride, 1, first);
+    k_reduce_parts_j<<<m + 2, 256, 0, cap>>>(nb, gm, 1, h->d_part, stride, h->d_hcol, first);
+    k_sub_combo_j<<<nb_comb, 256, 0, cap>>>(n2, gm, h->d_V, n2, h->d_hcol, h->d_w, first);
+    k_pythagoras_j<<<1, 1, 0, cap>>>(gmw, h->d_hcol, act);
+    k_multidot_j<<<nb, kRedThreads, 0, cap>>>(n2, gm, h->d_V, n2, h->d_w, h->d_part, stride, 0, guard);
+    k_reduce_parts_j<<<m + 1, 256, 0, cap>>>(nb, gm, 0, h->d_part, stride, h->d_hcol2, guard);
+    k_sub_combo_j<<<nb_comb, 256, 0, cap>>>(n2, gm, h->d_V, n2, h->d_hcol2, h->d_w, guard);
+    k_add_small_j<<<1, 128, 0, cap>>>(gm, h->d_hcol2, h->d_hcol, guard);
+    k_multidot_j<<<nb, kRedThreads, 0, cap>>>(n2, gm, h->d_V, n2, h->d_w, h->d_part, stride, 2, guard);
+    k_norm_to_j<<<1, 256, 0, cap>>>(nb, h->d_part, stride, gm, h->d_hcol, guard);
+  }
+  k_normalize_j<<<nb_el, 256, 0, cap>>>(n, h->d_w, h->d_hcol, gm, h->d_V, n2, act);
+  k_givens_j<<<1, 1, 0, cap>>>(gm, m, h->d_hcol, h->d_H, h->d_cs, h->d_sn, h->d_g, h->d_scal + 2, act);
+  return check_launch("arnoldi step");
+}
+
 // The cycle graph: a WHILE node whose body is one Arnoldi step (the FP32 product of V_j,
 // orthogonalisation, normalisation, Givens update, stop test).
 Err build_cycle_graph(afmpb_t *h, int m) {
-  const int64_t n = h->n, n2 = 2 * n;
   const int orth = h->opt.orth;
   if (h->graph_cycle) {
     cudaGraphExecDestroy(h->graph_cycle);
@@ -507,43 +561,11 @@ Err build_cycle_graph(afmpb_t *h, int m) {
   AFMPB_CUDA(cudaStreamCreateWithPriority(&cap, cudaStreamNonBlocking, hi));
   struct StreamGuard { cudaStream_t s; ~StreamGuard() { cudaStreamDestroy(s); } } sg{cap};
   AFMPB_CUDA(cudaStreamBeginCaptureToGraph(cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-  const int *gm = h->d_gm_int;
-  int *gmw = h->d_gm_int;
-  const int *guard = gm + 2;
-  const int nb = red_blocks(n2), stride = m + 2;
-  const int nb_el = div_up(n, 256), nb_el2 = div_up(n2, 256);
-  const int nb_comb = std::min(nb_el2, 4 * 1184);
-  Err e;
-  k_to_xs_j<<<nb_el, 256, 0, cap>>>(n, h->d_V, n2, gm, h->d_xs);
-  e = check_launch("k_to_xs_j");
+  Err e = enqueue_step_head(h, cap, nullptr);
   if (e.ok()) e = enqueue_product_kernels(h, cap);
+  if (e.ok()) e = enqueue_step_tail(h, m, cap, nullptr);
   if (e.ok()) {
-    k_from_ys<<<nb_el2, 256, 0, cap>>>(n2, h->d_ys, nullptr, h->d_w);
-    if (orth == 0) {      // classical Gram-Schmidt twice, then the norm: three reductions
-      k_multidot_j<<<nb, kRedThreads, 0, cap>>>(n2, gm, h->d_V, n2, h->d_w, h->d_part, stride, 0, nullptr);
-      k_reduce_parts_j<<<m + 1, 256, 0, cap>>>(nb, gm, 0, h->d_part, stride, h->d_hcol, nullptr);
-      k_sub_combo_j<<<nb_comb, 256, 0, cap>>>(n2, gm, h->d_V, n2, h->d_hcol, h->d_w, nullptr);
-      k_multidot_j<<<nb, kRedThreads, 0, cap>>>(n2, gm, h->d_V, n2, h->d_w, h->d_part, stride, 0, nullptr);
-      k_reduce_parts_j<<<m + 1, 256, 0, cap>>>(nb, gm, 0, h->d_part, stride, h->d_hcol2, nullptr);
-      k_sub_combo_j<<<nb_comb, 256, 0, cap>>>(n2, gm, h->d_V, n2, h->d_hcol2, h->d_w, nullptr);
-      k_add_small_j<<<1, 128, 0, cap>>>(gm, h->d_hcol2, h->d_hcol, nullptr);
-      k_multidot<<<nb, kRedThreads, 0, cap>>>(n2, 1, h->d_w, 0, h->d_w, h->d_part, stride);
-      k_norm_to_j<<<1, 256, 0, cap>>>(nb, h->d_part, stride, gm, h->d_hcol, nullptr);
-    } else {              // one fused reduction; a guarded second pass on loss of orthogonality
-      k_multidot_j<<<nb, kRedThreads, 0, cap>>>(n2, gm, h->d_V, n2, h->d_w, h->d_part, stride, 1, nullptr);
-      k_reduce_parts_j<<<m + 2, 256, 0, cap>>>(nb, gm, 1, h->d_part, stride, h->d_hcol, nullptr);
-      k_sub_combo_j<<<nb_comb, 256, 0, cap>>>(n2, gm, h->d_V, n2, h->d_hcol, h->d_w, nullptr);
-      k_pythagoras_j<<<1, 1, 0, cap>>>(gmw, h->d_hcol);
-      k_multidot_j<<<nb, kRedThreads, 0, cap>>>(n2, gm, h->d_V, n2, h->d_w, h->d_part, stride, 0, guard);
-      k_reduce_parts_j<<<m + 1, 256, 0, cap>>>(nb, gm, 0, h->d_part, stride, h->d_hcol2, guard);
-      k_sub_combo_j<<<nb_comb, 256, 0, cap>>>(n2, gm, h->d_V, n2, h->d_hcol2, h->d_w, guard);
-      k_add_small_j<<<1, 128, 0, cap>>>(gm, h->d_hcol2, h->d_hcol, guard);
-      k_multidot_j<<<nb, kRedThreads, 0, cap>>>(n2, gm, h->d_V, n2, h->d_w, h->d_part, stride, 2, guard);
-      k_norm_to_j<<<1, 256, 0, cap>>>(nb, h->d_part, stride, gm, h->d_hcol, guard);
-    }
-    k_normalize_j<<<nb_el, 256, 0, cap>>>(n, h->d_w, h->d_hcol, gm, h->d_V, n2);
-    k_givens_j<<<1, 1, 0, cap>>>(gm, m, h->d_hcol, h->d_H, h->d_cs, h->d_sn, h->d_g, h->d_scal + 2);
-    k_step_end<<<1, 1, 0, cap>>>(gmw, m, h->d_scal + 2, h->d_scal + 4, loop);
+    k_step_end<<<1, 1, 0, cap>>>(h->d_gm_int, m, h->d_scal + 2, h->d_scal + 4, loop);
     e = check_launch("arnoldi step");
   }
   cudaGraph_t out = nullptr;
@@ -557,14 +579,10 @@ Err build_cycle_graph(afmpb_t *h, int m) {
   return Err{};
 }
 
-}  // namespace
-
-Err run_solve(afmpb_t *h, afmpb_solve_info *info) {
-  const int64_t n = h->n, n2 = 2 * n;
-  int m = 0;
-  AFMPB_TRY(restart_length(h, &m));
-  const int max_restart = h->opt.max_restart;
-  cudaStream_t s = h->stream;
+// The Krylov basis, Hessenberg matrix, work vectors and step state of an m-step cycle
+// (kept from an earlier solve of the same m).
+Err prepare_gmres(afmpb_t *h, int m) {
+  const int64_t n2 = 2 * h->n;
   auto &A = h->arena;
   if (h->gm_m != m || !h->d_V) {
     if (h->d_V) {
@@ -583,11 +601,23 @@ Err run_solve(afmpb_t *h, afmpb_solve_info *info) {
     AFMPB_TRY(A.alloc(&h->d_hcol, m + 2, "gmres hcol"));
     AFMPB_TRY(A.alloc(&h->d_hcol2, m + 2, "gmres hcol2"));
     AFMPB_TRY(A.alloc(&h->d_scal, 8, "gmres scalars"));
-    if (!h->d_gm_int) AFMPB_TRY(A.alloc(&h->d_gm_int, 4, "gmres step state"));
+    if (!h->d_gm_int) AFMPB_TRY(A.alloc(&h->d_gm_int, 8, "gmres step state"));
     if (!h->h_pinned) AFMPB_CUDA(cudaMallocHost(&h->h_pinned, 8 * sizeof(double)));
   }
-  if (!h->graph_cycle || h->cycle_m != m || h->cycle_orth != h->opt.orth) AFMPB_TRY(build_cycle_graph(h, m));
   if (!h->d_sol) AFMPB_TRY(A.alloc(&h->d_sol, n2, "solution"));
+  return Err{};
+}
+
+}  // namespace
+
+Err run_solve(afmpb_t *h, afmpb_solve_info *info) {
+  const int64_t n = h->n, n2 = 2 * n;
+  int m = 0;
+  AFMPB_TRY(restart_length(h, &m));
+  const int max_restart = h->opt.max_restart;
+  cudaStream_t s = h->stream;
+  AFMPB_TRY(prepare_gmres(h, m));
+  if (!h->graph_cycle || h->cycle_m != m || h->cycle_orth != h->opt.orth) AFMPB_TRY(build_cycle_graph(h, m));
   double *x = h->d_sol;
   volatile double *hp = h->h_pinned;
   const int nb_el = div_up(n, 256), nb_el2 = div_up(n2, 256);
@@ -611,7 +641,7 @@ Err run_solve(afmpb_t *h, afmpb_solve_info *info) {
   const double tol = h->tol * bnorm + h->opt.abs_tol;
   hp[4] = tol;
   AFMPB_CUDA(cudaMemcpyAsync(h->d_scal + 4, (const double *)hp + 4, sizeof(double), cudaMemcpyHostToDevice, s));
-  AFMPB_CUDA(cudaMemsetAsync(h->d_gm_int, 0, 4 * sizeof(int), s));
+  AFMPB_CUDA(cudaMemsetAsync(h->d_gm_int, 0, 8 * sizeof(int), s));
   AFMPB_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n2, s));
   int restarts = 0, products = 0;
   bool converged = false;
@@ -623,7 +653,7 @@ Err run_solve(afmpb_t *h, afmpb_solve_info *info) {
       ++restarts;
       ++products;
       AFMPB_TRY(product_from64(h, s, x));
-      k_from_ys<<<nb_el2, 256, 0, s>>>(n2, h->d_ys, h->d_b, h->d_w);
+      k_from_ys<<<nb_el2, 256, 0, s>>>(n2, h->d_ys, h->d_b, h->d_w, nullptr);
       AFMPB_TRY(check_launch("residual"));
     }
     AFMPB_TRY(norm2(h, n2, h->d_w, h->d_scal + 1));
@@ -654,7 +684,7 @@ Err run_solve(afmpb_t *h, afmpb_solve_info *info) {
   AFMPB_TRY(product_from64(h, s, x));
   AFMPB_CUDA(cudaEventRecord(e1, s));
   ++products;
-  k_from_ys<<<nb_el2, 256, 0, s>>>(n2, h->d_ys, h->d_b, h->d_w);
+  k_from_ys<<<nb_el2, 256, 0, s>>>(n2, h->d_ys, h->d_b, h->d_w, nullptr);
   AFMPB_TRY(norm2(h, n2, h->d_w, h->d_scal + 3));
   AFMPB_TRY(read_scalar(h->d_scal + 3, 3));
   float ms_one = 0.f;
@@ -685,6 +715,321 @@ Err run_solve(afmpb_t *h, afmpb_solve_info *info) {
   }
   if (!converged) return make_err(AFMPB_ENOCONV, "GMRES did not reach the tolerance within max_restart cycles");
   return Err{};
+}
+
+// ---- batched solve: several problems' GMRES in lockstep ----------------------------------
+// Each problem keeps its own Krylov state; one graph launch runs a restart cycle of all of
+// them.  Its WHILE body is one Arnoldi step of every running problem with one P2P launch
+// and one tensor-core M2L launch over all their work, the rest of each product and each
+// orthogonalisation on a branch of its own.  gm[4] says whether a problem runs in the
+// cycle: it is set at the cycle start, cleared when its Givens residual meets the
+// tolerance or its basis is full, and every kernel of a stopped problem returns at once;
+// the loop ends when no problem runs.
+
+__global__ void k_cycle_start_b(int *__restrict__ gm, int run) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    gm[0] = 0;
+    gm[2] = 0;
+    gm[4] = run;
+  }
+}
+
+// End of a running problem's step: j += 1; it stops (and its second-pass flag is cleared,
+// so that no guarded kernel of it runs) when the residual estimate meets the tolerance or
+// the basis has no room.
+__global__ void k_step_end_b(int *__restrict__ gm, int m, const double *__restrict__ res,
+                             const double *__restrict__ tol) {
+  if (threadIdx.x != 0 || blockIdx.x != 0 || gm[4] == 0) return;
+  const int j = gm[0] + 1;
+  gm[0] = j;
+  gm[1] += 1;
+  const double r = res[0];
+  if (!(j < m && r > tol[0])) {
+    gm[4] = 0;
+    gm[2] = 0;
+  }
+}
+
+__global__ void k_batch_go(int k, int *const *__restrict__ gms, cudaGraphConditionalHandle loop) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  unsigned any = 0;
+  for (int i = 0; i < k; ++i) any |= gms[i][4] != 0 ? 1u : 0u;
+  cudaGraphSetConditional(loop, any);
+}
+
+namespace {
+
+// Fused M2L needs every problem on the target-stationary kernel with one compressed rank.
+bool batch_fuses_m2l(afmpb_t *const *hs, int k) {
+  for (int i = 0; i < k; ++i)
+    if (!m2l_ts_applies(hs[i]) || hs[i]->m2l_rank != hs[0]->m2l_rank || hs[i]->m2l_groups.empty()) return false;
+  return true;
+}
+
+struct BatchGraph {
+  cudaGraphExec_t exec = nullptr;
+  std::vector<cudaStream_t> streams;
+  std::vector<cudaEvent_t> events;
+  ~BatchGraph() {
+    if (exec) cudaGraphExecDestroy(exec);
+    for (auto e : events) cudaEventDestroy(e);
+    for (auto s : streams) cudaStreamDestroy(s);
+  }
+  Err stream(cudaStream_t *s, int prio) {
+    AFMPB_CUDA(cudaStreamCreateWithPriority(s, cudaStreamNonBlocking, prio));
+    streams.push_back(*s);
+    return Err{};
+  }
+  Err event(cudaEvent_t *e) {
+    AFMPB_CUDA(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+    events.push_back(*e);
+    return Err{};
+  }
+};
+
+Err build_batch_graph(afmpb_t *const *hs, int k, const int *ms, bool fuse_m2l, const BatchLists &L, BatchGraph &G) {
+  cudaGraph_t g = nullptr;
+  AFMPB_CUDA(cudaGraphCreate(&g, 0));
+  struct GraphGuard { cudaGraph_t g; ~GraphGuard() { if (g) cudaGraphDestroy(g); } } gg{g};
+  cudaGraphConditionalHandle loop;
+  AFMPB_CUDA(cudaGraphConditionalHandleCreate(&loop, g, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = loop;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node = nullptr;
+  AFMPB_CUDA(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  int lo = 0, hi = 0;
+  AFMPB_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+  cudaStream_t cap = nullptr, sp = nullptr, sm = nullptr;
+  AFMPB_TRY(G.stream(&cap, hi));
+  AFMPB_TRY(G.stream(&sp, lo));            // P2P fills the SMs the far-field chains leave free
+  AFMPB_TRY(G.stream(&sm, hi));
+  std::vector<cudaStream_t> si(k);
+  std::vector<cudaEvent_t> ev_a(k), ev_b(k), ev_e(k);
+  cudaEvent_t ev_fork = nullptr, ev_p = nullptr, ev_m = nullptr;
+  AFMPB_TRY(G.event(&ev_fork));
+  AFMPB_TRY(G.event(&ev_p));
+  AFMPB_TRY(G.event(&ev_m));
+  for (int i = 0; i < k; ++i) {
+    AFMPB_TRY(G.stream(&si[i], hi));
+    AFMPB_TRY(G.event(&ev_a[i]));
+    AFMPB_TRY(G.event(&ev_b[i]));
+    AFMPB_TRY(G.event(&ev_e[i]));
+  }
+  AFMPB_CUDA(cudaStreamBeginCaptureToGraph(cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  Err e;
+  auto step = [&]() -> Err {
+    AFMPB_CUDA(cudaEventRecord(ev_fork, cap));
+    for (int i = 0; i < k; ++i) {
+      afmpb_t *h = hs[i];
+      const int *act = h->d_gm_int + 4;
+      AFMPB_CUDA(cudaStreamWaitEvent(si[i], ev_fork, 0));
+      AFMPB_TRY(enqueue_step_head(h, si[i], act));
+      AFMPB_CUDA(cudaMemsetAsync(h->d_phi_near, 0, sizeof(float4) * h->n, si[i]));
+      AFMPB_CUDA(cudaEventRecord(ev_a[i], si[i]));
+      AFMPB_TRY(enqueue_far(h, si[i], nullptr, fuse_m2l ? kFarUp : kFarUp | kFarM2L));
+      AFMPB_CUDA(cudaEventRecord(ev_b[i], si[i]));
+    }
+    for (int i = 0; i < k; ++i) AFMPB_CUDA(cudaStreamWaitEvent(sp, ev_a[i], 0));
+    AFMPB_TRY(enqueue_p2p_batch(L.d_p2p, L.d_units, L.nunits, kP2PResident, sp));
+    AFMPB_CUDA(cudaEventRecord(ev_p, sp));
+    if (fuse_m2l) {
+      for (int i = 0; i < k; ++i) AFMPB_CUDA(cudaStreamWaitEvent(sm, ev_b[i], 0));
+      AFMPB_TRY(enqueue_m2l_ts_batch(L.d_ts, L.d_items, L.nitems, L.d_items_run, L.d_count, hs[0]->m2l_rank,
+                                     hs[0]->d_tc_flag, sm));
+      AFMPB_CUDA(cudaEventRecord(ev_m, sm));
+    }
+    for (int i = 0; i < k; ++i) {
+      afmpb_t *h = hs[i];
+      const int *act = h->d_gm_int + 4;
+      if (fuse_m2l) AFMPB_CUDA(cudaStreamWaitEvent(si[i], ev_m, 0));
+      AFMPB_TRY(enqueue_far(h, si[i], nullptr, kFarDown));
+      AFMPB_CUDA(cudaStreamWaitEvent(si[i], ev_p, 0));
+      AFMPB_TRY(enqueue_combine(h, si[i], AFMPB_PART_ALL));
+      AFMPB_TRY(enqueue_step_tail(h, ms[i], si[i], act));
+      k_step_end_b<<<1, 1, 0, si[i]>>>(h->d_gm_int, ms[i], h->d_scal + 2, h->d_scal + 4);
+      AFMPB_TRY(check_launch("k_step_end_b"));
+      AFMPB_CUDA(cudaEventRecord(ev_e[i], si[i]));
+      AFMPB_CUDA(cudaStreamWaitEvent(cap, ev_e[i], 0));
+    }
+    k_batch_go<<<1, 1, 0, cap>>>(k, L.d_gms, loop);
+    return check_launch("k_batch_go");
+  };
+  e = step();
+  cudaGraph_t out = nullptr;
+  cudaError_t ce = cudaStreamEndCapture(cap, &out);
+  if (!e.ok()) return e;
+  if (ce != cudaSuccess) return make_err(AFMPB_ECUDA, std::string("cudaStreamEndCapture (batch): ") + cudaGetErrorString(ce));
+  ce = cudaGraphInstantiate(&G.exec, g, 0);
+  if (ce != cudaSuccess) return make_err(AFMPB_ECUDA, std::string("cudaGraphInstantiate (batch): ") + cudaGetErrorString(ce));
+  return Err{};
+}
+
+}  // namespace
+
+Err run_solve_batch(afmpb_t *const *hs, int k, afmpb_solve_info *infos, afmpb_status *statuses) {
+  std::vector<int> ms(k);
+  for (int i = 0; i < k; ++i) {
+    AFMPB_TRY(restart_length(hs[i], &ms[i]));
+    AFMPB_TRY(prepare_gmres(hs[i], ms[i]));
+    AFMPB_CUDA(cudaStreamSynchronize(hs[i]->stream));
+  }
+  const bool fuse_m2l = batch_fuses_m2l(hs, k);
+  BatchGraph G;
+  cudaStream_t bs = nullptr;
+  {
+    int lo = 0, hi = 0;
+    AFMPB_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+    AFMPB_TRY(G.stream(&bs, hi));
+  }
+  BatchLists L;
+  L.stream = bs;
+  AFMPB_TRY(build_batch_lists(hs, k, fuse_m2l, L));
+  AFMPB_TRY(build_batch_graph(hs, k, ms.data(), fuse_m2l, L, G));
+
+  struct State {
+    double bnorm = 0, tol = 0, res = 0;
+    int restarts = 0, products = 0, cycles = 0;
+    bool running = true, converged = false;
+    int gm[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  };
+  std::vector<State> st(k);
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  AFMPB_CUDA(cudaEventCreate(&t0));
+  AFMPB_CUDA(cudaEventCreate(&t1));
+  struct EvGuard { cudaEvent_t a, b; ~EvGuard() { cudaEventDestroy(a); cudaEventDestroy(b); } } evg{t0, t1};
+  AFMPB_CUDA(cudaEventRecord(t0, bs));
+  AFMPB_CUDA(cudaStreamSynchronize(bs));
+  auto read_scalar = [&](afmpb_t *h, const double *d, int slot) -> Err {
+    AFMPB_CUDA(cudaMemcpyAsync((double *)h->h_pinned + slot, d, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    AFMPB_CUDA(cudaStreamSynchronize(h->stream));
+    return Err{};
+  };
+  for (int i = 0; i < k; ++i) {
+    afmpb_t *h = hs[i];
+    const int64_t n2 = 2 * h->n;
+    AFMPB_TRY(norm2(h, n2, h->d_b, h->d_scal + 0));
+    AFMPB_TRY(read_scalar(h, h->d_scal + 0, 0));
+    st[i].bnorm = h->h_pinned[0];
+    h->bnorm = st[i].bnorm;
+    st[i].tol = h->tol * st[i].bnorm + h->opt.abs_tol;
+    st[i].res = st[i].bnorm;
+    h->h_pinned[4] = st[i].tol;
+    AFMPB_CUDA(cudaMemcpyAsync(h->d_scal + 4, (const double *)h->h_pinned + 4, sizeof(double), cudaMemcpyHostToDevice,
+                               h->stream));
+    AFMPB_CUDA(cudaMemsetAsync(h->d_gm_int, 0, 8 * sizeof(int), h->stream));
+    AFMPB_CUDA(cudaMemsetAsync(h->d_sol, 0, sizeof(double) * n2, h->stream));
+  }
+  for (;;) {
+    // each running problem: residual of its current x, and the start of its next cycle
+    int nrun = 0;
+    for (int i = 0; i < k; ++i) {
+      afmpb_t *h = hs[i];
+      State &S = st[i];
+      const int64_t n = h->n, n2 = 2 * n;
+      if (S.running && S.cycles > h->opt.max_restart) S.running = false;
+      if (S.running) {
+        if (S.cycles == 0) {
+          AFMPB_CUDA(cudaMemcpyAsync(h->d_w, h->d_b, sizeof(double) * n2, cudaMemcpyDeviceToDevice, h->stream));
+        } else {
+          ++S.restarts;
+          ++S.products;
+          AFMPB_TRY(product_from64(h, h->stream, h->d_sol));
+          k_from_ys<<<div_up(n2, 256), 256, 0, h->stream>>>(n2, h->d_ys, h->d_b, h->d_w, nullptr);
+          AFMPB_TRY(check_launch("residual"));
+        }
+        AFMPB_TRY(norm2(h, n2, h->d_w, h->d_scal + 1));
+        AFMPB_TRY(read_scalar(h, h->d_scal + 1, 1));
+        S.res = h->h_pinned[1];
+        if (!(S.res > S.tol)) {
+          S.converged = !std::isnan(S.res);
+          S.running = false;
+        }
+      }
+      if (S.running) {
+        k_normalize<<<div_up(n, 256), 256, 0, h->stream>>>(n, h->d_w, h->d_scal + 1, h->d_V, nullptr);
+        k_set_beta<<<1, 1, 0, h->stream>>>(h->d_g, ms[i], h->d_scal + 1);
+        ++nrun;
+      }
+      k_cycle_start_b<<<1, 1, 0, h->stream>>>(h->d_gm_int, S.running ? 1 : 0);
+      AFMPB_TRY(check_launch("batch cycle start"));
+      AFMPB_CUDA(cudaStreamSynchronize(h->stream));
+    }
+    if (nrun == 0) break;
+    // the Arnoldi steps of every running problem: one graph launch
+    AFMPB_CUDA(cudaGraphLaunch(G.exec, bs));
+    AFMPB_CUDA(cudaStreamSynchronize(bs));
+    for (int i = 0; i < k; ++i) {
+      afmpb_t *h = hs[i];
+      State &S = st[i];
+      if (!S.running) continue;
+      const int64_t n2 = 2 * h->n;
+      k_backsolve_j<<<1, 1, 0, h->stream>>>(h->d_gm_int, ms[i], h->d_H, h->d_g);
+      k_update_x<<<std::min(div_up(n2, 256), 4 * 1184), 256, 0, h->stream>>>(n2, h->d_gm_int, h->d_V, n2, h->d_g,
+                                                                              h->d_sol);
+      AFMPB_TRY(check_launch("batch gmres update"));
+      AFMPB_CUDA(cudaMemcpyAsync(S.gm, h->d_gm_int, sizeof(S.gm), cudaMemcpyDeviceToHost, h->stream));
+      AFMPB_TRY(read_scalar(h, h->d_scal + 2, 2));
+      S.res = h->h_pinned[2];
+      S.products += S.gm[0];
+      ++S.cycles;
+      if (!(S.res > S.tol)) {
+        S.converged = !std::isnan(S.res);
+        S.running = false;
+      }
+    }
+  }
+  AFMPB_CUDA(cudaEventRecord(t1, bs));
+  AFMPB_CUDA(cudaEventSynchronize(t1));
+  float ms_all = 0.f;
+  AFMPB_CUDA(cudaEventElapsedTime(&ms_all, t0, t1));
+  Err first_fail;
+  for (int i = 0; i < k; ++i) {
+    afmpb_t *h = hs[i];
+    State &S = st[i];
+    const int64_t n2 = 2 * h->n;
+    // true residual with one more product (its CUDA-event time stands for every product)
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    AFMPB_CUDA(cudaEventCreate(&e0));
+    AFMPB_CUDA(cudaEventCreate(&e1));
+    EvGuard g2{e0, e1};
+    AFMPB_CUDA(cudaEventRecord(e0, h->stream));
+    AFMPB_TRY(product_from64(h, h->stream, h->d_sol));
+    AFMPB_CUDA(cudaEventRecord(e1, h->stream));
+    ++S.products;
+    k_from_ys<<<div_up(n2, 256), 256, 0, h->stream>>>(n2, h->d_ys, h->d_b, h->d_w, nullptr);
+    AFMPB_TRY(norm2(h, n2, h->d_w, h->d_scal + 3));
+    AFMPB_TRY(read_scalar(h, h->d_scal + 3, 3));
+    float ms_one = 0.f;
+    AFMPB_CUDA(cudaEventElapsedTime(&ms_one, e0, e1));
+    h->solved = true;
+    int flag = 0;
+    AFMPB_TRY(read_tc_error(h, &flag));
+    if (infos) {
+      afmpb_solve_info &I = infos[i];
+      I.iters = S.gm[1];
+      I.restarts = S.restarts;
+      I.res_est = S.res;
+      I.res_true = S.bnorm > 0 ? h->h_pinned[3] / S.bnorm : h->h_pinned[3];
+      I.bnorm = S.bnorm;
+      I.ms_setup = h->ms_setup;
+      I.ms_matvec_total = ms_one * S.products;
+      I.ms_gmres = ms_all;
+      I.nnz_near = h->nnz;
+      I.n_boxes = h->shape.nbox;
+      I.krylov_dim = ms[i];
+      I.second_passes = h->opt.orth == 0 ? S.gm[1] : S.gm[3];
+    }
+    if (statuses) statuses[i] = flag ? AFMPB_ETIMEOUT : S.converged ? AFMPB_OK : AFMPB_ENOCONV;
+    if (first_fail.ok() && flag)
+      first_fail = make_err(AFMPB_ETIMEOUT, "a bounded device wait expired during the batched solve; its products are not valid");
+    if (first_fail.ok() && !S.converged)
+      first_fail = make_err(AFMPB_ENOCONV, "GMRES did not reach the tolerance within max_restart cycles for a problem of the batch");
+  }
+  return first_fail;
 }
 
 Err run_energy(afmpb_t *h, double *E) {

@@ -57,6 +57,12 @@ def test_null_arguments_are_rejected_without_a_device():
     assert lib.afmpb_matvec(None, None, None) == 1
     assert lib.afmpb_sync(None) == 1
     assert lib.afmpb_inject_wait_expiry(None) == 1
+    # batched solve: no handles, too many, or a NULL handle -> EINVAL on the host
+    assert lib.afmpb_solve_batch(None, 1, None, None, None, None) == 1
+    hs = (ctypes.c_void_p * 2)(None, None)
+    assert lib.afmpb_solve_batch(hs, 0, None, None, None, None) == 1
+    assert lib.afmpb_solve_batch(hs, 65, None, None, None, None) == 1
+    assert lib.afmpb_solve_batch(hs, 2, None, None, None, None) == 1
     assert lib.afmpb_destroy(None) == 0
 
 
