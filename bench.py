@@ -72,8 +72,11 @@ def serving_leg(args):
     """The serving configuration: args.serve_requests solve requests (default 512), each a
     synthetic globule drawn from a seeded pool of args.serve_pool molecules whose atom
     counts are log-uniform in [500, 50,000] (surfaces on a 1.2 A lattice: ~10k-350k nodes),
-    with kappa ~ U(0.03, 0.3) drawn per request.  Four arms -- plain FP32 and mixed
-    precision, each on 1 and on args.serve_slots server slots -- run the same requests:
+    with kappa ~ U(0.03, 0.3) drawn per request.  Five arms -- plain FP32 and mixed
+    precision, each on 1 and on args.serve_slots server slots, and mixed precision on
+    args.serve_slots set-up slots and args.serve_solvers solver threads with batched solves
+    (up to args.serve_batch requests of similar size in one lockstep GMRES with fused P2P
+    and M2L launches) -- run the same requests:
       * capacity: the first args.serve_burst requests submitted at once (solves/s);
       * latency: all requests on one fixed Poisson arrival trace at 0.9x the capacity of
         plain FP32 on args.serve_slots slots, p50/p99 from submission to result (queueing
@@ -93,8 +96,9 @@ def serving_leg(args):
     reqs = [(int(rng.integers(len(pool))), float(rng.uniform(0.03, 0.3))) for _ in range(args.serve_requests)]
     gaps = rng.exponential(1.0, len(reqs))            # unit-rate gaps, scaled by the rate below
 
-    def run(precision, slots, items, rate=None):
-        with pb.Server(bytes_budget=int(args.serve_budget_gb * (1 << 30)), max_slots=slots) as srv:
+    def run(precision, slots, items, rate=None, batch=1):
+        with pb.Server(bytes_budget=int(args.serve_budget_gb * (1 << 30)), max_slots=slots, max_batch=batch,
+                       solvers=args.serve_solvers) as srv:
             start = time.perf_counter()
             due = start + np.cumsum(gaps[:len(items)]) / rate if rate else None
             tickets = []
@@ -120,23 +124,27 @@ def serving_leg(args):
                 "iters_max": max(r["info"]["iters"] for r in res), "max_running": info["max_running"],
                 "reserved_high_water_gb": round(info["bytes_high_water"] / 2**30, 2),
                 "used_high_water_gb": round(max(r["bytes_used"] for r in res) / 2**30, 2),
-                "slots": slots}, [r["energy"] for r in res]
+                "slots": slots, "max_batch": batch, "largest_batch": info["max_batch"],
+                "mean_batch": round(info["batched_requests"] / info["batches"], 2) if info["batches"] else None,
+                }, [r["energy"] for r in res]
 
     def ediff(e, e_ref):
         return max((abs(a / b - 1) for a, b in zip(e, e_ref) if a and b), default=None)
 
-    arms = [("plain_fp32_1slot", 0, 1), ("plain_fp32_%dslots" % args.serve_slots, 0, args.serve_slots),
-            ("mixed_1slot", 1, 1), ("mixed_%dslots" % args.serve_slots, 1, args.serve_slots)]
+    fused = "mixed_fused_%dslots" % args.serve_slots
+    arms = [("plain_fp32_1slot", 0, 1, 1), ("plain_fp32_%dslots" % args.serve_slots, 0, args.serve_slots, 1),
+            ("mixed_1slot", 1, 1, 1), ("mixed_%dslots" % args.serve_slots, 1, args.serve_slots, 1),
+            (fused, 1, args.serve_slots, args.serve_batch)]
     burst_items = reqs[:args.serve_burst]
     cap, cap_e = {}, {}
-    for name, prec, slots in arms:
-        cap[name], cap_e[name] = run(prec, slots, burst_items)
+    for name, prec, slots, batch in arms:
+        cap[name], cap_e[name] = run(prec, slots, burst_items, batch=batch)
     rate = 0.9 * cap["plain_fp32_%dslots" % args.serve_slots]["solves_per_s"]
     lat, lat_e = {}, {}
-    for name, prec, slots in arms:
-        lat[name], lat_e[name] = run(prec, slots, reqs, rate=rate)
+    for name, prec, slots, batch in arms:
+        lat[name], lat_e[name] = run(prec, slots, reqs, rate=rate, batch=batch)
     out = {}
-    for name, prec, slots in arms:
+    for name, prec, slots, batch in arms:
         ref = "plain_fp32_1slot" if slots == 1 else "plain_fp32_%dslots" % args.serve_slots
         out[name] = {"capacity": cap[name], "poisson": lat[name],
                      "energy_max_rel_diff_vs_plain": ediff(lat_e[name], lat_e[ref]),
@@ -154,7 +162,12 @@ def serving_leg(args):
             "mixed_vs_plain_same_slots": {
                 "capacity_ratio": round(cap[mix]["solves_per_s"] / cap[pla]["solves_per_s"], 3),
                 "p50_ratio": round(lat[mix]["p50_ms"] / lat[pla]["p50_ms"], 3),
-                "p99_ratio": round(lat[mix]["p99_ms"] / lat[pla]["p99_ms"], 3)}}
+                "p99_ratio": round(lat[mix]["p99_ms"] / lat[pla]["p99_ms"], 3)},
+            "fused_vs_unfused_mixed_same_slots": {
+                "capacity_ratio": round(cap[fused]["solves_per_s"] / cap[mix]["solves_per_s"], 3),
+                "poisson_solves_per_s_ratio": round(lat[fused]["solves_per_s"] / lat[mix]["solves_per_s"], 3),
+                "p50_ratio": round(lat[fused]["p50_ms"] / lat[mix]["p50_ms"], 3),
+                "p99_ratio": round(lat[fused]["p99_ms"] / lat[mix]["p99_ms"], 3)}}
 
 
 # ------------------------------------------------------------------------------------
@@ -731,6 +744,8 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=512)
     ap.add_argument("--serve-burst", type=int, default=128)
     ap.add_argument("--serve-slots", type=int, default=4)
+    ap.add_argument("--serve-batch", type=int, default=8)
+    ap.add_argument("--serve-solvers", type=int, default=2)
     ap.add_argument("--serve-budget-gb", type=float, default=96.0)
     ap.add_argument("--serve-restart", type=int, default=80)
     ap.add_argument("--no-capsid", action="store_true")

@@ -441,11 +441,25 @@ typedef struct {
     int64_t bytes_in_use, bytes_high_water, bytes_budget;   /* reservations              */
     int64_t max_running;         /* most requests running at once so far                  */
     int slots;
+    int max_batch;               /* batched servers: the largest batch solved so far      */
+    int64_t batches;             /* batched servers: batched solves run                   */
+    int64_t batched_requests;    /* batched servers: requests solved in them              */
 } afmpb_server_info;
 
 /* bytes_budget > 0; max_slots in [1, 256].  The server runs every request on the device
  * that is current in the calling thread. */
 afmpb_status afmpb_server_create(size_t bytes_budget, int max_slots, afmpb_server_t **out);
+
+/* As afmpb_server_create, with batched solves (max_batch in [1, AFMPB_BATCH_MAX]; 1 is
+ * afmpb_server_create; solvers in [1, 256], used when max_batch > 1).  The max_slots
+ * slots only set requests up (each handle on a stream of its own); each of the solver
+ * threads takes the oldest set-up request together with the other set-up requests of
+ * similar size (node counts within a factor of two), up to max_batch, and solves them
+ * with afmpb_solve_batch: their GMRES steps share fused P2P and M2L launches.  Requests
+ * set up while solves run form the next batches.  Admission, reservations and results
+ * are as for afmpb_server_create; a result's slot is the slot that set it up. */
+afmpb_status afmpb_server_create_batched(size_t bytes_budget, int max_slots, int solvers, int max_batch,
+                                         afmpb_server_t **out);
 /* EINVAL for missing arrays or sizes; ENOMEM when the reservation exceeds the whole budget
  * (the request could never run); otherwise queues it and returns its ticket. */
 afmpb_status afmpb_server_submit(afmpb_server_t *s, const afmpb_request *req, int64_t *ticket);

@@ -104,7 +104,8 @@ class ServerInfo(C.Structure):
     _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("failed", C.c_int64),
                 ("running", C.c_int64), ("queued", C.c_int64), ("bytes_in_use", C.c_int64),
                 ("bytes_high_water", C.c_int64), ("bytes_budget", C.c_int64),
-                ("max_running", C.c_int64), ("slots", C.c_int)]
+                ("max_running", C.c_int64), ("slots", C.c_int), ("max_batch", C.c_int),
+                ("batches", C.c_int64), ("batched_requests", C.c_int64)]
 
 
 class PlanInput(C.Structure):
@@ -136,7 +137,8 @@ EXPORTS = ["afmpb_create", "afmpb_matvec", "afmpb_matvec_parts", "afmpb_matvec_h
            "afmpb_server_get_info", "afmpb_server_destroy", "afmpb_get_autotune",
            "afmpb_selftest_bounded_wait", "afmpb_sync", "afmpb_inject_wait_expiry",
            "afmpb_plan_create", "afmpb_plan_get_rank", "afmpb_plan_get_halo", "afmpb_plan_get_send",
-           "afmpb_plan_get_boxes", "afmpb_plan_destroy", "afmpb_solve_batch"]
+           "afmpb_plan_get_boxes", "afmpb_plan_destroy", "afmpb_solve_batch",
+           "afmpb_server_create_batched"]
 
 
 def library_path() -> str:
@@ -191,6 +193,8 @@ def load(build: bool = True):
     lib.afmpb_selftest_bounded_wait.argtypes = [C.c_int, C.POINTER(C.c_int)]
     lib.afmpb_server_create.restype = I32
     lib.afmpb_server_create.argtypes = [C.c_size_t, C.c_int, C.POINTER(P)]
+    lib.afmpb_server_create_batched.restype = I32
+    lib.afmpb_server_create_batched.argtypes = [C.c_size_t, C.c_int, C.c_int, C.c_int, C.POINTER(P)]
     lib.afmpb_server_submit.restype = I32
     lib.afmpb_server_submit.argtypes = [P, C.POINTER(Request), C.POINTER(I64)]
     lib.afmpb_server_poll.restype = I32
@@ -517,10 +521,11 @@ class Server:
     """Continuous-batching solve server (afmpb_server_*): submit whole solves, poll or wait
     for their results; requests overlap on the GPU as slots and device memory allow."""
 
-    def __init__(self, bytes_budget, max_slots=4):
+    def __init__(self, bytes_budget, max_slots=4, max_batch=1, solvers=1):
         self._lib = load()
         h = C.c_void_p()
-        rc = self._lib.afmpb_server_create(int(bytes_budget), int(max_slots), C.byref(h))
+        rc = self._lib.afmpb_server_create_batched(int(bytes_budget), int(max_slots), int(solvers), int(max_batch),
+                                                   C.byref(h))
         if rc != 0:
             raise AfmpbError(rc, "afmpb_server_create failed")
         self.s = h.value

@@ -10,6 +10,15 @@
 // returned, which may admit the next request at once.  Requests on different slots
 // overlap on the device (their kernels run on separate streams) and on the host (setup
 // work runs on the slot threads).  Results are kept until a poll or wait hands them out.
+//
+// With batching (afmpb_server_create_batched, max_batch > 1) a slot only sets the request
+// up; the finished handle (on a stream of its own) joins a ready list, and each of the
+// solver threads takes the oldest ready request with the other ready requests of similar
+// size (node counts within a factor of two), up to max_batch, into one
+// afmpb_solve_batch: their GMRES steps run in lockstep with fused P2P and M2L launches.
+// Under light load a batch holds one request; requests that pile up while solves run are
+// solved together.  Grouping by size keeps a small request from waiting on a large one's
+// steps.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -46,6 +55,13 @@ struct Done {
   bool ready = false;
 };
 
+// A request whose handle is set up and waits for the batch solver.
+struct Ready {
+  std::unique_ptr<Job> job;
+  afmpb_t *h = nullptr;
+  afmpb_result r{};
+};
+
 }  // namespace
 
 struct afmpb_server_t {
@@ -58,6 +74,12 @@ struct afmpb_server_t {
   std::deque<std::unique_ptr<Job>> queue;
   std::unordered_map<int64_t, Done> results;
   std::vector<std::thread> slots;
+  int max_batch = 1;              // > 1: slots set up, one solver thread solves in batches
+  std::deque<Ready> ready;
+  std::condition_variable cv_ready;
+  std::vector<std::thread> solvers;
+  int setting_up = 0;             // batched: admitted requests still in setup on a slot
+  int64_t batches = 0, batched = 0, max_batch_seen = 0;
   bool stop = false;
   int64_t next_ticket = 1;
   size_t in_use = 0, high_water = 0;
@@ -81,7 +103,8 @@ std::unique_ptr<Job> take_admissible(afmpb_server_t *s) {
   return nullptr;
 }
 
-void run_job(afmpb_server_t *s, Job &j, cudaStream_t stream, afmpb_result &r) {
+// Handle setup of a request (nullptr with r.status set on failure).
+afmpb_t *setup_job(afmpb_server_t *s, Job &j, cudaStream_t stream, afmpb_result &r) {
   afmpb_mesh mesh{j.n_nodes, j.n_tris, j.xyz.data(), j.tri.data(), j.normals.empty() ? nullptr : j.normals.data()};
   afmpb_charges ch{j.n_atoms, j.atoms.data(), j.q.data()};
   afmpb_options opt = j.opt;
@@ -90,7 +113,7 @@ void run_job(afmpb_server_t *s, Job &j, cudaStream_t stream, afmpb_result &r) {
   r.status = afmpb_create(&mesh, j.n_atoms > 0 ? &ch : nullptr, j.eps_in, j.eps_out, j.kappa, j.order, j.tol, &opt, &h);
   if (r.status != AFMPB_OK) {
     std::strncpy(r.error, afmpb_last_error(nullptr), sizeof(r.error) - 1);
-    return;
+    return nullptr;
   }
   // Setup is done: shrink the reservation to what the handle holds at its peak, or now
   // plus the GMRES basis and work vectors still to come, whichever is larger.
@@ -108,12 +131,102 @@ void run_job(afmpb_server_t *s, Job &j, cudaStream_t stream, afmpb_result &r) {
     }
     s->cv_work.notify_all();
   }
-  r.status = afmpb_solve(h, j.f_out, j.h_out, &r.info);
+  return h;
+}
+
+// Energy (after a solve that reached the tolerance), memory high-water mark, handle freed.
+void finish_job(afmpb_t *h, afmpb_result &r) {
   if (r.status == AFMPB_OK) r.status = afmpb_energy(h, &r.energy_kcal_mol);
-  if (r.status != AFMPB_OK) std::strncpy(r.error, afmpb_last_error(h), sizeof(r.error) - 1);
+  if (r.status != AFMPB_OK && !r.error[0]) std::strncpy(r.error, afmpb_last_error(h), sizeof(r.error) - 1);
   afmpb_info inf{};
   if (afmpb_get_info(h, &inf) == AFMPB_OK) r.bytes_used = inf.device_bytes_peak;
   afmpb_destroy(h);
+}
+
+void run_job(afmpb_server_t *s, Job &j, cudaStream_t stream, afmpb_result &r) {
+  afmpb_t *h = setup_job(s, j, stream, r);
+  if (!h) return;
+  r.status = afmpb_solve(h, j.f_out, j.h_out, &r.info);
+  if (r.status != AFMPB_OK) std::strncpy(r.error, afmpb_last_error(h), sizeof(r.error) - 1);
+  finish_job(h, r);
+}
+
+// Hand a finished request's result out and return its reservation.
+void complete(afmpb_server_t *s, Job &j, afmpb_result &r) {
+  r.t_done = s->now();
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->in_use -= j.reserve;
+    --s->running;
+    ++s->completed;
+    if (r.status != AFMPB_OK) ++s->failed;
+    Done &d = s->results[j.ticket];
+    d.res = r;
+    d.ready = true;
+  }
+  s->cv_done.notify_all();
+  s->cv_work.notify_all();                              // freed memory may admit others
+}
+
+// Batched mode: take every ready request (up to max_batch) and solve them together.
+void solver_main(afmpb_server_t *s) {
+  const bool have_device = cudaSetDevice(s->device) == cudaSuccess;
+  for (;;) {
+    std::vector<Ready> batch;
+    {
+      std::unique_lock<std::mutex> lk(s->mu);
+      s->cv_ready.wait(lk, [&] { return !s->ready.empty() || (s->stop && s->setting_up == 0); });
+      if (s->ready.empty()) break;                      // stopping and nothing left to solve
+      // the oldest ready request, and ready ones within a factor of two of its size
+      const int64_t n0 = s->ready.front().job->n_nodes;
+      for (auto it = s->ready.begin(); it != s->ready.end() && (int)batch.size() < s->max_batch;) {
+        const int64_t n = it->job->n_nodes;
+        if (batch.empty() || (n <= 2 * n0 && 2 * n >= n0)) {
+          batch.push_back(std::move(*it));
+          it = s->ready.erase(it);
+        } else {
+          ++it;
+        }
+      }
+      ++s->batches;
+      s->batched += (int64_t)batch.size();
+      s->max_batch_seen = std::max<int64_t>(s->max_batch_seen, (int64_t)batch.size());
+    }
+    const int k = (int)batch.size();
+    std::vector<afmpb_t *> hs(k);
+    std::vector<double *> fo(k), ho(k);
+    std::vector<afmpb_solve_info> infos(k);
+    std::vector<afmpb_status> st(k, AFMPB_ECUDA);
+    for (int i = 0; i < k; ++i) {
+      hs[i] = batch[i].h;
+      fo[i] = batch[i].job->f_out;
+      ho[i] = batch[i].job->h_out;
+    }
+    afmpb_status rc = AFMPB_ECUDA;
+    std::string err;
+    if (have_device) {
+      try {
+        rc = afmpb_solve_batch(hs.data(), k, fo.data(), ho.data(), infos.data(), st.data());
+        if (rc != AFMPB_OK) err = afmpb_last_error(hs[0]);
+      } catch (...) {
+        rc = afmpb::current_exception_err().code;
+      }
+    } else {
+      err = "solver thread device selection failed";
+    }
+    for (int i = 0; i < k; ++i) {
+      afmpb_result &r = batch[i].r;
+      r.info = infos[i];
+      r.status = (rc == AFMPB_OK || rc == AFMPB_ENOCONV || rc == AFMPB_ETIMEOUT) ? st[i] : rc;
+      if (r.status != AFMPB_OK) std::strncpy(r.error, err.empty() ? "batched solve failed" : err.c_str(), sizeof(r.error) - 1);
+      try {
+        finish_job(batch[i].h, r);
+      } catch (...) {
+        r.status = afmpb::current_exception_err().code;
+      }
+      complete(s, *batch[i].job, r);
+    }
+  }
 }
 
 void slot_main(afmpb_server_t *s, int slot) {
@@ -131,13 +244,42 @@ void slot_main(afmpb_server_t *s, int slot) {
       s->high_water = std::max(s->high_water, s->in_use);
       ++s->running;
       s->max_running = std::max(s->max_running, s->running);
+      if (s->max_batch > 1) ++s->setting_up;
     }
     afmpb_result r{};
     r.t_submit = j->t_submit;
     r.t_admit = s->now();
     r.slot = slot;
     r.bytes_reserved = (int64_t)j->reserve;
-    if (have_stream) {
+    if (have_stream && s->max_batch > 1) {
+      // batched: set the request up on a stream of its own, then hand it to the solver
+      afmpb_t *h = nullptr;
+      try {
+        h = setup_job(s, *j, nullptr, r);
+      } catch (...) {
+        const afmpb::Err e = afmpb::current_exception_err();
+        r.status = e.code;
+        std::strncpy(r.error, e.msg.c_str(), sizeof(r.error) - 1);
+      }
+      if (h) {
+        {
+          std::lock_guard<std::mutex> lk(s->mu);
+          Ready rd;
+          rd.job = std::move(j);
+          rd.h = h;
+          rd.r = r;
+          s->ready.push_back(std::move(rd));
+          --s->setting_up;
+        }
+        s->cv_ready.notify_all();
+        continue;
+      }
+      {
+        std::lock_guard<std::mutex> lk(s->mu);
+        --s->setting_up;
+      }
+      s->cv_ready.notify_all();
+    } else if (have_stream) {
       try {
         run_job(s, *j, stream, r);
       } catch (...) {                                   // no exception may end a slot thread
@@ -148,20 +290,12 @@ void slot_main(afmpb_server_t *s, int slot) {
     } else {
       r.status = AFMPB_ECUDA;
       std::strncpy(r.error, "slot device selection or stream creation failed", sizeof(r.error) - 1);
+      if (s->max_batch > 1) {
+        std::lock_guard<std::mutex> lk(s->mu);
+        --s->setting_up;
+      }
     }
-    r.t_done = s->now();
-    {
-      std::lock_guard<std::mutex> lk(s->mu);
-      s->in_use -= j->reserve;
-      --s->running;
-      ++s->completed;
-      if (r.status != AFMPB_OK) ++s->failed;
-      Done &d = s->results[j->ticket];
-      d.res = r;
-      d.ready = true;
-    }
-    s->cv_done.notify_all();
-    s->cv_work.notify_all();                            // freed memory may admit others
+    complete(s, *j, r);
   }
   if (stream) cudaStreamDestroy(stream);
 }
@@ -179,18 +313,28 @@ bool copy_array(std::vector<double> &dst, const double *src, int64_t n) {
 extern "C" {
 
 afmpb_status afmpb_server_create(size_t bytes_budget, int max_slots, afmpb_server_t **out) {
-  if (!out || bytes_budget == 0 || max_slots < 1 || max_slots > 256) return AFMPB_EINVAL;
+  return afmpb_server_create_batched(bytes_budget, max_slots, 1, 1, out);
+}
+
+afmpb_status afmpb_server_create_batched(size_t bytes_budget, int max_slots, int solvers, int max_batch,
+                                         afmpb_server_t **out) {
+  if (!out || bytes_budget == 0 || max_slots < 1 || max_slots > 256 || max_batch < 1 || max_batch > AFMPB_BATCH_MAX ||
+      solvers < 1 || solvers > 256)
+    return AFMPB_EINVAL;
   *out = nullptr;
   afmpb_server_t *s = new (std::nothrow) afmpb_server_t();
   if (!s) return AFMPB_ENOMEM;
   s->budget = bytes_budget;
   s->max_slots = max_slots;
+  s->max_batch = max_batch;
   s->t0 = Clock::now();
   if (cudaGetDevice(&s->device) != cudaSuccess) {   // no device: every request fails at its slot
     cudaGetLastError();
     s->device = 0;
   }
   try {
+    if (max_batch > 1)
+      for (int i = 0; i < solvers; ++i) s->solvers.emplace_back(solver_main, s);
     for (int i = 0; i < max_slots; ++i) s->slots.emplace_back(slot_main, s, i);
   } catch (...) {
     {
@@ -198,7 +342,9 @@ afmpb_status afmpb_server_create(size_t bytes_budget, int max_slots, afmpb_serve
       s->stop = true;
     }
     s->cv_work.notify_all();
+    s->cv_ready.notify_all();
     for (auto &t : s->slots) t.join();
+    for (auto &t : s->solvers) t.join();
     delete s;
     return AFMPB_ENOMEM;
   }
@@ -317,6 +463,9 @@ afmpb_status afmpb_server_get_info(afmpb_server_t *s, afmpb_server_info *st) {
   st->bytes_budget = (int64_t)s->budget;
   st->max_running = s->max_running;
   st->slots = s->max_slots;
+  st->batches = s->batches;
+  st->batched_requests = s->batched;
+  st->max_batch = (int)s->max_batch_seen;
   return AFMPB_OK;
 }
 
@@ -329,6 +478,8 @@ afmpb_status afmpb_server_destroy(afmpb_server_t *s) {
   }
   s->cv_work.notify_all();
   for (auto &t : s->slots) t.join();                    // running requests finish first
+  s->cv_ready.notify_all();
+  for (auto &t : s->solvers) t.join();                  // then the requests set up for a batch
   delete s;
   return AFMPB_OK;
 }

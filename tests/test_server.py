@@ -47,6 +47,32 @@ def test_server_host_logic_without_compute():
         assert e.value.status == "ENOMEM"
 
 
+def test_batched_server_host_logic_without_compute():
+    """A batched server hands out every ticket exactly once and shuts down cleanly when
+    setups fail (no device here): the setup counter and the ready list drain."""
+    pb = _pb()
+    try:
+        import torch
+        if torch.cuda.is_available():
+            pytest.skip("host-only check; the GPU tests cover the same paths with real solves")
+    except ImportError:
+        pass
+    mol = synthetic.born_ion(subdiv=2)
+    est = pb.estimate_bytes(mol.n_nodes, 1)
+    with pb.Server(bytes_budget=8 * est, max_slots=3, max_batch=4, solvers=2) as s:
+        tickets = [s.submit_molecule(mol) for _ in range(7)]
+        for t in tickets:
+            r = s.wait(t, 120)
+            assert r["status"] != "OK" and r["error"]
+        info = s.info()
+    assert info["completed"] == 7 and info["failed"] == 7 and info["queued"] == 0
+    assert info["batches"] == 0                                # nothing reached the solver
+    with pytest.raises(pb.AfmpbError):
+        pb.Server(bytes_budget=est, max_slots=2, max_batch=65)
+    with pytest.raises(pb.AfmpbError):
+        pb.Server(bytes_budget=est, max_slots=2, max_batch=4, solvers=0)
+
+
 def _mix():
     """Requests of uneven size: Born ions, Kirkwood spheres and small globules."""
     k4 = synthetic.kirkwood_sphere(subdiv=4)
@@ -116,3 +142,33 @@ def test_server_admission_limits_overlap_and_reports_failures():
     e_ref = rb[0]["energy"]
     assert all(abs(r["energy"] / e_ref - 1) < 1e-6 for r in rb)
     assert info["failed"] == 1
+
+
+@pytest.mark.gpu
+def test_batched_server_results_equal_alone():
+    """With batched solves (one solver thread, fused P2P and M2L across the set-up
+    requests) each request's energy and surface solution equal its lone solve: 1e-6
+    relative on the energy, 1e-5 on f and h."""
+    pb = _pb()
+    mix = _mix()
+    alone = []
+    with pb.Server(bytes_budget=64 << 30, max_slots=1) as s:
+        for mol, kw in mix:
+            r = s.wait(s.submit_molecule(mol, want_solution=True, **kw), 600)
+            assert r["status"] == "OK", r["error"]
+            alone.append(r)
+    # four setup slots feed one solver: requests set up during a solve pile up and are
+    # solved together
+    with pb.Server(bytes_budget=64 << 30, max_slots=4, max_batch=8, solvers=1) as s:
+        tickets = [s.submit_molecule(mol, want_solution=True, **kw) for mol, kw in mix]
+        batched = [s.wait(t, 600) for t in tickets]
+        info = s.info()
+    assert info["batches"] >= 1 and info["batched_requests"] == len(mix)
+    assert info["max_batch"] >= 2, info                        # requests were solved together
+    for a, m in zip(alone, batched):
+        assert m["status"] == "OK", m["error"]
+        assert abs(m["energy"] / a["energy"] - 1) < 1e-6, (a["energy"], m["energy"])
+        for key in ("f", "h"):
+            err = np.linalg.norm(m[key] - a[key]) / np.linalg.norm(a[key])
+            assert err < 1e-5, (key, err)
+        assert m["bytes_used"] <= m["bytes_reserved"]
