@@ -444,6 +444,30 @@ def rooflines(prof, info, n, order, peaks, kind, precision, sms):
     return out, head
 
 
+def gmres_roofline(sinfo, n, peaks, kind):
+    """The Krylov side of a solve against HBM: the solve's CUDA-event time minus its
+    products' time, against the bytes its step kernels must move.  Arnoldi step j (one
+    fused reduction) reads V_0..V_j and w for the coefficients, V_0..V_j again and w
+    (read and written) for the update, w and V_{j+1} for the normalisation, ys / w and
+    V_j / xs for the FP32 product's input and output: 16 n (2 j + 8) bytes; a second
+    Gram-Schmidt pass adds 16 n (2 j + 6); a cycle's x update 16 n (k + 2).  The time also
+    holds the launch gaps and the host wait per cycle, so this is a floor on the fraction."""
+    k = int(sinfo["iters"])
+    ms = float(sinfo["ms_gmres"]) - float(sinfo["ms_matvec_total"])
+    if k <= 0 or ms <= 0:
+        return None
+    unit = 16.0 * n
+    byts = sum(unit * (2 * j + 8) for j in range(k)) + unit * (k + 2)
+    byts += int(sinfo.get("second_passes", 0)) * unit * (k + 5)         # at the mean j
+    e = {"bound": "hbm", "kernel": "GMRES Arnoldi steps (k_multidot_j, k_reduce_parts_j, k_sub_combo_j, "
+                                   "k_normalize_j, k_givens_j, k_to_xs_j, k_from_ys) and the x update",
+         "unit": "GB/s", "achieved": round(byts / (ms * 1e-3) / 1e9, 3), "peak": round(peaks["hbm_gbs"], 3),
+         "peak_kind": "measured copy bandwidth", "peak_source": kind, "ms_per_solve": round(ms, 4),
+         "work": "%d Arnoldi steps on %d unknowns: %.1f MB" % (k, 2 * n, byts / 1e6), "traffic": None}
+    e["frac"] = round(e["achieved"] / e["peak"], 4)
+    return e
+
+
 # ------------------------------------------------------------------------------------
 # oracle timing (CPU)
 # ------------------------------------------------------------------------------------
@@ -663,6 +687,7 @@ def run_gpu(args):
     # solves on the resident handle (outside the timed region): GMRES + energy latency
     lat, (sinfo, energy) = solve_latency(h, args.solve_reps)
     h.close()
+    roof_ops["gmres"] = gmres_roofline(sinfo, n, peaks, kind)
 
     # the plain FP32 path (M2L on the CUDA cores) at its own best leaf size, same workload
     plain = None
@@ -692,7 +717,8 @@ def run_gpu(args):
                      "m2l_pairs": info["n_m2l_pairs"], "m2l_rank": info["m2l_rank"],
                      "m2l_tables": info["m2l_tables"], "ms_create": [round(v, 1) for v in info["ms_create"]]},
             "solve": dict(lat, status=sinfo["status"], iters=sinfo["iters"],
-                          ms_gmres=round(sinfo["ms_gmres"], 2), res_true=sinfo["res_true"],
+                          ms_gmres=round(sinfo["ms_gmres"], 3), ms_products=round(sinfo["ms_matvec_total"], 3),
+                          second_passes=sinfo.get("second_passes"), res_true=sinfo["res_true"],
                           energy_kcal_mol=energy),
             "plain_fp32": plain}
     if args.workload == "kirkwood" and energy is not None:

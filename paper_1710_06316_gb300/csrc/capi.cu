@@ -72,8 +72,6 @@ void destroy_handle(afmpb_t *h) {
 // working sets far above it).
 constexpr int64_t kOverlapMaxNodes = 4000000;
 
-bool overlap_p2p(const afmpb_t *h) { return h->n <= kOverlapMaxNodes; }
-
 Err capture_product(afmpb_t *h, int parts, bool io = false, const float *x = nullptr, float *y = nullptr) {
   // The far-field chain (a long sequence of short, latency-bound launches) is captured
   // from a high-priority stream and P2P from a low-priority one: the kernel nodes keep the
@@ -254,6 +252,8 @@ Err create_impl(afmpb_t *h, const afmpb_mesh *mesh, const afmpb_charges *ch) {
 }  // namespace
 
 namespace afmpb {
+
+bool overlap_p2p(const afmpb_t *h) { return h->n <= kOverlapMaxNodes; }
 void keep_pool_memory() {
   static std::mutex mu;
   static std::vector<int> done;

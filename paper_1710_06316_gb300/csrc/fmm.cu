@@ -874,12 +874,17 @@ Err enqueue_far(afmpb_t *h, cudaStream_t s, StageTimer *tm, int parts) {
 }
 
 Err enqueue_p2p(afmpb_t *h, cudaStream_t s) {
-  // Six resident blocks per SM walk the leaves while the far-field chain's kernels run
-  // beside them at a higher stream priority (measured best among four to six).
+  // Beside the far-field chain, six resident blocks per SM walk the units while the
+  // chain's kernels run at a higher stream priority (measured best among four to six, and
+  // against one block per unit: 0.565 against 0.595 ms for the 163,842-node product).
+  // Alone (meshes above the overlap limit) one block per unit lets the block scheduler
+  // hand the cost-ordered units out as blocks finish, which balances better than the
+  // static deal (0.226 against 0.256 ms for the same sphere's P2P timed alone).
   int dev = 0, sms = 0;
   AFMPB_CUDA(cudaGetDevice(&dev));
   AFMPB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  const int grid = std::max(1, std::min(h->p2p_nunits, std::min(h->p2p_resident, kP2PRegBlocks) * sms));
+  const int grid = overlap_p2p(h) ? std::max(1, std::min(h->p2p_nunits, std::min(h->p2p_resident, kP2PRegBlocks) * sms))
+                                  : std::max(1, h->p2p_nunits);
   AFMPB_CUDA(cudaMemsetAsync(h->d_phi_near, 0, sizeof(float4) * h->n, s));   // split leaves add into it
   k_p2p<<<grid, kP2PThreads, 0, s>>>(h->p2p_nunits, h->d_p2p_units, h->d_leaves, h->d_p2p_ptr, h->d_p2p_idx, h->d_box_begin,
                                                   h->d_box_end, h->d_box_center, h->d_pos, h->d_nrm, h->d_xs,

@@ -410,6 +410,7 @@ Err build_fmm(afmpb_t *h);
 constexpr int kFarUp = 1, kFarM2L = 2, kFarDown = 4, kFarAll = 7;
 Err enqueue_far(afmpb_t *h, cudaStream_t s, StageTimer *tm = nullptr, int parts = kFarAll);   // P2M .. L2P
 Err enqueue_p2p(afmpb_t *h, cudaStream_t s);          // P2P into d_phi_near
+bool overlap_p2p(const afmpb_t *h);                   // P2P runs beside the far-field chain
 // The P2P arguments of a handle, with a stop flag for batched launches.
 P2PReq p2p_req_of(const afmpb_t *h, const int *active);
 // One P2P launch over the units of several problems (unit.w names the problem); every
