@@ -229,6 +229,71 @@ def globule_sweep_leg(args, stream):
 
 
 # ------------------------------------------------------------------------------------
+# M2L methods at equal accuracy: dense (compressed) translations against plane waves
+# ------------------------------------------------------------------------------------
+def m2l_compare_leg(args, mol, stream):
+    """The list-2 translations of the headline workload done four ways -- dense compressed
+    on the tensor cores (the default), dense compressed in FP32 at the default cutoff and
+    at a tighter one, and plane waves (the exponential expansions of FMM97, quadratures
+    to 1e-6 of 1/r, FP32) -- each with its product time (CUDA events, L2 flushed), its M2L
+    stage time and the product's relative L2 error against the FP64 oracle on 512 sampled
+    rows (smooth x).  Equal accuracy is read off the error column."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import paper_1710_06316_gb300 as pb
+    import synthetic
+
+    n = mol.n_nodes
+    xh = synthetic.smooth_unknowns(mol.xyz, 3)
+    x = torch.tensor(xh.astype(np.float32), device="cuda")
+    y = torch.empty_like(x)
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    rows = np.sort(np.random.default_rng(6).choice(n, 512, replace=False))
+    y1, y2 = oracle.Oracle.for_molecule(mol).matvec_rows(rows, xh)
+    ref = np.concatenate([y1, y2])
+    out = []
+    for name, kw in [("dense_tensor_core", dict(precision=1)), ("dense_fp32", dict(precision=0)),
+                     ("dense_fp32_tight", dict(precision=0, m2l_tol=1e-7)),
+                     ("plane_wave_fp32", dict(precision=0, m2l_method=1))]:
+        rec = {"method": name}
+        try:
+            t0 = time.perf_counter()
+            h = pb.Handle.for_molecule(mol, order=args.order, stream=stream.cuda_stream, **kw)
+            rec["setup_s"] = round(time.perf_counter() - t0, 3)
+        except pb.AfmpbError as e:
+            rec["error"] = str(e)[:120]
+            out.append(rec)
+            continue
+        for _ in range(3):
+            h.matvec(x, y)
+        ev = []
+        for i in range(10):
+            flush.fill_(float(i))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            h.matvec(x, y)
+            b.record(stream)
+            ev.append((a, b))
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in ev) / len(ev)
+        yv = y.cpu().numpy().astype(np.float64)
+        got = np.concatenate([yv[rows], yv[n + rows]])
+        prof = h.profile(reps=3, flush=flush, flush_bytes=FLUSH_BYTES)
+        st = {k: v for k, v, _ in prof["stages"]}
+        m2l = st.get("m2l", 0.0) + st.get("compress", 0.0) + st.get("expand", 0.0)
+        info = h.info()
+        rec.update({"ms_per_product": round(ms, 4), "m2l_ms": round(m2l, 4),
+                    "rel_err_vs_oracle_sampled": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
+                    "m2l_rank": info["m2l_rank"], "device_gb": round(info["device_bytes"] / 2**30, 2)})
+        h.close()
+        out.append(rec)
+    return {"workload": "%d nodes, order %d; m2l_ms = M2L stage (with the basis changes of the compressed "
+                        "forms)" % (n, args.order), "methods": out}
+
+
+# ------------------------------------------------------------------------------------
 # capsid scale: one 10M-node solve
 # ------------------------------------------------------------------------------------
 def capsid_leg(args, stream):
@@ -729,6 +794,8 @@ def run_gpu(args):
         line["solve"]["energy_rel_err_vs_series"] = abs(energy / e_ref - 1)
     if rank == 0 and world == 1 and not args.no_serving:
         line["serving"] = serving_leg(args)
+    if rank == 0 and world == 1 and not args.no_m2l_compare:
+        line["m2l_compare"] = m2l_compare_leg(args, mol, stream)
     if rank == 0 and world == 1 and not args.no_sweep:
         line["globule_sweep"] = globule_sweep_leg(args, stream)
     if rank == 0 and world == 1 and not args.no_capsid:
@@ -776,6 +843,7 @@ def main():
     ap.add_argument("--serve-restart", type=int, default=80)
     ap.add_argument("--no-capsid", action="store_true")
     ap.add_argument("--no-sweep", action="store_true")
+    ap.add_argument("--no-m2l-compare", action="store_true")
     ap.add_argument("--capsid-steps", type=int, default=10)
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--solve-reps", type=int, default=100)

@@ -108,7 +108,13 @@ typedef struct {
     int orth;            /* Arnoldi orthogonalisation: 0 = classical Gram-Schmidt applied
                             twice (three reductions per step, default); 1 = one reduction per
                             step (AFMPB_ORTH_ONE_REDUCTION) */
+    int m2l_method;      /* list-2 translations: 0 = dense (compressed, tensor cores with
+                            precision 1; default); 1 = plane waves (AFMPB_M2L_PLANE_WAVE):
+                            the exponential expansions of FMM97 (Sec. 3.1) in six directions,
+                            quadratures accurate to 1e-6 of 1/r, FP32 CUDA cores            */
 } afmpb_options;
+
+#define AFMPB_M2L_PLANE_WAVE 1
 
 /* afmpb_options.restart: no restart -- the Krylov dimension is the largest whose FP64
  * basis fits in half of the free device memory at the first solve (at most

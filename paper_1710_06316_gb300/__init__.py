@@ -43,7 +43,7 @@ class Options(C.Structure):
     _fields_ = [("leaf_cap", C.c_int), ("restart", C.c_int), ("max_restart", C.c_int),
                 ("abs_tol", C.c_double), ("precision", C.c_int), ("near_c", C.c_double),
                 ("stream", C.c_void_p), ("max_level", C.c_int), ("m2l_tol", C.c_double),
-                ("charge_fmm", C.c_int), ("orth", C.c_int)]
+                ("charge_fmm", C.c_int), ("orth", C.c_int), ("m2l_method", C.c_int)]
 
 
 class SolveInfo(C.Structure):
@@ -273,7 +273,7 @@ class Handle:
     def __init__(self, xyz, tri, atoms=None, q=None, eps_in=1.0, eps_out=80.0, kappa=0.0,
                  order=6, tol=1e-6, leaf_cap=0, restart=0, max_restart=0, abs_tol=0.0,
                  precision=0, near_c=0.0, stream=None, max_level=0, normals=None, m2l_tol=0.0,
-                 charge_fmm=0, orth=0):
+                 charge_fmm=0, orth=0, m2l_method=0):
         self._lib = load()
         self._xyz = _np(xyz, np.float64)
         self._tri = _np(tri, np.int32)
@@ -290,7 +290,8 @@ class Handle:
         if st is not None and not isinstance(st, int):
             st = int(getattr(st, "cuda_stream", st))
         opt = Options(int(leaf_cap), int(restart), int(max_restart), float(abs_tol), int(precision),
-                      float(near_c), st, int(max_level), float(m2l_tol), int(charge_fmm), int(orth))
+                      float(near_c), st, int(max_level), float(m2l_tol), int(charge_fmm), int(orth),
+                      int(m2l_method))
         h = C.c_void_p()
         rc = self._lib.afmpb_create(C.byref(mesh), None if ch is None else C.byref(ch),
                                     float(eps_in), float(eps_out), float(kappa), int(order),

@@ -184,6 +184,8 @@ Err check_params(const afmpb_mesh *mesh, double eps_in, double eps_out, double k
         o->max_restart < 0 || o->max_level < 0 || o->max_level > kMaxLevel)
       return make_err(AFMPB_EINVAL, "negative option or max_level above 20");
     if (o->orth != 0 && o->orth != AFMPB_ORTH_ONE_REDUCTION) return make_err(AFMPB_EINVAL, "orth must be 0 or 1");
+    if (o->m2l_method != 0 && o->m2l_method != AFMPB_M2L_PLANE_WAVE)
+      return make_err(AFMPB_EINVAL, "m2l_method must be 0 or 1");
     if (o->abs_tol < 0 || !(o->near_c >= 0)) return make_err(AFMPB_EINVAL, "abs_tol and near_c must be >= 0");
     if (o->precision != 0 && o->precision != 1) return make_err(AFMPB_EINVAL, "precision must be 0 or 1");
     if (o->restart > 4096) return make_err(AFMPB_EINVAL, "restart above 4096");

@@ -800,7 +800,8 @@ Err launch_far(afmpb_t *h, cudaStream_t s, StageTimer *tm, int parts) {
   const auto &T = h->shape;
   const float inv_ebar = (float)(1.0 / h->ebar);
   const int mthreads = ((2 * N3 + 31) / 32) * 32;
-  const bool compressed = !h->m2l_groups.empty() && h->m2l_rank > 0;
+  const bool plane_wave = h->opt.m2l_method == AFMPB_M2L_PLANE_WAVE;
+  const bool compressed = !h->m2l_groups.empty() && h->m2l_rank > 0 && !plane_wave;
   if (parts & kFarUp) {
   AFMPB_CUDA(cudaMemsetAsync(h->d_L, 0, sizeof(float) * (size_t)T.nbox * 2 * N3, s));
   k_p2m<N><<<T.nleaf, 256, 0, s>>>(T.nleaf, h->d_leaves, h->d_box_begin, h->d_box_end, h->d_box_center, h->d_pos,
@@ -817,7 +818,9 @@ Err launch_far(afmpb_t *h, cudaStream_t s, StageTimer *tm, int parts) {
   if (compressed) {
     AFMPB_TRY(enqueue_m2l_svd(h, s, tm, parts));  // marks compress, m2l, expand itself
   } else if (!h->m2l_groups.empty() && (parts & kFarM2L)) {
-    if (h->opt.precision == 1) {
+    if (plane_wave) {
+      AFMPB_TRY(enqueue_m2l_pw(h, s));
+    } else if (h->opt.precision == 1) {
       AFMPB_TRY(enqueue_m2l_tc(h, s));
     } else {
       constexpr int RT = 64, PC = 32;
@@ -971,6 +974,7 @@ Err build_fmm(afmpb_t *h) {
     AFMPB_TRY(A.alloc(&h->d_L, (size_t)T.nbox * 2 * N3, "L"));
     AFMPB_CUDA(cudaMemsetAsync(h->d_M, 0, sizeof(float) * (size_t)T.nbox * 2 * N3, s));
     if (h->opt.precision == 1) AFMPB_TRY(build_m2l_tc(h));
+    if (h->opt.m2l_method == AFMPB_M2L_PLANE_WAVE) AFMPB_TRY(build_m2l_pw(h));
     return Err{};
   }
   const size_t N6 = (size_t)N3 * N3;
@@ -1000,6 +1004,7 @@ Err build_fmm(afmpb_t *h) {
     default: return make_err(AFMPB_EINVAL, "fmm_order must be in [2, 8]");
   }
   if (h->opt.precision == 1) AFMPB_TRY(build_m2l_tc(h));
+  if (h->opt.m2l_method == AFMPB_M2L_PLANE_WAVE) AFMPB_TRY(build_m2l_pw(h));
   return Err{};
 }
 

@@ -347,6 +347,14 @@ struct afmpb_t {
   std::vector<uint32_t> ts_rkey;   // host copy of the runs: (block, offset) key and entry count,
   std::vector<int32_t> ts_rcnt;    // to cut the items again
   afmpb::TSItem *d_ts_items = nullptr;
+  // plane-wave M2L (options.m2l_method = 1): tables per (level, kernel), targets by direction
+  std::vector<int> pw_set_of, pw_level_t0;
+  int pw_pmax = 0, pw_maxlev = 0, pw_ntargets = 0;
+  void *d_pw_sets = nullptr;
+  int *d_pw_pnode = nullptr, *d_pw_pb = nullptr, *d_pw_perm = nullptr;
+  float *d_pw_exs = nullptr, *d_pw_ext = nullptr, *d_pw_om = nullptr;
+  float2 *d_pw_phx = nullptr, *d_pw_phy = nullptr, *d_pw_shift = nullptr, *d_pw_X = nullptr;
+  int *d_pw_tbox = nullptr, *d_pw_dptr = nullptr, *d_pw_esrc = nullptr, *d_pw_eslot = nullptr;
   int4 *d_ts_runs = nullptr;       // (offset slot, first entry, end entry, -)
   uint64_t *d_ts_ent = nullptr;    // row in the block << 32 | source box
   uint16_t *d_ts_tiles = nullptr;  // C_o as BF16 hi/lo B-operand tiles [table][slot][2][R x R]
@@ -436,7 +444,10 @@ Err autotune_leaf_cap(afmpb_t *h, afmpb_autotune_report *rep);
 int autotune_cached_cap(int precision, int order, double kappa, int64_t n);   // 0 if none
 // m2l_svd.cu: compressed translations; *compressed = false leaves the full ones in use
 Err build_m2l_svd(afmpb_t *h, bool *compressed);
-Err enqueue_m2l_svd(afmpb_t *h, cudaStream_t s, StageTimer *tm = nullptr, int parts = kFarAll);   // compress, translate, expand
+Err enqueue_m2l_svd(afmpb_t *h, cudaStream_t s, StageTimer *tm = nullptr, int parts = kFarAll);
+// m2l_pw.cu: plane-wave M2L (d_M -> d_L, FP32) and its tables
+Err build_m2l_pw(afmpb_t *h);
+Err enqueue_m2l_pw(afmpb_t *h, cudaStream_t s);   // compress, translate, expand
 Err alloc_wait_flag(afmpb_t *h);       // the mapped error flag of the bounded waits (once per handle)
 // Waits for the handle's stream, then reports (and clears) the bounded-wait flag: *flag = 1
 // when a wait of work queued on the handle expired since the last report.

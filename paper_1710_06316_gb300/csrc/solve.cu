@@ -762,7 +762,9 @@ namespace {
 // Fused M2L needs every problem on the target-stationary kernel with one compressed rank.
 bool batch_fuses_m2l(afmpb_t *const *hs, int k) {
   for (int i = 0; i < k; ++i)
-    if (!m2l_ts_applies(hs[i]) || hs[i]->m2l_rank != hs[0]->m2l_rank || hs[i]->m2l_groups.empty()) return false;
+    if (!m2l_ts_applies(hs[i]) || hs[i]->m2l_rank != hs[0]->m2l_rank || hs[i]->m2l_groups.empty() ||
+        hs[i]->opt.m2l_method != 0)
+      return false;
   return true;
 }
 

@@ -126,6 +126,7 @@ _BAD_OPTIONS = [
     ("NaN near_c", dict(near_c=float("nan")), b"near_c"),
     ("precision 2", dict(precision=2), b"precision"),
     ("charge_fmm -1", dict(charge_fmm=-1), b"charge_fmm"),
+    ("unknown M2L method", dict(m2l_method=2), b"m2l_method"),
 ]
 
 
