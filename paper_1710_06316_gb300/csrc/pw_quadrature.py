@@ -19,9 +19,9 @@ terms, so 1/r is the scale of each term.
 The t-nodes are chosen from a fine composite Gauss-Legendre rule on [0, 60] by a
 column-pivoted QR of the sampled integrand family (the numerical rank of the family at
 EPS), the weights by least squares on those columns; M_j is the smallest even count whose
-trapezoid error, weighted by w_j exp(-(k + t_j)), stays below EPS / (2 n_nodes) of 1/r at
-its largest, EPS / n of it with n nodes (bounds that do not add coherently: the check
-at the end evaluates the discrete double sum on fresh samples and must stay below EPS).
+trapezoid error, weighted by w_j exp(-(k + t_j)), stays below 4 EPS / n (n nodes) of the
+smallest 1/r -- per-node bounds that do not add up coherently, so the check at the end
+evaluates the whole discrete double sum on fresh samples and must stay below EPS.
 
 Run:  python pw_quadrature.py  (writes pw_quadrature.h next to this file; numpy + scipy)
 """
