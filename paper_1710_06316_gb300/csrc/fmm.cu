@@ -137,16 +137,27 @@ __global__ void __launch_bounds__(256) k_p2m(int nleaf, const int32_t *__restric
 // Apply the separable 1-D operator S2[c] along the three axes of a box of weights.
 // transpose == false: out[i,j,k] = sum S[cx][i][i'] S[cy][j][j'] S[cz][k][k'] in[i',j',k']
 // transpose == true : out[i',j',k'] = sum S[cx][i][i'] ... in[i,j,k]
+// The operators come from shared memory (sS[c][row][q], staged by stage_m2m_ops): a
+// thread's row depends on its output point, and constant-memory reads that differ across
+// a warp are serialised.
 template <int N>
-__device__ __forceinline__ float apply_axis(const float *in, int m, int axis, int c, bool transpose) {
+__device__ __forceinline__ void stage_m2m_ops(float *sS) {
+  for (int e = threadIdx.x; e < 2 * N * N; e += blockDim.x) {
+    const int c = e / (N * N), r = (e / N) % N, q = e % N;
+    sS[e] = c_m2m[N][c * kMaxOrder * kMaxOrder + r * kMaxOrder + q];
+  }
+}
+
+template <int N>
+__device__ __forceinline__ float apply_axis(const float *in, const float *sS, int m, int axis, int c, bool transpose) {
   const int i = m / (N * N), j = (m / N) % N, k = m % N;
-  const float *S = c_m2m[N] + c * kMaxOrder * kMaxOrder;
+  const float *S = sS + c * N * N;
   float acc = 0.0f;
 #pragma unroll
   for (int q = 0; q < N; ++q) {
     int src;
     int row = axis == 0 ? i : (axis == 1 ? j : k);
-    float w = transpose ? S[q * kMaxOrder + row] : S[row * kMaxOrder + q];
+    float w = transpose ? S[q * N + row] : S[row * N + q];
     if (axis == 0) src = q * N * N + j * N + k;
     else if (axis == 1) src = i * N * N + q * N + k;
     else src = i * N * N + j * N + q;
@@ -160,10 +171,11 @@ template <int N>
 __global__ void k_m2m(int ls, const int32_t *__restrict__ child0, const int32_t *__restrict__ nchild,
                       const int4 *__restrict__ anchor, float *__restrict__ M) {
   constexpr int N3 = N * N * N;
-  __shared__ float s0[2 * N3], s1[2 * N3];
+  __shared__ float s0[2 * N3], s1[2 * N3], sS[2 * N * N];
   const int b = ls + blockIdx.x;
   const int nc = nchild[b];
   if (nc == 0) return;
+  stage_m2m_ops<N>(sS);
   const int e = threadIdx.x;               // (kernel, m)
   const bool act = e < 2 * N3;
   const int kt = e / N3, m = e % N3;
@@ -173,15 +185,15 @@ __global__ void k_m2m(int ls, const int32_t *__restrict__ child0, const int32_t 
     const int4 a = anchor[c];
     if (act) s0[e] = M[(size_t)c * 2 * N3 + e];
     __syncthreads();
-    float v = act ? apply_axis<N>(s0 + kt * N3, m, 2, a.z & 1, false) : 0.0f;
+    float v = act ? apply_axis<N>(s0 + kt * N3, sS, m, 2, a.z & 1, false) : 0.0f;
     __syncthreads();
     if (act) s1[e] = v;
     __syncthreads();
-    v = act ? apply_axis<N>(s1 + kt * N3, m, 1, a.y & 1, false) : 0.0f;
+    v = act ? apply_axis<N>(s1 + kt * N3, sS, m, 1, a.y & 1, false) : 0.0f;
     __syncthreads();
     if (act) s0[e] = v;
     __syncthreads();
-    v = act ? apply_axis<N>(s0 + kt * N3, m, 0, a.x & 1, false) : 0.0f;
+    v = act ? apply_axis<N>(s0 + kt * N3, sS, m, 0, a.x & 1, false) : 0.0f;
     acc += v;
     __syncthreads();
   }
@@ -193,24 +205,25 @@ template <int N>
 __global__ void k_l2l(int ls, const int32_t *__restrict__ parent, const int4 *__restrict__ anchor,
                       float *__restrict__ L) {
   constexpr int N3 = N * N * N;
-  __shared__ float s0[2 * N3], s1[2 * N3];
+  __shared__ float s0[2 * N3], s1[2 * N3], sS[2 * N * N];
   const int b = ls + blockIdx.x;
   const int p = parent[b];
+  stage_m2m_ops<N>(sS);
   const int4 a = anchor[b];
   const int e = threadIdx.x;
   const bool act = e < 2 * N3;
   const int kt = e / N3, m = e % N3;
   if (act) s0[e] = L[(size_t)p * 2 * N3 + e];
   __syncthreads();
-  float v = act ? apply_axis<N>(s0 + kt * N3, m, 0, a.x & 1, true) : 0.0f;
+  float v = act ? apply_axis<N>(s0 + kt * N3, sS, m, 0, a.x & 1, true) : 0.0f;
   __syncthreads();
   if (act) s1[e] = v;
   __syncthreads();
-  v = act ? apply_axis<N>(s1 + kt * N3, m, 1, a.y & 1, true) : 0.0f;
+  v = act ? apply_axis<N>(s1 + kt * N3, sS, m, 1, a.y & 1, true) : 0.0f;
   __syncthreads();
   if (act) s0[e] = v;
   __syncthreads();
-  v = act ? apply_axis<N>(s0 + kt * N3, m, 2, a.z & 1, true) : 0.0f;
+  v = act ? apply_axis<N>(s0 + kt * N3, sS, m, 2, a.z & 1, true) : 0.0f;
   if (act) L[(size_t)b * 2 * N3 + e] += v;
 }
 
