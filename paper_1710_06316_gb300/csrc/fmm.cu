@@ -66,70 +66,78 @@ __device__ __forceinline__ void cheb_basis(float x, float s[N], float ds[N]) {
 // ------------------------------------------------------------------------------------
 template <int N>
 __global__ void __launch_bounds__(256) k_p2m(int nleaf, const int32_t *__restrict__ leaves,
-                                             const int32_t *__restrict__ bbeg, const int32_t *__restrict__ bend,
-                                             const dbl4 *__restrict__ center, const float4 *__restrict__ pos,
-                                             const float4 *__restrict__ nrm, const float2 *__restrict__ xs,
-                                             float inv_ebar, float *__restrict__ M) {
-  constexpr int N3 = N * N * N;
+                                            const int32_t *__restrict__ bbeg, const int32_t *__restrict__ bend,
+                                            const dbl4 *__restrict__ center, const float4 *__restrict__ pos,
+                                            const float4 *__restrict__ nrm, const float2 *__restrict__ xs,
+                                            float inv_ebar, float *__restrict__ M) {
+  // Four leaves per CTA, a group of 64 threads each (synchronised by its own named
+  // barrier); thread (j, k) of a group holds the N weights (i, j, k) of both sums, so a
+  // node's y-z factors are formed once and applied along the whole x axis:
+  //   A[ijk] += c Sx[i] (Sy[j] Sz[k]),  B[ijk] += dSx[i] (g_x Sy Sz) + Sx[i] (g_y dSy Sz + g_z Sy dSz)
+  // (one leaf per 64-thread CTA ran P2M faster alone but held up P2P beside it: the
+  // product took 0.565 against 0.532 ms on the 163,842-node sphere)
+  constexpr int N2 = N * N, N3 = N2 * N;
   constexpr int CH = 64;
-  __shared__ float sb[CH][6 * N];   // sx, dsx, sy, dsy, sz, dsz
-  __shared__ float sw[CH][4];       // c, g nx / w, g ny / w, g nz / w
-  const int b = leaves[blockIdx.x];
+  static_assert(N2 <= 64, "one thread per (j, k)");
+  __shared__ float sxa[4][CH][2 * N];   // Sx, dSx
+  __shared__ float syza[4][CH][4 * N];  // Sy, dSy, Sz, dSz
+  __shared__ float4 swa[4][CH];         // c, g nx / w, g ny / w, g nz / w
+  const int grp = threadIdx.x >> 6, gt = threadIdx.x & 63;
+  const int li = blockIdx.x * 4 + grp;
+  if (li >= nleaf) return;                              // whole groups only (named barriers below)
+  float (*sx)[2 * N] = sxa[grp];
+  float (*syz)[4 * N] = syza[grp];
+  float4 *sw = swa[grp];
+  const int b = leaves[li];
   const int beg = bbeg[b], end = bend[b];
   const float invw = (float)(1.0 / center[b].w);
-  float accA[(N3 + 255) / 256], accB[(N3 + 255) / 256];
+  const bool act = gt < N2;
+  const int j = act ? gt / N : 0, k = act ? gt % N : 0;
+  float A[N], B[N];
 #pragma unroll
-  for (int r = 0; r < (N3 + 255) / 256; ++r) accA[r] = accB[r] = 0.0f;
+  for (int i = 0; i < N; ++i) A[i] = B[i] = 0.0f;
   for (int c0 = beg; c0 < end; c0 += CH) {
     const int cnt = min(CH, end - c0);
-    for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
-      float4 p = pos[c0 + j], q = nrm[c0 + j];
-      float2 fh = xs[c0 + j];
+    if (gt < cnt) {
+      const int t = gt;
+      const float4 p = pos[c0 + t], q = nrm[c0 + t];
+      const float2 fh = xs[c0 + t];
       float s[N], ds[N];
       cheb_basis<N>(p.x * invw, s, ds);
 #pragma unroll
-      for (int m = 0; m < N; ++m) { sb[j][m] = s[m]; sb[j][N + m] = ds[m]; }
+      for (int m = 0; m < N; ++m) { sx[t][m] = s[m]; sx[t][N + m] = ds[m]; }
       cheb_basis<N>(p.y * invw, s, ds);
 #pragma unroll
-      for (int m = 0; m < N; ++m) { sb[j][2 * N + m] = s[m]; sb[j][3 * N + m] = ds[m]; }
+      for (int m = 0; m < N; ++m) { syz[t][m] = s[m]; syz[t][N + m] = ds[m]; }
       cheb_basis<N>(p.z * invw, s, ds);
 #pragma unroll
-      for (int m = 0; m < N; ++m) { sb[j][4 * N + m] = s[m]; sb[j][5 * N + m] = ds[m]; }
-      float g = -p.w * fh.x * invw;
-      sw[j][0] = p.w * fh.y;
-      sw[j][1] = g * q.x;
-      sw[j][2] = g * q.y;
-      sw[j][3] = g * q.z;
+      for (int m = 0; m < N; ++m) { syz[t][2 * N + m] = s[m]; syz[t][3 * N + m] = ds[m]; }
+      const float g = -p.w * fh.x * invw;
+      sw[t] = make_float4(p.w * fh.y, g * q.x, g * q.y, g * q.z);
     }
-    __syncthreads();
+    asm volatile("bar.sync %0, 64;" ::"r"(grp + 1) : "memory");
+    if (act) {
+      for (int t = 0; t < cnt; ++t) {
+        const float sy = syz[t][j], dsy = syz[t][N + j], sz = syz[t][2 * N + k], dsz = syz[t][3 * N + k];
+        const float4 w = sw[t];
+        const float yz = sy * sz;
+        const float pa = w.x * yz, pb = w.y * yz, pq = fmaf(w.z, dsy * sz, w.w * (sy * dsz));
 #pragma unroll
-    for (int r = 0; r < (N3 + 255) / 256; ++r) {
-      const int m = threadIdx.x + 256 * r;
-      if (m < N3) {
-        const int i = m / (N * N), jj = (m / N) % N, k = m % N;
-        float a = accA[r], bb = accB[r];
-        for (int t = 0; t < cnt; ++t) {
-          const float sx = sb[t][i], dsx = sb[t][N + i];
-          const float sy = sb[t][2 * N + jj], dsy = sb[t][3 * N + jj];
-          const float sz = sb[t][4 * N + k], dsz = sb[t][5 * N + k];
-          const float syz = sy * sz;
-          a = fmaf(sw[t][0], sx * syz, a);
-          bb = fmaf(sw[t][1], dsx * syz, bb);
-          bb = fmaf(sw[t][2], sx * dsy * sz, bb);
-          bb = fmaf(sw[t][3], sx * sy * dsz, bb);
+        for (int i = 0; i < N; ++i) {
+          const float x = sx[t][i], dx = sx[t][N + i];
+          A[i] = fmaf(pa, x, A[i]);
+          B[i] = fmaf(pb, dx, fmaf(pq, x, B[i]));
         }
-        accA[r] = a;
-        accB[r] = bb;
       }
     }
-    __syncthreads();
+    asm volatile("bar.sync %0, 64;" ::"r"(grp + 1) : "memory");
   }
+  if (act) {
 #pragma unroll
-  for (int r = 0; r < (N3 + 255) / 256; ++r) {
-    const int m = threadIdx.x + 256 * r;
-    if (m < N3) {
-      M[(size_t)b * 2 * N3 + m] = fmaf(accB[r], inv_ebar, accA[r]);
-      M[(size_t)b * 2 * N3 + N3 + m] = accA[r] + accB[r];
+    for (int i = 0; i < N; ++i) {
+      const int m = (i * N + j) * N + k;
+      M[(size_t)b * 2 * N3 + m] = fmaf(B[i], inv_ebar, A[i]);
+      M[(size_t)b * 2 * N3 + N3 + m] = A[i] + B[i];
     }
   }
 }
@@ -817,7 +825,7 @@ Err launch_far(afmpb_t *h, cudaStream_t s, StageTimer *tm, int parts) {
   const bool compressed = !h->m2l_groups.empty() && h->m2l_rank > 0 && !plane_wave;
   if (parts & kFarUp) {
   AFMPB_CUDA(cudaMemsetAsync(h->d_L, 0, sizeof(float) * (size_t)T.nbox * 2 * N3, s));
-  k_p2m<N><<<T.nleaf, 256, 0, s>>>(T.nleaf, h->d_leaves, h->d_box_begin, h->d_box_end, h->d_box_center, h->d_pos,
+  k_p2m<N><<<(T.nleaf + 3) / 4, 256, 0, s>>>(T.nleaf, h->d_leaves, h->d_box_begin, h->d_box_end, h->d_box_center, h->d_pos,
                                    h->d_nrm, h->d_xs, inv_ebar, h->d_M);
   AFMPB_TRY(check_launch("k_p2m"));
   if (tm) tm->mark("p2m", 1);
