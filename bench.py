@@ -509,16 +509,18 @@ def rooflines(prof, info, n, order, peaks, kind, precision, sms):
     return out, head
 
 
-def gmres_roofline(sinfo, n, peaks, kind):
+def gmres_roofline(sinfo, n, peaks, kind, ms_product):
     """The Krylov side of a solve against HBM: the solve's CUDA-event time minus its
-    products' time, against the bytes its step kernels must move.  Arnoldi step j (one
+    products' time (each at ms_product, the timed product of the same handle: iters +
+    restarts + 1 products), against the bytes its step kernels must move.  Arnoldi step j (one
     fused reduction) reads V_0..V_j and w for the coefficients, V_0..V_j again and w
     (read and written) for the update, w and V_{j+1} for the normalisation, ys / w and
     V_j / xs for the FP32 product's input and output: 16 n (2 j + 8) bytes; a second
     Gram-Schmidt pass adds 16 n (2 j + 6); a cycle's x update 16 n (k + 2).  The time also
     holds the launch gaps and the host wait per cycle, so this is a floor on the fraction."""
     k = int(sinfo["iters"])
-    ms = float(sinfo["ms_gmres"]) - float(sinfo["ms_matvec_total"])
+    products = k + int(sinfo.get("restarts", 0)) + 1
+    ms = float(sinfo["ms_gmres"]) - products * float(ms_product)
     if k <= 0 or ms <= 0:
         return None
     unit = 16.0 * n
@@ -752,7 +754,7 @@ def run_gpu(args):
     # solves on the resident handle (outside the timed region): GMRES + energy latency
     lat, (sinfo, energy) = solve_latency(h, args.solve_reps)
     h.close()
-    roof_ops["gmres"] = gmres_roofline(sinfo, n, peaks, kind)
+    roof_ops["gmres"] = gmres_roofline(sinfo, n, peaks, kind, ms_step)
 
     # the plain FP32 path (M2L on the CUDA cores) at its own best leaf size, same workload
     plain = None
