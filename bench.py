@@ -526,8 +526,8 @@ def gmres_roofline(sinfo, n, peaks, kind, ms_product):
     unit = 16.0 * n
     byts = sum(unit * (2 * j + 8) for j in range(k)) + unit * (k + 2)
     byts += int(sinfo.get("second_passes", 0)) * unit * (k + 5)         # at the mean j
-    e = {"bound": "hbm", "kernel": "GMRES Arnoldi steps (k_multidot_j, k_reduce_parts_j, k_sub_combo_j, "
-                                   "k_normalize_j, k_givens_j, k_to_xs_j, k_from_ys) and the x update",
+    e = {"bound": "hbm", "kernel": "GMRES Arnoldi steps (classical Gram-Schmidt twice: k_gs_first, k_gs_second, "
+                                   "k_gs_norm, k_gs_normalize) and the cycle's x update, with the host's waits",
          "unit": "GB/s", "achieved": round(byts / (ms * 1e-3) / 1e9, 3), "peak": round(peaks["hbm_gbs"], 3),
          "peak_kind": "measured copy bandwidth", "peak_source": kind, "ms_per_solve": round(ms, 4),
          "work": "%d Arnoldi steps on %d unknowns: %.1f MB" % (k, 2 * n, byts / 1e6), "traffic": None}

@@ -398,13 +398,11 @@ __global__ void k_normalize_j(int64_t n, const double *__restrict__ w, const dou
   v[n + p] = w[n + p] * inv;
 }
 
-// Givens update of Hessenberg column j (as k_givens, j from the device)
-__global__ void k_givens_j(const int *__restrict__ gm, int m, const double *__restrict__ hcol, double *__restrict__ H,
-                           double *__restrict__ cs, double *__restrict__ sn, double *__restrict__ g,
-                           double *__restrict__ res, const int *__restrict__ guard) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  if (guard && *guard == 0) return;
-  const int j = gm[0];
+// Givens update of Hessenberg column j: the new column from hcol, the earlier rotations
+// applied, a new rotation zeroing its subdiagonal, the residual estimate |g[j + 1]|.
+__device__ __forceinline__ void givens_update(int j, int m, const double *__restrict__ hcol, double *__restrict__ H,
+                                              double *__restrict__ cs, double *__restrict__ sn, double *__restrict__ g,
+                                              double *__restrict__ res) {
   double *col = H + (int64_t)j * (m + 1);
   for (int i = 0; i <= j + 1; ++i) col[i] = hcol[i];
   for (int i = 0; i < j; ++i) {
@@ -421,6 +419,15 @@ __global__ void k_givens_j(const int *__restrict__ gm, int m, const double *__re
   g[j + 1] = -sn[j] * g[j];
   g[j] = cs[j] * g[j];
   res[0] = fabs(g[j + 1]);
+}
+
+// (as k_givens, j from the device)
+__global__ void k_givens_j(const int *__restrict__ gm, int m, const double *__restrict__ hcol, double *__restrict__ H,
+                           double *__restrict__ cs, double *__restrict__ sn, double *__restrict__ g,
+                           double *__restrict__ res, const int *__restrict__ guard) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (guard && *guard == 0) return;
+  givens_update(gm[0], m, hcol, H, cs, sn, g, res);
 }
 
 // End of a step: j += 1; continue the WHILE loop while the Givens residual estimate is
@@ -465,6 +472,155 @@ __global__ void k_cycle_start(int *__restrict__ gm) {
   }
 }
 
+// ---- the default Arnoldi step (classical Gram-Schmidt twice) in four kernels ----------------
+// Each reduction is folded by the block that finishes last (an atomic ticket in gm[5..7]):
+// it sums every block's partial in block order, one warp per coefficient with a fixed
+// shuffle tree, so the result does not depend on which block ends last.  The three
+// passes over the basis are: w = y with the dots V^T w; w -= V h1 with the dots V^T w;
+// w -= V h2 with ||w||^2.  The third pass's last block also applies the Givens update and
+// the stop test of Eq. 7; the fourth kernel normalises V_{j+1} and writes it, in FP32, as
+// the next product's input.
+__device__ __forceinline__ bool last_block_of(int *ticket) {
+  __shared__ int s_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(ticket, 1) == (int)gridDim.x - 1;
+  __syncthreads();
+  if (s_last) __threadfence();
+  return s_last != 0;
+}
+
+__device__ __forceinline__ void fold_parts(int nb, int cnt, const double *part, int stride, double *out) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int i = warp; i < cnt; i += nw) {
+    double s = 0.0;
+    for (int b = lane; b < nb; b += 32) s += __ldcg(part + (int64_t)b * stride + i);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) out[i] = s;
+  }
+}
+
+// w = ys (FP32 -> FP64); h1 = V_{0..j}^T w
+__global__ void __launch_bounds__(kRedThreads) k_gs_first(int64_t len, int *__restrict__ gm, const double *__restrict__ V,
+                                                          int64_t ldv, const float *__restrict__ ys,
+                                                          double *__restrict__ w, double *__restrict__ part, int stride,
+                                                          double *__restrict__ hcol, const int *__restrict__ guard) {
+  if (guard && *guard == 0) return;
+  __shared__ double sh[32];
+  const int nv = gm[0] + 1;
+  const int64_t chunk = (len + gridDim.x - 1) / gridDim.x;
+  const int64_t lo = blockIdx.x * chunk, hi = min(len, lo + chunk);
+  for (int64_t k = lo + threadIdx.x; k < hi; k += blockDim.x) w[k] = (double)ys[k];
+  for (int i = 0; i < nv; ++i) {
+    const double *v = V + (int64_t)i * ldv;
+    double a = 0.0;
+    for (int64_t k = lo + threadIdx.x; k < hi; k += blockDim.x) a = fma(v[k], w[k], a);
+    a = block_sum(a, sh);
+    if (threadIdx.x == 0) part[(int64_t)blockIdx.x * stride + i] = a;
+  }
+  if (last_block_of(gm + 5)) {
+    fold_parts(gridDim.x, nv, part, stride, hcol);
+    if (threadIdx.x == 0) gm[5] = 0;
+  }
+}
+
+// w -= V h1; h2 = V^T w; h1 += h2
+__global__ void __launch_bounds__(kRedThreads) k_gs_second(int64_t len, int *__restrict__ gm, const double *__restrict__ V,
+                                                           int64_t ldv, double *__restrict__ w, double *__restrict__ part,
+                                                           int stride, double *__restrict__ hcol, double *__restrict__ hcol2,
+                                                           const int *__restrict__ guard) {
+  if (guard && *guard == 0) return;
+  __shared__ double sh[32];
+  const int nv = gm[0] + 1;
+  const int64_t chunk = (len + gridDim.x - 1) / gridDim.x;
+  const int64_t lo = blockIdx.x * chunk, hi = min(len, lo + chunk);
+  for (int64_t k = lo + threadIdx.x; k < hi; k += blockDim.x) {
+    double a = 0.0;
+    for (int i = 0; i < nv; ++i) a = fma(hcol[i], V[(int64_t)i * ldv + k], a);
+    w[k] -= a;
+  }
+  for (int i = 0; i < nv; ++i) {
+    const double *v = V + (int64_t)i * ldv;
+    double a = 0.0;
+    for (int64_t k = lo + threadIdx.x; k < hi; k += blockDim.x) a = fma(v[k], w[k], a);
+    a = block_sum(a, sh);
+    if (threadIdx.x == 0) part[(int64_t)blockIdx.x * stride + i] = a;
+  }
+  if (last_block_of(gm + 6)) {
+    fold_parts(gridDim.x, nv, part, stride, hcol2);
+    __syncthreads();
+    for (int i = threadIdx.x; i < nv; i += blockDim.x) hcol[i] += hcol2[i];
+    if (threadIdx.x == 0) gm[6] = 0;
+  }
+}
+
+// w -= V h2; ||w||; Givens update; j += 1 and the stop test (batch: the problem's running
+// flag, else the condition of the graph's WHILE loop)
+__global__ void __launch_bounds__(kRedThreads) k_gs_norm(int64_t len, int *__restrict__ gm, int m,
+                                                         const double *__restrict__ V, int64_t ldv, double *__restrict__ w,
+                                                         double *__restrict__ part, int stride, double *__restrict__ hcol,
+                                                         const double *__restrict__ hcol2, double *__restrict__ H,
+                                                         double *__restrict__ cs, double *__restrict__ sn,
+                                                         double *__restrict__ g, double *__restrict__ res,
+                                                         const double *__restrict__ tol, int batch,
+                                                         cudaGraphConditionalHandle loop, const int *__restrict__ guard) {
+  if (guard && *guard == 0) return;
+  __shared__ double sh[32];
+  const int j = gm[0], nv = j + 1;
+  const int64_t chunk = (len + gridDim.x - 1) / gridDim.x;
+  const int64_t lo = blockIdx.x * chunk, hi = min(len, lo + chunk);
+  double q = 0.0;
+  for (int64_t k = lo + threadIdx.x; k < hi; k += blockDim.x) {
+    double a = 0.0;
+    for (int i = 0; i < nv; ++i) a = fma(hcol2[i], V[(int64_t)i * ldv + k], a);
+    const double x = w[k] - a;
+    w[k] = x;
+    q = fma(x, x, q);
+  }
+  q = block_sum(q, sh);
+  if (threadIdx.x == 0) part[(int64_t)blockIdx.x * stride] = q;
+  if (last_block_of(gm + 7)) {
+    __shared__ double s_nrm;
+    fold_parts(gridDim.x, 1, part, stride, &s_nrm);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      gm[7] = 0;
+      hcol[j + 1] = sqrt(s_nrm);
+      givens_update(j, m, hcol, H, cs, sn, g, res);
+      gm[0] = j + 1;
+      gm[1] += 1;
+      const bool go = j + 1 < m && res[0] > tol[0];      // a NaN residual stops as well
+      if (batch) {
+        if (!go) {
+          gm[4] = 0;
+          gm[2] = 0;
+        }
+      } else {
+        cudaGraphSetConditional(loop, go ? 1u : 0u);
+      }
+    }
+  }
+}
+
+// V_{j+1} = w / ||w|| (j + 1 = gm[0] after the step end) and its FP32 copy for the next product
+__global__ void k_gs_normalize(int64_t n, const int *__restrict__ gm, const double *__restrict__ w,
+                               const double *__restrict__ hcol, double *__restrict__ V, int64_t n2,
+                               float2 *__restrict__ xs, const int *__restrict__ guard) {
+  if (guard && *guard == 0) return;
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  const int j = gm[0];
+  const double inv = 1.0 / hcol[j];
+  double *v = V + (int64_t)j * n2;
+  const double a = w[p] * inv, b = w[n + p] * inv;
+  v[p] = a;
+  v[n + p] = b;
+  xs[p] = make_float2((float)a, (float)b);
+}
+
+__global__ void k_step_end_b(int *__restrict__ gm, int m, const double *__restrict__ res,
+                             const double *__restrict__ tol);
+
 namespace {
 
 // Krylov dimension of the no-restart mode: the largest whose basis fits in half of the
@@ -490,14 +646,35 @@ Err restart_length(afmpb_t *h, int *m) {
 // product) orthogonalisation, normalisation and the Givens update.  `act` (nullable) is a
 // batch problem's running flag: every kernel returns at once while it is 0.
 Err enqueue_step_head(afmpb_t *h, cudaStream_t cap, const int *act) {
+  if (h->opt.orth == 0) return Err{};     // the previous step (or the cycle start) wrote xs
   const int64_t n = h->n, n2 = 2 * n;
   k_to_xs_j<<<div_up(n, 256), 256, 0, cap>>>(n, h->d_V, n2, h->d_gm_int, h->d_xs, act);
   return check_launch("k_to_xs_j");
 }
 
-Err enqueue_step_tail(afmpb_t *h, int m, cudaStream_t cap, const int *act) {
+// The product input V_j in FP32 at a cycle start (the fused step writes it for the next
+// step itself).
+Err enqueue_cycle_xs(afmpb_t *h, cudaStream_t s, const int *act) {
+  if (h->opt.orth != 0) return Err{};
+  const int64_t n = h->n, n2 = 2 * n;
+  k_to_xs_j<<<div_up(n, 256), 256, 0, s>>>(n, h->d_V, n2, h->d_gm_int, h->d_xs, act);
+  return check_launch("k_to_xs_j (cycle start)");
+}
+
+Err enqueue_step_tail(afmpb_t *h, int m, cudaStream_t cap, const int *act, bool batch, cudaGraphConditionalHandle loop) {
   const int64_t n = h->n, n2 = 2 * n;
   const int orth = h->opt.orth;
+  if (orth == 0) {
+    const int nb = red_blocks(n2), stride = m + 2;
+    int *gm = h->d_gm_int;
+    k_gs_first<<<nb, kRedThreads, 0, cap>>>(n2, gm, h->d_V, n2, h->d_ys, h->d_w, h->d_part, stride, h->d_hcol, act);
+    k_gs_second<<<nb, kRedThreads, 0, cap>>>(n2, gm, h->d_V, n2, h->d_w, h->d_part, stride, h->d_hcol, h->d_hcol2, act);
+    k_gs_norm<<<nb, kRedThreads, 0, cap>>>(n2, gm, m, h->d_V, n2, h->d_w, h->d_part, stride, h->d_hcol, h->d_hcol2,
+                                           h->d_H, h->d_cs, h->d_sn, h->d_g, h->d_scal + 2, h->d_scal + 4,
+                                           batch ? 1 : 0, loop, act);
+    k_gs_normalize<<<div_up(n, 256), 256, 0, cap>>>(n, gm, h->d_w, h->d_hcol, h->d_V, n2, h->d_xs, act);
+    return check_launch("arnoldi step (fused)");
+  }
   const int *gm = h->d_gm_int;
   int *gmw = h->d_gm_int;
   const int *guard = gm + 2;              // second-pass flag: 0 whenever the problem is stopped
@@ -531,6 +708,8 @@ Err enqueue_step_tail(afmpb_t *h, int m, cudaStream_t cap, const int *act) {
   }
   k_normalize_j<<<nb_el, 256, 0, cap>>>(n, h->d_w, h->d_hcol, gm, h->d_V, n2, act);
   k_givens_j<<<1, 1, 0, cap>>>(gm, m, h->d_hcol, h->d_H, h->d_cs, h->d_sn, h->d_g, h->d_scal + 2, act);
+  if (batch) k_step_end_b<<<1, 1, 0, cap>>>(gmw, m, h->d_scal + 2, h->d_scal + 4);
+  else k_step_end<<<1, 1, 0, cap>>>(gmw, m, h->d_scal + 2, h->d_scal + 4, loop);
   return check_launch("arnoldi step");
 }
 
@@ -563,11 +742,7 @@ Err build_cycle_graph(afmpb_t *h, int m) {
   AFMPB_CUDA(cudaStreamBeginCaptureToGraph(cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
   Err e = enqueue_step_head(h, cap, nullptr);
   if (e.ok()) e = enqueue_product_kernels(h, cap);
-  if (e.ok()) e = enqueue_step_tail(h, m, cap, nullptr);
-  if (e.ok()) {
-    k_step_end<<<1, 1, 0, cap>>>(h->d_gm_int, m, h->d_scal + 2, h->d_scal + 4, loop);
-    e = check_launch("arnoldi step");
-  }
+  if (e.ok()) e = enqueue_step_tail(h, m, cap, nullptr, false, loop);
   cudaGraph_t out = nullptr;
   cudaError_t ce = cudaStreamEndCapture(cap, &out);
   if (!e.ok()) return e;
@@ -667,6 +842,7 @@ Err run_solve(afmpb_t *h, afmpb_solve_info *info) {
     k_set_beta<<<1, 1, 0, s>>>(h->d_g, m, h->d_scal + 1);
     k_cycle_start<<<1, 1, 0, s>>>(h->d_gm_int);
     AFMPB_TRY(check_launch("gmres start"));
+    AFMPB_TRY(enqueue_cycle_xs(h, s, nullptr));
     // the Arnoldi steps of the cycle: one graph launch, no host synchronisation inside
     AFMPB_CUDA(cudaGraphLaunch(h->graph_cycle, s));
     // x += V y, H y = g
@@ -851,9 +1027,7 @@ Err build_batch_graph(afmpb_t *const *hs, int k, const int *ms, bool fuse_m2l, c
       AFMPB_TRY(enqueue_far(h, si[i], nullptr, kFarDown));
       AFMPB_CUDA(cudaStreamWaitEvent(si[i], ev_p, 0));
       AFMPB_TRY(enqueue_combine(h, si[i], AFMPB_PART_ALL));
-      AFMPB_TRY(enqueue_step_tail(h, ms[i], si[i], act));
-      k_step_end_b<<<1, 1, 0, si[i]>>>(h->d_gm_int, ms[i], h->d_scal + 2, h->d_scal + 4);
-      AFMPB_TRY(check_launch("k_step_end_b"));
+      AFMPB_TRY(enqueue_step_tail(h, ms[i], si[i], act, true, loop));
       AFMPB_CUDA(cudaEventRecord(ev_e[i], si[i]));
       AFMPB_CUDA(cudaStreamWaitEvent(cap, ev_e[i], 0));
     }
@@ -958,6 +1132,7 @@ Err run_solve_batch(afmpb_t *const *hs, int k, afmpb_solve_info *infos, afmpb_st
       }
       k_cycle_start_b<<<1, 1, 0, h->stream>>>(h->d_gm_int, S.running ? 1 : 0);
       AFMPB_TRY(check_launch("batch cycle start"));
+      if (S.running) AFMPB_TRY(enqueue_cycle_xs(h, h->stream, nullptr));
       AFMPB_CUDA(cudaStreamSynchronize(h->stream));
     }
     if (nrun == 0) break;
