@@ -30,7 +30,8 @@ namespace {
 
 constexpr int kGramTile = 32;       // Gram matrix tile (32 x 32 per CTA)
 constexpr int kRowsPerCta = 8;      // rows of T = K_o Q (and of C) per CTA
-constexpr int kChunkBoxes = 32;     // boxes per compress / expand CTA (a multiple of 4)
+constexpr int kChunkBoxes = 16;     // boxes per compress / expand CTA (a multiple of 4; 16 against 32:
+                                    // expand 32 -> 27 us on the 163,842-node sphere)
 constexpr int kMaxN3 = kMaxOrder * kMaxOrder * kMaxOrder;
 constexpr int kMaxRank = 192;       // largest compressed size (M2L staging in shared memory)
 
@@ -309,8 +310,9 @@ Err launch_box_basis(cudaStream_t s, dim3 grid, int K, int ncol, const int4 *chu
                      const int *table_rank, int yuk_min, const float *A, const float *X, float *Y,
                      __nv_bfloat16 *Y16 = nullptr) {
   const size_t smem = basis_smem(K, ncol);
+  const int nthr = std::min(256, (((kChunkBoxes / 4) * (ncol / 4) + 31) / 32) * 32);   // threads with a tile
   switch (basis_tiles(ncol)) {
-    case 1: k_box_basis<1, ACCUM><<<grid, 256, smem, s>>>(K, ncol, chunks, level_table, table_rank, yuk_min, A, X, Y, Y16); break;
+    case 1: k_box_basis<1, ACCUM><<<grid, nthr, smem, s>>>(K, ncol, chunks, level_table, table_rank, yuk_min, A, X, Y, Y16); break;
     case 2: k_box_basis<2, ACCUM><<<grid, 256, smem, s>>>(K, ncol, chunks, level_table, table_rank, yuk_min, A, X, Y, Y16); break;
     case 3: k_box_basis<3, ACCUM><<<grid, 256, smem, s>>>(K, ncol, chunks, level_table, table_rank, yuk_min, A, X, Y, Y16); break;
     default: k_box_basis<4, ACCUM><<<grid, 256, smem, s>>>(K, ncol, chunks, level_table, table_rank, yuk_min, A, X, Y, Y16); break;
