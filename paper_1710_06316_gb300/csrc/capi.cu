@@ -56,6 +56,9 @@ void destroy_handle(afmpb_t *h) {
   if (h->ev_t0) cudaEventDestroy(h->ev_t0);
   if (h->ev_t1) cudaEventDestroy(h->ev_t1);
   if (h->side) cudaStreamDestroy(h->side);
+  if (h->side2) cudaStreamDestroy(h->side2);
+  if (h->ev_fork2) cudaEventDestroy(h->ev_fork2);
+  if (h->ev_join2) cudaEventDestroy(h->ev_join2);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   delete h;
 }
@@ -210,9 +213,12 @@ Err create_impl(afmpb_t *h, const afmpb_mesh *mesh, const afmpb_charges *ch) {
     int lo = 0, hi = 0;
     AFMPB_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
     AFMPB_CUDA(cudaStreamCreateWithPriority(&h->side, cudaStreamNonBlocking, lo));   // P2P: lowest
+    AFMPB_CUDA(cudaStreamCreateWithPriority(&h->side2, cudaStreamNonBlocking, hi));  // P2L: with the chain
   }
   AFMPB_CUDA(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
   AFMPB_CUDA(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+  AFMPB_CUDA(cudaEventCreateWithFlags(&h->ev_fork2, cudaEventDisableTiming));
+  AFMPB_CUDA(cudaEventCreateWithFlags(&h->ev_join2, cudaEventDisableTiming));
   AFMPB_CUDA(cudaEventCreate(&h->ev_t0));
   AFMPB_CUDA(cudaEventCreate(&h->ev_t1));
   auto lap = [&](int i) {

@@ -823,8 +823,24 @@ Err launch_far(afmpb_t *h, cudaStream_t s, StageTimer *tm, int parts) {
   const int mthreads = ((2 * N3 + 31) / 32) * 32;
   const bool plane_wave = h->opt.m2l_method == AFMPB_M2L_PLANE_WAVE;
   const bool compressed = !h->m2l_groups.empty() && h->m2l_rank > 0 && !plane_wave;
+  // P2L adds into L, which the compressed M2L does not touch (it writes Lc; the expansion
+  // adds Lc into L afterwards): in a whole product it runs on a branch of its own from the
+  // zeroed L to just before the expansion, beside the upward pass and the M2L.
+  const bool p2l_beside = compressed && parts == kFarAll && !tm && h->side2 && h->n_xbox > 0;
+  auto launch_p2l = [&](cudaStream_t st) -> Err {
+    k_p2l<N><<<(unsigned)h->n_xbox, 256, 0, st>>>(h->d_xbox, h->d_x_ptr, h->d_x_idx, h->d_box_begin, h->d_box_end,
+                                                  h->d_box_center, h->d_pos, h->d_nrm, h->d_xs, inv_ebar,
+                                                  (float)h->kappa, h->d_L);
+    return check_launch("k_p2l");
+  };
   if (parts & kFarUp) {
   AFMPB_CUDA(cudaMemsetAsync(h->d_L, 0, sizeof(float) * (size_t)T.nbox * 2 * N3, s));
+  if (p2l_beside) {
+    AFMPB_CUDA(cudaEventRecord(h->ev_fork2, s));
+    AFMPB_CUDA(cudaStreamWaitEvent(h->side2, h->ev_fork2, 0));
+    AFMPB_TRY(launch_p2l(h->side2));
+    AFMPB_CUDA(cudaEventRecord(h->ev_join2, h->side2));
+  }
   k_p2m<N><<<(T.nleaf + 3) / 4, 256, 0, s>>>(T.nleaf, h->d_leaves, h->d_box_begin, h->d_box_end, h->d_box_center, h->d_pos,
                                    h->d_nrm, h->d_xs, inv_ebar, h->d_M);
   AFMPB_TRY(check_launch("k_p2m"));
@@ -836,7 +852,11 @@ Err launch_far(afmpb_t *h, cudaStream_t s, StageTimer *tm, int parts) {
   }
   if (tm) tm->mark("m2m", std::max(0, T.nlevel - 3));
   }
-  if (compressed) {
+  if (compressed && p2l_beside) {
+    AFMPB_TRY(enqueue_m2l_svd(h, s, tm, kFarUp | kFarM2L));
+    AFMPB_CUDA(cudaStreamWaitEvent(s, h->ev_join2, 0));
+    AFMPB_TRY(enqueue_m2l_svd(h, s, tm, kFarDown));
+  } else if (compressed) {
     AFMPB_TRY(enqueue_m2l_svd(h, s, tm, parts));  // marks compress, m2l, expand itself
   } else if (!h->m2l_groups.empty() && (parts & kFarM2L)) {
     if (plane_wave) {
@@ -854,12 +874,7 @@ Err launch_far(afmpb_t *h, cudaStream_t s, StageTimer *tm, int parts) {
   }
   if (tm && !compressed) tm->mark("m2l", h->m2l_groups.empty() ? 0 : 1);
   if (!(parts & kFarDown)) return Err{};
-  if (h->n_xbox > 0) {
-    k_p2l<N><<<(unsigned)h->n_xbox, 256, 0, s>>>(h->d_xbox, h->d_x_ptr, h->d_x_idx, h->d_box_begin,
-                                                        h->d_box_end, h->d_box_center, h->d_pos, h->d_nrm, h->d_xs,
-                                                        inv_ebar, (float)h->kappa, h->d_L);
-    AFMPB_TRY(check_launch("k_p2l"));
-  }
+  if (h->n_xbox > 0 && !p2l_beside) AFMPB_TRY(launch_p2l(s));
   if (tm) tm->mark("p2l", h->n_xbox > 0 ? 1 : 0);
   for (int level = 3; level < T.nlevel; ++level) {
     int ls = T.lvl_start[level], nl = T.lvl_start[level + 1] - ls;

@@ -253,6 +253,8 @@ struct afmpb_t {
   cudaStream_t stream = nullptr;   // handle stream (user's or own)
   bool own_stream = false;
   cudaStream_t side = nullptr;     // second stream: P2P beside the far-field chain
+  cudaStream_t side2 = nullptr;    // third stream: P2L beside the upward pass and the M2L
+  cudaEvent_t ev_fork2 = nullptr, ev_join2 = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaEvent_t ev_t0 = nullptr, ev_t1 = nullptr;
 
