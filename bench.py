@@ -711,7 +711,9 @@ def run_gpu(args):
         return max_over_ranks(sum(ms) / len(ms)), clk
 
     def solve_latency(hh, reps):
-        """Repeated solves (GMRES + energy) on a resident handle: p50 / p99 / solves/s."""
+        """Repeated solves (GMRES + energy) on a resident handle: p50 / p99 / solves/s, after
+        one untimed solve (it captures the handle's cycle graph)."""
+        hh.solve(raise_on_noconv=False)
         lat = []
         out = None
         for _ in range(reps):
