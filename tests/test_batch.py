@@ -127,3 +127,28 @@ def test_batch_rejects_bad_batches():
         with pytest.raises(pb.AfmpbError) as e:
             pb.solve_batch([h1, h0])
         assert e.value.status == "ESTATE"
+
+
+@pytest.mark.gpu
+def test_batch_of_one_and_per_problem_statuses():
+    """A batch of one equals the lone solve; a problem that cannot converge within its
+    restart budget reports ENOCONV while the others of the batch still reach OK."""
+    pb = _pb()
+    born = synthetic.born_ion()
+    k4 = synthetic.kirkwood_sphere(subdiv=4)
+    f1, h1, i1, E1 = _solve_alone(pb, born, order=6, precision=1)
+    with pb.Handle.for_molecule(born, order=6, precision=1) as h:
+        [(f, hh, info)] = pb.solve_batch([h])
+        E = h.energy()
+    assert info["status"] == "OK" and abs(E / E1 - 1) < 1e-6
+    assert relerr(np.concatenate([f, hh]), np.concatenate([f1, h1])) < 1e-5
+    hs = [pb.Handle.for_molecule(born, order=6, precision=1),
+          pb.Handle.for_molecule(k4, order=6, precision=1, restart=2, max_restart=1),   # cannot reach 1e-6
+          pb.Handle.for_molecule(k4, order=6, precision=1)]
+    try:
+        out = pb.solve_batch(hs, raise_on_noconv=False)
+    finally:
+        for h in hs:
+            h.close()
+    assert [o[2]["status"] for o in out] == ["OK", "ENOCONV", "OK"]
+    assert out[1][2]["restarts"] == 1 and out[1][2]["iters"] <= 4

@@ -121,3 +121,19 @@ def test_plane_wave_solve_and_energy():
     assert info["status"] == "OK"
     assert _rel(np.concatenate([f, hh]), np.concatenate([ref["f"], ref["h"]])) < 1e-4
     assert abs(E / ref["energy"] - 1) < 1e-4
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("order,kappa", [(4, 0.104), (8, 0.104), (6, 0.0)])
+def test_plane_wave_orders_and_laplace_only(order, kappa):
+    """Other expansion orders (4, 8: the tables and index maps are per order) and kappa = 0
+    (only the Laplace band) against the dense product without compression."""
+    import paper_1710_06316_gb300 as pb
+    mol = synthetic.kirkwood_sphere(subdiv=4, kappa=kappa)
+    x = synthetic.random_unknowns(mol.n_nodes, 17)
+    with pb.Handle.for_molecule(mol, order=order, precision=0, m2l_method=1, leaf_cap=32) as h:
+        assert h.info()["n_m2l_pairs"] > 0
+        y_pw = _gpu_matvec(h, x)
+    with pb.Handle.for_molecule(mol, order=order, precision=0, m2l_tol=-1.0, leaf_cap=32) as h:
+        y_dense = _gpu_matvec(h, x)
+    assert _rel(y_pw, y_dense) < 1e-5
