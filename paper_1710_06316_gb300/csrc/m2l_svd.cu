@@ -198,11 +198,17 @@ __device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_
 // compress: A = Q (K = n^3, ncol = r), X = M, Y = Mc;  expand: A = Q^T (K = r,
 // ncol = n^3), X = Lc, Y = L (accumulated).  The chunk's X vectors (X[k][box]) and slabs
 // of kSlabRows rows of A reach shared memory by cp.async in a kStages-deep pipeline, so
-// the copy of slab s + 2 overlaps the products of slab s.  A thread owns 4 boxes x 4
+// the copy of slab s + 2 overlaps the products of slab s (a K of one or two slabs gets
+// one or two buffers: the expand of r = 64 fits three CTAs per SM instead of two).  A thread owns 4 boxes x 4
 // columns per tile (two 16-byte shared loads per 16 FMAs) and up to TILES tiles; ncol is
 // a multiple of 4.
 constexpr int kSlabRows = 32;
 constexpr int kStages = 3;
+// buffers the pipeline needs for K rows: slab s + 2 is issued while slab s is used
+__host__ __device__ __forceinline__ int basis_stages(int K) {
+  const int nslab = (K + kSlabRows - 1) / kSlabRows;
+  return nslab < kStages ? (nslab > 0 ? nslab : 1) : kStages;
+}
 template <int TILES, bool ACCUM>
 __global__ void __launch_bounds__(256) k_box_basis(int K, int ncol, const int4 *__restrict__ chunks,
                                                    const int *__restrict__ level_table,
@@ -222,21 +228,31 @@ __global__ void __launch_bounds__(256) k_box_basis(int K, int ncol, const int4 *
   const int ceff = ACCUM ? ncol : table_rank[table];
   const int slab_elems = kSlabRows * ncol;
   const int nslab = (Keff + kSlabRows - 1) / kSlabRows;
+  const int nst = basis_stages(K);                     // slab buffers (fewer when K has fewer slabs)
   // X: the box index runs fastest so that the shared stores hit distinct banks
   for (int e = threadIdx.x; e < Keff * kChunkBoxes; e += blockDim.x) {
     const int j = e % kChunkBoxes, k = e / kChunkBoxes;
     const bool v = j < ch.y;
     cp_async4(Xs + e, v ? X + ((size_t)(ch.x + j) * 2 + kt) * K + k : X, v);
   }
+  // a thread's 16-byte groups of a slab: (row, group) from threadIdx.x, advanced by
+  // blockDim.x groups with a carry (no division in the copy loop)
+  const int c4n = ceff / 4;
+  const int c4d = max(c4n, 1);
+  const int r_first = c4n > 0 ? (int)threadIdx.x / c4d : kSlabRows, c_first = (int)threadIdx.x % c4d;
+  const int r_step = (int)blockDim.x / c4d, c_step = (int)blockDim.x % c4d;
   auto issue_slab = [&](int sl) {
     if (sl < nslab) {
-      float *dst = As + (size_t)(sl % kStages) * slab_elems;
+      float *dst = As + (size_t)(sl % nst) * slab_elems;
       const int k0 = sl * kSlabRows;
-      const int rows = min(kSlabRows, Keff - k0), c4n = ceff / 4;
-      for (int g = threadIdx.x; g < kSlabRows * c4n; g += blockDim.x) {   // 16-byte groups used
-        const int r = g / c4n, c = 4 * (g % c4n);
+      const int rows = min(kSlabRows, Keff - k0);
+      const float *src = At + (size_t)k0 * ncol;
+      for (int r = r_first, c = c_first; r < kSlabRows;) {   // 16-byte groups used
         const bool v = r < rows;
-        cp_async16(dst + r * ncol + c, v ? At + (size_t)(k0 + r) * ncol + c : At, v);
+        cp_async16(dst + r * ncol + 4 * c, v ? src + (size_t)r * ncol + 4 * c : At, v);
+        r += r_step;
+        c += c_step;
+        if (c >= c4n) { c -= c4n; ++r; }
       }
     }
     cp_async_commit();                                 // empty groups keep the count
@@ -250,7 +266,7 @@ __global__ void __launch_bounds__(256) k_box_basis(int K, int ncol, const int4 *
     cp_async_wait_1();                                 // X and slab sl have landed
     __syncthreads();
     issue_slab(sl + 2);                                // its buffer held slab sl - 1
-    const float *as = As + (size_t)(sl % kStages) * slab_elems;
+    const float *as = As + (size_t)(sl % nst) * slab_elems;
     const int k0 = sl * kSlabRows, rows = min(kSlabRows, Keff - k0);
 #pragma unroll
     for (int t = 0; t < TILES; ++t) {
@@ -302,7 +318,7 @@ __global__ void __launch_bounds__(256) k_box_basis(int K, int ncol, const int4 *
 
 int basis_tiles(int ncol) { return ((kChunkBoxes / 4) * (ncol / 4) + 255) / 256; }
 size_t basis_smem(int K, int ncol) {
-  return sizeof(float) * ((size_t)K * kChunkBoxes + (size_t)kStages * kSlabRows * ncol);
+  return sizeof(float) * ((size_t)K * kChunkBoxes + (size_t)basis_stages(K) * kSlabRows * ncol);
 }
 
 template <bool ACCUM>
