@@ -87,11 +87,16 @@ Err capture_product(afmpb_t *h, int parts, bool io = false, const float *x = nul
   AFMPB_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
   Err e;
   if (io) e = enqueue_gather(h, cap, x);
+  int cparts = parts;
   if (e.ok() && (parts & AFMPB_PART_FAR)) {
     if (overlap_p2p(h)) {
       cudaEventRecord(h->ev_fork, cap);
       cudaStreamWaitEvent(h->side, h->ev_fork, 0);
       e = enqueue_p2p(h, h->side);
+      if (e.ok() && (parts & AFMPB_PART_NEAR)) {   // the near SpMV beside the rest of the chain
+        e = enqueue_near_fold(h, h->side);
+        cparts |= kNearFolded;
+      }
       cudaEventRecord(h->ev_join, h->side);
       if (e.ok()) e = enqueue_far(h, cap);
       cudaStreamWaitEvent(cap, h->ev_join, 0);
@@ -100,7 +105,7 @@ Err capture_product(afmpb_t *h, int parts, bool io = false, const float *x = nul
       if (e.ok()) e = enqueue_far(h, cap);
     }
   }
-  if (e.ok()) e = enqueue_combine(h, cap, parts);
+  if (e.ok()) e = enqueue_combine(h, cap, cparts);
   if (e.ok() && io) e = enqueue_scatter(h, cap, y);
   cudaGraph_t g = nullptr;
   cudaError_t ce = cudaStreamEndCapture(cap, &g);
@@ -306,18 +311,7 @@ Err product_from64(afmpb_t *h, cudaStream_t s, const double *v) {
     struct StreamGuard { cudaStream_t s; ~StreamGuard() { cudaStreamDestroy(s); } } sg{cap};
     AFMPB_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
     Err e = enqueue_to_xs(h, cap, v);
-    if (e.ok() && overlap_p2p(h)) {
-      cudaEventRecord(h->ev_fork, cap);
-      cudaStreamWaitEvent(h->side, h->ev_fork, 0);
-      e = enqueue_p2p(h, h->side);
-      cudaEventRecord(h->ev_join, h->side);
-      if (e.ok()) e = enqueue_far(h, cap);
-      cudaStreamWaitEvent(cap, h->ev_join, 0);
-    } else if (e.ok()) {
-      e = enqueue_p2p(h, cap);
-      if (e.ok()) e = enqueue_far(h, cap);
-    }
-    if (e.ok()) e = enqueue_combine(h, cap, AFMPB_PART_ALL);
+    if (e.ok()) e = enqueue_product_kernels(h, cap);
     cudaGraph_t g = nullptr;
     cudaError_t ce = cudaStreamEndCapture(cap, &g);
     if (!e.ok() || ce != cudaSuccess) {
@@ -364,10 +358,15 @@ Err product_from64(afmpb_t *h, cudaStream_t s, const double *v) {
 // the combine.  Used by the GMRES cycle graph.
 Err enqueue_product_kernels(afmpb_t *h, cudaStream_t cap) {
   Err e;
+  int cparts = AFMPB_PART_ALL;
   if (overlap_p2p(h)) {
     cudaEventRecord(h->ev_fork, cap);
     cudaStreamWaitEvent(h->side, h->ev_fork, 0);
     e = enqueue_p2p(h, h->side);
+    if (e.ok()) {                                  // the near SpMV beside the rest of the chain
+      e = enqueue_near_fold(h, h->side);
+      cparts |= kNearFolded;
+    }
     cudaEventRecord(h->ev_join, h->side);
     if (e.ok()) e = enqueue_far(h, cap);
     cudaStreamWaitEvent(cap, h->ev_join, 0);
@@ -375,7 +374,7 @@ Err enqueue_product_kernels(afmpb_t *h, cudaStream_t cap) {
     e = enqueue_p2p(h, cap);
     if (e.ok()) e = enqueue_far(h, cap);
   }
-  if (e.ok()) e = enqueue_combine(h, cap, AFMPB_PART_ALL);
+  if (e.ok()) e = enqueue_combine(h, cap, cparts);
   return e;
 }
 

@@ -961,7 +961,73 @@ Err enqueue_p2p_batch(const P2PReq *d_reqs, const int4 *d_units, int nunits, int
   return check_launch("k_p2p_batch");
 }
 
+// The near-field correction of Eq. 5 folded into the P2P sums, on the P2P branch right
+// after P2P, so that it overlaps the rest of the far-field chain instead of following it:
+//   PhiL <- PhiL - sum_near (dB f - dA h),   dn PhiL <- dn PhiL - sum_near (dD f - dC h)
+// (the combine subtracts PhiL and dn PhiL, so the correction enters with its own sign).
+// Eight lanes per row walk the near-field CSR, as in k_combine.
+__global__ void __launch_bounds__(256) k_near_fold(int64_t n, const float2 *__restrict__ xs,
+                                                   const int64_t *__restrict__ nptr, const int32_t *__restrict__ ncol,
+                                                   const float4 *__restrict__ ncoef, float4 *__restrict__ pnear) {
+  const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t p = gid >> 3;
+  const int sub = threadIdx.x & 7;
+  const bool row = p < n;           // every lane stays for the shuffles below
+  float a1 = 0.f, a2 = 0.f;
+  if (row) {
+    for (int64_t j = nptr[p] + sub; j < nptr[p + 1]; j += 8) {
+      const float4 c = ncoef[j];
+      const float2 x = xs[ncol[j]];
+      a1 = fmaf(c.y, x.x, fmaf(-c.x, x.y, a1));
+      a2 = fmaf(c.w, x.x, fmaf(-c.z, x.y, a2));
+    }
+  }
+#pragma unroll
+  for (int o = 4; o > 0; o >>= 1) {
+    a1 += __shfl_xor_sync(0xffffffffu, a1, o, 8);
+    a2 += __shfl_xor_sync(0xffffffffu, a2, o, 8);
+  }
+  if (row && sub == 0) {
+    float4 v = pnear[p];
+    v.x -= a1;
+    v.y -= a2;
+    pnear[p] = v;
+  }
+}
+
+// Eq. 5 assembly when the near correction is already in the P2P sums: one thread per row.
+__global__ void __launch_bounds__(256) k_combine_folded(int64_t n, int parts, float alpha, float inv_ebar,
+                                                        const float2 *__restrict__ xs, const float4 *__restrict__ pfar,
+                                                        const float4 *__restrict__ pnear, float *__restrict__ ys) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  float a1 = 0.f, a2 = 0.f;
+  if (parts & AFMPB_PART_DIAG) {
+    const float2 x = xs[p];
+    a1 = alpha * x.x;
+    a2 = alpha * x.y;
+  }
+  const float4 u = pfar[p], v = pnear[p];
+  a1 += -(u.x + v.x) + (u.z + v.z);
+  a2 += -(u.y + v.y) + (u.w + v.w) * inv_ebar;
+  ys[p] = a1;
+  ys[n + p] = a2;
+}
+
+Err enqueue_near_fold(afmpb_t *h, cudaStream_t s) {
+  if (h->n == 0) return Err{};
+  k_near_fold<<<div_up(h->n * 8, 256), 256, 0, s>>>(h->n, h->d_xs, h->d_near_ptr, h->d_near_col, h->d_near_coef,
+                                                     h->d_phi_near);
+  return check_launch("k_near_fold");
+}
+
 Err enqueue_combine(afmpb_t *h, cudaStream_t s, int parts) {
+  if (parts & kNearFolded) {          // near correction already in the P2P sums (with the far part)
+    if (h->n == 0) return Err{};
+    k_combine_folded<<<div_up(h->n, 256), 256, 0, s>>>(h->n, parts, (float)h->alpha, (float)(1.0 / h->ebar), h->d_xs,
+                                                        h->d_phi_far, h->d_phi_near, h->d_ys);
+    return check_launch("k_combine_folded");
+  }
   k_combine<<<div_up(h->n * 8, 256), 256, 0, s>>>(h->n, parts, (float)h->alpha, (float)(1.0 / h->ebar), h->d_xs,
                                                    h->d_phi_far, h->d_phi_near, h->d_near_ptr, h->d_near_col,
                                                    h->d_near_coef, h->d_ys);

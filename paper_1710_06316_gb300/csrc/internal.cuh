@@ -426,6 +426,10 @@ P2PReq p2p_req_of(const afmpb_t *h, const int *active);
 // One P2P launch over the units of several problems (unit.w names the problem); every
 // problem's d_phi_near must be zeroed before it.
 Err enqueue_p2p_batch(const P2PReq *d_reqs, const int4 *d_units, int nunits, int resident, cudaStream_t s);
+// Combine flag beside the AFMPB_PART_* bits: the near correction was folded into the P2P
+// sums by enqueue_near_fold (on the P2P branch, after P2P), which requires the far part.
+constexpr int kNearFolded = 8;
+Err enqueue_near_fold(afmpb_t *h, cudaStream_t s);   // near SpMV into phi_near, after P2P
 Err enqueue_combine(afmpb_t *h, cudaStream_t s, int parts);
 Err enqueue_m2l_tc(afmpb_t *h, cudaStream_t s);       // tensor-core M2L (precision 1)
 Err build_m2l_tc(afmpb_t *h);
