@@ -906,7 +906,9 @@ afmpb_status afmpb_profile_product(afmpb_t *h, int reps, void *flush, size_t flu
       out->launches[i] = launches[i];
       kernels += launches[i];
     }
-    out->kernels_per_product = kernels;
+    // the captured product (overlapped P2P) runs the near correction as a kernel of its own
+    // on the P2P branch and an elementwise combine, where the stages above run one k_combine
+    out->kernels_per_product = kernels + (overlap_p2p(h) ? 1 : 0);
     // graph replays (the path afmpb_matvec takes), same flush between repetitions
     cudaEvent_t a = nullptr, b = nullptr;
     cudaEventCreate(&a);
