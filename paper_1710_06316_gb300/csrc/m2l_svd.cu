@@ -673,7 +673,7 @@ Err enqueue_m2l_svd(afmpb_t *h, cudaStream_t s, StageTimer *tm, int parts) {
     AFMPB_TRY(launch_box_basis<false>(s, cgrid, N3, R, h->d_m2l_chunks, h->d_level_table, h->d_table_rank,
                                        h->m2l_yuk_levels, h->d_Q, h->d_M, h->d_Mc,
                                        reinterpret_cast<__nv_bfloat16 *>(h->d_Mc16)));
-    if (tm) tm->mark("compress", 2);             // Lc memset + basis change
+    if (tm) tm->mark("compress", 1);             // Lc memset (not a kernel) + basis change
   }
   if (!(parts & kFarM2L)) {
   } else if (h->opt.precision == 1) {
