@@ -413,3 +413,24 @@ def test_bounded_wait_expires_and_the_context_stays_usable():
     with pb.Handle.for_molecule(mol, order=6, precision=1) as h:
         y = gpu_matvec(h, x)
     assert relerr(y, oracle.Oracle.for_molecule(mol).matvec(x)) < TOL_MATVEC
+
+
+@pytest.mark.parametrize("subdiv,precision", [(5, 0), (5, 1)])
+def test_folded_product_equals_its_parts(subdiv, precision):
+    """The whole product folds the near-field correction into the P2P sums on the P2P
+    branch (Eq. 5 assembled after the join); the part products keep the serialised
+    combine.  Whole = diagonal + far + near to FP32 rounding of the reordered sums, on
+    each block, with a random x; and both against the oracle at the product bar."""
+    import paper_1710_06316_gb300 as pb
+    mol = synthetic.kirkwood_sphere(subdiv=subdiv, kappa=0.2)
+    rng = np.random.default_rng(31)
+    x = rng.standard_normal(2 * mol.n_nodes)
+    with pb.Handle.for_molecule(mol, order=6, precision=precision) as h:
+        y = gpu_matvec(h, x, pb.PART_ALL)
+        parts = sum(gpu_matvec(h, x, p) for p in (pb.PART_DIAG, pb.PART_FAR, pb.PART_NEAR))
+    n = mol.n_nodes
+    for blk in (slice(0, n), slice(n, 2 * n)):
+        assert relerr(y[blk], parts[blk]) < 2e-6
+    ref = oracle.Oracle.for_molecule(mol).matvec(x)
+    for blk in (slice(0, n), slice(n, 2 * n)):
+        assert relerr(y[blk], ref[blk]) < TOL_MATVEC
