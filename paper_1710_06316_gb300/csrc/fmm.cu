@@ -527,9 +527,11 @@ __device__ __forceinline__ void p2p_pair2(const P2PTarget &t, const float4 &a, c
   const float2 Tn = __fmul2_rn(__fmul2_rn(__fmul2_rn(A, dup2(-3.0f)), npd), ri2);     // -T
   sL = __fadd2_rn(sL, __ffma2_rn(inv_e, A, cri));
   // nD accumulates -dn PhiL = c (n0.d)/r^3 - (1/eps_bar)(B - T)
-  nD = __ffma2_rn(__fmul2_rn(inv_e, dup2(-1.0f)), __fadd2_rn(B, Tn), __ffma2_rn(cc, npdG3, nD));
+  nD = __ffma2_rn(make_float2(-inv_e.x, -inv_e.y), __fadd2_rn(B, Tn), __ffma2_rn(cc, npdG3, nD));
   sY = __ffma2_rn(ex, cri, __ffma2_rn(e1, A, sY));
-  const float2 BmC = __ffma2_rn(__fmul2_rn(cc, dup2(-1.0f)), npdG3, B);             // B - c (n0.d)/r^3
+  // negated operands instead of products with -1 (measured: P2P 0.256 -> 0.2515 ms on the
+  // 163,842-node sphere)
+  const float2 BmC = __ffma2_rn(make_float2(-cc.x, -cc.y), npdG3, B);               // B - c (n0.d)/r^3
   dY = __ffma2_rn(e1, BmC, __ffma2_rn(e2, Tn, dY));
 }
 
